@@ -1,0 +1,141 @@
+"""Oracle for the block-sparse x dense product (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's
+``cpu_baseline`` / reference leg may import this package.  The product path
+(the CUDA library and its Python binding) never imports it, and this package
+imports nothing from the product.
+
+Contents
+--------
+* ``spmm(...)`` -- the FP64 definition of Section 3 (C, single thread), over
+  the inputs exactly as supplied (values widened to FP64 without rounding).
+* ``e4m3_to_f64`` -- FP8 E4M3 decoding from the format definition.
+* ``normwise_err`` -- ||Y - Y_o||_F / (||W||_F ||X||_F), the acceptance metric.
+* ``oracle.plan`` -- the integer plan / partition rules (Section 3.2, 3.3,
+  Appendix A.2, and this library's GPU work decomposition), plain Python.
+
+Parity pins: see tests/test_oracle_pins.py and tests/test_oracle_plan.py.
+Paper values: the paper prints no Y values and no worked plans (its Fig. 1
+and Fig. 7 images are missing), so no golden value comes from the paper
+itself except the App. A.2 partition formula's closed forms.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = _bind(ctypes.CDLL(path))
+    return _lib
+
+
+def _bind(lib):
+    i64, i32p = ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)
+    dp = ctypes.POINTER(ctypes.c_double)
+    lib.oracle_spmm_f64.restype = ctypes.c_int
+    lib.oracle_spmm_f64.argtypes = [i64, i64, i64, i64, i64, i32p, i32p, dp, dp,
+                                    i64, dp, i64]
+    lib.oracle_e4m3_to_f64.restype = ctypes.c_int64
+    lib.oracle_e4m3_to_f64.argtypes = [ctypes.POINTER(ctypes.c_uint8), i64, dp]
+    return lib
+
+
+def load_variant(path):
+    """Loads a separately built copy of the oracle (mutation tests)."""
+    return _bind(ctypes.CDLL(path))
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def to_f64(a):
+    """Widens a numpy array or torch CPU tensor (f16/bf16/f32/f64) to FP64
+    exactly; FP8 E4M3 bytes go through ``e4m3_to_f64``."""
+    if hasattr(a, "detach"):  # torch tensor: bf16 has no numpy dtype
+        import torch
+        t = a.detach().cpu()
+        if t.dtype == torch.float8_e4m3fn:
+            return e4m3_to_f64(t.view(torch.uint8).numpy())
+        return t.to(torch.float64).numpy()
+    return np.asarray(a, dtype=np.float64)
+
+
+def spmm(m, k, b, brow, bcol, vals, X, lib=None):
+    """Y = W.X in FP64 per Section 3.
+
+    brow, bcol: int arrays of length nnzb (block coordinates, user order).
+    vals: (nnzb, b, b) values, any float dtype, widened exactly to FP64.
+    X: (k, n).  Returns Y (m, n) float64.
+    """
+    lib = lib or _load()
+    brow = np.ascontiguousarray(brow, dtype=np.int32)
+    bcol = np.ascontiguousarray(bcol, dtype=np.int32)
+    nnzb = brow.shape[0]
+    v = np.ascontiguousarray(to_f64(vals)).reshape(nnzb * b * b)
+    x = np.ascontiguousarray(to_f64(X))
+    assert x.shape[0] == k
+    n = x.shape[1]
+    y = np.empty((m, n), dtype=np.float64)
+    rc = lib.oracle_spmm_f64(m, k, n, b, nnzb, _ptr(brow, ctypes.c_int32),
+                             _ptr(bcol, ctypes.c_int32), _ptr(v, ctypes.c_double),
+                             _ptr(x, ctypes.c_double), n, _ptr(y, ctypes.c_double), n)
+    if rc != 0:
+        raise ValueError("oracle_spmm_f64: pattern or sizes invalid (rc=%d)" % rc)
+    return y
+
+
+def e4m3_to_f64(codes, lib=None):
+    """Decodes uint8 E4M3 codes to FP64 from the format definition."""
+    lib = lib or _load()
+    c = np.ascontiguousarray(codes, dtype=np.uint8)
+    out = np.empty(c.shape, dtype=np.float64)
+    lib.oracle_e4m3_to_f64(_ptr(c.reshape(-1), ctypes.c_uint8), c.size,
+                           _ptr(out.reshape(-1), ctypes.c_double))
+    return out
+
+
+def e4m3_block_values(codes, scales):
+    """Effective FP64 values of E4M3 blocks with one FP32 scale per block:
+    v(p, i, l) = decode(code(p, i, l)) * scale[p]."""
+    d = e4m3_to_f64(codes)
+    s = np.asarray(scales, dtype=np.float64).reshape(-1, 1, 1)
+    return d * s
+
+
+def densify(m, k, b, brow, bcol, vals):
+    """Dense FP64 m x k matrix M (.) W built from the block list (truncating
+    blocks that hang over the edge, as in Section 3's ceil(m/b) grid)."""
+    W = np.zeros((m, k), dtype=np.float64)
+    v = to_f64(vals)
+    for p in range(len(brow)):
+        r0, c0 = int(brow[p]) * b, int(bcol[p]) * b
+        hi, wi = min(b, m - r0), min(b, k - c0)
+        W[r0:r0 + hi, c0:c0 + wi] = v[p, :hi, :wi]
+    return W
+
+
+def normwise_err(Y, Y_o, W_fro, X):
+    """||Y - Y_o||_F / (||W||_F * ||X||_F), all in FP64 on the host.
+
+    ``W_fro`` is ||W||_F (= || |W| ||_F).  When the denominator is 0 the
+    metric is defined as 0 if Y == 0 exactly and +inf otherwise."""
+    Y = to_f64(Y)
+    d = float(W_fro) * float(np.linalg.norm(to_f64(X)))
+    num = float(np.linalg.norm(Y - Y_o))
+    if d == 0.0:
+        return 0.0 if not np.any(Y) else float("inf")
+    return num / d
+
+
+def block_fro(vals):
+    """||W||_F from the block values (FP64)."""
+    return float(np.linalg.norm(to_f64(vals)))
