@@ -1,0 +1,240 @@
+/*
+ * spmm.h -- C ABI of the GB300 block-sparse x dense matrix product.
+ *
+ * Operation (Section 3, unnumbered equation):
+ *     Y = (M (.) W) * X,      M_ij = Mhat_{floor(i/b), floor(j/b)}
+ * W is m x k and holds its non-zeros in b x b blocks, b in {1, 4, 8, 16}
+ * (Section 3.1); X is a dense k x n matrix and Y a dense m x n matrix.
+ * Rows of Y whose block row holds no block are written as zeros.
+ *
+ * Two modes (Section 3.1, Table 1):
+ *   SPMM_STATIC  -- the pattern is fixed when the plan is built (Section 3.2).
+ *                   The host planner balances work, and the values are
+ *                   re-ordered once into the kernel's layout
+ *                   (spmm_pack_values), as the paper re-orders host-supplied
+ *                   values to its fixed distribution.
+ *   SPMM_DYNAMIC -- only the maximum block count is fixed (Section 3.3,
+ *                   Appendix A.2).  Every spmm_run takes a device-resident
+ *                   pattern and values and re-partitions them on the device.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layouts.  X is k x n and Y is m x n, row-major, with leading dimensions
+ *   ldx >= n and ldy >= n (in elements).  Values are nnzb blocks in the
+ *   pattern's order, each b x b row-major (element (i, l) of block p at
+ *   values[(p*b + i)*b + l]).  Pattern entry p is block (brow[p], bcol[p]) in
+ *   the (m/b) x (k/b) block grid.
+ * Types.  W in {F32, F16, BF16, E4M3}; X and Y share one type in {F32, F16,
+ *   BF16}.  Products accumulate in FP32; 16-bit outputs are rounded to
+ *   nearest-even from FP32.  E4M3 W carries one FP32 scale per block
+ *   (value = decode(code) * scale[p]) and needs 16-bit X.
+ * Pointers.  "d_" arguments are device pointers, "h_"/host arguments are
+ *   host pointers.  `stream` is a cudaStream_t (NULL = legacy default
+ *   stream).  Device work is enqueued asynchronously on `stream`.
+ * Ownership.  A plan owns its device copies of indices, packed values,
+ *   workspace and status word; the caller owns X, Y, values and patterns,
+ *   which must stay valid until `stream` has reached the call.
+ * Errors.  Argument, shape and host-detected pattern errors are returned
+ *   synchronously and nothing is enqueued.  Errors found on the device
+ *   (dynamic pattern invalid or over capacity, a bounded wait that timed
+ *   out) are recorded in the plan's device status word, Y is left unwritten
+ *   for a rejected dynamic pattern, and spmm_get_status reads the word.  No
+ *   C++ exception crosses this interface.  spmm_last_error() returns a
+ *   thread-local message for the last failing call on the calling thread.
+ * Concurrency.  One plan runs on one stream at a time: a call on a second
+ *   stream while the plan's previous call is still in flight on another
+ *   stream returns SPMM_ERR_BUSY.  Different plans are independent.
+ */
+#ifndef SPMM_H
+#define SPMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPMM_OK = 0,
+    SPMM_ERR_ARG = 1,          /* null pointer, negative size, bad enum value */
+    SPMM_ERR_SHAPE = 2,        /* b not in {1,4,8,16}; m or k not a multiple of b; n > n_max; ld < n */
+    SPMM_ERR_PATTERN = 3,      /* block coordinate out of range, or a block given twice */
+    SPMM_ERR_CAPACITY = 4,     /* dynamic: nnzb > nnzb_max (or < 0) */
+    SPMM_ERR_UNSUPPORTED = 5,  /* dtype / kernel / alignment combination not provided */
+    SPMM_ERR_CUDA = 6,         /* a CUDA runtime call failed; see spmm_last_error() */
+    SPMM_ERR_OOM = 7,          /* device or host allocation failed */
+    SPMM_ERR_TIMEOUT = 8,      /* a bounded device wait (or serve_wait) ran out */
+    SPMM_ERR_BUSY = 9,         /* the plan is in flight on another stream */
+    SPMM_ERR_NOT_PACKED = 10   /* static run without values and without spmm_pack_values */
+} spmm_status;
+
+typedef enum { SPMM_STATIC = 0, SPMM_DYNAMIC = 1 } spmm_mode;
+
+typedef enum { SPMM_F32 = 0, SPMM_F16 = 1, SPMM_BF16 = 2, SPMM_E4M3 = 3 } spmm_dtype;
+
+/* Kernel family.  AUTO picks GATHER for b = 1, TC for 16-bit/E4M3 W with
+ * b >= 4, PLAIN for FP32 W with b >= 4. */
+typedef enum {
+    SPMM_KERNEL_AUTO = 0,
+    SPMM_KERNEL_PLAIN = 1,   /* plain FP32 CUDA-core kernel: one thread per (row, column), F32 only */
+    SPMM_KERNEL_GATHER = 2,  /* b = 1 gather kernel: 128-bit X row loads, warp-shuffle reductions */
+    SPMM_KERNEL_TC = 3       /* b >= 4 tensor-core kernel (tcgen05 + TMEM + TMA), 16-bit X */
+} spmm_kernel;
+
+/* Host pattern (static mode): nnzb entries, block (brow[p], bcol[p]). */
+typedef struct {
+    int64_t nnzb;
+    const int32_t *brow;
+    const int32_t *bcol;
+} spmm_pattern;
+
+/* Device pattern (dynamic mode): the block count lives on the device
+ * (*d_nnzb, read by the kernels, so no host synchronisation is needed);
+ * d_brow / d_bcol hold nnzb_max entries of which the first *d_nnzb count. */
+typedef struct {
+    const int32_t *d_nnzb;
+    const int32_t *d_brow;
+    const int32_t *d_bcol;
+} spmm_dpattern;
+
+/* Planner options; pass NULL for defaults (all fields 0). */
+typedef struct {
+    int32_t kernel;               /* spmm_kernel */
+    int32_t rows_per_group;       /* TC: tile rows (16 rows each) per group, 1..16; 0 = planner's choice */
+    int32_t max_per_item;         /* TC: entries per work item; GATHER: blocks per row item; 0 = planner's choice */
+    int32_t host_only;            /* 1 = build the static plan on the host only (no device memory, no
+                                     CUDA calls): for inspection with spmm_plan_get_array */
+} spmm_plan_opts;
+
+typedef struct spmm_plan spmm_plan;
+
+/*
+ * spmm_plan_create -- builds a plan (Section 3.2 static partitioner /
+ * Section 3.3 and Appendix A.2 dynamic planner).
+ *   m, k      : W is m x k; both multiples of b (else SPMM_ERR_SHAPE).
+ *   n_max     : largest n any spmm_run of this plan will pass (sizes workspace).
+ *   b         : block size, 1, 4, 8 or 16.
+ *   mode      : SPMM_STATIC (pattern != NULL, host arrays, nnzb_max ignored)
+ *               or SPMM_DYNAMIC (pattern ignored, nnzb_max >= 0 fixes capacity).
+ *   w_dtype, x_dtype : see "Types" above.
+ *   opts      : NULL or options.
+ *   out       : receives the plan (NULL on error).
+ * Static patterns are validated here: SPMM_ERR_PATTERN for an out-of-range or
+ * repeated block.  The host arrays are read during the call only.
+ */
+spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spmm_mode mode,
+                             spmm_dtype w_dtype, spmm_dtype x_dtype,
+                             const spmm_pattern *pattern, int64_t nnzb_max,
+                             const spmm_plan_opts *opts, spmm_plan **out);
+
+/*
+ * spmm_pack_values -- static mode: re-orders the nnzb user-order blocks at
+ * d_values (device, w_dtype) into the kernel's layout held by the plan
+ * (Section 3.2: host-supplied values re-ordered to the fixed distribution).
+ * d_scales: device float[nnzb], one scale per block, E4M3 only (else NULL).
+ * Later spmm_run calls may pass d_values = NULL to use the packed copy.
+ */
+spmm_status spmm_pack_values(spmm_plan *plan, const void *d_values, const float *d_scales,
+                             void *stream);
+
+/*
+ * spmm_run -- Y = W.X on `stream`.
+ *   d_values : static: NULL to use packed values, else user-order values that
+ *              are packed first on the same stream.  dynamic: required,
+ *              user-order values matching the device pattern.
+ *   d_scales : E4M3 per-block scales for d_values (NULL otherwise / if packed).
+ *   dpat     : dynamic mode only: the device pattern of this call.
+ *   d_X, n, ldx : X (k x n), 0 <= n <= n_max.
+ *   d_Y, ldy    : Y (m x n).
+ * In dynamic mode the device validates the pattern; on an invalid pattern or
+ * nnzb outside [0, nnzb_max] the status word is set (see spmm_get_status)
+ * and Y is not written.
+ */
+spmm_status spmm_run(spmm_plan *plan, const void *d_values, const float *d_scales,
+                     const spmm_dpattern *dpat, const void *d_X, int64_t n, int64_t ldx,
+                     void *d_Y, int64_t ldy, void *stream);
+
+/*
+ * spmm_run_host -- the same product with X and Y in HOST memory: copies X to
+ * a device buffer owned by the plan, runs, copies Y back, and synchronises
+ * `stream` before returning.  Static plans with packed values only.
+ * h_X is k x n (ldx), h_Y is m x n (ldy), both in x_dtype.
+ */
+spmm_status spmm_run_host(spmm_plan *plan, const void *h_X, int64_t n, int64_t ldx, void *h_Y,
+                          int64_t ldy, void *stream);
+
+/*
+ * spmm_get_status -- synchronises the plan's last stream and returns the
+ * device status word in *device_status (0 = ok, else an spmm_status value
+ * recorded on the device), then clears it.
+ */
+spmm_status spmm_get_status(spmm_plan *plan, int32_t *device_status);
+
+/* Plan facts for reporting and tests. */
+typedef struct {
+    int64_t m, k, n_max, nnzb, nnzb_max;
+    int32_t b, mode, w_dtype, x_dtype, kernel;
+    int32_t rows_per_group, max_per_item;
+    int64_t n_items, n_groups, n_entries, n_tiles, ws_rows, n_reductions;
+    int64_t device_bytes;         /* device memory the plan holds */
+} spmm_plan_info;
+
+spmm_status spmm_plan_get_info(const spmm_plan *plan, spmm_plan_info *info);
+
+/* Integer plan arrays, in the exact definitions the oracle states.  After a
+ * dynamic spmm_run the device-built arrays are returned (the call
+ * synchronises the plan's last stream). */
+typedef enum {
+    SPMM_ARR_ROW_PTR = 0,   /* int32[m/b + 1] block-CSR row pointers */
+    SPMM_ARR_COL_IDX = 1,   /* int32[nnzb] block column of each CSR slot */
+    SPMM_ARR_PERM = 2,      /* int32[nnzb] user index of each CSR slot */
+    SPMM_ARR_ITEMS = 3,     /* int32[n_items * 6]: group/row, begin, end, chunk, n_chunks, ws_slot */
+    SPMM_ARR_GRP_ROW0 = 4,  /* TC: int32[n_groups] first tile row of each group */
+    SPMM_ARR_GRP_ROWS = 5,  /* TC: int32[n_groups] tile rows in each group */
+    SPMM_ARR_GRP_EBEG = 6,  /* TC: int32[n_groups + 1] first entry of each group */
+    SPMM_ARR_ENT_COL = 7,   /* TC: int32[n_entries] tile column of each entry */
+    SPMM_ARR_ENT_TBEG = 8,  /* TC: int32[n_entries + 1] first tile slot of each entry */
+    SPMM_ARR_TILE_ROW = 9,  /* TC: int32[n_tiles] tile row within its group */
+    SPMM_ARR_BLK_SLOT = 10, /* TC: int32[nnzb] tile slot of each user block */
+    SPMM_ARR_BLK_OFF = 11,  /* TC: int32[nnzb] offset (row*16 + col) of the block in its tile */
+    SPMM_ARR_WS_ROW0 = 12,  /* int64[n_ws_slots] first workspace row of each split item */
+    SPMM_ARR_RED = 13       /* int32[n_reductions * 3]: group/row, first ws slot, n_chunks */
+} spmm_array;
+
+/* Copies array `which` into host memory `dst` (capacity in elements) and
+ * stores the element count in *count.  dst may be NULL to query the count. */
+spmm_status spmm_plan_get_array(spmm_plan *plan, spmm_array which, void *dst, int64_t capacity,
+                                int64_t *count);
+
+void spmm_plan_destroy(spmm_plan *plan);
+
+/* Appendix A.2 planner formulas, exposed for reporting:
+ * equal partition of `extent` into q parts -> sizes[q] (q - 1 parts of
+ * floor(extent/q), the last extent - (q-1)*floor(extent/q));
+ * bucket size N_nz = ceil(m * k * d_max / (q_m * q_k)), d_max = num/den. */
+spmm_status spmm_equal_partition(int64_t extent, int64_t q, int64_t *sizes);
+int64_t spmm_bucket_size(int64_t m, int64_t k, int64_t d_max_num, int64_t d_max_den, int64_t q_m,
+                         int64_t q_k);
+
+/*
+ * spmm_batch_run -- `count` static TC plans with packed values run in ONE
+ * persistent launch that walks a shared work queue over (problem, item,
+ * n tile).  d_X[i], n[i], ldx[i], d_Y[i], ldy[i] as in spmm_run (ldx/ldy may
+ * be NULL for dense n).  All plans must share x_dtype.  Uneven m, k, n, b
+ * and density are allowed.  The call is CUDA-graph capturable.
+ */
+spmm_status spmm_batch_run(int32_t count, spmm_plan *const *plans, const void *const *d_X,
+                           const int64_t *n, const int64_t *ldx, void *const *d_Y,
+                           const int64_t *ldy, void *stream);
+
+/* Thread-local message describing the last error on this thread ("" if none). */
+const char *spmm_last_error(void);
+
+/* Library version string. */
+const char *spmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMM_H */

@@ -1,0 +1,581 @@
+// C ABI of the block-sparse x dense product: plan lifetime, value packing,
+// dispatch to the kernels, status and inspection.  No exception crosses the
+// interface; every failure returns an spmm_status and leaves a thread-local
+// message for spmm_last_error().
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "spmm_internal.h"
+
+namespace spmm {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+size_t dtype_size(spmm_dtype t) {
+    switch (t) {
+        case SPMM_F32: return 4;
+        case SPMM_F16:
+        case SPMM_BF16: return 2;
+        case SPMM_E4M3: return 1;
+    }
+    return 0;
+}
+
+bool build_csr_checked(int64_t mb, int64_t nnzb, const int32_t *brow, const int32_t *bcol,
+                       HostPlan &hp);
+
+static spmm_status cuda_fail(cudaError_t e, const char *what) {
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? SPMM_ERR_OOM : SPMM_ERR_CUDA;
+}
+
+template <typename T>
+static cudaError_t dalloc(spmm_plan *p, T **ptr, int64_t count) {
+    *ptr = nullptr;
+    if (count <= 0) return cudaSuccess;
+    void *v = nullptr;
+    cudaError_t e = cudaMalloc(&v, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    p->allocations.push_back(v);
+    p->device_bytes += count * (int64_t)sizeof(T);
+    *ptr = (T *)v;
+    return cudaSuccess;
+}
+
+template <typename T>
+static cudaError_t upload(spmm_plan *p, T **ptr, const std::vector<T> &v) {
+    cudaError_t e = dalloc(p, ptr, (int64_t)v.size());
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpy(*ptr, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+static void free_plan(spmm_plan *p) {
+    if (!p) return;
+    for (void *a : p->allocations) cudaFree(a);
+    if (p->done) cudaEventDestroy(p->done);
+    delete p;
+}
+
+static int pick_kernel(int req, int b, spmm_dtype w, spmm_dtype x) {
+    if (req != SPMM_KERNEL_AUTO) return req;
+    if (b == 1) return SPMM_KERNEL_GATHER;
+    if (w == SPMM_F32) return SPMM_KERNEL_PLAIN;
+    return SPMM_KERNEL_TC;
+}
+
+static spmm_status check_types(int kernel, int b, spmm_dtype w, spmm_dtype x, int64_t m,
+                               int64_t k) {
+    const bool x16 = (x == SPMM_F16 || x == SPMM_BF16);
+    switch (kernel) {
+        case SPMM_KERNEL_PLAIN:
+            if (w == SPMM_F32 && x == SPMM_F32) return SPMM_OK;
+            set_error("PLAIN kernel is FP32 only (W and X F32)");
+            return SPMM_ERR_UNSUPPORTED;
+        case SPMM_KERNEL_GATHER:
+            if (b != 1) {
+                set_error("GATHER kernel needs b = 1");
+                return SPMM_ERR_UNSUPPORTED;
+            }
+            if (w == x && w != SPMM_E4M3) return SPMM_OK;
+            set_error("GATHER kernel needs W and X of one type in {F32, F16, BF16}");
+            return SPMM_ERR_UNSUPPORTED;
+        case SPMM_KERNEL_TC:
+            if (b == 1) {
+                set_error("TC kernel needs b in {4, 8, 16}");
+                return SPMM_ERR_UNSUPPORTED;
+            }
+            if (m % kTile || k % kTile) {
+                set_error("TC kernel needs m and k multiples of 16");
+                return SPMM_ERR_UNSUPPORTED;
+            }
+            if (x16 && (w == x || w == SPMM_E4M3)) return SPMM_OK;
+            set_error("TC kernel needs 16-bit X and W of the same type (or E4M3 W)");
+            return SPMM_ERR_UNSUPPORTED;
+        default:
+            set_error("unknown kernel %d", kernel);
+            return SPMM_ERR_ARG;
+    }
+}
+
+static int default_R(int64_t mt, int64_t n_max, int sms) {
+    const int64_t ntn = std::max<int64_t>(1, (n_max + kNTile - 1) / kNTile);
+    int R = kMaxGroupRows;
+    while (R > 1 && (int64_t)group_partition(mt, R).size() * ntn < sms) R /= 2;
+    return R;
+}
+
+static spmm_status upload_plan(spmm_plan *p) {
+    HostPlan &hp = p->hp;
+    cudaError_t e = cudaSuccess;
+#define UP(field, vec) \
+    if (e == cudaSuccess) e = upload(p, &p->field, hp.vec)
+    UP(d_row_ptr, row_ptr);
+    UP(d_col_idx, col_idx);
+    UP(d_perm, perm);
+    UP(d_items, items);
+    UP(d_red, red);
+    UP(d_ws_row0, ws_row0);
+    if (p->kernel == SPMM_KERNEL_TC) {
+        UP(d_grp_row0, grp_row0);
+        UP(d_grp_rows, grp_rows);
+        UP(d_grp_ebeg, grp_ebeg);
+        UP(d_ent_col, ent_col);
+        UP(d_ent_tbeg, ent_tbeg);
+        UP(d_tile_row, tile_row);
+        UP(d_blk_slot, blk_slot);
+        UP(d_blk_off, blk_off);
+    }
+#undef UP
+    if (e != cudaSuccess) return cuda_fail(e, "plan upload");
+    return SPMM_OK;
+}
+
+}  // namespace spmm
+
+using namespace spmm;
+
+extern "C" {
+
+const char *spmm_last_error(void) { return g_err; }
+
+const char *spmm_version(void) { return "spmm-gb300 0.1 (sm_103a)"; }
+
+spmm_status spmm_equal_partition(int64_t extent, int64_t q, int64_t *sizes) {
+    if (extent < 0 || q <= 0 || !sizes) {
+        set_error("equal_partition: extent >= 0, q > 0 and sizes required");
+        return SPMM_ERR_ARG;
+    }
+    for (int64_t i = 0; i < q - 1; ++i) sizes[i] = extent / q;
+    sizes[q - 1] = extent - (q - 1) * (extent / q);
+    return SPMM_OK;
+}
+
+int64_t spmm_bucket_size(int64_t m, int64_t k, int64_t num, int64_t den, int64_t qm, int64_t qk) {
+    if (m < 0 || k < 0 || num < 0 || den <= 0 || qm <= 0 || qk <= 0) return -1;
+    // ceil(m * k * num / (den * qm * qk)) in 128-bit to avoid overflow
+    const __int128 a = (__int128)m * k * num, d = (__int128)den * qm * qk;
+    return (int64_t)((a + d - 1) / d);
+}
+
+spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spmm_mode mode,
+                             spmm_dtype w_dtype, spmm_dtype x_dtype, const spmm_pattern *pattern,
+                             int64_t nnzb_max, const spmm_plan_opts *opts, spmm_plan **out) {
+    g_err[0] = 0;
+    if (!out) {
+        set_error("out is NULL");
+        return SPMM_ERR_ARG;
+    }
+    *out = nullptr;
+    if (n_max < 0 || (mode != SPMM_STATIC && mode != SPMM_DYNAMIC) || w_dtype < SPMM_F32 ||
+        w_dtype > SPMM_E4M3 || x_dtype < SPMM_F32 || x_dtype > SPMM_BF16) {
+        set_error("bad n_max, mode or dtype");
+        return SPMM_ERR_ARG;
+    }
+    spmm_plan_opts o{};
+    if (opts) o = *opts;
+    spmm_status st = validate_pattern(m, k, b, 0, nullptr, nullptr);
+    if (st != SPMM_OK) return st;
+    const int kernel = pick_kernel(o.kernel, b, w_dtype, x_dtype);
+    st = check_types(kernel, b, w_dtype, x_dtype, m, k);
+    if (st != SPMM_OK) return st;
+    if (o.rows_per_group < 0 || o.rows_per_group > kMaxGroupRows || o.max_per_item < 0) {
+        set_error("rows_per_group must be in 0..%d, max_per_item >= 0", kMaxGroupRows);
+        return SPMM_ERR_ARG;
+    }
+    if (mode == SPMM_DYNAMIC && (nnzb_max < 0 || o.host_only)) {
+        set_error("dynamic plans need nnzb_max >= 0 and device memory");
+        return SPMM_ERR_ARG;
+    }
+    if (mode == SPMM_STATIC && !pattern) {
+        set_error("static plans need a pattern");
+        return SPMM_ERR_ARG;
+    }
+    spmm_plan *p = new (std::nothrow) spmm_plan();
+    if (!p) return SPMM_ERR_OOM;
+    p->m = m;
+    p->k = k;
+    p->n_max = n_max;
+    p->b = b;
+    p->mode = mode;
+    p->wdt = w_dtype;
+    p->xdt = x_dtype;
+    p->kernel = kernel;
+    p->host_only = o.host_only != 0;
+    p->sm_count = 152;
+    if (!p->host_only) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            free_plan(p);
+            return cuda_fail(e, "device query");
+        }
+    }
+    const int64_t mb = m / b, mt = m / kTile;
+    try {
+        if (mode == SPMM_STATIC) {
+            st = validate_pattern(m, k, b, pattern->nnzb, pattern->brow, pattern->bcol);
+            if (st != SPMM_OK) {
+                free_plan(p);
+                return st;
+            }
+            p->nnzb = pattern->nnzb;
+            if (!build_csr_checked(mb, p->nnzb, pattern->brow, pattern->bcol, p->hp)) {
+                free_plan(p);
+                return SPMM_ERR_PATTERN;
+            }
+            if (kernel == SPMM_KERNEL_GATHER) {
+                const int64_t avg = mb ? (p->nnzb + mb - 1) / mb : 0;
+                p->C = o.max_per_item ? o.max_per_item : (int)std::max<int64_t>(64, 2 * avg);
+                build_row_plan(mb, p->C, true, p->hp);
+            } else if (kernel == SPMM_KERNEL_TC) {
+                p->R = o.rows_per_group ? o.rows_per_group : default_R(mt, n_max, p->sm_count);
+                if (o.max_per_item) {
+                    p->C = o.max_per_item;
+                } else {
+                    // entries per group if spread evenly, with headroom: only
+                    // groups well above the mean are split
+                    HostPlan probe;
+                    build_tc_plan(m, k, b, p->nnzb, pattern->brow, pattern->bcol, p->R, 1 << 30,
+                                  false, probe);
+                    const int64_t G = (int64_t)probe.grp_rows.size();
+                    const int64_t E = (int64_t)probe.ent_col.size();
+                    p->C = (int)std::max<int64_t>(16, G ? (5 * E + 4 * G - 1) / (4 * G) : 16);
+                }
+                build_tc_plan(m, k, b, p->nnzb, pattern->brow, pattern->bcol, p->R, p->C, true,
+                              p->hp);
+            }
+            p->n_items = (int64_t)p->hp.items.size() / kItemFields;
+            p->n_red = (int64_t)p->hp.red.size() / 3;
+            p->n_groups = (int64_t)p->hp.grp_rows.size();
+            p->n_entries = (int64_t)p->hp.ent_col.size();
+            p->n_tiles = (int64_t)p->hp.tile_row.size();
+        } else {
+            p->nnzb_max = nnzb_max;
+            set_error("dynamic mode is not built yet");
+            free_plan(p);
+            return SPMM_ERR_UNSUPPORTED;
+        }
+    } catch (const std::bad_alloc &) {
+        free_plan(p);
+        set_error("host allocation failed while planning");
+        return SPMM_ERR_OOM;
+    }
+    if (!p->host_only) {
+        st = upload_plan(p);
+        cudaError_t e = cudaSuccess;
+        if (st == SPMM_OK) e = dalloc(p, &p->d_status, 1);
+        if (st == SPMM_OK && e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int32_t));
+        if (st == SPMM_OK && e == cudaSuccess && p->hp.ws_rows > 0)
+            e = dalloc(p, &p->d_ws, p->hp.ws_rows * std::max<int64_t>(n_max, 1));
+        if (st == SPMM_OK && e == cudaSuccess) {
+            // packed values: CSR order for PLAIN / GATHER, 16 x 16 tiles for TC
+            if (kernel == SPMM_KERNEL_TC)
+                p->packed_bytes = p->n_tiles * kTile * kTile * (int64_t)dtype_size(w_dtype);
+            else
+                p->packed_bytes = p->nnzb * b * b * (int64_t)dtype_size(w_dtype);
+            e = dalloc(p, (char **)&p->d_packed, p->packed_bytes);
+            if (e == cudaSuccess && w_dtype == SPMM_E4M3)
+                e = dalloc(p, &p->d_tile_scale, p->n_tiles * 16);
+        }
+        if (st == SPMM_OK && e != cudaSuccess) st = cuda_fail(e, "plan allocation");
+        if (st != SPMM_OK) {
+            free_plan(p);
+            return st;
+        }
+    }
+    *out = p;
+    return SPMM_OK;
+}
+
+void spmm_plan_destroy(spmm_plan *plan) {
+    if (plan && plan->ran && plan->done) cudaEventSynchronize(plan->done);
+    free_plan(plan);
+}
+
+static spmm_status busy_check(spmm_plan *p, cudaStream_t s) {
+    if (p->ran && p->last_stream != s) {
+        cudaError_t q = cudaEventQuery(p->done);
+        if (q == cudaErrorNotReady) {
+            set_error("plan is in flight on another stream");
+            return SPMM_ERR_BUSY;
+        }
+        if (q != cudaSuccess) return cuda_fail(q, "event query");
+    }
+    return SPMM_OK;
+}
+
+static spmm_status finish_call(spmm_plan *p, cudaStream_t s) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    e = cudaEventRecord(p->done, s);
+    if (e != cudaSuccess) return cuda_fail(e, "event record");
+    p->last_stream = s;
+    p->ran = true;
+    return SPMM_OK;
+}
+
+static spmm_status do_pack(spmm_plan *p, const void *d_values, const float *d_scales,
+                           cudaStream_t s) {
+    if (p->nnzb > 0 && !d_values) {
+        set_error("values required");
+        return SPMM_ERR_ARG;
+    }
+    if (p->wdt == SPMM_E4M3 && p->nnzb > 0 && !d_scales) {
+        set_error("E4M3 values need per-block scales");
+        return SPMM_ERR_ARG;
+    }
+    cudaError_t e = (p->kernel == SPMM_KERNEL_TC)
+                        ? launch_pack_tiles(p, d_values, d_scales, nullptr, s)
+                        : launch_pack_csr(p, d_values, s);
+    if (e != cudaSuccess) return cuda_fail(e, "pack");
+    p->packed = true;
+    return SPMM_OK;
+}
+
+spmm_status spmm_pack_values(spmm_plan *plan, const void *d_values, const float *d_scales,
+                             void *stream) {
+    g_err[0] = 0;
+    if (!plan || plan->host_only) {
+        set_error("plan is NULL or host-only");
+        return SPMM_ERR_ARG;
+    }
+    if (plan->mode != SPMM_STATIC) {
+        set_error("spmm_pack_values is for static plans");
+        return SPMM_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    spmm_status st = busy_check(plan, s);
+    if (st != SPMM_OK) return st;
+    st = do_pack(plan, d_values, d_scales, s);
+    if (st != SPMM_OK) return st;
+    return finish_call(plan, s);
+}
+
+static spmm_status launch_product(spmm_plan *p, const void *d_X, int64_t n, int64_t ldx,
+                                  void *d_Y, int64_t ldy, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    switch (p->kernel) {
+        case SPMM_KERNEL_PLAIN: e = launch_plain(p, d_X, n, ldx, d_Y, ldy, s); break;
+        case SPMM_KERNEL_GATHER: e = launch_gather(p, d_X, n, ldx, d_Y, ldy, s); break;
+        case SPMM_KERNEL_TC: e = launch_tc(p, d_X, n, ldx, d_Y, ldy, s); break;
+        default: set_error("bad kernel"); return SPMM_ERR_ARG;
+    }
+    if (e == cudaSuccess && p->n_red > 0 && p->kernel != SPMM_KERNEL_PLAIN)
+        e = launch_reduce(p, n, d_Y, ldy, s);
+    if (e != cudaSuccess) return cuda_fail(e, "launch");
+    return SPMM_OK;
+}
+
+static spmm_status check_run_args(spmm_plan *p, const void *d_X, int64_t n, int64_t ldx,
+                                  const void *d_Y, int64_t ldy) {
+    if (n < 0 || n > p->n_max) {
+        set_error("n=%lld outside [0, n_max=%lld]", (long long)n, (long long)p->n_max);
+        return SPMM_ERR_SHAPE;
+    }
+    if (ldx < std::max<int64_t>(n, 1) || ldy < std::max<int64_t>(n, 1)) {
+        set_error("ldx/ldy must be >= max(n, 1)");
+        return SPMM_ERR_SHAPE;
+    }
+    if (n > 0 && (!d_X || !d_Y)) {
+        set_error("X and Y required");
+        return SPMM_ERR_ARG;
+    }
+    return SPMM_OK;
+}
+
+spmm_status spmm_run(spmm_plan *plan, const void *d_values, const float *d_scales,
+                     const spmm_dpattern *dpat, const void *d_X, int64_t n, int64_t ldx, void *d_Y,
+                     int64_t ldy, void *stream) {
+    g_err[0] = 0;
+    if (!plan || plan->host_only) {
+        set_error("plan is NULL or host-only");
+        return SPMM_ERR_ARG;
+    }
+    spmm_status st = check_run_args(plan, d_X, n, ldx, d_Y, ldy);
+    if (st != SPMM_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    st = busy_check(plan, s);
+    if (st != SPMM_OK) return st;
+    if (plan->mode == SPMM_DYNAMIC) {
+        (void)dpat;
+        set_error("dynamic mode is not built yet");
+        return SPMM_ERR_UNSUPPORTED;
+    }
+    if (d_values) {
+        st = do_pack(plan, d_values, d_scales, s);
+        if (st != SPMM_OK) return st;
+    }
+    if (!plan->packed) {
+        set_error("static plan has no values: call spmm_pack_values or pass d_values");
+        return SPMM_ERR_NOT_PACKED;
+    }
+    if (n == 0) return finish_call(plan, s);
+    st = launch_product(plan, d_X, n, ldx, d_Y, ldy, s);
+    if (st != SPMM_OK) return st;
+    return finish_call(plan, s);
+}
+
+spmm_status spmm_run_host(spmm_plan *plan, const void *h_X, int64_t n, int64_t ldx, void *h_Y,
+                          int64_t ldy, void *stream) {
+    g_err[0] = 0;
+    if (!plan || plan->host_only || plan->mode != SPMM_STATIC) {
+        set_error("spmm_run_host needs a device static plan");
+        return SPMM_ERR_ARG;
+    }
+    spmm_status st = check_run_args(plan, h_X, n, ldx, h_Y, ldy);
+    if (st != SPMM_OK) return st;
+    if (!plan->packed) {
+        set_error("static plan has no values");
+        return SPMM_ERR_NOT_PACKED;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    st = busy_check(plan, s);
+    if (st != SPMM_OK) return st;
+    const size_t es = dtype_size(plan->xdt);
+    const int64_t xb = plan->k * std::max<int64_t>(n, 1) * (int64_t)es;
+    const int64_t yb = plan->m * std::max<int64_t>(n, 1) * (int64_t)es;
+    cudaError_t e = cudaSuccess;
+    if (xb > plan->xbuf_bytes) {
+        if (plan->d_xbuf) {
+            cudaFree(plan->d_xbuf);
+            plan->allocations.erase(std::find(plan->allocations.begin(), plan->allocations.end(), plan->d_xbuf));
+            plan->device_bytes -= plan->xbuf_bytes;
+        }
+        e = dalloc(plan, (char **)&plan->d_xbuf, xb);
+        plan->xbuf_bytes = e == cudaSuccess ? xb : 0;
+    }
+    if (e == cudaSuccess && yb > plan->ybuf_bytes) {
+        if (plan->d_ybuf) {
+            cudaFree(plan->d_ybuf);
+            plan->allocations.erase(std::find(plan->allocations.begin(), plan->allocations.end(), plan->d_ybuf));
+            plan->device_bytes -= plan->ybuf_bytes;
+        }
+        e = dalloc(plan, (char **)&plan->d_ybuf, yb);
+        plan->ybuf_bytes = e == cudaSuccess ? yb : 0;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "staging allocation");
+    if (n > 0) {
+        e = cudaMemcpy2DAsync(plan->d_xbuf, n * es, h_X, ldx * es, n * es, plan->k,
+                              cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(e, "X upload");
+        st = launch_product(plan, plan->d_xbuf, n, n, plan->d_ybuf, n, s);
+        if (st != SPMM_OK) return st;
+        e = cudaMemcpy2DAsync(h_Y, ldy * es, plan->d_ybuf, n * es, n * es, plan->m,
+                              cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) return cuda_fail(e, "Y download");
+    }
+    st = finish_call(plan, s);
+    if (st != SPMM_OK) return st;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "stream synchronize");
+    return SPMM_OK;
+}
+
+spmm_status spmm_get_status(spmm_plan *plan, int32_t *device_status) {
+    g_err[0] = 0;
+    if (!plan || !device_status || plan->host_only) {
+        set_error("plan (device) and device_status required");
+        return SPMM_ERR_ARG;
+    }
+    *device_status = 0;
+    if (plan->ran) {
+        cudaError_t e = cudaEventSynchronize(plan->done);
+        if (e != cudaSuccess) return cuda_fail(e, "event synchronize");
+    }
+    cudaError_t e = cudaMemcpy(device_status, plan->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemset(plan->d_status, 0, sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_fail(e, "status read");
+    return SPMM_OK;
+}
+
+spmm_status spmm_plan_get_info(const spmm_plan *p, spmm_plan_info *info) {
+    if (!p || !info) {
+        set_error("plan and info required");
+        return SPMM_ERR_ARG;
+    }
+    spmm_plan_info i{};
+    i.m = p->m;
+    i.k = p->k;
+    i.n_max = p->n_max;
+    i.nnzb = p->nnzb;
+    i.nnzb_max = p->nnzb_max;
+    i.b = p->b;
+    i.mode = p->mode;
+    i.w_dtype = p->wdt;
+    i.x_dtype = p->xdt;
+    i.kernel = p->kernel;
+    i.rows_per_group = p->R;
+    i.max_per_item = p->C;
+    i.n_items = p->n_items;
+    i.n_groups = p->n_groups;
+    i.n_entries = p->n_entries;
+    i.n_tiles = p->n_tiles;
+    i.ws_rows = p->hp.ws_rows;
+    i.n_reductions = p->n_red;
+    i.device_bytes = p->device_bytes;
+    *info = i;
+    return SPMM_OK;
+}
+
+spmm_status spmm_plan_get_array(spmm_plan *p, spmm_array which, void *dst, int64_t capacity,
+                                int64_t *count) {
+    g_err[0] = 0;
+    if (!p || !count) {
+        set_error("plan and count required");
+        return SPMM_ERR_ARG;
+    }
+    const HostPlan &hp = p->hp;
+    const void *src = nullptr;
+    int64_t n = 0;
+    size_t es = 4;
+    switch (which) {
+        case SPMM_ARR_ROW_PTR: src = hp.row_ptr.data(); n = hp.row_ptr.size(); break;
+        case SPMM_ARR_COL_IDX: src = hp.col_idx.data(); n = hp.col_idx.size(); break;
+        case SPMM_ARR_PERM: src = hp.perm.data(); n = hp.perm.size(); break;
+        case SPMM_ARR_ITEMS: src = hp.items.data(); n = hp.items.size(); break;
+        case SPMM_ARR_GRP_ROW0: src = hp.grp_row0.data(); n = hp.grp_row0.size(); break;
+        case SPMM_ARR_GRP_ROWS: src = hp.grp_rows.data(); n = hp.grp_rows.size(); break;
+        case SPMM_ARR_GRP_EBEG: src = hp.grp_ebeg.data(); n = hp.grp_ebeg.size(); break;
+        case SPMM_ARR_ENT_COL: src = hp.ent_col.data(); n = hp.ent_col.size(); break;
+        case SPMM_ARR_ENT_TBEG: src = hp.ent_tbeg.data(); n = hp.ent_tbeg.size(); break;
+        case SPMM_ARR_TILE_ROW: src = hp.tile_row.data(); n = hp.tile_row.size(); break;
+        case SPMM_ARR_BLK_SLOT: src = hp.blk_slot.data(); n = hp.blk_slot.size(); break;
+        case SPMM_ARR_BLK_OFF: src = hp.blk_off.data(); n = hp.blk_off.size(); break;
+        case SPMM_ARR_WS_ROW0: src = hp.ws_row0.data(); n = hp.ws_row0.size(); es = 8; break;
+        case SPMM_ARR_RED: src = hp.red.data(); n = hp.red.size(); break;
+        default: set_error("unknown array %d", (int)which); return SPMM_ERR_ARG;
+    }
+    *count = n;
+    if (!dst) return SPMM_OK;
+    if (capacity < n) {
+        set_error("capacity %lld < %lld", (long long)capacity, (long long)n);
+        return SPMM_ERR_ARG;
+    }
+    if (n) memcpy(dst, src, (size_t)n * es);
+    return SPMM_OK;
+}
+
+spmm_status spmm_batch_run(int32_t count, spmm_plan *const *plans, const void *const *d_X,
+                           const int64_t *n, const int64_t *ldx, void *const *d_Y,
+                           const int64_t *ldy, void *stream) {
+    (void)count; (void)plans; (void)d_X; (void)n; (void)ldx; (void)d_Y; (void)ldy; (void)stream;
+    set_error("batched launch is not built yet");
+    return SPMM_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

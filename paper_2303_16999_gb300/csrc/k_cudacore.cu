@@ -1,0 +1,279 @@
+// CUDA-core kernels: value packing into CSR order, the plain FP32 kernel,
+// the b = 1 gather kernel and the split-row reduction.
+//
+// Y[i, :] = sum over blocks (r, c) in block row r = i / b of
+//           sum_l W_blk[i % b, l] * X[c*b + l, :]           (Section 3)
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "spmm_internal.h"
+
+namespace spmm {
+namespace {
+
+// ------------------------------------------------------------- packing ----
+// Static values are re-ordered once into CSR slot order (Section 3.2: the
+// host-supplied values are re-ordered to match the fixed distribution).
+template <typename U>
+__global__ void pack_csr_kernel(const U *__restrict__ vals, const int32_t *__restrict__ perm,
+                                int64_t nnzb, int bb, U *__restrict__ out) {
+    const int64_t total = nnzb * bb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = t / bb, e = t - s * bb;
+        out[t] = vals[(int64_t)perm[s] * bb + e];
+    }
+}
+
+// ------------------------------------------------------- plain FP32 ------
+// One thread per (row i, column j); FP32 throughout.  The deliberately plain
+// baseline kernel.
+__global__ void plain_f32_kernel(const int32_t *__restrict__ row_ptr,
+                                 const int32_t *__restrict__ col_idx,
+                                 const float *__restrict__ vals, const float *__restrict__ X,
+                                 int64_t ldx, float *__restrict__ Y, int64_t ldy, int64_t m,
+                                 int64_t n, int b) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
+        const int64_t r = i / b, ii = i - r * b;
+        float acc = 0.f;
+        for (int32_t s = row_ptr[r]; s < row_ptr[r + 1]; ++s) {
+            const int64_t c = col_idx[s];
+            const float *v = vals + ((int64_t)s * b + ii) * b;
+            const float *x = X + c * b * ldx + j;
+            for (int l = 0; l < b; ++l) acc = fmaf(v[l], x[l * ldx], acc);
+        }
+        Y[i * ldy + j] = acc;
+    }
+}
+
+// ---------------------------------------------------------- b = 1 gather --
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+    static __device__ __forceinline__ float to_f(float v) { return v; }
+    static __device__ __forceinline__ float from_f(float v) { return v; }
+};
+template <> struct Vec<__half> {
+    static __device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+    static __device__ __forceinline__ __half from_f(float v) { return __float2half_rn(v); }
+};
+template <> struct Vec<__nv_bfloat16> {
+    static __device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+    static __device__ __forceinline__ __nv_bfloat16 from_f(float v) { return __float2bfloat16_rn(v); }
+};
+
+// V elements of T per lane, loaded as one vector (16 B when V * sizeof(T) == 16).
+template <typename T, int V> struct alignas(V * sizeof(T)) Pack {
+    T v[V];
+};
+
+// One warp per (row item, column chunk).  Lanes form G = 32 / LN sub-groups
+// along the row's non-zeros and LN lanes along n (V columns each).  Indices
+// and values of 32 non-zeros are read coalesced once and broadcast by
+// shuffles; every sub-group accumulates its share in FP32, and a butterfly
+// of shuffles sums the sub-groups at the end (fixed order: deterministic).
+template <typename T, int V>
+__global__ void __launch_bounds__(256) gather_kernel(
+    const int32_t *__restrict__ items, int64_t n_items, int nchunk, int LN,
+    const int32_t *__restrict__ col_idx, const T *__restrict__ vals, const T *__restrict__ X,
+    int64_t ldx, T *__restrict__ Y, int64_t ldy, int64_t n, float *__restrict__ ws,
+    const int64_t *__restrict__ ws_row0) {
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= n_items * nchunk) return;
+    const int64_t item = wid / nchunk;
+    const int chunk = (int)(wid - item * nchunk);
+    const int32_t *it = items + item * kItemFields;
+    const int32_t row = it[0], beg = it[1], end = it[2], slot = it[5];
+    const int G = 32 / LN;
+    const int sg = lane / LN;
+    const int64_t c0 = (int64_t)chunk * LN * V + (int64_t)(lane % LN) * V;
+    const bool active = c0 < n;
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+    const T *xcol = X + (active ? c0 : 0);
+    for (int32_t base = beg; base < end; base += 32) {
+        const int32_t idx = base + lane;
+        const int32_t mycol = idx < end ? col_idx[idx] : 0;
+        const float myw = idx < end ? Vec<T>::to_f(vals[idx]) : 0.f;
+        const int cnt = min(32, end - base);
+        // t is warp-uniform so every shuffle has all 32 lanes; sub-group sg
+        // takes non-zeros t*G + sg, four of them in flight per lane
+        for (int t = 0; t * G < cnt; t += 4) {
+            int64_t cc[4];
+            float ww[4];
+            bool ok[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = (t + u) * G + sg;
+                ok[u] = j < cnt;
+                const int src = ok[u] ? j : 0;
+                cc[u] = __shfl_sync(0xffffffffu, mycol, src);
+                ww[u] = __shfl_sync(0xffffffffu, myw, src);
+            }
+            Pack<T, V> xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (ok[u] && active) {
+                    xv[u] = *reinterpret_cast<const Pack<T, V> *>(xcol + cc[u] * ldx);
+                } else {
+#pragma unroll
+                    for (int v = 0; v < V; ++v) xv[u].v[v] = Vec<T>::from_f(0.f);
+                    ww[u] = 0.f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = fmaf(ww[u], Vec<T>::to_f(xv[u].v[v]), acc[v]);
+        }
+    }
+    for (int off = LN; off < 32; off <<= 1)
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+    if (sg != 0 || !active) return;
+    if (slot >= 0) {
+        float *dst = ws + ws_row0[slot] * n + c0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) dst[v] = acc[v];
+    } else {
+        Pack<T, V> out;
+#pragma unroll
+        for (int v = 0; v < V; ++v) out.v[v] = Vec<T>::from_f(acc[v]);
+        *reinterpret_cast<Pack<T, V> *>(Y + (int64_t)row * ldy + c0) = out;
+    }
+}
+
+// ------------------------------------------------- split-row reduction ---
+// Rows split over several items: Y = sum of the chunks' FP32 partials in
+// chunk order (deterministic), converted once.
+template <typename T>
+__global__ void reduce_kernel(const int32_t *__restrict__ red, const int32_t *__restrict__ grp_row0,
+                              const int32_t *__restrict__ grp_rows, int rows_per_unit,
+                              const float *__restrict__ ws, const int64_t *__restrict__ ws_row0,
+                              T *__restrict__ Y, int64_t ldy, int64_t n, int64_t n_red) {
+  for (int64_t q = blockIdx.z; q < n_red; q += gridDim.z) {
+    const int32_t *rd = red + q * 3;
+    const int32_t g = rd[0], slot0 = rd[1], nch = rd[2];
+    const int64_t nrows = grp_rows ? (int64_t)grp_rows[g] * rows_per_unit : 1;
+    const int64_t yrow0 = grp_row0 ? (int64_t)grp_row0[g] * rows_per_unit : g;
+    for (int64_t r = blockIdx.y; r < nrows; r += gridDim.y) {
+        for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n;
+             j += (int64_t)gridDim.x * blockDim.x) {
+            float acc = 0.f;
+            for (int c = 0; c < nch; ++c) acc += ws[(ws_row0[slot0 + c] + r) * n + j];
+            Y[(yrow0 + r) * ldy + j] = Vec<T>::from_f(acc);
+        }
+    }
+  }
+}
+
+inline unsigned grid1d(int64_t total, int threads) {
+    int64_t g = (total + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > (1 << 30)) g = 1 << 30;
+    return (unsigned)g;
+}
+
+template <typename T, int V>
+cudaError_t gather_launch(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
+                          int64_t ldy, cudaStream_t s) {
+    const int64_t vecs = (n + V - 1) / V;
+    int LN = 1;
+    while (LN < 32 && LN < vecs) LN <<= 1;
+    const int nchunk = (int)((n + (int64_t)LN * V - 1) / ((int64_t)LN * V));
+    const int64_t warps = p->n_items * nchunk;
+    if (warps == 0) return cudaSuccess;
+    gather_kernel<T, V><<<grid1d(warps * 32, 256), 256, 0, s>>>(
+        p->d_items, p->n_items, nchunk, LN, p->d_col_idx, (const T *)p->d_packed, (const T *)X,
+        ldx, (T *)Y, ldy, n, p->d_ws, p->d_ws_row0);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gather_dispatch(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
+                            int64_t ldy, cudaStream_t s) {
+    // widest vector that keeps every lane's load aligned and inside its row
+    constexpr int Vmax = 16 / sizeof(T);
+    auto ok = [&](int V) {
+        const int64_t bytes = V * (int64_t)sizeof(T);
+        return n % V == 0 && ldx % V == 0 && ldy % V == 0 &&
+               ((uintptr_t)X % bytes) == 0 && ((uintptr_t)Y % bytes) == 0;
+    };
+    if (Vmax >= 8 && ok(8)) return gather_launch<T, (Vmax >= 8 ? 8 : 1)>(p, X, n, ldx, Y, ldy, s);
+    if (ok(4)) return gather_launch<T, 4>(p, X, n, ldx, Y, ldy, s);
+    if (ok(2)) return gather_launch<T, 2>(p, X, n, ldx, Y, ldy, s);
+    return gather_launch<T, 1>(p, X, n, ldx, Y, ldy, s);
+}
+
+}  // namespace
+
+cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, cudaStream_t s) {
+    const int bb = p->b * p->b;
+    const int64_t total = p->nnzb * bb;
+    if (total == 0) return cudaSuccess;
+    const unsigned g = grid1d(total, 256) > 4096u ? 4096u : grid1d(total, 256);
+    switch (dtype_size(p->wdt)) {
+        case 4:
+            pack_csr_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t *)d_values, p->d_perm,
+                                                        p->nnzb, bb, (uint32_t *)p->d_packed);
+            break;
+        case 2:
+            pack_csr_kernel<uint16_t><<<g, 256, 0, s>>>((const uint16_t *)d_values, p->d_perm,
+                                                        p->nnzb, bb, (uint16_t *)p->d_packed);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
+                         int64_t ldy, cudaStream_t s) {
+    dim3 grid(grid1d(n, 128), (unsigned)(p->m < 65535 ? p->m : 65535));
+    plain_f32_kernel<<<grid, 128, 0, s>>>(p->d_row_ptr, p->d_col_idx, (const float *)p->d_packed,
+                                          (const float *)X, ldx, (float *)Y, ldy, p->m, n, p->b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
+                          int64_t ldy, cudaStream_t s) {
+    switch (p->xdt) {
+        case SPMM_F32: return gather_dispatch<float>(p, X, n, ldx, Y, ldy, s);
+        case SPMM_F16: return gather_dispatch<__half>(p, X, n, ldx, Y, ldy, s);
+        case SPMM_BF16: return gather_dispatch<__nv_bfloat16>(p, X, n, ldx, Y, ldy, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_reduce(const spmm_plan *p, int64_t n, void *Y, int64_t ldy, cudaStream_t s) {
+    if (p->n_red == 0 || n == 0) return cudaSuccess;
+    const bool tc = p->kernel == SPMM_KERNEL_TC;
+    const int rows_per_unit = tc ? kTile : 1;
+    const unsigned gy = tc ? (unsigned)(kMaxGroupRows * kTile) : 1u;
+    dim3 grid(grid1d(n, 128) > 64u ? 64u : grid1d(n, 128), gy,
+              (unsigned)(p->n_red < 65535 ? p->n_red : 65535));
+    const int32_t *r0 = tc ? p->d_grp_row0 : nullptr;
+    const int32_t *rn = tc ? p->d_grp_rows : nullptr;
+    switch (p->xdt) {
+        case SPMM_F32:
+            reduce_kernel<float><<<grid, 128, 0, s>>>(p->d_red, r0, rn, rows_per_unit, p->d_ws,
+                                                      p->d_ws_row0, (float *)Y, ldy, n, p->n_red);
+            break;
+        case SPMM_F16:
+            reduce_kernel<__half><<<grid, 128, 0, s>>>(p->d_red, r0, rn, rows_per_unit, p->d_ws,
+                                                       p->d_ws_row0, (__half *)Y, ldy, n, p->n_red);
+            break;
+        case SPMM_BF16:
+            reduce_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>(p->d_red, r0, rn, rows_per_unit,
+                                                              p->d_ws, p->d_ws_row0,
+                                                              (__nv_bfloat16 *)Y, ldy, n, p->n_red);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace spmm

@@ -1,0 +1,505 @@
+// Tensor-core block-sparse kernel for b in {4, 8, 16} (Section 3.1: b x b
+// blocks hold all non-zeros; b = 16 is one 16 x 16 tile, b = 4 / 8 blocks are
+// packed into 16 x 16 tiles with zero fill).
+//
+// The product is computed transposed, Y^T = X^T W^T, so one MMA is
+//   D[128 n x 16 m] += A[128 n x 16 k] * B[16 k x 16 m]
+// with A = a 16-row slab of X (read by TMA straight from X's row-major
+// layout, i.e. MN-major), B = one packed W tile (K-major), D = FP32 in TMEM.
+// A CTA owns a group of up to 16 tile rows (256 rows of Y) and 128 columns
+// of n; it walks the union of the group's tile columns ("entries"), loading
+// each X slab once and applying it to every tile of that column, with one
+// TMEM accumulator (16 columns) per tile row.  TMEM holds two accumulator
+// sets so the epilogue of one work unit overlaps the MMAs of the next.
+//
+// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
+// TMEM owner, warps 2..5 = epilogue (TMEM -> registers -> Y or workspace).
+// Every mbarrier wait is bounded (globaltimer); on expiry the CTA records
+// SPMM_ERR_TIMEOUT in the plan's status word, stops, frees TMEM and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "spmm_internal.h"
+
+namespace spmm {
+namespace {
+
+constexpr int kStages = 12;
+constexpr int kSlabBytes = kTile * kNTile * 2;                    // 4096: 16 k x 128 n, 16-bit
+constexpr int kStageBytes = kSlabBytes + kMaxGroupRows * kTileBytes16;  // 12288
+constexpr int kAccCols = kMaxGroupRows * kTile;                   // 256 TMEM columns per buffer
+constexpr int kThreads = 192;
+constexpr unsigned long long kWaitNs = 2000000000ull;             // 2 s per wait
+
+struct __align__(8) Smem {
+    uint64_t full[kStages], empty[kStages], accf[2], acce[2];
+    int32_t ntile[kStages];
+    uint8_t rows[kStages][kMaxGroupRows];
+    uint32_t acc_mask[2];
+    uint32_t tmem_base;
+    volatile int32_t abort_flag;
+    int32_t issued, consumed;
+};
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait: false after kWaitNs or once another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, Smem *sm) {
+    if (mbar_try(b, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (true) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try(b, parity)) return true;
+        if (sm->abort_flag) return false;
+        if (gtimer() - t0 > kWaitNs) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading
+// byte offset >> 4 in 16-29, stride byte offset >> 4 in 32-45, the fixed
+// value 1 in 46-48, swizzle mode in 61-63 (0 none, 2 = 128-byte).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo,
+                                              uint32_t swz) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46) | ((uint64_t)swz << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
+// format (bits 7-9 / 10-12: 0 = F16, 1 = BF16), A MN-major (bit 15),
+// B K-major (bit 16 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | (1u << 15) | ((N >> 3) << 17) |
+           ((M >> 4) << 24);
+}
+
+template <typename T> struct Cvt;
+template <> struct Cvt<__half> {
+    static constexpr uint32_t fmt = 0;
+    static __device__ __forceinline__ __half f(float v) { return __float2half_rn(v); }
+};
+template <> struct Cvt<__nv_bfloat16> {
+    static constexpr uint32_t fmt = 1;
+    static __device__ __forceinline__ __nv_bfloat16 f(float v) { return __float2bfloat16_rn(v); }
+};
+
+struct TcArgs {
+    const int32_t *items;
+    const int32_t *n_items_dev;  // dynamic plans: item count on the device (else null)
+    int64_t n_items;
+    const int32_t *grp_row0, *grp_rows, *ent_col, *ent_tbeg, *tile_row;
+    const uint8_t *packed;       // 16 x 16 tiles, 512 B each, MMA B layout
+    void *Y;
+    int64_t ldy, n;
+    float *ws;
+    const int64_t *ws_row0;
+    int32_t *status;
+    int ntn;                     // n tiles of 128
+    uint32_t a_lbo, a_sbo;
+};
+
+__device__ __forceinline__ void record(int32_t *status, int32_t code) {
+    atomicCAS(status, 0, code);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs args) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *stages =
+        (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    Smem *sm = (Smem *)(stages + kStages * kStageBytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    __shared__ int64_t s_nitems;
+    if (threadIdx.x == 0) {
+        // dynamic plans: a pattern rejected on the device leaves Y unwritten
+        const bool skip = args.n_items_dev && *(volatile int32_t *)args.status != 0;
+        s_nitems = skip ? 0 : (args.n_items_dev ? (int64_t)*args.n_items_dev : args.n_items);
+    }
+    __syncthreads();
+    const int64_t nunits = s_nitems * args.ntn;
+    if (nunits == 0) return;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&sm->full[s], 1);
+            mbar_init(&sm->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sm->accf[b], 2);    // MMA completion + the issuer's mask hand-off
+            mbar_init(&sm->acce[b], 128);  // every epilogue thread
+        }
+        sm->abort_flag = 0;
+        sm->issued = 0;
+        sm->consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                smem_u32(&sm->tmem_base)),
+            "r"(2 * kAccCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int32_t issued = 0;
+            for (int64_t u = blockIdx.x; u < nunits && !sm->abort_flag; u += gridDim.x) {
+                const int32_t *it = args.items + (u / args.ntn) * kItemFields;
+                const int n0 = (int)(u % args.ntn) * kNTile;
+                for (int32_t e = it[1]; e < it[2]; ++e) {
+                    if (!mbar_wait(&sm->empty[stage], phase ^ 1, sm)) {
+                        record(args.status, kDevTimeout);
+                        sm->abort_flag = 1;
+                        break;
+                    }
+                    const int32_t tb = args.ent_tbeg[e];
+                    const int32_t nt = args.ent_tbeg[e + 1] - tb;
+                    const int32_t col = args.ent_col[e];
+                    sm->ntile[stage] = nt;
+                    for (int j = 0; j < nt; ++j) sm->rows[stage][j] = (uint8_t)args.tile_row[tb + j];
+                    uint8_t *st = stages + stage * kStageBytes;
+                    mbar_expect_tx(&sm->full[stage], kSlabBytes + nt * kTileBytes16);
+                    tma_load_2d(st, &xmap, n0, col * kTile, &sm->full[stage]);
+                    tma_load_2d(st + kSlabBytes / 2, &xmap, n0 + kNTile / 2, col * kTile,
+                                &sm->full[stage]);
+                    bulk_load(st + kSlabBytes, args.packed + (int64_t)tb * kTileBytes16,
+                              nt * kTileBytes16, &sm->full[stage]);
+                    ++issued;
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+            sm->issued = issued;
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = make_idesc(Cvt<T>::fmt, kNTile, kTile);
+            int stage = 0;
+            uint32_t phase = 0;
+            int32_t consumed = 0;
+            int local = 0;
+            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, ++local) {
+                const int32_t *it = args.items + (u / args.ntn) * kItemFields;
+                const int ab = local & 1;
+                const uint32_t aphase = (local >> 1) & 1;
+                bool ok = mbar_wait(&sm->acce[ab], aphase ^ 1, sm);
+                tc_fence_after();
+                uint32_t mask = 0;
+                for (int32_t e = it[1]; ok && e < it[2]; ++e) {
+                    if (!mbar_wait(&sm->full[stage], phase, sm)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    ++consumed;
+                    const int nt = sm->ntile[stage];
+                    const uint32_t sbase = smem_u32(stages + stage * kStageBytes);
+                    const uint64_t adesc = smem_desc(sbase, args.a_lbo, args.a_sbo, 2);
+                    for (int j = 0; j < nt; ++j) {
+                        const uint32_t row = sm->rows[stage][j];
+                        const uint64_t bdesc =
+                            smem_desc(sbase + kSlabBytes + j * kTileBytes16, 128, 256, 0);
+                        tc_mma(tmem + ab * kAccCols + row * kTile, adesc, bdesc, idesc,
+                               (mask >> row) & 1u);
+                        mask |= 1u << row;
+                    }
+                    tc_commit(&sm->empty[stage]);
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+                if (!ok) {
+                    record(args.status, kDevTimeout);
+                    sm->abort_flag = 1;
+                    break;
+                }
+                sm->acc_mask[ab] = mask;
+                tc_commit(&sm->accf[ab]);
+                mbar_arrive(&sm->accf[ab]);
+            }
+            sm->consumed = consumed;
+        }
+    } else {
+        // ---------------------------------------------------- epilogue
+        const int q = warp & 3;              // TMEM lane quarter of this warp
+        const int nl = q * 32 + lane;        // D row = column of Y within the tile
+        T *Y = (T *)args.Y;
+        int local = 0;
+        for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, ++local) {
+            const int32_t *it = args.items + (u / args.ntn) * kItemFields;
+            const int ab = local & 1;
+            const uint32_t aphase = (local >> 1) & 1;
+            int okw = 1;
+            if (lane == 0) okw = mbar_wait(&sm->accf[ab], aphase, sm) ? 1 : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) {
+                if (lane == 0) {
+                    record(args.status, kDevTimeout);
+                    sm->abort_flag = 1;
+                }
+                break;
+            }
+            tc_fence_after();
+            const uint32_t mask = sm->acc_mask[ab];
+            const int32_t g = it[0], slot = it[5];
+            const int rows = args.grp_rows[g];
+            const int64_t yrow0 = (int64_t)args.grp_row0[g] * kTile;
+            const int64_t col = (int64_t)(u % args.ntn) * kNTile + nl;
+            const bool in = col < args.n;
+            for (int r = 0; r < rows; ++r) {
+                float v[16];
+                if ((mask >> r) & 1u) {
+                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ab * kAccCols + r * kTile, v);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] = 0.f;
+                }
+                if (!in) continue;
+                if (slot >= 0) {
+                    float *dst = args.ws + (args.ws_row0[slot] + r * kTile) * args.n + col;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) dst[i * args.n] = v[i];
+                } else {
+                    T *dst = Y + (yrow0 + r * kTile) * args.ldy + col;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) dst[i * args.ldy] = Cvt<T>::f(v[i]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&sm->acce[ab]);
+        }
+    }
+
+    __syncthreads();
+    // after an abort, let copies still in flight land before the CTA exits
+    if (threadIdx.x == 0 && sm->abort_flag) {
+        for (int32_t c = sm->consumed; c < sm->issued; ++c) {
+            const int s = c % kStages;
+            const uint32_t par = (uint32_t)((c / kStages) & 1);
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(&sm->full[s], par) && gtimer() - t0 < kWaitNs) {
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(2 * kAccCols));
+    }
+}
+
+// ------------------------------------------------------------- packing ---
+// Tile layout of the MMA B operand, K-major without swizzle: 8 x 8 core
+// matrices of 128 contiguous bytes; element (i = row of W in the tile,
+// j = column) at byte (i/8)*256 + (j/8)*128 + (i%8)*16 + (j%8)*2.
+template <typename U>
+__global__ void pack_tiles_kernel(const U *__restrict__ vals, const int32_t *__restrict__ blk_slot,
+                                  const int32_t *__restrict__ blk_off, int64_t nnzb, int b,
+                                  const int32_t *__restrict__ nnzb_dev, U *__restrict__ out) {
+    if (nnzb_dev) nnzb = *nnzb_dev;
+    const int bb = b * b;
+    const int64_t total = nnzb * bb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t / bb;
+        const int e = (int)(t - p * bb);
+        const int off = blk_off[p];
+        const int ti = off / kTile + e / b, tj = off % kTile + e % b;
+        const int64_t dst = (int64_t)blk_slot[p] * (kTile * kTile) + (ti >> 3) * 128 +
+                            (tj >> 3) * 64 + (ti & 7) * 8 + (tj & 7);
+        out[dst] = vals[t];
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+template <typename T>
+cudaError_t tc_launch(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
+                      int64_t ldy, const int32_t *n_items_dev, int64_t n_items_cap,
+                      cudaStream_t s) {
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    if (((uintptr_t)X & 15) || (ldx * 2) % 16) return cudaErrorMisalignedAddress;
+    CUtensorMap map;
+    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)p->k};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ldx * 2)};
+    const cuuint32_t box[2] = {kNTile / 2, kTile};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&map,
+                     Cvt<T>::fmt ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                     2, const_cast<void *>(X), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    TcArgs a;
+    a.items = p->d_items;
+    a.n_items_dev = n_items_dev;
+    a.n_items = n_items_cap;
+    a.grp_row0 = p->d_grp_row0;
+    a.grp_rows = p->d_grp_rows;
+    a.ent_col = p->d_ent_col;
+    a.ent_tbeg = p->d_ent_tbeg;
+    a.tile_row = p->d_tile_row;
+    a.packed = (const uint8_t *)p->d_packed;
+    a.Y = Y;
+    a.ldy = ldy;
+    a.n = n;
+    a.ws = p->d_ws;
+    a.ws_row0 = p->d_ws_row0;
+    a.status = p->d_status;
+    a.ntn = (int)((n + kNTile - 1) / kNTile);
+    a.a_lbo = 2048;
+    a.a_sbo = 1024;
+
+    const int64_t units = n_items_cap * a.ntn;
+    if (units == 0) return cudaSuccess;
+    const int grid = (int)(units < p->sm_count ? units : p->sm_count);
+    const size_t smem = 1024 + (size_t)kStages * kStageBytes + sizeof(Smem);
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[Cvt<T>::fmt]) {
+        cudaError_t e = cudaFuncSetAttribute(tc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set[Cvt<T>::fmt] = true;
+    }
+    tc_kernel<T><<<grid, kThreads, smem, s>>>(map, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
+                      int64_t ldy, cudaStream_t s) {
+    if (p->xdt == SPMM_F16) return tc_launch<__half>(p, X, n, ldx, Y, ldy, nullptr, p->n_items, s);
+    if (p->xdt == SPMM_BF16)
+        return tc_launch<__nv_bfloat16>(p, X, n, ldx, Y, ldy, nullptr, p->n_items, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const float *d_scales,
+                              const int32_t *d_nnzb, cudaStream_t s) {
+    (void)d_scales;
+    if (p->packed_bytes == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(p->d_packed, 0, p->packed_bytes, s);
+    if (e != cudaSuccess) return e;
+    if (p->wdt != SPMM_F16 && p->wdt != SPMM_BF16) return cudaErrorNotSupported;
+    const int64_t nmax = d_nnzb ? p->nnzb_max : p->nnzb;
+    const int64_t total = nmax * p->b * p->b;
+    if (total == 0) return cudaSuccess;
+    int64_t g = (total + 255) / 256;
+    if (g > 8192) g = 8192;
+    pack_tiles_kernel<uint16_t><<<(unsigned)g, 256, 0, s>>>(
+        (const uint16_t *)d_values, p->d_blk_slot, p->d_blk_off, p->nnzb, p->b, d_nnzb,
+        (uint16_t *)p->d_packed);
+    return cudaGetLastError();
+}
+
+}  // namespace spmm

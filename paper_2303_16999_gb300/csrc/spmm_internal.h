@@ -1,0 +1,114 @@
+// Internal declarations shared by the host planner, the C ABI and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/spmm.h"
+
+namespace spmm {
+
+constexpr int kTile = 16;          // tensor-core tile edge (one MMA K step, one N step)
+constexpr int kTileBytes16 = 512;  // 16 x 16 16-bit tile in the MMA operand layout
+constexpr int kNTile = 128;        // n columns per tensor-core work unit (MMA M)
+constexpr int kMaxGroupRows = 16;  // tile rows per group: 2 x 16 x 16 TMEM columns = 512
+constexpr int kItemFields = 6;     // group/row, begin, end, chunk, n_chunks, ws_slot
+
+// device status word codes (mirrors spmm_status where applicable)
+enum DeviceStatus : int32_t {
+    kDevOk = 0,
+    kDevPattern = SPMM_ERR_PATTERN,
+    kDevCapacity = SPMM_ERR_CAPACITY,
+    kDevTimeout = SPMM_ERR_TIMEOUT,
+};
+
+void set_error(const char *fmt, ...);
+
+// ---------------------------------------------------------------- host plan
+struct HostPlan {
+    // canonical block-CSR
+    std::vector<int32_t> row_ptr, col_idx, perm;
+    // work items (row items for GATHER, group items for TC), kItemFields each
+    std::vector<int32_t> items;
+    std::vector<int64_t> ws_row0;
+    int64_t ws_rows = 0;
+    std::vector<int32_t> red;  // 3 per split group/row
+    // tensor-core tile structure
+    std::vector<int32_t> grp_row0, grp_rows, grp_ebeg, ent_col, ent_tbeg, tile_row, blk_slot,
+        blk_off;
+};
+
+// Validates shape and pattern; returns SPMM_OK, SPMM_ERR_SHAPE or SPMM_ERR_PATTERN.
+spmm_status validate_pattern(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *brow,
+                             const int32_t *bcol);
+void build_csr(int64_t mb, int64_t nnzb, const int32_t *brow, const int32_t *bcol, HostPlan &hp);
+std::vector<int64_t> group_partition(int64_t mt, int64_t R);
+void build_row_plan(int64_t mb, int64_t C1, bool sort_items, HostPlan &hp);
+void build_tc_plan(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *brow,
+                   const int32_t *bcol, int64_t R, int64_t C, bool sort_items, HostPlan &hp);
+
+// ------------------------------------------------------------------- plan
+struct DevArr {
+    void *p = nullptr;
+    int64_t bytes = 0;
+};
+
+}  // namespace spmm
+
+struct spmm_plan {
+    int64_t m = 0, k = 0, n_max = 0, nnzb = 0, nnzb_max = 0;
+    int b = 0;
+    spmm_mode mode = SPMM_STATIC;
+    spmm_dtype wdt = SPMM_F32, xdt = SPMM_F32;
+    int kernel = SPMM_KERNEL_AUTO;
+    int R = 0, C = 0;
+    bool host_only = false;
+    spmm::HostPlan hp;
+
+    // device copies (static) / device-built arrays (dynamic)
+    int32_t *d_row_ptr = nullptr, *d_col_idx = nullptr, *d_perm = nullptr, *d_items = nullptr,
+            *d_red = nullptr, *d_grp_row0 = nullptr, *d_grp_rows = nullptr, *d_ent_col = nullptr,
+            *d_ent_tbeg = nullptr, *d_tile_row = nullptr, *d_blk_slot = nullptr,
+            *d_blk_off = nullptr, *d_grp_ebeg = nullptr;
+    int64_t *d_ws_row0 = nullptr;
+    int64_t n_items = 0, n_groups = 0, n_entries = 0, n_tiles = 0, n_red = 0;
+    void *d_packed = nullptr;      // packed values (kernel layout)
+    float *d_tile_scale = nullptr; // E4M3: per-element-block scales in tile layout
+    int64_t packed_bytes = 0;
+    bool packed = false;
+    float *d_ws = nullptr;         // split-row partials, ws_rows x n_max FP32
+    int32_t *d_status = nullptr;   // device status word
+    int32_t *d_counts = nullptr;   // dynamic: device counters (n_items, n_entries, ...)
+    void *d_scratch = nullptr;     // dynamic: re-partition scratch
+    int64_t scratch_bytes = 0;
+    void *d_xbuf = nullptr, *d_ybuf = nullptr;  // spmm_run_host staging
+    int64_t xbuf_bytes = 0, ybuf_bytes = 0;
+    int64_t device_bytes = 0;
+    int sm_count = 0;
+    cudaStream_t last_stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool ran = false;
+    std::vector<void *> allocations;
+};
+
+namespace spmm {
+
+// kernel launchers (return cudaSuccess or the launch error)
+cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, cudaStream_t s);
+cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const float *d_scales,
+                              const int32_t *d_nnzb, cudaStream_t s);
+cudaError_t launch_plain(const spmm_plan *p, const void *d_X, int64_t n, int64_t ldx, void *d_Y,
+                         int64_t ldy, cudaStream_t s);
+cudaError_t launch_gather(const spmm_plan *p, const void *d_X, int64_t n, int64_t ldx, void *d_Y,
+                          int64_t ldy, cudaStream_t s);
+cudaError_t launch_tc(const spmm_plan *p, const void *d_X, int64_t n, int64_t ldx, void *d_Y,
+                      int64_t ldy, cudaStream_t s);
+cudaError_t launch_reduce(const spmm_plan *p, int64_t n, void *d_Y, int64_t ldy, cudaStream_t s);
+cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s);
+
+size_t dtype_size(spmm_dtype t);
+
+}  // namespace spmm

@@ -1,0 +1,273 @@
+"""ctypes binding of the C ABI in ``include/spmm.h`` (argument marshalling only).
+
+The functions ``spmm_plan_create``, ``spmm_pack_values``, ``spmm_run``,
+``spmm_run_host``, ``spmm_batch_run``, ``spmm_get_status``,
+``spmm_plan_get_info``, ``spmm_plan_get_array``, ``spmm_plan_destroy``,
+``spmm_equal_partition`` and ``spmm_bucket_size`` carry the C names.  The
+``Plan`` class wraps a plan handle for torch tensors: torch provides device
+memory and streams only; every step of the product runs in the library's CUDA
+kernels.  There is no CPU fallback: if ``_build/libspmm.so`` is missing this
+module raises instead of computing anything.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libspmm.so")
+
+# status codes
+OK, ERR_ARG, ERR_SHAPE, ERR_PATTERN, ERR_CAPACITY, ERR_UNSUPPORTED, ERR_CUDA, ERR_OOM, \
+    ERR_TIMEOUT, ERR_BUSY, ERR_NOT_PACKED = range(11)
+STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_PATTERN", 4: "ERR_CAPACITY",
+                5: "ERR_UNSUPPORTED", 6: "ERR_CUDA", 7: "ERR_OOM", 8: "ERR_TIMEOUT",
+                9: "ERR_BUSY", 10: "ERR_NOT_PACKED"}
+STATIC, DYNAMIC = 0, 1
+F32, F16, BF16, E4M3 = 0, 1, 2, 3
+KERNEL_AUTO, KERNEL_PLAIN, KERNEL_GATHER, KERNEL_TC = 0, 1, 2, 3
+KERNELS = {"auto": 0, "plain": 1, "gather": 2, "tc": 3}
+ARRAYS = {"row_ptr": 0, "col_idx": 1, "perm": 2, "items": 3, "grp_row0": 4, "grp_rows": 5,
+          "grp_ebeg": 6, "ent_col": 7, "ent_tbeg": 8, "tile_row": 9, "blk_slot": 10,
+          "blk_off": 11, "ws_row0": 12, "red": 13}
+
+# exported symbols of include/spmm.h (checked by the CPU test-suite)
+EXPORTS = ["spmm_plan_create", "spmm_pack_values", "spmm_run", "spmm_run_host",
+           "spmm_get_status", "spmm_plan_get_info", "spmm_plan_get_array",
+           "spmm_plan_destroy", "spmm_equal_partition", "spmm_bucket_size", "spmm_batch_run",
+           "spmm_last_error", "spmm_version"]
+
+
+class SpmmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class Pattern(ctypes.Structure):
+    _fields_ = [("nnzb", ctypes.c_int64), ("brow", ctypes.c_void_p), ("bcol", ctypes.c_void_p)]
+
+
+class DPattern(ctypes.Structure):
+    _fields_ = [("d_nnzb", ctypes.c_void_p), ("d_brow", ctypes.c_void_p),
+                ("d_bcol", ctypes.c_void_p)]
+
+
+class PlanOpts(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("rows_per_group", ctypes.c_int32),
+                ("max_per_item", ctypes.c_int32), ("host_only", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("m", "k", "n_max", "nnzb", "nnzb_max")] + \
+        [(n, ctypes.c_int32) for n in ("b", "mode", "w_dtype", "x_dtype", "kernel",
+                                      "rows_per_group", "max_per_item")] + \
+        [(n, ctypes.c_int64) for n in ("n_items", "n_groups", "n_entries", "n_tiles",
+                                      "ws_rows", "n_reductions", "device_bytes")]
+
+
+_lib = None
+
+
+def lib():
+    """Loads the native library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("native library %s is not built: run "
+                               "`python -c \"import __graft_entry__ as g; g.build()\"`" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+        L.spmm_plan_create.argtypes = [i64, i64, i64, i32, i32, i32, i32, ctypes.POINTER(Pattern),
+                                       i64, ctypes.POINTER(PlanOpts), ctypes.POINTER(vp)]
+        L.spmm_pack_values.argtypes = [vp, vp, vp, vp]
+        L.spmm_run.argtypes = [vp, vp, vp, ctypes.POINTER(DPattern), vp, i64, i64, vp, i64, vp]
+        L.spmm_run_host.argtypes = [vp, vp, i64, i64, vp, i64, vp]
+        L.spmm_get_status.argtypes = [vp, ctypes.POINTER(i32)]
+        L.spmm_plan_get_info.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+        L.spmm_plan_get_array.argtypes = [vp, i32, vp, i64, ctypes.POINTER(i64)]
+        L.spmm_plan_destroy.argtypes = [vp]
+        L.spmm_plan_destroy.restype = None
+        L.spmm_equal_partition.argtypes = [i64, i64, ctypes.POINTER(i64)]
+        L.spmm_bucket_size.argtypes = [i64, i64, i64, i64, i64, i64]
+        L.spmm_bucket_size.restype = i64
+        L.spmm_batch_run.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(vp),
+                                     ctypes.POINTER(i64), vp]
+        L.spmm_last_error.restype = ctypes.c_char_p
+        L.spmm_version.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            getattr(L, name)
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        raise SpmmError(status, lib().spmm_last_error().decode())
+    return status
+
+
+# --------------------------------------------------- C names, thin wrappers
+def spmm_plan_create(m, k, n_max, b, mode, w_dtype, x_dtype, pattern, nnzb_max, opts):
+    h = ctypes.c_void_p()
+    _check(lib().spmm_plan_create(m, k, n_max, b, mode, w_dtype, x_dtype,
+                                  ctypes.byref(pattern) if pattern is not None else None,
+                                  nnzb_max, ctypes.byref(opts) if opts is not None else None,
+                                  ctypes.byref(h)))
+    return h
+
+
+def spmm_pack_values(plan, d_values, d_scales, stream):
+    return _check(lib().spmm_pack_values(plan, d_values, d_scales, stream))
+
+
+def spmm_run(plan, d_values, d_scales, dpat, d_X, n, ldx, d_Y, ldy, stream):
+    return _check(lib().spmm_run(plan, d_values, d_scales,
+                                 ctypes.byref(dpat) if dpat is not None else None,
+                                 d_X, n, ldx, d_Y, ldy, stream))
+
+
+def spmm_run_host(plan, h_X, n, ldx, h_Y, ldy, stream):
+    return _check(lib().spmm_run_host(plan, h_X, n, ldx, h_Y, ldy, stream))
+
+
+def spmm_get_status(plan):
+    s = ctypes.c_int32()
+    _check(lib().spmm_get_status(plan, ctypes.byref(s)))
+    return s.value
+
+
+def spmm_plan_get_info(plan):
+    i = PlanInfo()
+    _check(lib().spmm_plan_get_info(plan, ctypes.byref(i)))
+    return {f: getattr(i, f) for f, _ in PlanInfo._fields_}
+
+
+def spmm_plan_get_array(plan, name):
+    which = ARRAYS[name]
+    cnt = ctypes.c_int64()
+    _check(lib().spmm_plan_get_array(plan, which, None, 0, ctypes.byref(cnt)))
+    dt = np.int64 if name == "ws_row0" else np.int32
+    out = np.zeros(cnt.value, dtype=dt)
+    _check(lib().spmm_plan_get_array(plan, which, out.ctypes.data_as(ctypes.c_void_p),
+                                     cnt.value, ctypes.byref(cnt)))
+    return out
+
+
+def spmm_plan_destroy(plan):
+    lib().spmm_plan_destroy(plan)
+
+
+def spmm_equal_partition(extent, q):
+    out = (ctypes.c_int64 * q)()
+    _check(lib().spmm_equal_partition(extent, q, out))
+    return list(out)
+
+
+def spmm_bucket_size(m, k, d_num, d_den, q_m, q_k):
+    return lib().spmm_bucket_size(m, k, d_num, d_den, q_m, q_k)
+
+
+def spmm_version():
+    return lib().spmm_version().decode()
+
+
+# ------------------------------------------------------------- torch glue
+def dtype_code(t):
+    import torch
+    return {torch.float32: F32, torch.float16: F16, torch.bfloat16: BF16,
+            torch.float8_e4m3fn: E4M3}[t]
+
+
+def torch_dtype(code):
+    import torch
+    return {F32: torch.float32, F16: torch.float16, BF16: torch.bfloat16,
+            E4M3: torch.float8_e4m3fn}[code]
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Plan:
+    """One SpMM plan.  Static: ``Plan(m, k, n_max, b, brow=..., bcol=...)``;
+    dynamic: ``Plan(m, k, n_max, b, mode=DYNAMIC, nnzb_max=...)``."""
+
+    def __init__(self, m, k, n_max, b, w_dtype=F16, x_dtype=None, brow=None, bcol=None,
+                 mode=STATIC, nnzb_max=0, kernel="auto", rows_per_group=0, max_per_item=0,
+                 host_only=False):
+        x_dtype = w_dtype if x_dtype is None else x_dtype
+        opts = PlanOpts(KERNELS[kernel] if isinstance(kernel, str) else kernel,
+                        rows_per_group, max_per_item, 1 if host_only else 0)
+        pat = None
+        self._keep = None
+        if mode == STATIC:
+            brow = np.ascontiguousarray(brow, dtype=np.int32)
+            bcol = np.ascontiguousarray(bcol, dtype=np.int32)
+            self._keep = (brow, bcol)
+            pat = Pattern(len(brow), brow.ctypes.data, bcol.ctypes.data)
+        self.h = spmm_plan_create(m, k, n_max, b, mode, w_dtype, x_dtype, pat, nnzb_max, opts)
+        self.m, self.k, self.n_max, self.b = m, k, n_max, b
+        self.mode, self.w_dtype, self.x_dtype = mode, w_dtype, x_dtype
+
+    def close(self):
+        if self.h:
+            spmm_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        return spmm_plan_get_info(self.h)
+
+    def array(self, name):
+        return spmm_plan_get_array(self.h, name)
+
+    def pack(self, values, scales=None, stream=None):
+        spmm_pack_values(self.h, _ptr(values), _ptr(scales), _stream_handle(stream))
+
+    def run(self, X, Y=None, values=None, scales=None, pattern=None, stream=None):
+        """Y = W.X for device tensors; returns Y (allocated if not given)."""
+        import torch
+        n = X.shape[1]
+        if Y is None:
+            Y = torch.empty((self.m, n), dtype=X.dtype, device=X.device)
+        dp = None
+        if pattern is not None:
+            d_nnzb, d_brow, d_bcol = pattern
+            dp = DPattern(d_nnzb.data_ptr(), d_brow.data_ptr(), d_bcol.data_ptr())
+        spmm_run(self.h, _ptr(values), _ptr(scales), dp, _ptr(X), n, X.stride(0), _ptr(Y),
+                 Y.stride(0), _stream_handle(stream))
+        return Y
+
+    def run_host(self, X, Y, stream=None):
+        """Same product with host (CPU, ideally pinned) X and Y."""
+        spmm_run_host(self.h, ctypes.c_void_p(X.data_ptr()), X.shape[1], X.stride(0),
+                      ctypes.c_void_p(Y.data_ptr()), Y.stride(0), _stream_handle(stream))
+        return Y
+
+    def status(self):
+        return spmm_get_status(self.h)
+
+
+def spmm_batch_run(plans, Xs, Ys, stream=None):
+    count = len(plans)
+    vp, i64 = ctypes.c_void_p, ctypes.c_int64
+    hp = (vp * count)(*[p.h.value if hasattr(p.h, "value") else p.h for p in plans])
+    xp = (vp * count)(*[x.data_ptr() for x in Xs])
+    yp = (vp * count)(*[y.data_ptr() for y in Ys])
+    ns = (i64 * count)(*[x.shape[1] for x in Xs])
+    lx = (i64 * count)(*[x.stride(0) for x in Xs])
+    ly = (i64 * count)(*[y.stride(0) for y in Ys])
+    return _check(lib().spmm_batch_run(count, hp, xp, ns, lx, yp, ly, _stream_handle(stream)))

@@ -1,0 +1,141 @@
+"""C-ABI checks that need no GPU: the library loads and exports every entry
+point of include/spmm.h, argument / shape / pattern errors come back as
+status codes, and host-only static plans reproduce the oracle's integer plan
+arrays bit for bit."""
+import re
+
+import numpy as np
+import pytest
+
+from oracle import plan as P
+from paper_2303_16999_gb300 import spmm as S
+
+
+@pytest.fixture(scope="module", autouse=True)
+def native():
+    from paper_2303_16999_gb300 import build
+    build.build()
+    return S.lib()
+
+
+def test_exports_match_header():
+    import os
+    hdr = open(os.path.join(os.path.dirname(S.HERE), "include", "spmm.h")).read()
+    declared = set(re.findall(r"\b(spmm_[a-z_]+)\s*\(", hdr))
+    declared = {d for d in declared if not d.endswith("_t")}
+    assert declared == set(S.EXPORTS), declared ^ set(S.EXPORTS)
+    L = S.lib()
+    for name in declared:
+        assert hasattr(L, name)
+    assert "sm_103a" in S.spmm_version()
+
+
+def test_appendix_formulas_match_oracle():
+    for e, q in ((4096, 3), (4096, 4096), (9, 3), (10, 4), (7, 1), (0, 5)):
+        assert S.spmm_equal_partition(e, q) == P.equal_partition(e, q)
+    from fractions import Fraction
+    for m, k, d, qm, qk in ((4096, 4096, Fraction(1, 16), 4, 4), (9, 9, Fraction(1, 3), 1, 3),
+                            (10, 10, Fraction(1, 3), 1, 1), (8192, 8192, Fraction(1, 16), 7, 3)):
+        assert S.spmm_bucket_size(m, k, d.numerator, d.denominator, qm, qk) == \
+            P.bucket_size(m, k, d, qm, qk)
+
+
+def _plan(m, k, b, brow, bcol, **kw):
+    return S.Plan(m, k, kw.pop("n_max", 64), b, w_dtype=kw.pop("w_dtype", S.F16),
+                  brow=brow, bcol=bcol, host_only=True, **kw)
+
+
+def test_errors():
+    with pytest.raises(S.SpmmError) as e:
+        _plan(16, 16, 4, [4], [0])
+    assert e.value.status == S.ERR_PATTERN
+    with pytest.raises(S.SpmmError) as e:
+        _plan(16, 16, 4, [1, 1], [2, 2])
+    assert e.value.status == S.ERR_PATTERN
+    with pytest.raises(S.SpmmError) as e:
+        _plan(18, 16, 4, [0], [0])
+    assert e.value.status == S.ERR_SHAPE
+    with pytest.raises(S.SpmmError) as e:
+        _plan(16, 16, 2, [0], [0])
+    assert e.value.status == S.ERR_SHAPE
+    with pytest.raises(S.SpmmError) as e:
+        _plan(16, 16, 4, [0], [0], w_dtype=S.F16, kernel="plain")
+    assert e.value.status == S.ERR_UNSUPPORTED
+    with pytest.raises(S.SpmmError) as e:
+        _plan(16, 16, 4, [0], [0], kernel="gather")
+    assert e.value.status == S.ERR_UNSUPPORTED
+    with pytest.raises(S.SpmmError) as e:
+        _plan(24, 24, 4, [0], [0], kernel="tc")     # m, k not multiples of 16
+    assert e.value.status == S.ERR_UNSUPPORTED
+    p = _plan(16, 16, 4, [], [])
+    assert p.info()["nnzb"] == 0
+
+
+def _rand(rng, mb, kb, nnzb):
+    idx = rng.choice(mb * kb, nnzb, replace=False)
+    o = rng.permutation(nnzb)
+    return (idx // kb).astype(np.int32)[o], (idx % kb).astype(np.int32)[o]
+
+
+@pytest.mark.parametrize("b", [1, 4, 8, 16])
+def test_csr_bit_exact(b):
+    rng = np.random.default_rng(20 + b)
+    m = k = 256
+    mb, kb = m // b, k // b
+    for d in (0.0, 1 / 32, 1 / 4, 1.0):
+        brow, bcol = _rand(rng, mb, kb, int(d * mb * kb))
+        p = _plan(m, k, b, brow, bcol)
+        rp, ci, pm = P.csr(mb, brow, bcol)
+        assert np.array_equal(p.array("row_ptr"), rp)
+        assert np.array_equal(p.array("col_idx"), ci)
+        assert np.array_equal(p.array("perm"), pm)
+
+
+def test_row_plan_bit_exact():
+    rng = np.random.default_rng(3)
+    for m, k, nnzb, C in ((512, 512, 9000, 0), (64, 4096, 30000, 50), (300, 300, 0, 0)):
+        brow, bcol = _rand(rng, m, k, nnzb)
+        p = _plan(m, k, 1, brow, bcol, max_per_item=C)
+        info = p.info()
+        rp, _, _ = P.csr(m, brow, bcol)
+        want = P.row_plan(m, rp, info["max_per_item"], sort_items=True)
+        assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
+        assert np.array_equal(p.array("ws_row0"), want["ws_row0"])
+        assert np.array_equal(p.array("red").reshape(-1, 3), want["red"])
+        assert info["ws_rows"] == want["ws_rows"]
+
+
+TC_KEYS = ["grp_row0", "grp_rows", "grp_ebeg", "ent_col", "ent_tbeg", "tile_row", "blk_slot",
+           "blk_off", "ws_row0"]
+
+
+@pytest.mark.parametrize("b", [4, 8, 16])
+def test_tc_plan_bit_exact(b):
+    rng = np.random.default_rng(50 + b)
+    cases = [(256, 256, 1 / 8, 0, 0, 64), (512, 256, 1 / 4, 5, 7, 300), (1024, 512, 1 / 32, 16, 0, 2048),
+             (160, 96, 1 / 2, 3, 2, 16), (64, 64, 0.0, 0, 0, 8)]
+    for m, k, d, R, C, nmax in cases:
+        mb, kb = m // b, k // b
+        brow, bcol = _rand(rng, mb, kb, int(d * mb * kb))
+        p = _plan(m, k, b, brow, bcol, rows_per_group=R, max_per_item=C, n_max=nmax)
+        info = p.info()
+        want = P.tc_plan(m, k, b, brow, bcol, info["rows_per_group"], info["max_per_item"])
+        for key in TC_KEYS:
+            assert np.array_equal(p.array(key), want[key]), key
+        assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
+        assert np.array_equal(p.array("red").reshape(-1, 3), want["red"])
+        assert info["ws_rows"] == want["ws_rows"]
+        assert info["n_tiles"] == len(want["tile_row"])
+
+
+def test_tc_plan_worst_case_splits():
+    # Appendix A.2 worst case: every block in one tile row -> that group splits
+    m = k = 1024
+    b = 16
+    brow = np.zeros(64, np.int32)
+    bcol = np.arange(64, dtype=np.int32)
+    p = _plan(m, k, b, brow, bcol, n_max=256)
+    info = p.info()
+    want = P.tc_plan(m, k, b, brow, bcol, info["rows_per_group"], info["max_per_item"])
+    assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
+    assert info["n_reductions"] == 1 and info["ws_rows"] > 0

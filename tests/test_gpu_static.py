@@ -1,0 +1,224 @@
+"""GPU parity of the static path through the C ABI against the FP64 oracle.
+
+Bars (normwise ||Y - Y_o||_F / (||W||_F ||X||_F)): 1e-6 for FP32, 4e-3 for
+FP16 / BF16 inputs with FP32 accumulation.  Integer-valued inputs are exact
+in FP32 accumulation, so there the output must equal the oracle's value
+rounded once to the output type, bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_16999_gb300 import spmm as S
+from paper_2303_16999_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {torch.float32: 1e-6, torch.float16: 4e-3, torch.bfloat16: 4e-3}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2303_16999_gb300 import build
+    build.build()
+    return torch.device("cuda:0")
+
+
+def _x_dev(X, dt, ld=None):
+    """X on the device, optionally with leading dimension ld > n."""
+    k, n = X.shape
+    if ld is None or ld == n:
+        return X.to(dt).cuda()
+    buf = torch.zeros((k, ld), dtype=dt, device="cuda")
+    buf[:, :n] = X.to(dt).cuda()
+    return buf[:, :n]
+
+
+def run_case(m, k, n, b, nnzb, dt, kernel, seed, ldx=None, **kw):
+    c = wl.problem(seed, m, k, n, b, nnzb)
+    vals = torch.from_numpy(c["vals"]).to(dt)
+    X = torch.from_numpy(c["X"]).to(dt)
+    plan = S.Plan(m, k, max(n, 1), b, w_dtype=S.dtype_code(dt), brow=c["brow"], bcol=c["bcol"],
+                  kernel=kernel, **kw)
+    plan.pack(vals.cuda())
+    Xd = _x_dev(X, dt, ldx)
+    Y = torch.full((m, n), float("nan"), dtype=dt, device="cuda")
+    plan.run(Xd, Y)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X)
+    err = oracle.normwise_err(Y.cpu(), Yo, oracle.block_fro(vals), X)
+    return err, Y, Yo, plan
+
+
+CASES = [
+    # m, k, n, b, density
+    (256, 256, 64, 4, 1 / 8),
+    (512, 384, 200, 16, 1 / 4),
+    (384, 512, 130, 8, 1 / 8),
+    (256, 256, 1, 16, 1 / 4),
+    (512, 512, 257, 4, 1 / 32),
+    (2048, 1024, 384, 16, 1 / 16),
+]
+
+
+@pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("case", CASES)
+def test_tc_parity(case, dt):
+    m, k, n, b, d = case
+    err, Y, _, _ = run_case(m, k, n, b, wl.nnzb_for(m, k, b, d), dt, "tc", seed=m + n + b,
+                            ldx=((n + 7) // 8) * 8)
+    assert not torch.isnan(Y).any()
+    assert err <= TOL[dt], err
+
+
+@pytest.mark.parametrize("dt", [torch.float32, torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("n", [1, 4, 16, 33, 64, 2048])
+def test_gather_parity(n, dt):
+    m, k = 512, 768
+    err, Y, _, _ = run_case(m, k, n, 1, wl.nnzb_for(m, k, 1, 1 / 16), dt, "gather", seed=n)
+    assert not torch.isnan(Y).any()
+    assert err <= TOL[dt], err
+
+
+@pytest.mark.parametrize("b", [1, 4, 8, 16])
+def test_plain_parity(b):
+    m, k, n = 256, 512, 80
+    err, Y, _, _ = run_case(m, k, n, b, wl.nnzb_for(m, k, b, 1 / 8), torch.float32, "plain", seed=b)
+    assert err <= 1e-6, err
+
+
+def test_smoke_config_fp32():
+    c = wl.smoke_case()
+    vals = torch.from_numpy(c["vals"])
+    X = torch.from_numpy(c["X"])
+    plan = S.Plan(256, 256, 64, 4, w_dtype=S.F32, brow=c["brow"], bcol=c["bcol"])
+    plan.pack(vals.cuda())
+    Y = plan.run(X.cuda())
+    Yo = oracle.spmm(256, 256, 4, c["brow"], c["bcol"], vals, X)
+    assert oracle.normwise_err(Y.cpu(), Yo, oracle.block_fro(vals), X) <= 1e-6
+
+
+def _int_case(m, k, n, b, nnzb, seed):
+    rng = np.random.default_rng(seed)
+    mb, kb = m // b, k // b
+    idx = rng.choice(mb * kb, nnzb, replace=False)
+    brow, bcol = (idx // kb).astype(np.int32), (idx % kb).astype(np.int32)
+    vals = rng.integers(-3, 4, size=(nnzb, b, b)).astype(np.float32)
+    X = rng.integers(-3, 4, size=(k, n)).astype(np.float32)
+    return brow, bcol, vals, X
+
+
+@pytest.mark.parametrize("kernel,b,dt", [("tc", 16, torch.float16), ("tc", 8, torch.bfloat16),
+                                         ("tc", 4, torch.float16), ("gather", 1, torch.float16),
+                                         ("gather", 1, torch.bfloat16), ("gather", 1, torch.float32),
+                                         ("plain", 4, torch.float32)])
+def test_exact_integer_inputs(kernel, b, dt):
+    m, k, n = 256, 512, 136
+    brow, bcol, vals, X = _int_case(m, k, n, b, (m // b) * (k // b) // 4, seed=7 * b)
+    plan = S.Plan(m, k, n, b, w_dtype=S.dtype_code(dt), brow=brow, bcol=bcol, kernel=kernel)
+    plan.pack(torch.from_numpy(vals).to(dt).cuda())
+    Y = plan.run(_x_dev(torch.from_numpy(X), dt, 136)).cpu()
+    Yo = oracle.spmm(m, k, b, brow, bcol, vals, X)
+    want = torch.from_numpy(Yo).to(dt)
+    assert torch.equal(Y, want)
+
+
+@pytest.mark.parametrize("kernel,b", [("tc", 16), ("tc", 4), ("gather", 1)])
+def test_split_rows_worst_case(kernel, b):
+    """Appendix A.2's worst case: every block in one block row.  The row is
+    split over several work items and reduced in chunk order."""
+    m, k, n = 512, 2048, 160
+    kb = k // b
+    nnz = min(kb, 96)
+    brow = np.zeros(nnz, np.int32)
+    bcol = np.arange(nnz, dtype=np.int32) * (kb // nnz)
+    rng = np.random.default_rng(1)
+    vals = rng.standard_normal((nnz, b, b)).astype(np.float32)
+    X = rng.standard_normal((k, n)).astype(np.float32)
+    dt = torch.float16
+    plan = S.Plan(m, k, n, b, w_dtype=S.F16, brow=brow, bcol=bcol, kernel=kernel, max_per_item=8)
+    assert plan.info()["n_reductions"] == 1
+    vt = torch.from_numpy(vals).to(dt)
+    plan.pack(vt.cuda())
+    Y = plan.run(_x_dev(torch.from_numpy(X), dt)).cpu()
+    Yo = oracle.spmm(m, k, b, brow, bcol, vt, torch.from_numpy(X).to(dt))
+    err = oracle.normwise_err(Y, Yo, oracle.block_fro(vt), torch.from_numpy(X).to(dt))
+    assert err <= 4e-3
+    assert not torch.any(Y[b:]), "rows outside the single block row must be zero"
+
+
+@pytest.mark.parametrize("kernel,b,dt", [("tc", 16, torch.float16), ("gather", 1, torch.float16),
+                                         ("plain", 8, torch.float32)])
+def test_empty_pattern_zero_fill(kernel, b, dt):
+    m, k, n = 256, 256, 72
+    plan = S.Plan(m, k, n, b, w_dtype=S.dtype_code(dt), brow=[], bcol=[], kernel=kernel)
+    plan.pack(torch.zeros(1, dtype=dt, device="cuda"))
+    Y = torch.full((m, n), 7.0, dtype=dt, device="cuda")
+    plan.run(_x_dev(torch.ones(k, n), dt, 72), Y)
+    assert not torch.any(Y.cpu())
+
+
+def test_deterministic_repeat():
+    m, k, n, b = 1024, 1024, 256, 16
+    err, Y1, _, plan = run_case(m, k, n, b, wl.nnzb_for(m, k, b, 1 / 8), torch.float16, "tc", 3)
+    c = wl.problem(3, m, k, n, b, wl.nnzb_for(m, k, b, 1 / 8))
+    X = torch.from_numpy(c["X"]).half().cuda()
+    for _ in range(3):
+        assert torch.equal(plan.run(X), Y1)
+
+
+def test_run_host_buffers():
+    m, k, n, b = 512, 512, 96, 16
+    c = wl.problem(9, m, k, n, b, wl.nnzb_for(m, k, b, 1 / 8))
+    vals = torch.from_numpy(c["vals"]).half()
+    X = torch.from_numpy(c["X"]).half().pin_memory()
+    plan = S.Plan(m, k, n, b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"])
+    plan.pack(vals.cuda())
+    Y = torch.empty((m, n), dtype=torch.float16).pin_memory()
+    plan.run_host(X, Y)
+    Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X)
+    assert oracle.normwise_err(Y, Yo, oracle.block_fro(vals), X) <= 4e-3
+
+
+def test_not_packed_and_bad_n():
+    plan = S.Plan(256, 256, 64, 16, w_dtype=S.F16, brow=[0], bcol=[0])
+    X = torch.zeros(256, 64, dtype=torch.float16, device="cuda")
+    with pytest.raises(S.SpmmError) as e:
+        plan.run(X)
+    assert e.value.status == S.ERR_NOT_PACKED
+    plan.pack(torch.zeros(256, dtype=torch.float16, device="cuda"))
+    with pytest.raises(S.SpmmError) as e:
+        plan.run(torch.zeros(256, 65, dtype=torch.float16, device="cuda"))
+    assert e.value.status == S.ERR_SHAPE
+
+
+def _sub_oracle(c, rows_blk, dt):
+    """Oracle on a subset of block rows (full-size sampled parity)."""
+    b = c["b"]
+    sel = np.isin(c["brow"], rows_blk)
+    remap = {r: i for i, r in enumerate(rows_blk)}
+    brow = np.array([remap[r] for r in c["brow"][sel]], np.int32)
+    vals = torch.from_numpy(c["vals"][sel]).to(dt)
+    X = torch.from_numpy(c["X"]).to(dt)
+    Yo = oracle.spmm(len(rows_blk) * b, c["k"], b, brow, c["bcol"][sel], vals, X)
+    return Yo, oracle.block_fro(vals), X
+
+
+@pytest.mark.parametrize("b", [1, 4, 8, 16])
+def test_full_size_sweep_sampled(b):
+    """m = k = 4096, n = 2048 FP16 at d = 1/4, in the launch configuration the
+    benchmark times; 4 sampled block rows checked against the oracle."""
+    d = 1 / 4
+    c = wl.sweep_case(b, d)
+    dt = torch.float16
+    plan = S.Plan(4096, 4096, 2048, b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"])
+    plan.pack(torch.from_numpy(c["vals"]).to(dt).cuda())
+    Y = plan.run(torch.from_numpy(c["X"]).to(dt).cuda()).cpu()
+    rows = [0, 17, 4096 // b // 2, 4096 // b - 1]
+    Yo, wf, X = _sub_oracle(c, rows, dt)
+    Ys = torch.cat([Y[r * b:(r + 1) * b] for r in rows])
+    assert oracle.normwise_err(Ys, Yo, wf, X) <= 4e-3
