@@ -1,0 +1,444 @@
+"""Benchmark of the block-sparse x dense product Y = W.X on GB300.
+
+Workload (the static sweep of Table 2, restricted as the paper's headline
+comparisons are): m = k = 4096, n = 2048, FP16 values and X, FP32
+accumulation, block size b in {1, 4, 8, 16} x density d in {1/32, 1/16, 1/8,
+1/4}, uniform random block positions, N(0, 1) values.  One step runs all 16
+products once through the library's public C ABI (AUTO kernel: b = 1 gather
+kernel, b >= 4 tensor-core kernel).  The 16 problems' inputs total about
+0.6 GB, more than twice L2, and each is touched once per step, so every
+launch reads cold inputs.
+
+Prints one JSON line (rank 0).  ``value`` is nonzero-FLOP throughput
+(2 * nnz * n per product, Section 3) of the whole step in TFLOP/s, summed
+over ranks; ``e2e`` is the same metric through ``spmm_run_host`` with X and Y
+in pinned host memory; ``roofline`` describes the dominant kernel family;
+``cpu_baseline`` times the FP64 oracle on a bounded sample.
+``--impl reference`` times that oracle alone, as the reference arm.
+"""
+import argparse
+import ctypes
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}
+N_SMS = 152
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x 2.07 GHz
+ALU_PEAK_TFLOPS = N_SMS * 128 * 2 * 2.070e9 / 1e12
+METRIC = "effective TFLOP/s & %roofline, block-sparse vs plain FP32/dense; serve p50/p99"
+SWEEP_B = (1, 4, 8, 16)
+SWEEP_D = (1 / 32, 1 / 16, 1 / 8, 1 / 4)
+M = K = 4096
+N = 2048
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return dict(FALLBACK), "fallback"
+
+
+# ------------------------------------------------------------ clocks (NVML)
+class ClockSampler:
+    """Samples SM clock and clock-event reasons through NVML every few ms."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, bus_id=None):
+        self.ok = False
+        self.samples = []
+        self.reasons = 0
+        self.max_mhz = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            got = False
+            if bus_id:
+                got = nv.nvmlDeviceGetHandleByPciBusId_v2(bus_id.encode(), ctypes.byref(h)) == 0
+            if not got and nv.nvmlDeviceGetHandleByIndex_v2(0, ctypes.byref(h)) != 0:
+                return
+            self.nv, self.h = nv, h
+            try:
+                self._reasons_fn = nv.nvmlDeviceGetCurrentClocksEventReasons
+            except AttributeError:
+                self._reasons_fn = nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            mx = ctypes.c_uint()
+            if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = mx.value
+            self.ok = True
+        except OSError:
+            pass
+
+    def _run(self):
+        c = ctypes.c_uint()
+        r = ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(c)) == 0:
+                self.samples.append(c.value)
+            if self._reasons_fn(self.h, ctypes.byref(r)) == 0:
+                self.reasons |= r.value
+            time.sleep(0.002)
+
+    def __enter__(self):
+        if self.ok:
+            self._stop = threading.Event()
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            self._stop.set()
+            self._t.join()
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"]}
+        names = [v for k, v in self.REASONS.items() if self.reasons & k]
+        return {"sm_mhz": statistics.median(self.samples), "sm_max_mhz": self.max_mhz,
+                "reasons": names, "samples": len(self.samples)}
+
+
+# ----------------------------------------------------------- distributed
+def dist_setup(gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------- sweep points
+def roof_of(b, nnzb, peaks):
+    """Roofline of one product: nonzero FLOPs, compulsory bytes and the
+    bound (the slower of compute-at-peak and bytes-over-HBM)."""
+    flops = 2.0 * nnzb * b * b * N
+    es = 2
+    vals = nnzb * b * b * es
+    idx = nnzb * 4 + (M // b + 1) * 4
+    xy = (K * N + M * N) * es
+    bytes_ = vals + idx + xy
+    t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
+    if b == 1:
+        t_cmp, unit = flops / (ALU_PEAK_TFLOPS * 1e12), "alu"
+    else:
+        t_cmp, unit = flops / (peaks["bf16_tflops"] * 1e12), "tensor"
+    bound = unit if t_cmp >= t_hbm else "hbm"
+    return flops, bytes_, bound, max(t_cmp, t_hbm)
+
+
+def build_points(torch, S, wl, dev, only=None):
+    pts = []
+    for b in SWEEP_B:
+        for d in SWEEP_D:
+            if only is not None and (b, round(1 / d)) != only:
+                continue
+            c = wl.sweep_case(b, d)
+            vals = torch.from_numpy(c["vals"]).half()
+            X = torch.from_numpy(c["X"]).half()
+            plan = S.Plan(M, K, N, b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"])
+            plan.pack(vals.to(dev))
+            pts.append(dict(b=b, d=d, nnzb=len(c["brow"]), plan=plan, X=X.to(dev),
+                            Y=torch.empty((M, N), dtype=torch.float16, device=dev),
+                            Xh=X.pin_memory(),
+                            Yh=torch.empty((M, N), dtype=torch.float16).pin_memory(),
+                            kernel=plan.info()["kernel"], c=c))
+            del vals
+    torch.cuda.synchronize()
+    return pts
+
+
+def launches_per_run(p):
+    info = p["plan"].info()
+    return 1 + (1 if info["n_reductions"] > 0 else 0)
+
+
+# ------------------------------------------------------------ CPU oracle
+_ORACLE_CASE = {}
+
+
+def oracle_sample(target_s, b=16, d=1 / 16):
+    """Times the FP64 oracle on the first block rows of one sweep point,
+    sized to about target_s seconds of single-thread CPU work (only the
+    oracle call itself is timed)."""
+    import oracle
+    import torch
+    from paper_2303_16999_gb300 import workloads as wl
+    key = (b, d)
+    if key not in _ORACLE_CASE:
+        c = wl.sweep_case(b, d)
+        _ORACLE_CASE[key] = (c, torch.from_numpy(c["X"]).half(), torch.from_numpy(c["vals"]).half())
+    c, X, vals = _ORACLE_CASE[key]
+
+    def run(rows):
+        sel = c["brow"] < rows
+        br, bc, vv = c["brow"][sel], c["bcol"][sel], vals[sel]
+        t0 = time.perf_counter()
+        oracle.spmm(rows * b, K, b, br, bc, vv, X)
+        dt = time.perf_counter() - t0
+        return dt, 2.0 * int(sel.sum()) * b * b * N
+
+    dt, fl = run(2)
+    rate = fl / max(dt, 1e-9)
+    rows = int(min(M // b, max(1, target_s * rate / max(fl / 2, 1))))
+    dt, fl = run(rows)
+    return dict(value=fl / dt / 1e12, unit="TFLOP/s", cores=1, kind="oracle",
+                sample="FP64 single-thread oracle on the first %d of %d block rows of the "
+                       "b=%d, d=1/%d, m=k=4096, n=2048 point (%.2f GFLOP, %.1f s)"
+                       % (rows, M // b, b, round(1 / d), fl / 1e9, dt),
+                seconds=dt, gflop=fl / 1e9)
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    total = args.steps + args.warmup
+    per_step = max(0.05, min(2.0, 120.0 / max(total, 1)))
+    for _ in range(args.warmup):
+        oracle_sample(per_step)
+    fl = 0.0
+    dt = 0.0
+    last = None
+    for _ in range(args.steps):
+        last = oracle_sample(per_step)
+        fl += last["gflop"] * 1e9
+        dt += last["seconds"]
+    v = fl / dt / 1e12
+    cpu = dict(value=v, unit="TFLOP/s", cores=1, kind="oracle", sample=last["sample"])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(), "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config():
+    return {"workload": "static sweep m=k=4096 n=2048 FP16, b in {1,4,8,16} x d in "
+                        "{1/32,1/16,1/8,1/4}, 16 products per step",
+            "m": M, "k": K, "n": N, "block_sizes": list(SWEEP_B),
+            "densities": ["1/32", "1/16", "1/8", "1/4"], "mode": "static",
+            "parallelism": "replicas (weak)",
+            "l2": "inputs larger than L2: 16 problems (~0.6 GB) each read once per step"}
+
+
+# ------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--point", default=None,
+                    help="run one sweep point only, 'b:1/d' e.g. 16:4 (profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    from paper_2303_16999_gb300 import spmm as S
+    from paper_2303_16999_gb300 import workloads as wl
+    peaks, peak_src = load_peaks()
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local)
+    S.lib()
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_sample(12.0, b=16, d=1 / 4)  # before the GPU work: no process forks after it
+    only = tuple(int(v) for v in args.point.split(":")) if args.point else None
+    pts = build_points(torch, S, wl, dev, only)
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        for i, p in enumerate(pts):
+            if evs is not None:
+                evs[i][0].record(stream)
+            p["plan"].run(p["X"], p["Y"])
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+            for _ in pts] for _ in range(args.steps)]
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    try:
+        bus = torch.cuda.get_device_properties(dev).pci_bus_id
+    except Exception:
+        bus = None
+    sampler = ClockSampler(bus)
+    barrier(world)
+    torch.cuda.synchronize()
+    with sampler:
+        start.record(stream)
+        for s in range(args.steps):
+            step(evs[s])
+        end.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    t_ms = start.elapsed_time(end)
+    t_ms = max_over_ranks(t_ms, world)
+
+    per = [[evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(args.steps)]
+           for i in range(len(pts))]
+    flops_step = sum(2.0 * p["nnzb"] * p["b"] ** 2 * N for p in pts)
+    value = flops_step * args.steps * world / (t_ms * 1e-3) / 1e12
+
+    points, fam = [], {}
+    for i, p in enumerate(pts):
+        fl, by, bound, t_roof = roof_of(p["b"], p["nnzb"], peaks)
+        us = statistics.median(per[i]) * 1e3
+        kern = {1: "plain", 2: "gather", 3: "tc"}[p["kernel"]]
+        points.append({"b": p["b"], "d": "1/%d" % round(1 / p["d"]), "kernel": kern,
+                       "us_median": round(us, 2),
+                       "tflops_nz": round(fl / (us * 1e-6) / 1e12, 2),
+                       "tflops_dense_equiv": round(2.0 * M * K * N / (us * 1e-6) / 1e12, 2),
+                       "gbs_compulsory": round(by / (us * 1e-6) / 1e9, 1),
+                       "bound": bound, "roof_frac": round(t_roof / (us * 1e-6), 3)})
+        f = fam.setdefault(kern, {"t": 0.0, "flops": 0.0, "bytes": 0.0, "bounds": set()})
+        f["t"] += sum(per[i]) * 1e-3
+        f["flops"] += fl * args.steps
+        f["bytes"] += by * args.steps
+        f["bounds"].add(bound)
+    dom = max(fam, key=lambda k: fam[k]["t"])
+    F = fam[dom]
+    if F["bounds"] == {"hbm"}:
+        ach, pk, unit, bnd = F["bytes"] / F["t"] / 1e9, peaks["hbm_gbs"], "GB/s", "hbm"
+    elif "alu" in F["bounds"]:
+        ach, pk, unit, bnd = F["flops"] / F["t"] / 1e12, ALU_PEAK_TFLOPS, "TFLOP/s", "alu"
+    else:
+        ach, pk, unit, bnd = F["flops"] / F["t"] / 1e12, peaks["bf16_tflops"], "TFLOP/s", "tensor"
+    roofline = {"bound": bnd, "achieved": round(ach, 2), "peak": round(pk, 1), "unit": unit,
+                "frac": round(ach / pk, 4), "traffic": None, "kernel": dom,
+                "share_of_step": round(F["t"] / (sum(v["t"] for v in fam.values())), 3),
+                "peak_source": ("FP32 lanes x clock (152x128x2x2.07 GHz)" if bnd == "alu"
+                                else "%s (MEASURED_PEAKS.json)" % peak_src)}
+
+    # end to end through the public API with host buffers
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for p in pts:
+            p["plan"].run_host(p["Xh"], p["Yh"])
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e = {"value": flops_step * args.e2e_steps * world / e2e_s / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": sum(p["Xh"].numel() * 2 for p in pts),
+           "d2h_bytes_per_step": sum(p["Yh"].numel() * 2 for p in pts),
+           "steps": args.e2e_steps}
+
+    comparators = None
+    if rank == 0 and not args.no_comparators and any(
+            q["b"] == 16 and abs(q["d"] - 1 / 16) < 1e-12 for q in pts):
+        comparators = run_comparators(torch, S, wl, dev, pts)
+
+    launches = sum(launches_per_run(p) for p in pts) * args.steps
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f16 (fp32 accumulate)",
+                "data": "synthetic", "config": workload_config(),
+                "e2e": e2e, "gpu_launches": launches, "clocks": sampler.summary(),
+                "roofline": roofline, "cpu_baseline": cpu, "points": points,
+                "comparators": comparators}
+        print(json.dumps(line))
+    for p in pts:
+        p["plan"].close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def run_comparators(torch, S, wl, dev, pts):
+    """Context on the same GPU for b = 16, d = 1/16: the plain FP32 kernel on
+    FP32 copies of the inputs, and cuBLAS dense FP16 GEMM on the densified W."""
+    p = next(q for q in pts if q["b"] == 16 and abs(q["d"] - 1 / 16) < 1e-12)
+    c = p["c"]
+    out = {}
+
+    def timeit(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(reps):
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts) * 1e3
+
+    fl = 2.0 * p["nnzb"] * 256 * N
+    plan32 = S.Plan(M, K, N, 16, w_dtype=S.F32, brow=c["brow"], bcol=c["bcol"], kernel="plain")
+    plan32.pack(torch.from_numpy(c["vals"]).half().float().to(dev))
+    X32 = p["X"].float()
+    Y32 = torch.empty((M, N), dtype=torch.float32, device=dev)
+    us = timeit(lambda: plan32.run(X32, Y32))
+    out["plain_fp32_kernel"] = {"us": round(us, 1), "tflops_nz": round(fl / us / 1e6, 3)}
+    plan32.close()
+    Wd = torch.zeros((M, K), dtype=torch.float16, device=dev)
+    v = torch.from_numpy(c["vals"]).half().to(dev)
+    r = torch.from_numpy(c["brow"]).long().to(dev)
+    cc = torch.from_numpy(c["bcol"]).long().to(dev)
+    Wd.view(M // 16, 16, K // 16, 16).permute(0, 2, 1, 3)[r, cc] = v
+    us = timeit(lambda: torch.matmul(Wd, p["X"]))
+    out["cublas_dense_fp16"] = {"us": round(us, 1), "tflops_nz": round(fl / us / 1e6, 2),
+                                "tflops_dense": round(2.0 * M * K * N / us / 1e6, 1)}
+    out["point"] = "b=16, d=1/16, m=k=4096, n=2048"
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -194,11 +194,14 @@ typedef enum {
     SPMM_ARR_GRP_EBEG = 6,  /* TC: int32[n_groups + 1] first entry of each group */
     SPMM_ARR_ENT_COL = 7,   /* TC: int32[n_entries] tile column of each entry */
     SPMM_ARR_ENT_TBEG = 8,  /* TC: int32[n_entries + 1] first tile slot of each entry */
-    SPMM_ARR_TILE_ROW = 9,  /* TC: int32[n_tiles] tile row within its group */
+    SPMM_ARR_TILE_ROW = 9,  /* TC: int32[n_tiles] group row of each tile slot (slots of an entry
+                               cover its MMA intervals; rows without a block are zero tiles) */
     SPMM_ARR_BLK_SLOT = 10, /* TC: int32[nnzb] tile slot of each user block */
     SPMM_ARR_BLK_OFF = 11,  /* TC: int32[nnzb] offset (row*16 + col) of the block in its tile */
     SPMM_ARR_WS_ROW0 = 12,  /* int64[n_ws_slots] first workspace row of each split item */
-    SPMM_ARR_RED = 13       /* int32[n_reductions * 3]: group/row, first ws slot, n_chunks */
+    SPMM_ARR_RED = 13,      /* int32[n_reductions * 3]: group/row, first ws slot, n_chunks */
+    SPMM_ARR_ENT_COVER = 14 /* TC: int32[n_entries]: bits 0-15 rows covered by the entry's MMA
+                               intervals, bits 16-31 the rows where an interval starts */
 } spmm_array;
 
 /* Copies array `which` into host memory `dst` (capacity in elements) and

@@ -162,7 +162,35 @@ def row_plan(mb, row_ptr, C1, sort_items=True):
 
 
 # ---------------------------------------- b >= 4 tensor-core work items ----
-def tc_plan(m, k, b, brow, bcol, R, C, sort_items=True):
+def mma_cost(L):
+    """Cost, in units of two SM cycles, of one tensor-core product covering L
+    consecutive tile rows (N = 16 L): at least 40 cycles to issue, 8 cycles per
+    16 rows, plus one unit per tile slot moved through shared memory."""
+    return max(20, 4 * L) + L
+
+
+def cover_intervals(rows):
+    """Cheapest cover of an entry's tile rows (ascending) by intervals of
+    consecutive rows under ``mma_cost``; rows inside an interval without a
+    tile become zero tiles.  Exact DP over the rows; on ties the earliest
+    split point wins.  Returns [(start row, length), ...] ascending."""
+    n = len(rows)
+    dp = [0] + [None] * n
+    arg = [0] * (n + 1)
+    for j in range(1, n + 1):
+        for i in range(j):
+            c = dp[i] + mma_cost(rows[j - 1] - rows[i] + 1)
+            if dp[j] is None or c < dp[j]:
+                dp[j], arg[j] = c, i
+    out, j = [], n
+    while j > 0:
+        i = arg[j]
+        out.append((rows[i], rows[j - 1] - rows[i] + 1))
+        j = i
+    return out[::-1]
+
+
+def tc_plan(m, k, b, brow, bcol, R, C, sort_items=True, pad=None):
     """Decomposition of the tensor-core kernel.
 
     * Each b x b block lies in 16 x 16 tile (tr, tc) = (brow*b // 16,
@@ -170,14 +198,19 @@ def tc_plan(m, k, b, brow, bcol, R, C, sort_items=True):
     * Tile rows form groups by ``group_partition(m // 16, R)``.
     * A group's entries are the distinct tile columns of its tiles, ascending;
       entries of all groups are concatenated in group order.
-    * Tiles are packed in (group, tile column, tile row) order, so the tiles
-      of one entry are contiguous; ent_tbeg[e] is the first tile slot of
-      entry e (length E + 1).
+    * Each entry's rows are covered by intervals, one MMA each:
+      ``cover_intervals`` when ``pad`` (static plans), else one interval per
+      row (dynamic plans).  The entry owns one tile slot per covered row, in
+      interval order; ent_tbeg[e] is the first slot of entry e (length
+      E + 1); ent_cover[e] holds the covered-row mask in bits 0-15 and the
+      interval-start mask in bits 16-31; tile_row[s] is the group row of slot s.
     * Items: a group with L entries becomes ``chunk_sizes(L, C)`` chunks of
       consecutive entries; a group with no entries is one zero-fill item.
-      cost = tiles in the chunk + entries in the chunk.  Static plans order
+      cost = slots in the chunk + entries in the chunk.  Static plans order
       items by (-cost, group, chunk); dynamic plans by (group, chunk).
     """
+    if pad is None:
+        pad = sort_items
     mt = m // TILE
     nnzb = len(brow)
     tr = [int(brow[p]) * b // TILE for p in range(nnzb)]
@@ -193,21 +226,32 @@ def tc_plan(m, k, b, brow, bcol, R, C, sort_items=True):
         acc += sz
     grp_rows = np.array(sizes, dtype=np.int32)
 
-    tiles = sorted(set(zip(tr, tcol)), key=lambda t: (group_of[t[0]], t[1], t[0]))
-    slot_of = {t: s for s, t in enumerate(tiles)}
-    tile_row = np.array([t[0] - grp_row0[group_of[t[0]]] for t in tiles], dtype=np.int32)
-
-    ent_col, ent_tbeg, grp_ebeg = [], [], [0] * (len(sizes) + 1)
-    for s, t in enumerate(tiles):
+    # entries: (group, tile column) -> sorted group rows holding a tile
+    ent_rows = {}
+    for t in set(zip(tr, tcol)):
         g = group_of[t[0]]
-        if not ent_col or ent_grp_last != g or ent_col[-1] != t[1]:
-            ent_col.append(t[1])
-            ent_tbeg.append(s)
-            ent_grp_last = g
-            grp_ebeg[g + 1] += 1
+        ent_rows.setdefault((g, t[1]), []).append(t[0] - int(grp_row0[g]))
+    keys = sorted(ent_rows)
+    ent_col, ent_tbeg, ent_cover, tile_row = [], [], [], []
+    grp_ebeg = [0] * (len(sizes) + 1)
+    slot_of = {}
+    for (g, c) in keys:
+        rows = sorted(ent_rows[(g, c)])
+        ivs = cover_intervals(rows) if pad else [(r, 1) for r in rows]
+        ent_col.append(c)
+        ent_tbeg.append(len(tile_row))
+        cov = starts = 0
+        for (r0, L) in ivs:
+            starts |= 1 << r0
+            for r in range(r0, r0 + L):
+                cov |= 1 << r
+                slot_of[(int(grp_row0[g]) + r, c)] = len(tile_row)
+                tile_row.append(r)
+        ent_cover.append(cov | (starts << 16))
+        grp_ebeg[g + 1] += 1
     for g in range(len(sizes)):
         grp_ebeg[g + 1] += grp_ebeg[g]
-    ent_tbeg.append(len(tiles))
+    ent_tbeg.append(len(tile_row))
 
     items = []
     for g in range(len(sizes)):
@@ -215,9 +259,9 @@ def tc_plan(m, k, b, brow, bcol, R, C, sort_items=True):
         csz = chunk_sizes(e1 - e0, C)
         e = e0
         for ci, sz in enumerate(csz):
-            ntile = ent_tbeg[e + sz] - ent_tbeg[e]
+            nslot = ent_tbeg[e + sz] - ent_tbeg[e]
             items.append(dict(grp=g, beg=e, end=e + sz, chunk=ci, nch=len(csz),
-                              cost=ntile + sz))
+                              cost=nslot + sz))
             e += sz
     if sort_items:
         items.sort(key=lambda it: (-it["cost"], it["grp"], it["chunk"]))
@@ -231,7 +275,8 @@ def tc_plan(m, k, b, brow, bcol, R, C, sort_items=True):
         grp_ebeg=np.array(grp_ebeg, dtype=np.int32),
         ent_col=np.array(ent_col, dtype=np.int32),
         ent_tbeg=np.array(ent_tbeg, dtype=np.int32),
-        tile_row=tile_row,
+        ent_cover=np.array(ent_cover, dtype=np.uint32).view(np.int32),
+        tile_row=np.array(tile_row, dtype=np.int32),
         items=_items_array(items), ws_row0=ws_row0, ws_rows=ws_rows,
         red=_reductions(items),
         blk_slot=blk_slot, blk_off=blk_off,

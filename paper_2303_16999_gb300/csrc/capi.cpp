@@ -134,6 +134,7 @@ static spmm_status upload_plan(spmm_plan *p) {
         UP(d_grp_ebeg, grp_ebeg);
         UP(d_ent_col, ent_col);
         UP(d_ent_tbeg, ent_tbeg);
+        UP(d_ent_cover, ent_cover);
         UP(d_tile_row, tile_row);
         UP(d_blk_slot, blk_slot);
         UP(d_blk_off, blk_off);
@@ -251,13 +252,13 @@ spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spm
                     // groups well above the mean are split
                     HostPlan probe;
                     build_tc_plan(m, k, b, p->nnzb, pattern->brow, pattern->bcol, p->R, 1 << 30,
-                                  false, probe);
+                                  false, false, probe);
                     const int64_t G = (int64_t)probe.grp_rows.size();
                     const int64_t E = (int64_t)probe.ent_col.size();
                     p->C = (int)std::max<int64_t>(16, G ? (5 * E + 4 * G - 1) / (4 * G) : 16);
                 }
                 build_tc_plan(m, k, b, p->nnzb, pattern->brow, pattern->bcol, p->R, p->C, true,
-                              p->hp);
+                              true, p->hp);
             }
             p->n_items = (int64_t)p->hp.items.size() / kItemFields;
             p->n_red = (int64_t)p->hp.red.size() / 3;
@@ -558,6 +559,7 @@ spmm_status spmm_plan_get_array(spmm_plan *p, spmm_array which, void *dst, int64
         case SPMM_ARR_BLK_OFF: src = hp.blk_off.data(); n = hp.blk_off.size(); break;
         case SPMM_ARR_WS_ROW0: src = hp.ws_row0.data(); n = hp.ws_row0.size(); es = 8; break;
         case SPMM_ARR_RED: src = hp.red.data(); n = hp.red.size(); break;
+        case SPMM_ARR_ENT_COVER: src = hp.ent_cover.data(); n = hp.ent_cover.size(); break;
         default: set_error("unknown array %d", (int)which); return SPMM_ERR_ARG;
     }
     *count = n;

@@ -9,8 +9,22 @@
 // A CTA owns a group of up to 16 tile rows (256 rows of Y) and 128 columns
 // of n; it walks the union of the group's tile columns ("entries"), loading
 // each X slab once and applying it to every tile of that column, with one
-// TMEM accumulator (16 columns) per tile row.  TMEM holds two accumulator
-// sets so the epilogue of one work unit overlaps the MMAs of the next.
+// TMEM accumulator (16 columns) per tile row.  The planner covers each
+// entry's rows by intervals of consecutive rows (zero tiles fill the gaps);
+// one MMA with N = 16 x (interval length) serves an interval, since a
+// 128 x 16 x 16 MMA costs about as much to issue as a 128 x 80 x 16 one.
+// Accumulators start at zero in TMEM (the epilogue clears what it reads),
+// so every MMA accumulates.  TMEM holds two accumulator sets so
+// the epilogue of one work unit overlaps the MMAs of the next.
+//
+// Pipeline: a stage holds up to kEntStage entries (X slabs) and up to
+// kTileStage W tiles.  The producer warp reads entry metadata 32 entries at
+// a time (coalesced, broadcast by shuffles) so its issuing lane never waits
+// on a dependent global load per stage; the X slabs of a stage are requested
+// by one TMA instruction executed by one lane per entry (both 64-column
+// halves of a slab in one 3-D box when n is a multiple of 64), and the
+// stage's W tiles, contiguous in the packed array, by one bulk copy.  The
+// MMA warp stays converged and issues through elect.sync.
 //
 // Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
 // TMEM owner, warps 2..5 = epilogue (TMEM -> registers -> Y or workspace).
@@ -29,21 +43,43 @@
 namespace spmm {
 namespace {
 
-constexpr int kStages = 12;
+#ifndef SPMM_TC_CTAS
+#define SPMM_TC_CTAS 2      // CTAs per SM
+#define SPMM_TC_RCAP 16     // tile rows per group (accumulator columns / 16)
+#define SPMM_TC_STAGES 3
+#define SPMM_TC_ENT 4       // X slabs per stage
+#define SPMM_TC_TILES 32    // W tiles per stage
+#endif
+constexpr int kEntStage = SPMM_TC_ENT;                            // X slabs per stage
+constexpr int kTileStage = SPMM_TC_TILES;                         // W tiles per stage
 constexpr int kSlabBytes = kTile * kNTile * 2;                    // 4096: 16 k x 128 n, 16-bit
-constexpr int kStageBytes = kSlabBytes + kMaxGroupRows * kTileBytes16;  // 12288
-constexpr int kAccCols = kMaxGroupRows * kTile;                   // 256 TMEM columns per buffer
+constexpr int kStageBytes = kEntStage * kSlabBytes + kTileStage * kTileBytes16;  // 32 KB
+constexpr int kStages = SPMM_TC_STAGES;
+constexpr int kRowCap = SPMM_TC_RCAP;
+constexpr int kAccCols = kRowCap * kTile;                         // TMEM columns per buffer
+// Two CTAs share an SM: each holds one accumulator set (256 of the SM's 512
+// TMEM columns) and half the shared memory, so the two CTAs' producer / MMA
+// pipelines run side by side and one CTA's epilogue overlaps the other's MMAs.
+// (A single warp cannot issue its copies and MMAs faster than its own
+// dependent scalar work allows; a second pipeline per SM doubles that rate.)
+constexpr int kAccBufs = 1;
+constexpr int kCtasPerSm = SPMM_TC_CTAS;
+static_assert(kRowCap <= kMaxGroupRows && kTileStage >= kRowCap, "stage must hold a full entry");
 constexpr int kThreads = 192;
 constexpr unsigned long long kWaitNs = 2000000000ull;             // 2 s per wait
 
+struct StageMeta {
+    uint32_t nent;                 // entries in the stage; bit 31: last stage of the unit
+    uint32_t cover[kEntStage];     // per entry: covered rows | interval starts << 16
+};
+
 struct __align__(8) Smem {
-    uint64_t full[kStages], empty[kStages], accf[2], acce[2];
-    int32_t ntile[kStages];
-    uint8_t rows[kStages][kMaxGroupRows];
-    uint32_t acc_mask[2];
+    uint64_t full[kStages], empty[kStages], accf[kAccBufs], acce[kAccBufs];
+    StageMeta meta[kStages];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
     int32_t issued, consumed;
+    int64_t nitems;
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -55,11 +91,6 @@ __device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t *b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
-                 "r"(bytes)
-                 : "memory");
 }
 __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
     uint32_t ok;
@@ -87,22 +118,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, Smem *sm
         if (gtimer() - t0 > kWaitNs) return false;
     }
 }
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
-                                          uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_u32(dst)),
-        "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -115,13 +130,45 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar) {
             smem_u32(bar))
         : "memory");
 }
-__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
-                                       uint32_t acc) {
+// Asynchronous copies into shared memory, completing on an mbarrier.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar) {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
         : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y,
+                                            int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// Arrives once on the barrier and raises its expected transaction bytes.
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One MMA issued by a single elected lane of a converged warp.
+__device__ __forceinline__ void tc_mma_elect(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                             uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p, e;\n setp.ne.b32 p, %4, 0;\n elect.sync _|e, 0xffffffff;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     uint32_t r[16];
@@ -135,6 +182,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+    const uint32_t z = 0;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+        "%1,%1};" ::"r"(taddr),
+        "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading
@@ -168,7 +227,7 @@ struct TcArgs {
     const int32_t *items;
     const int32_t *n_items_dev;  // dynamic plans: item count on the device (else null)
     int64_t n_items;
-    const int32_t *grp_row0, *grp_rows, *ent_col, *ent_tbeg, *tile_row;
+    const int32_t *grp_row0, *grp_rows, *ent_col, *ent_tbeg, *ent_cover;
     const uint8_t *packed;       // 16 x 16 tiles, 512 B each, MMA B layout
     void *Y;
     int64_t ldy, n;
@@ -176,39 +235,39 @@ struct TcArgs {
     const int64_t *ws_row0;
     int32_t *status;
     int ntn;                     // n tiles of 128
-    uint32_t a_lbo, a_sbo;
+    int x3d;                     // 1: X map is 3-D (64, k, n/64), one box per slab
 };
 
 __device__ __forceinline__ void record(int32_t *status, int32_t code) {
     atomicCAS(status, 0, code);
 }
 
+// A-operand descriptor: X slab, MN-major, 128-byte swizzle; the two 64-column
+// halves of the slab are 2048 B apart (leading offset), the two 8-row k
+// groups 1024 B apart (stride offset).
+__device__ __forceinline__ uint64_t a_desc(uint32_t addr) { return smem_desc(addr, 2048, 1024, 2); }
+// B-operand descriptor: one W tile, K-major, no swizzle; 8 x 8 core matrices,
+// k-adjacent ones 128 B apart (leading), row-adjacent ones 256 B (stride).
+__device__ __forceinline__ uint64_t b_desc(uint32_t addr) { return smem_desc(addr, 128, 256, 0); }
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
     tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs args) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *stages =
-        (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *stages = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     Smem *sm = (Smem *)(stages + kStages * kStageBytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    __shared__ int64_t s_nitems;
     if (threadIdx.x == 0) {
         // dynamic plans: a pattern rejected on the device leaves Y unwritten
         const bool skip = args.n_items_dev && *(volatile int32_t *)args.status != 0;
-        s_nitems = skip ? 0 : (args.n_items_dev ? (int64_t)*args.n_items_dev : args.n_items);
-    }
-    __syncthreads();
-    const int64_t nunits = s_nitems * args.ntn;
-    if (nunits == 0) return;
-
-    if (threadIdx.x == 0) {
+        sm->nitems = skip ? 0 : (args.n_items_dev ? (int64_t)*args.n_items_dev : args.n_items);
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&sm->full[s], 1);
             mbar_init(&sm->empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&sm->accf[b], 2);    // MMA completion + the issuer's mask hand-off
+        for (int b = 0; b < kAccBufs; ++b) {
+            mbar_init(&sm->accf[b], 1);    // MMA completion
             mbar_init(&sm->acce[b], 128);  // every epilogue thread
         }
         sm->abort_flag = 0;
@@ -216,101 +275,165 @@ __global__ void __launch_bounds__(kThreads, 1)
         sm->consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    __syncthreads();
+    const int64_t nunits = sm->nitems * args.ntn;
+    if (nunits == 0) return;
     if (warp == 1) {
         asm volatile(
             "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                 smem_u32(&sm->tmem_base)),
-            "r"(2 * kAccCols));
+            "r"(kAccBufs * kAccCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sm->tmem_base;
+    if (warp >= 2) {
+        // accumulators start at zero: each epilogue warp clears its lane quarter
+        const uint32_t lq = (uint32_t)((warp & 3) * 32) << 16;
+        for (int c = 0; c < kAccBufs * kAccCols; c += 16) tmem_zero16(tmem + lq + c);
+        tmem_wait_st();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
-        if (lane == 0) {
-            int stage = 0;
-            uint32_t phase = 0;
-            int32_t issued = 0;
-            for (int64_t u = blockIdx.x; u < nunits && !sm->abort_flag; u += gridDim.x) {
-                const int32_t *it = args.items + (u / args.ntn) * kItemFields;
-                const int n0 = (int)(u % args.ntn) * kNTile;
-                for (int32_t e = it[1]; e < it[2]; ++e) {
-                    if (!mbar_wait(&sm->empty[stage], phase ^ 1, sm)) {
-                        record(args.status, kDevTimeout);
-                        sm->abort_flag = 1;
+        int stage = 0;
+        uint32_t phase = 0;
+        int32_t issued = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
+            const int32_t *it = args.items + (u / args.ntn) * kItemFields;
+            const int32_t e0 = it[1], e1 = it[2];
+            const int n0 = (int)(u % args.ntn) * kNTile;
+            for (int32_t eb = e0; ok && eb < e1; eb += 32) {
+                // lane l holds the metadata of entry eb + l
+                const int32_t e = eb + lane;
+                const bool valid = e < e1;
+                const int32_t mcol = valid ? args.ent_col[e] : 0;
+                const int32_t mtb = valid ? args.ent_tbeg[e] : 0;
+                const uint32_t mcov = valid ? (uint32_t)args.ent_cover[e] : 0u;
+                const int mslots = __popc(mcov & 0xFFFFu);
+                const int cnt = min(32, e1 - eb);
+                for (int j = 0; j < cnt;) {
+                    // a stage: consecutive entries j .. j+nent-1 while they fit
+                    int nent = 0, slots = 0;
+                    while (j + nent < cnt && nent < kEntStage) {
+                        const int t = __shfl_sync(0xffffffffu, mslots, j + nent);
+                        if (slots + t > kTileStage) break;
+                        slots += t;
+                        ++nent;
+                    }
+                    int w = 1;
+                    if (lane == 0) w = mbar_wait(&sm->empty[stage], phase ^ 1, sm) ? 1 : 0;
+                    if (!__shfl_sync(0xffffffffu, w, 0)) {
+                        ok = false;
                         break;
                     }
-                    const int32_t tb = args.ent_tbeg[e];
-                    const int32_t nt = args.ent_tbeg[e + 1] - tb;
-                    const int32_t col = args.ent_col[e];
-                    sm->ntile[stage] = nt;
-                    for (int j = 0; j < nt; ++j) sm->rows[stage][j] = (uint8_t)args.tile_row[tb + j];
+                    const int32_t stb = __shfl_sync(0xffffffffu, mtb, j);
+                    const bool last = (j + nent == cnt) && (eb + 32 >= e1);
                     uint8_t *st = stages + stage * kStageBytes;
-                    mbar_expect_tx(&sm->full[stage], kSlabBytes + nt * kTileBytes16);
-                    tma_load_2d(st, &xmap, n0, col * kTile, &sm->full[stage]);
-                    tma_load_2d(st + kSlabBytes / 2, &xmap, n0 + kNTile / 2, col * kTile,
-                                &sm->full[stage]);
-                    bulk_load(st + kSlabBytes, args.packed + (int64_t)tb * kTileBytes16,
-                              nt * kTileBytes16, &sm->full[stage]);
+                    const bool mine = lane >= j && lane < j + nent;
+                    if (mine) sm->meta[stage].cover[lane - j] = mcov;
+                    if (lane == 0) sm->meta[stage].nent = (uint32_t)nent | (last ? 0x80000000u : 0u);
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive_tx(&sm->full[stage], nent * kSlabBytes + slots * kTileBytes16);
+                        bulk_load(st + kEntStage * kSlabBytes, args.packed + (int64_t)stb * kTileBytes16,
+                                  slots * kTileBytes16, &sm->full[stage]);
+                    }
+                    if (mine) {
+                        uint8_t *slab = st + (lane - j) * kSlabBytes;
+                        if (args.x3d) {
+                            tma_load_3d(slab, &xmap, 0, mcol * kTile, n0 / (kNTile / 2),
+                                        &sm->full[stage]);
+                        } else {
+                            tma_load_2d(slab, &xmap, n0, mcol * kTile, &sm->full[stage]);
+                            tma_load_2d(slab + kSlabBytes / 2, &xmap, n0 + kNTile / 2,
+                                        mcol * kTile, &sm->full[stage]);
+                        }
+                    }
+                    __syncwarp();
                     ++issued;
                     if (++stage == kStages) {
                         stage = 0;
                         phase ^= 1;
                     }
+                    j += nent;
                 }
             }
-            sm->issued = issued;
         }
+        if (!ok && lane == 0) {
+            record(args.status, kDevTimeout);
+            sm->abort_flag = 1;
+        }
+        if (lane == 0) sm->issued = issued;
     } else if (warp == 1) {
-        // ------------------------------------------------- MMA issuer
-        if (lane == 0) {
-            constexpr uint32_t idesc = make_idesc(Cvt<T>::fmt, kNTile, kTile);
-            int stage = 0;
-            uint32_t phase = 0;
-            int32_t consumed = 0;
-            int local = 0;
-            for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, ++local) {
-                const int32_t *it = args.items + (u / args.ntn) * kItemFields;
-                const int ab = local & 1;
-                const uint32_t aphase = (local >> 1) & 1;
-                bool ok = mbar_wait(&sm->acce[ab], aphase ^ 1, sm);
-                tc_fence_after();
-                uint32_t mask = 0;
-                for (int32_t e = it[1]; ok && e < it[2]; ++e) {
-                    if (!mbar_wait(&sm->full[stage], phase, sm)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    ++consumed;
-                    const int nt = sm->ntile[stage];
-                    const uint32_t sbase = smem_u32(stages + stage * kStageBytes);
-                    const uint64_t adesc = smem_desc(sbase, args.a_lbo, args.a_sbo, 2);
-                    for (int j = 0; j < nt; ++j) {
-                        const uint32_t row = sm->rows[stage][j];
-                        const uint64_t bdesc =
-                            smem_desc(sbase + kSlabBytes + j * kTileBytes16, 128, 256, 0);
-                        tc_mma(tmem + ab * kAccCols + row * kTile, adesc, bdesc, idesc,
-                               (mask >> row) & 1u);
-                        mask |= 1u << row;
-                    }
-                    tc_commit(&sm->empty[stage]);
-                    if (++stage == kStages) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
-                }
-                if (!ok) {
-                    record(args.status, kDevTimeout);
-                    sm->abort_flag = 1;
+        // ---------------------------------- MMA issuer (converged warp)
+        constexpr uint32_t idesc0 = make_idesc(Cvt<T>::fmt, kNTile, 0);
+        int stage = 0;
+        uint32_t phase = 0;
+        int32_t consumed = 0;
+        int local = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, ++local) {
+            const int32_t *it = args.items + (u / args.ntn) * kItemFields;
+            const bool has_entries = it[2] > it[1];
+            const int ab = local % kAccBufs;
+            const uint32_t aphase = (local / kAccBufs) & 1;
+            int w = 1;
+            if (lane == 0) w = mbar_wait(&sm->acce[ab], aphase ^ 1, sm) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+            tc_fence_after();
+            const uint32_t dbase = tmem + ab * kAccCols;
+            bool last = !has_entries;
+            while (ok && !last) {
+                if (lane == 0) w = mbar_wait(&sm->full[stage], phase, sm) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, w, 0)) {
+                    ok = false;
                     break;
                 }
-                sm->acc_mask[ab] = mask;
-                tc_commit(&sm->accf[ab]);
-                mbar_arrive(&sm->accf[ab]);
+                tc_fence_after();
+                ++consumed;
+                const uint32_t mnent = __shfl_sync(0xffffffffu, sm->meta[stage].nent, 0);
+                const int nent = (int)(mnent & 0xffu);
+                last = (mnent >> 31) != 0;
+                const uint32_t sbase = smem_u32(stages + stage * kStageBytes);
+                uint64_t bdesc = b_desc(sbase + kEntStage * kSlabBytes);
+                for (int i = 0; i < nent; ++i) {
+                    const uint64_t adesc = a_desc(sbase + i * kSlabBytes);
+                    const uint32_t c = __shfl_sync(0xffffffffu, sm->meta[stage].cover[i], 0);
+                    const uint32_t cov = c & 0xFFFFu;
+                    uint32_t starts = c >> 16;
+                    while (starts) {
+                        const uint32_t r0 = __ffs(starts) - 1;
+                        starts &= starts - 1;
+                        const uint32_t next = starts ? (uint32_t)(__ffs(starts) - 1) : 16u;
+                        uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;   // run of covered rows
+                        len = len < next - r0 ? len : next - r0;
+                        tc_mma_elect(dbase + r0 * kTile, adesc, bdesc,
+                                     idesc0 | ((len * kTile) >> 3) << 17, 1u);
+                        bdesc += (uint64_t)((len * kTileBytes16) >> 4);
+                    }
+                }
+                if (lane == 0) tc_commit(&sm->empty[stage]);
+                __syncwarp();
+                if (++stage == kStages) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+            }
+            if (!ok) break;
+            if (lane == 0) tc_commit(&sm->accf[ab]);
+            __syncwarp();
+        }
+        if (lane == 0) {
+            if (!ok) {
+                record(args.status, kDevTimeout);
+                sm->abort_flag = 1;
             }
             sm->consumed = consumed;
         }
@@ -322,8 +445,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         int local = 0;
         for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, ++local) {
             const int32_t *it = args.items + (u / args.ntn) * kItemFields;
-            const int ab = local & 1;
-            const uint32_t aphase = (local >> 1) & 1;
+            const int ab = local % kAccBufs;
+            const uint32_t aphase = (local / kAccBufs) & 1;
             int okw = 1;
             if (lane == 0) okw = mbar_wait(&sm->accf[ab], aphase, sm) ? 1 : 0;
             okw = __shfl_sync(0xffffffffu, okw, 0);
@@ -335,23 +458,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc_fence_after();
-            const uint32_t mask = sm->acc_mask[ab];
             const int32_t g = it[0], slot = it[5];
             const int rows = args.grp_rows[g];
             const int64_t yrow0 = (int64_t)args.grp_row0[g] * kTile;
             const int64_t col = (int64_t)(u % args.ntn) * kNTile + nl;
             const bool in = col < args.n;
+            const int64_t wrow0 = slot >= 0 ? args.ws_row0[slot] : 0;
             for (int r = 0; r < rows; ++r) {
                 float v[16];
-                if ((mask >> r) & 1u) {
-                    tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + ab * kAccCols + r * kTile, v);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) v[i] = 0.f;
-                }
+                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + ab * kAccCols + r * kTile;
+                tmem_ld16(ta, v);
+                tmem_zero16(ta);
                 if (!in) continue;
                 if (slot >= 0) {
-                    float *dst = args.ws + (args.ws_row0[slot] + r * kTile) * args.n + col;
+                    float *dst = args.ws + (wrow0 + r * kTile) * args.n + col;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) dst[i * args.n] = v[i];
                 } else {
@@ -360,6 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int i = 0; i < 16; ++i) dst[i * args.ldy] = Cvt<T>::f(v[i]);
                 }
             }
+            tmem_wait_st();
             tc_fence_before();
             mbar_arrive(&sm->acce[ab]);
         }
@@ -380,7 +501,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(2 * kAccCols));
+                     "r"(kAccBufs * kAccCols));
     }
 }
 
@@ -427,17 +548,35 @@ cudaError_t tc_launch(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
                       cudaStream_t s) {
     auto enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
+    // the accumulators of a group must fit the TMEM this kernel allocates
+    if (p->R > kRowCap) return cudaErrorInvalidConfiguration;
     if (((uintptr_t)X & 15) || (ldx * 2) % 16) return cudaErrorMisalignedAddress;
     CUtensorMap map;
-    const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)p->k};
-    const cuuint64_t strides[1] = {(cuuint64_t)(ldx * 2)};
-    const cuuint32_t box[2] = {kNTile / 2, kTile};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&map,
-                     Cvt<T>::fmt ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
-                     2, const_cast<void *>(X), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const auto dt = Cvt<T>::fmt ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    // n a multiple of 64: X seen as (64 columns, k rows, n/64 column blocks) so
+    // one 64 x 16 x 2 box is a whole 16 x 128 slab (two 128-byte-swizzled
+    // halves, 2048 B apart); otherwise two 2-D 64 x 16 boxes per slab, whose
+    // out-of-range columns the TMA unit fills with zeros.
+    const int x3d = (n % (kNTile / 2)) == 0 ? 1 : 0;
+    CUresult r;
+    if (x3d) {
+        const cuuint64_t dims[3] = {(cuuint64_t)(kNTile / 2), (cuuint64_t)p->k,
+                                    (cuuint64_t)(n / (kNTile / 2))};
+        const cuuint64_t strides[2] = {(cuuint64_t)(ldx * 2), (cuuint64_t)kNTile};
+        const cuuint32_t box[3] = {kNTile / 2, kTile, 2};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        r = enc(&map, dt, 3, const_cast<void *>(X), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)p->k};
+        const cuuint64_t strides[1] = {(cuuint64_t)(ldx * 2)};
+        const cuuint32_t box[2] = {kNTile / 2, kTile};
+        const cuuint32_t estr[2] = {1, 1};
+        r = enc(&map, dt, 2, const_cast<void *>(X), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
     TcArgs a;
     a.items = p->d_items;
@@ -447,7 +586,7 @@ cudaError_t tc_launch(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
     a.grp_rows = p->d_grp_rows;
     a.ent_col = p->d_ent_col;
     a.ent_tbeg = p->d_ent_tbeg;
-    a.tile_row = p->d_tile_row;
+    a.ent_cover = p->d_ent_cover;
     a.packed = (const uint8_t *)p->d_packed;
     a.Y = Y;
     a.ldy = ldy;
@@ -456,12 +595,12 @@ cudaError_t tc_launch(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
     a.ws_row0 = p->d_ws_row0;
     a.status = p->d_status;
     a.ntn = (int)((n + kNTile - 1) / kNTile);
-    a.a_lbo = 2048;
-    a.a_sbo = 1024;
+    a.x3d = x3d;
 
     const int64_t units = n_items_cap * a.ntn;
     if (units == 0) return cudaSuccess;
-    const int grid = (int)(units < p->sm_count ? units : p->sm_count);
+    const int64_t slots = (int64_t)p->sm_count * kCtasPerSm;
+    const int grid = (int)(units < slots ? units : slots);
     const size_t smem = 1024 + (size_t)kStages * kStageBytes + sizeof(Smem);
     static bool attr_set[2] = {false, false};
     if (!attr_set[Cvt<T>::fmt]) {

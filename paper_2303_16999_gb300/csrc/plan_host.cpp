@@ -155,8 +155,36 @@ void build_row_plan(int64_t mb, int64_t C1, bool sort_items, HostPlan &hp) {
     finish_items(items, sort_items, one, hp);
 }
 
+// Cost, in units of two SM cycles, of one MMA over L consecutive tile rows
+// (N = 16 L): at least 40 cycles to issue, 8 cycles per 16 rows, plus one
+// unit per tile slot moved through shared memory.
+static int mma_cost(int L) { return std::max(20, 4 * L) + L; }
+
+// Cheapest cover of ascending rows by runs of consecutive rows (exact DP,
+// earliest split point on ties); rows inside a run without a tile are
+// zero tiles.
+static void cover_intervals(const std::vector<int> &rows, std::vector<std::pair<int, int>> &out) {
+    const int n = (int)rows.size();
+    int dp[kMaxGroupRows + 1], arg[kMaxGroupRows + 1];
+    dp[0] = 0;
+    for (int j = 1; j <= n; ++j) {
+        dp[j] = -1;
+        for (int i = 0; i < j; ++i) {
+            const int c = dp[i] + mma_cost(rows[j - 1] - rows[i] + 1);
+            if (dp[j] < 0 || c < dp[j]) {
+                dp[j] = c;
+                arg[j] = i;
+            }
+        }
+    }
+    out.clear();
+    for (int j = n; j > 0; j = arg[j]) out.push_back({rows[arg[j]], rows[j - 1] - rows[arg[j]] + 1});
+    std::reverse(out.begin(), out.end());
+}
+
 void build_tc_plan(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *brow,
-                   const int32_t *bcol, int64_t R, int64_t C, bool sort_items, HostPlan &hp) {
+                   const int32_t *bcol, int64_t R, int64_t C, bool sort_items, bool pad,
+                   HostPlan &hp) {
     const int64_t mt = m / kTile;
     (void)k;
     const std::vector<int64_t> sizes = group_partition(mt, R);
@@ -186,24 +214,51 @@ void build_tc_plan(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *bro
         v.erase(std::unique(v.begin(), v.end()), v.end());
         slot_base[g + 1] = slot_base[g] + (int64_t)v.size();
     }
-    const int64_t ntiles = slot_base[G];
-    hp.tile_row.assign(ntiles, 0);
+    // entries: runs of one tile column within a group's sorted keys; each
+    // entry's rows are covered by MMA intervals and get one slot per row
+    hp.tile_row.clear();
     hp.ent_col.clear();
     hp.ent_tbeg.clear();
+    hp.ent_cover.clear();
     hp.grp_ebeg.assign(G + 1, 0);
+    std::vector<int32_t> key_slot(slot_base[G]);
+    std::vector<int> rows;
+    std::vector<std::pair<int, int>> ivs;
     for (int64_t g = 0; g < G; ++g) {
         const auto &v = keys[g];
-        for (size_t i = 0; i < v.size(); ++i) {
-            const int64_t tc = v[i] / mt, tr = v[i] % mt, s = slot_base[g] + (int64_t)i;
-            hp.tile_row[s] = (int32_t)(tr - hp.grp_row0[g]);
-            if (i == 0 || v[i - 1] / mt != tc) {
-                hp.ent_col.push_back((int32_t)tc);
-                hp.ent_tbeg.push_back((int32_t)s);
+        size_t i = 0;
+        while (i < v.size()) {
+            const int64_t tc = v[i] / mt;
+            size_t j = i;
+            rows.clear();
+            while (j < v.size() && v[j] / mt == tc) {
+                rows.push_back((int)(v[j] % mt - hp.grp_row0[g]));
+                ++j;
             }
+            if (pad) {
+                cover_intervals(rows, ivs);
+            } else {
+                ivs.clear();
+                for (int r : rows) ivs.push_back({r, 1});
+            }
+            hp.ent_col.push_back((int32_t)tc);
+            hp.ent_tbeg.push_back((int32_t)hp.tile_row.size());
+            uint32_t cov = 0, starts = 0;
+            size_t q = i;
+            for (const auto &iv : ivs) {
+                starts |= 1u << iv.first;
+                for (int r = iv.first; r < iv.first + iv.second; ++r) {
+                    cov |= 1u << r;
+                    if (q < j && (int)(v[q] % mt - hp.grp_row0[g]) == r) key_slot[slot_base[g] + q++] = (int32_t)hp.tile_row.size();
+                    hp.tile_row.push_back(r);
+                }
+            }
+            hp.ent_cover.push_back((int32_t)(cov | (starts << 16)));
+            i = j;
         }
         hp.grp_ebeg[g + 1] = (int32_t)hp.ent_col.size();
     }
-    hp.ent_tbeg.push_back((int32_t)ntiles);
+    hp.ent_tbeg.push_back((int32_t)hp.tile_row.size());
     hp.blk_slot.assign(nnzb, 0);
     hp.blk_off.assign(nnzb, 0);
     for (int64_t p = 0; p < nnzb; ++p) {
@@ -211,7 +266,7 @@ void build_tc_plan(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *bro
         const int g = group_of[tr];
         const auto &v = keys[g];
         const int64_t i = std::lower_bound(v.begin(), v.end(), bkey[p]) - v.begin();
-        hp.blk_slot[p] = (int32_t)(slot_base[g] + i);
+        hp.blk_slot[p] = key_slot[slot_base[g] + i];
         hp.blk_off[p] = (int32_t)(((int64_t)brow[p] * b % kTile) * kTile + (int64_t)bcol[p] * b % kTile);
     }
     // items: near-equal chunks of each group's entries
@@ -228,9 +283,9 @@ void build_tc_plan(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *bro
             e += cs[c];
         }
     }
-    std::vector<int64_t> rows(G);
-    for (int64_t g = 0; g < G; ++g) rows[g] = (int64_t)hp.grp_rows[g] * kTile;
-    finish_items(items, sort_items, rows, hp);
+    std::vector<int64_t> grows(G);
+    for (int64_t g = 0; g < G; ++g) grows[g] = (int64_t)hp.grp_rows[g] * kTile;
+    finish_items(items, sort_items, grows, hp);
 }
 
 }  // namespace spmm

@@ -37,8 +37,8 @@ struct HostPlan {
     int64_t ws_rows = 0;
     std::vector<int32_t> red;  // 3 per split group/row
     // tensor-core tile structure
-    std::vector<int32_t> grp_row0, grp_rows, grp_ebeg, ent_col, ent_tbeg, tile_row, blk_slot,
-        blk_off;
+    std::vector<int32_t> grp_row0, grp_rows, grp_ebeg, ent_col, ent_tbeg, ent_cover, tile_row,
+        blk_slot, blk_off;
 };
 
 // Validates shape and pattern; returns SPMM_OK, SPMM_ERR_SHAPE or SPMM_ERR_PATTERN.
@@ -48,7 +48,8 @@ void build_csr(int64_t mb, int64_t nnzb, const int32_t *brow, const int32_t *bco
 std::vector<int64_t> group_partition(int64_t mt, int64_t R);
 void build_row_plan(int64_t mb, int64_t C1, bool sort_items, HostPlan &hp);
 void build_tc_plan(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *brow,
-                   const int32_t *bcol, int64_t R, int64_t C, bool sort_items, HostPlan &hp);
+                   const int32_t *bcol, int64_t R, int64_t C, bool sort_items, bool pad,
+                   HostPlan &hp);
 
 // ------------------------------------------------------------------- plan
 struct DevArr {
@@ -71,7 +72,7 @@ struct spmm_plan {
     // device copies (static) / device-built arrays (dynamic)
     int32_t *d_row_ptr = nullptr, *d_col_idx = nullptr, *d_perm = nullptr, *d_items = nullptr,
             *d_red = nullptr, *d_grp_row0 = nullptr, *d_grp_rows = nullptr, *d_ent_col = nullptr,
-            *d_ent_tbeg = nullptr, *d_tile_row = nullptr, *d_blk_slot = nullptr,
+            *d_ent_tbeg = nullptr, *d_ent_cover = nullptr, *d_tile_row = nullptr, *d_blk_slot = nullptr,
             *d_blk_off = nullptr, *d_grp_ebeg = nullptr;
     int64_t *d_ws_row0 = nullptr;
     int64_t n_items = 0, n_groups = 0, n_entries = 0, n_tiles = 0, n_red = 0;

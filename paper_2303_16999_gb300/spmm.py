@@ -29,7 +29,7 @@ KERNEL_AUTO, KERNEL_PLAIN, KERNEL_GATHER, KERNEL_TC = 0, 1, 2, 3
 KERNELS = {"auto": 0, "plain": 1, "gather": 2, "tc": 3}
 ARRAYS = {"row_ptr": 0, "col_idx": 1, "perm": 2, "items": 3, "grp_row0": 4, "grp_rows": 5,
           "grp_ebeg": 6, "ent_col": 7, "ent_tbeg": 8, "tile_row": 9, "blk_slot": 10,
-          "blk_off": 11, "ws_row0": 12, "red": 13}
+          "blk_off": 11, "ws_row0": 12, "red": 13, "ent_cover": 14}
 
 # exported symbols of include/spmm.h (checked by the CPU test-suite)
 EXPORTS = ["spmm_plan_create", "spmm_pack_values", "spmm_run", "spmm_run_host",

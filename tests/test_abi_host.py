@@ -105,8 +105,8 @@ def test_row_plan_bit_exact():
         assert info["ws_rows"] == want["ws_rows"]
 
 
-TC_KEYS = ["grp_row0", "grp_rows", "grp_ebeg", "ent_col", "ent_tbeg", "tile_row", "blk_slot",
-           "blk_off", "ws_row0"]
+TC_KEYS = ["grp_row0", "grp_rows", "grp_ebeg", "ent_col", "ent_tbeg", "ent_cover", "tile_row",
+           "blk_slot", "blk_off", "ws_row0"]
 
 
 @pytest.mark.parametrize("b", [4, 8, 16])

@@ -165,22 +165,40 @@ def _brute_tc(m, k, b, brow, bcol, R):
     return tmask, sizes, ents
 
 
-def _check_tc_plan(m, k, b, brow, bcol, R, C, pl, sort_items):
+def _check_tc_plan(m, k, b, brow, bcol, R, C, pl, sort_items, pad=None):
+    pad = sort_items if pad is None else pad
     tmask, sizes, ents = _brute_tc(m, k, b, brow, bcol, R)
     assert list(pl["grp_rows"]) == sizes
     assert list(pl["grp_row0"]) == list(np.cumsum([0] + sizes)[:-1])
     flat = [c for e in ents for c in e]
     assert list(pl["ent_col"]) == flat
     assert list(np.diff(pl["grp_ebeg"])) == [len(e) for e in ents]
-    ntiles = int(tmask.sum())
-    assert pl["ent_tbeg"][-1] == ntiles and len(pl["tile_row"]) == ntiles
-    # each entry's tiles: exactly the group's tile rows having that column, ascending
+    assert pl["ent_tbeg"][-1] == len(pl["tile_row"])
+    # each entry's slots: its real tile rows, plus (padded plans only) the
+    # rows inside each covering interval, ascending, one slot per row
     for g in range(len(sizes)):
         for e in range(pl["grp_ebeg"][g], pl["grp_ebeg"][g + 1]):
-            rows = pl["tile_row"][pl["ent_tbeg"][e]:pl["ent_tbeg"][e + 1]]
+            rows = list(pl["tile_row"][pl["ent_tbeg"][e]:pl["ent_tbeg"][e + 1]])
             col = pl["ent_col"][e]
-            want = np.nonzero(tmask[pl["grp_row0"][g]:pl["grp_row0"][g] + sizes[g], col])[0]
-            assert list(rows) == list(want)
+            real = list(np.nonzero(tmask[pl["grp_row0"][g]:pl["grp_row0"][g] + sizes[g], col])[0])
+            cov = pl["ent_cover"][e] & 0xFFFF
+            starts = (pl["ent_cover"][e] >> 16) & 0xFFFF
+            assert rows == sorted(rows) and len(set(rows)) == len(rows)
+            assert set(real) <= set(rows) and cov == sum(1 << int(r) for r in rows)
+            if not pad:
+                assert rows == real and starts == cov
+            # intervals: maximal runs split at start bits; each starts and ends on a real row
+            ivs = []
+            for r in rows:
+                if (starts >> r) & 1:
+                    ivs.append([r, r])
+                else:
+                    assert ivs and ivs[-1][1] == r - 1
+                    ivs[-1][1] = r
+            for a, z in ivs:
+                assert a in real and z in real
+            assert sum(P.mma_cost(z - a + 1) for a, z in ivs) == \
+                _best_cover_cost(real) if pad else True
     # items cover every entry exactly once, every group has an item
     cover = np.zeros(len(flat), int)
     for g, beg, end, ch, nch, ws in pl["items"]:
@@ -190,7 +208,7 @@ def _check_tc_plan(m, k, b, brow, bcol, R, C, pl, sort_items):
         assert (ws >= 0) == (nch > 1)
     assert np.all(cover == 1)
     assert set(pl["items"][:, 0]) == set(range(len(sizes)))
-    # every block lands in its tile at its offset
+    # every block lands in the slot of its entry and row, at its offset
     for p in range(len(brow)):
         s = pl["blk_slot"][p]
         tr = brow[p] * b // 16
@@ -207,6 +225,33 @@ def _check_tc_plan(m, k, b, brow, bcol, R, C, pl, sort_items):
     assert keys == sorted(keys)
 
 
+def _best_cover_cost(rows):
+    """Brute force over every split of the sorted rows into consecutive runs."""
+    n = len(rows)
+    best = None
+    for cuts in range(1 << max(n - 1, 0)):
+        c, a = 0, 0
+        for i in range(1, n + 1):
+            if i == n or (cuts >> (i - 1)) & 1:
+                c += P.mma_cost(rows[i - 1] - rows[a] + 1)
+                a = i
+        best = c if best is None else min(best, c)
+    return best
+
+
+def test_cover_intervals_brute_force():
+    rng = np.random.default_rng(8)
+    assert P.cover_intervals([3]) == [(3, 1)]
+    assert P.cover_intervals([0, 15]) == [(0, 1), (15, 1)]       # 42 < mma_cost(16) = 80
+    assert P.cover_intervals([0, 1, 2, 3]) == [(0, 4)]           # 24 < 4 * 21
+    for _ in range(400):
+        rows = sorted(rng.choice(16, size=rng.integers(1, 17), replace=False).tolist())
+        ivs = P.cover_intervals(rows)
+        assert sum(P.mma_cost(L) for _, L in ivs) == _best_cover_cost(rows)
+        covered = [r for a, L in ivs for r in range(a, a + L)]
+        assert set(rows) <= set(covered) and covered == sorted(covered)
+
+
 @pytest.mark.parametrize("b", [4, 8, 16])
 @pytest.mark.parametrize("sort_items", [True, False])
 def test_tc_plan_invariants(b, sort_items):
@@ -217,6 +262,8 @@ def test_tc_plan_invariants(b, sort_items):
         brow, bcol = _rand_pattern(rng, mb, kb, int(d * mb * kb))
         pl = P.tc_plan(m, k, b, brow, bcol, R, C, sort_items)
         _check_tc_plan(m, k, b, brow, bcol, R, C, pl, sort_items)
+        pl = P.tc_plan(m, k, b, brow, bcol, R, C, sort_items, pad=not sort_items)
+        _check_tc_plan(m, k, b, brow, bcol, R, C, pl, sort_items, pad=not sort_items)
 
 
 def test_tc_plan_extremes():
