@@ -144,6 +144,112 @@ static spmm_status upload_plan(spmm_plan *p) {
     return SPMM_OK;
 }
 
+// Device buffers of a dynamic plan, sized for nnzb_max blocks.  Work items
+// and workspace are bounded independently of the pattern: the chunk size
+// C >= 1.25 E / G keeps the split chunks below 1.6 G (TC); for b = 1,
+// C1 >= 2 nnzb / mb keeps them below mb.
+static spmm_status alloc_dynamic(spmm_plan *p) {
+    DynBufs &d = p->dyn;
+    const int64_t mb = p->m / p->b, cap = p->nnzb_max, G = p->n_groups;
+    const bool tc = p->kernel == SPMM_KERNEL_TC;
+    cudaError_t e = cudaSuccess;
+#define AL(ptr, n) \
+    if (e == cudaSuccess) e = dalloc(p, &(ptr), (int64_t)(n))
+    AL(d.row_cnt, mb);
+    AL(d.cursor, mb);
+    AL(d.tmp_col, cap);
+    AL(d.tmp_perm, cap);
+    AL(p->d_row_ptr, mb + 1);
+    AL(p->d_col_idx, cap);
+    AL(p->d_perm, cap);
+    AL(p->d_counts, kCntCount);
+    if (tc) {
+        d.items_cap = 2 * G + 2;
+        d.ws_slots_cap = 2 * G + 2;
+        d.red_cap = G;
+        p->hp.ws_rows = d.ws_slots_cap * p->R * kTile;
+        e = upload(p, &p->d_grp_row0, p->hp.grp_row0);
+        if (e == cudaSuccess) e = upload(p, &p->d_grp_rows, p->hp.grp_rows);
+        AL(d.grp_cnt, 2 * G);
+        AL(d.grp_sbeg, G);
+        AL(d.grp_ibeg, G);
+        AL(d.grp_wbeg, G);
+        AL(d.grp_rbeg, G);
+        AL(d.grp_wrow, G);
+        AL(p->d_grp_ebeg, G + 1);
+        AL(p->d_ent_col, cap);
+        AL(p->d_ent_tbeg, cap + 1);
+        AL(p->d_ent_cover, cap);
+        AL(p->d_tile_row, cap);
+        AL(p->d_blk_slot, cap);
+        AL(p->d_blk_off, cap);
+    } else {
+        d.items_cap = 2 * mb + 2;
+        d.ws_slots_cap = mb + 1;
+        d.red_cap = mb;
+        p->hp.ws_rows = d.ws_slots_cap;
+        AL(d.row_ibeg, mb);
+        AL(d.row_wbeg, mb);
+        AL(d.row_rbeg, mb);
+    }
+    AL(p->d_items, d.items_cap * kItemFields);
+    AL(p->d_ws_row0, d.ws_slots_cap);
+    AL(p->d_red, d.red_cap * 3);
+#undef AL
+    if (e != cudaSuccess) return cuda_fail(e, "dynamic plan allocation");
+    p->n_items = d.items_cap;
+    p->n_red = d.red_cap;
+    return SPMM_OK;
+}
+
+template <typename T>
+static cudaError_t download(std::vector<T> &dst, const T *src, int64_t n) {
+    dst.resize(n < 0 ? 0 : n);
+    if (n <= 0) return cudaSuccess;
+    return cudaMemcpy(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost);
+}
+
+// Dynamic plans: copies the arrays the last call built on the device into
+// the host mirror, with their true lengths.
+static spmm_status refresh_dynamic(spmm_plan *p) {
+    if (p->mode != SPMM_DYNAMIC || p->host_only) return SPMM_OK;
+    if (p->ran) {
+        cudaError_t e = cudaEventSynchronize(p->done);
+        if (e != cudaSuccess) return cuda_fail(e, "event synchronize");
+    }
+    int32_t c[kCntCount] = {0};
+    cudaError_t e = cudaMemcpy(c, p->d_counts, sizeof(c), cudaMemcpyDeviceToHost);
+    HostPlan &hp = p->hp;
+    const int64_t mb = p->m / p->b, nnzb = c[kCntNnzb];
+    p->nnzb = nnzb;
+    p->C = c[kCntChunk];
+    if (e == cudaSuccess) e = download(hp.row_ptr, p->d_row_ptr, mb + 1);
+    if (e == cudaSuccess) e = download(hp.col_idx, p->d_col_idx, nnzb);
+    if (e == cudaSuccess) e = download(hp.perm, p->d_perm, nnzb);
+    if (e == cudaSuccess) e = download(hp.items, p->d_items, (int64_t)c[kCntItems] * kItemFields);
+    if (e == cudaSuccess) e = download(hp.red, p->d_red, (int64_t)c[kCntRed] * 3);
+    if (p->kernel == SPMM_KERNEL_TC) {
+        const int64_t E = c[kCntEntries], S = c[kCntSlots];
+        if (e == cudaSuccess) e = download(hp.ws_row0, p->d_ws_row0, (int64_t)c[kCntWsSlots]);
+        if (e == cudaSuccess) e = download(hp.grp_ebeg, p->d_grp_ebeg, p->n_groups + 1);
+        if (e == cudaSuccess) e = download(hp.ent_col, p->d_ent_col, E);
+        if (e == cudaSuccess) e = download(hp.ent_tbeg, p->d_ent_tbeg, E + 1);
+        if (e == cudaSuccess) e = download(hp.ent_cover, p->d_ent_cover, E);
+        if (e == cudaSuccess) e = download(hp.tile_row, p->d_tile_row, S);
+        if (e == cudaSuccess) e = download(hp.blk_slot, p->d_blk_slot, nnzb);
+        if (e == cudaSuccess) e = download(hp.blk_off, p->d_blk_off, nnzb);
+        p->n_entries = E;
+        p->n_tiles = S;
+    } else {
+        if (e == cudaSuccess) e = download(hp.ws_row0, p->d_ws_row0, (int64_t)c[kCntWsRows]);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "dynamic plan download");
+    p->dyn_ws_rows = c[kCntWsRows];
+    p->dyn_items = c[kCntItems];
+    p->dyn_red = c[kCntRed];
+    return SPMM_OK;
+}
+
 }  // namespace spmm
 
 using namespace spmm;
@@ -267,9 +373,26 @@ spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spm
             p->n_tiles = (int64_t)p->hp.tile_row.size();
         } else {
             p->nnzb_max = nnzb_max;
-            set_error("dynamic mode is not built yet");
-            free_plan(p);
-            return SPMM_ERR_UNSUPPORTED;
+            if (kernel == SPMM_KERNEL_TC) {
+                if (k / kTile > kDynMaxTileCols) {
+                    set_error("dynamic TC plans need k <= %d", kDynMaxTileCols * kTile);
+                    free_plan(p);
+                    return SPMM_ERR_UNSUPPORTED;
+                }
+                p->R = o.rows_per_group ? o.rows_per_group : default_R(mt, n_max, p->sm_count);
+                const std::vector<int64_t> sz = group_partition(mt, p->R);
+                int64_t acc = 0;
+                for (int64_t v : sz) {
+                    p->hp.grp_row0.push_back((int32_t)acc);
+                    p->hp.grp_rows.push_back((int32_t)v);
+                    acc += v;
+                }
+                p->n_groups = (int64_t)sz.size();
+            } else if (kernel == SPMM_KERNEL_PLAIN) {
+                set_error("dynamic plans use the GATHER (b = 1) or TC (b >= 4) kernels");
+                free_plan(p);
+                return SPMM_ERR_UNSUPPORTED;
+            }
         }
     } catch (const std::bad_alloc &) {
         free_plan(p);
@@ -277,7 +400,7 @@ spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spm
         return SPMM_ERR_OOM;
     }
     if (!p->host_only) {
-        st = upload_plan(p);
+        st = p->mode == SPMM_STATIC ? upload_plan(p) : alloc_dynamic(p);
         cudaError_t e = cudaSuccess;
         if (st == SPMM_OK) e = dalloc(p, &p->d_status, 1);
         if (st == SPMM_OK && e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int32_t));
@@ -285,13 +408,15 @@ spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spm
             e = dalloc(p, &p->d_ws, p->hp.ws_rows * std::max<int64_t>(n_max, 1));
         if (st == SPMM_OK && e == cudaSuccess) {
             // packed values: CSR order for PLAIN / GATHER, 16 x 16 tiles for TC
+            const int64_t nb = p->mode == SPMM_STATIC ? p->nnzb : p->nnzb_max;
+            const int64_t nt = p->mode == SPMM_STATIC ? p->n_tiles : p->nnzb_max;
             if (kernel == SPMM_KERNEL_TC)
-                p->packed_bytes = p->n_tiles * kTile * kTile * (int64_t)dtype_size(w_dtype);
+                p->packed_bytes = nt * kTile * kTile * (int64_t)dtype_size(w_dtype);
             else
-                p->packed_bytes = p->nnzb * b * b * (int64_t)dtype_size(w_dtype);
+                p->packed_bytes = nb * b * b * (int64_t)dtype_size(w_dtype);
             e = dalloc(p, (char **)&p->d_packed, p->packed_bytes);
             if (e == cudaSuccess && w_dtype == SPMM_E4M3)
-                e = dalloc(p, &p->d_tile_scale, p->n_tiles * 16);
+                e = dalloc(p, &p->d_tile_scale, nt * 16);
         }
         if (st == SPMM_OK && e != cudaSuccess) st = cuda_fail(e, "plan allocation");
         if (st != SPMM_OK) {
@@ -342,7 +467,7 @@ static spmm_status do_pack(spmm_plan *p, const void *d_values, const float *d_sc
     }
     cudaError_t e = (p->kernel == SPMM_KERNEL_TC)
                         ? launch_pack_tiles(p, d_values, d_scales, nullptr, s)
-                        : launch_pack_csr(p, d_values, s);
+                        : launch_pack_csr(p, d_values, nullptr, s);
     if (e != cudaSuccess) return cuda_fail(e, "pack");
     p->packed = true;
     return SPMM_OK;
@@ -413,9 +538,25 @@ spmm_status spmm_run(spmm_plan *plan, const void *d_values, const float *d_scale
     st = busy_check(plan, s);
     if (st != SPMM_OK) return st;
     if (plan->mode == SPMM_DYNAMIC) {
-        (void)dpat;
-        set_error("dynamic mode is not built yet");
-        return SPMM_ERR_UNSUPPORTED;
+        if (!dpat || !dpat->d_nnzb || !dpat->d_brow || !dpat->d_bcol || !d_values) {
+            set_error("dynamic runs need a device pattern and values");
+            return SPMM_ERR_ARG;
+        }
+        if (plan->wdt == SPMM_E4M3 && !d_scales) {
+            set_error("E4M3 values need per-block scales");
+            return SPMM_ERR_ARG;
+        }
+        cudaError_t e = launch_dynamic_partition(plan, dpat, s);
+        if (e == cudaSuccess)
+            e = plan->kernel == SPMM_KERNEL_TC
+                    ? launch_pack_tiles(plan, d_values, d_scales, dpat->d_nnzb, s)
+                    : launch_pack_csr(plan, d_values, dpat->d_nnzb, s);
+        if (e != cudaSuccess) return cuda_fail(e, "dynamic re-partition");
+        if (n > 0) {
+            st = launch_product(plan, d_X, n, ldx, d_Y, ldy, s);
+            if (st != SPMM_OK) return st;
+        }
+        return finish_call(plan, s);
     }
     if (d_values) {
         st = do_pack(plan, d_values, d_scales, s);
@@ -504,10 +645,15 @@ spmm_status spmm_get_status(spmm_plan *plan, int32_t *device_status) {
     return SPMM_OK;
 }
 
-spmm_status spmm_plan_get_info(const spmm_plan *p, spmm_plan_info *info) {
-    if (!p || !info) {
+spmm_status spmm_plan_get_info(const spmm_plan *cp, spmm_plan_info *info) {
+    if (!cp || !info) {
         set_error("plan and info required");
         return SPMM_ERR_ARG;
+    }
+    spmm_plan *p = const_cast<spmm_plan *>(cp);
+    if (p->mode == SPMM_DYNAMIC && p->ran) {
+        spmm_status rs = refresh_dynamic(p);
+        if (rs != SPMM_OK) return rs;
     }
     spmm_plan_info i{};
     i.m = p->m;
@@ -522,12 +668,13 @@ spmm_status spmm_plan_get_info(const spmm_plan *p, spmm_plan_info *info) {
     i.kernel = p->kernel;
     i.rows_per_group = p->R;
     i.max_per_item = p->C;
-    i.n_items = p->n_items;
+    const bool dynran = p->mode == SPMM_DYNAMIC && p->ran;
+    i.n_items = dynran ? p->dyn_items : p->n_items;
     i.n_groups = p->n_groups;
     i.n_entries = p->n_entries;
     i.n_tiles = p->n_tiles;
-    i.ws_rows = p->hp.ws_rows;
-    i.n_reductions = p->n_red;
+    i.ws_rows = dynran ? p->dyn_ws_rows : p->hp.ws_rows;
+    i.n_reductions = dynran ? p->dyn_red : p->n_red;
     i.device_bytes = p->device_bytes;
     *info = i;
     return SPMM_OK;
@@ -540,6 +687,8 @@ spmm_status spmm_plan_get_array(spmm_plan *p, spmm_array which, void *dst, int64
         set_error("plan and count required");
         return SPMM_ERR_ARG;
     }
+    spmm_status rs = refresh_dynamic(p);
+    if (rs != SPMM_OK) return rs;
     const HostPlan &hp = p->hp;
     const void *src = nullptr;
     int64_t n = 0;

@@ -17,7 +17,9 @@ namespace {
 // host-supplied values are re-ordered to match the fixed distribution).
 template <typename U>
 __global__ void pack_csr_kernel(const U *__restrict__ vals, const int32_t *__restrict__ perm,
-                                int64_t nnzb, int bb, U *__restrict__ out) {
+                                int64_t nnzb, int bb, const int32_t *__restrict__ nnzb_dev,
+                                U *__restrict__ out) {
+    if (nnzb_dev) nnzb = min((int64_t)max(*nnzb_dev, 0), nnzb);
     const int64_t total = nnzb * bb;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -79,9 +81,15 @@ __global__ void __launch_bounds__(256) gather_kernel(
     const int32_t *__restrict__ items, int64_t n_items, int nchunk, int LN,
     const int32_t *__restrict__ col_idx, const T *__restrict__ vals, const T *__restrict__ X,
     int64_t ldx, T *__restrict__ Y, int64_t ldy, int64_t n, float *__restrict__ ws,
-    const int64_t *__restrict__ ws_row0) {
+    const int64_t *__restrict__ ws_row0, const int32_t *__restrict__ n_items_dev,
+    const int32_t *__restrict__ status) {
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    if (n_items_dev) {
+        // dynamic plans: item count from the device; a rejected pattern writes nothing
+        if (*status != 0) return;
+        n_items = min(n_items, (int64_t)*n_items_dev);
+    }
     if (wid >= n_items * nchunk) return;
     const int64_t item = wid / nchunk;
     const int chunk = (int)(wid - item * nchunk);
@@ -154,7 +162,13 @@ template <typename T>
 __global__ void reduce_kernel(const int32_t *__restrict__ red, const int32_t *__restrict__ grp_row0,
                               const int32_t *__restrict__ grp_rows, int rows_per_unit,
                               const float *__restrict__ ws, const int64_t *__restrict__ ws_row0,
-                              T *__restrict__ Y, int64_t ldy, int64_t n, int64_t n_red) {
+                              T *__restrict__ Y, int64_t ldy, int64_t n, int64_t n_red,
+                              const int32_t *__restrict__ n_red_dev,
+                              const int32_t *__restrict__ status) {
+  if (n_red_dev) {
+      if (*status != 0) return;
+      n_red = min(n_red, (int64_t)*n_red_dev);
+  }
   for (int64_t q = blockIdx.z; q < n_red; q += gridDim.z) {
     const int32_t *rd = red + q * 3;
     const int32_t g = rd[0], slot0 = rd[1], nch = rd[2];
@@ -181,15 +195,18 @@ inline unsigned grid1d(int64_t total, int threads) {
 template <typename T, int V>
 cudaError_t gather_launch(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
                           int64_t ldy, cudaStream_t s) {
+    const bool dyn = p->mode == SPMM_DYNAMIC;
+    const int64_t n_items = dyn ? p->dyn.items_cap : p->n_items;
     const int64_t vecs = (n + V - 1) / V;
     int LN = 1;
     while (LN < 32 && LN < vecs) LN <<= 1;
     const int nchunk = (int)((n + (int64_t)LN * V - 1) / ((int64_t)LN * V));
-    const int64_t warps = p->n_items * nchunk;
+    const int64_t warps = n_items * nchunk;
     if (warps == 0) return cudaSuccess;
     gather_kernel<T, V><<<grid1d(warps * 32, 256), 256, 0, s>>>(
-        p->d_items, p->n_items, nchunk, LN, p->d_col_idx, (const T *)p->d_packed, (const T *)X,
-        ldx, (T *)Y, ldy, n, p->d_ws, p->d_ws_row0);
+        p->d_items, n_items, nchunk, LN, p->d_col_idx, (const T *)p->d_packed, (const T *)X,
+        ldx, (T *)Y, ldy, n, p->d_ws, p->d_ws_row0, dyn ? p->d_counts + kCntItems : nullptr,
+        p->d_status);
     return cudaGetLastError();
 }
 
@@ -211,19 +228,21 @@ cudaError_t gather_dispatch(const spmm_plan *p, const void *X, int64_t n, int64_
 
 }  // namespace
 
-cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, cudaStream_t s) {
+cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, const int32_t *d_nnzb,
+                            cudaStream_t s) {
     const int bb = p->b * p->b;
-    const int64_t total = p->nnzb * bb;
+    const int64_t nmax = d_nnzb ? p->nnzb_max : p->nnzb;
+    const int64_t total = nmax * bb;
     if (total == 0) return cudaSuccess;
     const unsigned g = grid1d(total, 256) > 4096u ? 4096u : grid1d(total, 256);
     switch (dtype_size(p->wdt)) {
         case 4:
             pack_csr_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t *)d_values, p->d_perm,
-                                                        p->nnzb, bb, (uint32_t *)p->d_packed);
+                                                        nmax, bb, d_nnzb, (uint32_t *)p->d_packed);
             break;
         case 2:
             pack_csr_kernel<uint16_t><<<g, 256, 0, s>>>((const uint16_t *)d_values, p->d_perm,
-                                                        p->nnzb, bb, (uint16_t *)p->d_packed);
+                                                        nmax, bb, d_nnzb, (uint16_t *)p->d_packed);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -249,27 +268,30 @@ cudaError_t launch_gather(const spmm_plan *p, const void *X, int64_t n, int64_t 
 }
 
 cudaError_t launch_reduce(const spmm_plan *p, int64_t n, void *Y, int64_t ldy, cudaStream_t s) {
-    if (p->n_red == 0 || n == 0) return cudaSuccess;
+    const bool dyn = p->mode == SPMM_DYNAMIC;
+    const int64_t n_red = dyn ? p->dyn.red_cap : p->n_red;
+    const int32_t *n_red_dev = dyn ? p->d_counts + kCntRed : nullptr;
+    if (n_red == 0 || n == 0) return cudaSuccess;
     const bool tc = p->kernel == SPMM_KERNEL_TC;
     const int rows_per_unit = tc ? kTile : 1;
     const unsigned gy = tc ? (unsigned)(kMaxGroupRows * kTile) : 1u;
     dim3 grid(grid1d(n, 128) > 64u ? 64u : grid1d(n, 128), gy,
-              (unsigned)(p->n_red < 65535 ? p->n_red : 65535));
+              (unsigned)(n_red < 65535 ? n_red : 65535));
     const int32_t *r0 = tc ? p->d_grp_row0 : nullptr;
     const int32_t *rn = tc ? p->d_grp_rows : nullptr;
     switch (p->xdt) {
         case SPMM_F32:
             reduce_kernel<float><<<grid, 128, 0, s>>>(p->d_red, r0, rn, rows_per_unit, p->d_ws,
-                                                      p->d_ws_row0, (float *)Y, ldy, n, p->n_red);
+                                                      p->d_ws_row0, (float *)Y, ldy, n, n_red, n_red_dev, p->d_status);
             break;
         case SPMM_F16:
             reduce_kernel<__half><<<grid, 128, 0, s>>>(p->d_red, r0, rn, rows_per_unit, p->d_ws,
-                                                       p->d_ws_row0, (__half *)Y, ldy, n, p->n_red);
+                                                       p->d_ws_row0, (__half *)Y, ldy, n, n_red, n_red_dev, p->d_status);
             break;
         case SPMM_BF16:
             reduce_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>(p->d_red, r0, rn, rows_per_unit,
                                                               p->d_ws, p->d_ws_row0,
-                                                              (__nv_bfloat16 *)Y, ldy, n, p->n_red);
+                                                              (__nv_bfloat16 *)Y, ldy, n, n_red, n_red_dev, p->d_status);
             break;
         default: return cudaErrorInvalidValue;
     }

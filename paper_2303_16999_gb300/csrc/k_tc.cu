@@ -261,7 +261,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     if (threadIdx.x == 0) {
         // dynamic plans: a pattern rejected on the device leaves Y unwritten
         const bool skip = args.n_items_dev && *(volatile int32_t *)args.status != 0;
-        sm->nitems = skip ? 0 : (args.n_items_dev ? (int64_t)*args.n_items_dev : args.n_items);
+        int64_t ni = args.n_items;
+        if (args.n_items_dev) ni = min(ni, (int64_t)max(*args.n_items_dev, 0));
+        sm->nitems = skip ? 0 : ni;
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&sm->full[s], 1);
             mbar_init(&sm->empty[s], 1);
@@ -513,7 +515,7 @@ template <typename U>
 __global__ void pack_tiles_kernel(const U *__restrict__ vals, const int32_t *__restrict__ blk_slot,
                                   const int32_t *__restrict__ blk_off, int64_t nnzb, int b,
                                   const int32_t *__restrict__ nnzb_dev, U *__restrict__ out) {
-    if (nnzb_dev) nnzb = *nnzb_dev;
+    if (nnzb_dev) nnzb = min((int64_t)max(*nnzb_dev, 0), nnzb);
     const int bb = b * b;
     const int64_t total = nnzb * bb;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -617,9 +619,11 @@ cudaError_t tc_launch(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
 
 cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
                       int64_t ldy, cudaStream_t s) {
-    if (p->xdt == SPMM_F16) return tc_launch<__half>(p, X, n, ldx, Y, ldy, nullptr, p->n_items, s);
-    if (p->xdt == SPMM_BF16)
-        return tc_launch<__nv_bfloat16>(p, X, n, ldx, Y, ldy, nullptr, p->n_items, s);
+    const bool dyn = p->mode == SPMM_DYNAMIC;
+    const int32_t *nd = dyn ? p->d_counts + kCntItems : nullptr;
+    const int64_t cap = dyn ? p->dyn.items_cap : p->n_items;
+    if (p->xdt == SPMM_F16) return tc_launch<__half>(p, X, n, ldx, Y, ldy, nd, cap, s);
+    if (p->xdt == SPMM_BF16) return tc_launch<__nv_bfloat16>(p, X, n, ldx, Y, ldy, nd, cap, s);
     return cudaErrorInvalidValue;
 }
 
@@ -636,7 +640,7 @@ cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const fl
     int64_t g = (total + 255) / 256;
     if (g > 8192) g = 8192;
     pack_tiles_kernel<uint16_t><<<(unsigned)g, 256, 0, s>>>(
-        (const uint16_t *)d_values, p->d_blk_slot, p->d_blk_off, p->nnzb, p->b, d_nnzb,
+        (const uint16_t *)d_values, p->d_blk_slot, p->d_blk_off, nmax, p->b, d_nnzb,
         (uint16_t *)p->d_packed);
     return cudaGetLastError();
 }

@@ -16,6 +16,20 @@ constexpr int kTileBytes16 = 512;  // 16 x 16 16-bit tile in the MMA operand lay
 constexpr int kNTile = 128;        // n columns per tensor-core work unit (MMA M)
 constexpr int kMaxGroupRows = 16;  // tile rows per group: 2 x 16 x 16 TMEM columns = 512
 constexpr int kItemFields = 6;     // group/row, begin, end, chunk, n_chunks, ws_slot
+constexpr int kDynMaxTileCols = 4096;  // dynamic TC plans: k <= 65536 (per-group smem bitmaps)
+
+// dynamic plans: device-side counters written by the re-partition
+enum CountIdx : int {
+    kCntNnzb = 0,     // blocks of this call (clamped to capacity)
+    kCntItems = 1,    // work items
+    kCntEntries = 2,  // TC entries
+    kCntSlots = 3,    // TC tile slots
+    kCntWsSlots = 4,  // workspace slots (split items)
+    kCntWsRows = 5,   // workspace rows
+    kCntRed = 6,      // split groups / rows to reduce
+    kCntChunk = 7,    // chunk size C chosen on the device
+    kCntCount = 8
+};
 
 // device status word codes (mirrors spmm_status where applicable)
 enum DeviceStatus : int32_t {
@@ -52,9 +66,14 @@ void build_tc_plan(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *bro
                    HostPlan &hp);
 
 // ------------------------------------------------------------------- plan
-struct DevArr {
-    void *p = nullptr;
-    int64_t bytes = 0;
+// dynamic plans: scratch of the device re-partition
+struct DynBufs {
+    int32_t *row_cnt = nullptr, *cursor = nullptr, *tmp_col = nullptr, *tmp_perm = nullptr;
+    int32_t *row_ibeg = nullptr, *row_wbeg = nullptr, *row_rbeg = nullptr;
+    int32_t *grp_cnt = nullptr, *grp_sbeg = nullptr, *grp_ibeg = nullptr, *grp_wbeg = nullptr,
+            *grp_rbeg = nullptr;
+    int64_t *grp_wrow = nullptr;
+    int64_t items_cap = 0, ws_slots_cap = 0, red_cap = 0;
 };
 
 }  // namespace spmm
@@ -85,6 +104,8 @@ struct spmm_plan {
     int32_t *d_counts = nullptr;   // dynamic: device counters (n_items, n_entries, ...)
     void *d_scratch = nullptr;     // dynamic: re-partition scratch
     int64_t scratch_bytes = 0;
+    spmm::DynBufs dyn;
+    int64_t dyn_ws_rows = 0, dyn_items = 0, dyn_red = 0;  // counts of the last dynamic call
     void *d_xbuf = nullptr, *d_ybuf = nullptr;  // spmm_run_host staging
     int64_t xbuf_bytes = 0, ybuf_bytes = 0;
     int64_t device_bytes = 0;
@@ -98,7 +119,8 @@ struct spmm_plan {
 namespace spmm {
 
 // kernel launchers (return cudaSuccess or the launch error)
-cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, cudaStream_t s);
+cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, const int32_t *d_nnzb,
+                            cudaStream_t s);
 cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const float *d_scales,
                               const int32_t *d_nnzb, cudaStream_t s);
 cudaError_t launch_plain(const spmm_plan *p, const void *d_X, int64_t n, int64_t ldx, void *d_Y,

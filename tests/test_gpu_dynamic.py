@@ -1,0 +1,173 @@
+"""GPU tests of dynamic mode: the partition is rebuilt on the device every call
+(Section 3.3 / Appendix A.2).  Y is compared with the FP64 oracle; every
+integer array the device builds is compared bit for bit with the oracle's
+dynamic-plan rules (CSR, items in (group, chunk) order, unpadded slots).
+Invalid patterns must set the status word and leave Y untouched."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import plan as P
+from paper_2303_16999_gb300 import spmm as S
+from paper_2303_16999_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2303_16999_gb300 import build
+    build.build()
+
+
+def _dev_pattern(brow, bcol, cap, nnzb=None):
+    n = len(brow) if nnzb is None else nnzb
+    br = torch.zeros(cap, dtype=torch.int32)
+    bc = torch.zeros(cap, dtype=torch.int32)
+    br[:len(brow)] = torch.from_numpy(np.asarray(brow, np.int32))
+    bc[:len(bcol)] = torch.from_numpy(np.asarray(bcol, np.int32))
+    return (torch.tensor([n], dtype=torch.int32, device="cuda"), br.cuda(), bc.cuda())
+
+
+def _check_arrays(plan, m, k, b, brow, bcol):
+    info = plan.info()
+    mb = m // b
+    rp, ci, pm = P.csr(mb, brow, bcol)
+    assert np.array_equal(plan.array("row_ptr"), rp)
+    assert np.array_equal(plan.array("col_idx"), ci)
+    assert np.array_equal(plan.array("perm"), pm)
+    if b == 1:
+        want = P.row_plan(mb, rp, info["max_per_item"], sort_items=False)
+    else:
+        want = P.tc_plan(m, k, b, brow, bcol, info["rows_per_group"], info["max_per_item"],
+                         sort_items=False, pad=False)
+        for key in ("grp_ebeg", "ent_col", "ent_tbeg", "ent_cover", "tile_row", "blk_slot",
+                    "blk_off"):
+            assert np.array_equal(plan.array(key), want[key]), key
+    assert np.array_equal(plan.array("items").reshape(-1, 6), want["items"])
+    assert np.array_equal(plan.array("ws_row0"), want["ws_row0"])
+    assert np.array_equal(plan.array("red").reshape(-1, 3), want["red"])
+    assert info["ws_rows"] == want["ws_rows"]
+
+
+@pytest.mark.parametrize("b,dt", [(16, torch.bfloat16), (8, torch.float16), (4, torch.bfloat16),
+                                  (1, torch.float16)])
+def test_dynamic_calls_parity_and_plans(b, dt):
+    m = k = 1024 if b > 1 else 512
+    n = 136
+    cap = wl.nnzb_for(m, k, b, 1 / 16)
+    plan = S.Plan(m, k, n, b, w_dtype=S.dtype_code(dt), mode=S.DYNAMIC, nnzb_max=cap)
+    for call in range(3):
+        c = wl.dynamic_call(call + 10 * b, m=m, k=k, n=n, b=b, d_max=1 / 16)
+        vals = torch.from_numpy(c["vals"]).to(dt)
+        X = torch.from_numpy(c["X"]).to(dt)
+        pat = _dev_pattern(c["brow"], c["bcol"], cap)
+        vd = torch.zeros((cap, b, b), dtype=dt)
+        vd[:len(vals)] = vals
+        Y = plan.run(X.cuda(), values=vd.cuda(), pattern=pat)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X)
+        assert oracle.normwise_err(Y.cpu(), Yo, oracle.block_fro(vals), X) <= 4e-3
+        _check_arrays(plan, m, k, b, c["brow"], c["bcol"])
+
+
+@pytest.mark.parametrize("b", [16, 1])
+def test_dynamic_worst_case_single_row(b):
+    """Appendix A.2's worst case: every block in one partition.  The group
+    (or row) is split into chunks and reduced."""
+    m, k, n = 512, 4096, 64
+    kb = k // b
+    nnz = min(kb, 256)
+    brow = np.zeros(nnz, np.int32)
+    bcol = (np.arange(nnz) * (kb // nnz)).astype(np.int32)
+    cap = nnz + 64
+    dt = torch.float16
+    rng = np.random.default_rng(4)
+    vals = torch.from_numpy(rng.standard_normal((nnz, b, b)).astype(np.float32)).to(dt)
+    X = torch.from_numpy(rng.standard_normal((k, n)).astype(np.float32)).to(dt)
+    plan = S.Plan(m, k, n, b, w_dtype=S.F16, mode=S.DYNAMIC, nnzb_max=cap)
+    vd = torch.zeros((cap, b, b), dtype=dt)
+    vd[:nnz] = vals
+    Y = plan.run(X.cuda(), values=vd.cuda(), pattern=_dev_pattern(brow, bcol, cap))
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert plan.info()["n_reductions"] == 1
+    Yo = oracle.spmm(m, k, b, brow, bcol, vals, X)
+    assert oracle.normwise_err(Y.cpu(), Yo, oracle.block_fro(vals), X) <= 4e-3
+    _check_arrays(plan, m, k, b, brow, bcol)
+
+
+@pytest.mark.parametrize("b", [16, 1])
+@pytest.mark.parametrize("bad", ["duplicate", "row_range", "col_range", "over_capacity",
+                                 "negative"])
+def test_dynamic_rejects_bad_patterns(b, bad):
+    m = k = 256
+    n = 32
+    cap = 64
+    brow = np.arange(8, dtype=np.int32) % (m // b)
+    bcol = (np.arange(8, dtype=np.int32) * 3) % (k // b)
+    nnzb = 8
+    if bad == "duplicate":
+        brow[5], bcol[5] = brow[2], bcol[2]
+    elif bad == "row_range":
+        brow[3] = m // b
+    elif bad == "col_range":
+        bcol[7] = -1
+    elif bad == "over_capacity":
+        nnzb = cap + 1
+    elif bad == "negative":
+        nnzb = -3
+    plan = S.Plan(m, k, n, b, w_dtype=S.F16, mode=S.DYNAMIC, nnzb_max=cap)
+    X = torch.ones((k, n), dtype=torch.float16, device="cuda")
+    Y = torch.full((m, n), 5.0, dtype=torch.float16, device="cuda")
+    vals = torch.ones((cap, b, b), dtype=torch.float16, device="cuda")
+    plan.run(X, Y, values=vals, pattern=_dev_pattern(brow, bcol, cap, nnzb))
+    torch.cuda.synchronize()
+    want = S.ERR_CAPACITY if bad in ("over_capacity", "negative") else S.ERR_PATTERN
+    assert plan.status() == want
+    assert torch.all(Y == 5.0), "Y must be left unwritten"
+    # the plan recovers on the next valid call
+    Y2 = plan.run(X, values=vals, pattern=_dev_pattern(brow[:1] * 0, bcol[:1] * 0, cap))
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert torch.all(Y2[:b] == b) and not torch.any(Y2[b:])
+
+
+def test_dynamic_empty_pattern():
+    plan = S.Plan(512, 512, 64, 16, w_dtype=S.BF16, mode=S.DYNAMIC, nnzb_max=32)
+    Y = torch.full((512, 64), 3.0, dtype=torch.bfloat16, device="cuda")
+    vals = torch.zeros((32, 16, 16), dtype=torch.bfloat16, device="cuda")
+    plan.run(torch.ones((512, 64), dtype=torch.bfloat16, device="cuda"), Y, values=vals,
+             pattern=_dev_pattern([], [], 32, 0))
+    torch.cuda.synchronize()
+    assert plan.status() == 0 and not torch.any(Y)
+
+
+def test_dynamic_full_size_sampled():
+    """m = k = 8192, n = 1024, b = 16, d_max = 1/16 (nnzb_max = 16384): two
+    calls with fresh patterns; sampled block rows against the oracle."""
+    m = k = 8192
+    n = 1024
+    cap = 16384
+    plan = S.Plan(m, k, n, 16, w_dtype=S.BF16, mode=S.DYNAMIC, nnzb_max=cap)
+    for call in range(2):
+        c = wl.dynamic_call(call)
+        vals = torch.from_numpy(c["vals"]).to(torch.bfloat16)
+        X = torch.from_numpy(c["X"]).to(torch.bfloat16)
+        vd = torch.zeros((cap, 16, 16), dtype=torch.bfloat16)
+        vd[:len(vals)] = vals
+        Y = plan.run(X.cuda(), values=vd.cuda(), pattern=_dev_pattern(c["brow"], c["bcol"], cap))
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        rows = [0, 101, 511]
+        sel = np.isin(c["brow"], rows)
+        remap = {r: i for i, r in enumerate(rows)}
+        br = np.array([remap[r] for r in c["brow"][sel]], np.int32)
+        Yo = oracle.spmm(len(rows) * 16, k, 16, br, c["bcol"][sel], vals[sel], X)
+        Ys = torch.cat([Y[r * 16:(r + 1) * 16].cpu() for r in rows])
+        assert oracle.normwise_err(Ys, Yo, oracle.block_fro(vals[sel]), X) <= 4e-3
+        _check_arrays(plan, m, k, 16, c["brow"], c["bcol"])
