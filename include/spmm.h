@@ -230,6 +230,31 @@ spmm_status spmm_batch_run(int32_t count, spmm_plan *const *plans, const void *c
                            const int64_t *n, const int64_t *ldx, void *const *d_Y,
                            const int64_t *ldy, void *stream);
 
+/*
+ * spmm_gather_noalloc -- the dynamic b = 1 product (device re-partition,
+ * gather kernel, split-row reduction) for callers that cannot allocate
+ * device memory: it calls no cudaMalloc / cudaFree / allocating library
+ * routine and needs no plan.  The paper has no counterpart; this is a
+ * deployment convenience of this library.
+ *   m, k          : W is m x k (b = 1), m <= 8192.
+ *   dtype         : F32, F16 or BF16 for values, X and Y alike.
+ *   d_nnzb, d_brow, d_bcol : device pattern as in spmm_dpattern, nnzb_max <= 262144.
+ *   d_values      : device values in pattern order (nnzb_max entries).
+ *   d_X, n, ldx / d_Y, ldy : X (k x n) and Y (m x n), n <= 256.
+ *   d_status      : optional device int32 that receives the pattern status
+ *                   (0 or an spmm_status code); NULL keeps it internal.
+ * All scratch lives in one file-scope device array of about 14 MB that every
+ * GPU loading the library holds until exit; sizes beyond the limits above
+ * return SPMM_ERR_SHAPE before anything is enqueued.  Calls share that array
+ * (each clears what must start at zero), so calls that overlap on the GPU
+ * race: serialise them.  The first call on a device looks up the array's
+ * device address; make it before any stream capture.
+ */
+spmm_status spmm_gather_noalloc(int64_t m, int64_t k, spmm_dtype dtype, const int32_t *d_nnzb,
+                                const int32_t *d_brow, const int32_t *d_bcol, int64_t nnzb_max,
+                                const void *d_values, const void *d_X, int64_t n, int64_t ldx,
+                                void *d_Y, int64_t ldy, int32_t *d_status, void *stream);
+
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char *spmm_last_error(void);
 

@@ -35,7 +35,7 @@ ARRAYS = {"row_ptr": 0, "col_idx": 1, "perm": 2, "items": 3, "grp_row0": 4, "grp
 EXPORTS = ["spmm_plan_create", "spmm_pack_values", "spmm_run", "spmm_run_host",
            "spmm_get_status", "spmm_plan_get_info", "spmm_plan_get_array",
            "spmm_plan_destroy", "spmm_equal_partition", "spmm_bucket_size", "spmm_batch_run",
-           "spmm_last_error", "spmm_version"]
+           "spmm_last_error", "spmm_version", "spmm_gather_noalloc"]
 
 
 class SpmmError(RuntimeError):
@@ -94,6 +94,8 @@ def lib():
         L.spmm_batch_run.argtypes = [i32, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(vp),
                                      ctypes.POINTER(i64), vp]
+        L.spmm_gather_noalloc.argtypes = [i64, i64, i32, vp, vp, vp, i64, vp, vp, i64, i64, vp,
+                                          i64, vp, vp]
         L.spmm_last_error.restype = ctypes.c_char_p
         L.spmm_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -167,6 +169,13 @@ def spmm_equal_partition(extent, q):
 
 def spmm_bucket_size(m, k, d_num, d_den, q_m, q_k):
     return lib().spmm_bucket_size(m, k, d_num, d_den, q_m, q_k)
+
+
+def spmm_gather_noalloc(m, k, dtype, d_nnzb, d_brow, d_bcol, nnzb_max, d_values, d_X, n, ldx,
+                        d_Y, ldy, d_status, stream):
+    """The allocation-free dynamic b = 1 product (see include/spmm.h)."""
+    return _check(lib().spmm_gather_noalloc(m, k, dtype, d_nnzb, d_brow, d_bcol, nnzb_max,
+                                            d_values, d_X, n, ldx, d_Y, ldy, d_status, stream))
 
 
 def spmm_version():
