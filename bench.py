@@ -274,6 +274,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--no-dynamic", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--point", default=None,
                     help="run one sweep point only, 'b:1/d' e.g. 16:4 (profiling)")
@@ -295,13 +296,31 @@ def main():
     pts = build_points(torch, S, wl, dev, only)
     stream = torch.cuda.current_stream()
 
+    # each product is captured once in its own CUDA graph; a step replays the
+    # 16 graphs back to back with an event pair around each replay, so host
+    # launch latency never enters the device timings
+    cap_stream = torch.cuda.Stream()
+    cap_stream.wait_stream(torch.cuda.current_stream())
+    graphs = []
+    with torch.cuda.stream(cap_stream):
+        for _ in range(3):
+            for p in pts:           # eager warm-up: module load, kernel attributes
+                p["plan"].run(p["X"], p["Y"])
+        cap_stream.synchronize()
+        for p in pts:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=cap_stream):
+                p["plan"].run(p["X"], p["Y"])
+            graphs.append(g)
+    torch.cuda.current_stream().wait_stream(cap_stream)
+
     def step(evs=None):
-        for i, p in enumerate(pts):
+        for i, g in enumerate(graphs):
             if evs is not None:
-                evs[i][0].record(stream)
-            p["plan"].run(p["X"], p["Y"])
+                evs[i][0].record()
+            g.replay()
             if evs is not None:
-                evs[i][1].record(stream)
+                evs[i][1].record()
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -317,35 +336,36 @@ def main():
     barrier(world)
     torch.cuda.synchronize()
     with sampler:
-        start.record(stream)
-        for s in range(args.steps):
-            step(evs[s])
-        end.record(stream)
+        start.record()
+        for s_ in range(args.steps):
+            step(evs[s_])
+        end.record()
         torch.cuda.synchronize()
     barrier(world)
     t_ms = start.elapsed_time(end)
     t_ms = max_over_ranks(t_ms, world)
 
-    per = [[evs[s][i][0].elapsed_time(evs[s][i][1]) for s in range(args.steps)]
-           for i in range(len(pts))]
+    # per-launch durations over the timed steps (median per product)
+    per = [statistics.median(evs[s_][i][0].elapsed_time(evs[s_][i][1])
+                             for s_ in range(args.steps)) for i in range(len(pts))]
     flops_step = sum(2.0 * p["nnzb"] * p["b"] ** 2 * N for p in pts)
     value = flops_step * args.steps * world / (t_ms * 1e-3) / 1e12
 
     points, fam = [], {}
     for i, p in enumerate(pts):
         fl, by, bound, t_roof = roof_of(p["b"], p["nnzb"], peaks)
-        us = statistics.median(per[i]) * 1e3
+        us = per[i] * 1e3
         kern = {1: "plain", 2: "gather", 3: "tc"}[p["kernel"]]
         points.append({"b": p["b"], "d": "1/%d" % round(1 / p["d"]), "kernel": kern,
-                       "us_median": round(us, 2),
+                       "us": round(us, 2),
                        "tflops_nz": round(fl / (us * 1e-6) / 1e12, 2),
                        "tflops_dense_equiv": round(2.0 * M * K * N / (us * 1e-6) / 1e12, 2),
                        "gbs_compulsory": round(by / (us * 1e-6) / 1e9, 1),
                        "bound": bound, "roof_frac": round(t_roof / (us * 1e-6), 3)})
         f = fam.setdefault(kern, {"t": 0.0, "flops": 0.0, "bytes": 0.0, "bounds": set()})
-        f["t"] += sum(per[i]) * 1e-3
-        f["flops"] += fl * args.steps
-        f["bytes"] += by * args.steps
+        f["t"] += per[i] * 1e-3
+        f["flops"] += fl
+        f["bytes"] += by
         f["bounds"].add(bound)
     dom = max(fam, key=lambda k: fam[k]["t"])
     F = fam[dom]
@@ -380,6 +400,10 @@ def main():
             q["b"] == 16 and abs(q["d"] - 1 / 16) < 1e-12 for q in pts):
         comparators = run_comparators(torch, S, wl, dev, pts)
 
+    dynamic = None
+    if rank == 0 and not args.no_dynamic and args.point is None:
+        dynamic = run_dynamic(torch, S, wl, dev)
+
     launches = sum(launches_per_run(p) for p in pts) * args.steps
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s",
@@ -389,7 +413,7 @@ def main():
                 "data": "synthetic", "config": workload_config(),
                 "e2e": e2e, "gpu_launches": launches, "clocks": sampler.summary(),
                 "roofline": roofline, "cpu_baseline": cpu, "points": points,
-                "comparators": comparators}
+                "comparators": comparators, "dynamic": dynamic}
         print(json.dumps(line))
     for p in pts:
         p["plan"].close()
@@ -397,6 +421,92 @@ def main():
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def graph_time_us(torch, fn, reps):
+    """Median device time of fn() captured in a CUDA graph (one replay = one fn)."""
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        for _ in range(2):
+            fn()
+        st.synchronize()
+        with torch.cuda.graph(g, stream=st):
+            fn()
+    torch.cuda.current_stream().wait_stream(st)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        g.replay()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) * 1e3)
+    return statistics.median(ts)
+
+
+def run_dynamic(torch, S, wl, dev, calls=4, reps=10):
+    """Dynamic mode, m = k = 8192, n = 1024, b = 16, d_max = 1/16, BF16: every
+    call carries a fresh pattern (nnzb uniform in [8192, 16384]) and values,
+    re-partitioned on the device.  Reports the per-call time, the
+    re-partition + packing time alone (a call with n = 0), and the ratio to
+    a static plan of the same pattern (the analogue of Table 3)."""
+    m = k = 8192
+    n = 1024
+    cap = 16384
+    bf = torch.bfloat16
+    dplan = S.Plan(m, k, n, 16, w_dtype=S.BF16, mode=S.DYNAMIC, nnzb_max=cap)
+    inputs = []
+    for c in range(calls):
+        cs = wl.dynamic_call(c)
+        br = torch.zeros(cap, dtype=torch.int32)
+        bc = torch.zeros(cap, dtype=torch.int32)
+        br[:len(cs["brow"])] = torch.from_numpy(cs["brow"])
+        bc[:len(cs["bcol"])] = torch.from_numpy(cs["bcol"])
+        vd = torch.zeros((cap, 16, 16), dtype=bf)
+        vd[:len(cs["vals"])] = torch.from_numpy(cs["vals"]).to(bf)
+        inputs.append(dict(c=cs, pat=(torch.tensor([len(cs["brow"])], dtype=torch.int32, device=dev),
+                                      br.to(dev), bc.to(dev)),
+                           vals=vd.to(dev), X=torch.from_numpy(cs["X"]).to(bf).to(dev)))
+    Y = torch.empty((m, n), dtype=bf, device=dev)
+    Xe = torch.empty((k, 0), dtype=bf, device=dev)
+    Ye = torch.empty((m, 0), dtype=bf, device=dev)
+    flops = sum(2.0 * len(i["c"]["brow"]) * 256 * n for i in inputs)
+
+    def calls_fn():
+        for i in inputs:
+            dplan.run(i["X"], Y, values=i["vals"], pattern=i["pat"])
+
+    def part_fn():
+        for i in inputs:
+            dplan.run(Xe, Ye, values=i["vals"], pattern=i["pat"])
+
+    t_dyn = graph_time_us(torch, calls_fn, reps) / calls
+    t_part = graph_time_us(torch, part_fn, reps) / calls
+    i0 = inputs[0]
+    splan = S.Plan(m, k, n, 16, w_dtype=S.BF16, brow=i0["c"]["brow"], bcol=i0["c"]["bcol"])
+    splan.pack(i0["vals"][:len(i0["c"]["brow"])].contiguous())
+    t_static = graph_time_us(torch, lambda: splan.run(i0["X"], Y), reps)
+
+    def one_dyn():
+        dplan.run(i0["X"], Y, values=i0["vals"], pattern=i0["pat"])
+    t_dyn0 = graph_time_us(torch, one_dyn, reps)
+    fl0 = 2.0 * len(i0["c"]["brow"]) * 256 * n
+    out = {"workload": "dynamic m=k=8192 n=1024 b=16 d_max=1/16 BF16, fresh pattern per call",
+           "us_per_call": round(t_dyn, 1), "tflops_nz": round(flops / calls / t_dyn / 1e6, 2),
+           "repartition_pack_us": round(t_part, 1),
+           "static_same_pattern_us": round(t_static, 1),
+           "dynamic_same_pattern_us": round(t_dyn0, 1),
+           "dynamic_over_static_time": round(t_dyn0 / t_static, 3),
+           "static_tflops_nz": round(fl0 / t_static / 1e6, 2),
+           "gpu_launches_per_call": None}
+    dplan.close()
+    splan.close()
+    return out
 
 
 def run_comparators(torch, S, wl, dev, pts):

@@ -433,7 +433,16 @@ void spmm_plan_destroy(spmm_plan *plan) {
     free_plan(plan);
 }
 
+static bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone;
+}
+
+// A call inside a stream capture becomes part of a graph: it records no
+// completion event and skips the cross-stream check (a graph's replays are
+// ordered by the stream they are launched on).
 static spmm_status busy_check(spmm_plan *p, cudaStream_t s) {
+    if (capturing(s)) return SPMM_OK;
     if (p->ran && p->last_stream != s) {
         cudaError_t q = cudaEventQuery(p->done);
         if (q == cudaErrorNotReady) {
@@ -448,6 +457,7 @@ static spmm_status busy_check(spmm_plan *p, cudaStream_t s) {
 static spmm_status finish_call(spmm_plan *p, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "kernel launch");
+    if (capturing(s)) return SPMM_OK;
     e = cudaEventRecord(p->done, s);
     if (e != cudaSuccess) return cuda_fail(e, "event record");
     p->last_stream = s;
