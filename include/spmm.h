@@ -255,6 +255,17 @@ spmm_status spmm_gather_noalloc(int64_t m, int64_t k, spmm_dtype dtype, const in
                                 const void *d_values, const void *d_X, int64_t n, int64_t ldx,
                                 void *d_Y, int64_t ldy, int32_t *d_status, void *stream);
 
+/*
+ * spmm_quantize_e4m3 -- per-block FP8 quantiser for E4M3 plans (the
+ * precision form of the value packing step, Section 3.2's host-supplied
+ * values): for each of the nnzb b x b blocks at d_src (src_dtype F32, F16 or
+ * BF16, pattern order), scale = max|w| / 448 (1 for an all-zero block) and
+ * code = the E4M3 value nearest w / scale (round to nearest even,
+ * saturating).  Writes d_codes[nnzb * b * b] and d_scales[nnzb] (device).
+ */
+spmm_status spmm_quantize_e4m3(int64_t nnzb, int32_t b, spmm_dtype src_dtype, const void *d_src,
+                               uint8_t *d_codes, float *d_scales, void *stream);
+
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char *spmm_last_error(void);
 

@@ -734,9 +734,64 @@ spmm_status spmm_plan_get_array(spmm_plan *p, spmm_array which, void *dst, int64
 spmm_status spmm_batch_run(int32_t count, spmm_plan *const *plans, const void *const *d_X,
                            const int64_t *n, const int64_t *ldx, void *const *d_Y,
                            const int64_t *ldy, void *stream) {
-    (void)count; (void)plans; (void)d_X; (void)n; (void)ldx; (void)d_Y; (void)ldy; (void)stream;
-    set_error("batched launch is not built yet");
-    return SPMM_ERR_UNSUPPORTED;
+    g_err[0] = 0;
+    if (count <= 0 || count > kMaxBatchProblems || !plans || !d_X || !n || !d_Y) {
+        set_error("batch: 1 <= count <= %d and plans, X, n, Y required", kMaxBatchProblems);
+        return SPMM_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i) {
+        spmm_plan *p = plans[i];
+        if (!p || p->host_only || p->mode != SPMM_STATIC || p->kernel != SPMM_KERNEL_TC) {
+            set_error("batch: problem %d is not a device static TC plan", i);
+            return SPMM_ERR_UNSUPPORTED;
+        }
+        if (p->xdt != plans[0]->xdt || p->wdt != plans[0]->wdt) {
+            set_error("batch: all problems must share W and X types");
+            return SPMM_ERR_UNSUPPORTED;
+        }
+        if (!p->packed) {
+            set_error("batch: problem %d has no packed values", i);
+            return SPMM_ERR_NOT_PACKED;
+        }
+        const int64_t lx = ldx ? ldx[i] : n[i], ly = ldy ? ldy[i] : n[i];
+        spmm_status st = check_run_args(p, d_X[i], n[i], lx, d_Y[i], ly);
+        if (st != SPMM_OK) return st;
+        st = busy_check(p, s);
+        if (st != SPMM_OK) return st;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == p) {
+                set_error("batch: a plan may appear once per launch");
+                return SPMM_ERR_ARG;
+            }
+    }
+    cudaError_t e = launch_tc_batch(count, plans, d_X, n, ldx, d_Y, ldy, s);
+    if (e != cudaSuccess) return cuda_fail(e, "batched launch");
+    for (int i = 0; i < count; ++i) {
+        spmm_plan *p = plans[i];
+        if (p->n_red > 0 && n[i] > 0) {
+            e = launch_reduce(p, n[i], d_Y[i], ldy ? ldy[i] : n[i], s);
+            if (e != cudaSuccess) return cuda_fail(e, "batched reduction");
+        }
+        spmm_status st = finish_call(p, s);
+        if (st != SPMM_OK) return st;
+    }
+    return SPMM_OK;
+}
+
+spmm_status spmm_quantize_e4m3(int64_t nnzb, int32_t b, spmm_dtype src_dtype, const void *d_src,
+                               uint8_t *d_codes, float *d_scales, void *stream) {
+    g_err[0] = 0;
+    if (nnzb < 0 || !(b == 1 || b == 4 || b == 8 || b == 16) ||
+        (nnzb > 0 && (!d_src || !d_codes || !d_scales)) ||
+        !(src_dtype == SPMM_F32 || src_dtype == SPMM_F16 || src_dtype == SPMM_BF16)) {
+        set_error("quantize: nnzb >= 0, b in {1,4,8,16}, F32/F16/BF16 source and buffers required");
+        return SPMM_ERR_ARG;
+    }
+    cudaError_t e = launch_quantize_e4m3(nnzb, b, src_dtype, d_src, d_codes, d_scales,
+                                         (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "quantize");
+    return SPMM_OK;
 }
 
 }  // extern "C"

@@ -34,9 +34,13 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <map>
 #include <mutex>
+#include <vector>
 
 #include "spmm_internal.h"
 
@@ -48,15 +52,27 @@ namespace {
 #define SPMM_TC_RCAP 16     // tile rows per group (accumulator columns / 16)
 #define SPMM_TC_STAGES 3
 #define SPMM_TC_ENT 4       // X slabs per stage
-#define SPMM_TC_TILES 32    // W tiles per stage
+#define SPMM_TC_TILES 32    // W tiles per stage (16-bit values; E4M3 stages hold 24)
 #endif
 constexpr int kEntStage = SPMM_TC_ENT;                            // X slabs per stage
-constexpr int kTileStage = SPMM_TC_TILES;                         // W tiles per stage
 constexpr int kSlabBytes = kTile * kNTile * 2;                    // 4096: 16 k x 128 n, 16-bit
-constexpr int kStageBytes = kEntStage * kSlabBytes + kTileStage * kTileBytes16;  // 32 KB
+constexpr int kTileBytes8 = kTile * kTile;                        // 256: E4M3 tile, row-major
+constexpr int kScaleBytes = 16 * 4;                               // per slot: 4 x 4 sub-square scales
 constexpr int kStages = SPMM_TC_STAGES;
 constexpr int kRowCap = SPMM_TC_RCAP;
 constexpr int kAccCols = kRowCap * kTile;                         // TMEM columns per buffer
+constexpr int kMaxBatch = 64;                                     // problems per launch
+
+// Stage layout: X slabs | 16-bit W tiles (MMA B operand) | (E4M3 only) the
+// FP8 codes and their scales as loaded, which the converter warps expand
+// into the 16-bit area.
+template <bool W8> struct StageGeom {
+    static constexpr int tiles = W8 ? (SPMM_TC_TILES * 3) / 4 : SPMM_TC_TILES;
+    static constexpr int w16 = kEntStage * kSlabBytes;
+    static constexpr int w8 = w16 + tiles * kTileBytes16;
+    static constexpr int sc = w8 + tiles * kTileBytes8;
+    static constexpr int bytes = W8 ? sc + tiles * kScaleBytes : w8;
+};
 // Two CTAs share an SM: each holds one accumulator set (256 of the SM's 512
 // TMEM columns) and half the shared memory, so the two CTAs' producer / MMA
 // pipelines run side by side and one CTA's epilogue overlaps the other's MMAs.
@@ -64,22 +80,24 @@ constexpr int kAccCols = kRowCap * kTile;                         // TMEM column
 // dependent scalar work allows; a second pipeline per SM doubles that rate.)
 constexpr int kAccBufs = 1;
 constexpr int kCtasPerSm = SPMM_TC_CTAS;
-static_assert(kRowCap <= kMaxGroupRows && kTileStage >= kRowCap, "stage must hold a full entry");
+static_assert(kRowCap <= kMaxGroupRows && (SPMM_TC_TILES * 3) / 4 >= kRowCap,
+              "stage must hold a full entry");
 constexpr int kThreads = 192;
 constexpr unsigned long long kWaitNs = 2000000000ull;             // 2 s per wait
 
 struct StageMeta {
     uint32_t nent;                 // entries in the stage; bit 31: last stage of the unit
+    uint32_t nslots;               // W tiles in the stage
     uint32_t cover[kEntStage];     // per entry: covered rows | interval starts << 16
 };
 
 struct __align__(8) Smem {
-    uint64_t full[kStages], empty[kStages], accf[kAccBufs], acce[kAccBufs];
+    uint64_t full[kStages], empty[kStages], conv[kStages], accf[kAccBufs], acce[kAccBufs];
     StageMeta meta[kStages];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
     int32_t issued, consumed;
-    int64_t nitems;
+    int64_t nunits;
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -223,19 +241,27 @@ template <> struct Cvt<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 f(float v) { return __float2bfloat16_rn(v); }
 };
 
-struct TcArgs {
-    const int32_t *items;
-    const int32_t *n_items_dev;  // dynamic plans: item count on the device (else null)
-    int64_t n_items;
-    const int32_t *grp_row0, *grp_rows, *ent_col, *ent_tbeg, *ent_cover;
-    const uint8_t *packed;       // 16 x 16 tiles, 512 B each, MMA B layout
+// One product of a launch (a single spmm_run is a batch of one).
+struct TcProb {
+    const int32_t *items, *grp_row0, *grp_rows, *ent_col, *ent_tbeg, *ent_cover;
+    const uint8_t *packed;       // 16-bit tiles (512 B, MMA B layout) or E4M3 tiles (256 B)
+    const float *tile_scale;     // E4M3: 16 scales per slot (4 x 4 sub-squares of 4 x 4)
     void *Y;
-    int64_t ldy, n;
     float *ws;
     const int64_t *ws_row0;
+    int64_t ldy, n;
+    int64_t unit_base;           // first unit of this problem in launch order
+    int32_t ntn, x3d;            // n tiles of 128; X map is 3-D (64, k, n/64)
+};
+
+struct TcBatch {
+    CUtensorMap maps[kMaxBatch]; // X of each problem
+    TcProb prob[kMaxBatch];
+    const int32_t *units;        // optional schedule: (problem, unit) pairs, costliest first
+    int64_t total_units;
+    int32_t nprob;
+    const int32_t *n_items_dev;  // dynamic single problem: item count on the device
     int32_t *status;
-    int ntn;                     // n tiles of 128
-    int x3d;                     // 1: X map is 3-D (64, k, n/64), one box per slab
 };
 
 __device__ __forceinline__ void record(int32_t *status, int32_t code) {
@@ -250,23 +276,53 @@ __device__ __forceinline__ uint64_t a_desc(uint32_t addr) { return smem_desc(add
 // k-adjacent ones 128 B apart (leading), row-adjacent ones 256 B (stride).
 __device__ __forceinline__ uint64_t b_desc(uint32_t addr) { return smem_desc(addr, 128, 256, 0); }
 
-template <typename T>
+// Unit u of the launch -> (problem, item, n tile).
+struct Unit {
+    int p;
+    int64_t item;
+    int t;
+};
+__device__ __forceinline__ Unit decode_unit(const TcBatch &B, int64_t u) {
+    Unit r;
+    int64_t lu;
+    if (B.units) {
+        r.p = B.units[2 * u];
+        lu = B.units[2 * u + 1];
+    } else {
+        int p = 0;
+        while (p + 1 < B.nprob && B.prob[p + 1].unit_base <= u) ++p;
+        r.p = p;
+        lu = u - B.prob[p].unit_base;
+    }
+    const int ntn = B.prob[r.p].ntn;
+    r.item = lu / ntn;
+    r.t = (int)(lu - r.item * ntn);
+    return r;
+}
+
+template <typename T, bool W8>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
-    tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs args) {
+    tc_kernel(const __grid_constant__ TcBatch B) {
+    using G = StageGeom<W8>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *stages = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    Smem *sm = (Smem *)(stages + kStages * kStageBytes);
+    Smem *sm = (Smem *)(stages + kStages * G::bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        // dynamic plans: a pattern rejected on the device leaves Y unwritten
-        const bool skip = args.n_items_dev && *(volatile int32_t *)args.status != 0;
-        int64_t ni = args.n_items;
-        if (args.n_items_dev) ni = min(ni, (int64_t)max(*args.n_items_dev, 0));
-        sm->nitems = skip ? 0 : ni;
+        int64_t nu = B.total_units;
+        if (B.n_items_dev) {
+            // dynamic plans: item count from the device; a rejected pattern
+            // leaves Y unwritten
+            const int64_t cap = B.total_units / B.prob[0].ntn;
+            const int64_t ni = min(cap, (int64_t)max(*B.n_items_dev, 0));
+            nu = (*(volatile int32_t *)B.status != 0) ? 0 : ni * B.prob[0].ntn;
+        }
+        sm->nunits = nu;
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&sm->full[s], 1);
             mbar_init(&sm->empty[s], 1);
+            mbar_init(&sm->conv[s], 4);    // E4M3: one arrival per converter warp
         }
         for (int b = 0; b < kAccBufs; ++b) {
             mbar_init(&sm->accf[b], 1);    // MMA completion
@@ -278,7 +334,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const int64_t nunits = sm->nitems * args.ntn;
+    const int64_t nunits = sm->nunits;
     if (nunits == 0) return;
     if (warp == 1) {
         asm volatile(
@@ -308,16 +364,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         int32_t issued = 0;
         bool ok = true;
         for (int64_t u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
-            const int32_t *it = args.items + (u / args.ntn) * kItemFields;
+            const Unit un = decode_unit(B, u);
+            const TcProb &P = B.prob[un.p];
+            const CUtensorMap *xmap = &B.maps[un.p];
+            const int32_t *it = P.items + un.item * kItemFields;
             const int32_t e0 = it[1], e1 = it[2];
-            const int n0 = (int)(u % args.ntn) * kNTile;
+            const int n0 = un.t * kNTile;
             for (int32_t eb = e0; ok && eb < e1; eb += 32) {
                 // lane l holds the metadata of entry eb + l
                 const int32_t e = eb + lane;
                 const bool valid = e < e1;
-                const int32_t mcol = valid ? args.ent_col[e] : 0;
-                const int32_t mtb = valid ? args.ent_tbeg[e] : 0;
-                const uint32_t mcov = valid ? (uint32_t)args.ent_cover[e] : 0u;
+                const int32_t mcol = valid ? P.ent_col[e] : 0;
+                const int32_t mtb = valid ? P.ent_tbeg[e] : 0;
+                const uint32_t mcov = valid ? (uint32_t)P.ent_cover[e] : 0u;
                 const int mslots = __popc(mcov & 0xFFFFu);
                 const int cnt = min(32, e1 - eb);
                 for (int j = 0; j < cnt;) {
@@ -325,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                     int nent = 0, slots = 0;
                     while (j + nent < cnt && nent < kEntStage) {
                         const int t = __shfl_sync(0xffffffffu, mslots, j + nent);
-                        if (slots + t > kTileStage) break;
+                        if (slots + t > G::tiles) break;
                         slots += t;
                         ++nent;
                     }
@@ -337,24 +396,36 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                     }
                     const int32_t stb = __shfl_sync(0xffffffffu, mtb, j);
                     const bool last = (j + nent == cnt) && (eb + 32 >= e1);
-                    uint8_t *st = stages + stage * kStageBytes;
+                    uint8_t *st = stages + stage * G::bytes;
                     const bool mine = lane >= j && lane < j + nent;
                     if (mine) sm->meta[stage].cover[lane - j] = mcov;
-                    if (lane == 0) sm->meta[stage].nent = (uint32_t)nent | (last ? 0x80000000u : 0u);
+                    if (lane == 0) {
+                        sm->meta[stage].nent = (uint32_t)nent | (last ? 0x80000000u : 0u);
+                        sm->meta[stage].nslots = (uint32_t)slots;
+                    }
                     __syncwarp();
                     if (lane == 0) {
-                        mbar_arrive_tx(&sm->full[stage], nent * kSlabBytes + slots * kTileBytes16);
-                        bulk_load(st + kEntStage * kSlabBytes, args.packed + (int64_t)stb * kTileBytes16,
-                                  slots * kTileBytes16, &sm->full[stage]);
+                        if (W8) {
+                            mbar_arrive_tx(&sm->full[stage], nent * kSlabBytes +
+                                                                 slots * (kTileBytes8 + kScaleBytes));
+                            bulk_load(st + G::w8, P.packed + (int64_t)stb * kTileBytes8,
+                                      slots * kTileBytes8, &sm->full[stage]);
+                            bulk_load(st + G::sc, P.tile_scale + (int64_t)stb * 16,
+                                      slots * kScaleBytes, &sm->full[stage]);
+                        } else {
+                            mbar_arrive_tx(&sm->full[stage], nent * kSlabBytes + slots * kTileBytes16);
+                            bulk_load(st + G::w16, P.packed + (int64_t)stb * kTileBytes16,
+                                      slots * kTileBytes16, &sm->full[stage]);
+                        }
                     }
                     if (mine) {
                         uint8_t *slab = st + (lane - j) * kSlabBytes;
-                        if (args.x3d) {
-                            tma_load_3d(slab, &xmap, 0, mcol * kTile, n0 / (kNTile / 2),
+                        if (P.x3d) {
+                            tma_load_3d(slab, xmap, 0, mcol * kTile, n0 / (kNTile / 2),
                                         &sm->full[stage]);
                         } else {
-                            tma_load_2d(slab, &xmap, n0, mcol * kTile, &sm->full[stage]);
-                            tma_load_2d(slab + kSlabBytes / 2, &xmap, n0 + kNTile / 2,
+                            tma_load_2d(slab, xmap, n0, mcol * kTile, &sm->full[stage]);
+                            tma_load_2d(slab + kSlabBytes / 2, xmap, n0 + kNTile / 2,
                                         mcol * kTile, &sm->full[stage]);
                         }
                     }
@@ -369,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             }
         }
         if (!ok && lane == 0) {
-            record(args.status, kDevTimeout);
+            record(B.status, kDevTimeout);
             sm->abort_flag = 1;
         }
         if (lane == 0) sm->issued = issued;
@@ -379,10 +450,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         int stage = 0;
         uint32_t phase = 0;
         int32_t consumed = 0;
-        int local = 0;
         bool ok = true;
+        int local = 0;
         for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, ++local) {
-            const int32_t *it = args.items + (u / args.ntn) * kItemFields;
+            const Unit un = decode_unit(B, u);
+            const int32_t *it = B.prob[un.p].items + un.item * kItemFields;
             const bool has_entries = it[2] > it[1];
             const int ab = local % kAccBufs;
             const uint32_t aphase = (local / kAccBufs) & 1;
@@ -393,7 +465,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             const uint32_t dbase = tmem + ab * kAccCols;
             bool last = !has_entries;
             while (ok && !last) {
-                if (lane == 0) w = mbar_wait(&sm->full[stage], phase, sm) ? 1 : 0;
+                if (lane == 0)
+                    w = mbar_wait(W8 ? &sm->conv[stage] : &sm->full[stage], phase, sm) ? 1 : 0;
                 if (!__shfl_sync(0xffffffffu, w, 0)) {
                     ok = false;
                     break;
@@ -403,8 +476,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                 const uint32_t mnent = __shfl_sync(0xffffffffu, sm->meta[stage].nent, 0);
                 const int nent = (int)(mnent & 0xffu);
                 last = (mnent >> 31) != 0;
-                const uint32_t sbase = smem_u32(stages + stage * kStageBytes);
-                uint64_t bdesc = b_desc(sbase + kEntStage * kSlabBytes);
+                const uint32_t sbase = smem_u32(stages + stage * G::bytes);
+                uint64_t bdesc = b_desc(sbase + G::w16);
                 for (int i = 0; i < nent; ++i) {
                     const uint64_t adesc = a_desc(sbase + i * kSlabBytes);
                     const uint32_t c = __shfl_sync(0xffffffffu, sm->meta[stage].cover[i], 0);
@@ -434,38 +507,96 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         }
         if (lane == 0) {
             if (!ok) {
-                record(args.status, kDevTimeout);
+                record(B.status, kDevTimeout);
                 sm->abort_flag = 1;
             }
             sm->consumed = consumed;
         }
     } else {
-        // ---------------------------------------------------- epilogue
+        // ------------------------- converters (E4M3) and epilogue
         const int q = warp & 3;              // TMEM lane quarter of this warp
         const int nl = q * 32 + lane;        // D row = column of Y within the tile
-        T *Y = (T *)args.Y;
+        const int et = threadIdx.x - 64;     // 0..127 among the four warps
         int local = 0;
-        for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, ++local) {
-            const int32_t *it = args.items + (u / args.ntn) * kItemFields;
+        int cstage = 0;
+        uint32_t cphase = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; ok && u < nunits; u += gridDim.x, ++local) {
+            const Unit un = decode_unit(B, u);
+            const TcProb &P = B.prob[un.p];
+            const int32_t *it = P.items + un.item * kItemFields;
+            if (W8 && it[2] > it[1]) {
+                // expand this unit's E4M3 tiles to 16-bit MMA tiles, stage by stage
+                bool last = false;
+                while (!last) {
+                    int w = 1;
+                    if (lane == 0) w = mbar_wait(&sm->full[cstage], cphase, sm) ? 1 : 0;
+                    if (!__shfl_sync(0xffffffffu, w, 0)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t mnent = sm->meta[cstage].nent;
+                    last = (mnent >> 31) != 0;
+                    const int nslots = (int)sm->meta[cstage].nslots;
+                    uint8_t *st = stages + cstage * G::bytes;
+                    const uint8_t *w8 = st + G::w8;
+                    const float *sc = (const float *)(st + G::sc);
+                    // thread -> (slot, tile row i): 16 codes of one row per step
+                    for (int r = et; r < nslots * kTile; r += 128) {
+                        const int slot = r >> 4, i = r & 15;
+                        const uint4 codes = *(const uint4 *)(w8 + slot * kTileBytes8 + i * kTile);
+                        const float *s4 = sc + slot * 16 + (i >> 2) * 4;
+                        const uint32_t cw[4] = {codes.x, codes.y, codes.z, codes.w};
+                        uint32_t outw[8];
+#pragma unroll
+                        for (int qd = 0; qd < 4; ++qd) {          // columns 4qd .. 4qd+3
+                            const float scl = s4[qd];
+                            const __half2_raw h01 = __nv_cvt_fp8x2_to_halfraw2(
+                                (__nv_fp8x2_storage_t)(cw[qd] & 0xFFFFu), __NV_E4M3);
+                            const __half2_raw h23 = __nv_cvt_fp8x2_to_halfraw2(
+                                (__nv_fp8x2_storage_t)(cw[qd] >> 16), __NV_E4M3);
+                            const float2 f01 = __half22float2(*(const __half2 *)&h01);
+                            const float2 f23 = __half22float2(*(const __half2 *)&h23);
+                            const T o0 = Cvt<T>::f(f01.x * scl), o1 = Cvt<T>::f(f01.y * scl);
+                            const T o2 = Cvt<T>::f(f23.x * scl), o3 = Cvt<T>::f(f23.y * scl);
+                            outw[qd * 2] = (uint32_t)(*(const uint16_t *)&o0) |
+                                           ((uint32_t)(*(const uint16_t *)&o1) << 16);
+                            outw[qd * 2 + 1] = (uint32_t)(*(const uint16_t *)&o2) |
+                                               ((uint32_t)(*(const uint16_t *)&o3) << 16);
+                        }
+                        // columns 0-7 and 8-15 land in two core matrices
+                        uint8_t *dst = st + G::w16 + slot * kTileBytes16 + (i >> 3) * 256 + (i & 7) * 16;
+                        *(uint4 *)dst = make_uint4(outw[0], outw[1], outw[2], outw[3]);
+                        *(uint4 *)(dst + 128) = make_uint4(outw[4], outw[5], outw[6], outw[7]);
+                    }
+                    // make the generic-proxy writes visible to the tensor core
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm->conv[cstage]);
+                    if (++cstage == kStages) {
+                        cstage = 0;
+                        cphase ^= 1;
+                    }
+                }
+                if (!ok) break;
+            }
             const int ab = local % kAccBufs;
             const uint32_t aphase = (local / kAccBufs) & 1;
             int okw = 1;
             if (lane == 0) okw = mbar_wait(&sm->accf[ab], aphase, sm) ? 1 : 0;
             okw = __shfl_sync(0xffffffffu, okw, 0);
             if (!okw) {
-                if (lane == 0) {
-                    record(args.status, kDevTimeout);
-                    sm->abort_flag = 1;
-                }
+                ok = false;
                 break;
             }
             tc_fence_after();
             const int32_t g = it[0], slot = it[5];
-            const int rows = args.grp_rows[g];
-            const int64_t yrow0 = (int64_t)args.grp_row0[g] * kTile;
-            const int64_t col = (int64_t)(u % args.ntn) * kNTile + nl;
-            const bool in = col < args.n;
-            const int64_t wrow0 = slot >= 0 ? args.ws_row0[slot] : 0;
+            const int rows = P.grp_rows[g];
+            const int64_t yrow0 = (int64_t)P.grp_row0[g] * kTile;
+            const int64_t col = (int64_t)un.t * kNTile + nl;
+            const bool in = col < P.n;
+            const int64_t wrow0 = slot >= 0 ? P.ws_row0[slot] : 0;
+            T *Y = (T *)P.Y;
             for (int r = 0; r < rows; ++r) {
                 float v[16];
                 const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + ab * kAccCols + r * kTile;
@@ -473,18 +604,22 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                 tmem_zero16(ta);
                 if (!in) continue;
                 if (slot >= 0) {
-                    float *dst = args.ws + (wrow0 + r * kTile) * args.n + col;
+                    float *dst = P.ws + (wrow0 + r * kTile) * P.n + col;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) dst[i * args.n] = v[i];
+                    for (int i = 0; i < 16; ++i) dst[i * P.n] = v[i];
                 } else {
-                    T *dst = Y + (yrow0 + r * kTile) * args.ldy + col;
+                    T *dst = Y + (yrow0 + r * kTile) * P.ldy + col;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) dst[i * args.ldy] = Cvt<T>::f(v[i]);
+                    for (int i = 0; i < 16; ++i) dst[i * P.ldy] = Cvt<T>::f(v[i]);
                 }
             }
             tmem_wait_st();
             tc_fence_before();
             mbar_arrive(&sm->acce[ab]);
+        }
+        if (!ok && lane == 0) {
+            record(B.status, kDevTimeout);
+            sm->abort_flag = 1;
         }
     }
 
@@ -530,6 +665,50 @@ __global__ void pack_tiles_kernel(const U *__restrict__ vals, const int32_t *__r
     }
 }
 
+// E4M3 tiles: codes row-major (16 x 16 bytes per slot) and, per slot, the
+// scale of each 4 x 4 sub-square (the block covering it: one scale for
+// b = 16, four for b = 8, sixteen for b = 4).
+__global__ void pack_tiles_e4m3_kernel(const uint8_t *__restrict__ codes,
+                                       const float *__restrict__ scales,
+                                       const int32_t *__restrict__ blk_slot,
+                                       const int32_t *__restrict__ blk_off, int64_t nnzb, int b,
+                                       const int32_t *__restrict__ nnzb_dev, uint8_t *__restrict__ out,
+                                       float *__restrict__ tile_scale) {
+    if (nnzb_dev) nnzb = min((int64_t)max(*nnzb_dev, 0), nnzb);
+    const int bb = b * b;
+    const int64_t total = nnzb * bb;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t / bb;
+        const int e = (int)(t - p * bb);
+        const int off = blk_off[p];
+        const int ti = off / kTile + e / b, tj = off % kTile + e % b;
+        const int64_t s = blk_slot[p];
+        out[s * kTileBytes8 + ti * kTile + tj] = codes[t];
+        if ((ti & 3) == 0 && (tj & 3) == 0) tile_scale[s * 16 + (ti >> 2) * 4 + (tj >> 2)] = scales[p];
+    }
+}
+
+// Per block: scale = max|w| / 448 (1 for an all-zero block), code = the E4M3
+// value nearest w / scale (round to nearest even, saturating).
+template <typename U>
+__global__ void quantize_e4m3_kernel(const U *__restrict__ src, int64_t nnzb, int b,
+                                     uint8_t *__restrict__ codes, float *__restrict__ scales) {
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= nnzb) return;
+    const int bb = b * b;
+    const U *v = src + wid * bb;
+    float amax = 0.f;
+    for (int e = lane; e < bb; e += 32) amax = fmaxf(amax, fabsf((float)v[e]));
+    for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const float scale = amax > 0.f ? amax / 448.f : 1.f;
+    if (lane == 0) scales[wid] = scale;
+    for (int e = lane; e < bb; e += 32)
+        codes[wid * bb + e] =
+            (uint8_t)__nv_cvt_float_to_fp8((float)v[e] / scale, __NV_SATFINITE, __NV_E4M3);
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
@@ -544,104 +723,225 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <typename T>
-cudaError_t tc_launch(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
-                      int64_t ldy, const int32_t *n_items_dev, int64_t n_items_cap,
-                      cudaStream_t s) {
+// X tensor map of one problem.  n a multiple of 64: X seen as (64 columns,
+// k rows, n/64 column blocks) so one 64 x 16 x 2 box is a whole 16 x 128 slab
+// (two 128-byte-swizzled halves, 2048 B apart); otherwise two 2-D 64 x 16
+// boxes per slab, whose out-of-range columns the TMA unit fills with zeros.
+cudaError_t encode_x(CUtensorMap *map, int *x3d, bool bf16, const void *X, int64_t k, int64_t n,
+                     int64_t ldx) {
     auto enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
-    // the accumulators of a group must fit the TMEM this kernel allocates
-    if (p->R > kRowCap) return cudaErrorInvalidConfiguration;
     if (((uintptr_t)X & 15) || (ldx * 2) % 16) return cudaErrorMisalignedAddress;
-    CUtensorMap map;
-    const auto dt = Cvt<T>::fmt ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    // n a multiple of 64: X seen as (64 columns, k rows, n/64 column blocks) so
-    // one 64 x 16 x 2 box is a whole 16 x 128 slab (two 128-byte-swizzled
-    // halves, 2048 B apart); otherwise two 2-D 64 x 16 boxes per slab, whose
-    // out-of-range columns the TMA unit fills with zeros.
-    const int x3d = (n % (kNTile / 2)) == 0 ? 1 : 0;
+    const auto dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    *x3d = (n % (kNTile / 2)) == 0 ? 1 : 0;
     CUresult r;
-    if (x3d) {
-        const cuuint64_t dims[3] = {(cuuint64_t)(kNTile / 2), (cuuint64_t)p->k,
+    if (*x3d) {
+        const cuuint64_t dims[3] = {(cuuint64_t)(kNTile / 2), (cuuint64_t)k,
                                     (cuuint64_t)(n / (kNTile / 2))};
         const cuuint64_t strides[2] = {(cuuint64_t)(ldx * 2), (cuuint64_t)kNTile};
         const cuuint32_t box[3] = {kNTile / 2, kTile, 2};
         const cuuint32_t estr[3] = {1, 1, 1};
-        r = enc(&map, dt, 3, const_cast<void *>(X), dims, strides, box, estr,
+        r = enc(map, dt, 3, const_cast<void *>(X), dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
-        const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)p->k};
+        const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)k};
         const cuuint64_t strides[1] = {(cuuint64_t)(ldx * 2)};
         const cuuint32_t box[2] = {kNTile / 2, kTile};
         const cuuint32_t estr[2] = {1, 1};
-        r = enc(&map, dt, 2, const_cast<void *>(X), dims, strides, box, estr,
+        r = enc(map, dt, 2, const_cast<void *>(X), dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    TcArgs a;
-    a.items = p->d_items;
-    a.n_items_dev = n_items_dev;
-    a.n_items = n_items_cap;
-    a.grp_row0 = p->d_grp_row0;
-    a.grp_rows = p->d_grp_rows;
-    a.ent_col = p->d_ent_col;
-    a.ent_tbeg = p->d_ent_tbeg;
-    a.ent_cover = p->d_ent_cover;
-    a.packed = (const uint8_t *)p->d_packed;
-    a.Y = Y;
-    a.ldy = ldy;
-    a.n = n;
-    a.ws = p->d_ws;
-    a.ws_row0 = p->d_ws_row0;
-    a.status = p->d_status;
-    a.ntn = (int)((n + kNTile - 1) / kNTile);
-    a.x3d = x3d;
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
-    const int64_t units = n_items_cap * a.ntn;
-    if (units == 0) return cudaSuccess;
-    const int64_t slots = (int64_t)p->sm_count * kCtasPerSm;
-    const int grid = (int)(units < slots ? units : slots);
-    const size_t smem = 1024 + (size_t)kStages * kStageBytes + sizeof(Smem);
-    static bool attr_set[2] = {false, false};
-    if (!attr_set[Cvt<T>::fmt]) {
-        cudaError_t e = cudaFuncSetAttribute(tc_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, int x3d) {
+    P.items = p->d_items;
+    P.grp_row0 = p->d_grp_row0;
+    P.grp_rows = p->d_grp_rows;
+    P.ent_col = p->d_ent_col;
+    P.ent_tbeg = p->d_ent_tbeg;
+    P.ent_cover = p->d_ent_cover;
+    P.packed = (const uint8_t *)p->d_packed;
+    P.tile_scale = p->d_tile_scale;
+    P.Y = Y;
+    P.ws = p->d_ws;
+    P.ws_row0 = p->d_ws_row0;
+    P.ldy = ldy;
+    P.n = n;
+    P.ntn = (int)((n + kNTile - 1) / kNTile);
+    P.x3d = x3d;
+}
+
+template <typename T, bool W8>
+cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
+    if (B.total_units == 0) return cudaSuccess;
+    const int64_t slots = (int64_t)sm_count * kCtasPerSm;
+    const int grid = (int)(B.total_units < slots ? B.total_units : slots);
+    const size_t smem = 1024 + (size_t)kStages * StageGeom<W8>::bytes + sizeof(Smem);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(tc_kernel<T, W8>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr_set[Cvt<T>::fmt] = true;
+        attr_set = true;
     }
-    tc_kernel<T><<<grid, kThreads, smem, s>>>(map, a);
+    tc_kernel<T, W8><<<grid, kThreads, smem, s>>>(B);
     return cudaGetLastError();
 }
+
+cudaError_t dispatch_batch(const TcBatch &B, bool bf16, bool w8, int sm_count, cudaStream_t s) {
+    if (bf16) return w8 ? launch_batch<__nv_bfloat16, true>(B, sm_count, s)
+                        : launch_batch<__nv_bfloat16, false>(B, sm_count, s);
+    return w8 ? launch_batch<__half, true>(B, sm_count, s) : launch_batch<__half, false>(B, sm_count, s);
+}
+
+// Cached launch schedules of batches: (problem, unit) pairs of all problems,
+// costliest first (item cost = tile slots + entries, as the planner defines
+// it), then by problem and unit.  Keyed by the plans and each problem's n.
+struct SchedKey {
+    std::vector<const void *> plans;
+    std::vector<int64_t> n;
+    bool operator<(const SchedKey &o) const {
+        return plans != o.plans ? plans < o.plans : n < o.n;
+    }
+};
+std::mutex g_sched_mu;
+std::map<SchedKey, int32_t *> g_sched;
 
 }  // namespace
 
 cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
                       int64_t ldy, cudaStream_t s) {
+    if (p->R > kRowCap) return cudaErrorInvalidConfiguration;
+    TcBatch B;  // the launch parameter (copied at launch)
+    int x3d = 0;
+    cudaError_t e = encode_x(&B.maps[0], &x3d, p->xdt == SPMM_BF16, X, p->k, n, ldx);
+    if (e != cudaSuccess) return e;
+    fill_prob(B.prob[0], p, Y, n, ldy, x3d);
+    B.prob[0].unit_base = 0;
+    B.nprob = 1;
+    B.units = nullptr;
+    B.status = p->d_status;
     const bool dyn = p->mode == SPMM_DYNAMIC;
-    const int32_t *nd = dyn ? p->d_counts + kCntItems : nullptr;
-    const int64_t cap = dyn ? p->dyn.items_cap : p->n_items;
-    if (p->xdt == SPMM_F16) return tc_launch<__half>(p, X, n, ldx, Y, ldy, nd, cap, s);
-    if (p->xdt == SPMM_BF16) return tc_launch<__nv_bfloat16>(p, X, n, ldx, Y, ldy, nd, cap, s);
-    return cudaErrorInvalidValue;
+    B.n_items_dev = dyn ? p->d_counts + kCntItems : nullptr;
+    B.total_units = (dyn ? p->dyn.items_cap : p->n_items) * B.prob[0].ntn;
+    return dispatch_batch(B, p->xdt == SPMM_BF16, p->wdt == SPMM_E4M3, p->sm_count, s);
+}
+
+cudaError_t launch_tc_batch(int count, spmm_plan *const *plans, const void *const *X,
+                            const int64_t *n, const int64_t *ldx, void *const *Y,
+                            const int64_t *ldy, cudaStream_t s) {
+    if (count <= 0 || count > kMaxBatch) return cudaErrorInvalidValue;
+    TcBatch B;
+    std::lock_guard<std::mutex> lk(g_sched_mu);
+    SchedKey key;
+    int64_t base = 0;
+    for (int i = 0; i < count; ++i) {
+        const spmm_plan *p = plans[i];
+        if (p->R > kRowCap) return cudaErrorInvalidConfiguration;
+        int x3d = 0;
+        const int64_t lx = ldx ? ldx[i] : n[i], ly = ldy ? ldy[i] : n[i];
+        cudaError_t e = encode_x(&B.maps[i], &x3d, p->xdt == SPMM_BF16, X[i], p->k, n[i], lx);
+        if (e != cudaSuccess) return e;
+        fill_prob(B.prob[i], p, Y[i], n[i], ly, x3d);
+        B.prob[i].unit_base = base;
+        base += p->n_items * B.prob[i].ntn;
+        key.plans.push_back(p);
+        key.n.push_back(n[i]);
+    }
+    B.nprob = count;
+    B.total_units = base;
+    B.status = plans[0]->d_status;
+    B.n_items_dev = nullptr;
+    auto it = g_sched.find(key);
+    if (it == g_sched.end()) {
+        // the first launch of a plan set builds its schedule (this allocates:
+        // make it outside any stream capture)
+        struct U { int64_t cost; int32_t p, u; };
+        std::vector<U> us;
+        us.reserve(base);
+        for (int i = 0; i < count; ++i) {
+            const spmm_plan *p = plans[i];
+            const int ntn = B.prob[i].ntn;
+            for (int64_t item = 0; item < p->n_items; ++item) {
+                const int32_t *f = &p->hp.items[item * kItemFields];
+                const int64_t cost = (int64_t)(p->hp.ent_tbeg[f[2]] - p->hp.ent_tbeg[f[1]]) +
+                                     (f[2] - f[1]);
+                for (int t = 0; t < ntn; ++t) us.push_back({cost, i, (int32_t)(item * ntn + t)});
+            }
+        }
+        std::stable_sort(us.begin(), us.end(), [](const U &a, const U &b) {
+            if (a.cost != b.cost) return a.cost > b.cost;
+            if (a.p != b.p) return a.p < b.p;
+            return a.u < b.u;
+        });
+        std::vector<int32_t> flat(2 * us.size());
+        for (size_t j = 0; j < us.size(); ++j) {
+            flat[2 * j] = us[j].p;
+            flat[2 * j + 1] = us[j].u;
+        }
+        int32_t *d = nullptr;
+        if (!flat.empty()) {
+            cudaError_t e = cudaMalloc(&d, flat.size() * sizeof(int32_t));
+            if (e == cudaSuccess)
+                e = cudaMemcpy(d, flat.data(), flat.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return e;
+        }
+        it = g_sched.emplace(key, d).first;
+    }
+    B.units = it->second;
+    const bool bf16 = plans[0]->xdt == SPMM_BF16, w8 = plans[0]->wdt == SPMM_E4M3;
+    return dispatch_batch(B, bf16, w8, plans[0]->sm_count, s);
 }
 
 cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const float *d_scales,
                               const int32_t *d_nnzb, cudaStream_t s) {
-    (void)d_scales;
     if (p->packed_bytes == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(p->d_packed, 0, p->packed_bytes, s);
     if (e != cudaSuccess) return e;
-    if (p->wdt != SPMM_F16 && p->wdt != SPMM_BF16) return cudaErrorNotSupported;
     const int64_t nmax = d_nnzb ? p->nnzb_max : p->nnzb;
     const int64_t total = nmax * p->b * p->b;
     if (total == 0) return cudaSuccess;
     int64_t g = (total + 255) / 256;
     if (g > 8192) g = 8192;
+    if (p->wdt == SPMM_E4M3) {
+        const int64_t slots = p->mode == SPMM_STATIC ? p->n_tiles : p->nnzb_max;
+        e = cudaMemsetAsync(p->d_tile_scale, 0, sizeof(float) * 16 * slots, s);
+        if (e != cudaSuccess) return e;
+        pack_tiles_e4m3_kernel<<<(unsigned)g, 256, 0, s>>>(
+            (const uint8_t *)d_values, d_scales, p->d_blk_slot, p->d_blk_off, nmax, p->b, d_nnzb,
+            (uint8_t *)p->d_packed, p->d_tile_scale);
+        return cudaGetLastError();
+    }
+    if (p->wdt != SPMM_F16 && p->wdt != SPMM_BF16) return cudaErrorNotSupported;
     pack_tiles_kernel<uint16_t><<<(unsigned)g, 256, 0, s>>>(
         (const uint16_t *)d_values, p->d_blk_slot, p->d_blk_off, nmax, p->b, d_nnzb,
         (uint16_t *)p->d_packed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_e4m3(int64_t nnzb, int b, spmm_dtype src, const void *d_src,
+                                 uint8_t *d_codes, float *d_scales, cudaStream_t s) {
+    if (nnzb == 0) return cudaSuccess;
+    const int64_t threads = nnzb * 32;
+    const unsigned grid = (unsigned)((threads + 255) / 256);
+    switch (src) {
+        case SPMM_F32:
+            quantize_e4m3_kernel<float><<<grid, 256, 0, s>>>((const float *)d_src, nnzb, b, d_codes,
+                                                             d_scales);
+            break;
+        case SPMM_F16:
+            quantize_e4m3_kernel<__half><<<grid, 256, 0, s>>>((const __half *)d_src, nnzb, b, d_codes,
+                                                              d_scales);
+            break;
+        case SPMM_BF16:
+            quantize_e4m3_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)d_src,
+                                                                     nnzb, b, d_codes, d_scales);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -35,7 +35,7 @@ ARRAYS = {"row_ptr": 0, "col_idx": 1, "perm": 2, "items": 3, "grp_row0": 4, "grp
 EXPORTS = ["spmm_plan_create", "spmm_pack_values", "spmm_run", "spmm_run_host",
            "spmm_get_status", "spmm_plan_get_info", "spmm_plan_get_array",
            "spmm_plan_destroy", "spmm_equal_partition", "spmm_bucket_size", "spmm_batch_run",
-           "spmm_last_error", "spmm_version", "spmm_gather_noalloc"]
+           "spmm_last_error", "spmm_version", "spmm_gather_noalloc", "spmm_quantize_e4m3"]
 
 
 class SpmmError(RuntimeError):
@@ -96,6 +96,7 @@ def lib():
                                      ctypes.POINTER(i64), vp]
         L.spmm_gather_noalloc.argtypes = [i64, i64, i32, vp, vp, vp, i64, vp, vp, i64, i64, vp,
                                           i64, vp, vp]
+        L.spmm_quantize_e4m3.argtypes = [i64, i32, i32, vp, vp, vp, vp]
         L.spmm_last_error.restype = ctypes.c_char_p
         L.spmm_version.restype = ctypes.c_char_p
         for name in EXPORTS:
@@ -176,6 +177,22 @@ def spmm_gather_noalloc(m, k, dtype, d_nnzb, d_brow, d_bcol, nnzb_max, d_values,
     """The allocation-free dynamic b = 1 product (see include/spmm.h)."""
     return _check(lib().spmm_gather_noalloc(m, k, dtype, d_nnzb, d_brow, d_bcol, nnzb_max,
                                             d_values, d_X, n, ldx, d_Y, ldy, d_status, stream))
+
+
+def spmm_quantize_e4m3(nnzb, b, src_dtype, d_src, d_codes, d_scales, stream):
+    return _check(lib().spmm_quantize_e4m3(nnzb, b, src_dtype, d_src, d_codes, d_scales, stream))
+
+
+def quantize_e4m3(values, stream=None):
+    """E4M3 codes (torch.float8_e4m3fn) and FP32 per-block scales of device
+    values shaped (nnzb, b, b), by the library's quantiser kernel."""
+    import torch
+    nnzb, b = values.shape[0], values.shape[1]
+    codes = torch.empty(values.shape, dtype=torch.uint8, device=values.device)
+    scales = torch.empty(nnzb, dtype=torch.float32, device=values.device)
+    spmm_quantize_e4m3(nnzb, b, dtype_code(values.dtype), _ptr(values), _ptr(codes), _ptr(scales),
+                       _stream_handle(stream))
+    return codes.view(torch.float8_e4m3fn), scales
 
 
 def spmm_version():

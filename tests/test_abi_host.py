@@ -21,7 +21,7 @@ def native():
 def test_exports_match_header():
     import os
     hdr = open(os.path.join(os.path.dirname(S.HERE), "include", "spmm.h")).read()
-    declared = set(re.findall(r"\b(spmm_[a-z_]+)\s*\(", hdr))
+    declared = set(re.findall(r"\b(spmm_[a-z_0-9]+)\s*\(", hdr))
     declared = {d for d in declared if not d.endswith("_t")}
     assert declared == set(S.EXPORTS), declared ^ set(S.EXPORTS)
     L = S.lib()
