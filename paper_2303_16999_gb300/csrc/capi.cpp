@@ -765,7 +765,7 @@ spmm_status spmm_batch_run(int32_t count, spmm_plan *const *plans, const void *c
                 return SPMM_ERR_ARG;
             }
     }
-    cudaError_t e = launch_tc_batch(count, plans, d_X, n, ldx, d_Y, ldy, s);
+    cudaError_t e = launch_tc_batch(count, plans, d_X, n, ldx, d_Y, ldy, s, true);
     if (e != cudaSuccess) return cuda_fail(e, "batched launch");
     for (int i = 0; i < count; ++i) {
         spmm_plan *p = plans[i];

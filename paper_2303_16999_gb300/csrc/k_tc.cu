@@ -832,7 +832,7 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
 
 cudaError_t launch_tc_batch(int count, spmm_plan *const *plans, const void *const *X,
                             const int64_t *n, const int64_t *ldx, void *const *Y,
-                            const int64_t *ldy, cudaStream_t s) {
+                            const int64_t *ldy, cudaStream_t s, bool schedule) {
     if (count <= 0 || count > kMaxBatch) return cudaErrorInvalidValue;
     TcBatch B;
     std::lock_guard<std::mutex> lk(g_sched_mu);
@@ -855,6 +855,12 @@ cudaError_t launch_tc_batch(int count, spmm_plan *const *plans, const void *cons
     B.total_units = base;
     B.status = plans[0]->d_status;
     B.n_items_dev = nullptr;
+    B.units = nullptr;
+    if (!schedule) {
+        // problems in submission order (serving: every launch is a new mix)
+        const bool bf16 = plans[0]->xdt == SPMM_BF16, w8 = plans[0]->wdt == SPMM_E4M3;
+        return dispatch_batch(B, bf16, w8, plans[0]->sm_count, s);
+    }
     auto it = g_sched.find(key);
     if (it == g_sched.end()) {
         // the first launch of a plan set builds its schedule (this allocates:

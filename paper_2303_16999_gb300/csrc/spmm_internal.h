@@ -132,7 +132,7 @@ cudaError_t launch_tc(const spmm_plan *p, const void *d_X, int64_t n, int64_t ld
 cudaError_t launch_reduce(const spmm_plan *p, int64_t n, void *d_Y, int64_t ldy, cudaStream_t s);
 cudaError_t launch_tc_batch(int count, spmm_plan *const *plans, const void *const *X,
                             const int64_t *n, const int64_t *ldx, void *const *Y,
-                            const int64_t *ldy, cudaStream_t s);
+                            const int64_t *ldy, cudaStream_t s, bool schedule);
 cudaError_t launch_quantize_e4m3(int64_t nnzb, int b, spmm_dtype src, const void *d_src,
                                  uint8_t *d_codes, float *d_scales, cudaStream_t s);
 constexpr int kMaxBatchProblems = 64;

@@ -31,6 +31,10 @@ ARRAYS = {"row_ptr": 0, "col_idx": 1, "perm": 2, "items": 3, "grp_row0": 4, "grp
           "grp_ebeg": 6, "ent_col": 7, "ent_tbeg": 8, "tile_row": 9, "blk_slot": 10,
           "blk_off": 11, "ws_row0": 12, "red": 13, "ent_cover": 14}
 
+# exported symbols of include/spmm_serve.h
+SERVE_EXPORTS = ["serve_create", "serve_register_weight", "serve_submit", "serve_wait",
+                 "serve_stats", "serve_reset_stats", "serve_destroy"]
+
 # exported symbols of include/spmm.h (checked by the CPU test-suite)
 EXPORTS = ["spmm_plan_create", "spmm_pack_values", "spmm_run", "spmm_run_host",
            "spmm_get_status", "spmm_plan_get_info", "spmm_plan_get_array",
@@ -66,6 +70,20 @@ class PlanInfo(ctypes.Structure):
                                       "ws_rows", "n_reductions", "device_bytes")]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_inflight", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("max_batch_n", ctypes.c_int64),
+                ("inject_delay_us", ctypes.c_int32), ("inject_alloc_fail", ctypes.c_int32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "rejected",
+                                              "failed", "queued", "in_flight", "launches")] + \
+        [(n, ctypes.c_double) for n in ("mean_requests_per_launch", "mean_cols_per_launch",
+                                        "p50_us", "p99_us", "mean_us", "max_us", "span_s",
+                                        "throughput_rps", "tflops_nz")]
+
+
 _lib = None
 
 
@@ -99,7 +117,15 @@ def lib():
         L.spmm_quantize_e4m3.argtypes = [i64, i32, i32, vp, vp, vp, vp]
         L.spmm_last_error.restype = ctypes.c_char_p
         L.spmm_version.restype = ctypes.c_char_p
-        for name in EXPORTS:
+        L.serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
+        L.serve_register_weight.argtypes = [vp, vp, ctypes.POINTER(i32)]
+        L.serve_submit.argtypes = [vp, i32, vp, i64, vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.serve_wait.argtypes = [vp, ctypes.c_uint64, i64]
+        L.serve_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
+        L.serve_reset_stats.argtypes = [vp]
+        L.serve_destroy.argtypes = [vp]
+        L.serve_destroy.restype = None
+        for name in EXPORTS + SERVE_EXPORTS:
             getattr(L, name)
         _lib = L
     return _lib
@@ -297,3 +323,61 @@ def spmm_batch_run(plans, Xs, Ys, stream=None):
     lx = (i64 * count)(*[x.stride(0) for x in Xs])
     ly = (i64 * count)(*[y.stride(0) for y in Ys])
     return _check(lib().spmm_batch_run(count, hp, xp, ns, lx, yp, ly, _stream_handle(stream)))
+
+
+# ------------------------------------------------------------------ serving
+class Server:
+    """Serving loop of include/spmm_serve.h: resident weights, HBM-budget
+    admission, continuous batching on ``max_inflight`` streams.  Requests
+    pass host (CPU, preferably pinned) tensors X (k x n) and Y (m x n)."""
+
+    def __init__(self, hbm_budget_bytes, max_inflight=2, max_batch=64, max_batch_n=4096,
+                 inject_delay_us=0, inject_alloc_fail=0):
+        cfg = ServeConfig(hbm_budget_bytes, max_inflight, max_batch, max_batch_n,
+                          inject_delay_us, inject_alloc_fail)
+        h = ctypes.c_void_p()
+        _check(lib().serve_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        self._plans = []
+        self._live = {}
+
+    def register(self, plan):
+        w = ctypes.c_int32()
+        _check(lib().serve_register_weight(self.h, plan.h, ctypes.byref(w)))
+        self._plans.append(plan)
+        return w.value
+
+    def submit(self, weight_id, X, Y):
+        t = ctypes.c_uint64()
+        _check(lib().serve_submit(self.h, weight_id, ctypes.c_void_p(X.data_ptr()), X.shape[1],
+                                  ctypes.c_void_p(Y.data_ptr()), ctypes.byref(t)))
+        self._live[t.value] = (X, Y)        # keep the buffers alive until wait
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        st = lib().serve_wait(self.h, ticket, timeout_ms)
+        if st != TIMEOUT_STATUS:
+            self._live.pop(ticket, None)
+        return _check(st)
+
+    def stats(self):
+        s = ServeStats()
+        _check(lib().serve_stats(self.h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServeStats._fields_}
+
+    def reset_stats(self):
+        _check(lib().serve_reset_stats(self.h))
+
+    def close(self):
+        if self.h:
+            lib().serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+TIMEOUT_STATUS = ERR_TIMEOUT

@@ -28,6 +28,11 @@ def test_exports_match_header():
     for name in declared:
         assert hasattr(L, name)
     assert "sm_103a" in S.spmm_version()
+    shdr = open(os.path.join(os.path.dirname(S.HERE), "include", "spmm_serve.h")).read()
+    sdecl = set(re.findall(r"\b(serve_[a-z_0-9]+)\s*\(", shdr))
+    assert sdecl == set(S.SERVE_EXPORTS), sdecl ^ set(S.SERVE_EXPORTS)
+    for name in sdecl:
+        assert hasattr(L, name)
 
 
 def test_appendix_formulas_match_oracle():
