@@ -275,6 +275,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--no-dynamic", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--point", default=None,
                     help="run one sweep point only, 'b:1/d' e.g. 16:4 (profiling)")
@@ -400,9 +402,13 @@ def main():
             q["b"] == 16 and abs(q["d"] - 1 / 16) < 1e-12 for q in pts):
         comparators = run_comparators(torch, S, wl, dev, pts)
 
-    dynamic = None
+    dynamic = batched = serving = None
     if rank == 0 and not args.no_dynamic and args.point is None:
         dynamic = run_dynamic(torch, S, wl, dev)
+    if rank == 0 and not args.no_batched and args.point is None:
+        batched = run_batched(torch, S, wl, dev)
+    if rank == 0 and not args.no_serving and args.point is None:
+        serving = run_serving(torch, S, wl, dev)
 
     launches = sum(launches_per_run(p) for p in pts) * args.steps
     if rank == 0:
@@ -413,7 +419,8 @@ def main():
                 "data": "synthetic", "config": workload_config(),
                 "e2e": e2e, "gpu_launches": launches, "clocks": sampler.summary(),
                 "roofline": roofline, "cpu_baseline": cpu, "points": points,
-                "comparators": comparators, "dynamic": dynamic}
+                "comparators": comparators, "dynamic": dynamic, "batched": batched,
+                "serving": serving}
         print(json.dumps(line))
     for p in pts:
         p["plan"].close()
@@ -506,6 +513,133 @@ def run_dynamic(torch, S, wl, dev, calls=4, reps=10):
            "gpu_launches_per_call": None}
     dplan.close()
     splan.close()
+    return out
+
+
+def run_batched(torch, S, wl, dev, reps=5):
+    """48 uneven FFN-like products (W 4096 x 16384 / 16384 x 4096, b in {8, 16},
+    d in {1/16, 1/8}, n log-uniform in [1, 512]) with E4M3 weights (one FP32
+    scale per block) and BF16 X, in one persistent launch (CUDA graph),
+    against the same 48 plans launched one after another and against the
+    plain FP32 kernel run on FP32 copies, problem by problem."""
+    bf = torch.bfloat16
+    plans, p32, Xs, Ys, X32, Y32 = [], [], [], [], [], []
+    flops = 0.0
+    for i in range(48):
+        c = wl.batched_case(i)
+        v = torch.from_numpy(c["vals"]).to(dev)
+        codes, scales = S.quantize_e4m3(v.to(bf))
+        p = S.Plan(c["m"], c["k"], c["n"], c["b"], w_dtype=S.E4M3, x_dtype=S.BF16,
+                   brow=c["brow"], bcol=c["bcol"])
+        p.pack(codes.view(torch.uint8), scales)
+        n = c["n"]
+        ld = (n + 7) // 8 * 8
+        xb = torch.zeros((c["k"], ld), dtype=bf, device=dev)
+        xb[:, :n] = torch.from_numpy(c["X"]).to(bf).to(dev)
+        plans.append(p)
+        Xs.append(xb[:, :n])
+        Ys.append(torch.empty((c["m"], n), dtype=bf, device=dev))
+        q = S.Plan(c["m"], c["k"], n, c["b"], w_dtype=S.F32, brow=c["brow"], bcol=c["bcol"],
+                   kernel="plain")
+        q.pack(v)
+        p32.append(q)
+        X32.append(xb[:, :n].float().contiguous())
+        Y32.append(torch.empty((c["m"], n), dtype=torch.float32, device=dev))
+        flops += 2.0 * len(c["brow"]) * c["b"] ** 2 * n
+        del v, codes, scales
+    S.spmm_batch_run(plans, Xs, Ys)          # builds the cached schedule outside capture
+    torch.cuda.synchronize()
+    t_batch = graph_time_us(torch, lambda: S.spmm_batch_run(plans, Xs, Ys), reps)
+
+    def seq():
+        for p, x, y in zip(plans, Xs, Ys):
+            p.run(x, y)
+    t_seq = graph_time_us(torch, seq, reps)
+
+    def seq32():
+        for p, x, y in zip(p32, X32, Y32):
+            p.run(x, y)
+    t_32 = graph_time_us(torch, seq32, 2)
+    w_bytes = sum(p.info()["n_tiles"] * 256 + p.info()["n_tiles"] * 64 for p in plans)
+    out = {"workload": "batched: 48 FFN-like products, E4M3 W + FP32 block scales, BF16 X",
+           "us": round(t_batch, 1), "tflops_nz": round(flops / t_batch / 1e6, 2),
+           "sequential_same_plans_us": round(t_seq, 1),
+           "plain_fp32_sequential_us": round(t_32, 1),
+           "speedup_vs_plain_fp32": round(t_32 / t_batch, 2),
+           "speedup_vs_sequential": round(t_seq / t_batch, 3),
+           "packed_weight_gb": round(w_bytes / 1e9, 3), "gpu_launches": 1}
+    for p in plans + p32:
+        p.close()
+    return out
+
+
+def run_serving(torch, S, wl, dev, per_rate=1500, rates=(0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.2)):
+    """12 resident weights (m = k in {2048, 4096, 8192} x b in {8, 16} x 2
+    seeds, d = 1/16, FP16); Poisson requests, n log-uniform in [1, 256],
+    aimed uniformly at the weights.  Saturation throughput is measured with a
+    closed burst, then each rate runs ``per_rate`` requests; the plain FP32
+    kernel (one request per launch) serves the same streams as the baseline."""
+    ws = wl.serve_weights()
+
+    def make_server(fp32):
+        srv = S.Server(hbm_budget_bytes=2 << 30, max_inflight=4, max_batch=64, max_batch_n=4096)
+        plans, ids, xpool, ypool = [], [], [], []
+        for w in ws:
+            m, b = w["m"], w["b"]
+            v = torch.from_numpy(w["vals"])
+            if fp32:
+                p = S.Plan(m, m, 256, b, w_dtype=S.F32, brow=w["brow"], bcol=w["bcol"],
+                           kernel="plain")
+                p.pack(v.to(dev))
+                dt = torch.float32
+            else:
+                p = S.Plan(m, m, 256, b, w_dtype=S.F16, brow=w["brow"], bcol=w["bcol"])
+                p.pack(v.half().to(dev))
+                dt = torch.float16
+            plans.append(p)
+            ids.append(srv.register(p))
+            xpool.append(torch.from_numpy(wl.request_x(w["seed"], m, 256)).to(dt).pin_memory())
+            ypool.append(torch.empty((m, 256), dtype=dt).pin_memory())
+        return srv, plans, ids, xpool, ypool
+
+    def flat(t, rows, n):
+        return t.view(-1)[:rows * n].view(rows, n)
+
+    def run_stream(srv, ids, xpool, ypool, t_arr, wsel, ns):
+        srv.reset_stats()
+        tickets = []
+        t0 = time.perf_counter()
+        for t, w, n in zip(t_arr, wsel, ns):
+            while time.perf_counter() - t0 < t:
+                pass
+            m = ws[w]["m"]
+            tickets.append(srv.submit(ids[w], flat(xpool[w], m, int(n)), flat(ypool[w], m, int(n))))
+        for tk in tickets:
+            srv.wait(tk)
+        return srv.stats()
+
+    out = {"workload": "serving: 12 resident weights m=k in {2048,4096,8192}, b in {8,16}, "
+                       "d=1/16, FP16; Poisson requests n log-uniform [1,256]"}
+    for name, fp32 in (("tc_fp16", False), ("plain_fp32", True)):
+        srv, plans, ids, xpool, ypool = make_server(fp32)
+        # saturation: a closed burst of requests submitted at once
+        tb, wb, nb = wl.serve_requests(per_rate, 1e9, len(ws), 4090)
+        sat = run_stream(srv, ids, xpool, ypool, tb * 0, wb, nb)
+        lam = sat["throughput_rps"]
+        rows = []
+        for ri, f in enumerate(rates):
+            t_arr, wsel, ns = wl.serve_requests(per_rate, max(lam * f, 1.0), len(ws), 4000 + ri)
+            st = run_stream(srv, ids, xpool, ypool, t_arr, wsel, ns)
+            rows.append({"rate_x_sat": f, "offered_rps": round(lam * f, 1),
+                         "p50_us": round(st["p50_us"], 1), "p99_us": round(st["p99_us"], 1),
+                         "throughput_rps": round(st["throughput_rps"], 1),
+                         "tflops_nz": round(st["tflops_nz"], 3),
+                         "mean_requests_per_launch": round(st["mean_requests_per_launch"], 2)})
+        out[name] = {"saturation_rps": round(lam, 1), "saturation_tflops_nz": round(sat["tflops_nz"], 3),
+                     "rates": rows}
+        srv.close()
+        for p in plans:
+            p.close()
     return out
 
 
