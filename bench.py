@@ -148,9 +148,11 @@ def max_over_ranks(x, world):
 
 
 # ---------------------------------------------------------- sweep points
-def roof_of(b, nnzb, peaks):
-    """Roofline of one product: nonzero FLOPs, compulsory bytes and the
-    bound (the slower of compute-at-peak and bytes-over-HBM)."""
+def roof_of(b, nnzb, peaks, kernel):
+    """Roofline of one product on the kernel that runs it: nonzero FLOPs,
+    compulsory bytes and the bound (the slower of compute-at-peak -- tensor
+    cores for the TC kernel, FP32 lanes for the CUDA-core kernels -- and
+    bytes-over-HBM)."""
     flops = 2.0 * nnzb * b * b * N
     es = 2
     vals = nnzb * b * b * es
@@ -158,7 +160,7 @@ def roof_of(b, nnzb, peaks):
     xy = (K * N + M * N) * es
     bytes_ = vals + idx + xy
     t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
-    if b == 1:
+    if kernel != "tc":
         t_cmp, unit = flops / (ALU_PEAK_TFLOPS * 1e12), "alu"
     else:
         t_cmp, unit = flops / (peaks["bf16_tflops"] * 1e12), "tensor"
@@ -355,9 +357,9 @@ def main():
 
     points, fam = [], {}
     for i, p in enumerate(pts):
-        fl, by, bound, t_roof = roof_of(p["b"], p["nnzb"], peaks)
-        us = per[i] * 1e3
         kern = {1: "plain", 2: "gather", 3: "tc"}[p["kernel"]]
+        fl, by, bound, t_roof = roof_of(p["b"], p["nnzb"], peaks, kern)
+        us = per[i] * 1e3
         points.append({"b": p["b"], "d": "1/%d" % round(1 / p["d"]), "kernel": kern,
                        "us": round(us, 2),
                        "tflops_nz": round(fl / (us * 1e-6) / 1e12, 2),
@@ -402,7 +404,9 @@ def main():
             q["b"] == 16 and abs(q["d"] - 1 / 16) < 1e-12 for q in pts):
         comparators = run_comparators(torch, S, wl, dev, pts)
 
-    dynamic = batched = serving = None
+    dynamic = batched = serving = gsmall = None
+    if rank == 0 and args.point is None:
+        gsmall = run_gather_small_n(torch, S, wl, dev, peaks)
     if rank == 0 and not args.no_dynamic and args.point is None:
         dynamic = run_dynamic(torch, S, wl, dev)
     if rank == 0 and not args.no_batched and args.point is None:
@@ -420,7 +424,7 @@ def main():
                 "e2e": e2e, "gpu_launches": launches, "clocks": sampler.summary(),
                 "roofline": roofline, "cpu_baseline": cpu, "points": points,
                 "comparators": comparators, "dynamic": dynamic, "batched": batched,
-                "serving": serving}
+                "serving": serving, "gather_small_n": gsmall}
         print(json.dumps(line))
     for p in pts:
         p["plan"].close()
@@ -573,7 +577,7 @@ def run_batched(torch, S, wl, dev, reps=5):
     return out
 
 
-def run_serving(torch, S, wl, dev, per_rate=1500, rates=(0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.2)):
+def run_serving(torch, S, wl, dev, per_rate=4000, rates=(0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.2)):
     """12 resident weights (m = k in {2048, 4096, 8192} x b in {8, 16} x 2
     seeds, d = 1/16, FP16); Poisson requests, n log-uniform in [1, 256],
     aimed uniformly at the weights.  Saturation throughput is measured with a
@@ -606,17 +610,11 @@ def run_serving(torch, S, wl, dev, per_rate=1500, rates=(0.1, 0.25, 0.5, 0.75, 0
         return t.view(-1)[:rows * n].view(rows, n)
 
     def run_stream(srv, ids, xpool, ypool, t_arr, wsel, ns):
-        srv.reset_stats()
-        tickets = []
-        t0 = time.perf_counter()
-        for t, w, n in zip(t_arr, wsel, ns):
-            while time.perf_counter() - t0 < t:
-                pass
-            m = ws[w]["m"]
-            tickets.append(srv.submit(ids[w], flat(xpool[w], m, int(n)), flat(ypool[w], m, int(n))))
-        for tk in tickets:
-            srv.wait(tk)
-        return srv.stats()
+        # native trace replay: submission times are kept by the library, not
+        # by this interpreter; request contents do not matter for timing, so
+        # every request of a weight reads one pinned X and writes one pinned Y
+        return srv.replay(t_arr, [ids[w] for w in wsel], ns,
+                          [xpool[w].data_ptr() for w in wsel], [ypool[w].data_ptr() for w in wsel])
 
     out = {"workload": "serving: 12 resident weights m=k in {2048,4096,8192}, b in {8,16}, "
                        "d=1/16, FP16; Poisson requests n log-uniform [1,256]"}
@@ -641,6 +639,29 @@ def run_serving(torch, S, wl, dev, per_rate=1500, rates=(0.1, 0.25, 0.5, 0.75, 0
         for p in plans:
             p.close()
     return out
+
+
+def run_gather_small_n(torch, S, wl, dev, peaks, reps=20):
+    """The b = 1 gather kernel (CUDA cores) at small n, where it is bound by
+    HBM: m = k = 4096, d = 1/16, FP16; compulsory bytes (values, indices,
+    row pointers, X once, Y once) over the measured time, against the
+    measured HBM copy bandwidth."""
+    c = wl.sweep_case(1, 1 / 16, n=32)
+    plan = S.Plan(M, K, 32, 1, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"], kernel="gather")
+    plan.pack(torch.from_numpy(c["vals"]).half().to(dev))
+    out = []
+    for n in (1, 4, 16, 32):
+        X = torch.from_numpy(c["X"][:, :n].copy()).half().to(dev)
+        Y = torch.empty((M, n), dtype=torch.float16, device=dev)
+        us = graph_time_us(torch, lambda: plan.run(X, Y), reps)
+        nnzb = len(c["brow"])
+        by = nnzb * 2 + nnzb * 4 + (M + 1) * 4 + (K + M) * n * 2
+        gbs = by / us / 1e3
+        out.append({"n": n, "us": round(us, 2), "gbs": round(gbs, 1),
+                    "frac_of_hbm": round(gbs / peaks["hbm_gbs"], 3),
+                    "tflops_nz": round(2.0 * nnzb * n / us / 1e6, 3)})
+    plan.close()
+    return {"workload": "b=1 gather kernel, m=k=4096, d=1/16, FP16, small n", "points": out}
 
 
 def run_comparators(torch, S, wl, dev, pts):

@@ -78,6 +78,15 @@ spmm_status serve_wait(serve_server *srv, uint64_t ticket, int64_t timeout_ms);
 spmm_status serve_stats(serve_server *srv, serve_stats_t *out);
 spmm_status serve_reset_stats(serve_server *srv);
 
+/* Trace replay, for load tests without a client in the loop: resets the
+ * statistics, submits request i at t_arrive_s[i] seconds after the call
+ * starts (busy-waiting on the calling thread; times ascending), aimed at
+ * weight[i] with n[i] columns and host buffers h_X[i] / h_Y[i], waits for
+ * all of them and writes the statistics to *out.  Returns the first error. */
+spmm_status serve_replay(serve_server *srv, int64_t count, const double *t_arrive_s,
+                         const int32_t *weight, const int64_t *n, const void *const *h_X,
+                         void *const *h_Y, serve_stats_t *out);
+
 /* Drains in-flight work, stops the threads and frees the staging pool. */
 void serve_destroy(serve_server *srv);
 

@@ -93,10 +93,6 @@ static spmm_status check_types(int kernel, int b, spmm_dtype w, spmm_dtype x, in
             set_error("GATHER kernel needs W and X of one type in {F32, F16, BF16}");
             return SPMM_ERR_UNSUPPORTED;
         case SPMM_KERNEL_TC:
-            if (b == 1) {
-                set_error("TC kernel needs b in {4, 8, 16}");
-                return SPMM_ERR_UNSUPPORTED;
-            }
             if (m % kTile || k % kTile) {
                 set_error("TC kernel needs m and k multiples of 16");
                 return SPMM_ERR_UNSUPPORTED;
@@ -108,6 +104,26 @@ static spmm_status check_types(int kernel, int b, spmm_dtype w, spmm_dtype x, in
             set_error("unknown kernel %d", kernel);
             return SPMM_ERR_ARG;
     }
+}
+
+// b = 1 and 16-bit X: the tensor-core kernel (element blocks packed into 16 x
+// 16 tiles) wins once n fills its 128-column MMA tiles and the tiles are not
+// nearly empty; otherwise the CUDA-core gather kernel.
+static bool b1_prefers_tc(int64_t m, int64_t k, int64_t n_max, spmm_dtype w, spmm_dtype x,
+                          const spmm_pattern *pat) {
+    if (!pat || pat->nnzb <= 0 || !pat->brow || !pat->bcol || n_max < kNTile || m % kTile ||
+        k % kTile)
+        return false;
+    if (!((x == SPMM_F16 || x == SPMM_BF16) && w == x)) return false;
+    const int64_t kt = k / kTile;
+    std::vector<int64_t> t(pat->nnzb);
+    for (int64_t p = 0; p < pat->nnzb; ++p) {
+        if (pat->brow[p] < 0 || pat->bcol[p] < 0) return false;  // validated later
+        t[p] = (int64_t)(pat->brow[p] / kTile) * kt + pat->bcol[p] / kTile;
+    }
+    std::sort(t.begin(), t.end());
+    const int64_t tiles = std::unique(t.begin(), t.end()) - t.begin();
+    return pat->nnzb >= 4 * tiles;
 }
 
 static int default_R(int64_t mt, int64_t n_max, int sms) {
@@ -295,7 +311,10 @@ spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spm
     if (opts) o = *opts;
     spmm_status st = validate_pattern(m, k, b, 0, nullptr, nullptr);
     if (st != SPMM_OK) return st;
-    const int kernel = pick_kernel(o.kernel, b, w_dtype, x_dtype);
+    int kernel = pick_kernel(o.kernel, b, w_dtype, x_dtype);
+    if (o.kernel == SPMM_KERNEL_AUTO && b == 1 && mode == SPMM_STATIC &&
+        b1_prefers_tc(m, k, n_max, w_dtype, x_dtype, pattern))
+        kernel = SPMM_KERNEL_TC;
     st = check_types(kernel, b, w_dtype, x_dtype, m, k);
     if (st != SPMM_OK) return st;
     if (o.rows_per_group < 0 || o.rows_per_group > kMaxGroupRows || o.max_per_item < 0) {

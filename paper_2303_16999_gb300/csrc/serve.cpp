@@ -469,6 +469,39 @@ spmm_status serve_reset_stats(serve_server *s) {
     return SPMM_OK;
 }
 
+spmm_status serve_replay(serve_server *s, int64_t count, const double *t_arr, const int32_t *w,
+                         const int64_t *n, const void *const *hX, void *const *hY,
+                         serve_stats_t *out) {
+    if (!s || count < 0 || (count > 0 && (!t_arr || !w || !n || !hX || !hY)) || !out) {
+        set_error("serve_replay: server, arrays and out required");
+        return SPMM_ERR_ARG;
+    }
+    spmm_status st = serve_reset_stats(s);
+    if (st != SPMM_OK) return st;
+    std::vector<uint64_t> tickets;
+    tickets.reserve(count);
+    spmm_status first = SPMM_OK;
+    const double t0 = now_us();
+    for (int64_t i = 0; i < count; ++i) {
+        const double due = t0 + t_arr[i] * 1e6;
+        while (now_us() < due) {
+        }
+        uint64_t t = 0;
+        st = serve_submit(s, w[i], hX[i], n[i], hY[i], &t);
+        if (st != SPMM_OK) {
+            if (first == SPMM_OK) first = st;
+            continue;
+        }
+        tickets.push_back(t);
+    }
+    for (uint64_t t : tickets) {
+        st = serve_wait(s, t, -1);
+        if (st != SPMM_OK && first == SPMM_OK) first = st;
+    }
+    st = serve_stats(s, out);
+    return first != SPMM_OK ? first : st;
+}
+
 void serve_destroy(serve_server *s) {
     if (!s) return;
     {

@@ -33,7 +33,7 @@ ARRAYS = {"row_ptr": 0, "col_idx": 1, "perm": 2, "items": 3, "grp_row0": 4, "grp
 
 # exported symbols of include/spmm_serve.h
 SERVE_EXPORTS = ["serve_create", "serve_register_weight", "serve_submit", "serve_wait",
-                 "serve_stats", "serve_reset_stats", "serve_destroy"]
+                 "serve_stats", "serve_reset_stats", "serve_destroy", "serve_replay"]
 
 # exported symbols of include/spmm.h (checked by the CPU test-suite)
 EXPORTS = ["spmm_plan_create", "spmm_pack_values", "spmm_run", "spmm_run_host",
@@ -123,6 +123,7 @@ def lib():
         L.serve_wait.argtypes = [vp, ctypes.c_uint64, i64]
         L.serve_stats.argtypes = [vp, ctypes.POINTER(ServeStats)]
         L.serve_reset_stats.argtypes = [vp]
+        L.serve_replay.argtypes = [vp, i64, vp, vp, vp, vp, vp, ctypes.POINTER(ServeStats)]
         L.serve_destroy.argtypes = [vp]
         L.serve_destroy.restype = None
         for name in EXPORTS + SERVE_EXPORTS:
@@ -367,6 +368,20 @@ class Server:
 
     def reset_stats(self):
         _check(lib().serve_reset_stats(self.h))
+
+    def replay(self, t_arrive_s, weight, n, x_ptrs, y_ptrs):
+        """Native trace replay (serve_replay): arrival offsets in seconds,
+        weight ids, column counts and host buffer addresses per request."""
+        cnt = len(t_arrive_s)
+        t = np.ascontiguousarray(t_arrive_s, dtype=np.float64)
+        w = np.ascontiguousarray(weight, dtype=np.int32)
+        nn = np.ascontiguousarray(n, dtype=np.int64)
+        xp = np.ascontiguousarray(x_ptrs, dtype=np.uint64)
+        yp = np.ascontiguousarray(y_ptrs, dtype=np.uint64)
+        s = ServeStats()
+        _check(lib().serve_replay(self.h, cnt, t.ctypes.data, w.ctypes.data, nn.ctypes.data,
+                                  xp.ctypes.data, yp.ctypes.data, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in ServeStats._fields_}
 
     def close(self):
         if self.h:

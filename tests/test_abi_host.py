@@ -144,3 +144,22 @@ def test_tc_plan_worst_case_splits():
     want = P.tc_plan(m, k, b, brow, bcol, info["rows_per_group"], info["max_per_item"])
     assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
     assert info["n_reductions"] == 1 and info["ws_rows"] > 0
+
+
+def test_auto_kernel_choice_for_b1():
+    """b = 1 with 16-bit values: the tensor-core kernel when n_max >= 128 and
+    the tiles hold at least 4 non-zeros on average, else the gather kernel."""
+    rng = np.random.default_rng(0)
+    brow, bcol = _rand(rng, 512, 512, 512 * 512 // 8)        # ~32 per 16 x 16 tile
+    p = _plan(512, 512, 1, brow, bcol, n_max=256)
+    assert p.info()["kernel"] == S.KERNEL_TC
+    p = _plan(512, 512, 1, brow, bcol, n_max=64)
+    assert p.info()["kernel"] == S.KERNEL_GATHER
+    brow, bcol = _rand(rng, 512, 512, 300)                     # about one per tile
+    p = _plan(512, 512, 1, brow, bcol, n_max=256)
+    assert p.info()["kernel"] == S.KERNEL_GATHER
+    p = _plan(512, 512, 1, brow, bcol, n_max=256, kernel="tc")
+    assert p.info()["kernel"] == S.KERNEL_TC
+    want = P.tc_plan(512, 512, 1, brow, bcol, p.info()["rows_per_group"], p.info()["max_per_item"])
+    assert np.array_equal(p.array("ent_cover"), want["ent_cover"])
+    assert np.array_equal(p.array("blk_slot"), want["blk_slot"])

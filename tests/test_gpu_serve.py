@@ -168,3 +168,21 @@ def test_plain_fp32_weight_one_per_launch():
         Yo = oracle.spmm(m, m, b, c["brow"], c["bcol"], vals, X)
         assert oracle.normwise_err(Y, Yo, oracle.block_fro(vals), X) <= 1e-6
     srv.close()
+
+
+def test_native_replay_matches_submissions():
+    ws = _weights()
+    srv = S.Server(hbm_budget_bytes=64 << 20, max_inflight=4)
+    ids = [srv.register(w["plan"]) for w in ws]
+    reqs = _requests(ws, 40, 3)
+    outs = [torch.empty((ws[w]["m"], X.shape[1]), dtype=torch.float16).pin_memory()
+            for w, X in reqs]
+    t_arr = np.linspace(0.0, 0.01, len(reqs))
+    st = srv.replay(t_arr, [ids[w] for w, _ in reqs], [X.shape[1] for _, X in reqs],
+                    [X.data_ptr() for _, X in reqs], [Y.data_ptr() for Y in outs])
+    assert st["completed"] == len(reqs) and st["failed"] == 0 and st["p99_us"] > 0
+    for (w, X), Y in zip(reqs, outs):
+        c = ws[w]["c"]
+        Yo = oracle.spmm(ws[w]["m"], ws[w]["m"], c["b"], c["brow"], c["bcol"], ws[w]["vals"], X)
+        assert oracle.normwise_err(Y, Yo, oracle.block_fro(ws[w]["vals"]), X) <= 4e-3
+    srv.close()

@@ -62,6 +62,8 @@ CASES = [
     (256, 256, 1, 16, 1 / 4),
     (512, 512, 257, 4, 1 / 32),
     (2048, 1024, 384, 16, 1 / 16),
+    (512, 768, 200, 1, 1 / 8),
+    (256, 512, 33, 1, 1 / 32),
 ]
 
 
@@ -113,7 +115,8 @@ def _int_case(m, k, n, b, nnzb, seed):
 
 
 @pytest.mark.parametrize("kernel,b,dt", [("tc", 16, torch.float16), ("tc", 8, torch.bfloat16),
-                                         ("tc", 4, torch.float16), ("gather", 1, torch.float16),
+                                         ("tc", 4, torch.float16), ("tc", 1, torch.bfloat16),
+                                         ("gather", 1, torch.float16),
                                          ("gather", 1, torch.bfloat16), ("gather", 1, torch.float32),
                                          ("plain", 4, torch.float32)])
 def test_exact_integer_inputs(kernel, b, dt):
