@@ -154,6 +154,10 @@ static spmm_status upload_plan(spmm_plan *p) {
         UP(d_tile_row, tile_row);
         UP(d_blk_slot, blk_slot);
         UP(d_blk_off, blk_off);
+        // one stage record per entry at most (every stage holds an entry)
+        const int64_t E = std::max<int64_t>((int64_t)hp.ent_col.size(), 1);
+        if (e == cudaSuccess) e = dalloc(p, &p->d_srec, E * stage_record_words());
+        if (e == cudaSuccess) e = dalloc(p, &p->d_sprog, E * stage_prog_words());
     }
 #undef UP
     if (e != cudaSuccess) return cuda_fail(e, "plan upload");
@@ -199,6 +203,8 @@ static spmm_status alloc_dynamic(spmm_plan *p) {
         AL(p->d_tile_row, cap);
         AL(p->d_blk_slot, cap);
         AL(p->d_blk_off, cap);
+        AL(p->d_srec, std::max<int64_t>(cap, 1) * stage_record_words());
+        AL(p->d_sprog, std::max<int64_t>(cap, 1) * stage_prog_words());
     } else {
         d.items_cap = 2 * mb + 2;
         d.ws_slots_cap = mb + 1;
@@ -436,6 +442,12 @@ spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spm
             e = dalloc(p, (char **)&p->d_packed, p->packed_bytes);
             if (e == cudaSuccess && w_dtype == SPMM_E4M3)
                 e = dalloc(p, &p->d_tile_scale, nt * 16);
+        }
+        if (st == SPMM_OK && e == cudaSuccess && kernel == SPMM_KERNEL_TC &&
+            p->mode == SPMM_STATIC) {
+            // the static plan's stage records, once (dynamic plans: every call)
+            e = launch_stage_build(p, 0);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(0);
         }
         if (st == SPMM_OK && e != cudaSuccess) st = cuda_fail(e, "plan allocation");
         if (st != SPMM_OK) {

@@ -14,20 +14,24 @@
 // one MMA with N = 16 x (interval length) serves an interval, since a
 // 128 x 16 x 16 MMA costs about as much to issue as a 128 x 80 x 16 one.
 // Accumulators start at zero in TMEM (the epilogue clears what it reads),
-// so every MMA accumulates.  TMEM holds two accumulator sets so
-// the epilogue of one work unit overlaps the MMAs of the next.
+// so every MMA accumulates.
 //
 // Pipeline: a stage holds up to kEntStage entries (X slabs) and up to
-// kTileStage W tiles.  The producer warp reads entry metadata 32 entries at
-// a time (coalesced, broadcast by shuffles) so its issuing lane never waits
-// on a dependent global load per stage; the X slabs of a stage are requested
-// by one TMA instruction executed by one lane per entry (both 64-column
-// halves of a slab in one 3-D box when n is a multiple of 64), and the
-// stage's W tiles, contiguous in the packed array, by one bulk copy.  The
-// MMA warp stays converged and issues through elect.sync.
+// kTileStage W tiles.  How a work item's entries fall into stages, and the
+// MMAs of each stage (one word per MMA: slab, first W tile, first tile row,
+// rows), is fixed by the plan, so stage_build_kernel writes it once per
+// plan (every call for dynamic plans) as stage records.  Two producer warps
+// follow the records with three in flight: warp 0 copies the stage's W
+// tiles (contiguous in the packed array, one bulk copy) and its MMA program
+// into shared memory, warp 6 requests the X slabs (one TMA per slab, both
+// 64-column halves in one 3-D box when n is a multiple of 64).  Issuing a
+// copy costs its warp a few hundred cycles, so the two run side by side.
+// The MMA warp stays converged: each lane loads one program word and the
+// warp walks them with one shuffle per MMA, issuing through elect.sync.
 //
-// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
-// TMEM owner, warps 2..5 = epilogue (TMEM -> registers -> Y or workspace).
+// Warp roles (224 threads): warp 0 = W producer, warp 1 = MMA issuer and
+// TMEM owner, warps 2..5 = epilogue (TMEM -> registers -> Y or workspace) and,
+// for E4M3 weights, converters, warp 6 = X producer.
 // Every mbarrier wait is bounded (globaltimer); on expiry the CTA records
 // SPMM_ERR_TIMEOUT in the plan's status word, stops, frees TMEM and exits.
 #include <cuda.h>
@@ -82,13 +86,25 @@ constexpr int kAccBufs = 1;
 constexpr int kCtasPerSm = SPMM_TC_CTAS;
 static_assert(kRowCap <= kMaxGroupRows && (SPMM_TC_TILES * 3) / 4 >= kRowCap,
               "stage must hold a full entry");
-constexpr int kThreads = 192;
+constexpr int kThreads = 224;
+constexpr int kXWarp = 6;                                         // the X-slab producer warp
 constexpr unsigned long long kWaitNs = 2000000000ull;             // 2 s per wait
 
+// A stage's MMA program: one word per MMA (slab index in the stage | first
+// W tile in the stage << 4 | first tile row << 12 | rows << 16), so the MMA
+// warp decodes nothing on its critical path.
+constexpr int kMmaStage = 32;                                     // MMAs per stage (one per lane)
+static_assert(kEntStage <= 4, "a stage record holds four X columns");
+// Stage record (built before the launch; a work item's stages are records
+// e0, e0 + 1, ... where e0 is its first entry, since every stage holds at
+// least one entry): info (MMAs | entries << 8 | last << 31), W tiles, first
+// W tile, the X column of each entry; the stage's MMA program lives in a
+// parallel array, kMmaStage words per record.
+constexpr int kRecWords = 8;
 struct StageMeta {
-    uint32_t nent;                 // entries in the stage; bit 31: last stage of the unit
+    uint32_t info;                 // MMAs | entries << 8; bit 31: last stage of the unit
     uint32_t nslots;               // W tiles in the stage
-    uint32_t cover[kEntStage];     // per entry: covered rows | interval starts << 16
+    uint32_t prog[kMmaStage];
 };
 
 struct __align__(8) Smem {
@@ -96,7 +112,7 @@ struct __align__(8) Smem {
     StageMeta meta[kStages];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
-    int32_t issued, consumed;
+    int32_t issued[2], consumed;   // stages issued by the W / X producers
     int64_t nunits;
 };
 
@@ -249,6 +265,7 @@ struct TcProb {
     void *Y;
     float *ws;
     const int64_t *ws_row0;
+    const uint32_t *srec, *sprog;  // stage records and MMA programs
     int64_t ldy, n;
     int64_t unit_base;           // first unit of this problem in launch order
     int32_t ntn, x3d;            // n tiles of 128; X map is 3-D (64, k, n/64)
@@ -320,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         }
         sm->nunits = nu;
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&sm->full[s], 1);
+            mbar_init(&sm->full[s], 2);    // both producers
             mbar_init(&sm->empty[s], 1);
             mbar_init(&sm->conv[s], 4);    // E4M3: one arrival per converter warp
         }
@@ -329,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             mbar_init(&sm->acce[b], 128);  // every epilogue thread
         }
         sm->abort_flag = 0;
-        sm->issued = 0;
+        sm->issued[0] = sm->issued[1] = 0;
         sm->consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -347,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = sm->tmem_base;
-    if (warp >= 2) {
+    if (warp >= 2 && warp < 6) {
         // accumulators start at zero: each epilogue warp clears its lane quarter
         const uint32_t lq = (uint32_t)((warp & 3) * 32) << 16;
         for (int c = 0; c < kAccBufs * kAccCols; c += 16) tmem_zero16(tmem + lq + c);
@@ -357,8 +374,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     __syncthreads();
     tc_fence_after();
 
-    if (warp == 0) {
-        // ------------------------------------------------ TMA producer
+    if (warp == 0 || warp == kXWarp) {
+        // ------------------------------------------------ TMA producers
+        // Warp 0 copies each stage's W tiles and its MMA program; warp 6
+        // requests its X slabs.  Both follow the stage records of the unit
+        // (built ahead of the launch) with three records in flight, so
+        // neither waits on a global load or decodes anything per stage.
+        const bool wprod = warp == 0;
         int stage = 0;
         uint32_t phase = 0;
         int32_t issued = 0;
@@ -366,84 +388,107 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         for (int64_t u = blockIdx.x; ok && u < nunits; u += gridDim.x) {
             const Unit un = decode_unit(B, u);
             const TcProb &P = B.prob[un.p];
-            const CUtensorMap *xmap = &B.maps[un.p];
             const int32_t *it = P.items + un.item * kItemFields;
             const int32_t e0 = it[1], e1 = it[2];
+            if (e0 >= e1) continue;
             const int n0 = un.t * kNTile;
-            for (int32_t eb = e0; ok && eb < e1; eb += 32) {
-                // lane l holds the metadata of entry eb + l
-                const int32_t e = eb + lane;
-                const bool valid = e < e1;
-                const int32_t mcol = valid ? P.ent_col[e] : 0;
-                const int32_t mtb = valid ? P.ent_tbeg[e] : 0;
-                const uint32_t mcov = valid ? (uint32_t)P.ent_cover[e] : 0u;
-                const int mslots = __popc(mcov & 0xFFFFu);
-                const int cnt = min(32, e1 - eb);
-                for (int j = 0; j < cnt;) {
-                    // a stage: consecutive entries j .. j+nent-1 while they fit
-                    int nent = 0, slots = 0;
-                    while (j + nent < cnt && nent < kEntStage) {
-                        const int t = __shfl_sync(0xffffffffu, mslots, j + nent);
-                        if (slots + t > G::tiles) break;
-                        slots += t;
-                        ++nent;
-                    }
-                    int w = 1;
-                    if (lane == 0) w = mbar_wait(&sm->empty[stage], phase ^ 1, sm) ? 1 : 0;
-                    if (!__shfl_sync(0xffffffffu, w, 0)) {
-                        ok = false;
-                        break;
-                    }
-                    const int32_t stb = __shfl_sync(0xffffffffu, mtb, j);
-                    const bool last = (j + nent == cnt) && (eb + 32 >= e1);
-                    uint8_t *st = stages + stage * G::bytes;
-                    const bool mine = lane >= j && lane < j + nent;
-                    if (mine) sm->meta[stage].cover[lane - j] = mcov;
+            // lane l: word (l & 7) of the record, and (W producer) program word l
+            auto ld_rec = [&](int32_t r) -> uint32_t {
+                return r < e1 ? __ldg(P.srec + (int64_t)r * kRecWords + (lane & 7)) : 0u;
+            };
+            auto ld_prog = [&](int32_t r) -> uint32_t {
+                return (wprod && r < e1) ? __ldg(P.sprog + (int64_t)r * kMmaStage + lane) : 0u;
+            };
+            // one stage from its record word (lane l: word l & 7) and program
+            // word; 1 after the unit's last stage, -1 on a failed wait
+            auto stage_step = [&](uint32_t rc, uint32_t pc) -> int {
+                const uint32_t info = __shfl_sync(0xffffffffu, rc, 0);
+                const uint32_t nslots = __shfl_sync(0xffffffffu, rc, 1);
+                const uint32_t stb = __shfl_sync(0xffffffffu, rc, 2);
+                const uint32_t col = __shfl_sync(0xffffffffu, rc, 3 + (lane & 3));
+                const int nent = (int)((info >> 8) & 0xfu);
+                int w = 1;
+                if (lane == 0) w = mbar_wait(&sm->empty[stage], phase ^ 1, sm) ? 1 : 0;
+                if (!__shfl_sync(0xffffffffu, w, 0)) return -1;
+                uint8_t *st = stages + stage * G::bytes;
+                if (wprod) {
+                    sm->meta[stage].prog[lane] = pc;
                     if (lane == 0) {
-                        sm->meta[stage].nent = (uint32_t)nent | (last ? 0x80000000u : 0u);
-                        sm->meta[stage].nslots = (uint32_t)slots;
+                        sm->meta[stage].info = info;
+                        sm->meta[stage].nslots = nslots;
                     }
                     __syncwarp();
-                    if (lane == 0) {
+                    if (lane == 0 && nslots) {
                         if (W8) {
-                            mbar_arrive_tx(&sm->full[stage], nent * kSlabBytes +
-                                                                 slots * (kTileBytes8 + kScaleBytes));
+                            mbar_arrive_tx(&sm->full[stage], nslots * (kTileBytes8 + kScaleBytes));
                             bulk_load(st + G::w8, P.packed + (int64_t)stb * kTileBytes8,
-                                      slots * kTileBytes8, &sm->full[stage]);
+                                      nslots * kTileBytes8, &sm->full[stage]);
                             bulk_load(st + G::sc, P.tile_scale + (int64_t)stb * 16,
-                                      slots * kScaleBytes, &sm->full[stage]);
+                                      nslots * kScaleBytes, &sm->full[stage]);
                         } else {
-                            mbar_arrive_tx(&sm->full[stage], nent * kSlabBytes + slots * kTileBytes16);
+                            mbar_arrive_tx(&sm->full[stage], nslots * kTileBytes16);
                             bulk_load(st + G::w16, P.packed + (int64_t)stb * kTileBytes16,
-                                      slots * kTileBytes16, &sm->full[stage]);
+                                      nslots * kTileBytes16, &sm->full[stage]);
                         }
+                    } else if (lane == 0) {
+                        mbar_arrive(&sm->full[stage]);
                     }
-                    if (mine) {
-                        uint8_t *slab = st + (lane - j) * kSlabBytes;
+                } else {
+                    if (lane == 0) mbar_arrive_tx(&sm->full[stage], nent * kSlabBytes);
+                    __syncwarp();
+                    if (lane < nent) {
+                        const CUtensorMap *xmap = &B.maps[un.p];
+                        uint8_t *slab = st + lane * kSlabBytes;
                         if (P.x3d) {
-                            tma_load_3d(slab, xmap, 0, mcol * kTile, n0 / (kNTile / 2),
+                            tma_load_3d(slab, xmap, 0, (int)col * kTile, n0 / (kNTile / 2),
                                         &sm->full[stage]);
                         } else {
-                            tma_load_2d(slab, xmap, n0, mcol * kTile, &sm->full[stage]);
+                            tma_load_2d(slab, xmap, n0, (int)col * kTile, &sm->full[stage]);
                             tma_load_2d(slab + kSlabBytes / 2, xmap, n0 + kNTile / 2,
-                                        mcol * kTile, &sm->full[stage]);
+                                        (int)col * kTile, &sm->full[stage]);
                         }
                     }
-                    __syncwarp();
-                    ++issued;
-                    if (++stage == kStages) {
-                        stage = 0;
-                        phase ^= 1;
-                    }
-                    j += nent;
                 }
+                __syncwarp();
+                ++issued;
+                if (++stage == kStages) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+                return (info >> 31) ? 1 : 0;
+            };
+            // three records in flight, in three registers that are only ever
+            // reloaded (never moved: a move would wait for the load)
+            uint32_t ra = ld_rec(e0), rb = ld_rec(e0 + 1), rd = ld_rec(e0 + 2);
+            uint32_t pa = ld_prog(e0), pb = ld_prog(e0 + 1), pd = ld_prog(e0 + 2);
+            bool done = false;   // a unit's stages never outnumber its entries
+            for (int32_t r = e0; ok && !done && r < e1; r += 3) {
+                int v = stage_step(ra, pa);
+                ra = ld_rec(r + 3);
+                pa = ld_prog(r + 3);
+                if (v == 0 && r + 1 < e1) {
+                    v = stage_step(rb, pb);
+                    rb = ld_rec(r + 4);
+                    pb = ld_prog(r + 4);
+                    if (v == 0 && r + 2 < e1) {
+                        v = stage_step(rd, pd);
+                        rd = ld_rec(r + 5);
+                        pd = ld_prog(r + 5);
+                    }
+                }
+                if (v < 0) ok = false;
+                if (v > 0) done = true;
+            }
+            if (ok && !done) {
+                record(B.status, kDevBadPlan);
+                ok = false;
             }
         }
         if (!ok && lane == 0) {
-            record(B.status, kDevTimeout);
+            record(B.status, kDevTimeout);   // no effect if a bad plan was recorded first
             sm->abort_flag = 1;
         }
-        if (lane == 0) sm->issued = issued;
+        if (lane == 0) sm->issued[wprod ? 0 : 1] = issued;
     } else if (warp == 1) {
         // ---------------------------------- MMA issuer (converged warp)
         constexpr uint32_t idesc0 = make_idesc(Cvt<T>::fmt, kNTile, 0);
@@ -471,28 +516,25 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                     ok = false;
                     break;
                 }
+                __syncwarp();   // orders lane 0's acquire before every lane's reads
                 tc_fence_after();
                 ++consumed;
-                const uint32_t mnent = __shfl_sync(0xffffffffu, sm->meta[stage].nent, 0);
-                const int nent = (int)(mnent & 0xffu);
-                last = (mnent >> 31) != 0;
+                // every lane reads the stage header and one program word
+                const uint32_t info = sm->meta[stage].info;
+                const int nmma = (int)(info & 0xffu);
+                last = (info >> 31) != 0;
+                const uint32_t myword = sm->meta[stage].prog[lane];   // words >= nmma unused
                 const uint32_t sbase = smem_u32(stages + stage * G::bytes);
-                uint64_t bdesc = b_desc(sbase + G::w16);
-                for (int i = 0; i < nent; ++i) {
-                    const uint64_t adesc = a_desc(sbase + i * kSlabBytes);
-                    const uint32_t c = __shfl_sync(0xffffffffu, sm->meta[stage].cover[i], 0);
-                    const uint32_t cov = c & 0xFFFFu;
-                    uint32_t starts = c >> 16;
-                    while (starts) {
-                        const uint32_t r0 = __ffs(starts) - 1;
-                        starts &= starts - 1;
-                        const uint32_t next = starts ? (uint32_t)(__ffs(starts) - 1) : 16u;
-                        uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;   // run of covered rows
-                        len = len < next - r0 ? len : next - r0;
-                        tc_mma_elect(dbase + r0 * kTile, adesc, bdesc,
-                                     idesc0 | ((len * kTile) >> 3) << 17, 1u);
-                        bdesc += (uint64_t)((len * kTileBytes16) >> 4);
-                    }
+                const uint64_t adesc0 = a_desc(sbase);
+                const uint64_t bdesc0 = b_desc(sbase + G::w16);
+                for (int i = 0; i < nmma; ++i) {
+                    const uint32_t wd = __shfl_sync(0xffffffffu, myword, i);
+                    const uint32_t slab = wd & 15u, toff = (wd >> 4) & 255u;
+                    const uint32_t r0 = (wd >> 12) & 15u, len = (wd >> 16) & 31u;
+                    // descriptor start addresses are in 16-byte units (bits 0-13)
+                    tc_mma_elect(dbase + r0 * kTile, adesc0 + slab * (kSlabBytes >> 4),
+                                 bdesc0 + toff * (kTileBytes16 >> 4),
+                                 idesc0 | ((len * kTile) >> 3) << 17, 1u);
                 }
                 if (lane == 0) tc_commit(&sm->empty[stage]);
                 __syncwarp();
@@ -535,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                         ok = false;
                         break;
                     }
-                    const uint32_t mnent = sm->meta[cstage].nent;
+                    const uint32_t mnent = sm->meta[cstage].info;
                     last = (mnent >> 31) != 0;
                     const int nslots = (int)sm->meta[cstage].nslots;
                     uint8_t *st = stages + cstage * G::bytes;
@@ -626,9 +668,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     __syncthreads();
     // after an abort, let copies still in flight land before the CTA exits
     if (threadIdx.x == 0 && sm->abort_flag) {
-        for (int32_t c = sm->consumed; c < sm->issued; ++c) {
+        const int32_t lo = min(sm->issued[0], sm->issued[1]);
+        const int32_t hi = max(sm->issued[0], sm->issued[1]);
+        for (int32_t c = sm->consumed; c < hi; ++c) {
             const int s = c % kStages;
             const uint32_t par = (uint32_t)((c / kStages) & 1);
+            // a stage only one producer issued: stand in for the other's arrival
+            if (c >= lo) mbar_arrive(&sm->full[s]);
             const unsigned long long t0 = gtimer();
             while (!mbar_try(&sm->full[s], par) && gtimer() - t0 < kWaitNs) {
             }
@@ -639,6 +685,94 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kAccBufs * kAccCols));
+    }
+}
+
+// ------------------------------------------------------- stage records ---
+// One warp per work item cuts the item's entries into stages exactly as the
+// producers consume them: consecutive entries while the stage holds at most
+// kEntStage X slabs, `tiles_cap` W tiles and kMmaStage MMAs (one entry
+// always fits).  It writes the item's stage records at e0, e0 + 1, ... and
+// expands every entry's row intervals (runs of covered rows cut at
+// interval starts) into MMA words: slab | first W tile in the stage << 4 |
+// first tile row << 12 | rows << 16.  Dynamic plans read the item count and
+// the status word on the device (a rejected pattern builds nothing).
+__global__ void stage_build_kernel(const int32_t *__restrict__ items, int64_t n_items,
+                                   const int32_t *__restrict__ n_items_dev,
+                                   const int32_t *__restrict__ status,
+                                   const int32_t *__restrict__ ent_col,
+                                   const int32_t *__restrict__ ent_tbeg,
+                                   const int32_t *__restrict__ ent_cover, int tiles_cap,
+                                   uint32_t *__restrict__ srec, uint32_t *__restrict__ sprog) {
+    const int lane = threadIdx.x & 31;
+    const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int64_t ni = n_items;
+    if (n_items_dev) {
+        if (*status != 0) return;
+        ni = min(ni, (int64_t)max(*n_items_dev, 0));
+    }
+    if (item >= ni) return;
+    const int32_t *it = items + item * kItemFields;
+    const int32_t e0 = it[1], e1 = it[2];
+    int32_t rec = e0;
+    for (int32_t eb = e0; eb < e1; eb += 32) {
+        const int32_t e = eb + lane;
+        const bool valid = e < e1;
+        const int32_t mcol = valid ? ent_col[e] : 0;
+        const int32_t mtb = valid ? ent_tbeg[e] : 0;
+        const uint32_t mcov = valid ? (uint32_t)ent_cover[e] : 0u;
+        const int mslots = __popc(mcov & 0xFFFFu), mmmas = __popc(mcov >> 16);
+        // inclusive prefix sums of tiles and MMAs over the 32 entries
+        int S = mslots, M = mmmas;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int s2 = __shfl_up_sync(0xffffffffu, S, o);
+            const int m2 = __shfl_up_sync(0xffffffffu, M, o);
+            if (lane >= o) {
+                S += s2;
+                M += m2;
+            }
+        }
+        const int cnt = min(32, e1 - eb);
+        for (int j = 0; j < cnt;) {
+            // sums are monotone: the fitting lanes are contiguous from j
+            const int Sb = j ? __shfl_sync(0xffffffffu, S, j - 1) : 0;
+            const int Mb = j ? __shfl_sync(0xffffffffu, M, j - 1) : 0;
+            const bool fits = lane >= j && lane < j + kEntStage && lane < cnt &&
+                              S - Sb <= tiles_cap && M - Mb <= kMmaStage;
+            const int nent = __popc(__ballot_sync(0xffffffffu, fits));
+            const int slots = __shfl_sync(0xffffffffu, S, j + nent - 1) - Sb;
+            const int nmma = __shfl_sync(0xffffffffu, M, j + nent - 1) - Mb;
+            const int32_t stb = __shfl_sync(0xffffffffu, mtb, j);
+            // record word 3 + i holds the X column of the stage's entry i
+            const int32_t xc = __shfl_sync(0xffffffffu, mcol, min(j + max(lane - 3, 0), 31));
+            const bool last = (j + nent == cnt) && (eb + 32 >= e1);
+            if (lane >= j && lane < j + nent) {
+                uint32_t k = (uint32_t)(M - mmmas - Mb);
+                uint32_t toff = (uint32_t)(S - mslots - Sb);
+                const uint32_t cov = mcov & 0xFFFFu, slab = (uint32_t)(lane - j);
+                uint32_t starts = mcov >> 16;
+                while (starts) {
+                    const uint32_t r0 = __ffs(starts) - 1;
+                    starts &= starts - 1;
+                    const uint32_t next = starts ? (uint32_t)(__ffs(starts) - 1) : 16u;
+                    uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;   // run of covered rows
+                    len = len < next - r0 ? len : next - r0;
+                    sprog[(int64_t)rec * kMmaStage + k++] = slab | toff << 4 | r0 << 12 | len << 16;
+                    toff += len;
+                }
+            }
+            if (lane < kRecWords) {
+                uint32_t v = 0;
+                if (lane == 0) v = (uint32_t)nmma | (uint32_t)nent << 8 | (last ? 0x80000000u : 0u);
+                else if (lane == 1) v = (uint32_t)slots;
+                else if (lane == 2) v = (uint32_t)stb;
+                else if (lane < 3 + kEntStage) v = (lane - 3 < nent) ? (uint32_t)xc : 0u;
+                srec[(int64_t)rec * kRecWords + lane] = v;
+            }
+            ++rec;
+            j += nent;
+        }
     }
 }
 
@@ -768,6 +902,8 @@ void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, i
     P.Y = Y;
     P.ws = p->d_ws;
     P.ws_row0 = p->d_ws_row0;
+    P.srec = p->d_srec;
+    P.sprog = p->d_sprog;
     P.ldy = ldy;
     P.n = n;
     P.ntn = (int)((n + kNTile - 1) / kNTile);
@@ -827,6 +963,11 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
     const bool dyn = p->mode == SPMM_DYNAMIC;
     B.n_items_dev = dyn ? p->d_counts + kCntItems : nullptr;
     B.total_units = (dyn ? p->dyn.items_cap : p->n_items) * B.prob[0].ntn;
+    if (dyn) {
+        // this call's plan was built on the device: cut its stages now
+        e = launch_stage_build(p, s);
+        if (e != cudaSuccess) return e;
+    }
     return dispatch_batch(B, p->xdt == SPMM_BF16, p->wdt == SPMM_E4M3, p->sm_count, s);
 }
 
@@ -901,6 +1042,21 @@ cudaError_t launch_tc_batch(int count, spmm_plan *const *plans, const void *cons
     const bool bf16 = plans[0]->xdt == SPMM_BF16, w8 = plans[0]->wdt == SPMM_E4M3;
     return dispatch_batch(B, bf16, w8, plans[0]->sm_count, s);
 }
+
+cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s) {
+    const bool dyn = p->mode == SPMM_DYNAMIC;
+    const int64_t ni = dyn ? p->dyn.items_cap : p->n_items;
+    if (ni == 0 || !p->d_srec) return cudaSuccess;
+    const int tiles_cap = p->wdt == SPMM_E4M3 ? StageGeom<true>::tiles : StageGeom<false>::tiles;
+    const int64_t blocks = (ni + 3) / 4;   // 4 warps (items) per block
+    stage_build_kernel<<<(unsigned)blocks, 128, 0, s>>>(
+        p->d_items, ni, dyn ? p->d_counts + kCntItems : nullptr, p->d_status, p->d_ent_col,
+        p->d_ent_tbeg, p->d_ent_cover, tiles_cap, p->d_srec, p->d_sprog);
+    return cudaGetLastError();
+}
+
+int64_t stage_record_words() { return kRecWords; }
+int64_t stage_prog_words() { return kMmaStage; }
 
 cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const float *d_scales,
                               const int32_t *d_nnzb, cudaStream_t s) {

@@ -37,6 +37,7 @@ enum DeviceStatus : int32_t {
     kDevPattern = SPMM_ERR_PATTERN,
     kDevCapacity = SPMM_ERR_CAPACITY,
     kDevTimeout = SPMM_ERR_TIMEOUT,
+    kDevBadPlan = SPMM_ERR_CUDA,   // stage records inconsistent with the work items
 };
 
 void set_error(const char *fmt, ...);
@@ -93,6 +94,7 @@ struct spmm_plan {
             *d_red = nullptr, *d_grp_row0 = nullptr, *d_grp_rows = nullptr, *d_ent_col = nullptr,
             *d_ent_tbeg = nullptr, *d_ent_cover = nullptr, *d_tile_row = nullptr, *d_blk_slot = nullptr,
             *d_blk_off = nullptr, *d_grp_ebeg = nullptr;
+    uint32_t *d_srec = nullptr, *d_sprog = nullptr;  // TC: stage records and MMA programs
     int64_t *d_ws_row0 = nullptr;
     int64_t n_items = 0, n_groups = 0, n_entries = 0, n_tiles = 0, n_red = 0;
     void *d_packed = nullptr;      // packed values (kernel layout)
@@ -127,6 +129,10 @@ cudaError_t launch_plain(const spmm_plan *p, const void *d_X, int64_t n, int64_t
                          int64_t ldy, cudaStream_t s);
 cudaError_t launch_gather(const spmm_plan *p, const void *d_X, int64_t n, int64_t ldx, void *d_Y,
                           int64_t ldy, cudaStream_t s);
+// TC stage records of every work item (plan arrays only; no values)
+cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s);
+int64_t stage_record_words();
+int64_t stage_prog_words();
 cudaError_t launch_tc(const spmm_plan *p, const void *d_X, int64_t n, int64_t ldx, void *d_Y,
                       int64_t ldy, cudaStream_t s);
 cudaError_t launch_reduce(const spmm_plan *p, int64_t n, void *d_Y, int64_t ldy, cudaStream_t s);
