@@ -86,25 +86,30 @@ constexpr int kAccBufs = 1;
 constexpr int kCtasPerSm = SPMM_TC_CTAS;
 static_assert(kRowCap <= kMaxGroupRows && (SPMM_TC_TILES * 3) / 4 >= kRowCap,
               "stage must hold a full entry");
-constexpr int kThreads = 224;
-constexpr int kXWarp = 6;                                         // the X-slab producer warp
+constexpr int kThreads = 288;
+constexpr int kXWarp0 = 6, kXWarp1 = 7;                           // X-slab producers (slabs 0-1, 2-3)
+constexpr int kMmaWarpHi = 8;                                     // MMAs of tile rows 8-15
+constexpr int kProducers = 3;                                     // W + two X
 constexpr unsigned long long kWaitNs = 2000000000ull;             // 2 s per wait
 
 // A stage's MMA program: one word per MMA (slab index in the stage | first
 // W tile in the stage << 4 | first tile row << 12 | rows << 16), so the MMA
-// warp decodes nothing on its critical path.
-constexpr int kMmaStage = 32;                                     // MMAs per stage (one per lane)
+// warps decode nothing on their critical path.  Two MMA warps split the
+// accumulator by tile rows (0-7 and 8-15; an interval crossing row 8 becomes
+// two MMAs), so each TMEM column is written by one warp in a fixed order.
+constexpr int kMmaStage = 32;                                     // MMAs per stage and row half (one per lane)
 static_assert(kEntStage <= 4, "a stage record holds four X columns");
 // Stage record (built before the launch; a work item's stages are records
 // e0, e0 + 1, ... where e0 is its first entry, since every stage holds at
-// least one entry): info (MMAs | entries << 8 | last << 31), W tiles, first
-// W tile, the X column of each entry; the stage's MMA program lives in a
-// parallel array, kMmaStage words per record.
+// least one entry): info (MMAs of rows 0-7 | MMAs of rows 8-15 << 6 |
+// entries << 12 | last << 31), W tiles, first W tile, the X column of each
+// entry; the stage's MMA program lives in a parallel array of 2 x kMmaStage
+// words per record, (rows 0-7 word, rows 8-15 word) pairs.
 constexpr int kRecWords = 8;
 struct StageMeta {
-    uint32_t info;                 // MMAs | entries << 8; bit 31: last stage of the unit
+    uint32_t info;                 // as in the stage record
     uint32_t nslots;               // W tiles in the stage
-    uint32_t prog[kMmaStage];
+    uint32_t prog[2][kMmaStage];   // MMA words of rows 0-7 and of rows 8-15
 };
 
 struct __align__(8) Smem {
@@ -112,8 +117,9 @@ struct __align__(8) Smem {
     StageMeta meta[kStages];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
-    int32_t issued[2], consumed;   // stages issued by the W / X producers
+    int32_t issued[kProducers], consumed[2];   // per producer / per MMA warp
     int64_t nunits;
+    int32_t epi_ok[2];             // accumulator-ready verdict, per unit parity
 };
 
 // ------------------------------------------------------------ PTX helpers
@@ -337,17 +343,17 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         }
         sm->nunits = nu;
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&sm->full[s], 2);    // both producers
-            mbar_init(&sm->empty[s], 1);
+            mbar_init(&sm->full[s], kProducers);
+            mbar_init(&sm->empty[s], 2);   // both MMA warps
             mbar_init(&sm->conv[s], 4);    // E4M3: one arrival per converter warp
         }
         for (int b = 0; b < kAccBufs; ++b) {
-            mbar_init(&sm->accf[b], 1);    // MMA completion
+            mbar_init(&sm->accf[b], 2);    // MMA completion, both MMA warps
             mbar_init(&sm->acce[b], 128);  // every epilogue thread
         }
         sm->abort_flag = 0;
-        sm->issued[0] = sm->issued[1] = 0;
-        sm->consumed = 0;
+        for (int i = 0; i < kProducers; ++i) sm->issued[i] = 0;
+        sm->consumed[0] = sm->consumed[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -374,13 +380,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     __syncthreads();
     tc_fence_after();
 
-    if (warp == 0 || warp == kXWarp) {
+    if (warp == 0 || warp == kXWarp0 || warp == kXWarp1) {
         // ------------------------------------------------ TMA producers
         // Warp 0 copies each stage's W tiles and its MMA program; warp 6
         // requests its X slabs.  Both follow the stage records of the unit
         // (built ahead of the launch) with three records in flight, so
         // neither waits on a global load or decodes anything per stage.
         const bool wprod = warp == 0;
+        const int pid = wprod ? 0 : (warp == kXWarp0 ? 1 : 2);
+        const int xlo = pid == 2 ? 2 : 0;   // first slab of this X producer
         int stage = 0;
         uint32_t phase = 0;
         int32_t issued = 0;
@@ -396,23 +404,26 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             auto ld_rec = [&](int32_t r) -> uint32_t {
                 return r < e1 ? __ldg(P.srec + (int64_t)r * kRecWords + (lane & 7)) : 0u;
             };
-            auto ld_prog = [&](int32_t r) -> uint32_t {
-                return (wprod && r < e1) ? __ldg(P.sprog + (int64_t)r * kMmaStage + lane) : 0u;
+            auto ld_prog = [&](int32_t r) -> uint2 {
+                return (wprod && r < e1)
+                           ? __ldg((const uint2 *)(P.sprog + (int64_t)r * 2 * kMmaStage) + lane)
+                           : make_uint2(0u, 0u);
             };
             // one stage from its record word (lane l: word l & 7) and program
             // word; 1 after the unit's last stage, -1 on a failed wait
-            auto stage_step = [&](uint32_t rc, uint32_t pc) -> int {
+            auto stage_step = [&](uint32_t rc, uint2 pc) -> int {
                 const uint32_t info = __shfl_sync(0xffffffffu, rc, 0);
                 const uint32_t nslots = __shfl_sync(0xffffffffu, rc, 1);
                 const uint32_t stb = __shfl_sync(0xffffffffu, rc, 2);
-                const uint32_t col = __shfl_sync(0xffffffffu, rc, 3 + (lane & 3));
-                const int nent = (int)((info >> 8) & 0xfu);
+                const uint32_t col = __shfl_sync(0xffffffffu, rc, 3 + xlo + (lane & 1));
+                const int nent = (int)((info >> 12) & 0xfu);
                 int w = 1;
                 if (lane == 0) w = mbar_wait(&sm->empty[stage], phase ^ 1, sm) ? 1 : 0;
                 if (!__shfl_sync(0xffffffffu, w, 0)) return -1;
                 uint8_t *st = stages + stage * G::bytes;
                 if (wprod) {
-                    sm->meta[stage].prog[lane] = pc;
+                    sm->meta[stage].prog[0][lane] = pc.x;
+                    sm->meta[stage].prog[1][lane] = pc.y;
                     if (lane == 0) {
                         sm->meta[stage].info = info;
                         sm->meta[stage].nslots = nslots;
@@ -434,11 +445,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                         mbar_arrive(&sm->full[stage]);
                     }
                 } else {
-                    if (lane == 0) mbar_arrive_tx(&sm->full[stage], nent * kSlabBytes);
+                    const int mine = min(max(nent - xlo, 0), 2);
+                    if (lane == 0) mbar_arrive_tx(&sm->full[stage], mine * kSlabBytes);
                     __syncwarp();
-                    if (lane < nent) {
+                    if (lane < mine) {
                         const CUtensorMap *xmap = &B.maps[un.p];
-                        uint8_t *slab = st + lane * kSlabBytes;
+                        uint8_t *slab = st + (xlo + lane) * kSlabBytes;
                         if (P.x3d) {
                             tma_load_3d(slab, xmap, 0, (int)col * kTile, n0 / (kNTile / 2),
                                         &sm->full[stage]);
@@ -460,7 +472,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             // three records in flight, in three registers that are only ever
             // reloaded (never moved: a move would wait for the load)
             uint32_t ra = ld_rec(e0), rb = ld_rec(e0 + 1), rd = ld_rec(e0 + 2);
-            uint32_t pa = ld_prog(e0), pb = ld_prog(e0 + 1), pd = ld_prog(e0 + 2);
+            uint2 pa = ld_prog(e0), pb = ld_prog(e0 + 1), pd = ld_prog(e0 + 2);
             bool done = false;   // a unit's stages never outnumber its entries
             for (int32_t r = e0; ok && !done && r < e1; r += 3) {
                 int v = stage_step(ra, pa);
@@ -488,9 +500,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             record(B.status, kDevTimeout);   // no effect if a bad plan was recorded first
             sm->abort_flag = 1;
         }
-        if (lane == 0) sm->issued[wprod ? 0 : 1] = issued;
-    } else if (warp == 1) {
-        // ---------------------------------- MMA issuer (converged warp)
+        if (lane == 0) sm->issued[pid] = issued;
+    } else if (warp == 1 || warp == kMmaWarpHi) {
+        // ------------------------------- MMA issuers (converged warps)
+        const int half = warp == 1 ? 0 : 1;   // tile rows 0-7 / 8-15
         constexpr uint32_t idesc0 = make_idesc(Cvt<T>::fmt, kNTile, 0);
         int stage = 0;
         uint32_t phase = 0;
@@ -521,9 +534,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                 ++consumed;
                 // every lane reads the stage header and one program word
                 const uint32_t info = sm->meta[stage].info;
-                const int nmma = (int)(info & 0xffu);
+                const int nmma = (int)((info >> (6 * half)) & 63u);
                 last = (info >> 31) != 0;
-                const uint32_t myword = sm->meta[stage].prog[lane];   // words >= nmma unused
+                const uint32_t myword = sm->meta[stage].prog[half][lane];   // words >= nmma unused
                 const uint32_t sbase = smem_u32(stages + stage * G::bytes);
                 const uint64_t adesc0 = a_desc(sbase);
                 const uint64_t bdesc0 = b_desc(sbase + G::w16);
@@ -552,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                 record(B.status, kDevTimeout);
                 sm->abort_flag = 1;
             }
-            sm->consumed = consumed;
+            sm->consumed[half] = consumed;
         }
     } else {
         // ------------------------- converters (E4M3) and epilogue
@@ -574,7 +587,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                     int w = 1;
                     if (lane == 0) w = mbar_wait(&sm->full[cstage], cphase, sm) ? 1 : 0;
                     if (!__shfl_sync(0xffffffffu, w, 0)) {
-                        ok = false;
+                        // every epilogue warp still meets the named barrier
+                        // below, where the poller sees the abort
+                        if (lane == 0) {
+                            record(B.status, kDevTimeout);
+                            sm->abort_flag = 1;
+                        }
                         break;
                     }
                     const uint32_t mnent = sm->meta[cstage].info;
@@ -620,13 +638,27 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                         cphase ^= 1;
                     }
                 }
-                if (!ok) break;
             }
             const int ab = local % kAccBufs;
             const uint32_t aphase = (local / kAccBufs) & 1;
-            int okw = 1;
-            if (lane == 0) okw = mbar_wait(&sm->accf[ab], aphase, sm) ? 1 : 0;
-            okw = __shfl_sync(0xffffffffu, okw, 0);
+            // one thread polls the accumulator barrier, sleeping between polls
+            // (the mbarrier unit is shared with the copy and MMA pipelines of
+            // both CTAs of the SM); the other epilogue threads block on a
+            // named barrier, which costs the mbarrier unit nothing
+            if (warp == 2 && lane == 0) {
+                const unsigned long long t0 = gtimer();
+                int okp = 1;
+                while (!mbar_try(&sm->accf[ab], aphase)) {
+                    __nanosleep(400);
+                    if (sm->abort_flag || gtimer() - t0 > kWaitNs) {
+                        okp = 0;
+                        break;
+                    }
+                }
+                sm->epi_ok[local & 1] = okp;
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            const int okw = sm->epi_ok[local & 1];
             if (!okw) {
                 ok = false;
                 break;
@@ -645,6 +677,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                 tmem_ld16(ta, v);
                 tmem_zero16(ta);
                 if (!in) continue;
+                // (staging through shared memory for 16-byte row stores measured slower)
                 if (slot >= 0) {
                     float *dst = P.ws + (wrow0 + r * kTile) * P.n + col;
 #pragma unroll
@@ -668,13 +701,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     __syncthreads();
     // after an abort, let copies still in flight land before the CTA exits
     if (threadIdx.x == 0 && sm->abort_flag) {
-        const int32_t lo = min(sm->issued[0], sm->issued[1]);
-        const int32_t hi = max(sm->issued[0], sm->issued[1]);
-        for (int32_t c = sm->consumed; c < hi; ++c) {
+        int32_t hi = 0;
+        for (int i = 0; i < kProducers; ++i) hi = max(hi, sm->issued[i]);
+        for (int32_t c = min(sm->consumed[0], sm->consumed[1]); c < hi; ++c) {
             const int s = c % kStages;
             const uint32_t par = (uint32_t)((c / kStages) & 1);
-            // a stage only one producer issued: stand in for the other's arrival
-            if (c >= lo) mbar_arrive(&sm->full[s]);
+            // stand in for the arrivals of producers that stopped before stage c
+            for (int i = 0; i < kProducers; ++i)
+                if (c >= sm->issued[i]) mbar_arrive(&sm->full[s]);
             const unsigned long long t0 = gtimer();
             while (!mbar_try(&sm->full[s], par) && gtimer() - t0 < kWaitNs) {
             }
@@ -691,11 +725,12 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 // ------------------------------------------------------- stage records ---
 // One warp per work item cuts the item's entries into stages exactly as the
 // producers consume them: consecutive entries while the stage holds at most
-// kEntStage X slabs, `tiles_cap` W tiles and kMmaStage MMAs (one entry
+// kEntStage X slabs, `tiles_cap` W tiles and kMmaStage MMAs per row half (one entry
 // always fits).  It writes the item's stage records at e0, e0 + 1, ... and
 // expands every entry's row intervals (runs of covered rows cut at
 // interval starts) into MMA words: slab | first W tile in the stage << 4 |
-// first tile row << 12 | rows << 16.  Dynamic plans read the item count and
+// first tile row << 12 | rows << 16, one list per row half (an interval
+// across row 8 is cut there).  Dynamic plans read the item count and
 // the status word on the device (a rejected pattern builds nothing).
 __global__ void stage_build_kernel(const int32_t *__restrict__ items, int64_t n_items,
                                    const int32_t *__restrict__ n_items_dev,
@@ -721,50 +756,76 @@ __global__ void stage_build_kernel(const int32_t *__restrict__ items, int64_t n_
         const int32_t mcol = valid ? ent_col[e] : 0;
         const int32_t mtb = valid ? ent_tbeg[e] : 0;
         const uint32_t mcov = valid ? (uint32_t)ent_cover[e] : 0u;
-        const int mslots = __popc(mcov & 0xFFFFu), mmmas = __popc(mcov >> 16);
-        // inclusive prefix sums of tiles and MMAs over the 32 entries
-        int S = mslots, M = mmmas;
+        const uint32_t cov = mcov & 0xFFFFu;
+        // this entry's MMAs per row half: intervals below / above row 8, an
+        // interval across it counting in both
+        int nlo = 0, nhi = 0;
+        for (uint32_t st = mcov >> 16; st; st &= st - 1) {
+            const uint32_t r0 = __ffs(st) - 1;
+            const uint32_t rest = st & (st - 1);
+            const uint32_t next = rest ? (uint32_t)(__ffs(rest) - 1) : 16u;
+            uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;   // run of covered rows
+            len = len < next - r0 ? len : next - r0;
+            nlo += r0 < 8;
+            nhi += r0 + len > 8;
+        }
+        const int mslots = __popc(cov);
+        // inclusive prefix sums over the 32 entries: tiles, MMAs of each half
+        int S = mslots, L = nlo, H = nhi;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int s2 = __shfl_up_sync(0xffffffffu, S, o);
-            const int m2 = __shfl_up_sync(0xffffffffu, M, o);
+            const int l2 = __shfl_up_sync(0xffffffffu, L, o);
+            const int h2 = __shfl_up_sync(0xffffffffu, H, o);
             if (lane >= o) {
                 S += s2;
-                M += m2;
+                L += l2;
+                H += h2;
             }
         }
         const int cnt = min(32, e1 - eb);
         for (int j = 0; j < cnt;) {
             // sums are monotone: the fitting lanes are contiguous from j
             const int Sb = j ? __shfl_sync(0xffffffffu, S, j - 1) : 0;
-            const int Mb = j ? __shfl_sync(0xffffffffu, M, j - 1) : 0;
+            const int Lb = j ? __shfl_sync(0xffffffffu, L, j - 1) : 0;
+            const int Hb = j ? __shfl_sync(0xffffffffu, H, j - 1) : 0;
             const bool fits = lane >= j && lane < j + kEntStage && lane < cnt &&
-                              S - Sb <= tiles_cap && M - Mb <= kMmaStage;
+                              S - Sb <= tiles_cap && L - Lb <= kMmaStage && H - Hb <= kMmaStage;
             const int nent = __popc(__ballot_sync(0xffffffffu, fits));
             const int slots = __shfl_sync(0xffffffffu, S, j + nent - 1) - Sb;
-            const int nmma = __shfl_sync(0xffffffffu, M, j + nent - 1) - Mb;
+            const int mlo = __shfl_sync(0xffffffffu, L, j + nent - 1) - Lb;
+            const int mhi = __shfl_sync(0xffffffffu, H, j + nent - 1) - Hb;
             const int32_t stb = __shfl_sync(0xffffffffu, mtb, j);
             // record word 3 + i holds the X column of the stage's entry i
             const int32_t xc = __shfl_sync(0xffffffffu, mcol, min(j + max(lane - 3, 0), 31));
             const bool last = (j + nent == cnt) && (eb + 32 >= e1);
             if (lane >= j && lane < j + nent) {
-                uint32_t k = (uint32_t)(M - mmmas - Mb);
+                uint32_t klo = (uint32_t)(L - nlo - Lb), khi = (uint32_t)(H - nhi - Hb);
                 uint32_t toff = (uint32_t)(S - mslots - Sb);
-                const uint32_t cov = mcov & 0xFFFFu, slab = (uint32_t)(lane - j);
-                uint32_t starts = mcov >> 16;
-                while (starts) {
-                    const uint32_t r0 = __ffs(starts) - 1;
-                    starts &= starts - 1;
-                    const uint32_t next = starts ? (uint32_t)(__ffs(starts) - 1) : 16u;
-                    uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;   // run of covered rows
+                const uint32_t slab = (uint32_t)(lane - j);
+                uint32_t *pr = sprog + (int64_t)rec * 2 * kMmaStage;
+                for (uint32_t st = mcov >> 16; st; st &= st - 1) {
+                    const uint32_t r0 = __ffs(st) - 1;
+                    const uint32_t rest = st & (st - 1);
+                    const uint32_t next = rest ? (uint32_t)(__ffs(rest) - 1) : 16u;
+                    uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;
                     len = len < next - r0 ? len : next - r0;
-                    sprog[(int64_t)rec * kMmaStage + k++] = slab | toff << 4 | r0 << 12 | len << 16;
+                    if (r0 < 8) {
+                        const uint32_t l0 = r0 + len > 8 ? 8 - r0 : len;
+                        pr[2 * klo++] = slab | toff << 4 | r0 << 12 | l0 << 16;
+                    }
+                    if (r0 + len > 8) {
+                        const uint32_t a = r0 < 8 ? 8u : r0;   // first row at or above 8
+                        pr[2 * khi++ + 1] = slab | (toff + (a - r0)) << 4 | a << 12 | (r0 + len - a) << 16;
+                    }
                     toff += len;
                 }
             }
             if (lane < kRecWords) {
                 uint32_t v = 0;
-                if (lane == 0) v = (uint32_t)nmma | (uint32_t)nent << 8 | (last ? 0x80000000u : 0u);
+                if (lane == 0)
+                    v = (uint32_t)mlo | (uint32_t)mhi << 6 | (uint32_t)nent << 12 |
+                        (last ? 0x80000000u : 0u);
                 else if (lane == 1) v = (uint32_t)slots;
                 else if (lane == 2) v = (uint32_t)stb;
                 else if (lane < 3 + kEntStage) v = (lane - 3 < nent) ? (uint32_t)xc : 0u;
@@ -1056,7 +1117,7 @@ cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s) {
 }
 
 int64_t stage_record_words() { return kRecWords; }
-int64_t stage_prog_words() { return kMmaStage; }
+int64_t stage_prog_words() { return 2 * kMmaStage; }
 
 cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const float *d_scales,
                               const int32_t *d_nnzb, cudaStream_t s) {
