@@ -16,8 +16,8 @@
 // Accumulators start at zero in TMEM (the epilogue clears what it reads),
 // so every MMA accumulates.
 //
-// Pipeline: a stage holds up to kEntStage entries (X slabs) and up to
-// kTileStage W tiles.  How a work item's entries fall into stages, and the
+// Pipeline: a stage holds up to StageGeom::ent entries (X slabs) and up to
+// StageGeom::tiles W tiles.  How a work item's entries fall into stages, and the
 // MMAs of each stage (one word per MMA: slab, first W tile, first tile row,
 // rows), is fixed by the plan, so stage_build_kernel writes it once per
 // plan (every call for dynamic plans) as stage records.  Two producer warps
@@ -51,18 +51,35 @@
 namespace spmm {
 namespace {
 
+// Launch geometry (compile-time; overridable for experiments)
 #ifndef SPMM_TC_CTAS
 #define SPMM_TC_CTAS 2      // CTAs per SM
-#define SPMM_TC_RCAP 16     // tile rows per group (accumulator columns / 16)
-#define SPMM_TC_STAGES 3
-#define SPMM_TC_ENT 4       // X slabs per stage
-#define SPMM_TC_TILES 32    // W tiles per stage (16-bit values; E4M3 stages hold 24)
 #endif
-constexpr int kEntStage = SPMM_TC_ENT;                            // X slabs per stage
+#ifndef SPMM_TC_RCAP
+#define SPMM_TC_RCAP 16     // tile rows per group (accumulator columns / 16)
+#endif
+#ifndef SPMM_TC_STAGES
+#define SPMM_TC_STAGES 3    // 16-bit weights: stages, X slabs and W tiles per stage
+#endif
+#ifndef SPMM_TC_ENT
+#define SPMM_TC_ENT 4
+#endif
+#ifndef SPMM_TC_TILES
+#define SPMM_TC_TILES 32
+#endif
+#ifndef SPMM_TC_STAGES8
+#define SPMM_TC_STAGES8 3   // E4M3 weights
+#endif
+#ifndef SPMM_TC_ENT8
+#define SPMM_TC_ENT8 4
+#endif
+#ifndef SPMM_TC_TILES8
+#define SPMM_TC_TILES8 24
+#endif
 constexpr int kSlabBytes = kTile * kNTile * 2;                    // 4096: 16 k x 128 n, 16-bit
 constexpr int kTileBytes8 = kTile * kTile;                        // 256: E4M3 tile, row-major
 constexpr int kScaleBytes = 16 * 4;                               // per slot: 4 x 4 sub-square scales
-constexpr int kStages = SPMM_TC_STAGES;
+constexpr int kStagesMax = SPMM_TC_STAGES > SPMM_TC_STAGES8 ? SPMM_TC_STAGES : SPMM_TC_STAGES8;
 constexpr int kRowCap = SPMM_TC_RCAP;
 constexpr int kAccCols = kRowCap * kTile;                         // TMEM columns per buffer
 constexpr int kMaxBatch = 64;                                     // problems per launch
@@ -71,8 +88,10 @@ constexpr int kMaxBatch = 64;                                     // problems pe
 // FP8 codes and their scales as loaded, which the converter warps expand
 // into the 16-bit area.
 template <bool W8> struct StageGeom {
-    static constexpr int tiles = W8 ? (SPMM_TC_TILES * 3) / 4 : SPMM_TC_TILES;
-    static constexpr int w16 = kEntStage * kSlabBytes;
+    static constexpr int stages = W8 ? SPMM_TC_STAGES8 : SPMM_TC_STAGES;
+    static constexpr int ent = W8 ? SPMM_TC_ENT8 : SPMM_TC_ENT;   // X slabs per stage
+    static constexpr int tiles = W8 ? SPMM_TC_TILES8 : SPMM_TC_TILES;
+    static constexpr int w16 = ent * kSlabBytes;
     static constexpr int w8 = w16 + tiles * kTileBytes16;
     static constexpr int sc = w8 + tiles * kTileBytes8;
     static constexpr int bytes = W8 ? sc + tiles * kScaleBytes : w8;
@@ -84,10 +103,10 @@ template <bool W8> struct StageGeom {
 // dependent scalar work allows; a second pipeline per SM doubles that rate.)
 constexpr int kAccBufs = 1;
 constexpr int kCtasPerSm = SPMM_TC_CTAS;
-static_assert(kRowCap <= kMaxGroupRows && (SPMM_TC_TILES * 3) / 4 >= kRowCap,
+static_assert(kRowCap <= kMaxGroupRows && SPMM_TC_TILES >= kRowCap && SPMM_TC_TILES8 >= kRowCap,
               "stage must hold a full entry");
 constexpr int kThreads = 288;
-constexpr int kXWarp0 = 6, kXWarp1 = 7;                           // X-slab producers (slabs 0-1, 2-3)
+constexpr int kXWarp0 = 6, kXWarp1 = 7;                           // X-slab producers (two halves)
 constexpr int kMmaWarpHi = 8;                                     // MMAs of tile rows 8-15
 constexpr int kProducers = 3;                                     // W + two X
 constexpr unsigned long long kWaitNs = 2000000000ull;             // 2 s per wait
@@ -98,14 +117,14 @@ constexpr unsigned long long kWaitNs = 2000000000ull;             // 2 s per wai
 // accumulator by tile rows (0-7 and 8-15; an interval crossing row 8 becomes
 // two MMAs), so each TMEM column is written by one warp in a fixed order.
 constexpr int kMmaStage = 32;                                     // MMAs per stage and row half (one per lane)
-static_assert(kEntStage <= 4, "a stage record holds four X columns");
+static_assert(SPMM_TC_ENT <= 12 && SPMM_TC_ENT8 <= 12, "a stage record holds 12 X columns");
 // Stage record (built before the launch; a work item's stages are records
 // e0, e0 + 1, ... where e0 is its first entry, since every stage holds at
 // least one entry): info (MMAs of rows 0-7 | MMAs of rows 8-15 << 6 |
 // entries << 12 | last << 31), W tiles, first W tile, the X column of each
 // entry; the stage's MMA program lives in a parallel array of 2 x kMmaStage
 // words per record, (rows 0-7 word, rows 8-15 word) pairs.
-constexpr int kRecWords = 8;
+constexpr int kRecWords = 16;
 struct StageMeta {
     uint32_t info;                 // as in the stage record
     uint32_t nslots;               // W tiles in the stage
@@ -113,8 +132,8 @@ struct StageMeta {
 };
 
 struct __align__(8) Smem {
-    uint64_t full[kStages], empty[kStages], conv[kStages], accf[kAccBufs], acce[kAccBufs];
-    StageMeta meta[kStages];
+    uint64_t full[kStagesMax], empty[kStagesMax], conv[kStagesMax], accf[kAccBufs], acce[kAccBufs];
+    StageMeta meta[kStagesMax];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
     int32_t issued[kProducers], consumed[2];   // per producer / per MMA warp
@@ -329,6 +348,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     using G = StageGeom<W8>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *stages = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int kStages = G::stages;
     Smem *sm = (Smem *)(stages + kStages * G::bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -388,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         // neither waits on a global load or decodes anything per stage.
         const bool wprod = warp == 0;
         const int pid = wprod ? 0 : (warp == kXWarp0 ? 1 : 2);
-        const int xlo = pid == 2 ? 2 : 0;   // first slab of this X producer
+
         int stage = 0;
         uint32_t phase = 0;
         int32_t issued = 0;
@@ -402,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             const int n0 = un.t * kNTile;
             // lane l: word (l & 7) of the record, and (W producer) program word l
             auto ld_rec = [&](int32_t r) -> uint32_t {
-                return r < e1 ? __ldg(P.srec + (int64_t)r * kRecWords + (lane & 7)) : 0u;
+                return r < e1 ? __ldg(P.srec + (int64_t)r * kRecWords + (lane & (kRecWords - 1))) : 0u;
             };
             auto ld_prog = [&](int32_t r) -> uint2 {
                 return (wprod && r < e1)
@@ -415,8 +435,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                 const uint32_t info = __shfl_sync(0xffffffffu, rc, 0);
                 const uint32_t nslots = __shfl_sync(0xffffffffu, rc, 1);
                 const uint32_t stb = __shfl_sync(0xffffffffu, rc, 2);
-                const uint32_t col = __shfl_sync(0xffffffffu, rc, 3 + xlo + (lane & 1));
                 const int nent = (int)((info >> 12) & 0xfu);
+                // X producer 1 requests slabs [0, h), producer 2 slabs [h, nent)
+                const int h = (nent + 1) >> 1;
+                const int xlo = pid == 2 ? h : 0, mine = pid == 2 ? nent - h : h;
+                const uint32_t col = __shfl_sync(0xffffffffu, rc, min(3 + xlo + lane, kRecWords - 1));
                 int w = 1;
                 if (lane == 0) w = mbar_wait(&sm->empty[stage], phase ^ 1, sm) ? 1 : 0;
                 if (!__shfl_sync(0xffffffffu, w, 0)) return -1;
@@ -445,7 +468,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                         mbar_arrive(&sm->full[stage]);
                     }
                 } else {
-                    const int mine = min(max(nent - xlo, 0), 2);
                     if (lane == 0) mbar_arrive_tx(&sm->full[stage], mine * kSlabBytes);
                     __syncwarp();
                     if (lane < mine) {
@@ -705,7 +727,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
         for (int i = 0; i < kProducers; ++i) hi = max(hi, sm->issued[i]);
         for (int32_t c = min(sm->consumed[0], sm->consumed[1]); c < hi; ++c) {
             const int s = c % kStages;
-            const uint32_t par = (uint32_t)((c / kStages) & 1);
+            const uint32_t par = (uint32_t)((c / kStages) & 1);   // kStages = G::stages
             // stand in for the arrivals of producers that stopped before stage c
             for (int i = 0; i < kProducers; ++i)
                 if (c >= sm->issued[i]) mbar_arrive(&sm->full[s]);
@@ -723,87 +745,83 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 }
 
 // ------------------------------------------------------- stage records ---
-// One warp per work item cuts the item's entries into stages exactly as the
-// producers consume them: consecutive entries while the stage holds at most
-// kEntStage X slabs, `tiles_cap` W tiles and kMmaStage MMAs per row half (one entry
-// always fits).  It writes the item's stage records at e0, e0 + 1, ... and
-// expands every entry's row intervals (runs of covered rows cut at
-// interval starts) into MMA words: slab | first W tile in the stage << 4 |
-// first tile row << 12 | rows << 16, one list per row half (an interval
-// across row 8 is cut there).  Dynamic plans read the item count and
-// the status word on the device (a rejected pattern builds nothing).
-__global__ void stage_build_kernel(const int32_t *__restrict__ items, int64_t n_items,
-                                   const int32_t *__restrict__ n_items_dev,
-                                   const int32_t *__restrict__ status,
-                                   const int32_t *__restrict__ ent_col,
-                                   const int32_t *__restrict__ ent_tbeg,
-                                   const int32_t *__restrict__ ent_cover, int tiles_cap,
-                                   uint32_t *__restrict__ srec, uint32_t *__restrict__ sprog) {
+// Stages never span two 32-entry batches of an item, so the batches are cut
+// independently: one CTA per work item, one warp per batch.  A warp cuts
+// its batch exactly as the producers consume it (consecutive entries while
+// the stage holds at most `ent_cap` X slabs, `tiles_cap` W tiles and
+// kMmaStage MMAs per row half; one entry always fits), counts its stages,
+// and after a CTA-wide prefix of the counts writes its records at
+// e0 + (stages of earlier batches) + i, expanding every entry's row
+// intervals (runs of covered rows cut at interval starts) into MMA words:
+// slab | first W tile in the stage << 4 | first tile row << 12 | rows << 16,
+// one list per row half (an interval across row 8 is cut there).  Dynamic
+// plans read the item count and the status word on the device (a rejected
+// pattern builds nothing).
+constexpr int kBuildWarps = 8;
+
+// One batch of entries: cuts its stages; with `write`, stores their records
+// starting at record index `rec`.  Returns the number of stages.
+__device__ int build_batch(int32_t eb, int32_t e1, int ent_cap, int tiles_cap,
+                           const int32_t *__restrict__ ent_col, const int32_t *__restrict__ ent_tbeg,
+                           const int32_t *__restrict__ ent_cover, bool last_batch, bool write,
+                           int32_t rec, uint32_t *__restrict__ srec, uint32_t *__restrict__ sprog) {
     const int lane = threadIdx.x & 31;
-    const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int64_t ni = n_items;
-    if (n_items_dev) {
-        if (*status != 0) return;
-        ni = min(ni, (int64_t)max(*n_items_dev, 0));
+    const int32_t e = eb + lane;
+    const bool valid = e < e1;
+    const int32_t mcol = valid ? ent_col[e] : 0;
+    const int32_t mtb = valid ? ent_tbeg[e] : 0;
+    const uint32_t mcov = valid ? (uint32_t)ent_cover[e] : 0u;
+    const uint32_t cov = mcov & 0xFFFFu;
+    // this entry's MMAs per row half: intervals below / above row 8, an
+    // interval across it counting in both
+    int nlo = 0, nhi = 0;
+    for (uint32_t st = mcov >> 16; st; st &= st - 1) {
+        const uint32_t r0 = __ffs(st) - 1;
+        const uint32_t rest = st & (st - 1);
+        const uint32_t next = rest ? (uint32_t)(__ffs(rest) - 1) : 16u;
+        uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;   // run of covered rows
+        len = len < next - r0 ? len : next - r0;
+        nlo += r0 < 8;
+        nhi += r0 + len > 8;
     }
-    if (item >= ni) return;
-    const int32_t *it = items + item * kItemFields;
-    const int32_t e0 = it[1], e1 = it[2];
-    int32_t rec = e0;
-    for (int32_t eb = e0; eb < e1; eb += 32) {
-        const int32_t e = eb + lane;
-        const bool valid = e < e1;
-        const int32_t mcol = valid ? ent_col[e] : 0;
-        const int32_t mtb = valid ? ent_tbeg[e] : 0;
-        const uint32_t mcov = valid ? (uint32_t)ent_cover[e] : 0u;
-        const uint32_t cov = mcov & 0xFFFFu;
-        // this entry's MMAs per row half: intervals below / above row 8, an
-        // interval across it counting in both
-        int nlo = 0, nhi = 0;
-        for (uint32_t st = mcov >> 16; st; st &= st - 1) {
-            const uint32_t r0 = __ffs(st) - 1;
-            const uint32_t rest = st & (st - 1);
-            const uint32_t next = rest ? (uint32_t)(__ffs(rest) - 1) : 16u;
-            uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;   // run of covered rows
-            len = len < next - r0 ? len : next - r0;
-            nlo += r0 < 8;
-            nhi += r0 + len > 8;
-        }
-        const int mslots = __popc(cov);
-        // inclusive prefix sums over the 32 entries: tiles, MMAs of each half
-        int S = mslots, L = nlo, H = nhi;
+    const int mslots = __popc(cov);
+    // inclusive prefix sums over the batch: tiles, MMAs of each half
+    int S = mslots, L = nlo, H = nhi;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int s2 = __shfl_up_sync(0xffffffffu, S, o);
-            const int l2 = __shfl_up_sync(0xffffffffu, L, o);
-            const int h2 = __shfl_up_sync(0xffffffffu, H, o);
-            if (lane >= o) {
-                S += s2;
-                L += l2;
-                H += h2;
-            }
+    for (int o = 1; o < 32; o <<= 1) {
+        const int s2 = __shfl_up_sync(0xffffffffu, S, o);
+        const int l2 = __shfl_up_sync(0xffffffffu, L, o);
+        const int h2 = __shfl_up_sync(0xffffffffu, H, o);
+        if (lane >= o) {
+            S += s2;
+            L += l2;
+            H += h2;
         }
-        const int cnt = min(32, e1 - eb);
-        for (int j = 0; j < cnt;) {
-            // sums are monotone: the fitting lanes are contiguous from j
-            const int Sb = j ? __shfl_sync(0xffffffffu, S, j - 1) : 0;
-            const int Lb = j ? __shfl_sync(0xffffffffu, L, j - 1) : 0;
-            const int Hb = j ? __shfl_sync(0xffffffffu, H, j - 1) : 0;
-            const bool fits = lane >= j && lane < j + kEntStage && lane < cnt &&
-                              S - Sb <= tiles_cap && L - Lb <= kMmaStage && H - Hb <= kMmaStage;
-            const int nent = __popc(__ballot_sync(0xffffffffu, fits));
+    }
+    const int cnt = min(32, e1 - eb);
+    int nst = 0;
+    for (int j = 0; j < cnt; ++nst) {
+        // sums are monotone: the fitting lanes are contiguous from j
+        const int Sb = j ? __shfl_sync(0xffffffffu, S, j - 1) : 0;
+        const int Lb = j ? __shfl_sync(0xffffffffu, L, j - 1) : 0;
+        const int Hb = j ? __shfl_sync(0xffffffffu, H, j - 1) : 0;
+        const bool fits = lane >= j && lane < j + ent_cap && lane < cnt && S - Sb <= tiles_cap &&
+                          L - Lb <= kMmaStage && H - Hb <= kMmaStage;
+        const int nent = __popc(__ballot_sync(0xffffffffu, fits));
+        if (write) {
             const int slots = __shfl_sync(0xffffffffu, S, j + nent - 1) - Sb;
             const int mlo = __shfl_sync(0xffffffffu, L, j + nent - 1) - Lb;
             const int mhi = __shfl_sync(0xffffffffu, H, j + nent - 1) - Hb;
             const int32_t stb = __shfl_sync(0xffffffffu, mtb, j);
             // record word 3 + i holds the X column of the stage's entry i
             const int32_t xc = __shfl_sync(0xffffffffu, mcol, min(j + max(lane - 3, 0), 31));
-            const bool last = (j + nent == cnt) && (eb + 32 >= e1);
+            const bool last = last_batch && j + nent == cnt;
+            const int32_t r = rec + nst;
             if (lane >= j && lane < j + nent) {
                 uint32_t klo = (uint32_t)(L - nlo - Lb), khi = (uint32_t)(H - nhi - Hb);
                 uint32_t toff = (uint32_t)(S - mslots - Sb);
                 const uint32_t slab = (uint32_t)(lane - j);
-                uint32_t *pr = sprog + (int64_t)rec * 2 * kMmaStage;
+                uint32_t *pr = sprog + (int64_t)r * 2 * kMmaStage;
                 for (uint32_t st = mcov >> 16; st; st &= st - 1) {
                     const uint32_t r0 = __ffs(st) - 1;
                     const uint32_t rest = st & (st - 1);
@@ -816,7 +834,8 @@ __global__ void stage_build_kernel(const int32_t *__restrict__ items, int64_t n_
                     }
                     if (r0 + len > 8) {
                         const uint32_t a = r0 < 8 ? 8u : r0;   // first row at or above 8
-                        pr[2 * khi++ + 1] = slab | (toff + (a - r0)) << 4 | a << 12 | (r0 + len - a) << 16;
+                        pr[2 * khi++ + 1] =
+                            slab | (toff + (a - r0)) << 4 | a << 12 | (r0 + len - a) << 16;
                     }
                     toff += len;
                 }
@@ -828,12 +847,54 @@ __global__ void stage_build_kernel(const int32_t *__restrict__ items, int64_t n_
                         (last ? 0x80000000u : 0u);
                 else if (lane == 1) v = (uint32_t)slots;
                 else if (lane == 2) v = (uint32_t)stb;
-                else if (lane < 3 + kEntStage) v = (lane - 3 < nent) ? (uint32_t)xc : 0u;
-                srec[(int64_t)rec * kRecWords + lane] = v;
+                else if (lane - 3 < nent) v = (uint32_t)xc;
+                srec[(int64_t)r * kRecWords + lane] = v;
             }
-            ++rec;
-            j += nent;
         }
+        j += nent;
+    }
+    return nst;
+}
+
+__global__ void __launch_bounds__(kBuildWarps * 32)
+    stage_build_kernel(const int32_t *__restrict__ items, int64_t n_items,
+                       const int32_t *__restrict__ n_items_dev, const int32_t *__restrict__ status,
+                       const int32_t *__restrict__ ent_col, const int32_t *__restrict__ ent_tbeg,
+                       const int32_t *__restrict__ ent_cover, int ent_cap, int tiles_cap,
+                       uint32_t *__restrict__ srec, uint32_t *__restrict__ sprog) {
+    __shared__ int32_t counts[kBuildWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t ni = n_items;
+    if (n_items_dev) {
+        if (*status != 0) return;
+        ni = min(ni, (int64_t)max(*n_items_dev, 0));
+    }
+    const int64_t item = blockIdx.x;
+    if (item >= ni) return;
+    const int32_t *it = items + item * kItemFields;
+    const int32_t e0 = it[1], e1 = it[2];
+    const int32_t nb = (e1 - e0 + 31) / 32;
+    int32_t base = e0;
+    for (int32_t b0 = 0; b0 < nb; b0 += kBuildWarps) {
+        const int32_t b = b0 + warp;
+        const bool active = b < nb;
+        const int32_t eb = e0 + 32 * b;
+        int nst = 0;
+        if (active)
+            nst = build_batch(eb, e1, ent_cap, tiles_cap, ent_col, ent_tbeg, ent_cover, false,
+                              false, 0, srec, sprog);
+        if (lane == 0) counts[warp] = nst;
+        __syncthreads();
+        int32_t off = base, tot = 0;
+        for (int w = 0; w < kBuildWarps; ++w) {
+            if (w < warp) off += counts[w];
+            tot += counts[w];
+        }
+        if (active)
+            build_batch(eb, e1, ent_cap, tiles_cap, ent_col, ent_tbeg, ent_cover, b == nb - 1,
+                        true, off, srec, sprog);
+        base += tot;
+        __syncthreads();
     }
 }
 
@@ -976,7 +1037,7 @@ cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
     if (B.total_units == 0) return cudaSuccess;
     const int64_t slots = (int64_t)sm_count * kCtasPerSm;
     const int grid = (int)(B.total_units < slots ? B.total_units : slots);
-    const size_t smem = 1024 + (size_t)kStages * StageGeom<W8>::bytes + sizeof(Smem);
+    const size_t smem = 1024 + (size_t)StageGeom<W8>::stages * StageGeom<W8>::bytes + sizeof(Smem);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(tc_kernel<T, W8>,
@@ -1108,11 +1169,12 @@ cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s) {
     const bool dyn = p->mode == SPMM_DYNAMIC;
     const int64_t ni = dyn ? p->dyn.items_cap : p->n_items;
     if (ni == 0 || !p->d_srec) return cudaSuccess;
-    const int tiles_cap = p->wdt == SPMM_E4M3 ? StageGeom<true>::tiles : StageGeom<false>::tiles;
-    const int64_t blocks = (ni + 3) / 4;   // 4 warps (items) per block
-    stage_build_kernel<<<(unsigned)blocks, 128, 0, s>>>(
+    const bool w8 = p->wdt == SPMM_E4M3;
+    const int tiles_cap = w8 ? StageGeom<true>::tiles : StageGeom<false>::tiles;
+    const int ent_cap = w8 ? StageGeom<true>::ent : StageGeom<false>::ent;
+    stage_build_kernel<<<(unsigned)ni, kBuildWarps * 32, 0, s>>>(
         p->d_items, ni, dyn ? p->d_counts + kCntItems : nullptr, p->d_status, p->d_ent_col,
-        p->d_ent_tbeg, p->d_ent_cover, tiles_cap, p->d_srec, p->d_sprog);
+        p->d_ent_tbeg, p->d_ent_cover, ent_cap, tiles_cap, p->d_srec, p->d_sprog);
     return cudaGetLastError();
 }
 
