@@ -7,6 +7,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "spmm_internal.h"
 
 namespace spmm {
@@ -103,38 +105,47 @@ __global__ void __launch_bounds__(256) gather_kernel(
 #pragma unroll
     for (int v = 0; v < V; ++v) acc[v] = 0.f;
     const T *xcol = X + (active ? c0 : 0);
-    for (int32_t base = beg; base < end; base += 32) {
-        const int32_t idx = base + lane;
-        const int32_t mycol = idx < end ? col_idx[idx] : 0;
-        const float myw = idx < end ? Vec<T>::to_f(vals[idx]) : 0.f;
-        const int cnt = min(32, end - base);
-        // t is warp-uniform so every shuffle has all 32 lanes; sub-group sg
-        // takes non-zeros t*G + sg, four of them in flight per lane
-        for (int t = 0; t * G < cnt; t += 4) {
-            int64_t cc[4];
-            float ww[4];
-            bool ok[4];
+    // kChunks chunks of 32 non-zeros per round: their indices and values are
+    // requested together, so a warp keeps several loads in flight
+    constexpr int kChunks = 8;
+    __shared__ int2 stage_cw[8][kChunks * 32];   // per warp: (column, weight bits) of a round
+    int2 *mine = stage_cw[threadIdx.x >> 5];
+    for (int32_t base0 = beg; base0 < end; base0 += 32 * kChunks) {
+        int32_t mycol[kChunks];
+        float myw[kChunks];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = (t + u) * G + sg;
-                ok[u] = j < cnt;
-                const int src = ok[u] ? j : 0;
-                cc[u] = __shfl_sync(0xffffffffu, mycol, src);
-                ww[u] = __shfl_sync(0xffffffffu, myw, src);
-            }
-            Pack<T, V> xv[4];
+        for (int q = 0; q < kChunks; ++q) {
+            const int32_t idx = base0 + 32 * q + lane;
+            mycol[q] = idx < end ? col_idx[idx] : 0;
+            myw[q] = idx < end ? Vec<T>::to_f(vals[idx]) : 0.f;
+        }
+        // sub-groups of LN lanes share non-zeros: stage the round's (column,
+        // weight) pairs in shared memory; sub-group sg takes non-zeros
+        // j = sg, sg + G, ... of every chunk, eight X loads in flight per lane
+        __syncwarp();
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (ok[u] && active) {
-                    xv[u] = *reinterpret_cast<const Pack<T, V> *>(xcol + cc[u] * ldx);
+        for (int q = 0; q < kChunks; ++q) mine[q * 32 + lane] = make_int2(mycol[q], __float_as_int(myw[q]));
+        __syncwarp();
+        const int nround = min(32 * kChunks, end - base0);
+        const int slots = (nround + G - 1) / G;   // non-zeros per sub-group this round
+        for (int f0 = 0; f0 < slots; f0 += 8) {
+            float ww[8];
+            Pack<T, V> xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int j = (f0 + u) * G + sg;
+                const bool ok = f0 + u < slots && j < nround && active;
+                const int2 cw = mine[ok ? j : 0];
+                ww[u] = ok ? __int_as_float(cw.y) : 0.f;
+                if (ok) {
+                    xv[u] = *reinterpret_cast<const Pack<T, V> *>(xcol + (int64_t)cw.x * ldx);
                 } else {
 #pragma unroll
                     for (int v = 0; v < V; ++v) xv[u].v[v] = Vec<T>::from_f(0.f);
-                    ww[u] = 0.f;
                 }
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
                 for (int v = 0; v < V; ++v) acc[v] = fmaf(ww[u], Vec<T>::to_f(xv[u].v[v]), acc[v]);
         }
@@ -153,6 +164,150 @@ __global__ void __launch_bounds__(256) gather_kernel(
         for (int v = 0; v < V; ++v) out.v[v] = Vec<T>::from_f(acc[v]);
         *reinterpret_cast<Pack<T, V> *>(Y + (int64_t)row * ldy + c0) = out;
     }
+}
+
+// n <= V (one vector per X row).  The row's indices and values stream in as
+// 16-byte / 8-byte vectors, four non-zeros per lane per load and kRounds
+// loads per lane in flight, and every lane gathers the X rows of its own
+// non-zeros.  With SX, X (k x n, at most a few hundred KB at these n) is
+// first copied into shared memory by the persistent block: a warp's 32
+// random X reads then cost a few bank wavefronts instead of 32 L1 lines,
+// which was the limit at n = 1 (about one cycle per non-zero per SM), and
+// the kernel is left bound by the HBM stream of indices and values.  The
+// lanes' sums meet in a fixed butterfly (deterministic).
+template <typename T, int V, bool SX>
+__global__ void __launch_bounds__(512) gather1_kernel(
+    const int32_t *__restrict__ items, int64_t n_items, const int32_t *__restrict__ col_idx,
+    const T *__restrict__ vals, const T *__restrict__ X, int64_t ldx, int64_t k, T *__restrict__ Y,
+    int64_t ldy, float *__restrict__ ws, const int64_t *__restrict__ ws_row0,
+    const int32_t *__restrict__ n_items_dev, const int32_t *__restrict__ status) {
+    constexpr int kRounds = 4;            // 4 x 4 non-zeros per lane per pass
+    extern __shared__ __align__(16) uint8_t xs_raw[];
+    const int lane = threadIdx.x & 31;
+    if (n_items_dev) {
+        if (*status != 0) return;
+        n_items = min(n_items, (int64_t)*n_items_dev);
+    }
+    const T *xb = X;
+    int64_t lx = ldx;
+    if (SX) {
+        T *xs = (T *)xs_raw;
+        for (int64_t i = threadIdx.x; i < k; i += blockDim.x)
+            *reinterpret_cast<Pack<T, V> *>(xs + i * V) =
+                *reinterpret_cast<const Pack<T, V> *>(X + i * ldx);
+        __syncthreads();
+        xb = xs;
+        lx = V;
+    }
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; item < n_items;
+         item += nwarps) {
+        const int32_t *it = items + item * kItemFields;
+        const int32_t row = it[0], beg = it[1], end = it[2], slot = it[5];
+        float acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0.f;
+        auto add = [&](int32_t c, float w) {
+            const Pack<T, V> x = *reinterpret_cast<const Pack<T, V> *>(xb + (int64_t)c * lx);
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = fmaf(w, Vec<T>::to_f(x.v[v]), acc[v]);
+        };
+        // head up to a multiple of 4 (vector alignment), one non-zero per lane
+        const int32_t h = min(end, (beg + 3) & ~3);
+        if (beg + lane < h) add(col_idx[beg + lane], Vec<T>::to_f(vals[beg + lane]));
+        // full passes: no bounds checks
+        int32_t base = h;
+        for (; base + 128 * kRounds <= end; base += 128 * kRounds) {
+            int4 c[kRounds];
+            Pack<T, 4> w[kRounds];
+#pragma unroll
+            for (int q = 0; q < kRounds; ++q) {
+                const int32_t i0 = base + 128 * q + 4 * lane;
+                c[q] = *reinterpret_cast<const int4 *>(col_idx + i0);
+                w[q] = *reinterpret_cast<const Pack<T, 4> *>(vals + i0);
+            }
+#pragma unroll
+            for (int q = 0; q < kRounds; ++q) {
+                add(c[q].x, Vec<T>::to_f(w[q].v[0]));
+                add(c[q].y, Vec<T>::to_f(w[q].v[1]));
+                add(c[q].z, Vec<T>::to_f(w[q].v[2]));
+                add(c[q].w, Vec<T>::to_f(w[q].v[3]));
+            }
+        }
+        // the last partial pass
+        for (; base < end; base += 128 * kRounds) {
+            int4 c[kRounds];
+            Pack<T, 4> w[kRounds];
+#pragma unroll
+            for (int q = 0; q < kRounds; ++q) {
+                const int32_t i0 = base + 128 * q + 4 * lane;
+                if (i0 + 3 < end) {
+                    c[q] = *reinterpret_cast<const int4 *>(col_idx + i0);
+                    w[q] = *reinterpret_cast<const Pack<T, 4> *>(vals + i0);
+                } else {
+                    c[q] = make_int4(i0 < end ? col_idx[i0] : 0, i0 + 1 < end ? col_idx[i0 + 1] : 0,
+                                     i0 + 2 < end ? col_idx[i0 + 2] : 0, 0);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        w[q].v[e] = i0 + e < end ? vals[i0 + e] : Vec<T>::from_f(0.f);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kRounds; ++q) {
+                const int32_t i0 = base + 128 * q + 4 * lane;
+                const int32_t cq[4] = {c[q].x, c[q].y, c[q].z, c[q].w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (i0 + e < end) add(cq[e], Vec<T>::to_f(w[q].v[e]));
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+        if (lane == 0) {
+            if (slot >= 0) {
+                float *dst = ws + ws_row0[slot] * (int64_t)V;   // n == V here
+#pragma unroll
+                for (int v = 0; v < V; ++v) dst[v] = acc[v];
+            } else {
+                Pack<T, V> out;
+#pragma unroll
+                for (int v = 0; v < V; ++v) out.v[v] = Vec<T>::from_f(acc[v]);
+                *reinterpret_cast<Pack<T, V> *>(Y + (int64_t)row * ldy) = out;
+            }
+        }
+    }
+}
+
+#ifndef SPMM_GATHER_SMEMX
+#define SPMM_GATHER_SMEMX (48 * 1024)   // X copied to shared memory up to this size
+#endif
+template <typename T, int V, bool SX>
+cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const void *X, int64_t ldx, void *Y,
+                           int64_t ldy, cudaStream_t s) {
+    const bool dyn = p->mode == SPMM_DYNAMIC;
+    const size_t smem = SX ? (size_t)p->k * V * sizeof(T) : 0;
+    if (SX) {
+        static bool attr = false;
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(gather1_kernel<T, V, SX>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 200 * 1024);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+    }
+    // persistent: as many 512-thread blocks as fit (shared memory allowing)
+    const int per_sm = SX ? (smem <= 100 * 1024 ? 2 : 1) : 4;
+    int64_t blocks = (n_items * 32 + 511) / 512;
+    const int64_t cap = (int64_t)std::max(p->sm_count, 1) * per_sm;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    gather1_kernel<T, V, SX><<<(unsigned)blocks, 512, smem, s>>>(
+        p->d_items, n_items, p->d_col_idx, (const T *)p->d_packed, (const T *)X, ldx, p->k,
+        (T *)Y, ldy, p->d_ws, p->d_ws_row0, dyn ? p->d_counts + kCntItems : nullptr, p->d_status);
+    return cudaGetLastError();
 }
 
 // ------------------------------------------------- split-row reduction ---
@@ -203,6 +358,12 @@ cudaError_t gather_launch(const spmm_plan *p, const void *X, int64_t n, int64_t 
     const int nchunk = (int)((n + (int64_t)LN * V - 1) / ((int64_t)LN * V));
     const int64_t warps = n_items * nchunk;
     if (warps == 0) return cudaSuccess;
+    if (vecs == 1) {
+        // n == V: one vector per X row; X in shared memory when it fits
+        if ((int64_t)p->k * V * (int64_t)sizeof(T) <= SPMM_GATHER_SMEMX)
+            return gather1_launch<T, V, true>(p, n_items, X, ldx, Y, ldy, s);
+        return gather1_launch<T, V, false>(p, n_items, X, ldx, Y, ldy, s);
+    }
     gather_kernel<T, V><<<grid1d(warps * 32, 256), 256, 0, s>>>(
         p->d_items, n_items, nchunk, LN, p->d_col_idx, (const T *)p->d_packed, (const T *)X,
         ldx, (T *)Y, ldy, n, p->d_ws, p->d_ws_row0, dyn ? p->d_counts + kCntItems : nullptr,

@@ -131,6 +131,13 @@ extern "C" spmm_status spmm_gather_noalloc(int64_t m, int64_t k, spmm_dtype dtyp
     p.mode = SPMM_DYNAMIC;
     p.wdt = p.xdt = dtype;
     p.kernel = SPMM_KERNEL_GATHER;
+    {
+        // grid sizing of the persistent gather (an attribute query, no allocation)
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&p.sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            p.sm_count = 1;
+    }
     p.dyn.row_cnt = (int32_t *)(sc + oRowCnt);
     p.dyn.cursor = (int32_t *)(sc + oCursor);
     p.dyn.row_ibeg = (int32_t *)(sc + oRowIbeg);

@@ -225,3 +225,19 @@ def test_full_size_sweep_sampled(b):
     Yo, wf, X = _sub_oracle(c, rows, dt)
     Ys = torch.cat([Y[r * b:(r + 1) * b] for r in rows])
     assert oracle.normwise_err(Ys, Yo, wf, X) <= 4e-3
+
+
+@pytest.mark.parametrize("n", [1, 32])
+def test_gather_large_small_n_sampled(n):
+    """The configuration the benchmark's small-n gather section times:
+    m = k = 16384, d = 1/16, FP16; 4 sampled rows against the oracle."""
+    m = k = 16384
+    c = wl.problem(7, m, k, 32, 1, wl.nnzb_for(m, k, 1, 1 / 16))
+    dt = torch.float16
+    plan = S.Plan(m, k, 32, 1, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"], kernel="gather")
+    plan.pack(torch.from_numpy(c["vals"].reshape(-1)).to(dt).cuda())
+    cn = dict(c, X=c["X"][:, :n].copy())
+    Y = plan.run(torch.from_numpy(cn["X"]).to(dt).cuda()).cpu()
+    rows = [0, 4097, 9000, m - 1]
+    Yo, wf, X = _sub_oracle(cn, rows, dt)
+    assert oracle.normwise_err(Y[rows], Yo, wf, X) <= 4e-3
