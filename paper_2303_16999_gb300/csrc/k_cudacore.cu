@@ -20,7 +20,9 @@ namespace {
 template <typename U>
 __global__ void pack_csr_kernel(const U *__restrict__ vals, const int32_t *__restrict__ perm,
                                 int64_t nnzb, int bb, const int32_t *__restrict__ nnzb_dev,
-                                U *__restrict__ out) {
+                                const int32_t *__restrict__ status, U *__restrict__ out) {
+    // dynamic plans: a rejected pattern leaves perm incomplete; pack nothing
+    if (status && *status != 0) return;
     if (nnzb_dev) nnzb = min((int64_t)max(*nnzb_dev, 0), nnzb);
     const int64_t total = nnzb * bb;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
@@ -396,14 +398,17 @@ cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, const int3
     const int64_t total = nmax * bb;
     if (total == 0) return cudaSuccess;
     const unsigned g = grid1d(total, 256) > 4096u ? 4096u : grid1d(total, 256);
+    const int32_t *st = d_nnzb ? p->d_status : nullptr;
     switch (dtype_size(p->wdt)) {
         case 4:
             pack_csr_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t *)d_values, p->d_perm,
-                                                        nmax, bb, d_nnzb, (uint32_t *)p->d_packed);
+                                                        nmax, bb, d_nnzb, st,
+                                                        (uint32_t *)p->d_packed);
             break;
         case 2:
             pack_csr_kernel<uint16_t><<<g, 256, 0, s>>>((const uint16_t *)d_values, p->d_perm,
-                                                        nmax, bb, d_nnzb, (uint16_t *)p->d_packed);
+                                                        nmax, bb, d_nnzb, st,
+                                                        (uint16_t *)p->d_packed);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -435,9 +440,16 @@ cudaError_t launch_reduce(const spmm_plan *p, int64_t n, void *Y, int64_t ldy, c
     if (n_red == 0 || n == 0) return cudaSuccess;
     const bool tc = p->kernel == SPMM_KERNEL_TC;
     const int rows_per_unit = tc ? kTile : 1;
-    const unsigned gy = tc ? (unsigned)(kMaxGroupRows * kTile) : 1u;
-    dim3 grid(grid1d(n, 128) > 64u ? 64u : grid1d(n, 128), gy,
-              (unsigned)(n_red < 65535 ? n_red : 65535));
+    // about two waves of blocks whatever the capacity: every loop of the
+    // kernel strides, and a dynamic plan's capacity (launched in full, its
+    // true count read on the device) is usually far above the reductions
+    // it has
+    const unsigned gx = grid1d(n, 128) > 64u ? 64u : grid1d(n, 128);
+    const unsigned gz = (unsigned)(n_red < 64 ? n_red : 64);
+    const int64_t want = 2 * 16 * (int64_t)std::max(p->sm_count, 1);
+    int64_t gy = tc ? (int64_t)(kMaxGroupRows * kTile) : 1;
+    gy = std::max<int64_t>(1, std::min<int64_t>(gy, want / ((int64_t)gx * gz)));
+    dim3 grid(gx, (unsigned)gy, gz);
     const int32_t *r0 = tc ? p->d_grp_row0 : nullptr;
     const int32_t *rn = tc ? p->d_grp_rows : nullptr;
     switch (p->xdt) {

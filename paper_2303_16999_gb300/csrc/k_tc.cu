@@ -757,7 +757,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 // one list per row half (an interval across row 8 is cut there).  Dynamic
 // plans read the item count and the status word on the device (a rejected
 // pattern builds nothing).
-constexpr int kBuildWarps = 8;
+constexpr int kBuildWarps = 16;
 
 // One batch of entries: cuts its stages; with `write`, stores their records
 // starting at record index `rec`.  Returns the number of stages.
@@ -902,22 +902,38 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
 // Tile layout of the MMA B operand, K-major without swizzle: 8 x 8 core
 // matrices of 128 contiguous bytes; element (i = row of W in the tile,
 // j = column) at byte (i/8)*256 + (j/8)*128 + (i%8)*16 + (j%8)*2.
-template <typename U>
+// One thread per (block, row, segment of SEG columns): it reads SEG
+// consecutive values of the block row and writes them as one piece of an
+// 8 x 8 core-matrix row (SEG = min(b, 8): 8 or 16 bytes of 16-bit values;
+// SEG = 1 for values not aligned to a segment).
+template <typename U, int B, int SEG>
 __global__ void pack_tiles_kernel(const U *__restrict__ vals, const int32_t *__restrict__ blk_slot,
-                                  const int32_t *__restrict__ blk_off, int64_t nnzb, int b,
-                                  const int32_t *__restrict__ nnzb_dev, U *__restrict__ out) {
+                                  const int32_t *__restrict__ blk_off, int64_t nnzb,
+                                  const int32_t *__restrict__ nnzb_dev,
+                                  const int32_t *__restrict__ status, U *__restrict__ out) {
+    // dynamic plans: a rejected pattern leaves blk_slot / blk_off incomplete
+    if (status && *status != 0) return;
+    constexpr int kSeg = SEG;                           // values per thread
+    constexpr int kPer = B * (B / kSeg);                // threads per block
     if (nnzb_dev) nnzb = min((int64_t)max(*nnzb_dev, 0), nnzb);
-    const int bb = b * b;
-    const int64_t total = nnzb * bb;
+    const int64_t total = nnzb * kPer;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = t / bb;
-        const int e = (int)(t - p * bb);
+        const int64_t p = t / kPer;
+        const int r = (int)(t - p * kPer);
+        const int i = r / (B / kSeg), seg = r % (B / kSeg);   // block row, segment
         const int off = blk_off[p];
-        const int ti = off / kTile + e / b, tj = off % kTile + e % b;
-        const int64_t dst = (int64_t)blk_slot[p] * (kTile * kTile) + (ti >> 3) * 128 +
-                            (tj >> 3) * 64 + (ti & 7) * 8 + (tj & 7);
-        out[dst] = vals[t];
+        const int ti = off / kTile + i, tj = off % kTile + seg * kSeg;
+        const U *src = vals + p * (B * B) + i * B + seg * kSeg;
+        U *dst = out + (int64_t)blk_slot[p] * (kTile * kTile) + (ti >> 3) * 128 + (tj >> 3) * 64 +
+                 (ti & 7) * 8 + (tj & 7);
+        if constexpr (kSeg == 8) {
+            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(src);
+        } else if constexpr (kSeg == 4) {
+            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(src);
+        } else {
+            *dst = *src;
+        }
     }
 }
 
@@ -928,8 +944,10 @@ __global__ void pack_tiles_e4m3_kernel(const uint8_t *__restrict__ codes,
                                        const float *__restrict__ scales,
                                        const int32_t *__restrict__ blk_slot,
                                        const int32_t *__restrict__ blk_off, int64_t nnzb, int b,
-                                       const int32_t *__restrict__ nnzb_dev, uint8_t *__restrict__ out,
+                                       const int32_t *__restrict__ nnzb_dev,
+                                       const int32_t *__restrict__ status, uint8_t *__restrict__ out,
                                        float *__restrict__ tile_scale) {
+    if (status && *status != 0) return;   // rejected dynamic pattern
     if (nnzb_dev) nnzb = min((int64_t)max(*nnzb_dev, 0), nnzb);
     const int bb = b * b;
     const int64_t total = nnzb * bb;
@@ -1197,13 +1215,35 @@ cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const fl
         if (e != cudaSuccess) return e;
         pack_tiles_e4m3_kernel<<<(unsigned)g, 256, 0, s>>>(
             (const uint8_t *)d_values, d_scales, p->d_blk_slot, p->d_blk_off, nmax, p->b, d_nnzb,
-            (uint8_t *)p->d_packed, p->d_tile_scale);
+            d_nnzb ? p->d_status : nullptr, (uint8_t *)p->d_packed, p->d_tile_scale);
         return cudaGetLastError();
     }
     if (p->wdt != SPMM_F16 && p->wdt != SPMM_BF16) return cudaErrorNotSupported;
-    pack_tiles_kernel<uint16_t><<<(unsigned)g, 256, 0, s>>>(
-        (const uint16_t *)d_values, p->d_blk_slot, p->d_blk_off, nmax, p->b, d_nnzb,
-        (uint16_t *)p->d_packed);
+    const uint16_t *v = (const uint16_t *)d_values;
+    uint16_t *o = (uint16_t *)p->d_packed;
+    // vector loads need the values aligned to a block row segment
+    const bool al = ((uintptr_t)v % 16) == 0;
+    const unsigned gb = (unsigned)std::min<int64_t>(8192, (nmax * p->b * 2 + 255) / 256);
+    const unsigned g1 = (unsigned)std::min<int64_t>(8192, (total + 255) / 256);
+    const int32_t *bs = p->d_blk_slot, *bo = p->d_blk_off;
+    const int32_t *st = d_nnzb ? p->d_status : nullptr;
+    switch (p->b) {
+        case 16:
+            if (al) pack_tiles_kernel<uint16_t, 16, 8><<<gb, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
+            else pack_tiles_kernel<uint16_t, 16, 1><<<g1, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
+            break;
+        case 8:
+            if (al) pack_tiles_kernel<uint16_t, 8, 8><<<gb, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
+            else pack_tiles_kernel<uint16_t, 8, 1><<<g1, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
+            break;
+        case 4:
+            if (al) pack_tiles_kernel<uint16_t, 4, 4><<<gb, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
+            else pack_tiles_kernel<uint16_t, 4, 1><<<g1, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
+            break;
+        default:
+            pack_tiles_kernel<uint16_t, 1, 1><<<g1, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
+            break;
+    }
     return cudaGetLastError();
 }
 
