@@ -312,6 +312,19 @@ cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const void *X, i
     return cudaGetLastError();
 }
 
+// Dense rows (ld = n) -> rows of stride ld (serving: X staged in one
+// contiguous copy, re-strided for the kernels' aligned rows).
+template <typename E>
+__global__ void restride_kernel(const E *__restrict__ src, E *__restrict__ dst, int64_t rows,
+                                int64_t n, int64_t ld) {
+    const int64_t total = rows * n;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / n, c = t - r * n;
+        dst[r * ld + c] = src[t];
+    }
+}
+
 // ------------------------------------------------- split-row reduction ---
 // Rows split over several items: Y = sum of the chunks' FP32 partials in
 // chunk order (deterministic), converted once.
@@ -390,6 +403,20 @@ cudaError_t gather_dispatch(const spmm_plan *p, const void *X, int64_t n, int64_
 }
 
 }  // namespace
+
+cudaError_t launch_restride(const void *src, void *dst, int64_t rows, int64_t n, int64_t ld,
+                            size_t elem, cudaStream_t s) {
+    const int64_t total = rows * n;
+    if (total == 0) return cudaSuccess;
+    const unsigned g = grid1d(total, 256) > 2048u ? 2048u : grid1d(total, 256);
+    if (elem == 2)
+        restride_kernel<uint16_t><<<g, 256, 0, s>>>((const uint16_t *)src, (uint16_t *)dst, rows, n, ld);
+    else if (elem == 4)
+        restride_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t *)src, (uint32_t *)dst, rows, n, ld);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, const int32_t *d_nnzb,
                             cudaStream_t s) {

@@ -217,9 +217,23 @@ void serve_server::batcher_loop() {
         cudaStream_t s = streams[slot];
         cudaError_t e = cudaSuccess;
         for (int i = 0; i < cnt && e == cudaSuccess; ++i) {
+            // X arrives dense (ld = n) but the tensor map needs 16-byte rows:
+            // one contiguous copy, then (n not a multiple of 8) a re-stride
+            // on the device out of the Y staging, which is free until the
+            // product and at least as large when m >= k; a strided copy of
+            // k short rows is the fallback
             const size_t es = es_of(plans[i]);
-            e = cudaMemcpy2DAsync((void *)xs[i], lxs[i] * es, hx[i], ns[i] * es, ns[i] * es,
-                                  plans[i]->k, cudaMemcpyHostToDevice, s);
+            const int64_t k = plans[i]->k, m = plans[i]->m;
+            if (lxs[i] == ns[i]) {
+                e = cudaMemcpyAsync((void *)xs[i], hx[i], k * ns[i] * es, cudaMemcpyHostToDevice, s);
+            } else if (m >= k) {
+                e = cudaMemcpyAsync(ys[i], hx[i], k * ns[i] * es, cudaMemcpyHostToDevice, s);
+                if (e == cudaSuccess)
+                    e = launch_restride(ys[i], (void *)xs[i], k, ns[i], lxs[i], es, s);
+            } else {
+                e = cudaMemcpy2DAsync((void *)xs[i], lxs[i] * es, hx[i], ns[i] * es, ns[i] * es, k,
+                                      cudaMemcpyHostToDevice, s);
+            }
         }
         if (e == cudaSuccess) {
             if (tc) {

@@ -129,6 +129,9 @@ cudaError_t launch_plain(const spmm_plan *p, const void *d_X, int64_t n, int64_t
                          int64_t ldy, cudaStream_t s);
 cudaError_t launch_gather(const spmm_plan *p, const void *d_X, int64_t n, int64_t ldx, void *d_Y,
                           int64_t ldy, cudaStream_t s);
+// dense rows (ld = n) of 2- or 4-byte values -> stride ld, on the device
+cudaError_t launch_restride(const void *src, void *dst, int64_t rows, int64_t n, int64_t ld,
+                            size_t elem, cudaStream_t s);
 // TC stage records of every work item (plan arrays only; no values)
 cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s);
 int64_t stage_record_words();
