@@ -137,14 +137,22 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def max_over_ranks(x, world, device="cuda"):
+    """The slowest rank's time (every rank gets it)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(flop_per_rank_step, steps, world, seconds_max):
+    """Whole-job TFLOP/s: every rank runs the same step (weak scaling), so
+    the job did world x steps x the per-rank FLOPs in the slowest rank's
+    time."""
+    return flop_per_rank_step * steps * world / seconds_max / 1e12
 
 
 # ---------------------------------------------------------- sweep points
@@ -353,7 +361,7 @@ def main():
     per = [statistics.median(evs[s_][i][0].elapsed_time(evs[s_][i][1])
                              for s_ in range(args.steps)) for i in range(len(pts))]
     flops_step = sum(2.0 * p["nnzb"] * p["b"] ** 2 * N for p in pts)
-    value = flops_step * args.steps * world / (t_ms * 1e-3) / 1e12
+    value = job_throughput(flops_step, args.steps, world, t_ms * 1e-3)
 
     points, fam = [], {}
     for i, p in enumerate(pts):
@@ -394,7 +402,7 @@ def main():
             p["plan"].run_host(p["Xh"], p["Yh"])
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, world)
-    e2e = {"value": flops_step * args.e2e_steps * world / e2e_s / 1e12, "unit": "TFLOP/s",
+    e2e = {"value": job_throughput(flops_step, args.e2e_steps, world, e2e_s), "unit": "TFLOP/s",
            "h2d_bytes_per_step": sum(p["Xh"].numel() * 2 for p in pts),
            "d2h_bytes_per_step": sum(p["Yh"].numel() * 2 for p in pts),
            "steps": args.e2e_steps}

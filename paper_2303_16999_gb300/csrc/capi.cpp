@@ -653,13 +653,17 @@ spmm_status spmm_run_host(spmm_plan *plan, const void *h_X, int64_t n, int64_t l
     }
     if (e != cudaSuccess) return cuda_fail(e, "staging allocation");
     if (n > 0) {
-        e = cudaMemcpy2DAsync(plan->d_xbuf, n * es, h_X, ldx * es, n * es, plan->k,
-                              cudaMemcpyHostToDevice, s);
+        // one contiguous copy when the host rows are dense (a pitched copy
+        // moves k short rows one by one)
+        e = ldx == n ? cudaMemcpyAsync(plan->d_xbuf, h_X, plan->k * n * es, cudaMemcpyHostToDevice, s)
+                     : cudaMemcpy2DAsync(plan->d_xbuf, n * es, h_X, ldx * es, n * es, plan->k,
+                                         cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return cuda_fail(e, "X upload");
         st = launch_product(plan, plan->d_xbuf, n, n, plan->d_ybuf, n, s);
         if (st != SPMM_OK) return st;
-        e = cudaMemcpy2DAsync(h_Y, ldy * es, plan->d_ybuf, n * es, n * es, plan->m,
-                              cudaMemcpyDeviceToHost, s);
+        e = ldy == n ? cudaMemcpyAsync(h_Y, plan->d_ybuf, plan->m * n * es, cudaMemcpyDeviceToHost, s)
+                     : cudaMemcpy2DAsync(h_Y, ldy * es, plan->d_ybuf, n * es, n * es, plan->m,
+                                         cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) return cuda_fail(e, "Y download");
     }
     st = finish_call(plan, s);

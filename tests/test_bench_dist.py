@@ -1,0 +1,75 @@
+"""The benchmark's multi-rank logic on CPU: two gloo ranks (the GPU launch
+uses NCCL over one process per GPU; every GPU run here has one GPU).
+Checks the barrier, the max-over-ranks timing, the whole-job throughput
+and that the reference arm prints on rank 0 only."""
+import importlib.util
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    dist.init_process_group("gloo", init_method="tcp://127.0.0.1:%d" % port, rank=rank,
+                            world_size=world)
+    b = _bench()
+    b.barrier(world)
+    t = 1.0 + rank                       # rank 1 is the slow one
+    tmax = b.max_over_ranks(t, world, device="cpu")
+    value = b.job_throughput(2.0e12, 3, world, tmax)
+    out[rank] = (tmax, value)
+    b.barrier(world)
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks():
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        out = man.dict()
+        mp.start_processes(_rank, args=(2, port, out), nprocs=2, join=True, start_method="spawn")
+        res = dict(out)
+    assert res[0][0] == res[1][0] == 2.0                  # max over ranks
+    assert res[0][1] == res[1][1] == pytest.approx(6.0)   # 2 ranks x 3 steps x 2 TFLOP / 2 s
+
+
+def test_single_rank_is_identity():
+    b = _bench()
+    assert b.max_over_ranks(1.5, 1) == 1.5
+    assert b.job_throughput(1e12, 4, 1, 2.0) == pytest.approx(2.0)
+
+
+@pytest.mark.parametrize("rank,prints", [("0", True), ("1", False)])
+def test_reference_arm_prints_on_rank0_only(rank, prints):
+    env = dict(os.environ, RANK=rank, WORLD_SIZE="2", LOCAL_RANK=rank)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", "1", "--warmup", "0", "--gpus", "2"],
+                       env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert bool(lines) == prints
+    if prints:
+        import json
+        d = json.loads(lines[-1])
+        assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
