@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -396,6 +397,8 @@ spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spm
             p->n_groups = (int64_t)p->hp.grp_rows.size();
             p->n_entries = (int64_t)p->hp.ent_col.size();
             p->n_tiles = (int64_t)p->hp.tile_row.size();
+            if (kernel == SPMM_KERNEL_TC && p->n_entries > 0)
+                p->tc_geo = tc_geometry((double)p->n_tiles / (double)p->n_entries);
         } else {
             p->nnzb_max = nnzb_max;
             if (kernel == SPMM_KERNEL_TC) {
@@ -413,6 +416,16 @@ spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spm
                     acc += v;
                 }
                 p->n_groups = (int64_t)sz.size();
+                // expected tiles per entry of a random pattern at nnzb_max:
+                // a 16 x 16 tile is non-empty with probability q, an entry
+                // (column of a group of R tile rows) holds R q / (1 - (1-q)^R)
+                const double cells = (double)(m / b) * (double)(k / b);
+                const double dm = cells > 0 ? std::min(1.0, (double)nnzb_max / cells) : 0.0;
+                const double per = (double)(kTile / b) * (double)(kTile / b);
+                const double q = 1.0 - std::pow(1.0 - dm, per);
+                const double R = (double)p->R;
+                const double hit = 1.0 - std::pow(1.0 - q, R);
+                p->tc_geo = tc_geometry(hit > 0 ? R * q / hit : 0.0);
             } else if (kernel == SPMM_KERNEL_PLAIN) {
                 set_error("dynamic plans use the GATHER (b = 1) or TC (b >= 4) kernels");
                 free_plan(p);

@@ -58,17 +58,33 @@ namespace {
 #ifndef SPMM_TC_RCAP
 #define SPMM_TC_RCAP 16     // tile rows per group (accumulator columns / 16)
 #endif
-#ifndef SPMM_TC_STAGES
-#define SPMM_TC_STAGES 3    // 16-bit weights: stages, X slabs and W tiles per stage
+// Stage geometries of 16-bit weights (stages, X slabs and W tiles per
+// stage, all in about 110 KB of shared memory per CTA).  The plan picks one
+// by its tiles per entry: few-tile entries (sparse tiles) need many slabs
+// per stage to amortise the stage's fixed costs, many-tile entries need
+// room for their tiles.  Measured on m = k = 4096, n = 2048: the dense
+// geometry takes b=1 d=1/4 from 70 to 58 us, the sparse one b=16 d=1/32
+// from 25 to 21 us, against one geometry of 4 slabs x 32 tiles x 3 stages.
+#ifndef SPMM_TC_STAGES_D
+#define SPMM_TC_STAGES_D 2  // dense: 4 slabs, 64 tiles
 #endif
-#ifndef SPMM_TC_ENT
-#define SPMM_TC_ENT 4
+#ifndef SPMM_TC_ENT_D
+#define SPMM_TC_ENT_D 4
 #endif
-#ifndef SPMM_TC_TILES
-#define SPMM_TC_TILES 32
+#ifndef SPMM_TC_TILES_D
+#define SPMM_TC_TILES_D 64
+#endif
+#ifndef SPMM_TC_STAGES_S
+#define SPMM_TC_STAGES_S 2  // sparse: 8 slabs, 44 tiles
+#endif
+#ifndef SPMM_TC_ENT_S
+#define SPMM_TC_ENT_S 8
+#endif
+#ifndef SPMM_TC_TILES_S
+#define SPMM_TC_TILES_S 44
 #endif
 #ifndef SPMM_TC_STAGES8
-#define SPMM_TC_STAGES8 3   // E4M3 weights
+#define SPMM_TC_STAGES8 3   // E4M3 weights (one geometry)
 #endif
 #ifndef SPMM_TC_ENT8
 #define SPMM_TC_ENT8 4
@@ -79,7 +95,7 @@ namespace {
 constexpr int kSlabBytes = kTile * kNTile * 2;                    // 4096: 16 k x 128 n, 16-bit
 constexpr int kTileBytes8 = kTile * kTile;                        // 256: E4M3 tile, row-major
 constexpr int kScaleBytes = 16 * 4;                               // per slot: 4 x 4 sub-square scales
-constexpr int kStagesMax = SPMM_TC_STAGES > SPMM_TC_STAGES8 ? SPMM_TC_STAGES : SPMM_TC_STAGES8;
+constexpr int kStagesMax = 3;                                     // >= every geometry's stages
 constexpr int kRowCap = SPMM_TC_RCAP;
 constexpr int kAccCols = kRowCap * kTile;                         // TMEM columns per buffer
 constexpr int kMaxBatch = 64;                                     // problems per launch
@@ -87,10 +103,12 @@ constexpr int kMaxBatch = 64;                                     // problems pe
 // Stage layout: X slabs | 16-bit W tiles (MMA B operand) | (E4M3 only) the
 // FP8 codes and their scales as loaded, which the converter warps expand
 // into the 16-bit area.
-template <bool W8> struct StageGeom {
-    static constexpr int stages = W8 ? SPMM_TC_STAGES8 : SPMM_TC_STAGES;
-    static constexpr int ent = W8 ? SPMM_TC_ENT8 : SPMM_TC_ENT;   // X slabs per stage
-    static constexpr int tiles = W8 ? SPMM_TC_TILES8 : SPMM_TC_TILES;
+// GEO: 0 = dense, 1 = sparse (16-bit weights); E4M3 has one geometry.
+template <bool W8, int GEO> struct StageGeom {
+    static constexpr int stages = W8 ? SPMM_TC_STAGES8 : (GEO ? SPMM_TC_STAGES_S : SPMM_TC_STAGES_D);
+    static constexpr int ent = W8 ? SPMM_TC_ENT8 : (GEO ? SPMM_TC_ENT_S : SPMM_TC_ENT_D);   // X slabs
+    static constexpr int tiles = W8 ? SPMM_TC_TILES8 : (GEO ? SPMM_TC_TILES_S : SPMM_TC_TILES_D);
+    static_assert(stages <= kStagesMax && ent <= 12 && tiles >= 16, "stage geometry");
     static constexpr int w16 = ent * kSlabBytes;
     static constexpr int w8 = w16 + tiles * kTileBytes16;
     static constexpr int sc = w8 + tiles * kTileBytes8;
@@ -103,8 +121,7 @@ template <bool W8> struct StageGeom {
 // dependent scalar work allows; a second pipeline per SM doubles that rate.)
 constexpr int kAccBufs = 1;
 constexpr int kCtasPerSm = SPMM_TC_CTAS;
-static_assert(kRowCap <= kMaxGroupRows && SPMM_TC_TILES >= kRowCap && SPMM_TC_TILES8 >= kRowCap,
-              "stage must hold a full entry");
+static_assert(kRowCap <= kMaxGroupRows && kRowCap <= 16, "a stage must hold a full entry");
 constexpr int kThreads = 288;
 constexpr int kXWarp0 = 6, kXWarp1 = 7;                           // X-slab producers (two halves)
 constexpr int kMmaWarpHi = 8;                                     // MMAs of tile rows 8-15
@@ -117,7 +134,7 @@ constexpr unsigned long long kWaitNs = 2000000000ull;             // 2 s per wai
 // accumulator by tile rows (0-7 and 8-15; an interval crossing row 8 becomes
 // two MMAs), so each TMEM column is written by one warp in a fixed order.
 constexpr int kMmaStage = 32;                                     // MMAs per stage and row half (one per lane)
-static_assert(SPMM_TC_ENT <= 12 && SPMM_TC_ENT8 <= 12, "a stage record holds 12 X columns");
+// (StageGeom checks that a stage record's 12 X columns suffice)
 // Stage record (built before the launch; a work item's stages are records
 // e0, e0 + 1, ... where e0 is its first entry, since every stage holds at
 // least one entry): info (MMAs of rows 0-7 | MMAs of rows 8-15 << 6 |
@@ -342,10 +359,10 @@ __device__ __forceinline__ Unit decode_unit(const TcBatch &B, int64_t u) {
     return r;
 }
 
-template <typename T, bool W8>
+template <typename T, bool W8, int GEO>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     tc_kernel(const __grid_constant__ TcBatch B) {
-    using G = StageGeom<W8>;
+    using G = StageGeom<W8, GEO>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *stages = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int kStages = G::stages;
@@ -1050,27 +1067,33 @@ void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, i
     P.x3d = x3d;
 }
 
-template <typename T, bool W8>
+template <typename T, bool W8, int GEO>
 cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
     if (B.total_units == 0) return cudaSuccess;
     const int64_t slots = (int64_t)sm_count * kCtasPerSm;
     const int grid = (int)(B.total_units < slots ? B.total_units : slots);
-    const size_t smem = 1024 + (size_t)StageGeom<W8>::stages * StageGeom<W8>::bytes + sizeof(Smem);
+    using G = StageGeom<W8, GEO>;
+    const size_t smem = 1024 + (size_t)G::stages * G::bytes + sizeof(Smem);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_kernel<T, W8>,
+        cudaError_t e = cudaFuncSetAttribute(tc_kernel<T, W8, GEO>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    tc_kernel<T, W8><<<grid, kThreads, smem, s>>>(B);
+    tc_kernel<T, W8, GEO><<<grid, kThreads, smem, s>>>(B);
     return cudaGetLastError();
 }
 
-cudaError_t dispatch_batch(const TcBatch &B, bool bf16, bool w8, int sm_count, cudaStream_t s) {
-    if (bf16) return w8 ? launch_batch<__nv_bfloat16, true>(B, sm_count, s)
-                        : launch_batch<__nv_bfloat16, false>(B, sm_count, s);
-    return w8 ? launch_batch<__half, true>(B, sm_count, s) : launch_batch<__half, false>(B, sm_count, s);
+template <typename T>
+cudaError_t launch_geo(const TcBatch &B, int geo, bool w8, int sm_count, cudaStream_t s) {
+    if (w8) return launch_batch<T, true, 0>(B, sm_count, s);   // E4M3: one geometry
+    return geo ? launch_batch<T, false, 1>(B, sm_count, s) : launch_batch<T, false, 0>(B, sm_count, s);
+}
+cudaError_t dispatch_batch(const TcBatch &B, int geo, bool bf16, bool w8, int sm_count,
+                           cudaStream_t s) {
+    return bf16 ? launch_geo<__nv_bfloat16>(B, geo, w8, sm_count, s)
+                : launch_geo<__half>(B, geo, w8, sm_count, s);
 }
 
 // Cached launch schedules of batches: (problem, unit) pairs of all problems,
@@ -1108,13 +1131,50 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
         e = launch_stage_build(p, s);
         if (e != cudaSuccess) return e;
     }
-    return dispatch_batch(B, p->xdt == SPMM_BF16, p->wdt == SPMM_E4M3, p->sm_count, s);
+    return dispatch_batch(B, p->tc_geo, p->xdt == SPMM_BF16, p->wdt == SPMM_E4M3, p->sm_count, s);
 }
 
+namespace {
+cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *const *X,
+                            const int64_t *n, const int64_t *ldx, void *const *Y,
+                            const int64_t *ldy, cudaStream_t s, bool schedule);
+}
+
+// Plans of both stage geometries in one batch: one launch per geometry.
 cudaError_t launch_tc_batch(int count, spmm_plan *const *plans, const void *const *X,
                             const int64_t *n, const int64_t *ldx, void *const *Y,
                             const int64_t *ldy, cudaStream_t s, bool schedule) {
     if (count <= 0 || count > kMaxBatch) return cudaErrorInvalidValue;
+    bool mixed = false;
+    for (int i = 1; i < count; ++i) mixed |= plans[i]->tc_geo != plans[0]->tc_geo;
+    if (!mixed) return launch_tc_group(count, plans, X, n, ldx, Y, ldy, s, schedule);
+    for (int geo = 0; geo < 2; ++geo) {
+        spmm_plan *gp[kMaxBatch];
+        const void *gx[kMaxBatch];
+        void *gy[kMaxBatch];
+        int64_t gn[kMaxBatch], glx[kMaxBatch], gly[kMaxBatch];
+        int c = 0;
+        for (int i = 0; i < count; ++i) {
+            if (plans[i]->tc_geo != geo) continue;
+            gp[c] = plans[i];
+            gx[c] = X[i];
+            gy[c] = Y[i];
+            gn[c] = n[i];
+            glx[c] = ldx ? ldx[i] : n[i];
+            gly[c] = ldy ? ldy[i] : n[i];
+            ++c;
+        }
+        if (!c) continue;
+        cudaError_t e = launch_tc_group(c, gp, gx, gn, glx, gy, gly, s, schedule);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+namespace {
+cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *const *X,
+                            const int64_t *n, const int64_t *ldx, void *const *Y,
+                            const int64_t *ldy, cudaStream_t s, bool schedule) {
     TcBatch B;
     std::lock_guard<std::mutex> lk(g_sched_mu);
     SchedKey key;
@@ -1140,7 +1200,7 @@ cudaError_t launch_tc_batch(int count, spmm_plan *const *plans, const void *cons
     if (!schedule) {
         // problems in submission order (serving: every launch is a new mix)
         const bool bf16 = plans[0]->xdt == SPMM_BF16, w8 = plans[0]->wdt == SPMM_E4M3;
-        return dispatch_batch(B, bf16, w8, plans[0]->sm_count, s);
+        return dispatch_batch(B, plans[0]->tc_geo, bf16, w8, plans[0]->sm_count, s);
     }
     auto it = g_sched.find(key);
     if (it == g_sched.end()) {
@@ -1180,16 +1240,19 @@ cudaError_t launch_tc_batch(int count, spmm_plan *const *plans, const void *cons
     }
     B.units = it->second;
     const bool bf16 = plans[0]->xdt == SPMM_BF16, w8 = plans[0]->wdt == SPMM_E4M3;
-    return dispatch_batch(B, bf16, w8, plans[0]->sm_count, s);
+    return dispatch_batch(B, plans[0]->tc_geo, bf16, w8, plans[0]->sm_count, s);
 }
+}  // namespace
 
 cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s) {
     const bool dyn = p->mode == SPMM_DYNAMIC;
     const int64_t ni = dyn ? p->dyn.items_cap : p->n_items;
     if (ni == 0 || !p->d_srec) return cudaSuccess;
     const bool w8 = p->wdt == SPMM_E4M3;
-    const int tiles_cap = w8 ? StageGeom<true>::tiles : StageGeom<false>::tiles;
-    const int ent_cap = w8 ? StageGeom<true>::ent : StageGeom<false>::ent;
+    const int tiles_cap = w8 ? StageGeom<true, 0>::tiles
+                             : (p->tc_geo ? StageGeom<false, 1>::tiles : StageGeom<false, 0>::tiles);
+    const int ent_cap = w8 ? StageGeom<true, 0>::ent
+                           : (p->tc_geo ? StageGeom<false, 1>::ent : StageGeom<false, 0>::ent);
     stage_build_kernel<<<(unsigned)ni, kBuildWarps * 32, 0, s>>>(
         p->d_items, ni, dyn ? p->d_counts + kCntItems : nullptr, p->d_status, p->d_ent_col,
         p->d_ent_tbeg, p->d_ent_cover, ent_cap, tiles_cap, p->d_srec, p->d_sprog);
@@ -1197,6 +1260,7 @@ cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s) {
 }
 
 int64_t stage_record_words() { return kRecWords; }
+int tc_geometry(double tiles_per_entry) { return tiles_per_entry >= 8.0 ? 0 : 1; }
 int64_t stage_prog_words() { return 2 * kMmaStage; }
 
 cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const float *d_scales,

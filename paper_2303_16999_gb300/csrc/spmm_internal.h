@@ -95,6 +95,7 @@ struct spmm_plan {
             *d_ent_tbeg = nullptr, *d_ent_cover = nullptr, *d_tile_row = nullptr, *d_blk_slot = nullptr,
             *d_blk_off = nullptr, *d_grp_ebeg = nullptr;
     uint32_t *d_srec = nullptr, *d_sprog = nullptr;  // TC: stage records and MMA programs
+    int tc_geo = 0;                // TC stage geometry: 0 dense tiles, 1 sparse tiles
     int64_t *d_ws_row0 = nullptr;
     int64_t n_items = 0, n_groups = 0, n_entries = 0, n_tiles = 0, n_red = 0;
     void *d_packed = nullptr;      // packed values (kernel layout)
@@ -135,6 +136,8 @@ cudaError_t launch_restride(const void *src, void *dst, int64_t rows, int64_t n,
 // TC stage records of every work item (plan arrays only; no values)
 cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s);
 int64_t stage_record_words();
+// TC stage geometry for a plan whose entries hold this many tiles on average
+int tc_geometry(double tiles_per_entry);
 int64_t stage_prog_words();
 cudaError_t launch_tc(const spmm_plan *p, const void *d_X, int64_t n, int64_t ldx, void *d_Y,
                       int64_t ldy, cudaStream_t s);
