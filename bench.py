@@ -289,7 +289,11 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--point", default=None,
-                    help="run one sweep point only, 'b:1/d' e.g. 16:4 (profiling)")
+                    help="run one sweep point only, 'b:1/d' e.g. 16:4 (profiling); the other "
+                         "sections are then skipped unless named by --section")
+    ap.add_argument("--section", action="append", default=[],
+                    choices=["gather_small_n", "dynamic", "batched", "serving"],
+                    help="with --point: also run this section (repeatable)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -413,13 +417,16 @@ def main():
         comparators = run_comparators(torch, S, wl, dev, pts)
 
     dynamic = batched = serving = gsmall = None
-    if rank == 0 and args.point is None:
+
+    def want(name, off=False):
+        return rank == 0 and not off and (args.point is None or name in args.section)
+    if want("gather_small_n"):
         gsmall = run_gather_small_n(torch, S, wl, dev, peaks)
-    if rank == 0 and not args.no_dynamic and args.point is None:
+    if want("dynamic", args.no_dynamic):
         dynamic = run_dynamic(torch, S, wl, dev)
-    if rank == 0 and not args.no_batched and args.point is None:
+    if want("batched", args.no_batched):
         batched = run_batched(torch, S, wl, dev)
-    if rank == 0 and not args.no_serving and args.point is None:
+    if want("serving", args.no_serving):
         serving = run_serving(torch, S, wl, dev)
 
     launches = sum(launches_per_run(p) for p in pts) * args.steps
