@@ -58,8 +58,8 @@ namespace {
 #ifndef SPMM_TC_RCAP
 #define SPMM_TC_RCAP 16     // tile rows per group (accumulator columns / 16)
 #endif
-// Stage geometries of 16-bit weights (stages, X slabs and W tiles per
-// stage, all in about 110 KB of shared memory per CTA).  The plan picks one
+// Stage geometries (stages, X slabs and W tiles per stage, all in about
+// 110 KB of shared memory per CTA), for 16-bit and for E4M3 weights.  The plan picks one
 // by its tiles per entry: few-tile entries (sparse tiles) need many slabs
 // per stage to amortise the stage's fixed costs, many-tile entries need
 // room for their tiles.  Measured on m = k = 4096, n = 2048: the dense
@@ -84,13 +84,22 @@ namespace {
 #define SPMM_TC_TILES_S 44
 #endif
 #ifndef SPMM_TC_STAGES8
-#define SPMM_TC_STAGES8 3   // E4M3 weights (one geometry)
+#define SPMM_TC_STAGES8 3   // E4M3 weights, dense: 4 slabs, 24 tiles
 #endif
 #ifndef SPMM_TC_ENT8
 #define SPMM_TC_ENT8 4
 #endif
 #ifndef SPMM_TC_TILES8
 #define SPMM_TC_TILES8 24
+#endif
+#ifndef SPMM_TC_STAGES8_S
+#define SPMM_TC_STAGES8_S 2 // E4M3 weights, sparse: 8 slabs, 24 tiles
+#endif
+#ifndef SPMM_TC_ENT8_S
+#define SPMM_TC_ENT8_S 8
+#endif
+#ifndef SPMM_TC_TILES8_S
+#define SPMM_TC_TILES8_S 24
 #endif
 constexpr int kSlabBytes = kTile * kNTile * 2;                    // 4096: 16 k x 128 n, 16-bit
 constexpr int kTileBytes8 = kTile * kTile;                        // 256: E4M3 tile, row-major
@@ -103,11 +112,14 @@ constexpr int kMaxBatch = 64;                                     // problems pe
 // Stage layout: X slabs | 16-bit W tiles (MMA B operand) | (E4M3 only) the
 // FP8 codes and their scales as loaded, which the converter warps expand
 // into the 16-bit area.
-// GEO: 0 = dense, 1 = sparse (16-bit weights); E4M3 has one geometry.
+// GEO: 0 = dense, 1 = sparse.
 template <bool W8, int GEO> struct StageGeom {
-    static constexpr int stages = W8 ? SPMM_TC_STAGES8 : (GEO ? SPMM_TC_STAGES_S : SPMM_TC_STAGES_D);
-    static constexpr int ent = W8 ? SPMM_TC_ENT8 : (GEO ? SPMM_TC_ENT_S : SPMM_TC_ENT_D);   // X slabs
-    static constexpr int tiles = W8 ? SPMM_TC_TILES8 : (GEO ? SPMM_TC_TILES_S : SPMM_TC_TILES_D);
+    static constexpr int stages = W8 ? (GEO ? SPMM_TC_STAGES8_S : SPMM_TC_STAGES8)
+                                     : (GEO ? SPMM_TC_STAGES_S : SPMM_TC_STAGES_D);
+    static constexpr int ent = W8 ? (GEO ? SPMM_TC_ENT8_S : SPMM_TC_ENT8)
+                                  : (GEO ? SPMM_TC_ENT_S : SPMM_TC_ENT_D);   // X slabs
+    static constexpr int tiles = W8 ? (GEO ? SPMM_TC_TILES8_S : SPMM_TC_TILES8)
+                                    : (GEO ? SPMM_TC_TILES_S : SPMM_TC_TILES_D);
     static_assert(stages <= kStagesMax && ent <= 12 && tiles >= 16, "stage geometry");
     static constexpr int w16 = ent * kSlabBytes;
     static constexpr int w8 = w16 + tiles * kTileBytes16;
@@ -1087,7 +1099,7 @@ cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_geo(const TcBatch &B, int geo, bool w8, int sm_count, cudaStream_t s) {
-    if (w8) return launch_batch<T, true, 0>(B, sm_count, s);   // E4M3: one geometry
+    if (w8) return geo ? launch_batch<T, true, 1>(B, sm_count, s) : launch_batch<T, true, 0>(B, sm_count, s);
     return geo ? launch_batch<T, false, 1>(B, sm_count, s) : launch_batch<T, false, 0>(B, sm_count, s);
 }
 cudaError_t dispatch_batch(const TcBatch &B, int geo, bool bf16, bool w8, int sm_count,
@@ -1249,9 +1261,9 @@ cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s) {
     const int64_t ni = dyn ? p->dyn.items_cap : p->n_items;
     if (ni == 0 || !p->d_srec) return cudaSuccess;
     const bool w8 = p->wdt == SPMM_E4M3;
-    const int tiles_cap = w8 ? StageGeom<true, 0>::tiles
+    const int tiles_cap = w8 ? (p->tc_geo ? StageGeom<true, 1>::tiles : StageGeom<true, 0>::tiles)
                              : (p->tc_geo ? StageGeom<false, 1>::tiles : StageGeom<false, 0>::tiles);
-    const int ent_cap = w8 ? StageGeom<true, 0>::ent
+    const int ent_cap = w8 ? (p->tc_geo ? StageGeom<true, 1>::ent : StageGeom<true, 0>::ent)
                            : (p->tc_geo ? StageGeom<false, 1>::ent : StageGeom<false, 0>::ent);
     stage_build_kernel<<<(unsigned)ni, kBuildWarps * 32, 0, s>>>(
         p->d_items, ni, dyn ? p->d_counts + kCntItems : nullptr, p->d_status, p->d_ent_col,
