@@ -734,6 +734,8 @@ spmm_status spmm_plan_get_info(const spmm_plan *cp, spmm_plan_info *info) {
     i.ws_rows = dynran ? p->dyn_ws_rows : p->hp.ws_rows;
     i.n_reductions = dynran ? p->dyn_red : p->n_red;
     i.device_bytes = p->device_bytes;
+    i.stage_geometry = p->kernel == SPMM_KERNEL_TC ? p->tc_geo : 0;
+    i.reserved = 0;
     *info = i;
     return SPMM_OK;
 }

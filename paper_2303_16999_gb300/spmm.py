@@ -67,7 +67,8 @@ class PlanInfo(ctypes.Structure):
         [(n, ctypes.c_int32) for n in ("b", "mode", "w_dtype", "x_dtype", "kernel",
                                       "rows_per_group", "max_per_item")] + \
         [(n, ctypes.c_int64) for n in ("n_items", "n_groups", "n_entries", "n_tiles",
-                                      "ws_rows", "n_reductions", "device_bytes")]
+                                      "ws_rows", "n_reductions", "device_bytes")] + \
+        [(n, ctypes.c_int32) for n in ("stage_geometry", "reserved")]
 
 
 class ServeConfig(ctypes.Structure):

@@ -131,3 +131,18 @@ def test_batch_rejects_mixed_or_dynamic():
     with pytest.raises(S.SpmmError) as e:
         S.spmm_batch_run([p1, p3], [X, X], [torch.empty_like(X)] * 2)
     assert e.value.status == S.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("b,d,geo", [(8, 1 / 4, 0), (16, 1 / 32, 1)])
+def test_e4m3_both_stage_geometries(b, d, geo):
+    """E4M3 plans also choose dense- or sparse-tile stages; both within the
+    FP8 bound against the oracle on the decoded values."""
+    c = _problem(90 + b, 1024, 2048, 136, b, d)
+    plan, codes, scales = _e4m3_plan(c, rows_per_group=16)
+    assert plan.info()["stage_geometry"] == geo
+    X = _x(c, torch.bfloat16)
+    Y = plan.run(X)
+    torch.cuda.synchronize()
+    v = oracle.e4m3_block_values(codes.view(torch.uint8).numpy(), scales.numpy())
+    Yo = oracle.spmm(c["m"], c["k"], b, c["brow"], c["bcol"], v, X.cpu())
+    assert oracle.normwise_err(Y.cpu(), Yo, oracle.block_fro(v), X.cpu()) <= 3e-2

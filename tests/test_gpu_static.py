@@ -241,3 +241,19 @@ def test_gather_large_small_n_sampled(n):
     rows = [0, 4097, 9000, m - 1]
     Yo, wf, X = _sub_oracle(cn, rows, dt)
     assert oracle.normwise_err(Y[rows], Yo, wf, X) <= 4e-3
+
+
+@pytest.mark.parametrize("b,d,n,geo", [(16, 1 / 32, 200, 1), (1, 1 / 4, 136, 0), (8, 1 / 4, 256, 0),
+                                       (16, 1 / 16, 130, 1), (4, 1 / 8, 64, 0)])
+def test_both_stage_geometries(b, d, n, geo):
+    """Plans choose dense-tile or sparse-tile stages by tiles per entry (at
+    least 8: dense); both geometries stay within the bound against the
+    oracle.  Groups of 16 tile rows, so that entries can hold many tiles."""
+    m, k = 1024, 2048
+    err, Y, _, plan = run_case(m, k, n, b, wl.nnzb_for(m, k, b, d), torch.float16, "tc",
+                               seed=11 * b + n, ldx=((n + 7) // 8) * 8, rows_per_group=16)
+    info = plan.info()
+    assert (info["n_tiles"] >= 8 * info["n_entries"]) == (geo == 0)
+    assert info["stage_geometry"] == geo
+    assert not torch.isnan(Y).any()
+    assert err <= 4e-3, err
