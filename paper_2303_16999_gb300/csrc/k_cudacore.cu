@@ -9,6 +9,7 @@
 
 #include <algorithm>
 
+#include "pdl.cuh"
 #include "spmm_internal.h"
 
 namespace spmm {
@@ -21,6 +22,7 @@ template <typename U>
 __global__ void pack_csr_kernel(const U *__restrict__ vals, const int32_t *__restrict__ perm,
                                 int64_t nnzb, int bb, const int32_t *__restrict__ nnzb_dev,
                                 const int32_t *__restrict__ status, U *__restrict__ out) {
+    pdl_enter();
     // dynamic plans: a rejected pattern leaves perm incomplete; pack nothing
     if (status && *status != 0) return;
     if (nnzb_dev) nnzb = min((int64_t)max(*nnzb_dev, 0), nnzb);
@@ -40,6 +42,7 @@ __global__ void plain_f32_kernel(const int32_t *__restrict__ row_ptr,
                                  const float *__restrict__ vals, const float *__restrict__ X,
                                  int64_t ldx, float *__restrict__ Y, int64_t ldy, int64_t m,
                                  int64_t n, int b) {
+    pdl_enter();
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
     for (int64_t i = blockIdx.y; i < m; i += gridDim.y) {
@@ -87,6 +90,7 @@ __global__ void __launch_bounds__(256) gather_kernel(
     int64_t ldx, T *__restrict__ Y, int64_t ldy, int64_t n, float *__restrict__ ws,
     const int64_t *__restrict__ ws_row0, const int32_t *__restrict__ n_items_dev,
     const int32_t *__restrict__ status) {
+    pdl_enter();
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (n_items_dev) {
@@ -183,6 +187,7 @@ __global__ void __launch_bounds__(512) gather1_kernel(
     const T *__restrict__ vals, const T *__restrict__ X, int64_t ldx, int64_t k, T *__restrict__ Y,
     int64_t ldy, float *__restrict__ ws, const int64_t *__restrict__ ws_row0,
     const int32_t *__restrict__ n_items_dev, const int32_t *__restrict__ status) {
+    pdl_enter();
     constexpr int kRounds = 4;            // 4 x 4 non-zeros per lane per pass
     extern __shared__ __align__(16) uint8_t xs_raw[];
     const int lane = threadIdx.x & 31;
@@ -306,9 +311,9 @@ cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const void *X, i
     const int64_t cap = (int64_t)std::max(p->sm_count, 1) * per_sm;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    gather1_kernel<T, V, SX><<<(unsigned)blocks, 512, smem, s>>>(
-        p->d_items, n_items, p->d_col_idx, (const T *)p->d_packed, (const T *)X, ldx, p->k,
-        (T *)Y, ldy, p->d_ws, p->d_ws_row0, dyn ? p->d_counts + kCntItems : nullptr, p->d_status);
+    pdl_launch(gather1_kernel<T, V, SX>, dim3((unsigned)blocks), dim3(512), smem, s, p->d_items,
+        n_items, p->d_col_idx, (const T *)p->d_packed, (const T *)X, ldx, p->k, (T *)Y, ldy,
+        p->d_ws, p->d_ws_row0, dyn ? p->d_counts + kCntItems : nullptr, p->d_status);
     return cudaGetLastError();
 }
 
@@ -317,6 +322,7 @@ cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const void *X, i
 template <typename E>
 __global__ void restride_kernel(const E *__restrict__ src, E *__restrict__ dst, int64_t rows,
                                 int64_t n, int64_t ld) {
+    pdl_enter();
     const int64_t total = rows * n;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
@@ -335,6 +341,7 @@ __global__ void reduce_kernel(const int32_t *__restrict__ red, const int32_t *__
                               T *__restrict__ Y, int64_t ldy, int64_t n, int64_t n_red,
                               const int32_t *__restrict__ n_red_dev,
                               const int32_t *__restrict__ status) {
+    pdl_enter();
   if (n_red_dev) {
       if (*status != 0) return;
       n_red = min(n_red, (int64_t)*n_red_dev);
@@ -379,10 +386,9 @@ cudaError_t gather_launch(const spmm_plan *p, const void *X, int64_t n, int64_t 
             return gather1_launch<T, V, true>(p, n_items, X, ldx, Y, ldy, s);
         return gather1_launch<T, V, false>(p, n_items, X, ldx, Y, ldy, s);
     }
-    gather_kernel<T, V><<<grid1d(warps * 32, 256), 256, 0, s>>>(
-        p->d_items, n_items, nchunk, LN, p->d_col_idx, (const T *)p->d_packed, (const T *)X,
-        ldx, (T *)Y, ldy, n, p->d_ws, p->d_ws_row0, dyn ? p->d_counts + kCntItems : nullptr,
-        p->d_status);
+    pdl_launch(gather_kernel<T, V>, dim3(grid1d(warps * 32, 256)), dim3(256), 0, s, p->d_items,
+        n_items, nchunk, LN, p->d_col_idx, (const T *)p->d_packed, (const T *)X, ldx, (T *)Y, ldy,
+        n, p->d_ws, p->d_ws_row0, dyn ? p->d_counts + kCntItems : nullptr, p->d_status);
     return cudaGetLastError();
 }
 
@@ -410,9 +416,11 @@ cudaError_t launch_restride(const void *src, void *dst, int64_t rows, int64_t n,
     if (total == 0) return cudaSuccess;
     const unsigned g = grid1d(total, 256) > 2048u ? 2048u : grid1d(total, 256);
     if (elem == 2)
-        restride_kernel<uint16_t><<<g, 256, 0, s>>>((const uint16_t *)src, (uint16_t *)dst, rows, n, ld);
+        pdl_launch(restride_kernel<uint16_t>, dim3(g), dim3(256), 0, s, (const uint16_t *)src,
+            (uint16_t *)dst, rows, n, ld);
     else if (elem == 4)
-        restride_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t *)src, (uint32_t *)dst, rows, n, ld);
+        pdl_launch(restride_kernel<uint32_t>, dim3(g), dim3(256), 0, s, (const uint32_t *)src,
+            (uint32_t *)dst, rows, n, ld);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -428,14 +436,12 @@ cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, const int3
     const int32_t *st = d_nnzb ? p->d_status : nullptr;
     switch (dtype_size(p->wdt)) {
         case 4:
-            pack_csr_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t *)d_values, p->d_perm,
-                                                        nmax, bb, d_nnzb, st,
-                                                        (uint32_t *)p->d_packed);
+            pdl_launch(pack_csr_kernel<uint32_t>, dim3(g), dim3(256), 0, s,
+                (const uint32_t *)d_values, p->d_perm, nmax, bb, d_nnzb, st, (uint32_t *)p->d_packed);
             break;
         case 2:
-            pack_csr_kernel<uint16_t><<<g, 256, 0, s>>>((const uint16_t *)d_values, p->d_perm,
-                                                        nmax, bb, d_nnzb, st,
-                                                        (uint16_t *)p->d_packed);
+            pdl_launch(pack_csr_kernel<uint16_t>, dim3(g), dim3(256), 0, s,
+                (const uint16_t *)d_values, p->d_perm, nmax, bb, d_nnzb, st, (uint16_t *)p->d_packed);
             break;
         default: return cudaErrorInvalidValue;
     }
@@ -445,8 +451,8 @@ cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, const int3
 cudaError_t launch_plain(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
                          int64_t ldy, cudaStream_t s) {
     dim3 grid(grid1d(n, 128), (unsigned)(p->m < 65535 ? p->m : 65535));
-    plain_f32_kernel<<<grid, 128, 0, s>>>(p->d_row_ptr, p->d_col_idx, (const float *)p->d_packed,
-                                          (const float *)X, ldx, (float *)Y, ldy, p->m, n, p->b);
+    pdl_launch(plain_f32_kernel, dim3(grid), dim3(128), 0, s, p->d_row_ptr, p->d_col_idx,
+        (const float *)p->d_packed, (const float *)X, ldx, (float *)Y, ldy, p->m, n, p->b);
     return cudaGetLastError();
 }
 
@@ -481,17 +487,19 @@ cudaError_t launch_reduce(const spmm_plan *p, int64_t n, void *Y, int64_t ldy, c
     const int32_t *rn = tc ? p->d_grp_rows : nullptr;
     switch (p->xdt) {
         case SPMM_F32:
-            reduce_kernel<float><<<grid, 128, 0, s>>>(p->d_red, r0, rn, rows_per_unit, p->d_ws,
-                                                      p->d_ws_row0, (float *)Y, ldy, n, n_red, n_red_dev, p->d_status);
+            pdl_launch(reduce_kernel<float>, dim3(grid), dim3(128), 0, s, p->d_red, r0, rn,
+                rows_per_unit, p->d_ws, p->d_ws_row0, (float *)Y, ldy, n, n_red, n_red_dev,
+                p->d_status);
             break;
         case SPMM_F16:
-            reduce_kernel<__half><<<grid, 128, 0, s>>>(p->d_red, r0, rn, rows_per_unit, p->d_ws,
-                                                       p->d_ws_row0, (__half *)Y, ldy, n, n_red, n_red_dev, p->d_status);
+            pdl_launch(reduce_kernel<__half>, dim3(grid), dim3(128), 0, s, p->d_red, r0, rn,
+                rows_per_unit, p->d_ws, p->d_ws_row0, (__half *)Y, ldy, n, n_red, n_red_dev,
+                p->d_status);
             break;
         case SPMM_BF16:
-            reduce_kernel<__nv_bfloat16><<<grid, 128, 0, s>>>(p->d_red, r0, rn, rows_per_unit,
-                                                              p->d_ws, p->d_ws_row0,
-                                                              (__nv_bfloat16 *)Y, ldy, n, n_red, n_red_dev, p->d_status);
+            pdl_launch(reduce_kernel<__nv_bfloat16>, dim3(grid), dim3(128), 0, s, p->d_red, r0, rn,
+                rows_per_unit, p->d_ws, p->d_ws_row0, (__nv_bfloat16 *)Y, ldy, n, n_red, n_red_dev,
+                p->d_status);
             break;
         default: return cudaErrorInvalidValue;
     }

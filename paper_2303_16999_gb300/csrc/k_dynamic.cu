@@ -17,6 +17,7 @@
 // status word; the product kernels then skip, leaving Y unwritten.
 #include <cuda_runtime.h>
 
+#include "pdl.cuh"
 #include "spmm_internal.h"
 
 namespace spmm {
@@ -33,6 +34,7 @@ __device__ __forceinline__ int64_t clamp_nnzb(const int32_t *d_nnzb, int64_t cap
 __global__ void dyn_validate_hist(const int32_t *d_nnzb, const int32_t *brow, const int32_t *bcol,
                                   int64_t cap, int32_t mb, int32_t kb, int32_t *row_cnt,
                                   int32_t *status) {
+    pdl_enter();
     const int64_t raw = *d_nnzb;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (raw < 0 || raw > cap)) flag(status, kDevCapacity);
     const int64_t n = raw < 0 ? 0 : (raw > cap ? cap : raw);
@@ -85,6 +87,7 @@ __global__ void __launch_bounds__(1024) dyn_scan_rows(const int32_t *d_nnzb, int
                                                       int32_t *row_ibeg, int32_t *row_wbeg,
                                                       int32_t *row_rbeg, int32_t *counts,
                                                       int rows_items) {
+    pdl_enter();
     const int64_t nnzb = clamp_nnzb(d_nnzb, cap);
     const int64_t avg = mb ? (nnzb + mb - 1) / mb : 0;
     const int64_t C1 = avg * 2 > 64 ? avg * 2 : 64;
@@ -128,6 +131,7 @@ __global__ void __launch_bounds__(1024) dyn_scan_rows(const int32_t *d_nnzb, int
 __global__ void dyn_scatter(const int32_t *d_nnzb, const int32_t *brow, const int32_t *bcol,
                             int64_t cap, int32_t mb, int32_t kb, int32_t *cursor, int32_t *tmp_col,
                             int32_t *tmp_perm) {
+    pdl_enter();
     const int64_t n = clamp_nnzb(d_nnzb, cap);
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
@@ -148,6 +152,7 @@ __global__ void dyn_sort_rows(int32_t mb, const int32_t *row_ptr, const int32_t 
                               const int32_t *row_wbeg, const int32_t *row_rbeg,
                               const int32_t *counts, int32_t *items, int64_t *ws_row0,
                               int32_t *red) {
+    pdl_enter();
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= mb) return;
@@ -196,6 +201,7 @@ __global__ void dyn_sort_rows(int32_t mb, const int32_t *row_ptr, const int32_t 
 __global__ void dyn_group_count(int32_t kt, int32_t T, const int32_t *grp_row0,
                                 const int32_t *grp_rows, const int32_t *row_ptr,
                                 const int32_t *col_idx, int32_t *grp_cnt) {
+    pdl_enter();
     extern __shared__ uint32_t colmask[];
     const int g = blockIdx.x;
     for (int32_t c = threadIdx.x; c < kt; c += blockDim.x) colmask[c] = 0;
@@ -240,6 +246,7 @@ __global__ void __launch_bounds__(1024) dyn_group_scan(int32_t G, const int32_t 
                                                        int32_t *grp_wbeg, int64_t *grp_wrow,
                                                        int32_t *grp_rbeg, int32_t *ent_tbeg,
                                                        int32_t *counts) {
+    pdl_enter();
     __shared__ int64_t sE;
     int64_t tot;
     {
@@ -305,6 +312,7 @@ __global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *
                                int32_t *ent_tbeg, int32_t *ent_cover, int32_t *tile_row,
                                int32_t *blk_slot, int32_t *blk_off, int32_t *items,
                                int64_t *ws_row0, int32_t *red) {
+    pdl_enter();
     extern __shared__ uint32_t sm[];
     uint32_t *colmask = sm;                 // kt
     int32_t *ent_of = (int32_t *)(sm + kt); // kt: entry index of each column, slot base in ent_tbeg
@@ -409,27 +417,27 @@ cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_counts, 0, sizeof(int32_t) * kCntCount, s);
     if (e != cudaSuccess) return e;
     const unsigned gp = grid_for(cap, 256, 4096);
-    dyn_validate_hist<<<gp, 256, 0, s>>>(dp->d_nnzb, dp->d_brow, dp->d_bcol, cap, mb, kb, d.row_cnt,
-                                         p->d_status);
-    dyn_scan_rows<<<1, 1024, 0, s>>>(dp->d_nnzb, cap, mb, d.row_cnt, p->d_row_ptr, d.cursor,
-                                     d.row_ibeg, d.row_wbeg, d.row_rbeg, p->d_counts, tc ? 0 : 1);
-    dyn_scatter<<<gp, 256, 0, s>>>(dp->d_nnzb, dp->d_brow, dp->d_bcol, cap, mb, kb, d.cursor,
-                                   d.tmp_col, d.tmp_perm);
-    dyn_sort_rows<<<grid_for((int64_t)mb * 32, 256, 1u << 30), 256, 0, s>>>(
-        mb, p->d_row_ptr, d.tmp_col, d.tmp_perm, p->d_col_idx, p->d_perm, p->d_status, tc ? 0 : 1,
+    pdl_launch(dyn_validate_hist, dim3(gp), dim3(256), 0, s, dp->d_nnzb, dp->d_brow, dp->d_bcol,
+        cap, mb, kb, d.row_cnt, p->d_status);
+    pdl_launch(dyn_scan_rows, dim3(1), dim3(1024), 0, s, dp->d_nnzb, cap, mb, d.row_cnt,
+        p->d_row_ptr, d.cursor, d.row_ibeg, d.row_wbeg, d.row_rbeg, p->d_counts, tc ? 0 : 1);
+    pdl_launch(dyn_scatter, dim3(gp), dim3(256), 0, s, dp->d_nnzb, dp->d_brow, dp->d_bcol, cap, mb,
+        kb, d.cursor, d.tmp_col, d.tmp_perm);
+    pdl_launch(dyn_sort_rows, dim3(grid_for((int64_t)mb * 32, 256, 1u << 30)), dim3(256), 0, s, mb,
+        p->d_row_ptr, d.tmp_col, d.tmp_perm, p->d_col_idx, p->d_perm, p->d_status, tc ? 0 : 1,
         d.row_ibeg, d.row_wbeg, d.row_rbeg, p->d_counts, p->d_items, p->d_ws_row0, p->d_red);
     if (tc) {
         const int32_t kt = (int32_t)(p->k / kTile), T = kTile / p->b, G = (int32_t)p->n_groups;
-        dyn_group_count<<<G, 256, sizeof(uint32_t) * kt, s>>>(kt, T, p->d_grp_row0, p->d_grp_rows,
-                                                              p->d_row_ptr, p->d_col_idx, d.grp_cnt);
-        dyn_group_scan<<<1, 1024, 0, s>>>(G, p->d_grp_rows, d.grp_cnt, p->d_grp_ebeg, d.grp_sbeg,
-                                          d.grp_ibeg, d.grp_wbeg, d.grp_wrow, d.grp_rbeg,
-                                          p->d_ent_tbeg, p->d_counts);
-        dyn_group_fill<<<G, 1024, sizeof(uint32_t) * 3 * kt, s>>>(
-            kt, T, p->b, p->d_grp_row0, p->d_grp_rows, p->d_row_ptr, p->d_col_idx, p->d_perm,
-            p->d_grp_ebeg, d.grp_sbeg, d.grp_ibeg, d.grp_wbeg, d.grp_wrow, d.grp_rbeg, p->d_counts,
-            p->d_ent_col, p->d_ent_tbeg, p->d_ent_cover, p->d_tile_row, p->d_blk_slot, p->d_blk_off,
-            p->d_items, p->d_ws_row0, p->d_red);
+        pdl_launch(dyn_group_count, dim3(G), dim3(256), sizeof(uint32_t) * kt, s, kt, T,
+            p->d_grp_row0, p->d_grp_rows, p->d_row_ptr, p->d_col_idx, d.grp_cnt);
+        pdl_launch(dyn_group_scan, dim3(1), dim3(1024), 0, s, G, p->d_grp_rows, d.grp_cnt,
+            p->d_grp_ebeg, d.grp_sbeg, d.grp_ibeg, d.grp_wbeg, d.grp_wrow, d.grp_rbeg,
+            p->d_ent_tbeg, p->d_counts);
+        pdl_launch(dyn_group_fill, dim3(G), dim3(1024), sizeof(uint32_t) * 3 * kt, s, kt, T, p->b,
+            p->d_grp_row0, p->d_grp_rows, p->d_row_ptr, p->d_col_idx, p->d_perm, p->d_grp_ebeg,
+            d.grp_sbeg, d.grp_ibeg, d.grp_wbeg, d.grp_wrow, d.grp_rbeg, p->d_counts, p->d_ent_col,
+            p->d_ent_tbeg, p->d_ent_cover, p->d_tile_row, p->d_blk_slot, p->d_blk_off, p->d_items,
+            p->d_ws_row0, p->d_red);
     }
     return cudaGetLastError();
 }

@@ -46,6 +46,7 @@
 #include <mutex>
 #include <vector>
 
+#include "pdl.cuh"
 #include "spmm_internal.h"
 
 namespace spmm {
@@ -391,6 +392,7 @@ __device__ __forceinline__ Unit decode_unit(const TcBatch &B, int64_t u) {
 template <typename T, bool W8, int GEO>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     tc_kernel(const __grid_constant__ TcBatch B) {
+    pdl_enter();
     using G = StageGeom<W8, GEO>;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *stages = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -926,6 +928,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
                        const int32_t *__restrict__ ent_col, const int32_t *__restrict__ ent_tbeg,
                        const int32_t *__restrict__ ent_cover, int ent_cap, int tiles_cap,
                        uint32_t *__restrict__ srec, uint32_t *__restrict__ sprog) {
+    pdl_enter();
     __shared__ int32_t counts[kBuildWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int64_t ni = n_items;
@@ -975,6 +978,7 @@ __global__ void pack_tiles_kernel(const U *__restrict__ vals, const int32_t *__r
                                   const int32_t *__restrict__ blk_off, int64_t nnzb,
                                   const int32_t *__restrict__ nnzb_dev,
                                   const int32_t *__restrict__ status, U *__restrict__ out) {
+    pdl_enter();
     // dynamic plans: a rejected pattern leaves blk_slot / blk_off incomplete
     if (status && *status != 0) return;
     constexpr int kSeg = SEG;                           // values per thread
@@ -1011,6 +1015,7 @@ __global__ void pack_tiles_e4m3_kernel(const uint8_t *__restrict__ codes,
                                        const int32_t *__restrict__ nnzb_dev,
                                        const int32_t *__restrict__ status, uint8_t *__restrict__ out,
                                        float *__restrict__ tile_scale) {
+    pdl_enter();
     if (status && *status != 0) return;   // rejected dynamic pattern
     if (nnzb_dev) nnzb = min((int64_t)max(*nnzb_dev, 0), nnzb);
     const int bb = b * b;
@@ -1032,6 +1037,7 @@ __global__ void pack_tiles_e4m3_kernel(const uint8_t *__restrict__ codes,
 template <typename U>
 __global__ void quantize_e4m3_kernel(const U *__restrict__ src, int64_t nnzb, int b,
                                      uint8_t *__restrict__ codes, float *__restrict__ scales) {
+    pdl_enter();
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (wid >= nnzb) return;
@@ -1128,7 +1134,7 @@ cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    tc_kernel<T, W8, GEO><<<grid, kThreads, smem, s>>>(B);
+    pdl_launch(tc_kernel<T, W8, GEO>, dim3(grid), dim3(kThreads), smem, s, B);
     return cudaGetLastError();
 }
 
@@ -1300,9 +1306,9 @@ cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s) {
                              : (p->tc_geo ? StageGeom<false, 1>::tiles : StageGeom<false, 0>::tiles);
     const int ent_cap = w8 ? (p->tc_geo ? StageGeom<true, 1>::ent : StageGeom<true, 0>::ent)
                            : (p->tc_geo ? StageGeom<false, 1>::ent : StageGeom<false, 0>::ent);
-    stage_build_kernel<<<(unsigned)ni, kBuildWarps * 32, 0, s>>>(
-        p->d_items, ni, dyn ? p->d_counts + kCntItems : nullptr, p->d_status, p->d_ent_col,
-        p->d_ent_tbeg, p->d_ent_cover, ent_cap, tiles_cap, p->d_srec, p->d_sprog);
+    pdl_launch(stage_build_kernel, dim3((unsigned)ni), dim3(kBuildWarps * 32), 0, s, p->d_items, ni,
+        dyn ? p->d_counts + kCntItems : nullptr, p->d_status, p->d_ent_col, p->d_ent_tbeg,
+        p->d_ent_cover, ent_cap, tiles_cap, p->d_srec, p->d_sprog);
     return cudaGetLastError();
 }
 
@@ -1324,7 +1330,7 @@ cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const fl
         const int64_t slots = p->mode == SPMM_STATIC ? p->n_tiles : p->nnzb_max;
         e = cudaMemsetAsync(p->d_tile_scale, 0, sizeof(float) * 16 * slots, s);
         if (e != cudaSuccess) return e;
-        pack_tiles_e4m3_kernel<<<(unsigned)g, 256, 0, s>>>(
+        pdl_launch(pack_tiles_e4m3_kernel, dim3((unsigned)g), dim3(256), 0, s,
             (const uint8_t *)d_values, d_scales, p->d_blk_slot, p->d_blk_off, nmax, p->b, d_nnzb,
             d_nnzb ? p->d_status : nullptr, (uint8_t *)p->d_packed, p->d_tile_scale);
         return cudaGetLastError();
@@ -1340,19 +1346,26 @@ cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const fl
     const int32_t *st = d_nnzb ? p->d_status : nullptr;
     switch (p->b) {
         case 16:
-            if (al) pack_tiles_kernel<uint16_t, 16, 8><<<gb, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
-            else pack_tiles_kernel<uint16_t, 16, 1><<<g1, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
+            if (al) pdl_launch(pack_tiles_kernel<uint16_t, 16, 8>, dim3(gb), dim3(256), 0, s, v, bs,
+                bo, nmax, d_nnzb, st, o);
+            else pdl_launch(pack_tiles_kernel<uint16_t, 16, 1>, dim3(g1), dim3(256), 0, s, v, bs,
+                bo, nmax, d_nnzb, st, o);
             break;
         case 8:
-            if (al) pack_tiles_kernel<uint16_t, 8, 8><<<gb, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
-            else pack_tiles_kernel<uint16_t, 8, 1><<<g1, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
+            if (al) pdl_launch(pack_tiles_kernel<uint16_t, 8, 8>, dim3(gb), dim3(256), 0, s, v, bs,
+                bo, nmax, d_nnzb, st, o);
+            else pdl_launch(pack_tiles_kernel<uint16_t, 8, 1>, dim3(g1), dim3(256), 0, s, v, bs, bo,
+                nmax, d_nnzb, st, o);
             break;
         case 4:
-            if (al) pack_tiles_kernel<uint16_t, 4, 4><<<gb, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
-            else pack_tiles_kernel<uint16_t, 4, 1><<<g1, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
+            if (al) pdl_launch(pack_tiles_kernel<uint16_t, 4, 4>, dim3(gb), dim3(256), 0, s, v, bs,
+                bo, nmax, d_nnzb, st, o);
+            else pdl_launch(pack_tiles_kernel<uint16_t, 4, 1>, dim3(g1), dim3(256), 0, s, v, bs, bo,
+                nmax, d_nnzb, st, o);
             break;
         default:
-            pack_tiles_kernel<uint16_t, 1, 1><<<g1, 256, 0, s>>>(v, bs, bo, nmax, d_nnzb, st, o);
+            pdl_launch(pack_tiles_kernel<uint16_t, 1, 1>, dim3(g1), dim3(256), 0, s, v, bs, bo,
+                nmax, d_nnzb, st, o);
             break;
     }
     return cudaGetLastError();
@@ -1365,16 +1378,16 @@ cudaError_t launch_quantize_e4m3(int64_t nnzb, int b, spmm_dtype src, const void
     const unsigned grid = (unsigned)((threads + 255) / 256);
     switch (src) {
         case SPMM_F32:
-            quantize_e4m3_kernel<float><<<grid, 256, 0, s>>>((const float *)d_src, nnzb, b, d_codes,
-                                                             d_scales);
+            pdl_launch(quantize_e4m3_kernel<float>, dim3(grid), dim3(256), 0, s,
+                (const float *)d_src, nnzb, b, d_codes, d_scales);
             break;
         case SPMM_F16:
-            quantize_e4m3_kernel<__half><<<grid, 256, 0, s>>>((const __half *)d_src, nnzb, b, d_codes,
-                                                              d_scales);
+            pdl_launch(quantize_e4m3_kernel<__half>, dim3(grid), dim3(256), 0, s,
+                (const __half *)d_src, nnzb, b, d_codes, d_scales);
             break;
         case SPMM_BF16:
-            quantize_e4m3_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>((const __nv_bfloat16 *)d_src,
-                                                                     nnzb, b, d_codes, d_scales);
+            pdl_launch(quantize_e4m3_kernel<__nv_bfloat16>, dim3(grid), dim3(256), 0, s,
+                (const __nv_bfloat16 *)d_src, nnzb, b, d_codes, d_scales);
             break;
         default: return cudaErrorInvalidValue;
     }
