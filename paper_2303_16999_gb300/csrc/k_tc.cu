@@ -1,6 +1,6 @@
-// Tensor-core block-sparse kernel for b in {4, 8, 16} (Section 3.1: b x b
-// blocks hold all non-zeros; b = 16 is one 16 x 16 tile, b = 4 / 8 blocks are
-// packed into 16 x 16 tiles with zero fill).
+// Tensor-core block-sparse kernel for b in {4, 8, 16}, and for b = 1 where
+// tiles fill (Section 3.1: b x b blocks hold all non-zeros; b = 16 is one
+// 16 x 16 tile, smaller blocks are packed into 16 x 16 tiles with zero fill).
 //
 // The product is computed transposed, Y^T = X^T W^T, so one MMA is
 //   D[128 n x 16 m] += A[128 n x 16 k] * B[16 k x 16 m]
@@ -11,27 +11,33 @@
 // each X slab once and applying it to every tile of that column, with one
 // TMEM accumulator (16 columns) per tile row.  The planner covers each
 // entry's rows by intervals of consecutive rows (zero tiles fill the gaps);
-// one MMA with N = 16 x (interval length) serves an interval, since a
-// 128 x 16 x 16 MMA costs about as much to issue as a 128 x 80 x 16 one.
-// Accumulators start at zero in TMEM (the epilogue clears what it reads),
-// so every MMA accumulates.
+// one MMA with N = 16 x (interval length) serves an interval, since below
+// N = 128 an MMA costs about the reads of its 4 KB A operand.  Accumulators
+// start at zero in TMEM (the epilogue clears what it reads), so every MMA
+// accumulates.
 //
 // Pipeline: a stage holds up to StageGeom::ent entries (X slabs) and up to
-// StageGeom::tiles W tiles.  How a work item's entries fall into stages, and the
+// StageGeom::tiles W tiles, in one of two geometries the plan picks (dense
+// or sparse tiles).  How a work item's entries fall into stages, and the
 // MMAs of each stage (one word per MMA: slab, first W tile, first tile row,
-// rows), is fixed by the plan, so stage_build_kernel writes it once per
-// plan (every call for dynamic plans) as stage records.  Two producer warps
-// follow the records with three in flight: warp 0 copies the stage's W
-// tiles (contiguous in the packed array, one bulk copy) and its MMA program
-// into shared memory, warp 6 requests the X slabs (one TMA per slab, both
-// 64-column halves in one 3-D box when n is a multiple of 64).  Issuing a
-// copy costs its warp a few hundred cycles, so the two run side by side.
-// The MMA warp stays converged: each lane loads one program word and the
-// warp walks them with one shuffle per MMA, issuing through elect.sync.
+// rows; one list per half of the tile rows), is fixed by the plan, so
+// stage_build_kernel writes it once per plan (every call for dynamic plans)
+// as stage records.  Three producer warps follow the records with three in
+// flight: warp 0 copies the stage's W tiles (contiguous in the packed array,
+// one bulk copy) and its MMA program into shared memory, warps 6 and 7
+// request the two halves of its X slabs (one TMA per slab, both 64-column
+// halves in one 3-D box when n is a multiple of 64).  Issuing a copy costs
+// its warp a few hundred cycles, so they run side by side.  Two MMA warps
+// (1: tile rows 0-7, 8: rows 8-15) stay converged: each lane loads one
+// program word and the warp walks them with one shuffle per MMA, issuing
+// through elect.sync; each owns its accumulator columns, so the order of
+// accumulation into every column is fixed.  With two stages the ring is
+// bound by the copy latency (a stage is refilled only after its MMAs
+// complete): each role spends about a third of a stage waiting.
 //
-// Warp roles (224 threads): warp 0 = W producer, warp 1 = MMA issuer and
-// TMEM owner, warps 2..5 = epilogue (TMEM -> registers -> Y or workspace) and,
-// for E4M3 weights, converters, warp 6 = X producer.
+// Warp roles (288 threads): warp 0 = W producer, warps 1 and 8 = MMA issuers
+// (warp 1 owns TMEM), warps 2..5 = epilogue (TMEM -> registers -> Y or
+// workspace) and, for E4M3 weights, converters, warps 6 and 7 = X producers.
 // Every mbarrier wait is bounded (globaltimer); on expiry the CTA records
 // SPMM_ERR_TIMEOUT in the plan's status word, stops, frees TMEM and exits.
 #include <cuda.h>
