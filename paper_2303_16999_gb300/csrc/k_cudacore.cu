@@ -182,13 +182,19 @@ __global__ void __launch_bounds__(256) gather_kernel(
 // the kernel is left bound by the HBM stream of indices and values.  The
 // lanes' sums meet in a fixed butterfly (deterministic).
 template <typename T, int V, bool SX>
-__global__ void __launch_bounds__(512) gather1_kernel(
+#ifndef SPMM_G1_ROUNDS
+#define SPMM_G1_ROUNDS 4    // 16-byte index loads in flight per lane per pass
+#endif
+#ifndef SPMM_G1_BLOCKS
+#define SPMM_G1_BLOCKS 2    // resident 512-thread blocks per SM (bounds registers)
+#endif
+__global__ void __launch_bounds__(512, SPMM_G1_BLOCKS) gather1_kernel(
     const int32_t *__restrict__ items, int64_t n_items, const int32_t *__restrict__ col_idx,
     const T *__restrict__ vals, const T *__restrict__ X, int64_t ldx, int64_t k, T *__restrict__ Y,
     int64_t ldy, float *__restrict__ ws, const int64_t *__restrict__ ws_row0,
     const int32_t *__restrict__ n_items_dev, const int32_t *__restrict__ status) {
     pdl_enter();
-    constexpr int kRounds = 4;            // 4 x 4 non-zeros per lane per pass
+    constexpr int kRounds = SPMM_G1_ROUNDS;   // kRounds x 4 non-zeros per lane per pass
     extern __shared__ __align__(16) uint8_t xs_raw[];
     const int lane = threadIdx.x & 31;
     if (n_items_dev) {
@@ -306,7 +312,7 @@ cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const void *X, i
         }
     }
     // persistent: as many 512-thread blocks as fit (shared memory allowing)
-    const int per_sm = SX ? (smem <= 100 * 1024 ? 2 : 1) : 4;
+    const int per_sm = SX ? (smem <= 100 * 1024 ? 2 : 1) : SPMM_G1_BLOCKS;
     int64_t blocks = (n_items * 32 + 511) / 512;
     const int64_t cap = (int64_t)std::max(p->sm_count, 1) * per_sm;
     if (blocks > cap) blocks = cap;
