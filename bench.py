@@ -663,8 +663,9 @@ def run_gather_small_n(torch, S, wl, dev, peaks, reps=15):
     """The b = 1 gather kernel (CUDA cores) at small n, where it is bound by
     HBM: m = k = 16384, d = 1/16 (16.8 M non-zeros, 100 MB of FP16 values and
     int32 indices, so one pass does not fit the 129 MB L2 together with the
-    flush), FP16.  Each timed run follows a 256 MB write that evicts L2; the
-    events bracket the product alone.  Compulsory bytes (values, indices, row
+    flush), FP16.  Each timed run follows a 256 MB write and read-back that
+    evict L2 (the read-back lets the written lines drain first); the events
+    bracket the product alone.  Compulsory bytes (values, indices, row
     pointers, X once, Y once) over the measured time, against the measured
     HBM copy bandwidth."""
     m = k = 16384
@@ -681,7 +682,10 @@ def run_gather_small_n(torch, S, wl, dev, peaks, reps=15):
             plan.run(X, Y)
         ts = []
         for _ in range(reps):
+            # evict L2: write a buffer twice its size, then read it back, so
+            # the dirty lines are written back before the timed launch
             flush.zero_()
+            flush.max()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             plan.run(X, Y)
@@ -697,7 +701,7 @@ def run_gather_small_n(torch, S, wl, dev, peaks, reps=15):
     plan.close()
     del flush
     return {"workload": "b=1 gather kernel, m=k=16384, d=1/16 (16.8 M non-zeros), FP16, small n; "
-                        "L2 evicted before every timed run", "points": out}
+                        "L2 evicted (256 MB written and read back) before every timed run", "points": out}
 
 
 def run_comparators(torch, S, wl, dev, pts):
