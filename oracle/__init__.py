@@ -9,6 +9,8 @@ Contents
 --------
 * ``spmm(...)`` -- the FP64 definition of Section 3 (C, single thread), over
   the inputs exactly as supplied (values widened to FP64 without rounding).
+* ``spmm_t(...)`` -- the transposed product W^T.Y on the same blocks, written
+  out from its own definition (not through ``spmm``).
 * ``e4m3_to_f64`` -- FP8 E4M3 decoding from the format definition.
 * ``normwise_err`` -- ||Y - Y_o||_F / (||W||_F ||X||_F), the acceptance metric.
 * ``oracle.plan`` -- the integer plan / partition rules (Section 3.2, 3.3,
@@ -43,6 +45,9 @@ def _bind(lib):
     lib.oracle_spmm_f64.restype = ctypes.c_int
     lib.oracle_spmm_f64.argtypes = [i64, i64, i64, i64, i64, i32p, i32p, dp, dp,
                                     i64, dp, i64]
+    lib.oracle_spmm_t_f64.restype = ctypes.c_int
+    lib.oracle_spmm_t_f64.argtypes = [i64, i64, i64, i64, i64, i32p, i32p, dp, dp,
+                                      i64, dp, i64]
     lib.oracle_e4m3_to_f64.restype = ctypes.c_int64
     lib.oracle_e4m3_to_f64.argtypes = [ctypes.POINTER(ctypes.c_uint8), i64, dp]
     return lib
@@ -91,6 +96,29 @@ def spmm(m, k, b, brow, bcol, vals, X, lib=None):
     if rc != 0:
         raise ValueError("oracle_spmm_f64: pattern or sizes invalid (rc=%d)" % rc)
     return y
+
+
+def spmm_t(m, k, b, brow, bcol, vals, Y, lib=None):
+    """Z = W^T.Y in FP64 (the transposed product on the same blocks).
+
+    W is m x k given by brow, bcol, vals (user order, blocks row-major);
+    Y: (m, n).  Returns Z (k, n) float64.
+    """
+    lib = lib or _load()
+    brow = np.ascontiguousarray(brow, dtype=np.int32)
+    bcol = np.ascontiguousarray(bcol, dtype=np.int32)
+    nnzb = brow.shape[0]
+    v = np.ascontiguousarray(to_f64(vals)).reshape(nnzb * b * b)
+    y = np.ascontiguousarray(to_f64(Y))
+    assert y.shape[0] == m
+    n = y.shape[1]
+    z = np.empty((k, n), dtype=np.float64)
+    rc = lib.oracle_spmm_t_f64(m, k, n, b, nnzb, _ptr(brow, ctypes.c_int32),
+                               _ptr(bcol, ctypes.c_int32), _ptr(v, ctypes.c_double),
+                               _ptr(y, ctypes.c_double), n, _ptr(z, ctypes.c_double), n)
+    if rc != 0:
+        raise ValueError("oracle_spmm_t_f64: pattern or sizes invalid (rc=%d)" % rc)
+    return z
 
 
 def e4m3_to_f64(codes, lib=None):

@@ -108,4 +108,49 @@ int64_t oracle_e4m3_to_f64(const uint8_t *in, int64_t count, double *out)
         out[i] = s ? -mag : mag;
     }
     return nans;
+}/*
+ * The transposed product Z = W^T * Y (the step beside the path in sparse
+ * training, Section 1: the same block mask applied to the other operand),
+ * written out from its definition over the same user-order blocks:
+ *
+ * Z[c*b + l, j] = sum over blocks p with bcol[p] == c
+ *                    sum over ii < b with brow[p]*b + ii < m
+ *                        vals[p][ii][l] * Y[brow[p]*b + ii, j]
+ *
+ * W is m x k, Y is m x n (ldy), Z is k x n (ldz).  Same return codes as
+ * oracle_spmm_f64.
+ */
+int oracle_spmm_t_f64(int64_t m, int64_t k, int64_t n, int64_t b, int64_t nnzb,
+                      const int32_t *brow, const int32_t *bcol, const double *vals,
+                      const double *Y, int64_t ldy, double *Z, int64_t ldz)
+{
+    if (m < 0 || k < 0 || n < 0 || b <= 0 || nnzb < 0 || ldy < n || ldz < n)
+        return 2;
+    const int64_t mb = (m + b - 1) / b;
+    const int64_t kb = (k + b - 1) / b;
+    for (int64_t i = 0; i < k; ++i)
+        for (int64_t j = 0; j < n; ++j)
+            Z[i * ldz + j] = 0.0;
+    for (int64_t p = 0; p < nnzb; ++p) {
+        const int64_t r = brow[p], c = bcol[p];
+        if (r < 0 || r >= mb || c < 0 || c >= kb)
+            return 1;
+        const double *blk = vals + p * b * b;
+        for (int64_t l = 0; l < b; ++l) {
+            const int64_t zr = c * b + l;
+            if (zr >= k)
+                break;
+            for (int64_t ii = 0; ii < b; ++ii) {
+                const int64_t yr = r * b + ii;
+                if (yr >= m)
+                    break;
+                const double w = blk[ii * b + l];
+                for (int64_t j = 0; j < n; ++j)
+                    Z[zr * ldz + j] += w * Y[yr * ldy + j];
+            }
+        }
+    }
+    return 0;
 }
+
+

@@ -218,3 +218,52 @@ def test_workload_recipe_shapes():
     assert wl.sweep_seed(16, 1 / 32) == 16005 and wl.sweep_seed(1, 1 / 4) == 1002
     d = wl.dynamic_call(3, m=512, k=512, n=4)
     assert d["nnzb_max"] // 2 <= len(d["brow"]) <= d["nnzb_max"]
+
+
+# ---- the transposed product W^T.Y (oracle.spmm_t) ------------------------
+@pytest.mark.parametrize("b", [1, 2, 4, 8])
+def test_transposed_matches_dense_transpose(b):
+    """W^T.Y equals densify(W)^T @ Y computed by numpy in FP64."""
+    rng = np.random.default_rng(40 + b)
+    m, k, n = 8 * b, 12 * b, 5
+    mb, kb = m // b, k // b
+    idx = rng.choice(mb * kb, size=mb * kb // 3, replace=False)
+    brow, bcol = (idx // kb).astype(np.int32), (idx % kb).astype(np.int32)
+    vals = rng.standard_normal((len(idx), b, b))
+    Y = rng.standard_normal((m, n))
+    W = np.zeros((m, k))
+    for p in range(len(idx)):
+        W[brow[p] * b:(brow[p] + 1) * b, bcol[p] * b:(bcol[p] + 1) * b] = vals[p]
+    np.testing.assert_allclose(oracle.spmm_t(m, k, b, brow, bcol, vals, Y), W.T @ Y,
+                               rtol=1e-13, atol=1e-13)
+
+
+def test_transposed_is_the_adjoint():
+    """<W x, y> = <x, W^T y> for the oracle's own forward and transposed
+    products (a wrong transpose, row index or sign in either breaks it)."""
+    rng = np.random.default_rng(7)
+    b, m, k, n = 4, 32, 48, 3
+    mb, kb = m // b, k // b
+    idx = rng.choice(mb * kb, size=30, replace=False)
+    brow, bcol = (idx // kb).astype(np.int32), (idx % kb).astype(np.int32)
+    vals = rng.standard_normal((30, b, b))
+    X = rng.standard_normal((k, n))
+    Y = rng.standard_normal((m, n))
+    lhs = np.sum(oracle.spmm(m, k, b, brow, bcol, vals, X) * Y)
+    rhs = np.sum(X * oracle.spmm_t(m, k, b, brow, bcol, vals, Y))
+    assert abs(lhs - rhs) <= 1e-10 * (abs(lhs) + 1)
+
+
+def test_transposed_exact_integers_and_truncation():
+    """Integer blocks give an exact result; a block over the bottom edge is
+    truncated as in the forward product (rows >= m of W do not exist)."""
+    b, m, k = 4, 6, 8                       # the second block row hangs over m = 6
+    brow = np.array([0, 1], np.int32)
+    bcol = np.array([1, 0], np.int32)
+    vals = np.arange(2 * 16, dtype=np.float64).reshape(2, 4, 4) - 10
+    Y = np.arange(6 * 2, dtype=np.float64).reshape(6, 2)
+    Z = oracle.spmm_t(m, k, b, brow, bcol, vals, Y)
+    Wfull = np.zeros((8, k))                # the untruncated block grid, then cut to m rows
+    for p in range(2):
+        Wfull[brow[p] * b:(brow[p] + 1) * b, bcol[p] * b:(bcol[p] + 1) * b] = vals[p]
+    assert np.array_equal(Z, Wfull[:m].T @ Y)
