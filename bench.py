@@ -287,12 +287,13 @@ def main():
     ap.add_argument("--no-dynamic", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-transposed", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--point", default=None,
                     help="run one sweep point only, 'b:1/d' e.g. 16:4 (profiling); the other "
                          "sections are then skipped unless named by --section")
     ap.add_argument("--section", action="append", default=[],
-                    choices=["gather_small_n", "dynamic", "batched", "serving"],
+                    choices=["gather_small_n", "dynamic", "batched", "serving", "transposed"],
                     help="with --point: also run this section (repeatable)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -416,7 +417,7 @@ def main():
             q["b"] == 16 and abs(q["d"] - 1 / 16) < 1e-12 for q in pts):
         comparators = run_comparators(torch, S, wl, dev, pts)
 
-    dynamic = batched = serving = gsmall = None
+    dynamic = batched = serving = gsmall = transposed = None
 
     def want(name, off=False):
         return rank == 0 and not off and (args.point is None or name in args.section)
@@ -428,6 +429,8 @@ def main():
         batched = run_batched(torch, S, wl, dev)
     if want("serving", args.no_serving):
         serving = run_serving(torch, S, wl, dev)
+    if want("transposed", args.no_transposed):
+        transposed = run_transposed(torch, S, wl, dev)
 
     launches = sum(launches_per_run(p) for p in pts) * args.steps
     if rank == 0:
@@ -439,7 +442,7 @@ def main():
                 "e2e": e2e, "gpu_launches": launches, "clocks": sampler.summary(),
                 "roofline": roofline, "cpu_baseline": cpu, "points": points,
                 "comparators": comparators, "dynamic": dynamic, "batched": batched,
-                "serving": serving, "gather_small_n": gsmall}
+                "serving": serving, "gather_small_n": gsmall, "transposed": transposed}
         print(json.dumps(line))
     for p in pts:
         p["plan"].close()
@@ -702,6 +705,52 @@ def run_gather_small_n(torch, S, wl, dev, peaks, reps=15):
     del flush
     return {"workload": "b=1 gather kernel, m=k=16384, d=1/16 (16.8 M non-zeros), FP16, small n; "
                         "L2 evicted (256 MB written and read back) before every timed run", "points": out}
+
+
+def run_transposed(torch, S, wl, dev, reps=15,
+                   cases=((16, 1 / 16), (16, 1 / 4), (8, 1 / 16), (4, 1 / 16), (1, 1 / 16))):
+    """Z = W^T.Y against Y = W.X on the same W (sweep points, m = k = 4096,
+    n = 2048, FP16; the sweep's X serves as Y).  Both plans run from cold L2
+    (256 MB written and read back before every timed run); the events
+    bracket the product alone."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = []
+    for b, d in cases:
+        c = wl.sweep_case(b, d)
+        vals = torch.from_numpy(c["vals"]).half().to(dev)
+        X = torch.from_numpy(c["X"]).half().to(dev)
+        Y = torch.empty((M, N), dtype=torch.float16, device=dev)
+        row = {"b": b, "d": "1/%d" % round(1 / d)}
+        for name, tr in (("forward", False), ("transposed", True)):
+            plan = S.Plan(M, K, N, b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"],
+                          transposed=tr)
+            plan.pack(vals)
+            for _ in range(3):
+                plan.run(X, Y)
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                flush.max()
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                plan.run(X, Y)
+                e.record()
+                e.synchronize()
+                ts.append(a.elapsed_time(e) * 1e3)
+            if plan.status() != 0:
+                raise RuntimeError("plan status %d" % plan.status())
+            us = statistics.median(ts)
+            row[name] = {"us": round(us, 2), "kernel": {1: "plain", 2: "gather", 3: "tc"}[
+                plan.info()["kernel"]],
+                "tflops_nz": round(2.0 * len(c["brow"]) * b * b * N / us / 1e6, 2)}
+            plan.close()
+        row["transposed_over_forward_time"] = round(row["transposed"]["us"] /
+                                                    row["forward"]["us"], 3)
+        out.append(row)
+        del vals, X, Y
+    del flush
+    return {"workload": "Z = W^T.Y vs Y = W.X on one W, m=k=4096, n=2048, FP16; L2 evicted "
+                        "(256 MB written and read back) before every timed run", "points": out}
 
 
 def run_comparators(torch, S, wl, dev, pts):

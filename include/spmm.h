@@ -104,6 +104,10 @@ typedef struct {
     int32_t max_per_item;         /* TC: entries per work item; GATHER: blocks per row item; 0 = planner's choice */
     int32_t host_only;            /* 1 = build the static plan on the host only (no device memory, no
                                      CUDA calls): for inspection with spmm_plan_get_array */
+    int32_t transposed;           /* 1 = the plan applies W^T: spmm_run computes Z = W^T.Y (Z k x n,
+                                     Y m x n) for the W that the pattern and values describe in W's own
+                                     coordinates (m x k, blocks row-major); internally the plan is the
+                                     block-transposed operand, so plan info and arrays report k x m */
 } spmm_plan_opts;
 
 typedef struct spmm_plan spmm_plan;

@@ -300,10 +300,36 @@ int64_t spmm_bucket_size(int64_t m, int64_t k, int64_t num, int64_t den, int64_t
     return (int64_t)((a + d - 1) / d);
 }
 
+static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spmm_mode mode,
+                               spmm_dtype w_dtype, spmm_dtype x_dtype, const spmm_pattern *pattern,
+                               int64_t nnzb_max, const spmm_plan_opts *opts, spmm_plan **out);
+
+// A transposed plan is the plan of W^T (k x m, block (c, r) holding W's
+// block (r, c) transposed): the pattern is swapped here, the values are
+// transposed block by block when packed, and a dynamic call's pattern is
+// swapped before the re-partition.
 spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spmm_mode mode,
                              spmm_dtype w_dtype, spmm_dtype x_dtype, const spmm_pattern *pattern,
                              int64_t nnzb_max, const spmm_plan_opts *opts, spmm_plan **out) {
     g_err[0] = 0;
+    if (!opts || !opts->transposed)
+        return plan_create(m, k, n_max, b, mode, w_dtype, x_dtype, pattern, nnzb_max, opts, out);
+    spmm_pattern tp{};
+    const spmm_pattern *pp = nullptr;
+    if (pattern) {
+        tp.nnzb = pattern->nnzb;
+        tp.brow = pattern->bcol;
+        tp.bcol = pattern->brow;
+        pp = &tp;
+    }
+    spmm_status st = plan_create(k, m, n_max, b, mode, w_dtype, x_dtype, pp, nnzb_max, opts, out);
+    if (st == SPMM_OK) (*out)->transposed = true;
+    return st;
+}
+
+static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spmm_mode mode,
+                               spmm_dtype w_dtype, spmm_dtype x_dtype, const spmm_pattern *pattern,
+                               int64_t nnzb_max, const spmm_plan_opts *opts, spmm_plan **out) {
     if (!out) {
         set_error("out is NULL");
         return SPMM_ERR_ARG;
@@ -600,7 +626,9 @@ spmm_status spmm_run(spmm_plan *plan, const void *d_values, const float *d_scale
             set_error("E4M3 values need per-block scales");
             return SPMM_ERR_ARG;
         }
-        cudaError_t e = launch_dynamic_partition(plan, dpat, s);
+        // a transposed plan reads W's pattern with rows and columns swapped
+        const spmm_dpattern tdp{dpat->d_nnzb, dpat->d_bcol, dpat->d_brow};
+        cudaError_t e = launch_dynamic_partition(plan, plan->transposed ? &tdp : dpat, s);
         if (e == cudaSuccess)
             e = plan->kernel == SPMM_KERNEL_TC
                     ? launch_pack_tiles(plan, d_values, d_scales, dpat->d_nnzb, s)

@@ -20,17 +20,20 @@ namespace {
 // host-supplied values are re-ordered to match the fixed distribution).
 template <typename U>
 __global__ void pack_csr_kernel(const U *__restrict__ vals, const int32_t *__restrict__ perm,
-                                int64_t nnzb, int bb, const int32_t *__restrict__ nnzb_dev,
+                                int64_t nnzb, int b, int tr, const int32_t *__restrict__ nnzb_dev,
                                 const int32_t *__restrict__ status, U *__restrict__ out) {
     pdl_enter();
     // dynamic plans: a rejected pattern leaves perm incomplete; pack nothing
     if (status && *status != 0) return;
     if (nnzb_dev) nnzb = min((int64_t)max(*nnzb_dev, 0), nnzb);
+    const int bb = b * b;
     const int64_t total = nnzb * bb;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = t / bb, e = t - s * bb;
-        out[t] = vals[(int64_t)perm[s] * bb + e];
+        // transposed plans: element (i, j) of the packed block is W's (j, i)
+        const int64_t src = tr ? (e % b) * b + e / b : e;
+        out[t] = vals[(int64_t)perm[s] * bb + src];
     }
 }
 
@@ -443,11 +446,13 @@ cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, const int3
     switch (dtype_size(p->wdt)) {
         case 4:
             pdl_launch(pack_csr_kernel<uint32_t>, dim3(g), dim3(256), 0, s,
-                (const uint32_t *)d_values, p->d_perm, nmax, bb, d_nnzb, st, (uint32_t *)p->d_packed);
+                (const uint32_t *)d_values, p->d_perm, nmax, p->b, p->transposed ? 1 : 0, d_nnzb, st,
+                (uint32_t *)p->d_packed);
             break;
         case 2:
             pdl_launch(pack_csr_kernel<uint16_t>, dim3(g), dim3(256), 0, s,
-                (const uint16_t *)d_values, p->d_perm, nmax, bb, d_nnzb, st, (uint16_t *)p->d_packed);
+                (const uint16_t *)d_values, p->d_perm, nmax, p->b, p->transposed ? 1 : 0, d_nnzb, st,
+                (uint16_t *)p->d_packed);
             break;
         default: return cudaErrorInvalidValue;
     }

@@ -981,7 +981,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32)
 // SEG = 1 for values not aligned to a segment).
 template <typename U, int B, int SEG>
 __global__ void pack_tiles_kernel(const U *__restrict__ vals, const int32_t *__restrict__ blk_slot,
-                                  const int32_t *__restrict__ blk_off, int64_t nnzb,
+                                  const int32_t *__restrict__ blk_off, int64_t nnzb, int tr,
                                   const int32_t *__restrict__ nnzb_dev,
                                   const int32_t *__restrict__ status, U *__restrict__ out) {
     pdl_enter();
@@ -998,7 +998,8 @@ __global__ void pack_tiles_kernel(const U *__restrict__ vals, const int32_t *__r
         const int i = r / (B / kSeg), seg = r % (B / kSeg);   // block row, segment
         const int off = blk_off[p];
         const int ti = off / kTile + i, tj = off % kTile + seg * kSeg;
-        const U *src = vals + p * (B * B) + i * B + seg * kSeg;
+        // transposed plans (SEG = 1 only): element (i, j) is W's (j, i)
+        const U *src = vals + p * (B * B) + (tr ? seg * B + i : i * B + seg * kSeg);
         U *dst = out + (int64_t)blk_slot[p] * (kTile * kTile) + (ti >> 3) * 128 + (tj >> 3) * 64 +
                  (ti & 7) * 8 + (tj & 7);
         if constexpr (kSeg == 8) {
@@ -1018,7 +1019,7 @@ __global__ void pack_tiles_e4m3_kernel(const uint8_t *__restrict__ codes,
                                        const float *__restrict__ scales,
                                        const int32_t *__restrict__ blk_slot,
                                        const int32_t *__restrict__ blk_off, int64_t nnzb, int b,
-                                       const int32_t *__restrict__ nnzb_dev,
+                                       int tr, const int32_t *__restrict__ nnzb_dev,
                                        const int32_t *__restrict__ status, uint8_t *__restrict__ out,
                                        float *__restrict__ tile_scale) {
     pdl_enter();
@@ -1033,7 +1034,9 @@ __global__ void pack_tiles_e4m3_kernel(const uint8_t *__restrict__ codes,
         const int off = blk_off[p];
         const int ti = off / kTile + e / b, tj = off % kTile + e % b;
         const int64_t s = blk_slot[p];
-        out[s * kTileBytes8 + ti * kTile + tj] = codes[t];
+        // transposed plans: element (i, j) is W's (j, i); a block's scale is
+        // the same either way
+        out[s * kTileBytes8 + ti * kTile + tj] = codes[tr ? p * bb + (e % b) * b + e / b : t];
         if ((ti & 3) == 0 && (tj & 3) == 0) tile_scale[s * 16 + (ti >> 2) * 4 + (tj >> 2)] = scales[p];
     }
 }
@@ -1337,15 +1340,18 @@ cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const fl
         e = cudaMemsetAsync(p->d_tile_scale, 0, sizeof(float) * 16 * slots, s);
         if (e != cudaSuccess) return e;
         pdl_launch(pack_tiles_e4m3_kernel, dim3((unsigned)g), dim3(256), 0, s,
-            (const uint8_t *)d_values, d_scales, p->d_blk_slot, p->d_blk_off, nmax, p->b, d_nnzb,
-            d_nnzb ? p->d_status : nullptr, (uint8_t *)p->d_packed, p->d_tile_scale);
+            (const uint8_t *)d_values, d_scales, p->d_blk_slot, p->d_blk_off, nmax, p->b,
+            p->transposed ? 1 : 0, d_nnzb, d_nnzb ? p->d_status : nullptr, (uint8_t *)p->d_packed,
+            p->d_tile_scale);
         return cudaGetLastError();
     }
     if (p->wdt != SPMM_F16 && p->wdt != SPMM_BF16) return cudaErrorNotSupported;
     const uint16_t *v = (const uint16_t *)d_values;
     uint16_t *o = (uint16_t *)p->d_packed;
     // vector loads need the values aligned to a block row segment
-    const bool al = ((uintptr_t)v % 16) == 0;
+    // vector copies need aligned values and untransposed blocks
+    const bool al = ((uintptr_t)v % 16) == 0 && !p->transposed;
+    const int tr = p->transposed ? 1 : 0;
     const unsigned gb = (unsigned)std::min<int64_t>(8192, (nmax * p->b * 2 + 255) / 256);
     const unsigned g1 = (unsigned)std::min<int64_t>(8192, (total + 255) / 256);
     const int32_t *bs = p->d_blk_slot, *bo = p->d_blk_off;
@@ -1353,25 +1359,25 @@ cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const fl
     switch (p->b) {
         case 16:
             if (al) pdl_launch(pack_tiles_kernel<uint16_t, 16, 8>, dim3(gb), dim3(256), 0, s, v, bs,
-                bo, nmax, d_nnzb, st, o);
+                bo, nmax, tr, d_nnzb, st, o);
             else pdl_launch(pack_tiles_kernel<uint16_t, 16, 1>, dim3(g1), dim3(256), 0, s, v, bs,
-                bo, nmax, d_nnzb, st, o);
+                bo, nmax, tr, d_nnzb, st, o);
             break;
         case 8:
             if (al) pdl_launch(pack_tiles_kernel<uint16_t, 8, 8>, dim3(gb), dim3(256), 0, s, v, bs,
-                bo, nmax, d_nnzb, st, o);
+                bo, nmax, tr, d_nnzb, st, o);
             else pdl_launch(pack_tiles_kernel<uint16_t, 8, 1>, dim3(g1), dim3(256), 0, s, v, bs, bo,
-                nmax, d_nnzb, st, o);
+                nmax, tr, d_nnzb, st, o);
             break;
         case 4:
             if (al) pdl_launch(pack_tiles_kernel<uint16_t, 4, 4>, dim3(gb), dim3(256), 0, s, v, bs,
-                bo, nmax, d_nnzb, st, o);
+                bo, nmax, tr, d_nnzb, st, o);
             else pdl_launch(pack_tiles_kernel<uint16_t, 4, 1>, dim3(g1), dim3(256), 0, s, v, bs, bo,
-                nmax, d_nnzb, st, o);
+                nmax, tr, d_nnzb, st, o);
             break;
         default:
             pdl_launch(pack_tiles_kernel<uint16_t, 1, 1>, dim3(g1), dim3(256), 0, s, v, bs, bo,
-                nmax, d_nnzb, st, o);
+                nmax, tr, d_nnzb, st, o);
             break;
     }
     return cudaGetLastError();

@@ -96,6 +96,7 @@ struct spmm_plan {
             *d_blk_off = nullptr, *d_grp_ebeg = nullptr;
     uint32_t *d_srec = nullptr, *d_sprog = nullptr;  // TC: stage records and MMA programs
     int tc_geo = 0;                // TC stage geometry: 0 dense tiles, 1 sparse tiles
+    bool transposed = false;       // applies W^T: values arrive as W's blocks, packed transposed
     int64_t *d_ws_row0 = nullptr;
     int64_t n_items = 0, n_groups = 0, n_entries = 0, n_tiles = 0, n_red = 0;
     void *d_packed = nullptr;      // packed values (kernel layout)

@@ -59,7 +59,8 @@ class DPattern(ctypes.Structure):
 
 class PlanOpts(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("rows_per_group", ctypes.c_int32),
-                ("max_per_item", ctypes.c_int32), ("host_only", ctypes.c_int32)]
+                ("max_per_item", ctypes.c_int32), ("host_only", ctypes.c_int32),
+                ("transposed", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -252,14 +253,19 @@ def _ptr(t):
 
 class Plan:
     """One SpMM plan.  Static: ``Plan(m, k, n_max, b, brow=..., bcol=...)``;
-    dynamic: ``Plan(m, k, n_max, b, mode=DYNAMIC, nnzb_max=...)``."""
+    dynamic: ``Plan(m, k, n_max, b, mode=DYNAMIC, nnzb_max=...)``.
+
+    ``transposed=True``: the plan applies W^T for the m x k W that the pattern
+    and values describe (in W's own coordinates); ``run(Y)`` then returns
+    Z = W^T.Y (k x n) for Y (m x n), and ``self.m, self.k`` are k, m."""
 
     def __init__(self, m, k, n_max, b, w_dtype=F16, x_dtype=None, brow=None, bcol=None,
                  mode=STATIC, nnzb_max=0, kernel="auto", rows_per_group=0, max_per_item=0,
-                 host_only=False):
+                 host_only=False, transposed=False):
         x_dtype = w_dtype if x_dtype is None else x_dtype
         opts = PlanOpts(KERNELS[kernel] if isinstance(kernel, str) else kernel,
-                        rows_per_group, max_per_item, 1 if host_only else 0)
+                        rows_per_group, max_per_item, 1 if host_only else 0,
+                        1 if transposed else 0)
         pat = None
         self._keep = None
         if mode == STATIC:
@@ -268,7 +274,10 @@ class Plan:
             self._keep = (brow, bcol)
             pat = Pattern(len(brow), brow.ctypes.data, bcol.ctypes.data)
         self.h = spmm_plan_create(m, k, n_max, b, mode, w_dtype, x_dtype, pat, nnzb_max, opts)
+        if transposed:
+            m, k = k, m                       # the operator the plan applies is k x m
         self.m, self.k, self.n_max, self.b = m, k, n_max, b
+        self.transposed = transposed
         self.mode, self.w_dtype, self.x_dtype = mode, w_dtype, x_dtype
 
     def close(self):

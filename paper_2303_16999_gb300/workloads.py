@@ -33,6 +33,16 @@ def problem(seed, m, k, n, b, nnzb):
     return dict(m=m, k=k, n=n, b=b, brow=brow, bcol=bcol, vals=vals, X=X, seed=seed)
 
 
+def transposed_problem(seed, m, k, n, b, nnzb):
+    """Operands of Z = W^T.Y: W's pattern and values as in problem() (W is
+    m x k), then Y f32 (m, n) in place of X."""
+    rng = rng_for(seed)
+    brow, bcol = pattern(rng, m // b, k // b, nnzb)
+    vals = rng.standard_normal((nnzb, b, b), dtype=np.float32)
+    Y = rng.standard_normal((m, n), dtype=np.float32)
+    return dict(m=m, k=k, n=n, b=b, brow=brow, bcol=bcol, vals=vals, Y=Y, seed=seed)
+
+
 def nnzb_for(m, k, b, d):
     """nnzb = d * (m/b) * (k/b); Section 3 defines d over the element mask,
     which for b x b blocks is the same fraction of the block grid."""

@@ -163,3 +163,24 @@ def test_auto_kernel_choice_for_b1():
     want = P.tc_plan(512, 512, 1, brow, bcol, p.info()["rows_per_group"], p.info()["max_per_item"])
     assert np.array_equal(p.array("ent_cover"), want["ent_cover"])
     assert np.array_equal(p.array("blk_slot"), want["blk_slot"])
+
+
+@pytest.mark.parametrize("b", [1, 8, 16])
+def test_transposed_plan_is_the_plan_of_w_transpose(b):
+    """A transposed plan of W (m x k) is the plan of W^T (k x m): its CSR and
+    tile plan equal the oracle's for the swapped pattern, and it reports the
+    swapped shape."""
+    rng = np.random.default_rng(70 + b)
+    m, k = 512, 256
+    brow, bcol = _rand(rng, m // b, k // b, (m // b) * (k // b) // 8)
+    p = _plan(m, k, b, brow, bcol, n_max=256, transposed=True, kernel="tc")
+    info = p.info()
+    assert (info["m"], info["k"], p.m, p.k) == (k, m, k, m)
+    rp, ci, pm = P.csr(k // b, bcol, brow)
+    assert np.array_equal(p.array("row_ptr"), rp)
+    assert np.array_equal(p.array("col_idx"), ci)
+    assert np.array_equal(p.array("perm"), pm)
+    want = P.tc_plan(k, m, b, bcol, brow, info["rows_per_group"], info["max_per_item"])
+    for key in TC_KEYS:
+        assert np.array_equal(p.array(key), want[key]), key
+    assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
