@@ -11,6 +11,8 @@ Contents
   the inputs exactly as supplied (values widened to FP64 without rounding).
 * ``spmm_t(...)`` -- the transposed product W^T.Y on the same blocks, written
   out from its own definition (not through ``spmm``).
+* ``sddmm(...)`` -- dW = (dY.X^T) on the block mask (the product's gradient
+  with respect to the stored blocks), from its definition.
 * ``e4m3_to_f64`` -- FP8 E4M3 decoding from the format definition.
 * ``normwise_err`` -- ||Y - Y_o||_F / (||W||_F ||X||_F), the acceptance metric.
 * ``oracle.plan`` -- the integer plan / partition rules (Section 3.2, 3.3,
@@ -48,6 +50,9 @@ def _bind(lib):
     lib.oracle_spmm_t_f64.restype = ctypes.c_int
     lib.oracle_spmm_t_f64.argtypes = [i64, i64, i64, i64, i64, i32p, i32p, dp, dp,
                                       i64, dp, i64]
+    lib.oracle_sddmm_f64.restype = ctypes.c_int
+    lib.oracle_sddmm_f64.argtypes = [i64, i64, i64, i64, i64, i32p, i32p, dp, i64, dp, i64,
+                                     dp]
     lib.oracle_e4m3_to_f64.restype = ctypes.c_int64
     lib.oracle_e4m3_to_f64.argtypes = [ctypes.POINTER(ctypes.c_uint8), i64, dp]
     return lib
@@ -119,6 +124,30 @@ def spmm_t(m, k, b, brow, bcol, vals, Y, lib=None):
     if rc != 0:
         raise ValueError("oracle_spmm_t_f64: pattern or sizes invalid (rc=%d)" % rc)
     return z
+
+
+def sddmm(m, k, b, brow, bcol, dY, X, lib=None):
+    """dW = (dY.X^T) on the block mask in FP64: for every block p (user
+    order), dW[p][ii][l] = sum_j dY[brow*b+ii, j] * X[bcol*b+l, j] (Section 3's
+    product differentiated with respect to the stored blocks).
+
+    dY: (m, n), X: (k, n).  Returns dW (nnzb, b, b) float64.
+    """
+    lib = lib or _load()
+    brow = np.ascontiguousarray(brow, dtype=np.int32)
+    bcol = np.ascontiguousarray(bcol, dtype=np.int32)
+    nnzb = brow.shape[0]
+    dy = np.ascontiguousarray(to_f64(dY))
+    x = np.ascontiguousarray(to_f64(X))
+    assert dy.shape[0] == m and x.shape[0] == k and dy.shape[1] == x.shape[1]
+    n = x.shape[1]
+    out = np.empty((nnzb, b, b), dtype=np.float64)
+    rc = lib.oracle_sddmm_f64(m, k, n, b, nnzb, _ptr(brow, ctypes.c_int32),
+                              _ptr(bcol, ctypes.c_int32), _ptr(dy, ctypes.c_double), n,
+                              _ptr(x, ctypes.c_double), n, _ptr(out, ctypes.c_double))
+    if rc != 0:
+        raise ValueError("oracle_sddmm_f64: pattern or sizes invalid (rc=%d)" % rc)
+    return out
 
 
 def e4m3_to_f64(codes, lib=None):

@@ -153,4 +153,56 @@ int oracle_spmm_t_f64(int64_t m, int64_t k, int64_t n, int64_t b, int64_t nnzb,
     return 0;
 }
 
+/*
+ * The sampled dense-dense product on the block mask (SDDMM): the gradient
+ * of Section 3's product with respect to W's stored blocks, as used by the
+ * sparse training regimes of Section 1.  For L = sum_ij dY[i,j] * Y[i,j]
+ * with Y = (M (.) W) * X, dL/dW[i,l] = M[i,l] * sum_j dY[i,j] * X[l,j], so
+ * for every stored block p, written out from that definition:
+ *
+ * dW[p][ii][l] = sum over j < n of dY[brow[p]*b + ii, j] * X[bcol[p]*b + l, j]
+ *
+ * for brow[p]*b + ii < m and bcol[p]*b + l < k; entries of a truncated edge
+ * block outside the m x k matrix are not part of W and are set to 0.
+ * dY is m x n (lddy), X is k x n (ldx); dW holds nnzb blocks of b*b values,
+ * row-major, in the order of the pattern.  Same return codes as
+ * oracle_spmm_f64.
+ */
+int oracle_sddmm_f64(int64_t m, int64_t k, int64_t n, int64_t b, int64_t nnzb,
+                     const int32_t *brow, const int32_t *bcol,
+                     const double *dY, int64_t lddy, const double *X, int64_t ldx,
+                     double *dW)
+{
+    if (m < 0 || k < 0 || n < 0 || b <= 0 || nnzb < 0 || lddy < n || ldx < n)
+        return 2;
+    const int64_t mb = (m + b - 1) / b;
+    const int64_t kb = (k + b - 1) / b;
+    for (int64_t p = 0; p < nnzb; ++p) {
+        const int64_t r = brow[p], c = bcol[p];
+        if (r < 0 || r >= mb || c < 0 || c >= kb)
+            return 1;
+        double *blk = dW + p * b * b;
+        for (int64_t ii = 0; ii < b; ++ii) {
+            for (int64_t l = 0; l < b; ++l) {
+                const int64_t yr = r * b + ii, xr = c * b + l;
+                double acc = 0.0;
+#ifdef ORACLE_MUTANT_SDDMM_DROP_TERM
+                const int64_t nj = n - 1;       /* planted: the last term is lost */
+#else
+                const int64_t nj = n;
+#endif
+                if (yr < m && xr < k)
+                    for (int64_t j = 0; j < nj; ++j)
+                        acc += dY[yr * lddy + j] * X[xr * ldx + j];
+#ifdef ORACLE_MUTANT_SDDMM_TRANSPOSE
+                blk[l * b + ii] = acc;          /* planted: block stored transposed */
+#else
+                blk[ii * b + l] = acc;
+#endif
+            }
+        }
+    }
+    return 0;
+}
+
 

@@ -2,7 +2,8 @@
 
 Each mutant is the oracle's own C source compiled with one ``-D`` flag that
 plants a plausible error (a transposed block, a flipped sign on one block, an
-off-by-one X row, a dropped output row).  At least one pin must fail for
+off-by-one X row, a dropped output row; for the sampled product, a block
+stored transposed and a lost term of the sum over n).  At least one pin must fail for
 every mutant; otherwise the pins could not tell that mistake from the
 definition.
 """
@@ -12,7 +13,7 @@ import pytest
 
 import oracle
 from oracle import build as obuild
-from test_oracle_pins import ALL_CHECKS
+from test_oracle_pins import ALL_CHECKS, SDDMM_CHECKS
 
 MUTANTS = ["ORACLE_MUTANT_TRANSPOSE", "ORACLE_MUTANT_SIGN",
            "ORACLE_MUTANT_COLSHIFT", "ORACLE_MUTANT_DROP_LAST"]
@@ -24,6 +25,19 @@ def test_pins_catch_planted_mistake(flag, tmp_path):
     lib = oracle.load_variant(path)
     failed = []
     for check in ALL_CHECKS:
+        try:
+            check(lib)
+        except AssertionError:
+            failed.append(check.__name__)
+    assert failed, "no pin detects " + flag
+
+
+@pytest.mark.parametrize("flag", ["ORACLE_MUTANT_SDDMM_TRANSPOSE", "ORACLE_MUTANT_SDDMM_DROP_TERM"])
+def test_sddmm_pins_catch_planted_mistake(flag, tmp_path):
+    path = obuild.build_variant(os.path.join(str(tmp_path), flag + ".so"), [flag])
+    lib = oracle.load_variant(path)
+    failed = []
+    for check in SDDMM_CHECKS:
         try:
             check(lib)
         except AssertionError:

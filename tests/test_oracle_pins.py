@@ -267,3 +267,83 @@ def test_transposed_exact_integers_and_truncation():
     for p in range(2):
         Wfull[brow[p] * b:(brow[p] + 1) * b, bcol[p] * b:(bcol[p] + 1) * b] = vals[p]
     assert np.array_equal(Z, Wfull[:m].T @ Y)
+
+
+# ------------------------------------------------------------- SDDMM -------
+def _sddmm_case(rng, b, mb, kb, frac, n):
+    idx = rng.choice(mb * kb, size=max(1, int(mb * kb * frac)), replace=False)
+    brow, bcol = (idx // kb).astype(np.int32), (idx % kb).astype(np.int32)
+    return brow, bcol, rng.standard_normal((mb * b, n)), rng.standard_normal((kb * b, n))
+
+
+def check_sddmm_masked_dense(lib):
+    """Every block equals the matching b x b window of numpy's dense dY @ X^T."""
+    rng = np.random.default_rng(11)
+    for b in (1, 2, 4, 8):
+        mb, kb, n = 6, 5, 7
+        brow, bcol, dY, X = _sddmm_case(rng, b, mb, kb, 0.4, n)
+        dW = oracle.sddmm(mb * b, kb * b, b, brow, bcol, dY, X, lib=lib)
+        G = dY @ X.T
+        for p in range(len(brow)):
+            want = G[brow[p] * b:(brow[p] + 1) * b, bcol[p] * b:(bcol[p] + 1) * b]
+            np.testing.assert_allclose(dW[p], want, rtol=1e-12, atol=1e-12)
+
+
+def check_sddmm_is_the_gradient(lib):
+    """<dW, V> = <dY, (M . V) X> for any V on the pattern: dW is the gradient
+    of <dY, Y> with respect to the stored blocks, checked through the forward
+    oracle (a transposed block, a wrong row or a lost term breaks it)."""
+    rng = np.random.default_rng(12)
+    b, mb, kb, n = 4, 7, 9, 6
+    brow, bcol, dY, X = _sddmm_case(rng, b, mb, kb, 0.3, n)
+    V = rng.standard_normal((len(brow), b, b))
+    dW = oracle.sddmm(mb * b, kb * b, b, brow, bcol, dY, X, lib=lib)
+    lhs = float(np.sum(dW * V))
+    rhs = float(np.sum(dY * oracle.spmm(mb * b, kb * b, b, brow, bcol, V, X, lib=lib)))
+    assert abs(lhs - rhs) <= 1e-10 * (abs(rhs) + 1)
+
+
+def check_sddmm_exact_integers_and_truncation(lib):
+    """Small integers give exact sums; a block hanging over both edges keeps
+    only the entries inside m x k and is zero elsewhere."""
+    b, m, k, n = 4, 6, 10, 3                # block row 1 and block column 2 hang over
+    brow = np.array([0, 1, 1], np.int32)
+    bcol = np.array([2, 0, 2], np.int32)
+    dY = (np.arange(m * n).reshape(m, n) % 7 - 3).astype(np.float64)
+    X = (np.arange(k * n).reshape(k, n) % 5 - 2).astype(np.float64)
+    dW = oracle.sddmm(m, k, b, brow, bcol, dY, X, lib=lib)
+    G = np.zeros((8, 12))
+    G[:m, :k] = dY @ X.T
+    for p in range(3):
+        assert np.array_equal(dW[p], G[brow[p] * b:(brow[p] + 1) * b,
+                                       bcol[p] * b:(bcol[p] + 1) * b])
+    assert not np.any(dW[1][2:]) and not np.any(dW[2][:, 2:])
+
+
+def check_sddmm_hand_example(lib):
+    """b = 2, one block at (0, 1) of a 2 x 4 W, n = 2, worked by hand:
+    dY = [[1, 2], [3, 4]], X rows 2, 3 = [5, 6], [7, 8] give
+    [[1*5+2*6, 1*7+2*8], [3*5+4*6, 3*7+4*8]] = [[17, 23], [39, 53]]."""
+    dY = np.array([[1.0, 2.0], [3.0, 4.0]])
+    X = np.array([[0.0, 0.0], [0.0, 0.0], [5.0, 6.0], [7.0, 8.0]])
+    dW = oracle.sddmm(2, 4, 2, np.array([0], np.int32), np.array([1], np.int32), dY, X,
+                      lib=lib)
+    assert np.array_equal(dW[0], np.array([[17.0, 23.0], [39.0, 53.0]]))
+
+
+SDDMM_CHECKS = [check_sddmm_masked_dense, check_sddmm_is_the_gradient,
+                check_sddmm_exact_integers_and_truncation, check_sddmm_hand_example]
+
+
+@pytest.mark.parametrize("check", SDDMM_CHECKS, ids=lambda f: f.__name__)
+def test_sddmm_pin(check):
+    check(oracle._load())
+
+
+def test_sddmm_empty_and_rejects_out_of_range():
+    out = oracle.sddmm(8, 8, 4, np.zeros(0, np.int32), np.zeros(0, np.int32),
+                       np.ones((8, 3)), np.ones((8, 3)))
+    assert out.shape == (0, 4, 4)
+    with pytest.raises(ValueError):
+        oracle.sddmm(8, 8, 4, np.array([0], np.int32), np.array([2], np.int32),
+                     np.ones((8, 3)), np.ones((8, 3)))
