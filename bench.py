@@ -288,12 +288,14 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-transposed", action="store_true")
+    ap.add_argument("--no-sddmm", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--point", default=None,
                     help="run one sweep point only, 'b:1/d' e.g. 16:4 (profiling); the other "
                          "sections are then skipped unless named by --section")
     ap.add_argument("--section", action="append", default=[],
-                    choices=["gather_small_n", "dynamic", "batched", "serving", "transposed"],
+                    choices=["gather_small_n", "dynamic", "batched", "serving", "transposed",
+                             "sddmm"],
                     help="with --point: also run this section (repeatable)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -417,7 +419,7 @@ def main():
             q["b"] == 16 and abs(q["d"] - 1 / 16) < 1e-12 for q in pts):
         comparators = run_comparators(torch, S, wl, dev, pts)
 
-    dynamic = batched = serving = gsmall = transposed = None
+    dynamic = batched = serving = gsmall = transposed = sddmm = None
 
     def want(name, off=False):
         return rank == 0 and not off and (args.point is None or name in args.section)
@@ -431,6 +433,8 @@ def main():
         serving = run_serving(torch, S, wl, dev)
     if want("transposed", args.no_transposed):
         transposed = run_transposed(torch, S, wl, dev)
+    if want("sddmm", args.no_sddmm):
+        sddmm = run_sddmm(torch, S, wl, dev, peaks)
 
     launches = sum(launches_per_run(p) for p in pts) * args.steps
     if rank == 0:
@@ -442,7 +446,8 @@ def main():
                 "e2e": e2e, "gpu_launches": launches, "clocks": sampler.summary(),
                 "roofline": roofline, "cpu_baseline": cpu, "points": points,
                 "comparators": comparators, "dynamic": dynamic, "batched": batched,
-                "serving": serving, "gather_small_n": gsmall, "transposed": transposed}
+                "serving": serving, "gather_small_n": gsmall, "transposed": transposed,
+                "sddmm": sddmm}
         print(json.dumps(line))
     for p in pts:
         p["plan"].close()
@@ -751,6 +756,52 @@ def run_transposed(torch, S, wl, dev, reps=15,
     del flush
     return {"workload": "Z = W^T.Y vs Y = W.X on one W, m=k=4096, n=2048, FP16; L2 evicted "
                         "(256 MB written and read back) before every timed run", "points": out}
+
+
+def run_sddmm(torch, S, wl, dev, peaks, reps=10,
+              cases=((16, 1 / 16), (16, 1 / 4), (8, 1 / 16), (4, 1 / 16), (1, 1 / 16))):
+    """The sampled product dW = (dY.X^T) on the block mask, m = k = 4096,
+    n = 2048, BF16 inputs, FP32 dW; each timed run follows an L2 eviction
+    (256 MB written and read back) and the events bracket the call alone.
+    Useful FLOPs 2 nnzb b^2 n; the dense-tile kernel computes every 128 x 256
+    tile, so its roofline is the tensor peak on 2 m k n."""
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = []
+    for b, d in cases:
+        c = wl.sddmm_problem(sweep_seed_sd(b, d), M, K, N, b, wl.nnzb_for(M, K, b, d))
+        dY = torch.from_numpy(c["dY"]).bfloat16().to(dev)
+        X = torch.from_numpy(c["X"]).bfloat16().to(dev)
+        plan = S.Plan(M, K, N, b, w_dtype=S.BF16, brow=c["brow"], bcol=c["bcol"])
+        dW = torch.empty((len(c["brow"]), b, b), dtype=torch.float32, device=dev)
+        for _ in range(3):
+            plan.sddmm(dY, X, dW)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            flush.max()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            plan.sddmm(dY, X, dW)
+            e.record()
+            e.synchronize()
+            ts.append(a.elapsed_time(e) * 1e3)
+        if plan.status() != 0:
+            raise RuntimeError("plan status %d" % plan.status())
+        us = statistics.median(ts)
+        dense = 2.0 * M * K * N / us / 1e6
+        out.append({"b": b, "d": "1/%d" % round(1 / d), "kernel": "sddmm_dense", "us": round(us, 2),
+                    "tflops_nz": round(2.0 * len(c["brow"]) * b * b * N / us / 1e6, 2),
+                    "tflops_dense_equiv": round(dense, 1),
+                    "frac_of_tensor_peak": round(dense / peaks["bf16_tflops"], 3)})
+        plan.close()
+        del dY, X, dW
+    del flush
+    return {"workload": "dW = (dY.X^T) on the block mask, m=k=4096, n=2048, BF16 in, FP32 out; "
+                        "L2 evicted before every timed run", "points": out}
+
+
+def sweep_seed_sd(b, d):
+    return 7000 + 10 * b + int(round(math.log2(1 / d)))
 
 
 def run_comparators(torch, S, wl, dev, pts):

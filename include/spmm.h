@@ -272,6 +272,36 @@ spmm_status spmm_gather_noalloc(int64_t m, int64_t k, spmm_dtype dtype, const in
 spmm_status spmm_quantize_e4m3(int64_t nnzb, int32_t b, spmm_dtype src_dtype, const void *d_src,
                                uint8_t *d_codes, float *d_scales, void *stream);
 
+/*
+ * spmm_sddmm -- the sampled dense-dense product on the plan's block mask,
+ * i.e. the gradient of Section 3's product with respect to the stored blocks
+ * (the weight-gradient step of sparse training, Section 1):
+ *   dW[p][ii][l] = sum_{j < n} dY[brow_p*b + ii, j] * X[bcol_p*b + l, j]
+ * for every block p of the pattern, FP32 accumulation.
+ *   plan          : a device plan for W (not transposed, not host-only) whose
+ *                   x_dtype is F16 or BF16; its w_dtype plays no part.
+ *   pattern       : dynamic plans: the device pattern of this step (rebuilt
+ *                   into the plan's block CSR and validated on the device, as
+ *                   in spmm_run; a rejected pattern sets the status word and
+ *                   dW is not written).  Static plans: NULL (the plan's own).
+ *   d_dY, lddy    : dY (m x n, x_dtype), row-major, lddy >= n.
+ *   d_X, ldx      : X (k x n, x_dtype), row-major, ldx >= n.
+ *                   Both base addresses 16-byte aligned and lddy, ldx
+ *                   multiples of 8 elements (rows are read by TMA), else
+ *                   SPMM_ERR_ARG.
+ *   n             : >= 0 (no n_max limit); n = 0 writes zero blocks (dY and
+ *                   X may then be NULL).
+ *   d_dW          : device output, the pattern's blocks in the pattern's
+ *                   order, each b x b row-major (the layout spmm_pack_values
+ *                   reads), 16-byte aligned; static: nnzb blocks, dynamic:
+ *                   room for nnzb_max blocks, of which *d_nnzb are written.
+ *   dw_dtype      : F32, or the plan's x_dtype (rounded to nearest even).
+ * Asynchronous on `stream`, CUDA-graph capturable for static plans.
+ */
+spmm_status spmm_sddmm(spmm_plan *plan, const spmm_dpattern *pattern, const void *d_dY,
+                       int64_t lddy, const void *d_X, int64_t ldx, int64_t n, void *d_dW,
+                       spmm_dtype dw_dtype, void *stream);
+
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char *spmm_last_error(void);
 

@@ -29,7 +29,7 @@ def sources():
 
 def _compile(src, extra):
     obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     inc = os.path.join(ROOT, "include")
     headers += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     newest = max(os.path.getmtime(p) for p in [src] + headers)

@@ -872,4 +872,46 @@ spmm_status spmm_quantize_e4m3(int64_t nnzb, int32_t b, spmm_dtype src_dtype, co
     return SPMM_OK;
 }
 
+spmm_status spmm_sddmm(spmm_plan *plan, const spmm_dpattern *pattern, const void *d_dY,
+                       int64_t lddy, const void *d_X, int64_t ldx, int64_t n, void *d_dW,
+                       spmm_dtype dw_dtype, void *stream) {
+    g_err[0] = 0;
+    if (!plan || plan->host_only || plan->transposed) {
+        set_error("sddmm: plan is NULL, host-only or transposed");
+        return SPMM_ERR_ARG;
+    }
+    if (!(plan->xdt == SPMM_F16 || plan->xdt == SPMM_BF16)) {
+        set_error("sddmm: the plan's x_dtype must be F16 or BF16");
+        return SPMM_ERR_UNSUPPORTED;
+    }
+    if (!(dw_dtype == SPMM_F32 || dw_dtype == plan->xdt)) {
+        set_error("sddmm: dw_dtype must be F32 or the plan's x_dtype");
+        return SPMM_ERR_ARG;
+    }
+    if (n < 0 || lddy < std::max<int64_t>(n, 1) || ldx < std::max<int64_t>(n, 1) || lddy % 8 ||
+        ldx % 8) {
+        set_error("sddmm: n >= 0, lddy and ldx >= max(n, 1) and multiples of 8 elements");
+        return SPMM_ERR_ARG;
+    }
+    if (!d_dW || (n > 0 && (!d_dY || !d_X)) ||
+        ((uintptr_t)d_dY | (uintptr_t)d_X | (uintptr_t)d_dW) % 16) {
+        set_error("sddmm: dW (and for n > 0 dY and X) required, 16-byte aligned");
+        return SPMM_ERR_ARG;
+    }
+    const bool dyn = plan->mode == SPMM_DYNAMIC;
+    if (dyn != (pattern != nullptr) ||
+        (dyn && (!pattern->d_nnzb || !pattern->d_brow || !pattern->d_bcol))) {
+        set_error("sddmm: dynamic plans need the step's device pattern, static plans none");
+        return SPMM_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    spmm_status st = busy_check(plan, s);
+    if (st != SPMM_OK) return st;
+    if (!dyn && plan->nnzb == 0) return finish_call(plan, s);
+    cudaError_t e = dyn ? launch_dynamic_csr(plan, pattern, s) : cudaSuccess;
+    if (e == cudaSuccess) e = launch_sddmm(plan, d_dY, lddy, d_X, ldx, n, d_dW, dw_dtype, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sddmm");
+    return finish_call(plan, s);
+}
+
 }  // extern "C"

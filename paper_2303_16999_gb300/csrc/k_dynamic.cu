@@ -407,6 +407,27 @@ inline unsigned grid_for(int64_t n, int threads, unsigned cap) {
 
 }  // namespace
 
+cudaError_t launch_dynamic_csr(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s) {
+    DynBufs &d = p->dyn;
+    const int32_t mb = (int32_t)(p->m / p->b), kb = (int32_t)(p->k / p->b);
+    const int64_t cap = p->nnzb_max;
+    cudaError_t e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.row_cnt, 0, sizeof(int32_t) * mb, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_counts, 0, sizeof(int32_t) * kCntCount, s);
+    if (e != cudaSuccess) return e;
+    const unsigned gp = grid_for(cap, 256, 4096);
+    pdl_launch(dyn_validate_hist, dim3(gp), dim3(256), 0, s, dp->d_nnzb, dp->d_brow, dp->d_bcol,
+        cap, mb, kb, d.row_cnt, p->d_status);
+    pdl_launch(dyn_scan_rows, dim3(1), dim3(1024), 0, s, dp->d_nnzb, cap, mb, d.row_cnt,
+        p->d_row_ptr, d.cursor, d.row_ibeg, d.row_wbeg, d.row_rbeg, p->d_counts, 0);
+    pdl_launch(dyn_scatter, dim3(gp), dim3(256), 0, s, dp->d_nnzb, dp->d_brow, dp->d_bcol, cap, mb,
+        kb, d.cursor, d.tmp_col, d.tmp_perm);
+    pdl_launch(dyn_sort_rows, dim3(grid_for((int64_t)mb * 32, 256, 1u << 30)), dim3(256), 0, s, mb,
+        p->d_row_ptr, d.tmp_col, d.tmp_perm, p->d_col_idx, p->d_perm, p->d_status, 0,
+        d.row_ibeg, d.row_wbeg, d.row_rbeg, p->d_counts, p->d_items, p->d_ws_row0, p->d_red);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s) {
     DynBufs &d = p->dyn;
     const int32_t mb = (int32_t)(p->m / p->b), kb = (int32_t)(p->k / p->b);

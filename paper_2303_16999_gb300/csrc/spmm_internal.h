@@ -150,6 +150,11 @@ cudaError_t launch_quantize_e4m3(int64_t nnzb, int b, spmm_dtype src, const void
                                  uint8_t *d_codes, float *d_scales, cudaStream_t s);
 constexpr int kMaxBatchProblems = 64;
 cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s);
+// the block CSR part of the re-partition only (row_ptr, col_idx, perm; validation)
+cudaError_t launch_dynamic_csr(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s);
+// sampled dense-dense product on the plan's block CSR (k_sddmm.cu)
+cudaError_t launch_sddmm(const spmm_plan *p, const void *d_dY, int64_t lddy, const void *d_X,
+                         int64_t ldx, int64_t n, void *d_dW, spmm_dtype dw_dtype, cudaStream_t s);
 
 size_t dtype_size(spmm_dtype t);
 

@@ -39,7 +39,8 @@ SERVE_EXPORTS = ["serve_create", "serve_register_weight", "serve_submit", "serve
 EXPORTS = ["spmm_plan_create", "spmm_pack_values", "spmm_run", "spmm_run_host",
            "spmm_get_status", "spmm_plan_get_info", "spmm_plan_get_array",
            "spmm_plan_destroy", "spmm_equal_partition", "spmm_bucket_size", "spmm_batch_run",
-           "spmm_last_error", "spmm_version", "spmm_gather_noalloc", "spmm_quantize_e4m3"]
+           "spmm_last_error", "spmm_version", "spmm_gather_noalloc", "spmm_quantize_e4m3",
+           "spmm_sddmm"]
 
 
 class SpmmError(RuntimeError):
@@ -117,6 +118,8 @@ def lib():
         L.spmm_gather_noalloc.argtypes = [i64, i64, i32, vp, vp, vp, i64, vp, vp, i64, i64, vp,
                                           i64, vp, vp]
         L.spmm_quantize_e4m3.argtypes = [i64, i32, i32, vp, vp, vp, vp]
+        L.spmm_sddmm.argtypes = [vp, ctypes.POINTER(DPattern), vp, i64, vp, i64, i64, vp, i32,
+                                 vp]
         L.spmm_last_error.restype = ctypes.c_char_p
         L.spmm_version.restype = ctypes.c_char_p
         L.serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
@@ -210,6 +213,11 @@ def spmm_gather_noalloc(m, k, dtype, d_nnzb, d_brow, d_bcol, nnzb_max, d_values,
 
 def spmm_quantize_e4m3(nnzb, b, src_dtype, d_src, d_codes, d_scales, stream):
     return _check(lib().spmm_quantize_e4m3(nnzb, b, src_dtype, d_src, d_codes, d_scales, stream))
+
+
+def spmm_sddmm(plan, dpat, d_dY, lddy, d_X, ldx, n, d_dW, dw_dtype, stream):
+    """The sampled product dW = (dY.X^T) on the plan's block mask (see include/spmm.h)."""
+    return _check(lib().spmm_sddmm(plan, dpat, d_dY, lddy, d_X, ldx, n, d_dW, dw_dtype, stream))
 
 
 def quantize_e4m3(values, stream=None):
@@ -322,6 +330,27 @@ class Plan:
 
     def status(self):
         return spmm_get_status(self.h)
+
+    def sddmm(self, dY, X, dW=None, dw_dtype=None, pattern=None, capacity=None, stream=None):
+        """dW = (dY.X^T) on the plan's block mask for device tensors dY (m x n)
+        and X (k x n); returns dW (blocks, b, b) in the pattern's order
+        (allocated if not given: nnzb blocks, or ``capacity`` / nnzb_max
+        for dynamic plans).  dw_dtype defaults to FP32."""
+        import torch
+        if dW is None:
+            want = torch.float32 if dw_dtype is None else dw_dtype
+            if pattern is not None:
+                blocks = capacity if capacity is not None else self.info()["nnzb_max"]
+            else:
+                blocks = self.info()["nnzb"]
+            dW = torch.empty((blocks, self.b, self.b), dtype=want, device=dY.device)
+        dp = None
+        if pattern is not None:
+            d_nnzb, d_brow, d_bcol = pattern
+            dp = DPattern(d_nnzb.data_ptr(), d_brow.data_ptr(), d_bcol.data_ptr())
+        spmm_sddmm(self.h, dp, _ptr(dY), dY.stride(0), _ptr(X), X.stride(0), X.shape[1],
+                   _ptr(dW), dtype_code(dW.dtype), _stream_handle(stream))
+        return dW
 
 
 def spmm_batch_run(plans, Xs, Ys, stream=None):

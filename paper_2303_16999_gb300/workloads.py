@@ -43,6 +43,16 @@ def transposed_problem(seed, m, k, n, b, nnzb):
     return dict(m=m, k=k, n=n, b=b, brow=brow, bcol=bcol, vals=vals, Y=Y, seed=seed)
 
 
+def sddmm_problem(seed, m, k, n, b, nnzb):
+    """Operands of dW = (dY.X^T) on W's mask: the pattern as in problem()
+    (W is m x k), then dY f32 (m, n) and X f32 (k, n)."""
+    rng = rng_for(seed)
+    brow, bcol = pattern(rng, m // b, k // b, nnzb)
+    dY = rng.standard_normal((m, n), dtype=np.float32)
+    X = rng.standard_normal((k, n), dtype=np.float32)
+    return dict(m=m, k=k, n=n, b=b, brow=brow, bcol=bcol, dY=dY, X=X, seed=seed)
+
+
 def nnzb_for(m, k, b, d):
     """nnzb = d * (m/b) * (k/b); Section 3 defines d over the element mask,
     which for b x b blocks is the same fraction of the block grid."""

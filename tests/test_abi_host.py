@@ -74,6 +74,10 @@ def test_errors():
     assert e.value.status == S.ERR_UNSUPPORTED
     p = _plan(16, 16, 4, [], [])
     assert p.info()["nnzb"] == 0
+    # the sampled product refuses host-only plans before touching the device
+    with pytest.raises(S.SpmmError) as e:
+        S.spmm_sddmm(p.h, None, 16, 8, 16, 8, 4, 16, S.F32, None)
+    assert e.value.status == S.ERR_ARG
 
 
 def _rand(rng, mb, kb, nnzb):
