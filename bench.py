@@ -289,13 +289,16 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-transposed", action="store_true")
     ap.add_argument("--no-sddmm", action="store_true")
+    ap.add_argument("--refit", action="store_true",
+                    help="also sweep m, n, b, d against cuBLAS dense and refit the speed-up "
+                         "power law (a few minutes; off by default)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--point", default=None,
                     help="run one sweep point only, 'b:1/d' e.g. 16:4 (profiling); the other "
                          "sections are then skipped unless named by --section")
     ap.add_argument("--section", action="append", default=[],
                     choices=["gather_small_n", "dynamic", "batched", "serving", "transposed",
-                             "sddmm"],
+                             "sddmm", "refit"],
                     help="with --point: also run this section (repeatable)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -419,7 +422,7 @@ def main():
             q["b"] == 16 and abs(q["d"] - 1 / 16) < 1e-12 for q in pts):
         comparators = run_comparators(torch, S, wl, dev, pts)
 
-    dynamic = batched = serving = gsmall = transposed = sddmm = None
+    dynamic = batched = serving = gsmall = transposed = sddmm = refit = None
 
     def want(name, off=False):
         return rank == 0 and not off and (args.point is None or name in args.section)
@@ -435,6 +438,8 @@ def main():
         transposed = run_transposed(torch, S, wl, dev)
     if want("sddmm", args.no_sddmm):
         sddmm = run_sddmm(torch, S, wl, dev, peaks)
+    if rank == 0 and (args.refit or (args.point is not None and "refit" in args.section)):
+        refit = run_refit(torch, S, wl, dev)
 
     launches = sum(launches_per_run(p) for p in pts) * args.steps
     if rank == 0:
@@ -447,7 +452,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "points": points,
                 "comparators": comparators, "dynamic": dynamic, "batched": batched,
                 "serving": serving, "gather_small_n": gsmall, "transposed": transposed,
-                "sddmm": sddmm}
+                "sddmm": sddmm, "refit": refit}
         print(json.dumps(line))
     for p in pts:
         p["plan"].close()
@@ -533,6 +538,23 @@ def run_dynamic(torch, S, wl, dev, calls=4, reps=10):
         dplan.run(i0["X"], Y, values=i0["vals"], pattern=i0["pat"])
     t_dyn0 = graph_time_us(torch, one_dyn, reps)
     fl0 = 2.0 * len(i0["c"]["brow"]) * 256 * n
+
+    # the same calls in Blocked-ELL form (width = each pattern's longest row)
+    for i in inputs:
+        cols, src = wl.to_ell(i["c"]["brow"], i["c"]["bcol"], m // 16)
+        ev = torch.zeros((m // 16, cols.shape[1], 16, 16), dtype=bf)
+        sel = src >= 0
+        ev[torch.from_numpy(sel)] = torch.from_numpy(i["c"]["vals"]).to(bf)[
+            torch.from_numpy(src[sel])]
+        i["ell"] = (torch.from_numpy(cols).to(dev), ev.to(dev))
+
+    def ell_fn():
+        for i in inputs:
+            dplan.run_ell(i["ell"][0], i["ell"][1], i["X"], Y)
+    t_ell = graph_time_us(torch, ell_fn, reps) / calls
+    if dplan.status() != 0:
+        raise RuntimeError("ELL status %d" % dplan.status())
+    widths = [int(i["ell"][0].shape[1]) for i in inputs]
     out = {"workload": "dynamic m=k=8192 n=1024 b=16 d_max=1/16 BF16, fresh pattern per call",
            "us_per_call": round(t_dyn, 1), "tflops_nz": round(flops / calls / t_dyn / 1e6, 2),
            "repartition_pack_us": round(t_part, 1),
@@ -540,6 +562,11 @@ def run_dynamic(torch, S, wl, dev, calls=4, reps=10):
            "dynamic_same_pattern_us": round(t_dyn0, 1),
            "dynamic_over_static_time": round(t_dyn0 / t_static, 3),
            "static_tflops_nz": round(fl0 / t_static / 1e6, 2),
+           "ell": {"us_per_call": round(t_ell, 1),
+                   "tflops_nz": round(flops / calls / t_ell / 1e6, 2),
+                   "widths": widths, "ell_over_csr_time": round(t_ell / t_dyn, 3),
+                   "ell_over_static_time": round(t_ell / t_static, 3),
+                   "launches_per_call": 2},
            "gpu_launches_per_call": None}
     dplan.close()
     splan.close()
@@ -798,6 +825,119 @@ def run_sddmm(torch, S, wl, dev, peaks, reps=10,
     del flush
     return {"workload": "dW = (dY.X^T) on the block mask, m=k=4096, n=2048, BF16 in, FP32 out; "
                         "L2 evicted before every timed run", "points": out}
+
+
+def fit_power_law(rows):
+    """Least squares in log space: log S = log c + alpha log m + beta log d +
+    gamma log b over rows (m, d, b, S), the form of the speed-up model of
+    Section 5 ("Will my application speed up?").  Returns (c, alpha, beta,
+    gamma, r2)."""
+    A = np.array([[1.0, math.log(m), math.log(d), math.log(b)] for m, d, b, _ in rows])
+    y = np.array([math.log(r[3]) for r in rows])
+    coef, *_ = np.linalg.lstsq(A, y, rcond=None)
+    res = y - A @ coef
+    tot = y - y.mean()
+    r2 = 1.0 - float(res @ res) / float(tot @ tot) if float(tot @ tot) > 0 else 1.0
+    return math.exp(coef[0]), float(coef[1]), float(coef[2]), float(coef[3]), r2
+
+
+def run_refit(torch, S, wl, dev, ms=(1024, 2048, 4096, 8192), ns=(256, 1024, 4096, 16384),
+              bs=(1, 4, 8, 16), ds=(1 / 32, 1 / 16, 1 / 8, 1 / 4), reps=5):
+    """The paper's static sweep on this GPU (Table 2's m = k, n, b, d grid,
+    FP16): speed-up S = best-over-n sparse TFLOP/s / best-over-n dense
+    TFLOP/s, both counting the useful 2 m k n d FLOPs, i.e. cuBLAS dense
+    time over sparse time at each side's best n; then the power law of
+    Section 5 refitted to S, the largest density with S > 1 per (b, m), and
+    cuSPARSE CSR / BSR context at m = k = 4096, n = 2048, d = 1/16.  Timed
+    with CUDA events (median of reps after two warm-up runs), L2 warm on
+    both sides alike."""
+    def med_us(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            e.record()
+            e.synchronize()
+            ts.append(a.elapsed_time(e) * 1e3)
+        return statistics.median(ts)
+
+    t0 = time.perf_counter()
+    rows, grid = [], []
+    for m in ms:
+        rng = np.random.default_rng(m)
+        Xs = {n: torch.from_numpy(rng.standard_normal((m, n), dtype=np.float32)).half().to(dev)
+              for n in ns}
+        Ys = {n: torch.empty((m, n), dtype=torch.float16, device=dev) for n in ns}
+        Wd = torch.from_numpy(rng.standard_normal((m, m), dtype=np.float32)).half().to(dev)
+        dense = max(2.0 * m * m * n / med_us(lambda: torch.matmul(Wd, Xs[n], out=Ys[n])) / 1e6
+                    for n in ns)
+        del Wd
+        for b in bs:
+            for d in ds:
+                c = wl.problem(90000 + m + 100 * b + int(round(1 / d)), m, m, 0, b,
+                               wl.nnzb_for(m, m, b, d))
+                plan = S.Plan(m, m, max(ns), b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"])
+                plan.pack(torch.from_numpy(c["vals"]).half().to(dev))
+                best, best_n = 0.0, 0
+                for n in ns:
+                    us = med_us(lambda: plan.run(Xs[n], Ys[n]))
+                    tf = 2.0 * len(c["brow"]) * b * b * n / us / 1e6
+                    if tf > best:
+                        best, best_n = tf, n
+                if plan.status() != 0:
+                    raise RuntimeError("plan status %d" % plan.status())
+                plan.close()
+                sp = best / (d * dense)
+                rows.append((m, d, b, sp))
+                grid.append({"m": m, "b": b, "d": "1/%d" % round(1 / d),
+                             "sparse_tflops_nz": round(best, 2), "best_n": best_n,
+                             "dense_tflops": round(dense, 1), "speedup": round(sp, 3)})
+        del Xs, Ys
+    cfit, al, be, ga, r2 = fit_power_law(rows)
+    thresholds = {}
+    for label, bset in (("b=1", (1,)), ("b>=4", (4, 8, 16)), ("b>=8", (8, 16))):
+        for m in ms:
+            ok = [d for d in ds if all(sp > 1.0 for (mm, dd, bb, sp) in rows
+                                      if mm == m and dd == d and bb in bset)]
+            thresholds["%s, m=k=%d" % (label, m)] = ("d <= 1/%d" % round(1 / max(ok))) if ok else None
+    context = {}
+    try:
+        m, n, d = 4096, 2048, 1 / 16
+        X = torch.from_numpy(np.random.default_rng(5).standard_normal((m, n), dtype=np.float32))
+        for b, label in ((1, "cusparse_csr"), (16, "cusparse_bsr")):
+            c = wl.problem(777 + b, m, m, 0, b, wl.nnzb_for(m, m, b, d))
+            Wd = torch.zeros((m, m), dtype=torch.float32)
+            Wd.view(m // b, b, m // b, b).permute(0, 2, 1, 3)[
+                torch.from_numpy(c["brow"]).long(), torch.from_numpy(c["bcol"]).long()] = \
+                torch.from_numpy(c["vals"])
+            for dt in (torch.float16, torch.float32):
+                try:
+                    if b == 1:
+                        A = Wd.to(dt).to(dev).to_sparse_csr()
+                    else:
+                        A = Wd.to(dt).to(dev).to_sparse_bsr((b, b))
+                    Xd = X.to(dt).to(dev)
+                    us = med_us(lambda: torch.matmul(A, Xd))
+                    context["%s_%s" % (label, "fp16" if dt == torch.float16 else "fp32")] = {
+                        "us": round(us, 1),
+                        "tflops_nz": round(2.0 * len(c["brow"]) * b * b * n / us / 1e6, 2)}
+                except (RuntimeError, NotImplementedError) as ex:
+                    context["%s_%s" % (label, "fp16" if dt == torch.float16 else "fp32")] = \
+                        "unsupported: %s" % str(ex).splitlines()[0][:120]
+    except Exception as ex:  # context only: never fail the benchmark over it
+        context["error"] = str(ex).splitlines()[0][:200]
+    return {"workload": "static sweep m=k in %s, n in %s (best over n), b in %s, d in %s, FP16; "
+                        "speed-up = sparse TFLOP/s / dense (cuBLAS) TFLOP/s, useful FLOPs both"
+                        % (list(ms), list(ns), list(bs), ["1/%d" % round(1 / v) for v in ds]),
+            "fit": {"c": cfit, "alpha_m": round(al, 3), "beta_d": round(be, 3),
+                    "gamma_b": round(ga, 3), "r2": round(r2, 3),
+                    "condition": "%.3g * m^%.2f * d^%.2f * b^%.2f > 1" % (cfit, al, be, ga)},
+            "thresholds": thresholds, "grid": grid, "cusparse_context": context,
+            "seconds": round(time.perf_counter() - t0, 1)}
 
 
 def sweep_seed_sd(b, d):

@@ -273,6 +273,30 @@ spmm_status spmm_quantize_e4m3(int64_t nnzb, int32_t b, spmm_dtype src_dtype, co
                                uint8_t *d_codes, float *d_scales, void *stream);
 
 /*
+ * spmm_run_ell -- Y = W.X with W in Blocked-ELL form (padded block lists per
+ * block row, the FP16 block-sparse layout Section 5 discusses for GPUs),
+ * for dynamic sparsity without a device re-partition: a call validates the
+ * layout and runs one product launch.  b = 16 only.
+ *   plan        : a DYNAMIC device plan with b = 16 and w_dtype = x_dtype in
+ *                 {F16, BF16} (m, k multiples of 16); its re-partition
+ *                 buffers are not used.
+ *   d_ell_cols  : int32[(m/16) * ell_width] device: row r lists its block
+ *                 columns in slots r*ell_width ... in strictly increasing
+ *                 order, then -1 in every unused slot.
+ *   ell_width   : 0 <= ell_width <= k/16.
+ *   d_values    : (m/16) * ell_width blocks of 16 x 16 (x_dtype, row-major),
+ *                 block (r, slot e) at index r*ell_width + e, 16-byte
+ *                 aligned; values of padding slots are ignored.
+ *   d_X, n, ldx : X (k x n), 16-byte aligned, ldx a multiple of 8, n <= n_max.
+ *   d_Y, ldy    : Y (m x n).
+ * A layout that breaks these rules sets the status word to SPMM_ERR_PATTERN
+ * on the device and Y is not written.
+ */
+spmm_status spmm_run_ell(spmm_plan *plan, const int32_t *d_ell_cols, int32_t ell_width,
+                         const void *d_values, const void *d_X, int64_t n, int64_t ldx,
+                         void *d_Y, int64_t ldy, void *stream);
+
+/*
  * spmm_sddmm -- the sampled dense-dense product on the plan's block mask,
  * i.e. the gradient of Section 3's product with respect to the stored blocks
  * (the weight-gradient step of sparse training, Section 1):

@@ -872,6 +872,38 @@ spmm_status spmm_quantize_e4m3(int64_t nnzb, int32_t b, spmm_dtype src_dtype, co
     return SPMM_OK;
 }
 
+spmm_status spmm_run_ell(spmm_plan *plan, const int32_t *d_ell_cols, int32_t ell_width,
+                         const void *d_values, const void *d_X, int64_t n, int64_t ldx,
+                         void *d_Y, int64_t ldy, void *stream) {
+    g_err[0] = 0;
+    if (!plan || plan->host_only || plan->mode != SPMM_DYNAMIC || plan->transposed ||
+        plan->b != 16 || plan->kernel != SPMM_KERNEL_TC || plan->wdt != plan->xdt) {
+        set_error("ell: needs a dynamic, untransposed b = 16 tensor-core plan with w = x dtype");
+        return SPMM_ERR_UNSUPPORTED;
+    }
+    if (ell_width < 0 || ell_width > plan->k / 16) {
+        set_error("ell: ell_width must be in [0, k/16]");
+        return SPMM_ERR_SHAPE;
+    }
+    spmm_status st = check_run_args(plan, d_X, n, ldx, d_Y, ldy);
+    if (st != SPMM_OK) return st;
+    if (ell_width > 0 && (!d_ell_cols || !d_values || (uintptr_t)d_values % 16)) {
+        set_error("ell: columns and 16-byte aligned values required");
+        return SPMM_ERR_ARG;
+    }
+    if (n > 0 && ((uintptr_t)d_X % 16 || ldx % 8)) {
+        set_error("ell: X must be 16-byte aligned with ldx a multiple of 8");
+        return SPMM_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    st = busy_check(plan, s);
+    if (st != SPMM_OK) return st;
+    const cudaError_t e =
+        launch_ell(plan, d_ell_cols, ell_width, d_values, d_X, n, ldx, d_Y, ldy, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ell");
+    return finish_call(plan, s);
+}
+
 spmm_status spmm_sddmm(spmm_plan *plan, const spmm_dpattern *pattern, const void *d_dY,
                        int64_t lddy, const void *d_X, int64_t ldx, int64_t n, void *d_dW,
                        spmm_dtype dw_dtype, void *stream) {

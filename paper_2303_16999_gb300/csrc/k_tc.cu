@@ -928,39 +928,6 @@ __global__ void quantize_e4m3_kernel(const U *__restrict__ src, int64_t nnzb, in
             (uint8_t)__nv_cvt_float_to_fp8((float)v[e] / scale, __NV_SATFINITE, __NV_E4M3);
 }
 
-// X tensor map of one problem.  n a multiple of 64: X seen as (64 columns,
-// k rows, n/64 column blocks) so one 64 x 16 x 2 box is a whole 16 x 128 slab
-// (two 128-byte-swizzled halves, 2048 B apart); otherwise two 2-D 64 x 16
-// boxes per slab, whose out-of-range columns the TMA unit fills with zeros.
-cudaError_t encode_x(CUtensorMap *map, int *x3d, bool bf16, const void *X, int64_t k, int64_t n,
-                     int64_t ldx) {
-    auto enc = encode_fn();
-    if (!enc) return cudaErrorNotSupported;
-    if (((uintptr_t)X & 15) || (ldx * 2) % 16) return cudaErrorMisalignedAddress;
-    const auto dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    *x3d = (n % (kNTile / 2)) == 0 ? 1 : 0;
-    CUresult r;
-    if (*x3d) {
-        const cuuint64_t dims[3] = {(cuuint64_t)(kNTile / 2), (cuuint64_t)k,
-                                    (cuuint64_t)(n / (kNTile / 2))};
-        const cuuint64_t strides[2] = {(cuuint64_t)(ldx * 2), (cuuint64_t)kNTile};
-        const cuuint32_t box[3] = {kNTile / 2, kTile, 2};
-        const cuuint32_t estr[3] = {1, 1, 1};
-        r = enc(map, dt, 3, const_cast<void *>(X), dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    } else {
-        const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)k};
-        const cuuint64_t strides[1] = {(cuuint64_t)(ldx * 2)};
-        const cuuint32_t box[2] = {kNTile / 2, kTile};
-        const cuuint32_t estr[2] = {1, 1};
-        r = enc(map, dt, 2, const_cast<void *>(X), dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    }
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
 void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, int x3d) {
     P.items = p->d_items;
     P.grp_row0 = p->d_grp_row0;

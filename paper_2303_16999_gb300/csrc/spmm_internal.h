@@ -152,6 +152,10 @@ constexpr int kMaxBatchProblems = 64;
 cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s);
 // the block CSR part of the re-partition only (row_ptr, col_idx, perm; validation)
 cudaError_t launch_dynamic_csr(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s);
+// Blocked-ELL product, b = 16 (k_ell.cu): validation + one product launch
+cudaError_t launch_ell(spmm_plan *p, const int32_t *d_cols, int32_t E, const void *d_values,
+                       const void *d_X, int64_t n, int64_t ldx, void *d_Y, int64_t ldy,
+                       cudaStream_t s);
 // sampled dense-dense product on the plan's block CSR (k_sddmm.cu)
 cudaError_t launch_sddmm(const spmm_plan *p, const void *d_dY, int64_t lddy, const void *d_X,
                          int64_t ldx, int64_t n, void *d_dW, spmm_dtype dw_dtype, cudaStream_t s);

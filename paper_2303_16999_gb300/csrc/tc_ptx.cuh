@@ -170,6 +170,42 @@ inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// X slabs (16 rows of X x 128 columns of n, two 128-byte-swizzled halves of
+// 64 columns) as the MN-major A operand of the products.
+constexpr int kSlabRows = 16, kSlabHalf = 64;
+// X tensor map of one problem.  n a multiple of 64: X seen as (64 columns,
+// k rows, n/64 column blocks) so one 64 x 16 x 2 box is a whole 16 x 128 slab
+// (two 128-byte-swizzled halves, 2048 B apart); otherwise two 2-D 64 x 16
+// boxes per slab, whose out-of-range columns the TMA unit fills with zeros.
+inline cudaError_t encode_x(CUtensorMap *map, int *x3d, bool bf16, const void *X, int64_t k,
+                            int64_t n, int64_t ldx) {
+    auto enc = encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    if (((uintptr_t)X & 15) || (ldx * 2) % 16) return cudaErrorMisalignedAddress;
+    const auto dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    *x3d = (n % kSlabHalf) == 0 ? 1 : 0;
+    CUresult r;
+    if (*x3d) {
+        const cuuint64_t dims[3] = {(cuuint64_t)kSlabHalf, (cuuint64_t)k,
+                                    (cuuint64_t)(n / kSlabHalf)};
+        const cuuint64_t strides[2] = {(cuuint64_t)(ldx * 2), (cuuint64_t)(kSlabHalf * 2)};
+        const cuuint32_t box[3] = {kSlabHalf, kSlabRows, 2};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        r = enc(map, dt, 3, const_cast<void *>(X), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)k};
+        const cuuint64_t strides[1] = {(cuuint64_t)(ldx * 2)};
+        const cuuint32_t box[2] = {kSlabHalf, kSlabRows};
+        const cuuint32_t estr[2] = {1, 1};
+        r = enc(map, dt, 2, const_cast<void *>(X), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 }  // namespace
 }  // namespace spmm
 

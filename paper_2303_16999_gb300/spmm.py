@@ -40,7 +40,7 @@ EXPORTS = ["spmm_plan_create", "spmm_pack_values", "spmm_run", "spmm_run_host",
            "spmm_get_status", "spmm_plan_get_info", "spmm_plan_get_array",
            "spmm_plan_destroy", "spmm_equal_partition", "spmm_bucket_size", "spmm_batch_run",
            "spmm_last_error", "spmm_version", "spmm_gather_noalloc", "spmm_quantize_e4m3",
-           "spmm_sddmm"]
+           "spmm_sddmm", "spmm_run_ell"]
 
 
 class SpmmError(RuntimeError):
@@ -120,6 +120,7 @@ def lib():
         L.spmm_quantize_e4m3.argtypes = [i64, i32, i32, vp, vp, vp, vp]
         L.spmm_sddmm.argtypes = [vp, ctypes.POINTER(DPattern), vp, i64, vp, i64, i64, vp, i32,
                                  vp]
+        L.spmm_run_ell.argtypes = [vp, vp, i32, vp, vp, i64, i64, vp, i64, vp]
         L.spmm_last_error.restype = ctypes.c_char_p
         L.spmm_version.restype = ctypes.c_char_p
         L.serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
@@ -218,6 +219,12 @@ def spmm_quantize_e4m3(nnzb, b, src_dtype, d_src, d_codes, d_scales, stream):
 def spmm_sddmm(plan, dpat, d_dY, lddy, d_X, ldx, n, d_dW, dw_dtype, stream):
     """The sampled product dW = (dY.X^T) on the plan's block mask (see include/spmm.h)."""
     return _check(lib().spmm_sddmm(plan, dpat, d_dY, lddy, d_X, ldx, n, d_dW, dw_dtype, stream))
+
+
+def spmm_run_ell(plan, d_ell_cols, ell_width, d_values, d_X, n, ldx, d_Y, ldy, stream):
+    """Y = W.X with W in Blocked-ELL form, b = 16 (see include/spmm.h)."""
+    return _check(lib().spmm_run_ell(plan, d_ell_cols, ell_width, d_values, d_X, n, ldx, d_Y,
+                                     ldy, stream))
 
 
 def quantize_e4m3(values, stream=None):
@@ -330,6 +337,18 @@ class Plan:
 
     def status(self):
         return spmm_get_status(self.h)
+
+    def run_ell(self, ell_cols, values, X, Y=None, stream=None):
+        """Y = W.X for W in Blocked-ELL form: ell_cols (m/16, E) int32 and
+        values (m/16, E, 16, 16) device tensors (dynamic b = 16 plans)."""
+        import torch
+        n = X.shape[1]
+        if Y is None:
+            Y = torch.empty((self.m, n), dtype=X.dtype, device=X.device)
+        width = ell_cols.shape[1] if ell_cols.dim() == 2 else 0
+        spmm_run_ell(self.h, _ptr(ell_cols), width, _ptr(values), _ptr(X), n, X.stride(0),
+                     _ptr(Y), Y.stride(0), _stream_handle(stream))
+        return Y
 
     def sddmm(self, dY, X, dW=None, dw_dtype=None, pattern=None, capacity=None, stream=None):
         """dW = (dY.X^T) on the plan's block mask for device tensors dY (m x n)

@@ -53,6 +53,28 @@ def sddmm_problem(seed, m, k, n, b, nnzb):
     return dict(m=m, k=k, n=n, b=b, brow=brow, bcol=bcol, dY=dY, X=X, seed=seed)
 
 
+def to_ell(brow, bcol, mb, width=None):
+    """Blocked-ELL layout of a block pattern: cols (mb, E) int32 with each
+    row's block columns ascending and -1 padding, and src (mb, E) int64, the
+    pattern index of each slot (-1 for padding).  E = the largest row count
+    unless a larger width is given."""
+    brow = np.asarray(brow, np.int64)
+    bcol = np.asarray(bcol, np.int64)
+    counts = np.bincount(brow, minlength=mb) if len(brow) else np.zeros(mb, np.int64)
+    E = int(counts.max()) if len(brow) else 0
+    E = E if width is None else int(width)
+    cols = np.full((mb, E), -1, np.int32)
+    src = np.full((mb, E), -1, np.int64)
+    order = np.lexsort((bcol, brow))
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    for i, p in enumerate(order):
+        r = brow[p]
+        e = i - starts[r]
+        cols[r, e] = bcol[p]
+        src[r, e] = p
+    return cols, src
+
+
 def nnzb_for(m, k, b, d):
     """nnzb = d * (m/b) * (k/b); Section 3 defines d over the element mask,
     which for b x b blocks is the same fraction of the block grid."""

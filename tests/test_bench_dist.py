@@ -73,3 +73,17 @@ def test_reference_arm_prints_on_rank0_only(rank, prints):
         import json
         d = json.loads(lines[-1])
         assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_power_law_fit_recovers_exponents():
+    """The speed-up model refit: exact power-law data gives back its
+    coefficient and exponents, and R^2 = 1."""
+    bench = _bench()
+    rows = []
+    for m in (1024, 2048, 4096, 8192):
+        for d in (1 / 32, 1 / 16, 1 / 8, 1 / 4):
+            for b in (1, 4, 8, 16):
+                rows.append((m, d, b, 0.0013 * m ** 0.59 * d ** -0.54 * b ** 0.50))
+    c, al, be, ga, r2 = bench.fit_power_law(rows)
+    assert abs(c - 0.0013) < 1e-9 and abs(al - 0.59) < 1e-9
+    assert abs(be + 0.54) < 1e-9 and abs(ga - 0.50) < 1e-9 and abs(r2 - 1.0) < 1e-12
