@@ -66,6 +66,9 @@ namespace {
 #ifndef SPMM_TC_RCAP
 #define SPMM_TC_RCAP 16     // tile rows per group (accumulator columns / 16)
 #endif
+#ifndef SPMM_TC_ACCBUFS
+#define SPMM_TC_ACCBUFS 1   // accumulator sets per CTA (2 needs one CTA per SM)
+#endif
 // Stage geometries (stages, X slabs and W tiles per stage, all in about
 // 110 KB of shared memory per CTA), for 16-bit and for E4M3 weights.  The plan picks one
 // by its tiles per entry: few-tile entries (sparse tiles) need many slabs
@@ -112,7 +115,7 @@ namespace {
 constexpr int kSlabBytes = kTile * kNTile * 2;                    // 4096: 16 k x 128 n, 16-bit
 constexpr int kTileBytes8 = kTile * kTile;                        // 256: E4M3 tile, row-major
 constexpr int kScaleBytes = 16 * 4;                               // per slot: 4 x 4 sub-square scales
-constexpr int kStagesMax = 3;                                     // >= every geometry's stages
+constexpr int kStagesMax = 4;                                     // >= every geometry's stages
 constexpr int kRowCap = SPMM_TC_RCAP;
 constexpr int kAccCols = kRowCap * kTile;                         // TMEM columns per buffer
 constexpr int kMaxBatch = 64;                                     // problems per launch
@@ -139,7 +142,8 @@ template <bool W8, int GEO> struct StageGeom {
 // pipelines run side by side and one CTA's epilogue overlaps the other's MMAs.
 // (A single warp cannot issue its copies and MMAs faster than its own
 // dependent scalar work allows; a second pipeline per SM doubles that rate.)
-constexpr int kAccBufs = 1;
+constexpr int kAccBufs = SPMM_TC_ACCBUFS;
+static_assert(kAccBufs * SPMM_TC_CTAS * SPMM_TC_RCAP * 16 <= 512, "TMEM columns per SM");
 constexpr int kCtasPerSm = SPMM_TC_CTAS;
 static_assert(kRowCap <= kMaxGroupRows && kRowCap <= 16, "a stage must hold a full entry");
 constexpr int kThreads = 288;
@@ -215,8 +219,16 @@ struct TcProb {
     int32_t ntn, x3d;            // n tiles of 128; X map is 3-D (64, k, n/64)
 };
 
+// A stage whose entries are 2 to 4 consecutive tile columns (record info
+// bit 20) gets its X slabs in one TMA box of 4 slabs when X's map is 3-D;
+// the slabs then lie 2048 B apart inside each 64-column half, the halves
+// 8192 B apart.
+constexpr int kJointSlabs = 4;
+constexpr uint32_t kJointBit = 1u << 20;
+
 struct TcBatch {
     CUtensorMap maps[kMaxBatch]; // X of each problem
+    CUtensorMap maps4[kMaxBatch];// the same X, boxes of kJointSlabs slabs
     TcProb prob[kMaxBatch];
     const int32_t *units;        // optional schedule: (problem, unit) pairs, costliest first
     int64_t total_units;
@@ -224,6 +236,8 @@ struct TcBatch {
     const int32_t *n_items_dev;  // dynamic single problem: item count on the device
     int32_t *status;
 };
+
+static_assert(sizeof(TcBatch) <= 32764, "kernel parameter space");
 
 __device__ __forceinline__ void record(int32_t *status, int32_t code) {
     atomicCAS(status, 0, code);
@@ -233,6 +247,10 @@ __device__ __forceinline__ void record(int32_t *status, int32_t code) {
 // halves of the slab are 2048 B apart (leading offset), the two 8-row k
 // groups 1024 B apart (stride offset).
 __device__ __forceinline__ uint64_t a_desc(uint32_t addr) { return smem_desc(addr, 2048, 1024, 2); }
+// The same for a stage loaded as one box of kJointSlabs slabs.
+__device__ __forceinline__ uint64_t a_desc_joint(uint32_t addr) {
+    return smem_desc(addr, kJointSlabs * 2048, 1024, 2);
+}
 // B-operand descriptor: one W tile, K-major, no swizzle; 8 x 8 core matrices,
 // k-adjacent ones 128 B apart (leading), row-adjacent ones 256 B (stride).
 __device__ __forceinline__ uint64_t b_desc(uint32_t addr) { return smem_desc(addr, 128, 256, 0); }
@@ -387,6 +405,17 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                     } else if (lane == 0) {
                         mbar_arrive(&sm->full[stage]);
                     }
+                } else if ((info & kJointBit) && P.x3d) {
+                    // consecutive columns: X producer 1 requests all slabs in one box
+                    if (lane == 0) {
+                        if (pid == 1) {
+                            mbar_arrive_tx(&sm->full[stage], kJointSlabs * kSlabBytes);
+                            tma_load_3d(st, &B.maps4[un.p], 0, (int)col * kTile, n0 / (kNTile / 2),
+                                        &sm->full[stage]);
+                        } else {
+                            mbar_arrive(&sm->full[stage]);
+                        }
+                    }
                 } else {
                     if (lane == 0) mbar_arrive_tx(&sm->full[stage], mine * kSlabBytes);
                     __syncwarp();
@@ -480,14 +509,16 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                 last = (info >> 31) != 0;
                 const uint32_t myword = sm->meta[stage].prog[half][lane];   // words >= nmma unused
                 const uint32_t sbase = smem_u32(stages + stage * G::bytes);
-                const uint64_t adesc0 = a_desc(sbase);
+                const bool joint = (info & kJointBit) && B.prob[un.p].x3d;
+                const uint64_t adesc0 = joint ? a_desc_joint(sbase) : a_desc(sbase);
+                const uint32_t astep = joint ? (kSlabBytes / 2) >> 4 : kSlabBytes >> 4;
                 const uint64_t bdesc0 = b_desc(sbase + G::w16);
                 for (int i = 0; i < nmma; ++i) {
                     const uint32_t wd = __shfl_sync(0xffffffffu, myword, i);
                     const uint32_t slab = wd & 15u, toff = (wd >> 4) & 255u;
                     const uint32_t r0 = (wd >> 12) & 15u, len = (wd >> 16) & 31u;
                     // descriptor start addresses are in 16-byte units (bits 0-13)
-                    tc_mma_elect(dbase + r0 * kTile, adesc0 + slab * (kSlabBytes >> 4),
+                    tc_mma_elect(dbase + r0 * kTile, adesc0 + slab * astep,
                                  bdesc0 + toff * (kTileBytes16 >> 4),
                                  idesc0 | ((len * kTile) >> 3) << 17, 1u);
                 }
@@ -755,6 +786,11 @@ __device__ int build_batch(int32_t eb, int32_t e1, int ent_cap, int tiles_cap,
             const int32_t xc = __shfl_sync(0xffffffffu, mcol, min(j + max(lane - 3, 0), 31));
             const bool last = last_batch && j + nent == cnt;
             const int32_t r = rec + nst;
+            // 2 to 4 entries on consecutive tile columns: one X box serves the stage
+            const int32_t pcol = __shfl_up_sync(0xffffffffu, mcol, 1);
+            const bool consec = __all_sync(0xffffffffu, !(lane > j && lane < j + nent) ||
+                                                            mcol == pcol + 1);
+            const bool joint = consec && nent >= 2 && nent <= kJointSlabs;
             if (lane >= j && lane < j + nent) {
                 uint32_t klo = (uint32_t)(L - nlo - Lb), khi = (uint32_t)(H - nhi - Hb);
                 uint32_t toff = (uint32_t)(S - mslots - Sb);
@@ -782,7 +818,7 @@ __device__ int build_batch(int32_t eb, int32_t e1, int ent_cap, int tiles_cap,
                 uint32_t v = 0;
                 if (lane == 0)
                     v = (uint32_t)mlo | (uint32_t)mhi << 6 | (uint32_t)nent << 12 |
-                        (last ? 0x80000000u : 0u);
+                        (joint ? kJointBit : 0u) | (last ? 0x80000000u : 0u);
                 else if (lane == 1) v = (uint32_t)slots;
                 else if (lane == 2) v = (uint32_t)stb;
                 else if (lane - 3 < nent) v = (uint32_t)xc;
@@ -998,6 +1034,8 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
     TcBatch B;  // the launch parameter (copied at launch)
     int x3d = 0;
     cudaError_t e = encode_x(&B.maps[0], &x3d, p->xdt == SPMM_BF16, X, p->k, n, ldx);
+    if (e == cudaSuccess)
+        e = encode_x(&B.maps4[0], &x3d, p->xdt == SPMM_BF16, X, p->k, n, ldx, kJointSlabs);
     if (e != cudaSuccess) return e;
     fill_prob(B.prob[0], p, Y, n, ldy, x3d);
     B.prob[0].unit_base = 0;
@@ -1066,6 +1104,9 @@ cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *cons
         int x3d = 0;
         const int64_t lx = ldx ? ldx[i] : n[i], ly = ldy ? ldy[i] : n[i];
         cudaError_t e = encode_x(&B.maps[i], &x3d, p->xdt == SPMM_BF16, X[i], p->k, n[i], lx);
+        if (e == cudaSuccess)
+            e = encode_x(&B.maps4[i], &x3d, p->xdt == SPMM_BF16, X[i], p->k, n[i], lx,
+                         kJointSlabs);
         if (e != cudaSuccess) return e;
         fill_prob(B.prob[i], p, Y[i], n[i], ly, x3d);
         B.prob[i].unit_base = base;

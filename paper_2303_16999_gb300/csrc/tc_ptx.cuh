@@ -177,8 +177,9 @@ constexpr int kSlabRows = 16, kSlabHalf = 64;
 // k rows, n/64 column blocks) so one 64 x 16 x 2 box is a whole 16 x 128 slab
 // (two 128-byte-swizzled halves, 2048 B apart); otherwise two 2-D 64 x 16
 // boxes per slab, whose out-of-range columns the TMA unit fills with zeros.
+// With slabs > 1 a box spans that many consecutive slabs (16 * slabs rows).
 inline cudaError_t encode_x(CUtensorMap *map, int *x3d, bool bf16, const void *X, int64_t k,
-                            int64_t n, int64_t ldx) {
+                            int64_t n, int64_t ldx, int slabs = 1) {
     auto enc = encode_fn();
     if (!enc) return cudaErrorNotSupported;
     if (((uintptr_t)X & 15) || (ldx * 2) % 16) return cudaErrorMisalignedAddress;
@@ -189,7 +190,7 @@ inline cudaError_t encode_x(CUtensorMap *map, int *x3d, bool bf16, const void *X
         const cuuint64_t dims[3] = {(cuuint64_t)kSlabHalf, (cuuint64_t)k,
                                     (cuuint64_t)(n / kSlabHalf)};
         const cuuint64_t strides[2] = {(cuuint64_t)(ldx * 2), (cuuint64_t)(kSlabHalf * 2)};
-        const cuuint32_t box[3] = {kSlabHalf, kSlabRows, 2};
+        const cuuint32_t box[3] = {kSlabHalf, (cuuint32_t)(kSlabRows * slabs), 2};
         const cuuint32_t estr[3] = {1, 1, 1};
         r = enc(map, dt, 3, const_cast<void *>(X), dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -197,7 +198,7 @@ inline cudaError_t encode_x(CUtensorMap *map, int *x3d, bool bf16, const void *X
     } else {
         const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)k};
         const cuuint64_t strides[1] = {(cuuint64_t)(ldx * 2)};
-        const cuuint32_t box[2] = {kSlabHalf, kSlabRows};
+        const cuuint32_t box[2] = {kSlabHalf, (cuuint32_t)(kSlabRows * slabs)};
         const cuuint32_t estr[2] = {1, 1};
         r = enc(map, dt, 2, const_cast<void *>(X), dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
