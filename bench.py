@@ -808,7 +808,8 @@ def run_sddmm(torch, S, wl, dev, peaks, reps=10,
     n = 2048, BF16 inputs, FP32 dW; each timed run follows an L2 eviction
     (256 MB written and read back) and the events bracket the call alone.
     Useful FLOPs 2 nnzb b^2 n; the dense-tile kernel computes every 128 x 256
-    tile, so its roofline is the tensor peak on 2 m k n."""
+    tile, so its roofline is the tensor peak on 2 m k n (reported for both
+    forms as the dense-equivalent rate)."""
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = []
     for b, d in cases:
@@ -833,10 +834,21 @@ def run_sddmm(torch, S, wl, dev, peaks, reps=10,
             raise RuntimeError("plan status %d" % plan.status())
         us = statistics.median(ts)
         dense = 2.0 * M * K * N / us / 1e6
-        out.append({"b": b, "d": "1/%d" % round(1 / d), "kernel": "sddmm_dense", "us": round(us, 2),
-                    "tflops_nz": round(2.0 * len(c["brow"]) * b * b * N / us / 1e6, 2),
-                    "tflops_dense_equiv": round(dense, 1),
-                    "frac_of_tensor_peak": round(dense / peaks["bf16_tflops"], 3)})
+        gathered = plan.info()["sddmm_form"] == 1
+        row = {"b": b, "d": "1/%d" % round(1 / d),
+               "kernel": "sddmm_gather" if gathered else "sddmm_dense", "us": round(us, 2),
+               "tflops_nz": round(2.0 * len(c["brow"]) * b * b * N / us / 1e6, 2)}
+        if gathered:
+            # rows moved from L2: each block's 16 X rows plus one block row of
+            # dY per item of up to 8 blocks (items counted as in the kernel)
+            counts = np.bincount(c["brow"], minlength=M // 16)
+            items = int(np.sum((counts + 7) // 8))
+            moved = (len(c["brow"]) + items) * 16 * N * 2
+            row["l2_to_sm_tbs"] = round(moved / us / 1e6, 2)
+        else:
+            row["tflops_dense_equiv"] = round(dense, 1)
+            row["frac_of_tensor_peak"] = round(dense / peaks["bf16_tflops"], 3)
+        out.append(row)
         plan.close()
         del dY, X, dW
     del flush

@@ -182,7 +182,7 @@ typedef struct {
     int64_t n_items, n_groups, n_entries, n_tiles, ws_rows, n_reductions;
     int64_t device_bytes;         /* device memory the plan holds */
     int32_t stage_geometry;       /* TC: 0 dense-tile stages, 1 sparse-tile stages (other kernels: 0) */
-    int32_t reserved;
+    int32_t sddmm_form;           /* spmm_sddmm on this plan: 0 dense tiles, 1 gathered blocks */
 } spmm_plan_info;
 
 spmm_status spmm_plan_get_info(const spmm_plan *plan, spmm_plan_info *info);

@@ -468,6 +468,12 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
         cudaError_t e = cudaSuccess;
         if (st == SPMM_OK) e = dalloc(p, &p->d_status, 1);
         if (st == SPMM_OK && e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int32_t));
+        if (st == SPMM_OK && e == cudaSuccess && b == 16) {
+            // the gathered SDDMM's work items: at most nnzb / 8 + one per block row
+            const int64_t nb = p->mode == SPMM_STATIC ? p->nnzb : p->nnzb_max;
+            p->sd_items_cap = nb / 8 + m / 16 + 1;
+            e = dalloc(p, &p->d_sd_items, 1 + 3 * p->sd_items_cap);
+        }
         if (st == SPMM_OK && e == cudaSuccess && p->hp.ws_rows > 0)
             e = dalloc(p, &p->d_ws, p->hp.ws_rows * std::max<int64_t>(n_max, 1));
         if (st == SPMM_OK && e == cudaSuccess) {
@@ -763,7 +769,7 @@ spmm_status spmm_plan_get_info(const spmm_plan *cp, spmm_plan_info *info) {
     i.n_reductions = dynran ? p->dyn_red : p->n_red;
     i.device_bytes = p->device_bytes;
     i.stage_geometry = p->kernel == SPMM_KERNEL_TC ? p->tc_geo : 0;
-    i.reserved = 0;
+    i.sddmm_form = sddmm_gathers(p) ? 1 : 0;
     *info = i;
     return SPMM_OK;
 }

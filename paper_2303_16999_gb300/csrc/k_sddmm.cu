@@ -19,11 +19,19 @@
 // so the epilogue of one tile overlaps the MMAs of the next), each CTA taking
 // a contiguous run of tiles in row-major order.
 //
-// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
-// TMEM owner, warps 2..5 = epilogue (warp w reads TMEM lanes 32 (w % 4) on).
-// Every mbarrier wait is bounded; on expiry the CTA records SPMM_ERR_TIMEOUT
-// in the plan's status word, lets its copies and MMAs in flight finish,
-// frees TMEM and exits.
+// Gathered form (b = 16, low density): a work item is up to eight blocks of
+// one block row r.  Their X rows (8 x 16 = 128 rows) are gathered by TMA as
+// the MMA's A operand and the 16 rows of dY at r as its B operand, so
+// D[128 x 16] = X rows . dY rows^T holds the eight blocks, transposed, in
+// TMEM (M = 128, N = 16).  Only the stored blocks' rows move: about
+// nnzb * 1.125 * 16 * n * 2 bytes from L2, against the dense form's whole
+// tiles, which wins below a density of about 1/7.
+//
+// Warp roles (192 threads) in both kernels: warp 0 = TMA producer, warp 1 =
+// MMA issuer and TMEM owner, warps 2..5 = epilogue (warp w reads TMEM lanes
+// 32 (w % 4) on).  Every mbarrier wait is bounded; on expiry the CTA records
+// SPMM_ERR_TIMEOUT in the plan's status word, lets its copies and MMAs in
+// flight finish, frees TMEM and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -56,6 +64,7 @@ struct __align__(8) SdSmem {
     uint32_t tmem_base;
     volatile int32_t abort_flag;
     int32_t issued, consumed;      // stages issued by the producer / consumed by the MMA warp
+    int32_t issued2[4];            // gathered form: next stage index of each of its producers
 };
 
 struct SdArgs {
@@ -393,6 +402,269 @@ __global__ void __launch_bounds__(kSdThreads, 1)
     }
 }
 
+// ------------------------------------------------------ gathered form ----
+constexpr int kSgBlocks = 8;                      // blocks per work item (A = 128 rows)
+constexpr int kSgStages = 4;
+constexpr int kSgCtasPerSm = 3;
+#ifndef SPMM_SG_PRODUCERS
+#define SPMM_SG_PRODUCERS 2
+#endif
+constexpr int kSgProducers = SPMM_SG_PRODUCERS;   // warp 0 and warps 6, 7, ...
+static_assert(kSgProducers >= 1 && kSgProducers <= 4, "producer warps");
+constexpr int kSgThreads = kSdThreads + 32 * (kSgProducers - 1);
+constexpr uint32_t kSgBox = 16 * kSdBK * 2;       // 2048: 16 rows x 64 elements
+constexpr uint32_t kSgStageBytes = (kSgBlocks + 1) * kSgBox;
+static_assert(kSgStages <= kSdStages, "the barrier arrays of SdSmem hold kSdStages stages");
+
+// Work items of the gathered form from the block CSR: row r gives
+// ceil(count / 8) items (r, first entry, end entry); items[0] = the count.
+// One CTA; rows in chunks of 1024, an exclusive scan of the item counts.
+__global__ void __launch_bounds__(1024)
+    sddmm_items_kernel(const int32_t *row_ptr, int32_t mb, const int32_t *skip_if,
+                       int32_t *items) {
+    pdl_enter();
+    __shared__ int32_t warp_sum[32];
+    __shared__ int32_t base_s;
+    if (threadIdx.x == 0) base_s = 0;
+    __syncthreads();
+    const bool skip = skip_if && *skip_if != 0;    // a rejected pattern: no items
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int32_t r0 = 0; r0 < mb && !skip; r0 += 1024) {
+        const int32_t r = r0 + threadIdx.x;
+        const int32_t beg = r < mb ? row_ptr[r] : 0, end = r < mb ? row_ptr[r + 1] : 0;
+        const int32_t ni = (end - beg + kSgBlocks - 1) / kSgBlocks;
+        int32_t incl = ni;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) warp_sum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int32_t ws = warp_sum[lane], wi = ws;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t v = __shfl_up_sync(0xffffffffu, wi, o);
+                if (lane >= o) wi += v;
+            }
+            warp_sum[lane] = wi - ws;              // exclusive prefix of the warp sums
+        }
+        __syncthreads();
+        const int32_t first = base_s + warp_sum[wid] + incl - ni;
+        for (int32_t j = 0; j < ni; ++j) {
+            int32_t *it = items + 1 + 3 * (int64_t)(first + j);
+            it[0] = r;
+            it[1] = beg + j * kSgBlocks;
+            it[2] = min(beg + (j + 1) * kSgBlocks, end);
+        }
+        __syncthreads();
+        if (threadIdx.x == 1023) base_s = first + ni;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) items[0] = skip ? 0 : base_s;
+}
+
+// K-major, 128-byte swizzle, N = 16: D[128 x 16] fp32.
+__device__ __forceinline__ uint32_t sg_idesc(uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+struct SgArgs {
+    const int32_t *items, *col_idx, *perm;
+    void *dW;
+    int32_t *status;
+    int32_t ksteps, fmt;
+};
+
+template <int OUT>
+__global__ void __launch_bounds__(kSgThreads, kSgCtasPerSm)
+    sddmm_gather_kernel(const __grid_constant__ CUtensorMap map_dy,
+                        const __grid_constant__ CUtensorMap map_x, const SgArgs args) {
+    pdl_enter();
+    const int32_t nitems = *args.items;            // 0 for a rejected dynamic pattern
+    if ((int32_t)blockIdx.x >= nitems) return;
+    extern __shared__ __align__(1024) uint8_t sm_raw[];
+    uint8_t *stages = (uint8_t *)(((uintptr_t)sm_raw + 1023) & ~(uintptr_t)1023);
+    SdSmem *sm = reinterpret_cast<SdSmem *>(stages + kSgStages * kSgStageBytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSgStages; ++s) {
+            mbar_init(&sm->full[s], 1);
+            mbar_init(&sm->empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&sm->accf[a], 1);
+            mbar_init(&sm->acce[a], 128);
+        }
+        mbar_init(&sm->drain, 1);
+        sm->abort_flag = 0;
+        sm->issued = sm->consumed = 0;
+        for (int i = 0; i < 4; ++i) sm->issued2[i] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                smem_u32(&sm->tmem_base)),
+            "r"(32));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm->tmem_base;
+    const int ksteps = args.ksteps;
+    const int32_t *items = args.items + 1;
+
+    if (warp == 0 || warp >= 6) {
+        // ---- producers: producer j fills stages it with it % kSgProducers
+        // == j (each issue costs its warp time, so warps issue side by side);
+        // lane i < 8 copies block i's X rows, lane 8 the dY rows
+        const int pid = warp == 0 ? 0 : warp - 5;
+        int32_t it = 0, mine = 0;
+        bool ok = true;
+        int32_t nx = (int32_t)blockIdx.x;
+        int32_t ncol = 0;
+        {
+            const int32_t e0 = items[3 * nx + 1], e1 = items[3 * nx + 2];
+            ncol = lane < e1 - e0 ? __ldg(args.col_idx + e0 + lane) : 0;
+        }
+        for (int32_t w = (int32_t)blockIdx.x; w < nitems && ok; w += gridDim.x) {
+            const int32_t r = items[3 * w], nb = items[3 * w + 2] - items[3 * w + 1];
+            const int32_t col = ncol;
+            const int32_t wn = w + (int32_t)gridDim.x;
+            if (wn < nitems) {   // the next item's columns, loaded while this one is issued
+                const int32_t e0 = items[3 * wn + 1], e1 = items[3 * wn + 2];
+                ncol = lane < e1 - e0 ? __ldg(args.col_idx + e0 + lane) : 0;
+            }
+            for (int ks = 0; ks < ksteps; ++ks, ++it) {
+                if (it % kSgProducers != pid) continue;
+                const int s = it % kSgStages;
+                const uint32_t ph = (uint32_t)((it / kSgStages) & 1);
+                if (!sd_wait_warp(&sm->empty[s], ph ^ 1u, sm, lane)) {
+                    if (lane == 0) sd_abort(sm, args.status);
+                    ok = false;
+                    break;
+                }
+                mine = it + 1;
+                uint8_t *base = stages + s * kSgStageBytes;
+                if (lane == 0) mbar_arrive_tx(&sm->full[s], (uint32_t)(nb + 1) * kSgBox);
+                __syncwarp();
+                if (lane < nb)
+                    tma_load_2d(base + lane * kSgBox, &map_x, ks * kSdBK, col * 16, &sm->full[s]);
+                else if (lane == kSgBlocks)
+                    tma_load_2d(base + kSgBlocks * kSgBox, &map_dy, ks * kSdBK, r * 16,
+                                &sm->full[s]);
+                __syncwarp();
+            }
+        }
+        if (lane == 0) sm->issued2[pid] = mine;
+    } else if (warp == 1) {
+        // ---- MMA issuer
+        const uint32_t idesc = sg_idesc((uint32_t)args.fmt);
+        int32_t it = 0;
+        bool ok = true;
+        int32_t lt = 0;
+        for (int32_t w = (int32_t)blockIdx.x; w < nitems && ok; w += gridDim.x, ++lt) {
+            const uint32_t a = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
+            if (!sd_wait_warp(&sm->acce[a], aph ^ 1u, sm, lane)) {
+                if (lane == 0) sd_abort(sm, args.status);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t d = tmem + a * 16;
+            for (int ks = 0; ks < ksteps; ++ks, ++it) {
+                const int s = it % kSgStages;
+                const uint32_t ph = (uint32_t)((it / kSgStages) & 1);
+                if (!sd_wait_warp(&sm->full[s], ph, sm, lane)) {
+                    if (lane == 0) sd_abort(sm, args.status);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t abase = smem_u32(stages + s * kSgStageBytes);
+                const uint32_t bbase = abase + kSgBlocks * kSgBox;
+#pragma unroll
+                for (int kk = 0; kk < kSdBK / 16; ++kk)
+                    tc_mma_elect(d, sd_desc(abase + kk * 32), sd_desc(bbase + kk * 32), idesc,
+                                 (ks | kk) ? 1u : 0u);
+                __syncwarp();
+                if (lane == 0) tc_commit(&sm->empty[s]);
+            }
+            if (!ok) break;
+            __syncwarp();
+            if (lane == 0) {
+                if (ksteps > 0) tc_commit(&sm->accf[a]);
+                else mbar_arrive(&sm->accf[a]);   // n = 0: nothing accumulated
+            }
+        }
+        if (lane == 0) sm->consumed = it;
+    } else {
+        // ---- epilogue: TMEM lane t = 16 e + l holds row l of block e, transposed
+        const int q = warp & 3;
+        const int t = q * 32 + lane, e = t >> 4, l = t & 15;
+        const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        using O = SdOut<OUT>;
+        typename O::T *dW = reinterpret_cast<typename O::T *>(args.dW);
+        int32_t lt = 0;
+        for (int32_t w = (int32_t)blockIdx.x; w < nitems; w += gridDim.x, ++lt) {
+            const int32_t e0 = items[3 * w + 1], nb = items[3 * w + 2] - e0;
+            const int32_t p = e < nb ? __ldg(args.perm + e0 + e) : 0;
+            const uint32_t a = (uint32_t)(lt & 1), aph = (uint32_t)((lt >> 1) & 1);
+            if (!sd_wait_warp(&sm->accf[a], aph, sm, lane)) {
+                if (lane == 0) sd_abort(sm, args.status);
+                break;
+            }
+            tc_fence_after();
+            float v[16];
+            tmem_ld16(tmem + lane_addr + a * 16, v);
+            if (e < nb) {
+                typename O::T *dst = dW + (int64_t)p * 256 + l;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float x = ksteps > 0 ? v[i] : 0.f;
+                    O::put(dst + i * 16, &x, 1);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&sm->acce[a]);
+        }
+    }
+
+    __syncthreads();
+    if (sm->abort_flag) {
+        if (threadIdx.x == 0) {
+            // stages each producer issued and the MMA warp did not consume
+            int32_t hi = 0;
+            for (int i = 0; i < kSgProducers; ++i) hi = max(hi, sm->issued2[i]);
+            for (int32_t c = sm->consumed; c < hi; ++c) {
+                if (c >= sm->issued2[c % kSgProducers]) continue;
+                const int s = c % kSgStages;
+                const uint32_t par = (uint32_t)((c / kSgStages) & 1);
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try(&sm->full[s], par) && gtimer() - t0 < kSdWaitNs) {
+                }
+            }
+        }
+        if (warp == 1) {
+            if (lane == 0) {
+                tc_commit(&sm->drain);
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try(&sm->drain, 0) && gtimer() - t0 < kSdWaitNs) {
+                }
+            }
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
+    }
+}
+
 cudaError_t encode_rows(CUtensorMap *map, bool bf16, const void *base, int64_t rows, int64_t n,
                         int64_t ld, uint32_t box_rows) {
     auto enc = encode_fn();
@@ -424,6 +696,24 @@ cudaError_t launch_dense(const CUtensorMap &mdy, const CUtensorMap &mx, const Sd
     return cudaGetLastError();
 }
 
+template <int OUT>
+cudaError_t launch_gather(const CUtensorMap &mdy, const CUtensorMap &mx, const SgArgs &a, int grid,
+                          cudaStream_t s) {
+    const size_t smem = 1024 + (size_t)kSgStages * kSgStageBytes + sizeof(SdSmem);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sddmm_gather_kernel<OUT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(sddmm_gather_kernel<OUT>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    pdl_launch(sddmm_gather_kernel<OUT>, dim3(grid), dim3(kSgThreads), smem, s, mdy, mx, a);
+    return cudaGetLastError();
+}
+
 template <int B>
 cudaError_t launch_dense_b(int out, const CUtensorMap &mdy, const CUtensorMap &mx, const SdArgs &a,
                            int grid, cudaStream_t s) {
@@ -435,6 +725,17 @@ cudaError_t launch_dense_b(int out, const CUtensorMap &mdy, const CUtensorMap &m
 }
 
 }  // namespace
+
+// The gathered form moves about 1.125 x 16 rows x 2 n bytes per stored
+// block, issued as nine 2 KB boxes per step (measured ~7.6 TB/s from L2 at
+// m = k = 4096, n = 2048, d = 1/16: 41 us against 49 us of dense tiles at
+// ~1.4 PFLOP/s); the times cross near d = 1/13, so blocks of 16 below that
+// density (nnzb_max for dynamic plans) take the gathered form.
+bool sddmm_gathers(const spmm_plan *p) {
+    if (p->b != 16 || !p->d_sd_items) return false;
+    const double nb = (double)(p->mode == SPMM_STATIC ? p->nnzb : p->nnzb_max);
+    return nb * 256.0 * 13.0 < (double)p->m * (double)p->k;
+}
 
 cudaError_t launch_sddmm(const spmm_plan *p, const void *d_dY, int64_t lddy, const void *d_X,
                          int64_t ldx, int64_t n, void *d_dW, spmm_dtype dw_dtype, cudaStream_t s) {
@@ -463,6 +764,37 @@ cudaError_t launch_sddmm(const spmm_plan *p, const void *d_dY, int64_t lddy, con
     a.ntiles = ntm * a.ntn;
     const int grid = (int)(a.ntiles < p->sm_count ? a.ntiles : p->sm_count);
     const int out = dw_dtype == SPMM_F32 ? 0 : (dw_dtype == SPMM_F16 ? 1 : 2);
+    if (sddmm_gathers(p)) {
+        // dY rows of one block row: a 16-row box (the dense form's map has 128)
+        if (n > 0) e = encode_rows(&mdy, bf16, d_dY, p->m, n, lddy, 16);
+        if (n > 0 && e == cudaSuccess) e = encode_rows(&mx, bf16, d_X, p->k, n, ldx, 16);
+        if (n == 0) {
+            e = encode_rows(&mdy, bf16, d_dW, 1, 8, 8, 16);
+            if (e == cudaSuccess) e = encode_rows(&mx, bf16, d_dW, 1, 8, 8, 16);
+        }
+        if (e != cudaSuccess) return e;
+        const int32_t mb = (int32_t)(p->m / 16);
+        pdl_launch(sddmm_items_kernel, dim3(1), dim3(1024), 0, s, p->d_row_ptr, mb, a.skip_if,
+                   p->d_sd_items);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        SgArgs g{};
+        g.items = p->d_sd_items;
+        g.col_idx = p->d_col_idx;
+        g.perm = p->d_perm;
+        g.dW = d_dW;
+        g.status = p->d_status;
+        g.ksteps = a.ksteps;
+        g.fmt = a.fmt;
+        // the item count is known on the device only: one CTA per item up to three per SM
+        const int64_t cap = p->sd_items_cap, slots = (int64_t)p->sm_count * kSgCtasPerSm;
+        const int ggrid = (int)(cap < slots ? cap : slots);
+        switch (out) {
+            case 0: return launch_gather<0>(mdy, mx, g, ggrid, s);
+            case 1: return launch_gather<1>(mdy, mx, g, ggrid, s);
+            default: return launch_gather<2>(mdy, mx, g, ggrid, s);
+        }
+    }
     switch (p->b) {
         case 1: return launch_dense_b<1>(out, mdy, mx, a, grid, s);
         case 4: return launch_dense_b<4>(out, mdy, mx, a, grid, s);

@@ -97,6 +97,8 @@ struct spmm_plan {
     uint32_t *d_srec = nullptr, *d_sprog = nullptr;  // TC: stage records and MMA programs
     int tc_geo = 0;                // TC stage geometry: 0 dense tiles, 1 sparse tiles
     bool transposed = false;       // applies W^T: values arrive as W's blocks, packed transposed
+    int32_t *d_sd_items = nullptr; // b = 16: SDDMM work items (count, then (row, e0, e1) triples)
+    int64_t sd_items_cap = 0;
     int64_t *d_ws_row0 = nullptr;
     int64_t n_items = 0, n_groups = 0, n_entries = 0, n_tiles = 0, n_red = 0;
     void *d_packed = nullptr;      // packed values (kernel layout)
@@ -156,7 +158,9 @@ cudaError_t launch_dynamic_csr(spmm_plan *p, const spmm_dpattern *dp, cudaStream
 cudaError_t launch_ell(spmm_plan *p, const int32_t *d_cols, int32_t E, const void *d_values,
                        const void *d_X, int64_t n, int64_t ldx, void *d_Y, int64_t ldy,
                        cudaStream_t s);
-// sampled dense-dense product on the plan's block CSR (k_sddmm.cu)
+// sampled dense-dense product on the plan's block CSR (k_sddmm.cu); true when
+// spmm_sddmm takes the gathered form on this plan
+bool sddmm_gathers(const spmm_plan *p);
 cudaError_t launch_sddmm(const spmm_plan *p, const void *d_dY, int64_t lddy, const void *d_X,
                          int64_t ldx, int64_t n, void *d_dW, spmm_dtype dw_dtype, cudaStream_t s);
 

@@ -70,7 +70,7 @@ class PlanInfo(ctypes.Structure):
                                       "rows_per_group", "max_per_item")] + \
         [(n, ctypes.c_int64) for n in ("n_items", "n_groups", "n_entries", "n_tiles",
                                       "ws_rows", "n_reductions", "device_bytes")] + \
-        [(n, ctypes.c_int32) for n in ("stage_geometry", "reserved")]
+        [(n, ctypes.c_int32) for n in ("stage_geometry", "sddmm_form")]
 
 
 class ServeConfig(ctypes.Structure):

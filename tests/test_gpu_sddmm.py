@@ -2,6 +2,9 @@
 gradient of Section 3's product with respect to the stored blocks) against
 the FP64 oracle's ``sddmm``.
 
+Blocks of 16 below a density of 1/13 take the gathered kernel, every other
+case the dense-tile kernel; the cases below cover both.
+
 Bars: FP32 output within 1e-5 of the oracle relative to ||dW_o||_F (16-bit
 inputs are exact in FP32 products; only the FP32 accumulation order
 differs), 16-bit output within 4e-3 normwise (||dW - dW_o||_F /
@@ -51,6 +54,7 @@ def run_case(m, k, n, b, d, dt, out_dt, seed):
     dY = torch.from_numpy(c["dY"]).to(dt)
     X = torch.from_numpy(c["X"]).to(dt)
     plan = S.Plan(m, k, max(n, 1), b, w_dtype=S.dtype_code(dt), brow=c["brow"], bcol=c["bcol"])
+    assert plan.info()["sddmm_form"] == (1 if b == 16 and d * 13 < 1 else 0)
     dW = torch.full((len(c["brow"]), b, b), float("nan"), dtype=out_dt, device="cuda")
     plan.sddmm(_dev_rows(dY, dt), _dev_rows(X, dt), dW)
     torch.cuda.synchronize()
@@ -67,6 +71,8 @@ CASES = [
     (520, 700, 33, 1, 1 / 16),
     (2048, 4096, 64, 16, 1 / 16),    # 256 tiles: CTAs span several rows of tiles
     (256, 256, 1000, 8, 1 / 4),      # 16 steps along n
+    (512, 512, 130, 16, 1 / 4),      # b = 16 above density 1/13: dense tiles
+    (1024, 768, 200, 16, 1 / 16),    # b = 16 below it: gathered blocks, rows of 1 to 8+ blocks
 ]
 
 
@@ -80,17 +86,20 @@ def test_sddmm_parity(case, dt, out):
     _check(dW, dWo, dY, X, out_dt)
 
 
+@pytest.mark.parametrize("d", [1 / 16, 1 / 4])
 @pytest.mark.parametrize("n", [1, 7, 8])
-def test_sddmm_small_n(n):
-    dW, dWo, dY, X = run_case(256, 384, n, 16, 1 / 8, torch.bfloat16, torch.float32, seed=3 + n)
+def test_sddmm_small_n(n, d):
+    dW, dWo, dY, X = run_case(256, 384, n, 16, d, torch.bfloat16, torch.float32, seed=3 + n)
     _check(dW, dWo, dY, X, torch.float32)
 
 
-def test_sddmm_n_zero_writes_zero_blocks():
-    c = wl.sddmm_problem(5, 256, 256, 8, 16, 32)
-    plan = S.Plan(256, 256, 8, 16, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"])
+@pytest.mark.parametrize("b,nnzb,form", [(16, 16, 1), (16, 64, 0), (4, 64, 0)])
+def test_sddmm_n_zero_writes_zero_blocks(b, nnzb, form):
+    c = wl.sddmm_problem(5, 256, 256, 8, b, nnzb)
+    plan = S.Plan(256, 256, 8, b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"])
+    assert plan.info()["sddmm_form"] == form
     dY = torch.zeros((256, 8), dtype=torch.float16, device="cuda")[:, :0]
-    dW = torch.full((32, 16, 16), 7.0, dtype=torch.float32, device="cuda")
+    dW = torch.full((nnzb, b, b), 7.0, dtype=torch.float32, device="cuda")
     plan.sddmm(dY, dY, dW)
     torch.cuda.synchronize()
     assert plan.status() == 0 and not torch.any(dW)
