@@ -20,8 +20,10 @@
 // Units go to CTAs in contiguous runs (persistent, three CTAs per SM); the
 // epilogue of one unit overlaps the MMAs of the next (two accumulators).
 //
-// Warp roles (192 threads): warp 0 = TMA producer, warp 1 = MMA issuer and
-// TMEM owner, warps 2..5 = epilogue (TMEM -> Y, 16-bit).  Every mbarrier
+// Warp roles (224 threads): warps 0 and 6 = TMA producers (alternate
+// stages; one warp alone issued too slowly: 52.9 against 48.6 us per call
+// at m = k = 8192, n = 1024, d = 1/16), warp 1 = MMA issuer and TMEM owner,
+// warps 2..5 = epilogue (TMEM -> Y, 16-bit).  Every mbarrier
 // wait is bounded; on expiry the CTA records SPMM_ERR_TIMEOUT in the
 // status word, lets its copies and MMAs in flight land and exits.
 #include <cuda.h>
@@ -39,7 +41,12 @@ namespace {
 
 constexpr int kEllSlots = 4;          // ELL slots per stage
 constexpr int kEllStages = 4;
-constexpr int kEllThreads = 192;
+#ifndef SPMM_ELL_PRODUCERS
+#define SPMM_ELL_PRODUCERS 2
+#endif
+constexpr int kEllProducers = SPMM_ELL_PRODUCERS;   // warp 0 and warps 6, 7, ...
+static_assert(kEllProducers >= 1 && kEllProducers <= 4, "producer warps");
+constexpr int kEllThreads = 192 + 32 * (kEllProducers - 1);
 constexpr int kEllCtasPerSm = 3;
 constexpr uint32_t kEllSlab = kSlabRows * kSlabHalf * 2 * 2;   // 4096: X slab, 16 x 128
 constexpr uint32_t kEllBlock = 16 * 16 * 2;                     // 512: one W block
@@ -51,7 +58,7 @@ struct __align__(8) EllSmem {
     uint32_t mask[kEllStages];        // per stage: valid slots (bits 0-3) | last stage of unit << 8
     uint32_t tmem_base;
     volatile int32_t abort_flag;
-    int32_t issued, consumed;
+    int32_t issued[4], consumed;      // next stage index of each producer / stages consumed
 };
 
 struct EllArgs {
@@ -149,7 +156,8 @@ __global__ void __launch_bounds__(kEllThreads, kEllCtasPerSm)
         }
         mbar_init(&sm->drain, 1);
         sm->abort_flag = 0;
-        sm->issued = sm->consumed = 0;
+        for (int i = 0; i < 4; ++i) sm->issued[i] = 0;
+        sm->consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -166,10 +174,14 @@ __global__ void __launch_bounds__(kEllThreads, kEllCtasPerSm)
     const uint32_t tmem = sm->tmem_base;
     const int32_t mb = args.mb, E = args.E;   // E >= 1 (the host handles width 0)
 
-    if (warp == 0) {
-        // ---- producer: lanes 0..3 copy the stage's X slabs, lane 4 its blocks.
-        // The first 64 slots of the next unit's row are loaded while this
-        // unit's copies are issued (slot lane and 32 + lane in c0 / c1).
+    if (warp == 0 || warp >= 6) {
+        // ---- producers: lanes 0..3 copy the stage's X slabs, lane 4 its blocks;
+        // producer j (warp 0, then warps 6, 7, ...) fills the stages it with
+        // it % kEllProducers == j.  The first 64 slots of the next unit's row
+        // are loaded while this unit's copies are issued (slot lane and
+        // 32 + lane in c0 / c1).
+        const int pid = warp == 0 ? 0 : warp - 5;
+        int32_t mine = 0;
         const int32_t *rn = args.cols + (int64_t)(ub % mb) * E;
         int32_t n0c = lane < E ? __ldg(rn + lane) : -1;
         int32_t n1c = 32 + lane < E ? __ldg(rn + 32 + lane) : -1;
@@ -194,6 +206,7 @@ __global__ void __launch_bounds__(kEllThreads, kEllCtasPerSm)
             }
             const int32_t nst = nvalid > 0 ? (nvalid + kEllSlots - 1) / kEllSlots : 1;
             for (int32_t st = 0; st < nst; ++st, ++it) {
+                if (it % kEllProducers != pid) continue;
                 const int s = it % kEllStages;
                 const uint32_t ph = (uint32_t)((it / kEllStages) & 1);
                 if (!ell_wait_warp(&sm->empty[s], ph ^ 1u, sm, lane)) {
@@ -201,6 +214,7 @@ __global__ void __launch_bounds__(kEllThreads, kEllCtasPerSm)
                     ok = false;
                     break;
                 }
+                mine = it + 1;
                 const int32_t e0 = st * kEllSlots;
                 const int nv = min(kEllSlots, nvalid - e0);
                 // column of slot e0 + lane (lanes below nv use it)
@@ -230,7 +244,7 @@ __global__ void __launch_bounds__(kEllThreads, kEllCtasPerSm)
                 __syncwarp();
             }
         }
-        if (lane == 0) sm->issued = it;
+        if (lane == 0) sm->issued[pid] = mine;
     } else if (warp == 1) {
         // ---- MMA issuer
         const uint32_t idesc = ell_idesc((uint32_t)args.fmt);
@@ -309,7 +323,10 @@ __global__ void __launch_bounds__(kEllThreads, kEllCtasPerSm)
     __syncthreads();
     if (sm->abort_flag) {
         if (threadIdx.x == 0) {
-            for (int32_t c = sm->consumed; c < sm->issued; ++c) {
+            int32_t hi = 0;
+            for (int i = 0; i < kEllProducers; ++i) hi = max(hi, sm->issued[i]);
+            for (int32_t c = sm->consumed; c < hi; ++c) {
+                if (c >= sm->issued[c % kEllProducers]) continue;
                 const int s = c % kEllStages;
                 const uint32_t par = (uint32_t)((c / kEllStages) & 1);
                 const unsigned long long t0 = gtimer();
