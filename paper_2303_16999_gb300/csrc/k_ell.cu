@@ -70,22 +70,10 @@ struct EllArgs {
     int64_t units;
 };
 
-__device__ __forceinline__ bool ell_wait(uint64_t *bar, uint32_t parity, EllSmem *sm) {
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = gtimer();
-    while (true) {
-        for (int i = 0; i < 32; ++i)
-            if (mbar_try(bar, parity)) return true;
-        if (sm->abort_flag) return false;
-        if (gtimer() - t0 > kEllWaitNs) return false;
-    }
-}
-// Waited on by lane 0 and broadcast, so the warp stays converged.
+// Bounded wait (lane 0 waits, the warp learns the verdict).
 __device__ __forceinline__ bool ell_wait_warp(uint64_t *bar, uint32_t parity, EllSmem *sm,
                                               int lane) {
-    int ok = 1;
-    if (lane == 0) ok = ell_wait(bar, parity, sm) ? 1 : 0;
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    return mbar_wait_warp(bar, parity, &sm->abort_flag, kEllWaitNs, lane);
 }
 __device__ __forceinline__ void ell_abort(EllSmem *sm, int32_t *status) {
     sm->abort_flag = 1;
@@ -162,11 +150,7 @@ __global__ void __launch_bounds__(kEllThreads, kEllCtasPerSm)
     }
     __syncthreads();
     if (warp == 1) {
-        asm volatile(
-            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                smem_u32(&sm->tmem_base)),
-            "r"(32));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        tmem_alloc(&sm->tmem_base, 32);
     }
     tc_fence_before();
     __syncthreads();
@@ -347,7 +331,7 @@ __global__ void __launch_bounds__(kEllThreads, kEllCtasPerSm)
     }
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
+        tmem_dealloc(tmem, 32);
     }
 }
 

@@ -77,22 +77,10 @@ struct SdArgs {
     int64_t ntiles;
 };
 
-__device__ __forceinline__ bool sd_wait(uint64_t *bar, uint32_t parity, SdSmem *sm) {
-    if (mbar_try(bar, parity)) return true;
-    const unsigned long long t0 = gtimer();
-    while (true) {
-        for (int i = 0; i < 32; ++i)
-            if (mbar_try(bar, parity)) return true;
-        if (sm->abort_flag) return false;
-        if (gtimer() - t0 > kSdWaitNs) return false;
-    }
-}
-// The same, waited on by lane 0 and broadcast, so a warp stays converged.
+// Bounded wait (lane 0 waits, the warp learns the verdict).
 __device__ __forceinline__ bool sd_wait_warp(uint64_t *bar, uint32_t parity, SdSmem *sm,
                                              int lane) {
-    int ok = 1;
-    if (lane == 0) ok = sd_wait(bar, parity, sm) ? 1 : 0;
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    return mbar_wait_warp(bar, parity, &sm->abort_flag, kSdWaitNs, lane);
 }
 __device__ __forceinline__ void sd_abort(SdSmem *sm, int32_t *status) {
     sm->abort_flag = 1;
@@ -235,11 +223,7 @@ __global__ void __launch_bounds__(kSdThreads, 1)
     }
     __syncthreads();
     if (warp == 1) {
-        asm volatile(
-            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                smem_u32(&sm->tmem_base)),
-            "r"(2 * kSdBN));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        tmem_alloc(&sm->tmem_base, 2 * kSdBN);
     }
     tc_fence_before();
     __syncthreads();
@@ -257,7 +241,7 @@ __global__ void __launch_bounds__(kSdThreads, 1)
                 for (int ks = 0; ks < ksteps; ++ks, ++it) {
                     const int s = it % kSdStages;
                     const uint32_t ph = (uint32_t)((it / kSdStages) & 1);
-                    if (!sd_wait(&sm->empty[s], ph ^ 1u, sm)) {
+                    if (!mbar_wait_bounded(&sm->empty[s], ph ^ 1u, &sm->abort_flag, kSdWaitNs)) {
                         sd_abort(sm, args.status);
                         ok = false;
                         break;
@@ -397,8 +381,7 @@ __global__ void __launch_bounds__(kSdThreads, 1)
     }
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(2 * kSdBN));
+        tmem_dealloc(tmem, 2 * kSdBN);
     }
 }
 
@@ -505,11 +488,7 @@ __global__ void __launch_bounds__(kSgThreads, kSgCtasPerSm)
     }
     __syncthreads();
     if (warp == 1) {
-        asm volatile(
-            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                smem_u32(&sm->tmem_base)),
-            "r"(32));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        tmem_alloc(&sm->tmem_base, 32);
     }
     tc_fence_before();
     __syncthreads();
@@ -661,7 +640,7 @@ __global__ void __launch_bounds__(kSgThreads, kSgCtasPerSm)
     }
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(32));
+        tmem_dealloc(tmem, 32);
     }
 }
 

@@ -186,14 +186,7 @@ struct __align__(8) Smem {
 // (generic ones in tc_ptx.cuh)
 // Bounded wait: false after kWaitNs or once another role has aborted.
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, Smem *sm) {
-    if (mbar_try(b, parity)) return true;
-    const unsigned long long t0 = gtimer();
-    while (true) {
-        for (int i = 0; i < 32; ++i)
-            if (mbar_try(b, parity)) return true;
-        if (sm->abort_flag) return false;
-        if (gtimer() - t0 > kWaitNs) return false;
-    }
+    return mbar_wait_bounded(b, parity, &sm->abort_flag, kWaitNs);
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
@@ -318,11 +311,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     const int64_t nunits = sm->nunits;
     if (nunits == 0) return;
     if (warp == 1) {
-        asm volatile(
-            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                smem_u32(&sm->tmem_base)),
-            "r"(kAccBufs * kAccCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        tmem_alloc(&sm->tmem_base, kAccBufs * kAccCols);
     }
     tc_fence_before();
     __syncthreads();
@@ -708,8 +697,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kAccBufs * kAccCols));
+        tmem_dealloc(tmem, kAccBufs * kAccCols);
     }
 }
 
