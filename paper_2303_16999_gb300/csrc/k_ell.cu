@@ -70,7 +70,7 @@ struct EllArgs {
     int64_t units;
 };
 
-// Bounded wait (lane 0 waits, the warp learns the verdict).
+// Bounded wait (lane 0 waits, the warp learns the outcome).
 __device__ __forceinline__ bool ell_wait_warp(uint64_t *bar, uint32_t parity, EllSmem *sm,
                                               int lane) {
     return mbar_wait_warp(bar, parity, &sm->abort_flag, kEllWaitNs, lane);

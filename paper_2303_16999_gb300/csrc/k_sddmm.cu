@@ -77,7 +77,7 @@ struct SdArgs {
     int64_t ntiles;
 };
 
-// Bounded wait (lane 0 waits, the warp learns the verdict).
+// Bounded wait (lane 0 waits, the warp learns the outcome).
 __device__ __forceinline__ bool sd_wait_warp(uint64_t *bar, uint32_t parity, SdSmem *sm,
                                              int lane) {
     return mbar_wait_warp(bar, parity, &sm->abort_flag, kSdWaitNs, lane);

@@ -179,7 +179,7 @@ struct __align__(8) Smem {
     volatile int32_t abort_flag;
     int32_t issued[kProducers], consumed[2];   // per producer / per MMA warp
     int64_t nunits;
-    int32_t epi_ok[2];             // accumulator-ready verdict, per unit parity
+    int32_t epi_ok[2];             // accumulator-ready outcome, per unit parity
 };
 
 // ------------------------------------------------------------ PTX helpers
