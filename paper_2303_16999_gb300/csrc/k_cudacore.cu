@@ -305,14 +305,10 @@ cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const void *X, i
     const bool dyn = p->mode == SPMM_DYNAMIC;
     const size_t smem = SX ? (size_t)p->k * V * sizeof(T) : 0;
     if (SX) {
-        static bool attr = false;
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(gather1_kernel<T, V, SX>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 200 * 1024);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
+        static std::atomic<uint64_t> attrs{0};
+        const cudaError_t e =
+            set_smem_attrs_once(attrs, gather1_kernel<T, V, SX>, 200 * 1024, false);
+        if (e != cudaSuccess) return e;
     }
     // persistent: as many 512-thread blocks as fit (shared memory allowing)
     const int per_sm = SX ? (smem <= 100 * 1024 ? 2 : 1) : SPMM_G1_BLOCKS;
@@ -484,13 +480,15 @@ cudaError_t launch_reduce(const spmm_plan *p, int64_t n, void *Y, int64_t ldy, c
     if (n_red == 0 || n == 0) return cudaSuccess;
     const bool tc = p->kernel == SPMM_KERNEL_TC;
     const int rows_per_unit = tc ? kTile : 1;
-    // about two waves of blocks whatever the capacity: every loop of the
-    // kernel strides, and a dynamic plan's capacity (launched in full, its
-    // true count read on the device) is usually far above the reductions
-    // it has
+    // about two waves of blocks whatever the capacity (every loop of the
+    // kernel strides); a dynamic plan's capacity, launched in full with its
+    // true count read on the device, is usually far above the reductions it
+    // has (mostly none), so it gets about two blocks per SM and the empty
+    // launch stays short
     const unsigned gx = grid1d(n, 128) > 64u ? 64u : grid1d(n, 128);
-    const unsigned gz = (unsigned)(n_red < 64 ? n_red : 64);
-    const int64_t want = 2 * 16 * (int64_t)std::max(p->sm_count, 1);
+    const int64_t zcap = dyn ? 8 : 64;
+    const unsigned gz = (unsigned)(n_red < zcap ? n_red : zcap);
+    const int64_t want = (dyn ? 2 : 2 * 16) * (int64_t)std::max(p->sm_count, 1);
     int64_t gy = tc ? (int64_t)(kMaxGroupRows * kTile) : 1;
     gy = std::max<int64_t>(1, std::min<int64_t>(gy, want / ((int64_t)gx * gz)));
     dim3 grid(gx, (unsigned)gy, gz);

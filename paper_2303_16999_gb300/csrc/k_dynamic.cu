@@ -5,13 +5,17 @@
 // The paper's host utility encodes metaInfo buckets and the device walks
 // distribution and propagation phases; here the whole re-partition runs on
 // the device in a handful of stream-ordered kernels with no host round trip:
-//   1. validate + histogram of block rows          (grid over the pattern)
-//   2. exclusive scan -> row_ptr (and b = 1 items)  (one CTA)
-//   3. scatter into rows                            (grid over the pattern)
-//   4. per-row rank sort by column, duplicate check (one warp per row)
-//   5. tensor-core plans: per-group column bitmap -> entry / slot counts,
-//      a group scan (chunk size, item / workspace offsets), and a per-group
-//      fill of entries, slots, items and block -> slot maps.
+//   1. validate + histogram of block rows, then (the last block to finish)
+//      the exclusive scan -> row_ptr (and b = 1 items) (grid over the pattern)
+//   2. scatter into rows                            (grid over the pattern)
+//   3. per-row rank sort by column, duplicate check (one warp per row)
+//   4. tensor-core plans: per-group column bitmap -> entry / slot counts,
+//      then (the last block) the group scan (chunk size, item / workspace
+//      offsets), and a per-group fill of entries, slots, items and
+//      block -> slot maps.
+// A scan runs in the last block of the kernel before it (a ticket counter,
+// with fences on both sides) rather than as its own launch: each launch of
+// this latency-bound chain costs a few microseconds.
 // The arrays equal the oracle's dynamic-plan rules bit for bit (no item
 // reordering, no zero-padded intervals).  A rejected pattern sets the plan's
 // status word; the product kernels then skip, leaving Y unwritten.
@@ -30,10 +34,28 @@ __device__ __forceinline__ int64_t clamp_nnzb(const int32_t *d_nnzb, int64_t cap
     return n < 0 ? 0 : (n > cap ? cap : n);
 }
 
-// 1. range check and block-row histogram
-__global__ void dyn_validate_hist(const int32_t *d_nnzb, const int32_t *brow, const int32_t *bcol,
-                                  int64_t cap, int32_t mb, int32_t kb, int32_t *row_cnt,
-                                  int32_t *status) {
+// True in the one block that finishes last: every block fences its writes
+// and takes a ticket; the block that draws the last ticket fences again
+// before it reads what the others wrote.
+__device__ bool last_block_done(int32_t *ticket) {
+    __shared__ int is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1) == (int)(gridDim.x - 1) ? 1 : 0;
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last != 0;
+}
+
+__device__ void scan_rows(const int32_t *d_nnzb, int64_t cap, int32_t mb, const int32_t *row_cnt,
+                          int32_t *row_ptr, int32_t *cursor, int32_t *row_ibeg, int32_t *row_wbeg,
+                          int32_t *row_rbeg, int32_t *counts, int rows_items);
+
+// 1. range check and block-row histogram; the last block scans the rows
+__global__ void __launch_bounds__(1024) dyn_validate_scan(
+    const int32_t *d_nnzb, const int32_t *brow, const int32_t *bcol, int64_t cap, int32_t mb,
+    int32_t kb, int32_t *row_cnt, int32_t *status, int32_t *row_ptr, int32_t *cursor,
+    int32_t *row_ibeg, int32_t *row_wbeg, int32_t *row_rbeg, int32_t *counts, int rows_items) {
     pdl_enter();
     const int64_t raw = *d_nnzb;
     if (blockIdx.x == 0 && threadIdx.x == 0 && (raw < 0 || raw > cap)) flag(status, kDevCapacity);
@@ -47,6 +69,9 @@ __global__ void dyn_validate_hist(const int32_t *d_nnzb, const int32_t *brow, co
         }
         atomicAdd(&row_cnt[r], 1);
     }
+    if (!last_block_done(counts + kCntTicketRows)) return;
+    scan_rows(d_nnzb, cap, mb, row_cnt, row_ptr, cursor, row_ibeg, row_wbeg, row_rbeg, counts,
+              rows_items);
 }
 
 // Block-wide exclusive scan of one value per thread (blockDim.x == 1024).
@@ -79,22 +104,19 @@ __device__ __forceinline__ int32_t nchunks(int64_t L, int64_t C) {
     return (int32_t)(L <= C ? 1 : (L + C - 1) / C);
 }
 
-// 2. row_ptr / cursor; for b = 1 also the row-item, workspace and reduction
-// offsets (C1 = max(64, 2 * ceil(nnzb / mb)), the static default).
-__global__ void __launch_bounds__(1024) dyn_scan_rows(const int32_t *d_nnzb, int64_t cap,
-                                                      int32_t mb, const int32_t *row_cnt,
-                                                      int32_t *row_ptr, int32_t *cursor,
-                                                      int32_t *row_ibeg, int32_t *row_wbeg,
-                                                      int32_t *row_rbeg, int32_t *counts,
-                                                      int rows_items) {
-    pdl_enter();
+// row_ptr / cursor; for b = 1 also the row-item, workspace and reduction
+// offsets (C1 = max(64, 2 * ceil(nnzb / mb)), the static default).  One
+// block of 1024 threads (the histogram's last).
+__device__ void scan_rows(const int32_t *d_nnzb, int64_t cap, int32_t mb, const int32_t *row_cnt,
+                          int32_t *row_ptr, int32_t *cursor, int32_t *row_ibeg, int32_t *row_wbeg,
+                          int32_t *row_rbeg, int32_t *counts, int rows_items) {
     const int64_t nnzb = clamp_nnzb(d_nnzb, cap);
     const int64_t avg = mb ? (nnzb + mb - 1) / mb : 0;
     const int64_t C1 = avg * 2 > 64 ? avg * 2 : 64;
     int64_t base = 0, ibase = 0, wbase = 0, rbase = 0;
     for (int32_t r0 = 0; r0 < mb; r0 += 1024) {
         const int32_t r = r0 + threadIdx.x;
-        const int64_t L = r < mb ? row_cnt[r] : 0;
+        const int64_t L = r < mb ? __ldcg(row_cnt + r) : 0;
         const int32_t nch = r < mb ? nchunks(L, C1) : 0;
         int64_t t0, t1, t2, t3;
         const int64_t e0 = block_scan(L, &t0);
@@ -127,7 +149,7 @@ __global__ void __launch_bounds__(1024) dyn_scan_rows(const int32_t *d_nnzb, int
     }
 }
 
-// 3. scatter into rows (order within a row fixed by step 4)
+// 2. scatter into rows (order within a row fixed by step 3)
 __global__ void dyn_scatter(const int32_t *d_nnzb, const int32_t *brow, const int32_t *bcol,
                             int64_t cap, int32_t mb, int32_t kb, int32_t *cursor, int32_t *tmp_col,
                             int32_t *tmp_perm) {
@@ -143,7 +165,7 @@ __global__ void dyn_scatter(const int32_t *d_nnzb, const int32_t *brow, const in
     }
 }
 
-// 4. one warp per row: rank of each element among the row's columns (keys
+// 3. one warp per row: rank of each element among the row's columns (keys
 // are unique unless the pattern repeats a block, which is flagged); for
 // b = 1 the warp also writes its row's items.
 __global__ void dyn_sort_rows(int32_t mb, const int32_t *row_ptr, const int32_t *tmp_col,
@@ -197,10 +219,18 @@ __global__ void dyn_sort_rows(int32_t mb, const int32_t *row_ptr, const int32_t 
     }
 }
 
-// 5a. per group: bitmap of group rows per tile column -> entry and slot counts
-__global__ void dyn_group_count(int32_t kt, int32_t T, const int32_t *grp_row0,
-                                const int32_t *grp_rows, const int32_t *row_ptr,
-                                const int32_t *col_idx, int32_t *grp_cnt) {
+__device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *grp_cnt,
+                           int32_t *grp_ebeg, int32_t *grp_sbeg, int32_t *grp_ibeg,
+                           int32_t *grp_wbeg, int64_t *grp_wrow, int32_t *grp_rbeg,
+                           int32_t *ent_tbeg, int32_t *counts);
+
+// 4a. per group: bitmap of group rows per tile column -> entry and slot
+// counts; the last block scans the groups
+__global__ void __launch_bounds__(1024) dyn_group_count_scan(
+    int32_t kt, int32_t T, const int32_t *grp_row0, const int32_t *grp_rows,
+    const int32_t *row_ptr, const int32_t *col_idx, int32_t *grp_cnt, int32_t *grp_ebeg,
+    int32_t *grp_sbeg, int32_t *grp_ibeg, int32_t *grp_wbeg, int64_t *grp_wrow,
+    int32_t *grp_rbeg, int32_t *ent_tbeg, int32_t *counts) {
     pdl_enter();
     extern __shared__ uint32_t colmask[];
     const int g = blockIdx.x;
@@ -237,21 +267,22 @@ __global__ void dyn_group_count(int32_t kt, int32_t T, const int32_t *grp_row0,
         grp_cnt[g * 2] = acc[0];
         grp_cnt[g * 2 + 1] = acc[1];
     }
+    if (!last_block_done(counts + kCntTicketGroups)) return;
+    group_scan((int32_t)gridDim.x, grp_rows, grp_cnt, grp_ebeg, grp_sbeg, grp_ibeg, grp_wbeg,
+               grp_wrow, grp_rbeg, ent_tbeg, counts);
 }
 
-// 5b. group offsets and the chunk size C = max(16, ceil(5E / 4G))
-__global__ void __launch_bounds__(1024) dyn_group_scan(int32_t G, const int32_t *grp_rows,
-                                                       const int32_t *grp_cnt, int32_t *grp_ebeg,
-                                                       int32_t *grp_sbeg, int32_t *grp_ibeg,
-                                                       int32_t *grp_wbeg, int64_t *grp_wrow,
-                                                       int32_t *grp_rbeg, int32_t *ent_tbeg,
-                                                       int32_t *counts) {
-    pdl_enter();
+// 4b. group offsets and the chunk size C = max(16, ceil(5E / 4G)); one block
+// of 1024 threads (the group counts' last).
+__device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *grp_cnt,
+                           int32_t *grp_ebeg, int32_t *grp_sbeg, int32_t *grp_ibeg,
+                           int32_t *grp_wbeg, int64_t *grp_wrow, int32_t *grp_rbeg,
+                           int32_t *ent_tbeg, int32_t *counts) {
     __shared__ int64_t sE;
     int64_t tot;
     {
         int64_t part = 0;
-        for (int32_t g = threadIdx.x; g < G; g += 1024) part += grp_cnt[g * 2];
+        for (int32_t g = threadIdx.x; g < G; g += 1024) part += __ldcg(grp_cnt + g * 2);
         block_scan(part, &tot);
         if (threadIdx.x == 0) sE = tot;
         __syncthreads();
@@ -262,8 +293,8 @@ __global__ void __launch_bounds__(1024) dyn_group_scan(int32_t G, const int32_t 
     int64_t be = 0, bs = 0, bi = 0, bw = 0, bwr = 0, br = 0;
     for (int32_t g0 = 0; g0 < G; g0 += 1024) {
         const int32_t g = g0 + threadIdx.x;
-        const int64_t L = g < G ? grp_cnt[g * 2] : 0;
-        const int64_t S = g < G ? grp_cnt[g * 2 + 1] : 0;
+        const int64_t L = g < G ? __ldcg(grp_cnt + g * 2) : 0;
+        const int64_t S = g < G ? __ldcg(grp_cnt + g * 2 + 1) : 0;
         const int32_t nch = g < G ? nchunks(L, C) : 0;
         const int64_t rows = g < G ? (int64_t)grp_rows[g] * kTile : 0;
         int64_t t0, t1, t2, t3, t4, t5;
@@ -301,7 +332,7 @@ __global__ void __launch_bounds__(1024) dyn_group_scan(int32_t G, const int32_t 
     }
 }
 
-// 5c. per group: entries (ascending tile column), slots (ascending rows, one
+// 4c. per group: entries (ascending tile column), slots (ascending rows, one
 // per tile), block -> slot / offset, items and workspace / reduction records
 __global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *grp_row0,
                                const int32_t *grp_rows, const int32_t *row_ptr,
@@ -416,10 +447,9 @@ cudaError_t launch_dynamic_csr(spmm_plan *p, const spmm_dpattern *dp, cudaStream
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_counts, 0, sizeof(int32_t) * kCntCount, s);
     if (e != cudaSuccess) return e;
     const unsigned gp = grid_for(cap, 256, 4096);
-    pdl_launch(dyn_validate_hist, dim3(gp), dim3(256), 0, s, dp->d_nnzb, dp->d_brow, dp->d_bcol,
-        cap, mb, kb, d.row_cnt, p->d_status);
-    pdl_launch(dyn_scan_rows, dim3(1), dim3(1024), 0, s, dp->d_nnzb, cap, mb, d.row_cnt,
-        p->d_row_ptr, d.cursor, d.row_ibeg, d.row_wbeg, d.row_rbeg, p->d_counts, 0);
+    pdl_launch(dyn_validate_scan, dim3(grid_for(cap, 1024, 1024)), dim3(1024), 0, s, dp->d_nnzb,
+        dp->d_brow, dp->d_bcol, cap, mb, kb, d.row_cnt, p->d_status, p->d_row_ptr, d.cursor,
+        d.row_ibeg, d.row_wbeg, d.row_rbeg, p->d_counts, 0);
     pdl_launch(dyn_scatter, dim3(gp), dim3(256), 0, s, dp->d_nnzb, dp->d_brow, dp->d_bcol, cap, mb,
         kb, d.cursor, d.tmp_col, d.tmp_perm);
     pdl_launch(dyn_sort_rows, dim3(grid_for((int64_t)mb * 32, 256, 1u << 30)), dim3(256), 0, s, mb,
@@ -438,10 +468,9 @@ cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cuda
     if (e == cudaSuccess) e = cudaMemsetAsync(p->d_counts, 0, sizeof(int32_t) * kCntCount, s);
     if (e != cudaSuccess) return e;
     const unsigned gp = grid_for(cap, 256, 4096);
-    pdl_launch(dyn_validate_hist, dim3(gp), dim3(256), 0, s, dp->d_nnzb, dp->d_brow, dp->d_bcol,
-        cap, mb, kb, d.row_cnt, p->d_status);
-    pdl_launch(dyn_scan_rows, dim3(1), dim3(1024), 0, s, dp->d_nnzb, cap, mb, d.row_cnt,
-        p->d_row_ptr, d.cursor, d.row_ibeg, d.row_wbeg, d.row_rbeg, p->d_counts, tc ? 0 : 1);
+    pdl_launch(dyn_validate_scan, dim3(grid_for(cap, 1024, 1024)), dim3(1024), 0, s, dp->d_nnzb,
+        dp->d_brow, dp->d_bcol, cap, mb, kb, d.row_cnt, p->d_status, p->d_row_ptr, d.cursor,
+        d.row_ibeg, d.row_wbeg, d.row_rbeg, p->d_counts, tc ? 0 : 1);
     pdl_launch(dyn_scatter, dim3(gp), dim3(256), 0, s, dp->d_nnzb, dp->d_brow, dp->d_bcol, cap, mb,
         kb, d.cursor, d.tmp_col, d.tmp_perm);
     pdl_launch(dyn_sort_rows, dim3(grid_for((int64_t)mb * 32, 256, 1u << 30)), dim3(256), 0, s, mb,
@@ -449,11 +478,10 @@ cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cuda
         d.row_ibeg, d.row_wbeg, d.row_rbeg, p->d_counts, p->d_items, p->d_ws_row0, p->d_red);
     if (tc) {
         const int32_t kt = (int32_t)(p->k / kTile), T = kTile / p->b, G = (int32_t)p->n_groups;
-        pdl_launch(dyn_group_count, dim3(G), dim3(256), sizeof(uint32_t) * kt, s, kt, T,
-            p->d_grp_row0, p->d_grp_rows, p->d_row_ptr, p->d_col_idx, d.grp_cnt);
-        pdl_launch(dyn_group_scan, dim3(1), dim3(1024), 0, s, G, p->d_grp_rows, d.grp_cnt,
-            p->d_grp_ebeg, d.grp_sbeg, d.grp_ibeg, d.grp_wbeg, d.grp_wrow, d.grp_rbeg,
-            p->d_ent_tbeg, p->d_counts);
+        pdl_launch(dyn_group_count_scan, dim3(G), dim3(1024), sizeof(uint32_t) * kt, s, kt, T,
+            p->d_grp_row0, p->d_grp_rows, p->d_row_ptr, p->d_col_idx, d.grp_cnt, p->d_grp_ebeg,
+            d.grp_sbeg, d.grp_ibeg, d.grp_wbeg, d.grp_wrow, d.grp_rbeg, p->d_ent_tbeg,
+            p->d_counts);
         pdl_launch(dyn_group_fill, dim3(G), dim3(1024), sizeof(uint32_t) * 3 * kt, s, kt, T, p->b,
             p->d_grp_row0, p->d_grp_rows, p->d_row_ptr, p->d_col_idx, p->d_perm, p->d_grp_ebeg,
             d.grp_sbeg, d.grp_ibeg, d.grp_wbeg, d.grp_wrow, d.grp_rbeg, p->d_counts, p->d_ent_col,

@@ -355,17 +355,10 @@ template <typename T>
 cudaError_t launch_ell_t(const CUtensorMap &mx, const CUtensorMap &mw, const EllArgs &a, int sms,
                          cudaStream_t s) {
     const size_t smem = 1024 + (size_t)kEllStages * kEllStageBytes + sizeof(EllSmem);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(ell_kernel<T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        // all of the unified L1 / shared memory as shared: three CTAs per SM
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(ell_kernel<T>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     100);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    // all of the unified L1 / shared memory as shared: three CTAs per SM
+    static std::atomic<uint64_t> attrs{0};
+    const cudaError_t e = set_smem_attrs_once(attrs, ell_kernel<T>, (int)smem, true);
+    if (e != cudaSuccess) return e;
     const int per_sm = kEllCtasPerSm;
     const int64_t slots = (int64_t)sms * per_sm;
     const int grid = (int)(a.units < slots ? a.units : slots);

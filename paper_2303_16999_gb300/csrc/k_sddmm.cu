@@ -664,13 +664,9 @@ cudaError_t launch_dense(const CUtensorMap &mdy, const CUtensorMap &mx, const Sd
                          cudaStream_t s) {
     const size_t smem = 1024 + (size_t)kSdStages * kSdStageBytes +
                         sizeof(int2) * kSdRing * 128 + sizeof(SdSmem);
-    static bool attr_set = false;
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            sddmm_dense_kernel<B, OUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attrs{0};
+    const cudaError_t e = set_smem_attrs_once(attrs, sddmm_dense_kernel<B, OUT>, (int)smem, false);
+    if (e != cudaSuccess) return e;
     pdl_launch(sddmm_dense_kernel<B, OUT>, dim3(grid), dim3(kSdThreads), smem, s, mdy, mx, a);
     return cudaGetLastError();
 }
@@ -679,16 +675,9 @@ template <int OUT>
 cudaError_t launch_gather(const CUtensorMap &mdy, const CUtensorMap &mx, const SgArgs &a, int grid,
                           cudaStream_t s) {
     const size_t smem = 1024 + (size_t)kSgStages * kSgStageBytes + sizeof(SdSmem);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sddmm_gather_kernel<OUT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(sddmm_gather_kernel<OUT>,
-                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attrs{0};
+    const cudaError_t e = set_smem_attrs_once(attrs, sddmm_gather_kernel<OUT>, (int)smem, true);
+    if (e != cudaSuccess) return e;
     pdl_launch(sddmm_gather_kernel<OUT>, dim3(grid), dim3(kSgThreads), smem, s, mdy, mx, a);
     return cudaGetLastError();
 }

@@ -979,13 +979,9 @@ cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
     const int grid = (int)(B.total_units < slots ? B.total_units : slots);
     using G = StageGeom<W8, GEO>;
     const size_t smem = 1024 + (size_t)G::stages * G::bytes + sizeof(Smem);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(tc_kernel<T, W8, GEO>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attrs{0};
+    const cudaError_t e = set_smem_attrs_once(attrs, tc_kernel<T, W8, GEO>, (int)smem, false);
+    if (e != cudaSuccess) return e;
     pdl_launch(tc_kernel<T, W8, GEO>, dim3(grid), dim3(kThreads), smem, s, B);
     return cudaGetLastError();
 }

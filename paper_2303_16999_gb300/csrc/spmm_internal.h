@@ -28,7 +28,9 @@ enum CountIdx : int {
     kCntWsRows = 5,   // workspace rows
     kCntRed = 6,      // split groups / rows to reduce
     kCntChunk = 7,    // chunk size C chosen on the device
-    kCntCount = 8
+    kCntTicketRows = 8,    // blocks done with the row histogram (the last one scans)
+    kCntTicketGroups = 9,  // blocks done with the group counts (the last one scans)
+    kCntCount = 10
 };
 
 // device status word codes (mirrors spmm_status where applicable)
