@@ -406,7 +406,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                         }
                     }
                 } else {
-                    if (lane == 0) mbar_arrive_tx(&sm->full[stage], mine * kSlabBytes);
+                    // a column tile whose upper 64 columns lie past n (small n)
+                    // fetches its lower halves only: the upper half of the
+                    // accumulator then holds rows of Y that are never stored
+                    const bool half = !P.x3d && n0 + kNTile / 2 >= P.n;
+                    if (lane == 0)
+                        mbar_arrive_tx(&sm->full[stage],
+                                       mine * (half ? kSlabBytes / 2 : kSlabBytes));
                     __syncwarp();
                     if (lane < mine) {
                         const CUtensorMap *xmap = &B.maps[un.p];
@@ -416,8 +422,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                                         &sm->full[stage]);
                         } else {
                             tma_load_2d(slab, xmap, n0, (int)col * kTile, &sm->full[stage]);
-                            tma_load_2d(slab + kSlabBytes / 2, xmap, n0 + kNTile / 2,
-                                        (int)col * kTile, &sm->full[stage]);
+                            if (!half)
+                                tma_load_2d(slab + kSlabBytes / 2, xmap, n0 + kNTile / 2,
+                                            (int)col * kTile, &sm->full[stage]);
                         }
                     }
                 }
