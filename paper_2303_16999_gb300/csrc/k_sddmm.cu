@@ -700,7 +700,8 @@ cudaError_t launch_dense_b(int out, const CUtensorMap &mdy, const CUtensorMap &m
 // ~1.4 PFLOP/s); the times cross near d = 1/13, so blocks of 16 below that
 // density (nnzb_max for dynamic plans) take the gathered form.
 bool sddmm_gathers(const spmm_plan *p) {
-    if (p->b != 16 || !p->d_sd_items) return false;
+    // (host-only plans report the choice a device plan of theirs would make)
+    if (p->b != 16 || (!p->host_only && !p->d_sd_items)) return false;
     const double nb = (double)(p->mode == SPMM_STATIC ? p->nnzb : p->nnzb_max);
     return nb * 256.0 * 13.0 < (double)p->m * (double)p->k;
 }

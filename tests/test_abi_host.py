@@ -80,6 +80,16 @@ def test_errors():
     assert e.value.status == S.ERR_ARG
 
 
+def test_sddmm_form_follows_density():
+    """spmm_sddmm gathers blocks of 16 below a density of 1/13 and computes
+    dense tiles otherwise (reported in the plan info)."""
+    rng = np.random.default_rng(3)
+    for b, d, form in ((16, 1 / 16, 1), (16, 1 / 8, 0), (16, 1 / 4, 0), (8, 1 / 32, 0), (1, 1 / 64, 0)):
+        mb = kb = 512 // b
+        brow, bcol = _rand(rng, mb, kb, int(d * mb * kb))
+        assert _plan(512, 512, b, brow, bcol).info()["sddmm_form"] == form, (b, d)
+
+
 def _rand(rng, mb, kb, nnzb):
     idx = rng.choice(mb * kb, nnzb, replace=False)
     o = rng.permutation(nnzb)
