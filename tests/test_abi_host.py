@@ -198,3 +198,26 @@ def test_transposed_plan_is_the_plan_of_w_transpose(b):
     for key in TC_KEYS:
         assert np.array_equal(p.array(key), want[key]), key
     assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
+
+
+def test_ell_layout_of_a_pattern():
+    """workloads.to_ell, the Blocked-ELL layout the ELL tests and benchmark
+    feed spmm_run_ell: every block appears once in its row, columns ascend,
+    -1 padding follows the blocks, src maps each slot back to the pattern."""
+    from paper_2303_16999_gb300 import workloads as wl
+    rng = np.random.default_rng(12)
+    mb, kb = 40, 30
+    brow, bcol = _rand(rng, mb, kb, 300)
+    cols, src = wl.to_ell(brow, bcol, mb)
+    counts = np.bincount(brow, minlength=mb)
+    assert cols.shape == (mb, counts.max())
+    for r in range(mb):
+        c = cols[r]
+        nv = counts[r]
+        assert np.all(c[nv:] == -1) and np.all(c[:nv] >= 0)
+        assert np.all(np.diff(c[:nv]) > 0)
+        assert np.array_equal(np.sort(bcol[brow == r]), c[:nv])
+        assert np.all(brow[src[r, :nv]] == r) and np.array_equal(bcol[src[r, :nv]], c[:nv])
+        assert np.all(src[r, nv:] == -1)
+    wide, _ = wl.to_ell(brow, bcol, mb, width=counts.max() + 3)
+    assert wide.shape[1] == counts.max() + 3 and np.all(wide[:, -3:] == -1)
