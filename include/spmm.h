@@ -115,11 +115,14 @@ typedef struct spmm_plan spmm_plan;
 /*
  * spmm_plan_create -- builds a plan (Section 3.2 static partitioner /
  * Section 3.3 and Appendix A.2 dynamic planner).
- *   m, k      : W is m x k; both multiples of b (else SPMM_ERR_SHAPE).
+ *   m, k      : W is m x k; both multiples of b, m/b and k/b at most INT32_MAX
+ *               (block indices are int32; else SPMM_ERR_SHAPE).
  *   n_max     : largest n any spmm_run of this plan will pass (sizes workspace).
  *   b         : block size, 1, 4, 8 or 16.
  *   mode      : SPMM_STATIC (pattern != NULL, host arrays, nnzb_max ignored)
- *               or SPMM_DYNAMIC (pattern ignored, nnzb_max >= 0 fixes capacity).
+ *               or SPMM_DYNAMIC (pattern ignored, 0 <= nnzb_max <= INT32_MAX fixes
+ *               capacity, else SPMM_ERR_ARG).  A static pattern->nnzb above
+ *               INT32_MAX is SPMM_ERR_SHAPE.
  *   w_dtype, x_dtype : see "Types" above.
  *   opts      : NULL or options.
  *   out       : receives the plan (NULL on error).

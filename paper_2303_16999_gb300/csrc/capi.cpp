@@ -354,8 +354,8 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
         set_error("rows_per_group must be in 0..%d, max_per_item >= 0", kMaxGroupRows);
         return SPMM_ERR_ARG;
     }
-    if (mode == SPMM_DYNAMIC && (nnzb_max < 0 || o.host_only)) {
-        set_error("dynamic plans need nnzb_max >= 0 and device memory");
+    if (mode == SPMM_DYNAMIC && (nnzb_max < 0 || nnzb_max > INT32_MAX || o.host_only)) {
+        set_error("dynamic plans need 0 <= nnzb_max <= INT32_MAX and device memory");
         return SPMM_ERR_ARG;
     }
     if (mode == SPMM_STATIC && !pattern) {

@@ -20,6 +20,12 @@ spmm_status validate_pattern(int64_t m, int64_t k, int b, int64_t nnzb, const in
                   (long long)m, (long long)k);
         return SPMM_ERR_SHAPE;
     }
+    // block indices, block-CSR offsets and tile slots are int32 on the device
+    if (m / b > INT32_MAX || k / b > INT32_MAX || nnzb > INT32_MAX) {
+        set_error("shape: %lld x %lld blocks or nnzb=%lld outside the int32 index range",
+                  (long long)(m / b), (long long)(k / b), (long long)nnzb);
+        return SPMM_ERR_SHAPE;
+    }
     if (nnzb < 0 || (nnzb > 0 && (!brow || !bcol))) {
         set_error("pattern: nnzb=%lld with null arrays", (long long)nnzb);
         return SPMM_ERR_ARG;

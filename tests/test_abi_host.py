@@ -80,6 +80,25 @@ def test_errors():
     assert e.value.status == S.ERR_ARG
 
 
+def test_int32_index_range_is_enforced():
+    """Block indices, block-CSR offsets and tile slots are int32 on the
+    device: shapes and block counts beyond that range are refused before any
+    pattern array is read or any memory is allocated."""
+    import ctypes
+    big = 1 << 31
+    opts = S.PlanOpts(host_only=1)
+    tiny = np.zeros(1, np.int32)
+    ptr = tiny.ctypes.data_as(ctypes.c_void_p)
+    for m, k, nnzb in ((big, 16, 1), (16, big, 1), (16, 16, big)):
+        with pytest.raises(S.SpmmError) as e:
+            S.spmm_plan_create(m, k, 8, 1, S.STATIC, S.F16, S.F16,
+                               S.Pattern(nnzb, ptr, ptr), 0, opts)
+        assert e.value.status == S.ERR_SHAPE, (m, k, nnzb)
+    with pytest.raises(S.SpmmError) as e:
+        S.spmm_plan_create(256, 256, 8, 16, S.DYNAMIC, S.F16, S.F16, None, big, None)
+    assert e.value.status == S.ERR_ARG
+
+
 def test_sddmm_form_follows_density():
     """spmm_sddmm gathers blocks of 16 below a density of 1/13 and computes
     dense tiles otherwise (reported in the plan info)."""
