@@ -350,8 +350,10 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
         kernel = SPMM_KERNEL_TC;
     st = check_types(kernel, b, w_dtype, x_dtype, m, k);
     if (st != SPMM_OK) return st;
-    if (o.rows_per_group < 0 || o.rows_per_group > kMaxGroupRows || o.max_per_item < 0) {
-        set_error("rows_per_group must be in 0..%d, max_per_item >= 0", kMaxGroupRows);
+    if (o.rows_per_group < 0 || o.rows_per_group > kMaxGroupRows || o.max_per_item < 0 ||
+        o.col_tiles < 0 || o.col_tiles > 2) {
+        set_error("rows_per_group must be in 0..%d, max_per_item >= 0, col_tiles in 0..2",
+                  kMaxGroupRows);
         return SPMM_ERR_ARG;
     }
     if (mode == SPMM_DYNAMIC && (nnzb_max < 0 || nnzb_max > INT32_MAX || o.host_only)) {
@@ -367,6 +369,7 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
     p->m = m;
     p->k = k;
     p->n_max = n_max;
+    p->col_tiles = o.col_tiles;
     p->b = b;
     p->mode = mode;
     p->wdt = w_dtype;

@@ -35,6 +35,11 @@
 // bound by the copy latency (a stage is refilled only after its MMAs
 // complete): each role spends about a third of a stage waiting.
 //
+// Wide launches (stage geometry 2, dense tiles): one CTA per SM covers two
+// 128-column tiles of n with all 512 TMEM columns; each stage holds both
+// tiles' X slabs and one set of W tiles, and every MMA word is issued once
+// per tile, so each W tile is read from L2 once per 256 columns.
+//
 // Warp roles (288 threads): warp 0 = W producer, warps 1 and 8 = MMA issuers
 // (warp 1 owns TMEM), warps 2..5 = epilogue (TMEM -> registers -> Y or
 // workspace) and, for E4M3 weights, converters, warps 6 and 7 = X producers.
@@ -85,6 +90,15 @@ namespace {
 #ifndef SPMM_TC_TILES_D
 #define SPMM_TC_TILES_D 64
 #endif
+#ifndef SPMM_TC_STAGES_W
+#define SPMM_TC_STAGES_W 3  // dense, two column tiles per CTA: 2 x 4 slabs, 64 tiles
+#endif
+#ifndef SPMM_TC_WIDE_MIN
+#define SPMM_TC_WIDE_MIN 3  // wide launches need work units >= this x SMs / 2
+#endif
+#ifndef SPMM_TC_WIDE_TPM
+#define SPMM_TC_WIDE_TPM 7  // ... and at least this many tiles per MMA
+#endif
 #ifndef SPMM_TC_STAGES_S
 #define SPMM_TC_STAGES_S 2  // sparse: 8 slabs, 44 tiles
 #endif
@@ -119,20 +133,28 @@ constexpr int kStagesMax = 4;                                     // >= every ge
 constexpr int kRowCap = SPMM_TC_RCAP;
 constexpr int kAccCols = kRowCap * kTile;                         // TMEM columns per buffer
 constexpr int kMaxBatch = 64;                                     // problems per launch
+constexpr int kJointSlabsG = 4;                                   // slabs of a joint X box
 
-// Stage layout: X slabs | 16-bit W tiles (MMA B operand) | (E4M3 only) the
-// FP8 codes and their scales as loaded, which the converter warps expand
-// into the 16-bit area.
-// GEO: 0 = dense, 1 = sparse.
+// Stage layout: X slabs (of each column tile the CTA covers) | 16-bit W
+// tiles (MMA B operand) | (E4M3 only) the FP8 codes and their scales as
+// loaded, which the converter warps expand into the 16-bit area.
+// GEO: 0 = dense, 1 = sparse, 2 = dense over two column tiles per CTA
+// ("wide": one CTA per SM, each W tile serves 256 columns of n; the same
+// stage records as GEO 0, since the entry and tile caps are the same).
 template <bool W8, int GEO> struct StageGeom {
+    static_assert(GEO != 2 || !W8, "wide stages take 16-bit weights only");
+    static constexpr int sets = GEO == 2 ? 2 : 1;   // column tiles per CTA
     static constexpr int stages = W8 ? (GEO ? SPMM_TC_STAGES8_S : SPMM_TC_STAGES8)
-                                     : (GEO ? SPMM_TC_STAGES_S : SPMM_TC_STAGES_D);
+                                     : (GEO == 2 ? SPMM_TC_STAGES_W
+                                                 : GEO ? SPMM_TC_STAGES_S : SPMM_TC_STAGES_D);
     static constexpr int ent = W8 ? (GEO ? SPMM_TC_ENT8_S : SPMM_TC_ENT8)
-                                  : (GEO ? SPMM_TC_ENT_S : SPMM_TC_ENT_D);   // X slabs
+                                  : (GEO == 1 ? SPMM_TC_ENT_S : SPMM_TC_ENT_D);   // X slabs
     static constexpr int tiles = W8 ? (GEO ? SPMM_TC_TILES8_S : SPMM_TC_TILES8)
-                                    : (GEO ? SPMM_TC_TILES_S : SPMM_TC_TILES_D);
+                                    : (GEO == 1 ? SPMM_TC_TILES_S : SPMM_TC_TILES_D);
     static_assert(stages <= kStagesMax && ent <= 12 && tiles >= 16, "stage geometry");
-    static constexpr int w16 = ent * kSlabBytes;
+    static_assert(GEO != 2 || ent == kJointSlabsG, "wide stages: one joint box per column tile");
+    static constexpr int xset = ent * kSlabBytes;    // X bytes of one column tile
+    static constexpr int w16 = sets * xset;
     static constexpr int w8 = w16 + tiles * kTileBytes16;
     static constexpr int sc = w8 + tiles * kTileBytes8;
     static constexpr int bytes = W8 ? sc + tiles * kScaleBytes : w8;
@@ -216,7 +238,7 @@ struct TcProb {
 // bit 20) gets its X slabs in one TMA box of 4 slabs when X's map is 3-D;
 // the slabs then lie 2048 B apart inside each 64-column half, the halves
 // 8192 B apart.
-constexpr int kJointSlabs = 4;
+constexpr int kJointSlabs = kJointSlabsG;
 constexpr uint32_t kJointBit = 1u << 20;
 
 struct TcBatch {
@@ -273,10 +295,14 @@ __device__ __forceinline__ Unit decode_unit(const TcBatch &B, int64_t u) {
 }
 
 template <typename T, bool W8, int GEO>
-__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+__global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
     tc_kernel(const __grid_constant__ TcBatch B) {
     pdl_enter();
     using G = StageGeom<W8, GEO>;
+    // wide CTAs hold one accumulator set per column tile (all 512 columns)
+    constexpr int kBufs = G::sets > 1 ? 1 : kAccBufs;
+    constexpr int kTmemCols = kBufs * G::sets * kAccCols;
+    static_assert(G::sets == 1 || kAccCols * G::sets <= 512, "TMEM columns");
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *stages = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int kStages = G::stages;
@@ -298,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             mbar_init(&sm->empty[s], 2);   // both MMA warps
             mbar_init(&sm->conv[s], 4);    // E4M3: one arrival per converter warp
         }
-        for (int b = 0; b < kAccBufs; ++b) {
+        for (int b = 0; b < kBufs; ++b) {
             mbar_init(&sm->accf[b], 2);    // MMA completion, both MMA warps
             mbar_init(&sm->acce[b], 128);  // every epilogue thread
         }
@@ -311,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     const int64_t nunits = sm->nunits;
     if (nunits == 0) return;
     if (warp == 1) {
-        tmem_alloc(&sm->tmem_base, kAccBufs * kAccCols);
+        tmem_alloc(&sm->tmem_base, kTmemCols);
     }
     tc_fence_before();
     __syncthreads();
@@ -320,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     if (warp >= 2 && warp < 6) {
         // accumulators start at zero: each epilogue warp clears its lane quarter
         const uint32_t lq = (uint32_t)((warp & 3) * 32) << 16;
-        for (int c = 0; c < kAccBufs * kAccCols; c += 16) tmem_zero16(tmem + lq + c);
+        for (int c = 0; c < kTmemCols; c += 16) tmem_zero16(tmem + lq + c);
         tmem_wait_st();
     }
     tc_fence_before();
@@ -346,7 +372,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             const int32_t *it = P.items + un.item * kItemFields;
             const int32_t e0 = it[1], e1 = it[2];
             if (e0 >= e1) continue;
-            const int n0 = un.t * kNTile;
+            const int n0 = un.t * kNTile * G::sets;
+            // wide: the second column tile, unless it lies wholly past n
+            const bool two = G::sets > 1 && n0 + kNTile < P.n;
             // lane l: word (l & 7) of the record, and (W producer) program word l
             auto ld_rec = [&](int32_t r) -> uint32_t {
                 return r < e1 ? __ldg(P.srec + (int64_t)r * kRecWords + (lane & (kRecWords - 1))) : 0u;
@@ -394,6 +422,26 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                     } else if (lane == 0) {
                         mbar_arrive(&sm->full[stage]);
                     }
+                } else if (G::sets > 1) {
+                    // wide (3-D X map only): producer 1 brings the stage's
+                    // slabs of the first column tile, producer 2 those of the
+                    // second, each as one box of consecutive slabs or one
+                    // box per slab
+                    const bool joint = (info & kJointBit) != 0;
+                    const bool act = pid == 1 || two;
+                    const uint32_t xc = __shfl_sync(0xffffffffu, rc, min(3 + lane, kRecWords - 1));
+                    // (a joint box always lands all kJointSlabs slabs)
+                    if (lane == 0)
+                        mbar_arrive_tx(&sm->full[stage],
+                                       act ? (joint ? kJointSlabs : nent) * kSlabBytes : 0);
+                    __syncwarp();
+                    uint8_t *xs = st + (pid - 1) * G::xset;
+                    const int nh = n0 / (kNTile / 2) + (pid - 1) * 2;
+                    if (act && joint && lane == 0)
+                        tma_load_3d(xs, &B.maps4[un.p], 0, (int)xc * kTile, nh, &sm->full[stage]);
+                    if (act && !joint && lane < nent)
+                        tma_load_3d(xs + lane * kSlabBytes, &B.maps[un.p], 0, (int)xc * kTile, nh,
+                                    &sm->full[stage]);
                 } else if ((info & kJointBit) && P.x3d) {
                     // consecutive columns: X producer 1 requests all slabs in one box
                     if (lane == 0) {
@@ -481,13 +529,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             const Unit un = decode_unit(B, u);
             const int32_t *it = B.prob[un.p].items + un.item * kItemFields;
             const bool has_entries = it[2] > it[1];
-            const int ab = local % kAccBufs;
-            const uint32_t aphase = (local / kAccBufs) & 1;
+            const bool two = G::sets > 1 && (int64_t)un.t * kNTile * G::sets + kNTile < B.prob[un.p].n;
+            const int ab = local % kBufs;
+            const uint32_t aphase = (local / kBufs) & 1;
             int w = 1;
             if (lane == 0) w = mbar_wait(&sm->acce[ab], aphase ^ 1, sm) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, w, 0) != 0;
             tc_fence_after();
-            const uint32_t dbase = tmem + ab * kAccCols;
+            const uint32_t dbase = tmem + ab * G::sets * kAccCols;
             bool last = !has_entries;
             while (ok && !last) {
                 if (lane == 0)
@@ -514,9 +563,14 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                     const uint32_t slab = wd & 15u, toff = (wd >> 4) & 255u;
                     const uint32_t r0 = (wd >> 12) & 15u, len = (wd >> 16) & 31u;
                     // descriptor start addresses are in 16-byte units (bits 0-13)
-                    tc_mma_elect(dbase + r0 * kTile, adesc0 + slab * astep,
-                                 bdesc0 + toff * (kTileBytes16 >> 4),
-                                 idesc0 | ((len * kTile) >> 3) << 17, 1u);
+                    const uint64_t bd = bdesc0 + toff * (kTileBytes16 >> 4);
+                    const uint32_t id = idesc0 | ((len * kTile) >> 3) << 17;
+                    tc_mma_elect(dbase + r0 * kTile, adesc0 + slab * astep, bd, id, 1u);
+                    // wide: the same W tiles against the second column tile's
+                    // slabs, into the second accumulator set
+                    if (G::sets > 1 && two)
+                        tc_mma_elect(dbase + kAccCols + r0 * kTile,
+                                     adesc0 + (G::xset >> 4) + slab * astep, bd, id, 1u);
                 }
                 if (lane == 0) tc_commit(&sm->empty[stage]);
                 __syncwarp();
@@ -608,8 +662,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
                     }
                 }
             }
-            const int ab = local % kAccBufs;
-            const uint32_t aphase = (local / kAccBufs) & 1;
+            const int ab = local % kBufs;
+            const uint32_t aphase = (local / kBufs) & 1;
             // one thread polls the accumulator barrier, sleeping between polls
             // (the mbarrier unit is shared with the copy and MMA pipelines of
             // both CTAs of the SM); the other epilogue threads block on a
@@ -636,43 +690,50 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
             const int32_t g = it[0], slot = it[5];
             const int rows = P.grp_rows[g];
             const int64_t yrow0 = (int64_t)P.grp_row0[g] * kTile;
-            const int64_t col = (int64_t)un.t * kNTile + nl;
-            const bool in = col < P.n;
             const int64_t wrow0 = slot >= 0 ? P.ws_row0[slot] : 0;
             T *Y = (T *)P.Y;
-            // four tile rows (64 accumulator columns) per TMEM load and wait
-            int r = 0;
-            for (; r + 4 <= rows; r += 4) {
-                float v[64];
-                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + ab * kAccCols + r * kTile;
-                tmem_ld64(ta, v);
-                tmem_zero64(ta);
-                if (!in) continue;
-                if (slot >= 0) {
-                    float *dst = P.ws + (wrow0 + r * kTile) * P.n + col;
+            // one pass per column tile of the unit (wide CTAs: two, the second
+            // skipped when it lies wholly past n: its MMAs were never issued)
+            for (int h = 0; h < G::sets; ++h) {
+                const int64_t cbase = ((int64_t)un.t * G::sets + h) * kNTile;
+                if (h > 0 && cbase >= P.n) break;
+                const int64_t col = cbase + nl;
+                const bool in = col < P.n;
+                const uint32_t acc = (uint32_t)((ab * G::sets + h) * kAccCols);
+                // four tile rows (64 accumulator columns) per TMEM load and wait
+                int r = 0;
+                for (; r + 4 <= rows; r += 4) {
+                    float v[64];
+                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + acc + r * kTile;
+                    tmem_ld64(ta, v);
+                    tmem_zero64(ta);
+                    if (!in) continue;
+                    if (slot >= 0) {
+                        float *dst = P.ws + (wrow0 + r * kTile) * P.n + col;
 #pragma unroll
-                    for (int i = 0; i < 64; ++i) dst[i * P.n] = v[i];
-                } else {
-                    T *dst = Y + (yrow0 + r * kTile) * P.ldy + col;
+                        for (int i = 0; i < 64; ++i) dst[i * P.n] = v[i];
+                    } else {
+                        T *dst = Y + (yrow0 + r * kTile) * P.ldy + col;
 #pragma unroll
-                    for (int i = 0; i < 64; ++i) dst[i * P.ldy] = Cvt<T>::f(v[i]);
+                        for (int i = 0; i < 64; ++i) dst[i * P.ldy] = Cvt<T>::f(v[i]);
+                    }
                 }
-            }
-            for (; r < rows; ++r) {
-                float v[16];
-                const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + ab * kAccCols + r * kTile;
-                tmem_ld16(ta, v);
-                tmem_zero16(ta);
-                if (!in) continue;
-                // (staging through shared memory for 16-byte row stores measured slower)
-                if (slot >= 0) {
-                    float *dst = P.ws + (wrow0 + r * kTile) * P.n + col;
+                for (; r < rows; ++r) {
+                    float v[16];
+                    const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + acc + r * kTile;
+                    tmem_ld16(ta, v);
+                    tmem_zero16(ta);
+                    if (!in) continue;
+                    // (staging through shared memory for 16-byte row stores measured slower)
+                    if (slot >= 0) {
+                        float *dst = P.ws + (wrow0 + r * kTile) * P.n + col;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) dst[i * P.n] = v[i];
-                } else {
-                    T *dst = Y + (yrow0 + r * kTile) * P.ldy + col;
+                        for (int i = 0; i < 16; ++i) dst[i * P.n] = v[i];
+                    } else {
+                        T *dst = Y + (yrow0 + r * kTile) * P.ldy + col;
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) dst[i * P.ldy] = Cvt<T>::f(v[i]);
+                        for (int i = 0; i < 16; ++i) dst[i * P.ldy] = Cvt<T>::f(v[i]);
+                    }
                 }
             }
             tmem_wait_st();
@@ -704,7 +765,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(tmem, kAccBufs * kAccCols);
+        tmem_dealloc(tmem, kTmemCols);
     }
 }
 
@@ -959,6 +1020,25 @@ __global__ void quantize_e4m3_kernel(const U *__restrict__ src, int64_t nnzb, in
             (uint8_t)__nv_cvt_float_to_fp8((float)v[e] / scale, __NV_SATFINITE, __NV_E4M3);
 }
 
+// Wide launches (two column tiles per CTA, one CTA per SM, each W tile read
+// once per 256 columns of n): static 16-bit plans of the dense stage
+// geometry over a 3-D X map.  Automatically when the MMAs are wide (at
+// least SPMM_TC_WIDE_TPM tiles per MMA on average: one issuing warp pair
+// then keeps the tensor pipe busy with twice the MMAs, and the halved W
+// traffic pays; with narrower MMAs two CTAs per SM issue faster) and there
+// are enough work units that halving them still fills the SMs.  Measured at
+// m = k = 4096, n = 2048: 8 tiles per MMA 6-9 % faster, 6 even, 4.4-5.2
+// 3 % slower.
+bool use_wide(const spmm_plan *p, int64_t n, int x3d) {
+    if (p->col_tiles == 1 || p->mode != SPMM_STATIC || p->wdt == SPMM_E4M3 || p->tc_geo != 0 ||
+        !x3d || n <= kNTile)
+        return false;
+    if (p->col_tiles == 2) return true;
+    const int64_t units = p->n_items * ((n + kNTile - 1) / kNTile);
+    return p->n_tiles >= (int64_t)SPMM_TC_WIDE_TPM * p->hp.n_mma &&
+           2 * units >= (int64_t)SPMM_TC_WIDE_MIN * p->sm_count;
+}
+
 void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, int x3d) {
     P.items = p->d_items;
     P.grp_row0 = p->d_grp_row0;
@@ -982,12 +1062,12 @@ void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, i
 template <typename T, bool W8, int GEO>
 cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
     if (B.total_units == 0) return cudaSuccess;
-    const int64_t slots = (int64_t)sm_count * kCtasPerSm;
+    const int64_t slots = (int64_t)sm_count * (GEO == 2 ? 1 : kCtasPerSm);
     const int grid = (int)(B.total_units < slots ? B.total_units : slots);
     using G = StageGeom<W8, GEO>;
     const size_t smem = 1024 + (size_t)G::stages * G::bytes + sizeof(Smem);
     static std::atomic<uint64_t> attrs{0};
-    const cudaError_t e = set_smem_attrs_once(attrs, tc_kernel<T, W8, GEO>, (int)smem, false);
+    const cudaError_t e = set_smem_attrs_once(attrs, tc_kernel<T, W8, GEO>, (int)smem, GEO == 2);
     if (e != cudaSuccess) return e;
     pdl_launch(tc_kernel<T, W8, GEO>, dim3(grid), dim3(kThreads), smem, s, B);
     return cudaGetLastError();
@@ -996,6 +1076,7 @@ cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
 template <typename T>
 cudaError_t launch_geo(const TcBatch &B, int geo, bool w8, int sm_count, cudaStream_t s) {
     if (w8) return geo ? launch_batch<T, true, 1>(B, sm_count, s) : launch_batch<T, true, 0>(B, sm_count, s);
+    if (geo == 2) return launch_batch<T, false, 2>(B, sm_count, s);
     return geo ? launch_batch<T, false, 1>(B, sm_count, s) : launch_batch<T, false, 0>(B, sm_count, s);
 }
 cudaError_t dispatch_batch(const TcBatch &B, int geo, bool bf16, bool w8, int sm_count,
@@ -1034,6 +1115,8 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
     B.units = nullptr;
     B.status = p->d_status;
     const bool dyn = p->mode == SPMM_DYNAMIC;
+    const bool wide = use_wide(p, n, x3d);
+    if (wide) B.prob[0].ntn = (B.prob[0].ntn + 1) / 2;   // units of two column tiles
     B.n_items_dev = dyn ? p->d_counts + kCntItems : nullptr;
     B.total_units = (dyn ? p->dyn.items_cap : p->n_items) * B.prob[0].ntn;
     if (dyn) {
@@ -1041,7 +1124,8 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
         e = launch_stage_build(p, s);
         if (e != cudaSuccess) return e;
     }
-    return dispatch_batch(B, p->tc_geo, p->xdt == SPMM_BF16, p->wdt == SPMM_E4M3, p->sm_count, s);
+    return dispatch_batch(B, wide ? 2 : p->tc_geo, p->xdt == SPMM_BF16, p->wdt == SPMM_E4M3,
+                          p->sm_count, s);
 }
 
 namespace {

@@ -56,6 +56,7 @@ struct HostPlan {
     // tensor-core tile structure
     std::vector<int32_t> grp_row0, grp_rows, grp_ebeg, ent_col, ent_tbeg, ent_cover, tile_row,
         blk_slot, blk_off;
+    int64_t n_mma = 0;  // MMAs of all entries (intervals split at tile row 8)
 };
 
 // Validates shape and pattern; returns SPMM_OK, SPMM_ERR_SHAPE or SPMM_ERR_PATTERN.
@@ -98,6 +99,7 @@ struct spmm_plan {
             *d_blk_off = nullptr, *d_grp_ebeg = nullptr;
     uint32_t *d_srec = nullptr, *d_sprog = nullptr;  // TC: stage records and MMA programs
     int tc_geo = 0;                // TC stage geometry: 0 dense tiles, 1 sparse tiles
+    int col_tiles = 0;             // TC: column tiles per CTA, 0 automatic (launch-time choice)
     bool transposed = false;       // applies W^T: values arrive as W's blocks, packed transposed
     int32_t *d_sd_items = nullptr; // b = 16: SDDMM work items (count, then (row, e0, e1) triples)
     int64_t sd_items_cap = 0;

@@ -72,6 +72,10 @@ def test_errors():
     with pytest.raises(S.SpmmError) as e:
         _plan(24, 24, 4, [0], [0], kernel="tc")     # m, k not multiples of 16
     assert e.value.status == S.ERR_UNSUPPORTED
+    for bad in (-1, 3):
+        with pytest.raises(S.SpmmError) as e:
+            _plan(16, 16, 4, [0], [0], col_tiles=bad)
+        assert e.value.status == S.ERR_ARG
     p = _plan(16, 16, 4, [], [])
     assert p.info()["nnzb"] == 0
     # the sampled product refuses host-only plans before touching the device

@@ -257,3 +257,49 @@ def test_both_stage_geometries(b, d, n, geo):
     assert info["stage_geometry"] == geo
     assert not torch.isnan(Y).any()
     assert err <= 4e-3, err
+
+
+@pytest.mark.parametrize("b,d,n", [(1, 1 / 4, 192), (1, 1 / 8, 256), (8, 1 / 4, 320),
+                                   (4, 1 / 4, 640), (1, 1 / 4, 384), (8, 1 / 4, 200)])
+@pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16])
+def test_two_column_tiles_per_cta(b, d, n, dt):
+    """Dense-tile plans whose CTAs cover two 128-column tiles of n (the two
+    share each stage's W tiles; the second tile's slabs and accumulators are
+    separate).  n = 192: the second tile is partly past n; 320 and 640: the
+    last CTA has one tile only; 200: not a multiple of 64, so the launch
+    keeps one tile per CTA.  Within the bound against the oracle, and bit
+    for bit equal to one tile per CTA (every accumulator column sees the same
+    MMAs in the same order)."""
+    m, k = 1024, 1024
+    nnzb = wl.nnzb_for(m, k, b, d)
+    err, Y2, _, plan = run_case(m, k, n, b, nnzb, dt, "tc", seed=5 * b + n,
+                                ldx=((n + 7) // 8) * 8, rows_per_group=16, col_tiles=2)
+    assert plan.info()["stage_geometry"] == 0
+    assert not torch.isnan(Y2).any()
+    assert err <= TOL[dt], err
+    _, Y1, _, _ = run_case(m, k, n, b, nnzb, dt, "tc", seed=5 * b + n,
+                           ldx=((n + 7) // 8) * 8, rows_per_group=16, col_tiles=1)
+    assert torch.equal(Y1, Y2)
+
+
+def test_two_column_tiles_split_rows():
+    """Two column tiles per CTA with rows split across work items (partials
+    through the FP32 workspace and the reduction)."""
+    m, k, n, b = 512, 4096, 384, 1
+    err, Y, _, plan = run_case(m, k, n, b, wl.nnzb_for(m, k, b, 1 / 4), torch.float16, "tc",
+                               seed=77, rows_per_group=16, max_per_item=32, col_tiles=2)
+    info = plan.info()
+    assert info["stage_geometry"] == 0 and info["n_reductions"] > 0
+    assert err <= 4e-3, err
+
+
+def test_two_column_tiles_integers_bit_exact():
+    m, k, n, b = 256, 512, 256, 1
+    brow, bcol, vals, X = _int_case(m, k, n, b, (m // b) * (k // b) // 4, seed=99)
+    plan = S.Plan(m, k, n, b, w_dtype=S.F16, brow=brow, bcol=bcol, kernel="tc",
+                  rows_per_group=16, col_tiles=2)
+    assert plan.info()["stage_geometry"] == 0
+    plan.pack(torch.from_numpy(vals).half().cuda())
+    Y = plan.run(torch.from_numpy(X).half().cuda()).cpu()
+    Yo = oracle.spmm(m, k, b, brow, bcol, vals, X)
+    assert torch.equal(Y, torch.from_numpy(Yo).half())
