@@ -93,6 +93,12 @@ namespace {
 #ifndef SPMM_TC_STAGES_W
 #define SPMM_TC_STAGES_W 3  // dense, two column tiles per CTA: 2 x 4 slabs, 64 tiles
 #endif
+#ifndef SPMM_TC_ENT_W
+#define SPMM_TC_ENT_W 4
+#endif
+#ifndef SPMM_TC_TILES_W
+#define SPMM_TC_TILES_W 64
+#endif
 #ifndef SPMM_TC_WIDE_MIN
 #define SPMM_TC_WIDE_MIN 3  // wide launches need work units >= this x SMs / 2
 #endif
@@ -129,7 +135,7 @@ namespace {
 constexpr int kSlabBytes = kTile * kNTile * 2;                    // 4096: 16 k x 128 n, 16-bit
 constexpr int kTileBytes8 = kTile * kTile;                        // 256: E4M3 tile, row-major
 constexpr int kScaleBytes = 16 * 4;                               // per slot: 4 x 4 sub-square scales
-constexpr int kStagesMax = 4;                                     // >= every geometry's stages
+constexpr int kStagesMax = 8;                                     // >= every geometry's stages
 constexpr int kRowCap = SPMM_TC_RCAP;
 constexpr int kAccCols = kRowCap * kTile;                         // TMEM columns per buffer
 constexpr int kMaxBatch = 64;                                     // problems per launch
@@ -148,11 +154,17 @@ template <bool W8, int GEO> struct StageGeom {
                                      : (GEO == 2 ? SPMM_TC_STAGES_W
                                                  : GEO ? SPMM_TC_STAGES_S : SPMM_TC_STAGES_D);
     static constexpr int ent = W8 ? (GEO ? SPMM_TC_ENT8_S : SPMM_TC_ENT8)
-                                  : (GEO == 1 ? SPMM_TC_ENT_S : SPMM_TC_ENT_D);   // X slabs
+                                  : (GEO == 2 ? SPMM_TC_ENT_W
+                                              : GEO == 1 ? SPMM_TC_ENT_S : SPMM_TC_ENT_D);   // X slabs
     static constexpr int tiles = W8 ? (GEO ? SPMM_TC_TILES8_S : SPMM_TC_TILES8)
-                                    : (GEO == 1 ? SPMM_TC_TILES_S : SPMM_TC_TILES_D);
+                                    : (GEO == 2 ? SPMM_TC_TILES_W
+                                                : GEO == 1 ? SPMM_TC_TILES_S : SPMM_TC_TILES_D);
     static_assert(stages <= kStagesMax && ent <= 12 && tiles >= 16, "stage geometry");
-    static_assert(GEO != 2 || ent == kJointSlabsG, "wide stages: one joint box per column tile");
+    // wide stages load each column tile's consecutive slabs as one box of
+    // `ent` slabs (the stage builder marks runs of 2-4 consecutive columns)
+    static_assert(GEO != 2 || (ent >= 2 && ent <= kJointSlabsG), "wide stage entries");
+    // slab and box destinations stay on 1024-byte (128-byte swizzle) boundaries
+    static_assert((ent * 4096) % 1024 == 0, "stage alignment");
     static constexpr int xset = ent * kSlabBytes;    // X bytes of one column tile
     static constexpr int w16 = sets * xset;
     static constexpr int w8 = w16 + tiles * kTileBytes16;
@@ -194,9 +206,10 @@ struct StageMeta {
     uint32_t prog[2][kMmaStage];   // MMA words of rows 0-7 and of rows 8-15
 };
 
-struct __align__(8) Smem {
-    uint64_t full[kStagesMax], empty[kStagesMax], conv[kStagesMax], accf[kAccBufs], acce[kAccBufs];
-    StageMeta meta[kStagesMax];
+// Control block after the stages; S = the geometry's stage count.
+template <int S> struct __align__(8) SmemT {
+    uint64_t full[S], empty[S], conv[S], accf[kAccBufs], acce[kAccBufs];
+    StageMeta meta[S];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
     int32_t issued[kProducers], consumed[2];   // per producer / per MMA warp
@@ -207,7 +220,8 @@ struct __align__(8) Smem {
 // ------------------------------------------------------------ PTX helpers
 // (generic ones in tc_ptx.cuh)
 // Bounded wait: false after kWaitNs or once another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, Smem *sm) {
+template <class SM>
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, SM *sm) {
     return mbar_wait_bounded(b, parity, &sm->abort_flag, kWaitNs);
 }
 
@@ -263,8 +277,9 @@ __device__ __forceinline__ void record(int32_t *status, int32_t code) {
 // groups 1024 B apart (stride offset).
 __device__ __forceinline__ uint64_t a_desc(uint32_t addr) { return smem_desc(addr, 2048, 1024, 2); }
 // The same for a stage loaded as one box of kJointSlabs slabs.
-__device__ __forceinline__ uint64_t a_desc_joint(uint32_t addr) {
-    return smem_desc(addr, kJointSlabs * 2048, 1024, 2);
+// (wide stages: boxes of the geometry's entry count)
+__device__ __forceinline__ uint64_t a_desc_joint(uint32_t addr, int slabs = kJointSlabs) {
+    return smem_desc(addr, (uint32_t)slabs * 2048, 1024, 2);
 }
 // B-operand descriptor: one W tile, K-major, no swizzle; 8 x 8 core matrices,
 // k-adjacent ones 128 B apart (leading), row-adjacent ones 256 B (stride).
@@ -306,6 +321,7 @@ __global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *stages = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int kStages = G::stages;
+    using Smem = SmemT<kStages>;
     Smem *sm = (Smem *)(stages + kStages * G::bytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -430,10 +446,11 @@ __global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
                     const bool joint = (info & kJointBit) != 0;
                     const bool act = pid == 1 || two;
                     const uint32_t xc = __shfl_sync(0xffffffffu, rc, min(3 + lane, kRecWords - 1));
-                    // (a joint box always lands all kJointSlabs slabs)
+                    // (a joint box, encoded for this geometry, always lands
+                    // G::ent slabs)
                     if (lane == 0)
                         mbar_arrive_tx(&sm->full[stage],
-                                       act ? (joint ? kJointSlabs : nent) * kSlabBytes : 0);
+                                       act ? (joint ? G::ent : nent) * kSlabBytes : 0);
                     __syncwarp();
                     uint8_t *xs = st + (pid - 1) * G::xset;
                     const int nh = n0 / (kNTile / 2) + (pid - 1) * 2;
@@ -555,7 +572,8 @@ __global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
                 const uint32_t myword = sm->meta[stage].prog[half][lane];   // words >= nmma unused
                 const uint32_t sbase = smem_u32(stages + stage * G::bytes);
                 const bool joint = (info & kJointBit) && B.prob[un.p].x3d;
-                const uint64_t adesc0 = joint ? a_desc_joint(sbase) : a_desc(sbase);
+                const uint64_t adesc0 =
+                    joint ? a_desc_joint(sbase, G::sets > 1 ? G::ent : kJointSlabs) : a_desc(sbase);
                 const uint32_t astep = joint ? (kSlabBytes / 2) >> 4 : kSlabBytes >> 4;
                 const uint64_t bdesc0 = b_desc(sbase + G::w16);
                 for (int i = 0; i < nmma; ++i) {
@@ -1029,14 +1047,20 @@ __global__ void quantize_e4m3_kernel(const U *__restrict__ src, int64_t nnzb, in
 // are enough work units that halving them still fills the SMs.  Measured at
 // m = k = 4096, n = 2048: 8 tiles per MMA 6-9 % faster, 6 even, 4.4-5.2
 // 3 % slower.
-bool use_wide(const spmm_plan *p, int64_t n, int x3d) {
+// (The 3-D X map, n a multiple of 64, is checked per launch; the rest holds
+// for every n up to n if it holds for n, so a plan builds the wide stage
+// records at creation only when it can go wide at n_max.)
+bool wide_rule(const spmm_plan *p, int64_t n) {
     if (p->col_tiles == 1 || p->mode != SPMM_STATIC || p->wdt == SPMM_E4M3 || p->tc_geo != 0 ||
-        !x3d || n <= kNTile)
+        n <= kNTile)
         return false;
     if (p->col_tiles == 2) return true;
     const int64_t units = p->n_items * ((n + kNTile - 1) / kNTile);
     return p->n_tiles >= (int64_t)SPMM_TC_WIDE_TPM * p->hp.n_mma &&
            2 * units >= (int64_t)SPMM_TC_WIDE_MIN * p->sm_count;
+}
+bool use_wide(const spmm_plan *p, int64_t n, int x3d) {
+    return x3d && p->d_srec_w && wide_rule(p, n);
 }
 
 void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, int x3d) {
@@ -1065,7 +1089,7 @@ cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
     const int64_t slots = (int64_t)sm_count * (GEO == 2 ? 1 : kCtasPerSm);
     const int grid = (int)(B.total_units < slots ? B.total_units : slots);
     using G = StageGeom<W8, GEO>;
-    const size_t smem = 1024 + (size_t)G::stages * G::bytes + sizeof(Smem);
+    const size_t smem = 1024 + (size_t)G::stages * G::bytes + sizeof(SmemT<G::stages>);
     static std::atomic<uint64_t> attrs{0};
     const cudaError_t e = set_smem_attrs_once(attrs, tc_kernel<T, W8, GEO>, (int)smem, GEO == 2);
     if (e != cudaSuccess) return e;
@@ -1106,8 +1130,11 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
     TcBatch B;  // the launch parameter (copied at launch)
     int x3d = 0;
     cudaError_t e = encode_x(&B.maps[0], &x3d, p->xdt == SPMM_BF16, X, p->k, n, ldx);
-    if (e == cudaSuccess)
-        e = encode_x(&B.maps4[0], &x3d, p->xdt == SPMM_BF16, X, p->k, n, ldx, kJointSlabs);
+    if (e != cudaSuccess) return e;
+    const bool wide = use_wide(p, n, x3d);
+    // joint boxes: kJointSlabs slabs, or the wide geometry's entries per stage
+    e = encode_x(&B.maps4[0], &x3d, p->xdt == SPMM_BF16, X, p->k, n, ldx,
+                 wide ? StageGeom<false, 2>::ent : kJointSlabs);
     if (e != cudaSuccess) return e;
     fill_prob(B.prob[0], p, Y, n, ldy, x3d);
     B.prob[0].unit_base = 0;
@@ -1115,8 +1142,11 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
     B.units = nullptr;
     B.status = p->d_status;
     const bool dyn = p->mode == SPMM_DYNAMIC;
-    const bool wide = use_wide(p, n, x3d);
-    if (wide) B.prob[0].ntn = (B.prob[0].ntn + 1) / 2;   // units of two column tiles
+    if (wide) {
+        B.prob[0].ntn = (B.prob[0].ntn + 1) / 2;   // units of two column tiles
+        B.prob[0].srec = p->d_srec_w;              // stages cut for the wide geometry
+        B.prob[0].sprog = p->d_sprog_w;
+    }
     B.n_items_dev = dyn ? p->d_counts + kCntItems : nullptr;
     B.total_units = (dyn ? p->dyn.items_cap : p->n_items) * B.prob[0].ntn;
     if (dyn) {
@@ -1241,20 +1271,27 @@ cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *cons
 }
 }  // namespace
 
-cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s) {
+cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s, bool wide) {
     const bool dyn = p->mode == SPMM_DYNAMIC;
     const int64_t ni = dyn ? p->dyn.items_cap : p->n_items;
-    if (ni == 0 || !p->d_srec) return cudaSuccess;
+    uint32_t *srec = wide ? p->d_srec_w : p->d_srec, *sprog = wide ? p->d_sprog_w : p->d_sprog;
+    if (ni == 0 || !srec) return cudaSuccess;
     const bool w8 = p->wdt == SPMM_E4M3;
-    const int tiles_cap = w8 ? (p->tc_geo ? StageGeom<true, 1>::tiles : StageGeom<true, 0>::tiles)
-                             : (p->tc_geo ? StageGeom<false, 1>::tiles : StageGeom<false, 0>::tiles);
-    const int ent_cap = w8 ? (p->tc_geo ? StageGeom<true, 1>::ent : StageGeom<true, 0>::ent)
-                           : (p->tc_geo ? StageGeom<false, 1>::ent : StageGeom<false, 0>::ent);
+    int tiles_cap = w8 ? (p->tc_geo ? StageGeom<true, 1>::tiles : StageGeom<true, 0>::tiles)
+                       : (p->tc_geo ? StageGeom<false, 1>::tiles : StageGeom<false, 0>::tiles);
+    int ent_cap = w8 ? (p->tc_geo ? StageGeom<true, 1>::ent : StageGeom<true, 0>::ent)
+                     : (p->tc_geo ? StageGeom<false, 1>::ent : StageGeom<false, 0>::ent);
+    if (wide) {
+        tiles_cap = StageGeom<false, 2>::tiles;
+        ent_cap = StageGeom<false, 2>::ent;
+    }
     pdl_launch(stage_build_kernel, dim3((unsigned)ni), dim3(kBuildWarps * 32), 0, s, p->d_items, ni,
         dyn ? p->d_counts + kCntItems : nullptr, p->d_status, p->d_ent_col, p->d_ent_tbeg,
-        p->d_ent_cover, ent_cap, tiles_cap, p->d_srec, p->d_sprog);
+        p->d_ent_cover, ent_cap, tiles_cap, srec, sprog);
     return cudaGetLastError();
 }
+
+bool tc_wide_possible(const spmm_plan *p) { return wide_rule(p, p->n_max); }
 
 int64_t stage_record_words() { return kRecWords; }
 int tc_geometry(double tiles_per_entry) { return tiles_per_entry >= 8.0 ? 0 : 1; }
