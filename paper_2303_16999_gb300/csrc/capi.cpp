@@ -497,10 +497,15 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
             // and those of the wide geometry where a launch may take it
             e = launch_stage_build(p, 0);
             if (e == cudaSuccess && tc_wide_possible(p)) {
-                const int64_t E = std::max<int64_t>((int64_t)p->hp.ent_col.size(), 1);
-                e = dalloc(p, &p->d_srec_w, E * stage_record_words());
-                if (e == cudaSuccess) e = dalloc(p, &p->d_sprog_w, E * stage_prog_words());
-                if (e == cudaSuccess) e = launch_stage_build(p, 0, true);
+                if (tc_wide_shares_records()) {
+                    p->d_srec_w = p->d_srec;
+                    p->d_sprog_w = p->d_sprog;
+                } else {
+                    const int64_t E = std::max<int64_t>((int64_t)p->hp.ent_col.size(), 1);
+                    e = dalloc(p, &p->d_srec_w, E * stage_record_words());
+                    if (e == cudaSuccess) e = dalloc(p, &p->d_sprog_w, E * stage_prog_words());
+                    if (e == cudaSuccess) e = launch_stage_build(p, 0, true);
+                }
             }
             if (e == cudaSuccess) e = cudaStreamSynchronize(0);
         }

@@ -90,8 +90,13 @@ namespace {
 #ifndef SPMM_TC_TILES_D
 #define SPMM_TC_TILES_D 64
 #endif
+// Two column tiles per CTA (one CTA per SM): 2 x 4 slabs and 64 tiles in
+// each of 3 stages.  Measured at b = 1 against smaller stages in the same
+// shared memory: 2 x 3 slabs, 48 tiles, 4 stages 65 us; 2 x 2 slabs, 32
+// tiles, 6 stages 80 us; this one 59 us (each stage's fixed costs, not the
+// bytes in flight, set the pace).
 #ifndef SPMM_TC_STAGES_W
-#define SPMM_TC_STAGES_W 3  // dense, two column tiles per CTA: 2 x 4 slabs, 64 tiles
+#define SPMM_TC_STAGES_W 3
 #endif
 #ifndef SPMM_TC_ENT_W
 #define SPMM_TC_ENT_W 4
@@ -1292,6 +1297,10 @@ cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s, bool wide) {
 }
 
 bool tc_wide_possible(const spmm_plan *p) { return wide_rule(p, p->n_max); }
+bool tc_wide_shares_records() {
+    return StageGeom<false, 2>::ent == StageGeom<false, 0>::ent &&
+           StageGeom<false, 2>::tiles == StageGeom<false, 0>::tiles;
+}
 
 int64_t stage_record_words() { return kRecWords; }
 int tc_geometry(double tiles_per_entry) { return tiles_per_entry >= 8.0 ? 0 : 1; }

@@ -146,6 +146,8 @@ cudaError_t launch_restride(const void *src, void *dst, int64_t rows, int64_t n,
 cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s, bool wide = false);
 // whether a static plan may launch with two column tiles per CTA at some n <= n_max
 bool tc_wide_possible(const spmm_plan *p);
+// whether the wide geometry cuts stages exactly as the dense one (same caps)
+bool tc_wide_shares_records();
 int64_t stage_record_words();
 // TC stage geometry for a plan whose entries hold this many tiles on average
 int tc_geometry(double tiles_per_entry);
