@@ -493,20 +493,8 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
         }
         if (st == SPMM_OK && e == cudaSuccess && kernel == SPMM_KERNEL_TC &&
             p->mode == SPMM_STATIC) {
-            // the static plan's stage records, once (dynamic plans: every call),
-            // and those of the wide geometry where a launch may take it
+            // the static plan's stage records, once (dynamic plans: every call)
             e = launch_stage_build(p, 0);
-            if (e == cudaSuccess && tc_wide_possible(p)) {
-                if (tc_wide_shares_records()) {
-                    p->d_srec_w = p->d_srec;
-                    p->d_sprog_w = p->d_sprog;
-                } else {
-                    const int64_t E = std::max<int64_t>((int64_t)p->hp.ent_col.size(), 1);
-                    e = dalloc(p, &p->d_srec_w, E * stage_record_words());
-                    if (e == cudaSuccess) e = dalloc(p, &p->d_sprog_w, E * stage_prog_words());
-                    if (e == cudaSuccess) e = launch_stage_build(p, 0, true);
-                }
-            }
             if (e == cudaSuccess) e = cudaStreamSynchronize(0);
         }
         if (st == SPMM_OK && e != cudaSuccess) st = cuda_fail(e, "plan allocation");

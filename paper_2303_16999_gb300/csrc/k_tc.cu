@@ -90,19 +90,16 @@ namespace {
 #ifndef SPMM_TC_TILES_D
 #define SPMM_TC_TILES_D 64
 #endif
-// Two column tiles per CTA (one CTA per SM): 2 x 4 slabs and 64 tiles in
-// each of 3 stages.  Measured at b = 1 against smaller stages in the same
-// shared memory: 2 x 3 slabs, 48 tiles, 4 stages 65 us; 2 x 2 slabs, 32
-// tiles, 6 stages 80 us; this one 59 us (each stage's fixed costs, not the
-// bytes in flight, set the pace).
+// Two column tiles per CTA (one CTA per SM), dense tiles: 2 x 4 slabs and
+// 64 tiles in each of 3 stages.  Measured at b = 1 against smaller stages
+// in the same shared memory: 2 x 3 slabs, 48 tiles, 4 stages 65 us; 2 x 2
+// slabs, 32 tiles, 6 stages 80 us; this one 59 us (each stage's fixed
+// costs, not the bytes in flight, set the pace).
 #ifndef SPMM_TC_STAGES_W
 #define SPMM_TC_STAGES_W 3
 #endif
-#ifndef SPMM_TC_ENT_W
-#define SPMM_TC_ENT_W 4
-#endif
-#ifndef SPMM_TC_TILES_W
-#define SPMM_TC_TILES_W 64
+#ifndef SPMM_TC_STAGES_WS
+#define SPMM_TC_STAGES_WS 2  // sparse tiles, two column tiles: 2 x 8 slabs, 44 tiles
 #endif
 #ifndef SPMM_TC_WIDE_MIN
 #define SPMM_TC_WIDE_MIN 3  // wide launches need work units >= this x SMs / 2
@@ -149,27 +146,27 @@ constexpr int kJointSlabsG = 4;                                   // slabs of a 
 // Stage layout: X slabs (of each column tile the CTA covers) | 16-bit W
 // tiles (MMA B operand) | (E4M3 only) the FP8 codes and their scales as
 // loaded, which the converter warps expand into the 16-bit area.
-// GEO: 0 = dense, 1 = sparse, 2 = dense over two column tiles per CTA
-// ("wide": one CTA per SM, each W tile serves 256 columns of n; the same
-// stage records as GEO 0, since the entry and tile caps are the same).
+// GEO: 0 = dense, 1 = sparse; 2 and 3 = the same over two column tiles per
+// CTA ("wide": one CTA per SM, each W tile serves 256 columns of n; the
+// same entry and tile caps, hence the same stage records, as GEO - 2).
 template <bool W8, int GEO> struct StageGeom {
-    static_assert(GEO != 2 || !W8, "wide stages take 16-bit weights only");
-    static constexpr int sets = GEO == 2 ? 2 : 1;   // column tiles per CTA
+    static_assert(GEO < 2 || !W8, "wide stages take 16-bit weights only");
+    static constexpr int base = GEO & 1;            // dense (0) or sparse (1) tiles
+    static constexpr int sets = GEO >= 2 ? 2 : 1;   // column tiles per CTA
+    static constexpr int threads = sets > 1 ? 352 : 288;
+    static constexpr int mma_warps = 2 * sets;      // one per row half and column tile
     static constexpr int stages = W8 ? (GEO ? SPMM_TC_STAGES8_S : SPMM_TC_STAGES8)
-                                     : (GEO == 2 ? SPMM_TC_STAGES_W
-                                                 : GEO ? SPMM_TC_STAGES_S : SPMM_TC_STAGES_D);
+                                     : GEO == 3   ? SPMM_TC_STAGES_WS
+                                       : GEO == 2 ? SPMM_TC_STAGES_W
+                                       : GEO      ? SPMM_TC_STAGES_S
+                                                  : SPMM_TC_STAGES_D;
     static constexpr int ent = W8 ? (GEO ? SPMM_TC_ENT8_S : SPMM_TC_ENT8)
-                                  : (GEO == 2 ? SPMM_TC_ENT_W
-                                              : GEO == 1 ? SPMM_TC_ENT_S : SPMM_TC_ENT_D);   // X slabs
+                                  : (base ? SPMM_TC_ENT_S : SPMM_TC_ENT_D);   // X slabs
     static constexpr int tiles = W8 ? (GEO ? SPMM_TC_TILES8_S : SPMM_TC_TILES8)
-                                    : (GEO == 2 ? SPMM_TC_TILES_W
-                                                : GEO == 1 ? SPMM_TC_TILES_S : SPMM_TC_TILES_D);
+                                    : (base ? SPMM_TC_TILES_S : SPMM_TC_TILES_D);
     static_assert(stages <= kStagesMax && ent <= 12 && tiles >= 16, "stage geometry");
-    // wide stages load each column tile's consecutive slabs as one box of
-    // `ent` slabs (the stage builder marks runs of 2-4 consecutive columns)
-    static_assert(GEO != 2 || (ent >= 2 && ent <= kJointSlabsG), "wide stage entries");
-    // slab and box destinations stay on 1024-byte (128-byte swizzle) boundaries
-    static_assert((ent * 4096) % 1024 == 0, "stage alignment");
+    // a joint box of consecutive slabs must fit one column tile's slab area
+    static_assert(sets == 1 || ent >= kJointSlabsG, "wide stage entries");
     static constexpr int xset = ent * kSlabBytes;    // X bytes of one column tile
     static constexpr int w16 = sets * xset;
     static constexpr int w8 = w16 + tiles * kTileBytes16;
@@ -185,7 +182,8 @@ constexpr int kAccBufs = SPMM_TC_ACCBUFS;
 static_assert(kAccBufs * SPMM_TC_CTAS * SPMM_TC_RCAP * 16 <= 512, "TMEM columns per SM");
 constexpr int kCtasPerSm = SPMM_TC_CTAS;
 static_assert(kRowCap <= kMaxGroupRows && kRowCap <= 16, "a stage must hold a full entry");
-constexpr int kThreads = 288;
+constexpr int kThreads = 288;                                     // one column tile per CTA
+constexpr int kMmaWarpsMax = 4;
 constexpr int kXWarp0 = 6, kXWarp1 = 7;                           // X-slab producers (two halves)
 constexpr int kMmaWarpHi = 8;                                     // MMAs of tile rows 8-15
 constexpr int kProducers = 3;                                     // W + two X
@@ -217,7 +215,7 @@ template <int S> struct __align__(8) SmemT {
     StageMeta meta[S];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
-    int32_t issued[kProducers], consumed[2];   // per producer / per MMA warp
+    int32_t issued[kProducers], consumed[kMmaWarpsMax];   // per producer / per MMA warp
     int64_t nunits;
     int32_t epi_ok[2];             // accumulator-ready outcome, per unit parity
 };
@@ -282,9 +280,8 @@ __device__ __forceinline__ void record(int32_t *status, int32_t code) {
 // groups 1024 B apart (stride offset).
 __device__ __forceinline__ uint64_t a_desc(uint32_t addr) { return smem_desc(addr, 2048, 1024, 2); }
 // The same for a stage loaded as one box of kJointSlabs slabs.
-// (wide stages: boxes of the geometry's entry count)
-__device__ __forceinline__ uint64_t a_desc_joint(uint32_t addr, int slabs = kJointSlabs) {
-    return smem_desc(addr, (uint32_t)slabs * 2048, 1024, 2);
+__device__ __forceinline__ uint64_t a_desc_joint(uint32_t addr) {
+    return smem_desc(addr, kJointSlabs * 2048, 1024, 2);
 }
 // B-operand descriptor: one W tile, K-major, no swizzle; 8 x 8 core matrices,
 // k-adjacent ones 128 B apart (leading), row-adjacent ones 256 B (stride).
@@ -315,7 +312,7 @@ __device__ __forceinline__ Unit decode_unit(const TcBatch &B, int64_t u) {
 }
 
 template <typename T, bool W8, int GEO>
-__global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
+__global__ void __launch_bounds__(GEO >= 2 ? 352 : kThreads, GEO >= 2 ? 1 : kCtasPerSm)
     tc_kernel(const __grid_constant__ TcBatch B) {
     pdl_enter();
     using G = StageGeom<W8, GEO>;
@@ -342,16 +339,16 @@ __global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
         sm->nunits = nu;
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&sm->full[s], kProducers);
-            mbar_init(&sm->empty[s], 2);   // both MMA warps
+            mbar_init(&sm->empty[s], G::mma_warps);   // every MMA warp
             mbar_init(&sm->conv[s], 4);    // E4M3: one arrival per converter warp
         }
         for (int b = 0; b < kBufs; ++b) {
-            mbar_init(&sm->accf[b], 2);    // MMA completion, both MMA warps
+            mbar_init(&sm->accf[b], G::mma_warps);    // MMA completion, every MMA warp
             mbar_init(&sm->acce[b], 128);  // every epilogue thread
         }
         sm->abort_flag = 0;
         for (int i = 0; i < kProducers; ++i) sm->issued[i] = 0;
-        sm->consumed[0] = sm->consumed[1] = 0;
+        for (int i = 0; i < kMmaWarpsMax; ++i) sm->consumed[i] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -451,11 +448,10 @@ __global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
                     const bool joint = (info & kJointBit) != 0;
                     const bool act = pid == 1 || two;
                     const uint32_t xc = __shfl_sync(0xffffffffu, rc, min(3 + lane, kRecWords - 1));
-                    // (a joint box, encoded for this geometry, always lands
-                    // G::ent slabs)
+                    // (a joint box always lands all kJointSlabs slabs)
                     if (lane == 0)
                         mbar_arrive_tx(&sm->full[stage],
-                                       act ? (joint ? G::ent : nent) * kSlabBytes : 0);
+                                       act ? (joint ? kJointSlabs : nent) * kSlabBytes : 0);
                     __syncwarp();
                     uint8_t *xs = st + (pid - 1) * G::xset;
                     const int nh = n0 / (kNTile / 2) + (pid - 1) * 2;
@@ -538,9 +534,13 @@ __global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
             sm->abort_flag = 1;
         }
         if (lane == 0) sm->issued[pid] = issued;
-    } else if (warp == 1 || warp == kMmaWarpHi) {
+    } else if (warp == 1 || warp == kMmaWarpHi || warp > kMmaWarpHi) {
         // ------------------------------- MMA issuers (converged warps)
-        const int half = warp == 1 ? 0 : 1;   // tile rows 0-7 / 8-15
+        // warps 1 / 8: tile rows 0-7 / 8-15 of the first column tile; wide
+        // CTAs: warps 9 / 10 the same rows of the second column tile
+        const int mw = warp == 1 ? 0 : warp - kMmaWarpHi + 1;   // 0..3
+        const int half = mw & 1;              // tile rows 0-7 / 8-15
+        const int tset = mw >> 1;             // column tile
         constexpr uint32_t idesc0 = make_idesc(Cvt<T>::fmt, kNTile, 0);
         int stage = 0;
         uint32_t phase = 0;
@@ -572,13 +572,13 @@ __global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
                 ++consumed;
                 // every lane reads the stage header and one program word
                 const uint32_t info = sm->meta[stage].info;
-                const int nmma = (int)((info >> (6 * half)) & 63u);
+                // (a second column tile wholly past n gets no MMAs)
+                const int nmma = (tset && !two) ? 0 : (int)((info >> (6 * half)) & 63u);
                 last = (info >> 31) != 0;
                 const uint32_t myword = sm->meta[stage].prog[half][lane];   // words >= nmma unused
                 const uint32_t sbase = smem_u32(stages + stage * G::bytes);
                 const bool joint = (info & kJointBit) && B.prob[un.p].x3d;
-                const uint64_t adesc0 =
-                    joint ? a_desc_joint(sbase, G::sets > 1 ? G::ent : kJointSlabs) : a_desc(sbase);
+                const uint64_t adesc0 = joint ? a_desc_joint(sbase) : a_desc(sbase);
                 const uint32_t astep = joint ? (kSlabBytes / 2) >> 4 : kSlabBytes >> 4;
                 const uint64_t bdesc0 = b_desc(sbase + G::w16);
                 for (int i = 0; i < nmma; ++i) {
@@ -586,14 +586,12 @@ __global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
                     const uint32_t slab = wd & 15u, toff = (wd >> 4) & 255u;
                     const uint32_t r0 = (wd >> 12) & 15u, len = (wd >> 16) & 31u;
                     // descriptor start addresses are in 16-byte units (bits 0-13)
-                    const uint64_t bd = bdesc0 + toff * (kTileBytes16 >> 4);
-                    const uint32_t id = idesc0 | ((len * kTile) >> 3) << 17;
-                    tc_mma_elect(dbase + r0 * kTile, adesc0 + slab * astep, bd, id, 1u);
-                    // wide: the same W tiles against the second column tile's
-                    // slabs, into the second accumulator set
-                    if (G::sets > 1 && two)
-                        tc_mma_elect(dbase + kAccCols + r0 * kTile,
-                                     adesc0 + (G::xset >> 4) + slab * astep, bd, id, 1u);
+                    // wide, second column tile: the same W tiles against that
+                    // tile's slabs, into the second accumulator set
+                    tc_mma_elect(dbase + tset * kAccCols + r0 * kTile,
+                                 adesc0 + tset * (G::xset >> 4) + slab * astep,
+                                 bdesc0 + toff * (kTileBytes16 >> 4),
+                                 idesc0 | ((len * kTile) >> 3) << 17, 1u);
                 }
                 if (lane == 0) tc_commit(&sm->empty[stage]);
                 __syncwarp();
@@ -611,7 +609,7 @@ __global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
                 record(B.status, kDevTimeout);
                 sm->abort_flag = 1;
             }
-            sm->consumed[half] = consumed;
+            sm->consumed[mw] = consumed;
         }
     } else {
         // ------------------------- converters (E4M3) and epilogue
@@ -774,7 +772,9 @@ __global__ void __launch_bounds__(kThreads, GEO == 2 ? 1 : kCtasPerSm)
     if (threadIdx.x == 0 && sm->abort_flag) {
         int32_t hi = 0;
         for (int i = 0; i < kProducers; ++i) hi = max(hi, sm->issued[i]);
-        for (int32_t c = min(sm->consumed[0], sm->consumed[1]); c < hi; ++c) {
+        int32_t lo = sm->consumed[0];
+        for (int i = 1; i < G::mma_warps; ++i) lo = min(lo, sm->consumed[i]);
+        for (int32_t c = lo; c < hi; ++c) {
             const int s = c % kStages;
             const uint32_t par = (uint32_t)((c / kStages) & 1);   // kStages = G::stages
             // stand in for the arrivals of producers that stopped before stage c
@@ -1044,28 +1044,19 @@ __global__ void quantize_e4m3_kernel(const U *__restrict__ src, int64_t nnzb, in
 }
 
 // Wide launches (two column tiles per CTA, one CTA per SM, each W tile read
-// once per 256 columns of n): static 16-bit plans of the dense stage
-// geometry over a 3-D X map.  Automatically when the MMAs are wide (at
-// least SPMM_TC_WIDE_TPM tiles per MMA on average: one issuing warp pair
-// then keeps the tensor pipe busy with twice the MMAs, and the halved W
-// traffic pays; with narrower MMAs two CTAs per SM issue faster) and there
-// are enough work units that halving them still fills the SMs.  Measured at
-// m = k = 4096, n = 2048: 8 tiles per MMA 6-9 % faster, 6 even, 4.4-5.2
-// 3 % slower.
-// (The 3-D X map, n a multiple of 64, is checked per launch; the rest holds
-// for every n up to n if it holds for n, so a plan builds the wide stage
-// records at creation only when it can go wide at n_max.)
-bool wide_rule(const spmm_plan *p, int64_t n) {
-    if (p->col_tiles == 1 || p->mode != SPMM_STATIC || p->wdt == SPMM_E4M3 || p->tc_geo != 0 ||
+// once per 256 columns of n): static 16-bit plans over a 3-D X map (n a
+// multiple of 64) with n > 128.  Automatically when the plan averages at
+// least SPMM_TC_WIDE_TPM tiles per MMA and there are enough work units that
+// halving them still fills the SMs (a wide CTA does the work of two narrow
+// ones, which share an SM otherwise).
+bool use_wide(const spmm_plan *p, int64_t n, int x3d) {
+    if (!x3d || p->col_tiles == 1 || p->mode != SPMM_STATIC || p->wdt == SPMM_E4M3 ||
         n <= kNTile)
         return false;
     if (p->col_tiles == 2) return true;
     const int64_t units = p->n_items * ((n + kNTile - 1) / kNTile);
     return p->n_tiles >= (int64_t)SPMM_TC_WIDE_TPM * p->hp.n_mma &&
            2 * units >= (int64_t)SPMM_TC_WIDE_MIN * p->sm_count;
-}
-bool use_wide(const spmm_plan *p, int64_t n, int x3d) {
-    return x3d && p->d_srec_w && wide_rule(p, n);
 }
 
 void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, int x3d) {
@@ -1091,20 +1082,21 @@ void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, i
 template <typename T, bool W8, int GEO>
 cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
     if (B.total_units == 0) return cudaSuccess;
-    const int64_t slots = (int64_t)sm_count * (GEO == 2 ? 1 : kCtasPerSm);
+    const int64_t slots = (int64_t)sm_count * (GEO >= 2 ? 1 : kCtasPerSm);
     const int grid = (int)(B.total_units < slots ? B.total_units : slots);
     using G = StageGeom<W8, GEO>;
     const size_t smem = 1024 + (size_t)G::stages * G::bytes + sizeof(SmemT<G::stages>);
     static std::atomic<uint64_t> attrs{0};
-    const cudaError_t e = set_smem_attrs_once(attrs, tc_kernel<T, W8, GEO>, (int)smem, GEO == 2);
+    const cudaError_t e = set_smem_attrs_once(attrs, tc_kernel<T, W8, GEO>, (int)smem, GEO >= 2);
     if (e != cudaSuccess) return e;
-    pdl_launch(tc_kernel<T, W8, GEO>, dim3(grid), dim3(kThreads), smem, s, B);
+    pdl_launch(tc_kernel<T, W8, GEO>, dim3(grid), dim3(G::threads), smem, s, B);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_geo(const TcBatch &B, int geo, bool w8, int sm_count, cudaStream_t s) {
     if (w8) return geo ? launch_batch<T, true, 1>(B, sm_count, s) : launch_batch<T, true, 0>(B, sm_count, s);
+    if (geo == 3) return launch_batch<T, false, 3>(B, sm_count, s);
     if (geo == 2) return launch_batch<T, false, 2>(B, sm_count, s);
     return geo ? launch_batch<T, false, 1>(B, sm_count, s) : launch_batch<T, false, 0>(B, sm_count, s);
 }
@@ -1137,9 +1129,7 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
     cudaError_t e = encode_x(&B.maps[0], &x3d, p->xdt == SPMM_BF16, X, p->k, n, ldx);
     if (e != cudaSuccess) return e;
     const bool wide = use_wide(p, n, x3d);
-    // joint boxes: kJointSlabs slabs, or the wide geometry's entries per stage
-    e = encode_x(&B.maps4[0], &x3d, p->xdt == SPMM_BF16, X, p->k, n, ldx,
-                 wide ? StageGeom<false, 2>::ent : kJointSlabs);
+    e = encode_x(&B.maps4[0], &x3d, p->xdt == SPMM_BF16, X, p->k, n, ldx, kJointSlabs);
     if (e != cudaSuccess) return e;
     fill_prob(B.prob[0], p, Y, n, ldy, x3d);
     B.prob[0].unit_base = 0;
@@ -1147,11 +1137,7 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
     B.units = nullptr;
     B.status = p->d_status;
     const bool dyn = p->mode == SPMM_DYNAMIC;
-    if (wide) {
-        B.prob[0].ntn = (B.prob[0].ntn + 1) / 2;   // units of two column tiles
-        B.prob[0].srec = p->d_srec_w;              // stages cut for the wide geometry
-        B.prob[0].sprog = p->d_sprog_w;
-    }
+    if (wide) B.prob[0].ntn = (B.prob[0].ntn + 1) / 2;   // units of two column tiles
     B.n_items_dev = dyn ? p->d_counts + kCntItems : nullptr;
     B.total_units = (dyn ? p->dyn.items_cap : p->n_items) * B.prob[0].ntn;
     if (dyn) {
@@ -1159,8 +1145,8 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
         e = launch_stage_build(p, s);
         if (e != cudaSuccess) return e;
     }
-    return dispatch_batch(B, wide ? 2 : p->tc_geo, p->xdt == SPMM_BF16, p->wdt == SPMM_E4M3,
-                          p->sm_count, s);
+    return dispatch_batch(B, p->tc_geo + (wide ? 2 : 0), p->xdt == SPMM_BF16,
+                          p->wdt == SPMM_E4M3, p->sm_count, s);
 }
 
 namespace {
@@ -1276,30 +1262,20 @@ cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *cons
 }
 }  // namespace
 
-cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s, bool wide) {
+cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s) {
     const bool dyn = p->mode == SPMM_DYNAMIC;
     const int64_t ni = dyn ? p->dyn.items_cap : p->n_items;
-    uint32_t *srec = wide ? p->d_srec_w : p->d_srec, *sprog = wide ? p->d_sprog_w : p->d_sprog;
-    if (ni == 0 || !srec) return cudaSuccess;
+    if (ni == 0 || !p->d_srec) return cudaSuccess;
     const bool w8 = p->wdt == SPMM_E4M3;
-    int tiles_cap = w8 ? (p->tc_geo ? StageGeom<true, 1>::tiles : StageGeom<true, 0>::tiles)
-                       : (p->tc_geo ? StageGeom<false, 1>::tiles : StageGeom<false, 0>::tiles);
-    int ent_cap = w8 ? (p->tc_geo ? StageGeom<true, 1>::ent : StageGeom<true, 0>::ent)
-                     : (p->tc_geo ? StageGeom<false, 1>::ent : StageGeom<false, 0>::ent);
-    if (wide) {
-        tiles_cap = StageGeom<false, 2>::tiles;
-        ent_cap = StageGeom<false, 2>::ent;
-    }
+    // (wide launches use these records too: their caps are the base geometry's)
+    const int tiles_cap = w8 ? (p->tc_geo ? StageGeom<true, 1>::tiles : StageGeom<true, 0>::tiles)
+                             : (p->tc_geo ? StageGeom<false, 1>::tiles : StageGeom<false, 0>::tiles);
+    const int ent_cap = w8 ? (p->tc_geo ? StageGeom<true, 1>::ent : StageGeom<true, 0>::ent)
+                           : (p->tc_geo ? StageGeom<false, 1>::ent : StageGeom<false, 0>::ent);
     pdl_launch(stage_build_kernel, dim3((unsigned)ni), dim3(kBuildWarps * 32), 0, s, p->d_items, ni,
         dyn ? p->d_counts + kCntItems : nullptr, p->d_status, p->d_ent_col, p->d_ent_tbeg,
-        p->d_ent_cover, ent_cap, tiles_cap, srec, sprog);
+        p->d_ent_cover, ent_cap, tiles_cap, p->d_srec, p->d_sprog);
     return cudaGetLastError();
-}
-
-bool tc_wide_possible(const spmm_plan *p) { return wide_rule(p, p->n_max); }
-bool tc_wide_shares_records() {
-    return StageGeom<false, 2>::ent == StageGeom<false, 0>::ent &&
-           StageGeom<false, 2>::tiles == StageGeom<false, 0>::tiles;
 }
 
 int64_t stage_record_words() { return kRecWords; }

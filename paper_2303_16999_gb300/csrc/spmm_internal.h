@@ -98,7 +98,6 @@ struct spmm_plan {
             *d_ent_tbeg = nullptr, *d_ent_cover = nullptr, *d_tile_row = nullptr, *d_blk_slot = nullptr,
             *d_blk_off = nullptr, *d_grp_ebeg = nullptr;
     uint32_t *d_srec = nullptr, *d_sprog = nullptr;  // TC: stage records and MMA programs
-    uint32_t *d_srec_w = nullptr, *d_sprog_w = nullptr;  // the same, cut for wide launches
     int tc_geo = 0;                // TC stage geometry: 0 dense tiles, 1 sparse tiles
     int col_tiles = 0;             // TC: column tiles per CTA, 0 automatic (launch-time choice)
     bool transposed = false;       // applies W^T: values arrive as W's blocks, packed transposed
@@ -142,12 +141,7 @@ cudaError_t launch_gather(const spmm_plan *p, const void *d_X, int64_t n, int64_
 cudaError_t launch_restride(const void *src, void *dst, int64_t rows, int64_t n, int64_t ld,
                             size_t elem, cudaStream_t s);
 // TC stage records of every work item (plan arrays only; no values)
-// stage records of a tensor-core plan (wide: the two-column-tile geometry's)
-cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s, bool wide = false);
-// whether a static plan may launch with two column tiles per CTA at some n <= n_max
-bool tc_wide_possible(const spmm_plan *p);
-// whether the wide geometry cuts stages exactly as the dense one (same caps)
-bool tc_wide_shares_records();
+cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s);
 int64_t stage_record_words();
 // TC stage geometry for a plan whose entries hold this many tiles on average
 int tc_geometry(double tiles_per_entry);

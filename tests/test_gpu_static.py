@@ -259,22 +259,24 @@ def test_both_stage_geometries(b, d, n, geo):
     assert err <= 4e-3, err
 
 
-@pytest.mark.parametrize("b,d,n", [(1, 1 / 4, 192), (1, 1 / 8, 256), (8, 1 / 4, 320),
-                                   (4, 1 / 4, 640), (1, 1 / 4, 384), (8, 1 / 4, 200)])
+@pytest.mark.parametrize("b,d,n,geo", [(1, 1 / 4, 192, 0), (1, 1 / 8, 256, 0), (8, 1 / 4, 320, 0),
+                                       (4, 1 / 4, 640, 0), (1, 1 / 4, 384, 0), (8, 1 / 4, 200, 0),
+                                       (16, 1 / 16, 256, 1), (16, 1 / 4, 448, 1),
+                                       (8, 1 / 32, 192, 1), (16, 1 / 32, 130, 1)])
 @pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16])
-def test_two_column_tiles_per_cta(b, d, n, dt):
-    """Dense-tile plans whose CTAs cover two 128-column tiles of n (the two
-    share each stage's W tiles; the second tile's slabs and accumulators are
-    separate).  n = 192: the second tile is partly past n; 320 and 640: the
-    last CTA has one tile only; 200: not a multiple of 64, so the launch
-    keeps one tile per CTA.  Within the bound against the oracle, and bit
-    for bit equal to one tile per CTA (every accumulator column sees the same
-    MMAs in the same order)."""
+def test_two_column_tiles_per_cta(b, d, n, geo, dt):
+    """Plans of either stage geometry whose CTAs cover two 128-column tiles
+    of n (the two share each stage's W tiles; the second tile's slabs,
+    accumulators and MMA warps are separate).  n = 192: the second tile is
+    partly past n; 320, 448 and 640: the last CTA has one tile only; 200 and
+    130: not multiples of 64, so the launch keeps one tile per CTA.  Within
+    the bound against the oracle, and bit for bit equal to one tile per CTA
+    (every accumulator column sees the same MMAs in the same order)."""
     m, k = 1024, 1024
     nnzb = wl.nnzb_for(m, k, b, d)
     err, Y2, _, plan = run_case(m, k, n, b, nnzb, dt, "tc", seed=5 * b + n,
                                 ldx=((n + 7) // 8) * 8, rows_per_group=16, col_tiles=2)
-    assert plan.info()["stage_geometry"] == 0
+    assert plan.info()["stage_geometry"] == geo
     assert not torch.isnan(Y2).any()
     assert err <= TOL[dt], err
     _, Y1, _, _ = run_case(m, k, n, b, nnzb, dt, "tc", seed=5 * b + n,
