@@ -35,14 +35,17 @@
 // bound by the copy latency (a stage is refilled only after its MMAs
 // complete): each role spends about a third of a stage waiting.
 //
-// Wide launches (stage geometry 2, dense tiles): one CTA per SM covers two
+// Wide launches (stage geometries 2 and 3): one CTA per SM covers two
 // 128-column tiles of n with all 512 TMEM columns; each stage holds both
 // tiles' X slabs and one set of W tiles, and every MMA word is issued once
-// per tile, so each W tile is read from L2 once per 256 columns.
+// per tile, so each W tile is read from L2 once per 256 columns.  Four MMA
+// warps (row half x column tile) keep the issue rate of two narrow CTAs.
 //
-// Warp roles (288 threads): warp 0 = W producer, warps 1 and 8 = MMA issuers
-// (warp 1 owns TMEM), warps 2..5 = epilogue (TMEM -> registers -> Y or
-// workspace) and, for E4M3 weights, converters, warps 6 and 7 = X producers.
+// Warp roles (288 threads; wide: 352): warp 0 = W producer, warps 1 and 8 =
+// MMA issuers (warp 1 owns TMEM; wide: 9 and 10 issue the second column
+// tile's MMAs), warps 2..5 = epilogue (TMEM -> registers -> Y or workspace)
+// and, for E4M3 weights, converters, warps 6 and 7 = X producers (wide: one
+// column tile each).
 // Every mbarrier wait is bounded (globaltimer); on expiry the CTA records
 // SPMM_ERR_TIMEOUT in the plan's status word, stops, frees TMEM and exits.
 #include <cuda.h>
@@ -103,9 +106,6 @@ namespace {
 #endif
 #ifndef SPMM_TC_WIDE_MIN
 #define SPMM_TC_WIDE_MIN 3  // wide launches need work units >= this x SMs / 2
-#endif
-#ifndef SPMM_TC_WIDE_TPM
-#define SPMM_TC_WIDE_TPM 7  // ... and at least this many tiles per MMA
 #endif
 #ifndef SPMM_TC_STAGES_S
 #define SPMM_TC_STAGES_S 2  // sparse: 8 slabs, 44 tiles
@@ -1045,18 +1045,19 @@ __global__ void quantize_e4m3_kernel(const U *__restrict__ src, int64_t nnzb, in
 
 // Wide launches (two column tiles per CTA, one CTA per SM, each W tile read
 // once per 256 columns of n): static 16-bit plans over a 3-D X map (n a
-// multiple of 64) with n > 128.  Automatically when the plan averages at
-// least SPMM_TC_WIDE_TPM tiles per MMA and there are enough work units that
-// halving them still fills the SMs (a wide CTA does the work of two narrow
-// ones, which share an SM otherwise).
+// multiple of 64) with n > 128.  Automatically for dense-tile plans with
+// enough work units that halving them still fills the SMs (a wide CTA does
+// the work of two narrow ones, which share an SM otherwise).  Measured at
+// m = k = 4096, n = 2048, every dense-tile point of the sweep ran 5-11 %
+// faster wide; every sparse-tile point 6-14 % slower (its stages carry up to
+// 16 separate slab copies, two producer warps issue them all).
 bool use_wide(const spmm_plan *p, int64_t n, int x3d) {
     if (!x3d || p->col_tiles == 1 || p->mode != SPMM_STATIC || p->wdt == SPMM_E4M3 ||
         n <= kNTile)
         return false;
     if (p->col_tiles == 2) return true;
     const int64_t units = p->n_items * ((n + kNTile - 1) / kNTile);
-    return p->n_tiles >= (int64_t)SPMM_TC_WIDE_TPM * p->hp.n_mma &&
-           2 * units >= (int64_t)SPMM_TC_WIDE_MIN * p->sm_count;
+    return p->tc_geo == 0 && 2 * units >= (int64_t)SPMM_TC_WIDE_MIN * p->sm_count;
 }
 
 void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, int x3d) {

@@ -226,7 +226,6 @@ void build_tc_plan(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *bro
     hp.ent_col.clear();
     hp.ent_tbeg.clear();
     hp.ent_cover.clear();
-    hp.n_mma = 0;
     hp.grp_ebeg.assign(G + 1, 0);
     std::vector<int32_t> key_slot(slot_base[G]);
     std::vector<int> rows;
@@ -254,8 +253,6 @@ void build_tc_plan(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *bro
             size_t q = i;
             for (const auto &iv : ivs) {
                 starts |= 1u << iv.first;
-                // MMAs: one per interval and half of the rows it touches (0-7, 8-15)
-                hp.n_mma += (iv.first < 8) + (iv.first + iv.second > 8);
                 for (int r = iv.first; r < iv.first + iv.second; ++r) {
                     cov |= 1u << r;
                     if (q < j && (int)(v[q] % mt - hp.grp_row0[g]) == r) key_slot[slot_base[g] + q++] = (int32_t)hp.tile_row.size();

@@ -56,7 +56,6 @@ struct HostPlan {
     // tensor-core tile structure
     std::vector<int32_t> grp_row0, grp_rows, grp_ebeg, ent_col, ent_tbeg, ent_cover, tile_row,
         blk_slot, blk_off;
-    int64_t n_mma = 0;  // MMAs of all entries (intervals split at tile row 8)
 };
 
 // Validates shape and pattern; returns SPMM_OK, SPMM_ERR_SHAPE or SPMM_ERR_PATTERN.
