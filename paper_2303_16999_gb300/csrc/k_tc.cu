@@ -153,7 +153,11 @@ template <bool W8, int GEO> struct StageGeom {
     static_assert(GEO < 2 || !W8, "wide stages take 16-bit weights only");
     static constexpr int base = GEO & 1;            // dense (0) or sparse (1) tiles
     static constexpr int sets = GEO >= 2 ? 2 : 1;   // column tiles per CTA
-    static constexpr int threads = sets > 1 ? 352 : 288;
+    // X producer warps per column tile in wide CTAs: sparse-tile stages
+    // carry up to 2 x 8 separate slab copies, so two warps share each tile's
+    static constexpr int xprod = GEO == 3 ? 2 : 1;
+    static constexpr int producers = sets > 1 ? 1 + sets * xprod : 3;   // W + X warps
+    static constexpr int threads = GEO == 3 ? 416 : sets > 1 ? 352 : 288;
     static constexpr int mma_warps = 2 * sets;      // one per row half and column tile
     static constexpr int stages = W8 ? (GEO ? SPMM_TC_STAGES8_S : SPMM_TC_STAGES8)
                                      : GEO == 3   ? SPMM_TC_STAGES_WS
@@ -185,8 +189,9 @@ static_assert(kRowCap <= kMaxGroupRows && kRowCap <= 16, "a stage must hold a fu
 constexpr int kThreads = 288;                                     // one column tile per CTA
 constexpr int kMmaWarpsMax = 4;
 constexpr int kXWarp0 = 6, kXWarp1 = 7;                           // X-slab producers (two halves)
+constexpr int kXWarp2 = 11;                                       // wide sparse: warps 11, 12 as well
 constexpr int kMmaWarpHi = 8;                                     // MMAs of tile rows 8-15
-constexpr int kProducers = 3;                                     // W + two X
+constexpr int kProducersMax = 5;                                  // W + up to four X
 constexpr unsigned long long kWaitNs = 2000000000ull;             // 2 s per wait
 
 // A stage's MMA program: one word per MMA (slab index in the stage | first
@@ -215,7 +220,7 @@ template <int S> struct __align__(8) SmemT {
     StageMeta meta[S];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
-    int32_t issued[kProducers], consumed[kMmaWarpsMax];   // per producer / per MMA warp
+    int32_t issued[kProducersMax], consumed[kMmaWarpsMax];   // per producer / per MMA warp
     int64_t nunits;
     int32_t epi_ok[2];             // accumulator-ready outcome, per unit parity
 };
@@ -312,7 +317,7 @@ __device__ __forceinline__ Unit decode_unit(const TcBatch &B, int64_t u) {
 }
 
 template <typename T, bool W8, int GEO>
-__global__ void __launch_bounds__(GEO >= 2 ? 352 : kThreads, GEO >= 2 ? 1 : kCtasPerSm)
+__global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GEO >= 2 ? 1 : kCtasPerSm)
     tc_kernel(const __grid_constant__ TcBatch B) {
     pdl_enter();
     using G = StageGeom<W8, GEO>;
@@ -338,7 +343,7 @@ __global__ void __launch_bounds__(GEO >= 2 ? 352 : kThreads, GEO >= 2 ? 1 : kCta
         }
         sm->nunits = nu;
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&sm->full[s], kProducers);
+            mbar_init(&sm->full[s], G::producers);
             mbar_init(&sm->empty[s], G::mma_warps);   // every MMA warp
             mbar_init(&sm->conv[s], 4);    // E4M3: one arrival per converter warp
         }
@@ -347,7 +352,7 @@ __global__ void __launch_bounds__(GEO >= 2 ? 352 : kThreads, GEO >= 2 ? 1 : kCta
             mbar_init(&sm->acce[b], 128);  // every epilogue thread
         }
         sm->abort_flag = 0;
-        for (int i = 0; i < kProducers; ++i) sm->issued[i] = 0;
+        for (int i = 0; i < kProducersMax; ++i) sm->issued[i] = 0;
         for (int i = 0; i < kMmaWarpsMax; ++i) sm->consumed[i] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -371,14 +376,14 @@ __global__ void __launch_bounds__(GEO >= 2 ? 352 : kThreads, GEO >= 2 ? 1 : kCta
     __syncthreads();
     tc_fence_after();
 
-    if (warp == 0 || warp == kXWarp0 || warp == kXWarp1) {
+    if (warp == 0 || warp == kXWarp0 || warp == kXWarp1 || warp >= kXWarp2) {
         // ------------------------------------------------ TMA producers
         // Warp 0 copies each stage's W tiles and its MMA program; warp 6
         // requests its X slabs.  Both follow the stage records of the unit
         // (built ahead of the launch) with three records in flight, so
         // neither waits on a global load or decodes anything per stage.
         const bool wprod = warp == 0;
-        const int pid = wprod ? 0 : (warp == kXWarp0 ? 1 : 2);
+        const int pid = wprod ? 0 : warp == kXWarp0 ? 1 : warp == kXWarp1 ? 2 : warp - kXWarp2 + 3;
 
         int stage = 0;
         uint32_t phase = 0;
@@ -441,25 +446,29 @@ __global__ void __launch_bounds__(GEO >= 2 ? 352 : kThreads, GEO >= 2 ? 1 : kCta
                         mbar_arrive(&sm->full[stage]);
                     }
                 } else if (G::sets > 1) {
-                    // wide (3-D X map only): producer 1 brings the stage's
-                    // slabs of the first column tile, producer 2 those of the
-                    // second, each as one box of consecutive slabs or one
-                    // box per slab
+                    // wide (3-D X map only): producers 1 and 3 bring the
+                    // stage's slabs of the first column tile, 2 and 4 those
+                    // of the second (G::xprod warps per tile, each a share of
+                    // the slabs), as one box of consecutive slabs (the first
+                    // warp of the tile) or one box per slab
                     const bool joint = (info & kJointBit) != 0;
-                    const bool act = pid == 1 || two;
-                    const uint32_t xc = __shfl_sync(0xffffffffu, rc, min(3 + lane, kRecWords - 1));
+                    const int tset = (pid - 1) & 1, part = (pid - 1) >> 1;
+                    const bool act = tset == 0 || two;
+                    const int per = (nent + G::xprod - 1) / G::xprod;
+                    const int lo = part * per;
+                    const int cnt = joint ? (part == 0 ? kJointSlabs : 0) : max(0, min(nent, lo + per) - lo);
+                    const uint32_t xc =
+                        __shfl_sync(0xffffffffu, rc, min(3 + (joint ? 0 : lo) + lane, kRecWords - 1));
                     // (a joint box always lands all kJointSlabs slabs)
-                    if (lane == 0)
-                        mbar_arrive_tx(&sm->full[stage],
-                                       act ? (joint ? kJointSlabs : nent) * kSlabBytes : 0);
+                    if (lane == 0) mbar_arrive_tx(&sm->full[stage], act ? cnt * kSlabBytes : 0);
                     __syncwarp();
-                    uint8_t *xs = st + (pid - 1) * G::xset;
-                    const int nh = n0 / (kNTile / 2) + (pid - 1) * 2;
-                    if (act && joint && lane == 0)
+                    uint8_t *xs = st + tset * G::xset;
+                    const int nh = n0 / (kNTile / 2) + tset * 2;
+                    if (act && joint && cnt && lane == 0)
                         tma_load_3d(xs, &B.maps4[un.p], 0, (int)xc * kTile, nh, &sm->full[stage]);
-                    if (act && !joint && lane < nent)
-                        tma_load_3d(xs + lane * kSlabBytes, &B.maps[un.p], 0, (int)xc * kTile, nh,
-                                    &sm->full[stage]);
+                    if (act && !joint && lane < cnt)
+                        tma_load_3d(xs + (lo + lane) * kSlabBytes, &B.maps[un.p], 0, (int)xc * kTile,
+                                    nh, &sm->full[stage]);
                 } else if ((info & kJointBit) && P.x3d) {
                     // consecutive columns: X producer 1 requests all slabs in one box
                     if (lane == 0) {
@@ -534,7 +543,7 @@ __global__ void __launch_bounds__(GEO >= 2 ? 352 : kThreads, GEO >= 2 ? 1 : kCta
             sm->abort_flag = 1;
         }
         if (lane == 0) sm->issued[pid] = issued;
-    } else if (warp == 1 || warp == kMmaWarpHi || warp > kMmaWarpHi) {
+    } else if (warp == 1 || (warp >= kMmaWarpHi && warp <= kMmaWarpHi + 2)) {
         // ------------------------------- MMA issuers (converged warps)
         // warps 1 / 8: tile rows 0-7 / 8-15 of the first column tile; wide
         // CTAs: warps 9 / 10 the same rows of the second column tile
@@ -771,14 +780,14 @@ __global__ void __launch_bounds__(GEO >= 2 ? 352 : kThreads, GEO >= 2 ? 1 : kCta
     // after an abort, let copies still in flight land before the CTA exits
     if (threadIdx.x == 0 && sm->abort_flag) {
         int32_t hi = 0;
-        for (int i = 0; i < kProducers; ++i) hi = max(hi, sm->issued[i]);
+        for (int i = 0; i < G::producers; ++i) hi = max(hi, sm->issued[i]);
         int32_t lo = sm->consumed[0];
         for (int i = 1; i < G::mma_warps; ++i) lo = min(lo, sm->consumed[i]);
         for (int32_t c = lo; c < hi; ++c) {
             const int s = c % kStages;
             const uint32_t par = (uint32_t)((c / kStages) & 1);   // kStages = G::stages
             // stand in for the arrivals of producers that stopped before stage c
-            for (int i = 0; i < kProducers; ++i)
+            for (int i = 0; i < G::producers; ++i)
                 if (c >= sm->issued[i]) mbar_arrive(&sm->full[s]);
             const unsigned long long t0 = gtimer();
             while (!mbar_try(&sm->full[s], par) && gtimer() - t0 < kWaitNs) {
