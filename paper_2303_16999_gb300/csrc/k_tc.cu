@@ -1058,8 +1058,8 @@ __global__ void quantize_e4m3_kernel(const U *__restrict__ src, int64_t nnzb, in
 // enough work units that halving them still fills the SMs (a wide CTA does
 // the work of two narrow ones, which share an SM otherwise).  Measured at
 // m = k = 4096, n = 2048, every dense-tile point of the sweep ran 5-11 %
-// faster wide; every sparse-tile point 6-14 % slower (its stages carry up to
-// 16 separate slab copies, two producer warps issue them all).
+// faster wide; every sparse-tile point 6-11 % slower (two 86 KB stages per
+// CTA, against two narrow CTAs whose stages interleave).
 bool use_wide(const spmm_plan *p, int64_t n, int x3d) {
     if (!x3d || p->col_tiles == 1 || p->mode != SPMM_STATIC || p->wdt == SPMM_E4M3 ||
         n <= kNTile)
