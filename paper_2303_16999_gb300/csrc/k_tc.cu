@@ -141,7 +141,7 @@ constexpr int kStagesMax = 8;                                     // >= every ge
 constexpr int kRowCap = SPMM_TC_RCAP;
 constexpr int kAccCols = kRowCap * kTile;                         // TMEM columns per buffer
 constexpr int kMaxBatch = 64;                                     // problems per launch
-constexpr int kJointSlabsG = 4;                                   // slabs of a joint X box
+constexpr int kJointSlabs = 4;                                    // slabs of a joint X box
 
 // Stage layout: X slabs (of each column tile the CTA covers) | 16-bit W
 // tiles (MMA B operand) | (E4M3 only) the FP8 codes and their scales as
@@ -170,7 +170,7 @@ template <bool W8, int GEO> struct StageGeom {
                                     : (base ? SPMM_TC_TILES_S : SPMM_TC_TILES_D);
     static_assert(stages <= kStagesMax && ent <= 12 && tiles >= 16, "stage geometry");
     // a joint box of consecutive slabs must fit one column tile's slab area
-    static_assert(sets == 1 || ent >= kJointSlabsG, "wide stage entries");
+    static_assert(sets == 1 || ent >= kJointSlabs, "wide stage entries");
     static constexpr int xset = ent * kSlabBytes;    // X bytes of one column tile
     static constexpr int w16 = sets * xset;
     static constexpr int w8 = w16 + tiles * kTileBytes16;
@@ -260,7 +260,6 @@ struct TcProb {
 // bit 20) gets its X slabs in one TMA box of 4 slabs when X's map is 3-D;
 // the slabs then lie 2048 B apart inside each 64-column half, the halves
 // 8192 B apart.
-constexpr int kJointSlabs = kJointSlabsG;
 constexpr uint32_t kJointBit = 1u << 20;
 
 struct TcBatch {
