@@ -109,9 +109,10 @@ typedef struct {
                                      coordinates (m x k, blocks row-major); internally the plan is the
                                      block-transposed operand, so plan info and arrays report k x m */
     int32_t col_tiles;            /* TC, static plans with 16-bit weights: 128-column tiles of n per
-                                     CTA.  0 = automatic, 1 = one, 2 = two where the launch allows it
-                                     (dense stage geometry, n > 128 and a multiple of 64): the two tiles
-                                     share every W stage, one CTA per SM.  Other values SPMM_ERR_ARG. */
+                                     CTA.  1 = one; 2 = two where the launch allows it (n > 128 and a
+                                     multiple of 64): the two tiles share every W stage, one CTA per SM;
+                                     0 = automatic (two for dense-tile plans with enough work units).
+                                     Results are identical either way.  Other values SPMM_ERR_ARG. */
 } spmm_plan_opts;
 
 typedef struct spmm_plan spmm_plan;
