@@ -113,6 +113,12 @@ typedef struct {
                                      multiple of 64): the two tiles share every W stage, one CTA per SM;
                                      0 = automatic (two for dense-tile plans with enough work units).
                                      Results are identical either way.  Other values SPMM_ERR_ARG. */
+    int64_t groups;               /* static TC plans: split the m/16 tile rows into exactly this many
+                                     groups of near-equal size (sizes differ by at most one, larger
+                                     first; at most 16 rows each), instead of the equal partition with
+                                     rows_per_group rows.  0 = planner's choice.  Plan info then
+                                     reports rows_per_group = 0 and n_groups = groups.  Not combined
+                                     with rows_per_group; SPMM_ERR_ARG if out of range. */
 } spmm_plan_opts;
 
 typedef struct spmm_plan spmm_plan;
@@ -186,7 +192,7 @@ spmm_status spmm_get_status(spmm_plan *plan, int32_t *device_status);
 typedef struct {
     int64_t m, k, n_max, nnzb, nnzb_max;
     int32_t b, mode, w_dtype, x_dtype, kernel;
-    int32_t rows_per_group, max_per_item;
+    int32_t rows_per_group, max_per_item;   /* rows_per_group 0: near-equal groups (opts.groups) */
     int64_t n_items, n_groups, n_entries, n_tiles, ws_rows, n_reductions;
     int64_t device_bytes;         /* device memory the plan holds */
     int32_t stage_geometry;       /* TC: 0 dense-tile stages, 1 sparse-tile stages (other kernels: 0) */

@@ -96,6 +96,13 @@ def group_partition(mt, R):
     return equal_partition(mt, q)
 
 
+def near_equal_groups(mt, q):
+    """Tile-row groups of a plan built with an explicit group count q: mt
+    rows in q groups whose sizes differ by at most one, the larger first."""
+    base, rem = divmod(mt, q)
+    return [base + (1 if i < rem else 0) for i in range(q)]
+
+
 def chunk_sizes(L, C):
     """Splits a list of L work units into ceil(L / C) near-equal chunks (one
     chunk when L <= C); the first L mod q chunks get one unit more."""
@@ -190,12 +197,13 @@ def cover_intervals(rows):
     return out[::-1]
 
 
-def tc_plan(m, k, b, brow, bcol, R, C, sort_items=True, pad=None):
+def tc_plan(m, k, b, brow, bcol, R, C, sort_items=True, pad=None, groups=None):
     """Decomposition of the tensor-core kernel.
 
     * Each b x b block lies in 16 x 16 tile (tr, tc) = (brow*b // 16,
       bcol*b // 16) at offset (brow*b % 16, bcol*b % 16).
-    * Tile rows form groups by ``group_partition(m // 16, R)``.
+    * Tile rows form groups by ``group_partition(m // 16, R)``; with R = 0,
+      ``near_equal_groups(m // 16, groups)`` instead.
     * A group's entries are the distinct tile columns of its tiles, ascending;
       entries of all groups are concatenated in group order.
     * Each entry's rows are covered by intervals, one MMA each:
@@ -215,7 +223,7 @@ def tc_plan(m, k, b, brow, bcol, R, C, sort_items=True, pad=None):
     nnzb = len(brow)
     tr = [int(brow[p]) * b // TILE for p in range(nnzb)]
     tcol = [int(bcol[p]) * b // TILE for p in range(nnzb)]
-    sizes = group_partition(mt, R)
+    sizes = near_equal_groups(mt, groups) if R == 0 else group_partition(mt, R)
     grp_row0 = np.zeros(len(sizes), dtype=np.int32)
     acc = 0
     group_of = {}

@@ -351,9 +351,12 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
     st = check_types(kernel, b, w_dtype, x_dtype, m, k);
     if (st != SPMM_OK) return st;
     if (o.rows_per_group < 0 || o.rows_per_group > kMaxGroupRows || o.max_per_item < 0 ||
-        o.col_tiles < 0 || o.col_tiles > 2) {
-        set_error("rows_per_group must be in 0..%d, max_per_item >= 0, col_tiles in 0..2",
-                  kMaxGroupRows);
+        o.col_tiles < 0 || o.col_tiles > 2 || o.groups < 0 ||
+        (o.groups > 0 && (o.rows_per_group || o.groups > m / kTile ||
+                          (m / kTile + o.groups - 1) / o.groups > kMaxGroupRows))) {
+        set_error("rows_per_group must be in 0..%d, max_per_item >= 0, col_tiles in 0..2, "
+                  "groups in 0 or ceil(m/16/%d)..m/16 without rows_per_group",
+                  kMaxGroupRows, kMaxGroupRows);
         return SPMM_ERR_ARG;
     }
     if (mode == SPMM_DYNAMIC && (nnzb_max < 0 || nnzb_max > INT32_MAX || o.host_only)) {
@@ -405,7 +408,11 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
                 p->C = o.max_per_item ? o.max_per_item : (int)std::max<int64_t>(64, 2 * avg);
                 build_row_plan(mb, p->C, true, p->hp);
             } else if (kernel == SPMM_KERNEL_TC) {
-                p->R = o.rows_per_group ? o.rows_per_group : default_R(mt, n_max, p->sm_count);
+                p->groups = o.groups;
+                if (p->groups > 0)
+                    p->R = (int)((mt + p->groups - 1) / p->groups);
+                else
+                    p->R = o.rows_per_group ? o.rows_per_group : default_R(mt, n_max, p->sm_count);
                 if (o.max_per_item) {
                     p->C = o.max_per_item;
                 } else {
@@ -413,13 +420,13 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
                     // groups well above the mean are split
                     HostPlan probe;
                     build_tc_plan(m, k, b, p->nnzb, pattern->brow, pattern->bcol, p->R, 1 << 30,
-                                  false, false, probe);
+                                  false, false, probe, p->groups);
                     const int64_t G = (int64_t)probe.grp_rows.size();
                     const int64_t E = (int64_t)probe.ent_col.size();
                     p->C = (int)std::max<int64_t>(16, G ? (5 * E + 4 * G - 1) / (4 * G) : 16);
                 }
                 build_tc_plan(m, k, b, p->nnzb, pattern->brow, pattern->bcol, p->R, p->C, true,
-                              true, p->hp);
+                              true, p->hp, p->groups);
             }
             p->n_items = (int64_t)p->hp.items.size() / kItemFields;
             p->n_red = (int64_t)p->hp.red.size() / 3;
@@ -761,7 +768,7 @@ spmm_status spmm_plan_get_info(const spmm_plan *cp, spmm_plan_info *info) {
     i.w_dtype = p->wdt;
     i.x_dtype = p->xdt;
     i.kernel = p->kernel;
-    i.rows_per_group = p->R;
+    i.rows_per_group = p->groups > 0 ? 0 : p->R;
     i.max_per_item = p->C;
     const bool dynran = p->mode == SPMM_DYNAMIC && p->ran;
     i.n_items = dynran ? p->dyn_items : p->n_items;

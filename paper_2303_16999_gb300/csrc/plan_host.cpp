@@ -89,6 +89,14 @@ std::vector<int64_t> group_partition(int64_t mt, int64_t R) {
     return equal_partition(mt, q);
 }
 
+std::vector<int64_t> near_equal_partition(int64_t mt, int64_t q) {
+    std::vector<int64_t> out;
+    if (mt == 0 || q <= 0) return out;
+    out.assign(q, mt / q);
+    for (int64_t i = 0; i < mt % q; ++i) out[i]++;
+    return out;
+}
+
 static void chunk_sizes(int64_t L, int64_t C, std::vector<int64_t> &out) {
     const int64_t q = (L <= C) ? 1 : (L + C - 1) / C;
     out.assign(q, L / q);
@@ -190,10 +198,11 @@ static void cover_intervals(const std::vector<int> &rows, std::vector<std::pair<
 
 void build_tc_plan(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *brow,
                    const int32_t *bcol, int64_t R, int64_t C, bool sort_items, bool pad,
-                   HostPlan &hp) {
+                   HostPlan &hp, int64_t groups) {
     const int64_t mt = m / kTile;
     (void)k;
-    const std::vector<int64_t> sizes = group_partition(mt, R);
+    const std::vector<int64_t> sizes =
+        groups > 0 ? near_equal_partition(mt, groups) : group_partition(mt, R);
     const int64_t G = (int64_t)sizes.size();
     hp.grp_row0.assign(G, 0);
     hp.grp_rows.assign(G, 0);

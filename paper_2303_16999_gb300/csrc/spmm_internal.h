@@ -63,10 +63,14 @@ spmm_status validate_pattern(int64_t m, int64_t k, int b, int64_t nnzb, const in
                              const int32_t *bcol);
 void build_csr(int64_t mb, int64_t nnzb, const int32_t *brow, const int32_t *bcol, HostPlan &hp);
 std::vector<int64_t> group_partition(int64_t mt, int64_t R);
+// mt tile rows in q groups whose sizes differ by at most one (larger first)
+std::vector<int64_t> near_equal_partition(int64_t mt, int64_t q);
 void build_row_plan(int64_t mb, int64_t C1, bool sort_items, HostPlan &hp);
+// groups > 0: the tile rows in that many near-equal groups, else the
+// equal partition with at most R rows per group
 void build_tc_plan(int64_t m, int64_t k, int b, int64_t nnzb, const int32_t *brow,
                    const int32_t *bcol, int64_t R, int64_t C, bool sort_items, bool pad,
-                   HostPlan &hp);
+                   HostPlan &hp, int64_t groups = 0);
 
 // ------------------------------------------------------------------- plan
 // dynamic plans: scratch of the device re-partition
@@ -99,6 +103,7 @@ struct spmm_plan {
     uint32_t *d_srec = nullptr, *d_sprog = nullptr;  // TC: stage records and MMA programs
     int tc_geo = 0;                // TC stage geometry: 0 dense tiles, 1 sparse tiles
     int col_tiles = 0;             // TC: column tiles per CTA, 0 automatic (launch-time choice)
+    int64_t groups = 0;            // static TC: near-equal tile-row groups (0: equal partition by R)
     bool transposed = false;       // applies W^T: values arrive as W's blocks, packed transposed
     int32_t *d_sd_items = nullptr; // b = 16: SDDMM work items (count, then (row, e0, e1) triples)
     int64_t sd_items_cap = 0;

@@ -61,7 +61,8 @@ class DPattern(ctypes.Structure):
 class PlanOpts(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("rows_per_group", ctypes.c_int32),
                 ("max_per_item", ctypes.c_int32), ("host_only", ctypes.c_int32),
-                ("transposed", ctypes.c_int32), ("col_tiles", ctypes.c_int32)]
+                ("transposed", ctypes.c_int32), ("col_tiles", ctypes.c_int32),
+                ("groups", ctypes.c_int64)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -275,15 +276,16 @@ class Plan:
     Z = W^T.Y (k x n) for Y (m x n), and ``self.m, self.k`` are k, m.
 
     ``col_tiles``: 128-column tiles of n per tensor-core CTA (0 automatic,
-    1, or 2 where the launch allows it), as ``spmm_plan_opts.col_tiles``."""
+    1, or 2 where the launch allows it), as ``spmm_plan_opts.col_tiles``;
+    ``groups``: near-equal tile-row groups, as ``spmm_plan_opts.groups``."""
 
     def __init__(self, m, k, n_max, b, w_dtype=F16, x_dtype=None, brow=None, bcol=None,
                  mode=STATIC, nnzb_max=0, kernel="auto", rows_per_group=0, max_per_item=0,
-                 host_only=False, transposed=False, col_tiles=0):
+                 host_only=False, transposed=False, col_tiles=0, groups=0):
         x_dtype = w_dtype if x_dtype is None else x_dtype
         opts = PlanOpts(KERNELS[kernel] if isinstance(kernel, str) else kernel,
                         rows_per_group, max_per_item, 1 if host_only else 0,
-                        1 if transposed else 0, col_tiles)
+                        1 if transposed else 0, col_tiles, groups)
         pat = None
         self._keep = None
         if mode == STATIC:

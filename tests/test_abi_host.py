@@ -161,13 +161,44 @@ def test_tc_plan_bit_exact(b):
         brow, bcol = _rand(rng, mb, kb, int(d * mb * kb))
         p = _plan(m, k, b, brow, bcol, rows_per_group=R, max_per_item=C, n_max=nmax)
         info = p.info()
-        want = P.tc_plan(m, k, b, brow, bcol, info["rows_per_group"], info["max_per_item"])
+        want = P.tc_plan(m, k, b, brow, bcol, info["rows_per_group"], info["max_per_item"],
+                         groups=info["n_groups"])
         for key in TC_KEYS:
             assert np.array_equal(p.array(key), want[key]), key
         assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
         assert np.array_equal(p.array("red").reshape(-1, 3), want["red"])
         assert info["ws_rows"] == want["ws_rows"]
         assert info["n_tiles"] == len(want["tile_row"])
+
+
+@pytest.mark.parametrize("b", [1, 4, 16])
+def test_tc_plan_near_equal_groups_bit_exact(b):
+    """Plans with an explicit group count: the tile rows in near-equal groups
+    (the shape that fills the SMs with whole units), bit for bit against
+    the oracle's plan, with and without split items."""
+    rng = np.random.default_rng(70 + b)
+    for m, k, d, q, C in ((4096, 512, 1 / 8, 19, 0), (1024, 768, 1 / 4, 5, 9), (272, 256, 1 / 4, 17, 0),
+                          (528, 320, 1 / 16, 3, 0)):
+        mb, kb = m // b, k // b
+        brow, bcol = _rand(rng, mb, kb, int(d * mb * kb))
+        p = _plan(m, k, b, brow, bcol, groups=q, max_per_item=C, kernel="tc")
+        info = p.info()
+        assert info["rows_per_group"] == 0 and info["n_groups"] == q
+        rows = p.array("grp_rows")
+        assert rows.sum() == m // 16 and rows.max() - rows.min() <= 1 and rows.max() <= 16
+        want = P.tc_plan(m, k, b, brow, bcol, 0, info["max_per_item"], groups=q)
+        for key in TC_KEYS:
+            assert np.array_equal(p.array(key), want[key]), key
+        assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
+        assert np.array_equal(p.array("red").reshape(-1, 3), want["red"])
+
+
+def test_groups_option_errors():
+    brow, bcol = [0], [0]
+    for q, extra in ((1, {}), (65, {}), (-1, {}), (8, {"rows_per_group": 4})):
+        with pytest.raises(S.SpmmError) as e:
+            _plan(1024, 64, 16, brow, bcol, groups=q, kernel="tc", **extra)
+        assert e.value.status == S.ERR_ARG, q
 
 
 def test_tc_plan_worst_case_splits():
@@ -178,7 +209,8 @@ def test_tc_plan_worst_case_splits():
     bcol = np.arange(64, dtype=np.int32)
     p = _plan(m, k, b, brow, bcol, n_max=256)
     info = p.info()
-    want = P.tc_plan(m, k, b, brow, bcol, info["rows_per_group"], info["max_per_item"])
+    want = P.tc_plan(m, k, b, brow, bcol, info["rows_per_group"], info["max_per_item"],
+                         groups=info["n_groups"])
     assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
     assert info["n_reductions"] == 1 and info["ws_rows"] > 0
 
@@ -197,7 +229,8 @@ def test_auto_kernel_choice_for_b1():
     assert p.info()["kernel"] == S.KERNEL_GATHER
     p = _plan(512, 512, 1, brow, bcol, n_max=256, kernel="tc")
     assert p.info()["kernel"] == S.KERNEL_TC
-    want = P.tc_plan(512, 512, 1, brow, bcol, p.info()["rows_per_group"], p.info()["max_per_item"])
+    want = P.tc_plan(512, 512, 1, brow, bcol, p.info()["rows_per_group"], p.info()["max_per_item"],
+                     groups=p.info()["n_groups"])
     assert np.array_equal(p.array("ent_cover"), want["ent_cover"])
     assert np.array_equal(p.array("blk_slot"), want["blk_slot"])
 
@@ -217,7 +250,8 @@ def test_transposed_plan_is_the_plan_of_w_transpose(b):
     assert np.array_equal(p.array("row_ptr"), rp)
     assert np.array_equal(p.array("col_idx"), ci)
     assert np.array_equal(p.array("perm"), pm)
-    want = P.tc_plan(k, m, b, bcol, brow, info["rows_per_group"], info["max_per_item"])
+    want = P.tc_plan(k, m, b, bcol, brow, info["rows_per_group"], info["max_per_item"],
+                     groups=info["n_groups"])
     for key in TC_KEYS:
         assert np.array_equal(p.array(key), want[key]), key
     assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])

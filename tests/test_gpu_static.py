@@ -305,3 +305,24 @@ def test_two_column_tiles_integers_bit_exact():
     Y = plan.run(torch.from_numpy(X).half().cuda()).cpu()
     Yo = oracle.spmm(m, k, b, brow, bcol, vals, X)
     assert torch.equal(Y, torch.from_numpy(Yo).half())
+
+
+@pytest.mark.parametrize("b,d,n,ct", [(1, 1 / 4, 256, 2), (16, 1 / 16, 256, 0), (4, 1 / 8, 192, 2),
+                                      (8, 1 / 4, 130, 0), (16, 1 / 4, 384, 2)])
+def test_near_equal_groups(b, d, n, ct):
+    """Tile rows in 19 near-equal groups (3 or 4 rows each here) instead of the
+    planner's equal partition: within the bound against the oracle, and,
+    where no row is split across items in either plan, bit for bit equal to
+    the default grouping (every row of Y sums its tiles in ascending column
+    order either way)."""
+    m, k = 1024, 1024
+    nnzb = wl.nnzb_for(m, k, b, d)
+    ld = ((n + 7) // 8) * 8
+    err, Yq, _, pq = run_case(m, k, n, b, nnzb, torch.float16, "tc", seed=9 * b + n, ldx=ld,
+                              groups=19, col_tiles=ct)
+    assert pq.info()["n_groups"] == 19 and pq.info()["rows_per_group"] == 0
+    assert err <= 4e-3, err
+    _, Y0, _, p0 = run_case(m, k, n, b, nnzb, torch.float16, "tc", seed=9 * b + n, ldx=ld,
+                            col_tiles=ct)
+    if pq.info()["n_reductions"] == 0 and p0.info()["n_reductions"] == 0:
+        assert torch.equal(Yq, Y0)

@@ -292,3 +292,13 @@ def test_tile_values():
     assert np.array_equal(t[0, 0:4, 4:8], vals[0])
     assert np.array_equal(t[0, 12:16, 8:12], vals[1])
     assert t[0].sum() == vals.sum()
+
+
+@pytest.mark.parametrize("mt,q", [(256, 19), (256, 16), (17, 17), (100, 7), (5, 1)])
+def test_near_equal_groups(mt, q):
+    """q groups covering every tile row once, sizes within one of each
+    other, larger groups first."""
+    g = P.near_equal_groups(mt, q)
+    assert len(g) == q and sum(g) == mt
+    assert max(g) - min(g) <= 1
+    assert g == sorted(g, reverse=True)
