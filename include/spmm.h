@@ -113,7 +113,7 @@ typedef struct {
                                      multiple of 64): the two tiles share every W stage, one CTA per SM;
                                      0 = automatic (two for dense-tile plans with enough work units).
                                      Results are identical either way.  Other values SPMM_ERR_ARG. */
-    int64_t groups;               /* static TC plans: split the m/16 tile rows into exactly this many
+    int64_t groups;               /* TC plans: split the m/16 tile rows into exactly this many
                                      groups of near-equal size (sizes differ by at most one, larger
                                      first; at most 16 rows each), instead of the equal partition with
                                      rows_per_group rows.  0 = planner's choice.  Plan info then

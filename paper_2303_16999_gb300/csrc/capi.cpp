@@ -483,8 +483,17 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
                     free_plan(p);
                     return SPMM_ERR_UNSUPPORTED;
                 }
-                p->R = o.rows_per_group ? o.rows_per_group : default_R(mt, n_max, p->sm_count);
-                const std::vector<int64_t> sz = group_partition(mt, p->R);
+                // near-equal groups as for static plans (dynamic launches
+                // take one column tile per CTA), else the equal partition
+                p->groups = o.groups;
+                if (!p->groups && !o.rows_per_group)
+                    p->groups = auto_groups(mt, n_max, p->sm_count, false);
+                if (p->groups > 0)
+                    p->R = (int)((mt + p->groups - 1) / p->groups);
+                else
+                    p->R = o.rows_per_group ? o.rows_per_group : default_R(mt, n_max, p->sm_count);
+                const std::vector<int64_t> sz =
+                    p->groups > 0 ? near_equal_partition(mt, p->groups) : group_partition(mt, p->R);
                 int64_t acc = 0;
                 for (int64_t v : sz) {
                     p->hp.grp_row0.push_back((int32_t)acc);

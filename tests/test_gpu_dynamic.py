@@ -43,7 +43,7 @@ def _check_arrays(plan, m, k, b, brow, bcol):
         want = P.row_plan(mb, rp, info["max_per_item"], sort_items=False)
     else:
         want = P.tc_plan(m, k, b, brow, bcol, info["rows_per_group"], info["max_per_item"],
-                         sort_items=False, pad=False)
+                         sort_items=False, pad=False, groups=info["n_groups"])
         for key in ("grp_ebeg", "ent_col", "ent_tbeg", "ent_cover", "tile_row", "blk_slot",
                     "blk_off"):
             assert np.array_equal(plan.array(key), want[key]), key
