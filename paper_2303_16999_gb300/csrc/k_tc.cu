@@ -41,11 +41,12 @@
 // per tile, so each W tile is read from L2 once per 256 columns.  Four MMA
 // warps (row half x column tile) keep the issue rate of two narrow CTAs.
 //
-// Warp roles (288 threads; wide: 352): warp 0 = W producer, warps 1 and 8 =
-// MMA issuers (warp 1 owns TMEM; wide: 9 and 10 issue the second column
-// tile's MMAs), warps 2..5 = epilogue (TMEM -> registers -> Y or workspace)
-// and, for E4M3 weights, converters, warps 6 and 7 = X producers (wide: one
-// column tile each).
+// Warp roles (288 threads; wide: 352, wide sparse-tile: 416): warp 0 = W
+// producer, warps 1 and 8 = MMA issuers (warp 1 owns TMEM; wide: 9 and 10
+// issue the second column tile's MMAs), warps 2..5 = epilogue (TMEM ->
+// registers -> Y or workspace) and, for E4M3 weights, converters, warps 6
+// and 7 = X producers (wide: one column tile each; wide sparse-tile: warps
+// 11 and 12 take a share of each tile's slabs).
 // Every mbarrier wait is bounded (globaltimer); on expiry the CTA records
 // SPMM_ERR_TIMEOUT in the plan's status word, stops, frees TMEM and exits.
 #include <cuda.h>
