@@ -257,6 +257,22 @@ def test_transposed_plan_is_the_plan_of_w_transpose(b):
     assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
 
 
+@pytest.mark.parametrize("b", [4, 16])
+def test_transposed_plan_with_near_equal_groups(b):
+    """A transposed plan with an explicit group count splits W^T's tile rows
+    (W's tile columns) into near-equal groups, as the oracle's plan of W^T."""
+    rng = np.random.default_rng(90 + b)
+    m, k, q = 256, 1024, 11
+    brow, bcol = _rand(rng, m // b, k // b, (m // b) * (k // b) // 8)
+    p = _plan(m, k, b, brow, bcol, n_max=256, transposed=True, kernel="tc", groups=q)
+    info = p.info()
+    assert info["n_groups"] == q and info["rows_per_group"] == 0
+    want = P.tc_plan(k, m, b, bcol, brow, 0, info["max_per_item"], groups=q)
+    for key in TC_KEYS:
+        assert np.array_equal(p.array(key), want[key]), key
+    assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
+
+
 def test_ell_layout_of_a_pattern():
     """workloads.to_ell, the Blocked-ELL layout the ELL tests and benchmark
     feed spmm_run_ell: every block appears once in its row, columns ascend,
