@@ -14,7 +14,13 @@ Contents
 * ``sddmm(...)`` -- dW = (dY.X^T) on the block mask (the product's gradient
   with respect to the stored blocks), from its definition.
 * ``e4m3_to_f64`` -- FP8 E4M3 decoding from the format definition.
+* ``e4m3_block_values`` -- effective FP64 values of E4M3 blocks, one FP32
+  scale per block (pattern order).
 * ``normwise_err`` -- ||Y - Y_o||_F / (||W||_F ||X||_F), the acceptance metric.
+* ``relative_err`` -- ||Y - Y_o||_F / ||Y_o||_F, the bar that still bites at
+  large k (the normwise metric shrinks like 1/sqrt(k) for random data).
+* ``componentwise_ratio`` -- max_ij |Y - Y_o|_ij / (|W| |X|)_ij, the
+  componentwise diagnostic of the error analysis of a sum of products.
 * ``oracle.plan`` -- the integer plan / partition rules (Section 3.2, 3.3,
   Appendix A.2, and this library's GPU work decomposition), plain Python.
 
@@ -162,22 +168,15 @@ def e4m3_to_f64(codes, lib=None):
 
 def e4m3_block_values(codes, scales):
     """Effective FP64 values of E4M3 blocks with one FP32 scale per block:
-    v(p, i, l) = decode(code(p, i, l)) * scale[p]."""
+    v(p, i, l) = decode(code(p, i, l)) * scale[p], codes (nnzb, b, b) and
+    scales (nnzb,) both in the pattern's order (block p of the pattern)."""
     d = e4m3_to_f64(codes)
-    s = np.asarray(scales, dtype=np.float64).reshape(-1, 1, 1)
-    return d * s
-
-
-def densify(m, k, b, brow, bcol, vals):
-    """Dense FP64 m x k matrix M (.) W built from the block list (truncating
-    blocks that hang over the edge, as in Section 3's ceil(m/b) grid)."""
-    W = np.zeros((m, k), dtype=np.float64)
-    v = to_f64(vals)
-    for p in range(len(brow)):
-        r0, c0 = int(brow[p]) * b, int(bcol[p]) * b
-        hi, wi = min(b, m - r0), min(b, k - c0)
-        W[r0:r0 + hi, c0:c0 + wi] = v[p, :hi, :wi]
-    return W
+    if d.ndim != 3:
+        raise ValueError("codes must be (nnzb, b, b)")
+    s = np.asarray(scales, dtype=np.float64).reshape(-1)
+    if s.shape[0] != d.shape[0]:
+        raise ValueError("one scale per block required")
+    return d * s[:, None, None]
 
 
 def normwise_err(Y, Y_o, W_fro, X):
@@ -191,6 +190,39 @@ def normwise_err(Y, Y_o, W_fro, X):
     if d == 0.0:
         return 0.0 if not np.any(Y) else float("inf")
     return num / d
+
+
+def relative_err(Y, Y_o):
+    """||Y - Y_o||_F / ||Y_o||_F in FP64 (0 when both are 0, +inf when only
+    Y_o is).  For N(0, 1) data ||Y||_F is about ||W||_F ||X||_F / sqrt(k),
+    so a bar on this ratio sees a dropped block that the normwise metric
+    would admit at large k."""
+    Y = to_f64(Y)
+    Y_o = to_f64(Y_o)
+    num = float(np.linalg.norm(Y - Y_o))
+    den = float(np.linalg.norm(Y_o))
+    if den == 0.0:
+        return 0.0 if num == 0.0 else float("inf")
+    return num / den
+
+
+def componentwise_ratio(Y, Y_o, absWX):
+    """max_ij |Y - Y_o|_ij / (|W| |X|)_ij over the entries where the
+    denominator is positive; an entry with (|W| |X|)_ij = 0 must match
+    exactly (else +inf).  ``absWX`` is the product of the absolute values,
+    e.g. ``spmm(m, k, b, brow, bcol, |vals|, |X|)``.  Rounding the FP32
+    accumulation of s terms and then the output to unit roundoff u bounds it
+    by about u + s * 2^-24."""
+    Y = to_f64(Y)
+    Y_o = to_f64(Y_o)
+    A = to_f64(absWX)
+    diff = np.abs(Y - Y_o)
+    pos = A > 0
+    if np.any(diff[~pos] != 0):
+        return float("inf")
+    if not np.any(pos):
+        return 0.0
+    return float(np.max(diff[pos] / A[pos]))
 
 
 def block_fro(vals):

@@ -197,6 +197,54 @@ def test_e4m3_matches_library_decoder():
     assert both_nan.sum() == 2
 
 
+# E4M3 blocks with one FP32 scale each.  Codes are sign | 4 exponent bits
+# (bias 7) | 3 mantissa bits, decoded here by hand:
+#   0x38 = +1.0, 0x40 = +2.0, 0xB8 = -1.0, 0x3C = +1.5,
+#   0x7E = +448 (1.75 * 2^8), 0x01 = 2^-9 (smallest subnormal), 0xC0 = -2.0,
+#   0x44 = +3.0.
+# As many blocks as a block has rows, so that a scale broadcast along the
+# wrong axis still has the right shape and must be caught by value.
+E4M3_CODES = np.array([[[0x38, 0x40], [0xB8, 0x3C]],
+                       [[0x7E, 0x01], [0xC0, 0x44]]], np.uint8)
+E4M3_SCALES = np.array([0.5, 3.0], np.float32)
+E4M3_WANT = np.array([[[0.5, 1.0], [-0.5, 0.75]],
+                      [[1344.0, 3.0 * 2.0 ** -9], [-6.0, 9.0]]])
+
+
+def check_e4m3_block_values(fn):
+    """Block p scaled by its own scale, every element of the block alike."""
+    got = fn(E4M3_CODES, E4M3_SCALES)
+    assert got.shape == E4M3_WANT.shape
+    assert np.array_equal(got, E4M3_WANT)
+
+
+def check_e4m3_pattern_order(fn):
+    """Scales follow the pattern's order, not the block-CSR order: with the
+    pattern listing block rows 1, 0 (b = 2, m = 4, k = 2) and X = I, Y's
+    block row r is the block whose pattern entry names row r."""
+    brow = np.array([1, 0], np.int32)
+    bcol = np.zeros(2, np.int32)
+    v = fn(E4M3_CODES, E4M3_SCALES)
+    Y = oracle.spmm(4, 2, 2, brow, bcol, v, np.eye(2))
+    want = np.concatenate([E4M3_WANT[1], E4M3_WANT[0]])
+    assert np.array_equal(Y, want)
+
+
+E4M3_CHECKS = [check_e4m3_block_values, check_e4m3_pattern_order]
+
+
+@pytest.mark.parametrize("check", E4M3_CHECKS, ids=lambda f: f.__name__)
+def test_e4m3_block_values_pin(check):
+    check(oracle.e4m3_block_values)
+
+
+def test_e4m3_block_values_rejects_bad_shapes():
+    with pytest.raises(ValueError):
+        oracle.e4m3_block_values(E4M3_CODES, E4M3_SCALES[:1])
+    with pytest.raises(ValueError):
+        oracle.e4m3_block_values(E4M3_CODES.reshape(2, 4), E4M3_SCALES)
+
+
 # ------------------------------------------------------- error metric ------
 def test_normwise_err_closed_form():
     Yo = np.zeros((3, 4))
@@ -207,6 +255,42 @@ def test_normwise_err_closed_form():
     assert oracle.normwise_err(Y, Yo, 10.0, X) == 5.0 / 20.0
     assert oracle.normwise_err(Yo, Yo, 0.0, X) == 0.0
     assert oracle.normwise_err(Y, Yo, 0.0, X) == float("inf")
+
+
+def test_relative_err_closed_form():
+    Yo = np.zeros((2, 2))
+    Yo[0, 0], Yo[1, 1] = 3.0, 4.0        # ||Yo||_F = 5
+    Y = Yo.copy()
+    Y[0, 1] = 1.0                        # ||Y - Yo||_F = 1
+    assert oracle.relative_err(Y, Yo) == 0.2
+    assert oracle.relative_err(np.zeros(3), np.zeros(3)) == 0.0
+    assert oracle.relative_err(np.ones(3), np.zeros(3)) == float("inf")
+
+
+def test_componentwise_ratio_closed_form():
+    Yo = np.array([[1.0, 2.0], [0.0, 5.0]])
+    A = np.array([[4.0, 8.0], [0.0, 10.0]])
+    Y = np.array([[1.5, 2.0], [0.0, 4.0]])     # |dY| / A = 0.125, 0, -, 0.1
+    assert oracle.componentwise_ratio(Y, Yo, A) == 0.125
+    Y[1, 0] = 1e-30                             # a nonzero where |W||X| = 0
+    assert oracle.componentwise_ratio(Y, Yo, A) == float("inf")
+
+
+def test_componentwise_ratio_sees_a_dropped_block():
+    """At large k a dropped block moves ||Y - Y_o||_F / (||W||_F ||X||_F)
+    by about 1/sqrt(k * nnz_row) only, but the relative and componentwise
+    ratios by far more than any 16-bit rounding (u = 2^-8 for BF16)."""
+    rng = np.random.default_rng(3)
+    m, k, n, b = 64, 4096, 16, 16
+    c = wl.problem(5, m, k, n, b, wl.nnzb_for(m, k, b, 1 / 4))
+    Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], c["vals"], c["X"])
+    keep = np.ones(len(c["brow"]), bool)
+    keep[rng.integers(len(keep))] = False
+    Yd = oracle.spmm(m, k, b, c["brow"][keep], c["bcol"][keep], c["vals"][keep], c["X"])
+    A = oracle.spmm(m, k, b, c["brow"], c["bcol"], np.abs(c["vals"]), np.abs(c["X"]))
+    assert oracle.normwise_err(Yd, Yo, oracle.block_fro(c["vals"]), c["X"]) < 4e-3
+    assert oracle.relative_err(Yd, Yo) > 1e-2
+    assert oracle.componentwise_ratio(Yd, Yo, A) > 2 * 2.0 ** -8 + 4096 * 2.0 ** -24
 
 
 def test_workload_recipe_shapes():
@@ -223,7 +307,7 @@ def test_workload_recipe_shapes():
 # ---- the transposed product W^T.Y (oracle.spmm_t) ------------------------
 @pytest.mark.parametrize("b", [1, 2, 4, 8])
 def test_transposed_matches_dense_transpose(b):
-    """W^T.Y equals densify(W)^T @ Y computed by numpy in FP64."""
+    """W^T.Y equals the dense W^T @ Y computed by numpy in FP64."""
     rng = np.random.default_rng(40 + b)
     m, k, n = 8 * b, 12 * b, 5
     mb, kb = m // b, k // b
