@@ -176,3 +176,17 @@ def serve_requests(count, rate_per_s, n_weights, seed, n_max=256):
 
 def request_x(seed, k, n):
     return rng_for(seed).standard_normal((k, n), dtype=np.float32)
+
+
+# ---- integer-valued operands (exact-arithmetic parity cases) ----------------
+def integer_problem(seed, m, k, n, b, nnzb, vals_range=(-2, 2), x_range=(-1, 1)):
+    """The pattern recipe of problem(), then integer values uniform in
+    ``vals_range`` and integer X uniform in ``x_range`` (inclusive), as FP32.
+    Small integers are exact in every input type, and their sums of
+    products are exact in FP32 accumulation."""
+    rng = rng_for(seed)
+    brow, bcol = pattern(rng, m // b, k // b, nnzb)
+    vals = rng.integers(vals_range[0], vals_range[1], size=(nnzb, b, b),
+                        endpoint=True).astype(np.float32)
+    X = rng.integers(x_range[0], x_range[1], size=(k, n), endpoint=True).astype(np.float32)
+    return dict(m=m, k=k, n=n, b=b, brow=brow, bcol=bcol, vals=vals, X=X, seed=seed)

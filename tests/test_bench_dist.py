@@ -87,3 +87,36 @@ def test_power_law_fit_recovers_exponents():
     c, al, be, ga, r2 = bench.fit_power_law(rows)
     assert abs(c - 0.0013) < 1e-9 and abs(al - 0.59) < 1e-9
     assert abs(be + 0.54) < 1e-9 and abs(ga - 0.50) < 1e-9 and abs(r2 - 1.0) < 1e-12
+
+
+def test_roofline_fraction_is_recomputable():
+    """frac = sum of per-launch roofline times (max(FLOP / P_tensor,
+    bytes / P_hbm)) over the sum of measured times; the object carries both
+    sums, and the bound is the roof that holds most of the roofline time."""
+    bench = _bench()
+    peaks = {"hbm_gbs": 1000.0, "bf16_tflops": 100.0}
+    # launch 1: tensor-bound, t_roof = 1e12 / 1e14 = 10 ms; launch 2: HBM-bound,
+    # t_roof = 5e9 / 1e12 = 5 ms; measured 20 ms and 25 ms
+    r = bench.roofline_obj([(1e12, 1e9, 0.020), (1e9, 5e9, 0.025)], peaks, "tensor")
+    assert r["t_roof_us"] == pytest.approx(15000.0)
+    assert r["t_meas_us"] == pytest.approx(45000.0)
+    assert r["frac"] == pytest.approx(r["t_roof_us"] / r["t_meas_us"], abs=1e-4)
+    assert r["bound"] == "tensor" and r["peak"] == 100.0
+    assert r["achieved"] == pytest.approx(r["frac"] * r["peak"], abs=0.01)
+    assert r["roof_share"] == {"tensor": pytest.approx(2 / 3, abs=1e-3),
+                               "hbm": pytest.approx(1 / 3, abs=1e-3)}
+
+
+def test_sweep_traffic_only_for_the_captured_sources():
+    """DRAM traffic from an ncu capture is reported only while the kernel and
+    planner sources hash to the captured value."""
+    bench = _bench()
+    saved = dict(bench.SWEEP_TRAFFIC)
+    try:
+        bench.SWEEP_TRAFFIC.update(sha16=bench.kernel_source_sha16(), bytes_per_launch=123.0)
+        assert bench.sweep_traffic() == 123.0
+        bench.SWEEP_TRAFFIC.update(sha16="0" * 16)
+        assert bench.sweep_traffic() is None
+    finally:
+        bench.SWEEP_TRAFFIC.clear()
+        bench.SWEEP_TRAFFIC.update(saved)

@@ -6,6 +6,7 @@ Invalid patterns must set the status word and leave Y untouched."""
 import numpy as np
 import pytest
 
+import checks
 import oracle
 from oracle import plan as P
 from paper_2303_16999_gb300 import spmm as S
@@ -149,7 +150,9 @@ def test_dynamic_empty_pattern():
 
 def test_dynamic_full_size_sampled():
     """m = k = 8192, n = 1024, b = 16, d_max = 1/16 (nnzb_max = 16384): two
-    calls with fresh patterns; sampled block rows against the oracle."""
+    calls with fresh patterns; 8 sampled block rows against the oracle with
+    the normwise, relative and componentwise bars; every device-built array
+    bit for bit."""
     m = k = 8192
     n = 1024
     cap = 16384
@@ -163,11 +166,74 @@ def test_dynamic_full_size_sampled():
         Y = plan.run(X.cuda(), values=vd.cuda(), pattern=_dev_pattern(c["brow"], c["bcol"], cap))
         torch.cuda.synchronize()
         assert plan.status() == 0
-        rows = [0, 101, 511]
-        sel = np.isin(c["brow"], rows)
-        remap = {r: i for i, r in enumerate(rows)}
-        br = np.array([remap[r] for r in c["brow"][sel]], np.int32)
-        Yo = oracle.spmm(len(rows) * 16, k, 16, br, c["bcol"][sel], vals[sel], X)
-        Ys = torch.cat([Y[r * 16:(r + 1) * 16].cpu() for r in rows])
-        assert oracle.normwise_err(Ys, Yo, oracle.block_fro(vals[sel]), X) <= 4e-3
+        rows = [0, 101, 170, 255, 256, 340, 510, 511]
+        checks.check_rows(Y.cpu(), rows, m, k, 16, c["brow"], c["bcol"], vals, X, torch.bfloat16)
         _check_arrays(plan, m, k, 16, c["brow"], c["bcol"])
+
+
+def test_dynamic_full_size_integers_exact():
+    """The dynamic benchmark's shape (m = k = 8192, n = 1024, b = 16, BF16,
+    nnzb_max = 16384) with integer values in [-2, 2] and X in [-1, 1]: sums
+    are exact in FP32 and the results fit BF16 exactly, so every row and
+    column of Y is checked through exact identities and 8 block rows bit
+    for bit, on two calls with different patterns and block counts."""
+    m = k = 8192
+    n = 1024
+    cap = 16384
+    plan = S.Plan(m, k, n, 16, w_dtype=S.BF16, mode=S.DYNAMIC, nnzb_max=cap)
+    for call, nnz in enumerate((cap, 9001)):
+        c = wl.integer_problem(8900 + call, m, k, n, 16, nnz)
+        vd = torch.zeros((cap, 16, 16), dtype=torch.bfloat16)
+        vd[:nnz] = torch.from_numpy(c["vals"]).to(torch.bfloat16)
+        X = torch.from_numpy(c["X"]).to(torch.bfloat16)
+        Y = plan.run(X.cuda(), values=vd.cuda(), pattern=_dev_pattern(c["brow"], c["bcol"], cap))
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        Y = Y.cpu()
+        checks.exact_identities(Y, m, k, 16, c["brow"], c["bcol"], c["vals"], c["X"], seed=call)
+        checks.exact_rows(Y, [0, 3, 100, 255, 256, 400, 510, 511], k, 16, c["brow"], c["bcol"],
+                          c["vals"], c["X"], torch.bfloat16)
+
+
+@pytest.mark.parametrize("b", [4, 8, 16])
+def test_dynamic_near_equal_groups(b):
+    """Dynamic tensor-core plans with an explicit count of near-equal
+    tile-row groups (11 groups of 5 or 6 tile rows at m = 1024): the device
+    re-partition over groups of unequal size (group offsets, chunking,
+    workspace rows) equals the oracle's plan of the same groups bit for bit,
+    and Y is within the bars, on three calls."""
+    m = k = 1024
+    n = 136
+    cap = wl.nnzb_for(m, k, b, 1 / 16)
+    dt = torch.bfloat16
+    plan = S.Plan(m, k, n, b, w_dtype=S.BF16, mode=S.DYNAMIC, nnzb_max=cap, groups=11)
+    info = plan.info()
+    assert info["n_groups"] == 11 and info["rows_per_group"] == 0
+    for call in range(3):
+        c = wl.dynamic_call(call + 40 * b, m=m, k=k, n=n, b=b, d_max=1 / 16)
+        if call == 2:
+            # one crowded block row (for b = 16 its group is split over
+            # several items and reduced)
+            keep = c["brow"] != 3
+            extra = np.arange(0, k // b, 2, dtype=np.int32)[:cap - int(keep.sum())]
+            c["brow"] = np.concatenate([c["brow"][keep], np.full(len(extra), 3, np.int32)])
+            c["bcol"] = np.concatenate([c["bcol"][keep], extra])
+            c["vals"] = np.concatenate([c["vals"][keep],
+                                        np.ones((len(extra), b, b), np.float32)])
+        vals = torch.from_numpy(c["vals"]).to(dt)
+        X = torch.from_numpy(c["X"]).to(dt)
+        vd = torch.zeros((cap, b, b), dtype=dt)
+        vd[:len(vals)] = vals
+        Y = plan.run(X.cuda(), values=vd.cuda(), pattern=_dev_pattern(c["brow"], c["bcol"], cap))
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        info = plan.info()
+        assert info["n_groups"] == 11 and info["rows_per_group"] == 0
+        Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X)
+        A = oracle.spmm(m, k, b, c["brow"], c["bcol"], np.abs(oracle.to_f64(vals)),
+                        np.abs(oracle.to_f64(X)))
+        checks.assert_parity(Y.cpu(), Yo, oracle.block_fro(vals), X, A, dt,
+                             checks.max_terms(c["brow"], b))
+        _check_arrays(plan, m, k, b, c["brow"], c["bcol"])
+        if call == 2 and b == 16:
+            assert info["n_reductions"] > 0

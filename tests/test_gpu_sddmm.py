@@ -192,4 +192,10 @@ def test_sddmm_full_size_sampled(b, d):
     assert plan.status() == 0
     sel = np.random.default_rng(9).choice(len(c["brow"]), size=96, replace=False)
     dWo = oracle.sddmm(m, k, b, c["brow"][sel], c["bcol"][sel], dY, X)
-    _check(dW[torch.from_numpy(sel)], dWo, dY, X, torch.float32)
+    dWs = dW[torch.from_numpy(sel)]
+    _check(dWs, dWo, dY, X, torch.float32)
+    # componentwise: an FP32 sum of n products, rounded once, stays within
+    # 2 (u + n 2^-24) of sum |dY| |X| for every element of every block
+    A = oracle.sddmm(m, k, b, c["brow"][sel], c["bcol"][sel], np.abs(oracle.to_f64(dY)),
+                     np.abs(oracle.to_f64(X)))
+    assert oracle.componentwise_ratio(dWs.cpu(), dWo, A) <= 2 * (2.0 ** -24 + n * 2.0 ** -24)

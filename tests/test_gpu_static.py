@@ -8,6 +8,7 @@ rounded once to the output type, bit for bit.
 import numpy as np
 import pytest
 
+import checks
 import oracle
 from paper_2303_16999_gb300 import spmm as S
 from paper_2303_16999_gb300 import workloads as wl
@@ -199,32 +200,46 @@ def test_not_packed_and_bad_n():
     assert e.value.status == S.ERR_SHAPE
 
 
-def _sub_oracle(c, rows_blk, dt):
-    """Oracle on a subset of block rows (full-size sampled parity)."""
-    b = c["b"]
-    sel = np.isin(c["brow"], rows_blk)
-    remap = {r: i for i, r in enumerate(rows_blk)}
-    brow = np.array([remap[r] for r in c["brow"][sel]], np.int32)
-    vals = torch.from_numpy(c["vals"][sel]).to(dt)
-    X = torch.from_numpy(c["X"]).to(dt)
-    Yo = oracle.spmm(len(rows_blk) * b, c["k"], b, brow, c["bcol"][sel], vals, X)
-    return Yo, oracle.block_fro(vals), X
-
-
 @pytest.mark.parametrize("b", [1, 4, 8, 16])
 def test_full_size_sweep_sampled(b):
     """m = k = 4096, n = 2048 FP16 at d = 1/4, in the launch configuration the
-    benchmark times; 4 sampled block rows checked against the oracle."""
+    benchmark times; 8 sampled block rows checked against the oracle with the
+    normwise, relative and componentwise bars."""
     d = 1 / 4
     c = wl.sweep_case(b, d)
     dt = torch.float16
     plan = S.Plan(4096, 4096, 2048, b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"])
     plan.pack(torch.from_numpy(c["vals"]).to(dt).cuda())
     Y = plan.run(torch.from_numpy(c["X"]).to(dt).cuda()).cpu()
-    rows = [0, 17, 4096 // b // 2, 4096 // b - 1]
-    Yo, wf, X = _sub_oracle(c, rows, dt)
-    Ys = torch.cat([Y[r * b:(r + 1) * b] for r in rows])
-    assert oracle.normwise_err(Ys, Yo, wf, X) <= 4e-3
+    mb = 4096 // b
+    rows = [0, 17, mb // 3, mb // 2, mb // 2 + 1, 2 * mb // 3 + 5, mb - 2, mb - 1]
+    checks.check_rows(Y, rows, 4096, 4096, b, c["brow"], c["bcol"],
+                      torch.from_numpy(c["vals"]).to(dt), torch.from_numpy(c["X"]).to(dt), dt)
+
+
+@pytest.mark.parametrize("b,d", [(1, 1 / 4), (4, 1 / 16), (8, 1 / 8), (16, 1 / 4), (16, 1 / 32)])
+def test_full_size_sweep_integers_exact(b, d):
+    """The sweep's shape (m = k = 4096, n = 2048, FP16) with integer values in
+    [-2, 2] and X in [-1, 1]: every sum is exact in FP32 and every result
+    fits FP16 exactly, so Y must equal the oracle bit for bit.  Every row and
+    column of Y is checked through exact identities (Y c = W X c, r^T Y =
+    r^T W X), and 12 block rows element by element.  The points cover both
+    stage geometries and both launch widths the benchmark uses."""
+    m = k = 4096
+    n = 2048
+    c = wl.integer_problem(8800 + b, m, k, n, b, wl.nnzb_for(m, k, b, d))
+    dt = torch.float16
+    plan = S.Plan(m, k, n, b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"])
+    plan.pack(torch.from_numpy(c["vals"]).to(dt).cuda())
+    Y = plan.run(torch.from_numpy(c["X"]).to(dt).cuda())
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    Y = Y.cpu()
+    checks.exact_identities(Y, m, k, b, c["brow"], c["bcol"], c["vals"], c["X"], seed=b)
+    mb = m // b
+    rows = sorted(set([0, 1, mb // 4, mb // 3, mb // 2, mb // 2 + 1, 2 * mb // 3, 3 * mb // 4,
+                       mb - 3, mb - 2, mb - 1, 7 % mb]))
+    checks.exact_rows(Y, rows, k, b, c["brow"], c["bcol"], c["vals"], c["X"], dt)
 
 
 @pytest.mark.parametrize("n", [1, 32])
@@ -236,11 +251,11 @@ def test_gather_large_small_n_sampled(n):
     dt = torch.float16
     plan = S.Plan(m, k, 32, 1, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"], kernel="gather")
     plan.pack(torch.from_numpy(c["vals"].reshape(-1)).to(dt).cuda())
-    cn = dict(c, X=c["X"][:, :n].copy())
-    Y = plan.run(torch.from_numpy(cn["X"]).to(dt).cuda()).cpu()
-    rows = [0, 4097, 9000, m - 1]
-    Yo, wf, X = _sub_oracle(cn, rows, dt)
-    assert oracle.normwise_err(Y[rows], Yo, wf, X) <= 4e-3
+    Xn = torch.from_numpy(c["X"][:, :n].copy()).to(dt)
+    Y = plan.run(Xn.cuda()).cpu()
+    rows = [0, 4097, 9000, 12000, m - 2, m - 1]
+    checks.check_rows(Y, rows, m, k, 1, c["brow"], c["bcol"],
+                      torch.from_numpy(c["vals"]).to(dt), Xn, dt)
 
 
 @pytest.mark.parametrize("b,d,n,geo", [(16, 1 / 32, 200, 1), (1, 1 / 4, 136, 0), (8, 1 / 4, 256, 0),
