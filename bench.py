@@ -177,6 +177,82 @@ def roof_of(b, nnzb, peaks, kernel):
     return flops, bytes_, bound, max(t_cmp, t_hbm)
 
 
+def roof_time(flops, bytes_, peaks, compute="tensor"):
+    """Roofline time of one launch, max(FLOP / P_compute, bytes / HBM), and
+    which of the two binds ("tensor" or "alu" for compute, else "hbm")."""
+    pc = (peaks["bf16_tflops"] if compute == "tensor" else ALU_PEAK_TFLOPS) * 1e12
+    t_c = flops / pc
+    t_m = bytes_ / (peaks["hbm_gbs"] * 1e9)
+    return (t_c, compute) if t_c >= t_m else (t_m, "hbm")
+
+
+def roofline_obj(launches, peaks, compute="tensor", traffic=None, kernel=None):
+    """Roofline of a set of launches of one kernel, each given as (FLOP,
+    compulsory bytes, measured seconds): frac = sum of the launches'
+    roofline times over the sum of their measured times (a launch's
+    roofline time is max(FLOP / P_compute, bytes / HBM), Section 3's nonzero
+    FLOPs 2 nnzb b^2 n); bound = the roof that holds most of the roofline
+    time; achieved = frac x that roof's peak (the roofline-equivalent rate),
+    with the plain nonzero-FLOP and compulsory-byte rates beside it.  Every
+    input of frac is in the object, so it can be recomputed from it."""
+    roofs = [roof_time(f, b, peaks, compute) for f, b, _ in launches]
+    t_roof = sum(t for t, _ in roofs)
+    t_meas = sum(t for _, _, t in launches)
+    share = {}
+    for t, bd in roofs:
+        share[bd] = share.get(bd, 0.0) + t
+    bound = max(share, key=share.get) if share else "hbm"
+    if bound == "hbm":
+        peak, unit = peaks["hbm_gbs"], "GB/s"
+    elif bound == "alu":
+        peak, unit = ALU_PEAK_TFLOPS, "TFLOP/s"
+    else:
+        peak, unit = peaks["bf16_tflops"], "TFLOP/s"
+    frac = t_roof / t_meas if t_meas > 0 else None
+    flops = sum(f for f, _, _ in launches)
+    bytes_ = sum(b for _, b, _ in launches)
+    out = {"bound": bound, "achieved": round(frac * peak, 2) if frac else None,
+           "peak": round(peak, 1), "unit": unit, "frac": round(frac, 4) if frac else None,
+           "traffic": traffic, "kernel": kernel, "launches": len(launches),
+           "t_roof_us": round(t_roof * 1e6, 3), "t_meas_us": round(t_meas * 1e6, 3),
+           "roof_share": {k: round(v / t_roof, 3) for k, v in share.items()} if t_roof else {},
+           "flop_nz": flops, "bytes_compulsory": bytes_,
+           "achieved_tflops_nz": round(flops / t_meas / 1e12, 2) if t_meas else None,
+           "achieved_gbs_compulsory": round(bytes_ / t_meas / 1e9, 1) if t_meas else None,
+           "definition": "frac = t_roof_us / t_meas_us, t_roof = sum over launches of "
+                         "max(FLOP_nz / P_%s, compulsory bytes / P_hbm); achieved = frac x peak"
+                         % compute}
+    return out
+
+
+def kernel_source_sha16(files=("csrc/k_tc.cu", "csrc/tc_ptx.cuh", "csrc/capi.cpp",
+                               "csrc/plan_host.cpp")):
+    """Hash of the sources that decide what the tensor-core launches read
+    (the kernel and its planner): DRAM traffic taken by ncu stays valid
+    only while this hash is unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2303_16999_gb300", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM traffic per tc_kernel launch of the static sweep step, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum over the 16 launches
+# of one step; the command and the per-launch table are in
+# profiles/tc_kernel_sweep_dram.md).  Used only while the kernel and planner
+# sources hash to `sha16`; otherwise the bench reports traffic null.
+SWEEP_TRAFFIC = {"sha16": None, "bytes_per_launch": None,
+                 "source": "profiles/tc_kernel_sweep_dram.md"}
+
+
+def sweep_traffic():
+    if SWEEP_TRAFFIC["sha16"] and SWEEP_TRAFFIC["sha16"] == kernel_source_sha16():
+        return SWEEP_TRAFFIC["bytes_per_launch"]
+    return None
+
+
 def build_points(torch, S, wl, dev, only=None):
     pts = []
     for b in SWEEP_B:
@@ -207,10 +283,15 @@ def launches_per_run(p):
 _ORACLE_CASE = {}
 
 
-def oracle_sample(target_s, b=16, d=1 / 16):
+def oracle_sample(target_s, b=16, d=1 / 16, threads=1):
     """Times the FP64 oracle on the first block rows of one sweep point,
-    sized to about target_s seconds of single-thread CPU work (only the
-    oracle call itself is timed)."""
+    sized to about target_s seconds of work on ``threads`` host cores.  With
+    several threads the sample's block rows are cut into that many
+    contiguous slices and the unmodified oracle runs on each slice in its
+    own thread at once (the C oracle releases the interpreter lock), i.e.
+    the oracle parallelised over block rows; only the oracle calls are
+    timed."""
+    import concurrent.futures as cf
     import oracle
     import torch
     from paper_2303_16999_gb300 import workloads as wl
@@ -219,24 +300,61 @@ def oracle_sample(target_s, b=16, d=1 / 16):
         c = wl.sweep_case(b, d)
         _ORACLE_CASE[key] = (c, torch.from_numpy(c["X"]).half(), torch.from_numpy(c["vals"]).half())
     c, X, vals = _ORACLE_CASE[key]
+    Xf = oracle.to_f64(X)
+
+    def slices(rows):
+        cuts = [rows * t // threads for t in range(threads + 1)]
+        out = []
+        for lo, hi in zip(cuts[:-1], cuts[1:]):
+            if hi <= lo:
+                continue
+            sel = (c["brow"] >= lo) & (c["brow"] < hi)
+            out.append((hi - lo, (c["brow"][sel] - lo).astype(np.int32), c["bcol"][sel],
+                        vals[sel], int(sel.sum())))
+        return out
 
     def run(rows):
-        sel = c["brow"] < rows
-        br, bc, vv = c["brow"][sel], c["bcol"][sel], vals[sel]
-        t0 = time.perf_counter()
-        oracle.spmm(rows * b, K, b, br, bc, vv, X)
-        dt = time.perf_counter() - t0
-        return dt, 2.0 * int(sel.sum()) * b * b * N
+        parts = slices(rows)
+        with cf.ThreadPoolExecutor(max_workers=len(parts)) as ex:
+            t0 = time.perf_counter()
+            list(ex.map(lambda q: oracle.spmm(q[0] * b, K, b, q[1], q[2], q[3], Xf), parts))
+            dt = time.perf_counter() - t0
+        return dt, 2.0 * sum(q[4] for q in parts) * b * b * N
 
-    dt, fl = run(2)
+    dt, fl = run(max(2, threads))
     rate = fl / max(dt, 1e-9)
-    rows = int(min(M // b, max(1, target_s * rate / max(fl / 2, 1))))
+    per_row = fl / max(2, threads)
+    rows = int(min(M // b, max(threads, target_s * rate / max(per_row, 1))))
     dt, fl = run(rows)
-    return dict(value=fl / dt / 1e12, unit="TFLOP/s", cores=1, kind="oracle",
-                sample="FP64 single-thread oracle on the first %d of %d block rows of the "
-                       "b=%d, d=1/%d, m=k=4096, n=2048 point (%.2f GFLOP, %.1f s)"
-                       % (rows, M // b, b, round(1 / d), fl / 1e9, dt),
+    return dict(value=fl / dt / 1e12, unit="TFLOP/s", cores=threads, kind="oracle",
+                sample="FP64 oracle (%s) on the first %d of %d block rows of the b=%d, d=1/%d, "
+                       "m=k=4096, n=2048 point (%.2f GFLOP, %.1f s)"
+                       % ("single thread" if threads == 1 else
+                          "%d threads, one slice of block rows each" % threads,
+                          rows, M // b, b, round(1 / d), fl / 1e9, dt),
                 seconds=dt, gflop=fl / 1e9)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_leg(target_s=8.0):
+    """The oracle timed on this host: all cores (the reported baseline) and
+    one core beside it."""
+    par = oracle_sample(target_s, b=16, d=1 / 4, threads=host_cores())
+    one = oracle_sample(target_s, b=16, d=1 / 4, threads=1)
+    out = {k: par[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    out["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample")}
+    try:
+        import platform
+        out["host"] = "%s, %d cores visible" % (platform.machine(), host_cores())
+    except Exception:
+        pass
+    return out
 
 
 def reference_arm(args):
@@ -245,17 +363,18 @@ def reference_arm(args):
         return 0
     total = args.steps + args.warmup
     per_step = max(0.05, min(2.0, 120.0 / max(total, 1)))
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle_sample(per_step)
+        oracle_sample(per_step, threads=cores)
     fl = 0.0
     dt = 0.0
     last = None
     for _ in range(args.steps):
-        last = oracle_sample(per_step)
+        last = oracle_sample(per_step, threads=cores)
         fl += last["gflop"] * 1e9
         dt += last["seconds"]
     v = fl / dt / 1e12
-    cpu = dict(value=v, unit="TFLOP/s", cores=1, kind="oracle", sample=last["sample"])
+    cpu = dict(value=v, unit="TFLOP/s", cores=cores, kind="oracle", sample=last["sample"])
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / max(args.steps, 1), "higher_is_better": True,
@@ -290,9 +409,12 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-transposed", action="store_true")
     ap.add_argument("--no-sddmm", action="store_true")
-    ap.add_argument("--refit", action="store_true",
-                    help="also sweep m, n, b, d against cuBLAS dense and refit the speed-up "
-                         "power law (a few minutes; off by default)")
+    ap.add_argument("--no-refit", action="store_true",
+                    help="skip the compact refit of the speed-up power law (m = k in {1024, "
+                         "2048, 4096}, n in {1024, 4096}, every b and d; under a minute)")
+    ap.add_argument("--refit-full", action="store_true",
+                    help="refit on the full grid instead (m = k up to 8192, n up to 16384; a "
+                         "few minutes)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--point", default=None,
                     help="run one sweep point only, 'b:1/d' e.g. 16:4 (profiling); the other "
@@ -314,7 +436,7 @@ def main():
     S.lib()
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = oracle_sample(12.0, b=16, d=1 / 4)  # before the GPU work: no process forks after it
+        cpu = cpu_baseline_leg()  # threads only, before the GPU work
     only = tuple(int(v) for v in args.point.split(":")) if args.point else None
     pts = build_points(torch, S, wl, dev, only)
     stream = torch.cuda.current_stream()
@@ -374,7 +496,7 @@ def main():
     flops_step = sum(2.0 * p["nnzb"] * p["b"] ** 2 * N for p in pts)
     value = job_throughput(flops_step, args.steps, world, t_ms * 1e-3)
 
-    points, fam = [], {}
+    points, tc_launches = [], []
     for i, p in enumerate(pts):
         kern = {1: "plain", 2: "gather", 3: "tc"}[p["kernel"]]
         fl, by, bound, t_roof = roof_of(p["b"], p["nnzb"], peaks, kern)
@@ -384,25 +506,19 @@ def main():
                        "tflops_nz": round(fl / (us * 1e-6) / 1e12, 2),
                        "tflops_dense_equiv": round(2.0 * M * K * N / (us * 1e-6) / 1e12, 2),
                        "gbs_compulsory": round(by / (us * 1e-6) / 1e9, 1),
-                       "bound": bound, "roof_frac": round(t_roof / (us * 1e-6), 3)})
-        f = fam.setdefault(kern, {"t": 0.0, "flops": 0.0, "bytes": 0.0, "bounds": set()})
-        f["t"] += per[i] * 1e-3
-        f["flops"] += fl
-        f["bytes"] += by
-        f["bounds"].add(bound)
-    dom = max(fam, key=lambda k: fam[k]["t"])
-    F = fam[dom]
-    if F["bounds"] == {"hbm"}:
-        ach, pk, unit, bnd = F["bytes"] / F["t"] / 1e9, peaks["hbm_gbs"], "GB/s", "hbm"
-    elif "alu" in F["bounds"]:
-        ach, pk, unit, bnd = F["flops"] / F["t"] / 1e12, ALU_PEAK_TFLOPS, "TFLOP/s", "alu"
-    else:
-        ach, pk, unit, bnd = F["flops"] / F["t"] / 1e12, peaks["bf16_tflops"], "TFLOP/s", "tensor"
-    roofline = {"bound": bnd, "achieved": round(ach, 2), "peak": round(pk, 1), "unit": unit,
-                "frac": round(ach / pk, 4), "traffic": None, "kernel": dom,
-                "share_of_step": round(F["t"] / (sum(v["t"] for v in fam.values())), 3),
-                "peak_source": ("FP32 lanes x clock (152x128x2x2.07 GHz)" if bnd == "alu"
-                                else "%s (MEASURED_PEAKS.json)" % peak_src)}
+                       "bound": bound, "t_roof_us": round(t_roof * 1e6, 3),
+                       "roof_frac": round(t_roof / (us * 1e-6), 3)})
+        if kern == "tc":
+            tc_launches.append((fl, by, us * 1e-6))
+    # the dominant kernel: every product of the step runs on tc_kernel at
+    # these sizes (AUTO takes b = 1 to the tensor cores at n = 2048)
+    roofline = roofline_obj(tc_launches, peaks, "tensor", traffic=sweep_traffic(),
+                            kernel="tc_kernel")
+    roofline["share_of_step"] = round(sum(t for _, _, t in tc_launches) /
+                                      max(sum(per) * 1e-3, 1e-12), 3)
+    roofline["peak_source"] = "%s (MEASURED_PEAKS.json, burst)" % peak_src
+    roofline["traffic_source"] = (SWEEP_TRAFFIC["source"] if roofline["traffic"] is not None
+                                  else "null: no ncu capture of the current kernel sources")
 
     # end to end through the public API with host buffers: spmm_run_host
     # copies X in, runs, copies Y out and synchronises its own stream, so a
@@ -446,17 +562,20 @@ def main():
     if want("gather_small_n"):
         gsmall = run_gather_small_n(torch, S, wl, dev, peaks)
     if want("dynamic", args.no_dynamic):
-        dynamic = run_dynamic(torch, S, wl, dev)
+        dynamic = run_dynamic(torch, S, wl, dev, peaks)
     if want("batched", args.no_batched):
-        batched = run_batched(torch, S, wl, dev)
+        batched = run_batched(torch, S, wl, dev, peaks)
     if want("serving", args.no_serving):
-        serving = run_serving(torch, S, wl, dev)
+        serving = run_serving(torch, S, wl, dev, peaks)
     if want("transposed", args.no_transposed):
-        transposed = run_transposed(torch, S, wl, dev)
+        transposed = run_transposed(torch, S, wl, dev, peaks)
     if want("sddmm", args.no_sddmm):
         sddmm = run_sddmm(torch, S, wl, dev, peaks)
-    if rank == 0 and (args.refit or (args.point is not None and "refit" in args.section)):
-        refit = run_refit(torch, S, wl, dev)
+    if want("refit", args.no_refit):
+        if args.refit_full:
+            refit = run_refit(torch, S, wl, dev)
+        else:
+            refit = run_refit(torch, S, wl, dev, ms=(1024, 2048, 4096), ns=(1024, 4096))
 
     launches = sum(launches_per_run(p) for p in pts) * args.steps
     if rank == 0:
@@ -508,7 +627,7 @@ def graph_time_us(torch, fn, reps, inner=1):
     return statistics.median(ts)
 
 
-def run_dynamic(torch, S, wl, dev, calls=4, reps=10):
+def run_dynamic(torch, S, wl, dev, peaks, calls=4, reps=10):
     """Dynamic mode, m = k = 8192, n = 1024, b = 16, d_max = 1/16, BF16: every
     call carries a fresh pattern (nnzb uniform in [8192, 16384]) and values,
     re-partitioned on the device.  Reports the per-call time, the
@@ -585,12 +704,23 @@ def run_dynamic(torch, S, wl, dev, calls=4, reps=10):
                    "ell_over_static_time": round(t_ell / t_static, 3),
                    "launches_per_call": 2},
            "gpu_launches_per_call": None}
+    # compulsory bytes of a call: values, the pattern (8 B per block), the
+    # block CSR written and read back (8 B per block each way), X and Y
+    def dyn_bytes(nb):
+        return nb * 256 * 2 + nb * 8 + nb * 16 + (k + m) * n * 2
+    out["roofline"] = roofline_obj(
+        [(2.0 * len(i["c"]["brow"]) * 256 * n, dyn_bytes(len(i["c"]["brow"])), t_dyn * 1e-6)
+         for i in inputs], peaks, "tensor", kernel="dynamic call (re-partition + tc_kernel)")
+    out["roofline_ell"] = roofline_obj(
+        [(2.0 * len(i["c"]["brow"]) * 256 * n,
+          int(i["ell"][0].numel()) * (256 * 2 + 4) + (k + m) * n * 2, t_ell * 1e-6)
+         for i in inputs], peaks, "tensor", kernel="ell_kernel (padded slots read)")
     dplan.close()
     splan.close()
     return out
 
 
-def run_batched(torch, S, wl, dev, reps=5):
+def run_batched(torch, S, wl, dev, peaks, reps=5):
     """48 uneven FFN-like products (W 4096 x 16384 / 16384 x 4096, b in {8, 16},
     d in {1/16, 1/8}, n log-uniform in [1, 512]) with E4M3 weights (one FP32
     scale per block) and BF16 X, in one persistent launch (CUDA graph),
@@ -599,6 +729,7 @@ def run_batched(torch, S, wl, dev, reps=5):
     bf = torch.bfloat16
     plans, p32, Xs, Ys, X32, Y32 = [], [], [], [], [], []
     flops = 0.0
+    comp_bytes = 0
     for i in range(48):
         c = wl.batched_case(i)
         v = torch.from_numpy(c["vals"]).to(dev)
@@ -620,6 +751,9 @@ def run_batched(torch, S, wl, dev, reps=5):
         X32.append(xb[:, :n].float().contiguous())
         Y32.append(torch.empty((c["m"], n), dtype=torch.float32, device=dev))
         flops += 2.0 * len(c["brow"]) * c["b"] ** 2 * n
+        nb = len(c["brow"])
+        comp_bytes += nb * c["b"] ** 2 + 8 * nb + 4 * (c["m"] // c["b"] + 1) + \
+            (c["k"] + c["m"]) * n * 2
         del v, codes, scales
     S.spmm_batch_run(plans, Xs, Ys)          # builds the cached schedule outside capture
     torch.cuda.synchronize()
@@ -642,12 +776,18 @@ def run_batched(torch, S, wl, dev, reps=5):
            "speedup_vs_plain_fp32": round(t_32 / t_batch, 2),
            "speedup_vs_sequential": round(t_seq / t_batch, 3),
            "packed_weight_gb": round(w_bytes / 1e9, 3), "gpu_launches": 1}
+    # one launch: its roofline is that of all 48 problems together, compulsory
+    # bytes = E4M3 values + one FP32 scale and one int32 column per block + row
+    # pointers + X once + Y once (BF16)
+    out["roofline"] = roofline_obj([(flops, comp_bytes, t_batch * 1e-6)], peaks, "tensor",
+                                   kernel="tc_kernel (E4M3 weights, 48 problems)")
     for p in plans + p32:
         p.close()
     return out
 
 
-def run_serving(torch, S, wl, dev, per_rate=4000, rates=(0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.2)):
+def run_serving(torch, S, wl, dev, peaks, per_rate=4000,
+                rates=(0.1, 0.25, 0.5, 0.75, 0.9, 1.0, 1.2)):
     """12 resident weights (m = k in {2048, 4096, 8192} x b in {8, 16} x 2
     seeds, d = 1/16, FP16); Poisson requests, n log-uniform in [1, 256],
     aimed uniformly at the weights.  Saturation throughput is measured with a
@@ -705,6 +845,19 @@ def run_serving(torch, S, wl, dev, per_rate=4000, rates=(0.1, 0.25, 0.5, 0.75, 0
                          "mean_requests_per_launch": round(st["mean_requests_per_launch"], 2)})
         out[name] = {"saturation_rps": round(lam, 1), "saturation_tflops_nz": round(sat["tflops_nz"], 3),
                      "rates": rows}
+        # the burst's roofline: every request's nonzero FLOPs against the
+        # tensor peak (FP32 lanes for the plain kernel), and as compulsory
+        # bytes each weight read once for the whole burst plus every
+        # request's X and Y once (host-link time not counted)
+        es = 4 if fp32 else 2
+        used = set(int(w) for w in wb)
+        fl = sum(2.0 * len(ws[w]["brow"]) * ws[w]["b"] ** 2 * int(nn) for w, nn in zip(wb, nb))
+        by = sum(len(ws[w]["brow"]) * (ws[w]["b"] ** 2 * es + 4) + 4 * (ws[w]["m"] // ws[w]["b"] + 1)
+                 for w in used)
+        by += sum((ws[w]["k"] + ws[w]["m"]) * int(nn) * es for w, nn in zip(wb, nb))
+        out[name]["roofline_saturation"] = roofline_obj(
+            [(fl, by, len(wb) / max(lam, 1e-9))], peaks, "alu" if fp32 else "tensor",
+            kernel="serving loop at saturation (%d requests)" % len(wb))
         srv.close()
         for p in plans:
             p.close()
@@ -752,18 +905,23 @@ def run_gather_small_n(torch, S, wl, dev, peaks, reps=15):
                     "tflops_nz": round(2.0 * nnzb * n / us / 1e6, 3)})
     plan.close()
     del flush
+    launches = [(2.0 * nnzb * q["n"], nnzb * 2 + nnzb * 4 + (m + 1) * 4 + (k + m) * q["n"] * 2,
+                 q["us"] * 1e-6) for q in out]
     return {"workload": "b=1 gather kernel, m=k=16384, d=1/16 (16.8 M non-zeros), FP16, small n; "
-                        "L2 evicted (256 MB written and read back) before every timed run", "points": out}
+                        "L2 evicted (256 MB written and read back) before every timed run",
+            "points": out,
+            "roofline_n1": roofline_obj(launches[:1], peaks, "alu", kernel="gather1_kernel n=1"),
+            "roofline": roofline_obj(launches, peaks, "alu", kernel="gather kernels n in {1,4,16,32}")}
 
 
-def run_transposed(torch, S, wl, dev, reps=15,
+def run_transposed(torch, S, wl, dev, peaks, reps=15,
                    cases=((16, 1 / 16), (16, 1 / 4), (8, 1 / 16), (4, 1 / 16), (1, 1 / 16))):
     """Z = W^T.Y against Y = W.X on the same W (sweep points, m = k = 4096,
     n = 2048, FP16; the sweep's X serves as Y).  Both plans run from cold L2
     (256 MB written and read back before every timed run); the events
     bracket the product alone."""
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    out = []
+    out, tr_launches = [], []
     for b, d in cases:
         c = wl.sweep_case(b, d)
         vals = torch.from_numpy(c["vals"]).half().to(dev)
@@ -796,10 +954,14 @@ def run_transposed(torch, S, wl, dev, reps=15,
         row["transposed_over_forward_time"] = round(row["transposed"]["us"] /
                                                     row["forward"]["us"], 3)
         out.append(row)
+        fl, by, _, _ = roof_of(b, len(c["brow"]), peaks, "tc")
+        tr_launches.append((fl, by, row["transposed"]["us"] * 1e-6))
         del vals, X, Y
     del flush
     return {"workload": "Z = W^T.Y vs Y = W.X on one W, m=k=4096, n=2048, FP16; L2 evicted "
-                        "(256 MB written and read back) before every timed run", "points": out}
+                        "(256 MB written and read back) before every timed run", "points": out,
+            "roofline": roofline_obj(tr_launches, peaks, "tensor",
+                                     kernel="transposed products (square W: same bytes)")}
 
 
 def run_sddmm(torch, S, wl, dev, peaks, reps=10,
@@ -811,7 +973,7 @@ def run_sddmm(torch, S, wl, dev, peaks, reps=10,
     tile, so its roofline is the tensor peak on 2 m k n (reported for both
     forms as the dense-equivalent rate)."""
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    out = []
+    out, sd_launches = [], []
     for b, d in cases:
         c = wl.sddmm_problem(sweep_seed_sd(b, d), M, K, N, b, wl.nnzb_for(M, K, b, d))
         dY = torch.from_numpy(c["dY"]).bfloat16().to(dev)
@@ -848,12 +1010,22 @@ def run_sddmm(torch, S, wl, dev, peaks, reps=10,
         else:
             row["tflops_dense_equiv"] = round(dense, 1)
             row["frac_of_tensor_peak"] = round(dense / peaks["bf16_tflops"], 3)
+        # useful work: 2 nnzb b^2 n FLOPs; compulsory bytes dY and X once
+        # (BF16) and dW once (FP32)
+        fl_u = 2.0 * len(c["brow"]) * b * b * N
+        by_u = (M + K) * N * 2 + len(c["brow"]) * b * b * 4 + len(c["brow"]) * 8
+        t_r, bd = roof_time(fl_u, by_u, peaks, "tensor")
+        row["bound"] = bd
+        row["roof_frac"] = round(t_r / (us * 1e-6), 3)
+        sd_launches.append((fl_u, by_u, us * 1e-6))
         out.append(row)
         plan.close()
         del dY, X, dW
     del flush
     return {"workload": "dW = (dY.X^T) on the block mask, m=k=4096, n=2048, BF16 in, FP32 out; "
-                        "L2 evicted before every timed run", "points": out}
+                        "L2 evicted before every timed run", "points": out,
+            "roofline": roofline_obj(sd_launches, peaks, "tensor",
+                                     kernel="sddmm kernels (useful FLOPs)")}
 
 
 def fit_power_law(rows):
@@ -877,7 +1049,8 @@ def run_refit(torch, S, wl, dev, ms=(1024, 2048, 4096, 8192), ns=(256, 1024, 409
     TFLOP/s, both counting the useful 2 m k n d FLOPs, i.e. cuBLAS dense
     time over sparse time at each side's best n; then the power law of
     Section 5 refitted to S, the largest density with S > 1 per (b, m), and
-    cuSPARSE CSR / BSR context at m = k = 4096, n = 2048, d = 1/16.  Timed
+    cuSPARSE CSR / BSR context at m = k = 4096, n = 2048, d = 1/16 (the
+    library's generic SpMM called directly).  Timed
     with CUDA events (median of reps after two warm-up runs), L2 warm on
     both sides alike."""
     def med_us(fn):
@@ -936,27 +1109,22 @@ def run_refit(torch, S, wl, dev, ms=(1024, 2048, 4096, 8192), ns=(256, 1024, 409
     context = {}
     try:
         m, n, d = 4096, 2048, 1 / 16
+        lib = _cusparse()
         X = torch.from_numpy(np.random.default_rng(5).standard_normal((m, n), dtype=np.float32))
-        for b, label in ((1, "cusparse_csr"), (16, "cusparse_bsr")):
+        Xd = X.half().cuda()
+        for b, label in ((1, "cusparse_csr_fp16"), (16, "cusparse_bsr_fp16")):
             c = wl.problem(777 + b, m, m, 0, b, wl.nnzb_for(m, m, b, d))
-            Wd = torch.zeros((m, m), dtype=torch.float32)
-            Wd.view(m // b, b, m // b, b).permute(0, 2, 1, 3)[
-                torch.from_numpy(c["brow"]).long(), torch.from_numpy(c["bcol"]).long()] = \
-                torch.from_numpy(c["vals"])
-            for dt in (torch.float16, torch.float32):
-                try:
-                    if b == 1:
-                        A = Wd.to(dt).to(dev).to_sparse_csr()
-                    else:
-                        A = Wd.to(dt).to(dev).to_sparse_bsr((b, b))
-                    Xd = X.to(dt).to(dev)
-                    us = med_us(lambda: torch.matmul(A, Xd))
-                    context["%s_%s" % (label, "fp16" if dt == torch.float16 else "fp32")] = {
-                        "us": round(us, 1),
-                        "tflops_nz": round(2.0 * len(c["brow"]) * b * b * n / us / 1e6, 2)}
-                except (RuntimeError, NotImplementedError) as ex:
-                    context["%s_%s" % (label, "fp16" if dt == torch.float16 else "fp32")] = \
-                        "unsupported: %s" % str(ex).splitlines()[0][:120]
+            try:
+                if lib is None:
+                    raise RuntimeError("libcusparse.so.12 not found")
+                us = cusparse_spmm_us(torch, lib, m, m, n, b, c["brow"], c["bcol"],
+                                      torch.from_numpy(c["vals"]).half(), Xd)
+                context[label] = {"us": round(us, 1),
+                                  "tflops_nz": round(2.0 * len(c["brow"]) * b * b * n / us / 1e6, 2)}
+            except Exception as ex:  # context only
+                context[label] = "unavailable: %s" % str(ex).splitlines()[0][:160]
+        context["point"] = "m=k=4096, n=2048, d=1/16, FP16 values and X, FP32 compute"
+        context["call"] = "cusparseSpMM (generic API; CSR default algorithm, BSR_ALG1)"
     except Exception as ex:  # context only: never fail the benchmark over it
         context["error"] = str(ex).splitlines()[0][:200]
     return {"workload": "static sweep m=k in %s, n in %s (best over n), b in %s, d in %s, FP16; "
@@ -967,6 +1135,89 @@ def run_refit(torch, S, wl, dev, ms=(1024, 2048, 4096, 8192), ns=(256, 1024, 409
                     "condition": "%.3g * m^%.2f * d^%.2f * b^%.2f > 1" % (cfit, al, be, ga)},
             "thresholds": thresholds, "grid": grid, "cusparse_context": context,
             "seconds": round(time.perf_counter() - t0, 1)}
+
+
+def _cusparse():
+    """libcusparse through ctypes (context numbers only; None if absent)."""
+    import glob
+    cands = ["libcusparse.so.12", "/usr/local/cuda/lib64/libcusparse.so.12"]
+    cands += glob.glob("/usr/local/cuda*/targets/*/lib/libcusparse.so.12")
+    for c in cands:
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    return None
+
+
+def cusparse_spmm_us(torch, lib, m, k, n, b, brow, bcol, vals, X, reps=10):
+    """Median time of one cusparseSpMM call (generic API, FP16 values and
+    X, FP32 compute, row-major dense operands) with W in CSR (b = 1) or BSR
+    (b > 1, row-major blocks) form, on torch's current stream.  Context
+    for the paper's GPU comparison system (Section 5), not part of the
+    product."""
+    vp = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    order = np.lexsort((bcol, brow))
+    mb = m // b
+    rp = np.zeros(mb + 1, np.int32)
+    np.add.at(rp, np.asarray(brow, np.int64) + 1, 1)
+    rp = np.cumsum(rp).astype(np.int32)
+    d_rp = torch.from_numpy(rp).cuda()
+    d_ci = torch.from_numpy(np.asarray(bcol, np.int32)[order]).cuda()
+    d_v = vals[torch.from_numpy(order)].contiguous().cuda()
+    Y = torch.empty((m, n), dtype=torch.float16, device="cuda")
+    h, A, Bd, Cd = vp(), vp(), vp(), vp()
+    chk = []
+
+    def ok(st, what):
+        if st != 0:
+            raise RuntimeError("%s returned %d" % (what, st))
+    ok(lib.cusparseCreate(ctypes.byref(h)), "cusparseCreate")
+    try:
+        ok(lib.cusparseSetStream(h, vp(torch.cuda.current_stream().cuda_stream)), "SetStream")
+        R16F, R32F, I32, BASE0, ROW = 2, 0, 2, 0, 2
+        if b == 1:
+            ok(lib.cusparseCreateCsr(ctypes.byref(A), i64(m), i64(k), i64(len(brow)),
+                                     vp(d_rp.data_ptr()), vp(d_ci.data_ptr()),
+                                     vp(d_v.data_ptr()), I32, I32, BASE0, R16F), "CreateCsr")
+            alg = 0
+        else:
+            ok(lib.cusparseCreateBsr(ctypes.byref(A), i64(mb), i64(k // b), i64(len(brow)),
+                                     i64(b), i64(b), vp(d_rp.data_ptr()), vp(d_ci.data_ptr()),
+                                     vp(d_v.data_ptr()), I32, I32, BASE0, R16F, ROW),
+               "CreateBsr")
+            alg = 14   # CUSPARSE_SPMM_BSR_ALG1
+        ok(lib.cusparseCreateDnMat(ctypes.byref(Bd), i64(k), i64(n), i64(n),
+                                   vp(X.data_ptr()), R16F, ROW), "CreateDnMat B")
+        ok(lib.cusparseCreateDnMat(ctypes.byref(Cd), i64(m), i64(n), i64(n),
+                                   vp(Y.data_ptr()), R16F, ROW), "CreateDnMat C")
+        one, zero = ctypes.c_float(1.0), ctypes.c_float(0.0)
+        sz = ctypes.c_size_t()
+        ok(lib.cusparseSpMM_bufferSize(h, 0, 0, ctypes.byref(one), A, Bd, ctypes.byref(zero), Cd,
+                                       R32F, alg, ctypes.byref(sz)), "SpMM_bufferSize")
+        buf = torch.empty(max(int(sz.value), 16), dtype=torch.uint8, device="cuda")
+
+        def call():
+            ok(lib.cusparseSpMM(h, 0, 0, ctypes.byref(one), A, Bd, ctypes.byref(zero), Cd, R32F,
+                                alg, vp(buf.data_ptr())), "SpMM")
+        for _ in range(2):
+            call()
+        torch.cuda.synchronize()
+        for _ in range(reps):
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            call()
+            e.record()
+            e.synchronize()
+            chk.append(a.elapsed_time(e) * 1e3)
+    finally:
+        for d, f in ((A, "cusparseDestroySpMat"), (Bd, "cusparseDestroyDnMat"),
+                     (Cd, "cusparseDestroyDnMat")):
+            if d.value:
+                getattr(lib, f)(d)
+        lib.cusparseDestroy(h)
+    return statistics.median(chk)
 
 
 def sweep_seed_sd(b, d):

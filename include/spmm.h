@@ -72,8 +72,11 @@ typedef enum { SPMM_STATIC = 0, SPMM_DYNAMIC = 1 } spmm_mode;
 
 typedef enum { SPMM_F32 = 0, SPMM_F16 = 1, SPMM_BF16 = 2, SPMM_E4M3 = 3 } spmm_dtype;
 
-/* Kernel family.  AUTO picks GATHER for b = 1, TC for 16-bit/E4M3 W with
- * b >= 4, PLAIN for FP32 W with b >= 4. */
+/* Kernel family.  AUTO picks, for b = 1: TC for a static plan with 16-bit
+ * W = X type, n_max >= 128, m and k multiples of 16 and on average at least
+ * 4 non-zeros per non-empty 16 x 16 tile (the tensor cores then beat the
+ * gather), else GATHER; for b >= 4: TC for 16-bit or E4M3 W, PLAIN for FP32
+ * W. */
 typedef enum {
     SPMM_KERNEL_AUTO = 0,
     SPMM_KERNEL_PLAIN = 1,   /* plain FP32 CUDA-core kernel: one thread per (row, column), F32 only */
@@ -240,11 +243,17 @@ int64_t spmm_bucket_size(int64_t m, int64_t k, int64_t d_max_num, int64_t d_max_
                          int64_t q_k);
 
 /*
- * spmm_batch_run -- `count` static TC plans with packed values run in ONE
- * persistent launch that walks a shared work queue over (problem, item,
- * n tile).  d_X[i], n[i], ldx[i], d_Y[i], ldy[i] as in spmm_run (ldx/ldy may
- * be NULL for dense n).  All plans must share x_dtype.  Uneven m, k, n, b
- * and density are allowed.  The call is CUDA-graph capturable.
+ * spmm_batch_run -- `count` (<= 64) static TC plans with packed values in
+ * one persistent tensor-core launch per stage geometry among the plans.
+ * The launch's CTAs walk one schedule of (problem, work item, n tile)
+ * units, precomputed on the host when this plan set is first run
+ * (costliest units first) and cached; each CTA takes every gridDim-th unit
+ * of it (no atomic work queue).  Each problem with rows split over several
+ * work items adds one reduction launch.  d_X[i], n[i], ldx[i], d_Y[i],
+ * ldy[i] as in spmm_run (ldx/ldy may be NULL for dense n).  All plans must
+ * share w_dtype and x_dtype; uneven m, k, n, b and density are allowed.
+ * The first call with a plan set allocates its schedule (make it outside
+ * any stream capture); later calls are CUDA-graph capturable.
  */
 spmm_status spmm_batch_run(int32_t count, spmm_plan *const *plans, const void *const *d_X,
                            const int64_t *n, const int64_t *ldx, void *const *d_Y,
@@ -265,10 +274,13 @@ spmm_status spmm_batch_run(int32_t count, spmm_plan *const *plans, const void *c
  *                   (0 or an spmm_status code); NULL keeps it internal.
  * All scratch lives in one file-scope device array of about 14 MB that every
  * GPU loading the library holds until exit; sizes beyond the limits above
- * return SPMM_ERR_SHAPE before anything is enqueued.  Calls share that array
- * (each clears what must start at zero), so calls that overlap on the GPU
- * race: serialise them.  The first call on a device looks up the array's
- * device address; make it before any stream capture.
+ * (or k > 2^30) return SPMM_ERR_SHAPE before anything is enqueued.  Each
+ * device has its own copy of the array, and all calls on one device share
+ * it (each clears what must start at zero): calls that overlap on one
+ * device race, so serialise them.  Outside a stream capture a call looks up
+ * the array's device address afresh (so a reset device is picked up);
+ * inside a capture it uses the address of the last uncaptured call on the
+ * device, so make one uncaptured call on the device before capturing.
  */
 spmm_status spmm_gather_noalloc(int64_t m, int64_t k, spmm_dtype dtype, const int32_t *d_nnzb,
                                 const int32_t *d_brow, const int32_t *d_bcol, int64_t nnzb_max,

@@ -127,9 +127,10 @@ static bool b1_prefers_tc(int64_t m, int64_t k, int64_t n_max, spmm_dtype w, spm
     return pat->nnzb >= 4 * tiles;
 }
 
-// Static tensor-core plans with work for at least a full wave at 16 rows
-// per group: the number of near-equal tile-row groups that best fills the
-// CTA slots (one per SM for two-column-tile launches, two otherwise),
+// Tensor-core plans with work for at least a full wave at 16 rows per
+// group: the number of near-equal tile-row groups that best fills the CTA
+// slots (one per SM for two-column-tile launches, two otherwise; dynamic
+// plans always launch one column tile per CTA, so they pass wide = false),
 // measured by waves x rows per unit, ceil(q U / S) / q; 0 keeps the equal
 // partition.  Groups keep at least 12 rows and a new count must be at least
 // 3 % better.  At m = k = 4096, n = 2048 this gives 19 groups of 13-14 rows

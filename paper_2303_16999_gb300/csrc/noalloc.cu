@@ -13,14 +13,16 @@
 //    until the process exits.
 //  * Limits: m <= 8192, nnzb_max <= 262144, n <= 256; larger requests are
 //    rejected with SPMM_ERR_SHAPE before anything is enqueued.
-//  * All calls share the one array and it keeps the last call's contents.
-//    Each call clears what must start at zero (row counts, counters, the
-//    status word).  Calls that overlap on the GPU (different streams, or
-//    devices sharing nothing but this array's symbol on one device) race on
-//    it: serialise them.
-//  * The first call on a device looks up the array's device address
-//    (cudaGetSymbolAddress, with that device current); make that first call
-//    before any stream capture.
+//  * Each device has its own copy of the array.  All calls on one device
+//    share that copy, and it keeps the last call's contents: each call
+//    clears what must start at zero (row counts, counters, the status
+//    word).  Calls that overlap on one device (different streams, or host
+//    threads without ordering) race on it: serialise them.
+//  * A call looks up the array's device address (cudaGetSymbolAddress, with
+//    the device current) whenever its stream is not being captured, so a
+//    device reset or a re-created context is picked up.  A call inside a
+//    stream capture uses the address of the device's last uncaptured call:
+//    make one call on the device before any stream capture.
 //  * No cudaMalloc, cudaFree or allocating library routine is called.
 #include <cuda_runtime.h>
 
@@ -65,19 +67,26 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void *g_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once
-// per device; the host-side symbol is not a device address).
-cudaError_t scratch_address(void **out) {
+// Device address of the scratch array on the current device (the host-side
+// symbol is not a device address).  Outside a stream capture it is looked up
+// again on every call (no allocation; a reset device gets its new address);
+// inside one, the address of the last uncaptured call on the device is used.
+cudaError_t scratch_address(cudaStream_t s, void **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    if (cs == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_addr[dev] = p;
+    } else if (!g_addr[dev]) {
+        return cudaErrorStreamCaptureUnsupported;
     }
     *out = g_addr[dev];
     return cudaSuccess;
@@ -100,10 +109,12 @@ extern "C" spmm_status spmm_gather_noalloc(int64_t m, int64_t k, spmm_dtype dtyp
     }
     if (m <= 0 || k <= 0 || n < 0 || nnzb_max < 0 || m > kNaMaxRows || nnzb_max > kNaMaxNnzb ||
         n > kNaMaxN || k > (int64_t)1 << 30) {
-        set_error("spmm_gather_noalloc: needs 0 < m <= %lld, 0 <= nnzb_max <= %lld, "
-                  "0 <= n <= %lld (got m=%lld, nnzb_max=%lld, n=%lld)",
-                  (long long)kNaMaxRows, (long long)kNaMaxNnzb, (long long)kNaMaxN, (long long)m,
-                  (long long)nnzb_max, (long long)n);
+        set_error("spmm_gather_noalloc: needs 0 < m <= %lld, 0 < k <= %lld, "
+                  "0 <= nnzb_max <= %lld, 0 <= n <= %lld (got m=%lld, k=%lld, nnzb_max=%lld, "
+                  "n=%lld)",
+                  (long long)kNaMaxRows, (long long)1 << 30, (long long)kNaMaxNnzb,
+                  (long long)kNaMaxN, (long long)m, (long long)k, (long long)nnzb_max,
+                  (long long)n);
         return SPMM_ERR_SHAPE;
     }
     if (ldx < (n > 0 ? n : 1) || ldy < (n > 0 ? n : 1)) {
@@ -115,9 +126,11 @@ extern "C" spmm_status spmm_gather_noalloc(int64_t m, int64_t k, spmm_dtype dtyp
         return SPMM_ERR_ARG;
     }
     void *base = nullptr;
-    cudaError_t e = scratch_address(&base);
+    cudaError_t e = scratch_address((cudaStream_t)stream, &base);
     if (e != cudaSuccess) {
-        set_error("spmm_gather_noalloc: scratch address lookup failed: %s", cudaGetErrorString(e));
+        set_error("spmm_gather_noalloc: scratch address lookup failed: %s (inside a stream "
+                  "capture, make one uncaptured call on the device first)",
+                  cudaGetErrorString(e));
         return SPMM_ERR_CUDA;
     }
     char *sc = (char *)base;
