@@ -157,16 +157,16 @@ def job_throughput(flop_per_rank_step, steps, world, seconds_max):
 
 
 # ---------------------------------------------------------- sweep points
-def roof_of(b, nnzb, peaks, kernel):
-    """Roofline of one product on the kernel that runs it: nonzero FLOPs,
-    compulsory bytes and the bound (the slower of compute-at-peak -- tensor
-    cores for the TC kernel, FP32 lanes for the CUDA-core kernels -- and
-    bytes-over-HBM)."""
+def roof_of(b, nnzb, peaks, kernel, m=M):
+    """Roofline of one product (m rows of Y; fewer for a row slice) on the
+    kernel that runs it: nonzero FLOPs, compulsory bytes and the bound (the
+    slower of compute-at-peak -- tensor cores for the TC kernel, FP32 lanes
+    for the CUDA-core kernels -- and bytes-over-HBM)."""
     flops = 2.0 * nnzb * b * b * N
     es = 2
     vals = nnzb * b * b * es
-    idx = nnzb * 4 + (M // b + 1) * 4
-    xy = (K * N + M * N) * es
+    idx = nnzb * 4 + (m // b + 1) * 4
+    xy = (K * N + m * N) * es
     bytes_ = vals + idx + xy
     t_hbm = bytes_ / (peaks["hbm_gbs"] * 1e9)
     if kernel != "tc":
@@ -253,8 +253,21 @@ def sweep_traffic():
     return None
 
 
-def build_points(torch, S, wl, dev, only=None):
+def row_range(rank, world, m=M, align=16):
+    """This rank's rows of a product split by rows over ``world`` GPUs:
+    near-equal slices on a 16-row grid (the first ones one unit larger)."""
+    units = m // align
+    lo = rank * (units // world) + min(rank, units % world)
+    hi = lo + units // world + (1 if rank < units % world else 0)
+    return lo * align, hi * align
+
+
+def build_points(torch, S, wl, dev, only=None, rows=None):
+    """The 16 sweep products; with ``rows`` each plan covers that slice of
+    Y's rows only (strong scaling: the whole W's pattern and values are
+    passed, the plan keeps its blocks)."""
     pts = []
+    mr = M if rows is None else rows[1] - rows[0]
     for b in SWEEP_B:
         for d in SWEEP_D:
             if only is not None and (b, round(1 / d)) != only:
@@ -262,13 +275,15 @@ def build_points(torch, S, wl, dev, only=None):
             c = wl.sweep_case(b, d)
             vals = torch.from_numpy(c["vals"]).half()
             X = torch.from_numpy(c["X"]).half()
-            plan = S.Plan(M, K, N, b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"])
+            plan = S.Plan(M, K, N, b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"], rows=rows)
             plan.pack(vals.to(dev))
-            pts.append(dict(b=b, d=d, nnzb=len(c["brow"]), plan=plan, X=X.to(dev),
-                            Y=torch.empty((M, N), dtype=torch.float16, device=dev),
+            info = plan.info()
+            pts.append(dict(b=b, d=d, nnzb=info["nnzb"], nnzb_whole=len(c["brow"]), m=mr,
+                            plan=plan, X=X.to(dev),
+                            Y=torch.empty((mr, N), dtype=torch.float16, device=dev),
                             Xh=X.pin_memory(),
-                            Yh=torch.empty((M, N), dtype=torch.float16).pin_memory(),
-                            kernel=plan.info()["kernel"], c=c))
+                            Yh=torch.empty((mr, N), dtype=torch.float16).pin_memory(),
+                            kernel=info["kernel"], c=c))
             del vals
     torch.cuda.synchronize()
     return pts
@@ -386,12 +401,14 @@ def reference_arm(args):
     return 0
 
 
-def workload_config():
+def workload_config(strong=False, world=1):
     return {"workload": "static sweep m=k=4096 n=2048 FP16, b in {1,4,8,16} x d in "
                         "{1/32,1/16,1/8,1/4}, 16 products per step",
             "m": M, "k": K, "n": N, "block_sizes": list(SWEEP_B),
             "densities": ["1/32", "1/16", "1/8", "1/4"], "mode": "static",
-            "parallelism": "replicas (weak)",
+            "parallelism": ("row split over %d GPUs (X replicated, NCCL all-gather of the Y "
+                            "slices after every product)" % world) if strong else
+                           "replicas (weak)",
             "l2": "inputs larger than L2: 16 problems (~0.6 GB) each read once per step"}
 
 
@@ -416,6 +433,10 @@ def main():
                     help="refit on the full grid instead (m = k up to 8192, n up to 16384; a "
                          "few minutes)")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="weak: every rank runs the whole sweep (replicas); strong: every "
+                         "product is split by rows over the ranks (X replicated) and the Y "
+                         "slices are all-gathered after each product")
     ap.add_argument("--point", default=None,
                     help="run one sweep point only, 'b:1/d' e.g. 16:4 (profiling); the other "
                          "sections are then skipped unless named by --section")
@@ -438,7 +459,20 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_leg()  # threads only, before the GPU work
     only = tuple(int(v) for v in args.point.split(":")) if args.point else None
-    pts = build_points(torch, S, wl, dev, only)
+    strong = args.scaling == "strong"
+    rows = row_range(rank, world) if strong and world > 1 else None
+    pts = build_points(torch, S, wl, dev, only, rows)
+    gather = None
+    if strong and world > 1:
+        import torch.distributed as dist
+        if M % (16 * world):
+            raise SystemExit("--scaling strong needs m = %d to split into equal 16-row slices "
+                             "over %d ranks" % (M, world))
+        full = [torch.empty((M, N), dtype=torch.float16, device=dev) for _ in pts]
+
+        def gather():
+            for p, f in zip(pts, full):
+                dist.all_gather_into_tensor(f, p["Y"])
     stream = torch.cuda.current_stream()
 
     # each product is captured once in its own CUDA graph; a step replays the
@@ -466,6 +500,8 @@ def main():
             g.replay()
             if evs is not None:
                 evs[i][1].record()
+        if gather is not None:
+            gather()
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -494,12 +530,18 @@ def main():
     per = [statistics.median(evs[s_][i][0].elapsed_time(evs[s_][i][1])
                              for s_ in range(args.steps)) for i in range(len(pts))]
     flops_step = sum(2.0 * p["nnzb"] * p["b"] ** 2 * N for p in pts)
-    value = job_throughput(flops_step, args.steps, world, t_ms * 1e-3)
+    if strong:
+        # the whole problems once per step, whatever the number of ranks
+        flops_job = sum(2.0 * p["nnzb_whole"] * p["b"] ** 2 * N for p in pts)
+        value = flops_job * args.steps / (t_ms * 1e-3) / 1e12
+    else:
+        flops_job = flops_step * world
+        value = job_throughput(flops_step, args.steps, world, t_ms * 1e-3)
 
     points, tc_launches = [], []
     for i, p in enumerate(pts):
         kern = {1: "plain", 2: "gather", 3: "tc"}[p["kernel"]]
-        fl, by, bound, t_roof = roof_of(p["b"], p["nnzb"], peaks, kern)
+        fl, by, bound, t_roof = roof_of(p["b"], p["nnzb"], peaks, kern, p["m"])
         us = per[i] * 1e3
         points.append({"b": p["b"], "d": "1/%d" % round(1 / p["d"]), "kernel": kern,
                        "us": round(us, 2),
@@ -545,7 +587,7 @@ def main():
     e2e_pass(args.e2e_steps)
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, world)
-    e2e = {"value": job_throughput(flops_step, args.e2e_steps, world, e2e_s), "unit": "TFLOP/s",
+    e2e = {"value": flops_job * args.e2e_steps / e2e_s / 1e12, "unit": "TFLOP/s",
            "h2d_bytes_per_step": sum(p["Xh"].numel() * 2 for p in pts),
            "d2h_bytes_per_step": sum(p["Yh"].numel() * 2 for p in pts),
            "steps": args.e2e_steps, "host_threads": workers}
@@ -582,8 +624,8 @@ def main():
         line = {"metric": METRIC, "value": round(value, 3), "unit": "TFLOP/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(t_ms / args.steps, 4), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f16 (fp32 accumulate)",
-                "data": "synthetic", "config": workload_config(),
+                "scaling": args.scaling, "vs_baseline": None, "dtype": "f16 (fp32 accumulate)",
+                "data": "synthetic", "config": workload_config(strong, world),
                 "e2e": e2e, "gpu_launches": launches, "clocks": sampler.summary(),
                 "roofline": roofline, "cpu_baseline": cpu, "points": points,
                 "comparators": comparators, "dynamic": dynamic, "batched": batched,

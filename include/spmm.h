@@ -122,6 +122,22 @@ typedef struct {
                                      rows_per_group rows.  0 = planner's choice.  Plan info then
                                      reports rows_per_group = 0 and n_groups = groups.  Not combined
                                      with rows_per_group; SPMM_ERR_ARG if out of range. */
+    int64_t row_begin, row_end;   /* static plans: a slice of the output rows, rows [row_begin,
+                                     row_end) of Y = W.X (of Z = W^T.Y for transposed plans), for
+                                     running one product row-split over several GPUs (Section 3.2's
+                                     distribution of the non-zeros over workers, X replicated).
+                                     Both multiples of b (of 16 for the TC kernel), 0 <= row_begin
+                                     < row_end <= m, else SPMM_ERR_SHAPE; 0, 0 = all rows.  The
+                                     pattern and values passed are the WHOLE W's: the plan keeps
+                                     the blocks of its block rows (in pattern order, rows counted
+                                     from row_begin), and spmm_pack_values / spmm_run read each
+                                     kept block's values from the whole W's value array.  spmm_run
+                                     writes the slice only: Y is (row_end - row_begin) x n.  The
+                                     whole pattern is validated (a repeated or out-of-range block
+                                     anywhere is SPMM_ERR_PATTERN).  Plan info and arrays describe
+                                     the slice (m = row_end - row_begin); spmm_sddmm on a
+                                     slice writes the kept blocks in the slice's order.
+                                     Dynamic plans: SPMM_ERR_UNSUPPORTED. */
 } spmm_plan_opts;
 
 typedef struct spmm_plan spmm_plan;
@@ -191,6 +207,22 @@ spmm_status spmm_run_host(spmm_plan *plan, const void *h_X, int64_t n, int64_t l
  */
 spmm_status spmm_get_status(spmm_plan *plan, int32_t *device_status);
 
+/*
+ * spmm_plan_set_wait -- failure detection of the tensor-core launches (the
+ * product and spmm_batch_run, which takes the first plan's setting).  Every
+ * wait of such a launch on its copy / MMA pipeline is bounded: once a wait
+ * has lasted `limit_ns` (0 = the default, 2 s) the CTA records
+ * SPMM_ERR_TIMEOUT in the plan's status word, stops, lets its copies and
+ * MMAs in flight complete, frees its tensor memory and exits; Y is then not
+ * to be trusted, and spmm_get_status reports the timeout.  The context
+ * stays usable and the next call runs normally.  stall = 1 is a test hook:
+ * after their first stage the MMA warps wait on a barrier that nothing
+ * arrives on, so that every CTA takes the timeout path after limit_ns
+ * (use a short limit).  This library's own extension, not in the paper.
+ * Returns SPMM_ERR_ARG for a NULL plan, limit_ns < 0 or stall not 0/1.
+ */
+spmm_status spmm_plan_set_wait(spmm_plan *plan, int64_t limit_ns, int32_t stall);
+
 /* Plan facts for reporting and tests. */
 typedef struct {
     int64_t m, k, n_max, nnzb, nnzb_max;
@@ -200,6 +232,7 @@ typedef struct {
     int64_t device_bytes;         /* device memory the plan holds */
     int32_t stage_geometry;       /* TC: 0 dense-tile stages, 1 sparse-tile stages (other kernels: 0) */
     int32_t sddmm_form;           /* spmm_sddmm on this plan: 0 dense tiles, 1 gathered blocks */
+    int64_t row_begin, row_end;   /* the plan's slice of output rows (0, m for a whole plan) */
 } spmm_plan_info;
 
 spmm_status spmm_plan_get_info(const spmm_plan *plan, spmm_plan_info *info);
@@ -223,8 +256,11 @@ typedef enum {
     SPMM_ARR_BLK_OFF = 11,  /* TC: int32[nnzb] offset (row*16 + col) of the block in its tile */
     SPMM_ARR_WS_ROW0 = 12,  /* int64[n_ws_slots] first workspace row of each split item */
     SPMM_ARR_RED = 13,      /* int32[n_reductions * 3]: group/row, first ws slot, n_chunks */
-    SPMM_ARR_ENT_COVER = 14 /* TC: int32[n_entries]: bits 0-15 rows covered by the entry's MMA
+    SPMM_ARR_ENT_COVER = 14,/* TC: int32[n_entries]: bits 0-15 rows covered by the entry's MMA
                                intervals, bits 16-31 the rows where an interval starts */
+    SPMM_ARR_SRC_INDEX = 15 /* row-slice plans: int32[nnzb] index in the whole pattern of each
+                               block the slice keeps (the slice's pattern order); whole plans:
+                               empty */
 } spmm_array;
 
 /* Copies array `which` into host memory `dst` (capacity in elements) and

@@ -302,3 +302,36 @@ def tile_values(b, ntiles, blk_slot, blk_off, vals):
         i0, j0 = divmod(int(blk_off[p]), TILE)
         out[blk_slot[p], i0:i0 + b, j0:j0 + b] = v[p]
     return out
+
+
+# ------------------------------------------------------------ row slices ----
+def row_slice(brow, bcol, b, row_begin, row_end):
+    """One worker's share of a product split by rows of W (Section 3.2
+    distributes W's non-zeros over workers; here each worker owns whole rows
+    and X is replicated): the blocks whose rows lie in [row_begin, row_end),
+    kept in the pattern's order with their block rows counted from
+    row_begin, and the pattern index of each kept block.  Returns
+    (brow_slice, bcol_slice, src_index) as int32 arrays."""
+    if row_begin % b or row_end % b or not 0 <= row_begin < row_end:
+        raise ValueError("slice bounds must be multiples of b with row_begin < row_end")
+    r0, r1 = row_begin // b, row_end // b
+    keep = [p for p in range(len(brow)) if r0 <= int(brow[p]) < r1]
+    return (np.array([int(brow[p]) - r0 for p in keep], np.int32),
+            np.array([int(bcol[p]) for p in keep], np.int32),
+            np.array(keep, np.int32))
+
+
+def row_split(m, b, workers, align=TILE):
+    """Row ranges of ``workers`` near-equal slices of m rows, each boundary a
+    multiple of ``align`` (and of b): the first m_a % workers slices get one
+    more unit of ``align`` rows than the rest, m_a = m / align."""
+    unit = max(align, b)
+    if m % unit:
+        raise ValueError("m must be a multiple of the alignment")
+    units = m // unit
+    sizes = [units // workers + (1 if w < units % workers else 0) for w in range(workers)]
+    out, acc = [], 0
+    for s in sizes:
+        out.append((acc * unit, (acc + s) * unit))
+        acc += s
+    return out

@@ -349,6 +349,80 @@ spmm_status spmm_plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spm
     return st;
 }
 
+// A row-slice plan (opts row_begin / row_end): the plan of the slice's
+// blocks (those of its block rows, in pattern order, rows counted from
+// row_begin), plus each kept block's index in the whole pattern, through
+// which the whole W's values are gathered before packing.
+static spmm_status plan_create_slice(int64_t m, int64_t k, int64_t n_max, int32_t b,
+                                     spmm_mode mode, spmm_dtype w_dtype, spmm_dtype x_dtype,
+                                     const spmm_pattern *pattern, const spmm_plan_opts &o,
+                                     spmm_plan **out) {
+    *out = nullptr;
+    if (mode != SPMM_STATIC) {
+        set_error("row slices are for static plans");
+        return SPMM_ERR_UNSUPPORTED;
+    }
+    if (!pattern) {
+        set_error("static plans need a pattern");
+        return SPMM_ERR_ARG;
+    }
+    spmm_status st = validate_pattern(m, k, b, pattern->nnzb, pattern->brow, pattern->bcol);
+    if (st != SPMM_OK) return st;
+    const int64_t rb = o.row_begin, re = o.row_end;
+    if (rb < 0 || re <= rb || re > m || rb % b || re % b) {
+        set_error("row slice [%lld, %lld): needs 0 <= row_begin < row_end <= m = %lld, both "
+                  "multiples of b = %d", (long long)rb, (long long)re, (long long)m, b);
+        return SPMM_ERR_SHAPE;
+    }
+    std::vector<int32_t> sb, sc, src;
+    try {
+        // the whole pattern is checked for repeated blocks, so every rank of
+        // a row split accepts or rejects the same pattern
+        const int64_t kb = k / b;
+        std::vector<int64_t> key(pattern->nnzb);
+        for (int64_t p = 0; p < pattern->nnzb; ++p)
+            key[p] = (int64_t)pattern->brow[p] * kb + pattern->bcol[p];
+        std::sort(key.begin(), key.end());
+        if (std::adjacent_find(key.begin(), key.end()) != key.end()) {
+            set_error("pattern: a block is given twice");
+            return SPMM_ERR_PATTERN;
+        }
+        const int32_t r0 = (int32_t)(rb / b), r1 = (int32_t)(re / b);
+        for (int64_t p = 0; p < pattern->nnzb; ++p) {
+            const int32_t r = pattern->brow[p];
+            if (r < r0 || r >= r1) continue;
+            sb.push_back(r - r0);
+            sc.push_back(pattern->bcol[p]);
+            src.push_back((int32_t)p);
+        }
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed while slicing the pattern");
+        return SPMM_ERR_OOM;
+    }
+    spmm_plan_opts o2 = o;
+    o2.row_begin = o2.row_end = 0;
+    const spmm_pattern sub{(int64_t)sb.size(), sb.data(), sc.data()};
+    st = plan_create(re - rb, k, n_max, b, mode, w_dtype, x_dtype, &sub, 0, &o2, out);
+    if (st != SPMM_OK) return st;
+    spmm_plan *p = *out;
+    p->row_begin = rb;
+    p->row_end = re;
+    p->src_index = std::move(src);
+    if (!p->host_only) {
+        const int64_t nb = (int64_t)p->src_index.size();
+        cudaError_t e = upload(p, &p->d_src_index, p->src_index);
+        if (e == cudaSuccess)
+            e = dalloc(p, (char **)&p->d_slice_vals, nb * b * b * (int64_t)dtype_size(w_dtype));
+        if (e == cudaSuccess && w_dtype == SPMM_E4M3) e = dalloc(p, &p->d_slice_scales, nb);
+        if (e != cudaSuccess) {
+            free_plan(p);
+            *out = nullptr;
+            return cuda_fail(e, "row-slice allocation");
+        }
+    }
+    return SPMM_OK;
+}
+
 static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, spmm_mode mode,
                                spmm_dtype w_dtype, spmm_dtype x_dtype, const spmm_pattern *pattern,
                                int64_t nnzb_max, const spmm_plan_opts *opts, spmm_plan **out) {
@@ -357,6 +431,8 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
         return SPMM_ERR_ARG;
     }
     *out = nullptr;
+    if (opts && (opts->row_begin || opts->row_end))
+        return plan_create_slice(m, k, n_max, b, mode, w_dtype, x_dtype, pattern, *opts, out);
     if (n_max < 0 || (mode != SPMM_STATIC && mode != SPMM_DYNAMIC) || w_dtype < SPMM_F32 ||
         w_dtype > SPMM_E4M3 || x_dtype < SPMM_F32 || x_dtype > SPMM_BF16) {
         set_error("bad n_max, mode or dtype");
@@ -611,9 +687,20 @@ static spmm_status do_pack(spmm_plan *p, const void *d_values, const float *d_sc
         set_error("E4M3 values need per-block scales");
         return SPMM_ERR_ARG;
     }
-    cudaError_t e = (p->kernel == SPMM_KERNEL_TC)
-                        ? launch_pack_tiles(p, d_values, d_scales, nullptr, s)
-                        : launch_pack_csr(p, d_values, nullptr, s);
+    cudaError_t e = cudaSuccess;
+    if (p->d_src_index && p->nnzb > 0) {
+        // row-slice plan: the kept blocks' values (and E4M3 scales) from the
+        // whole W's arrays, in the slice's order
+        const int64_t bb = (int64_t)p->b * p->b * (int64_t)dtype_size(p->wdt);
+        e = launch_gather_blocks(d_values, p->d_src_index, p->nnzb, bb, p->d_slice_vals, s);
+        if (e == cudaSuccess && p->wdt == SPMM_E4M3)
+            e = launch_gather_blocks(d_scales, p->d_src_index, p->nnzb, 4, p->d_slice_scales, s);
+        if (e != cudaSuccess) return cuda_fail(e, "row-slice gather");
+        d_values = p->d_slice_vals;
+        if (p->wdt == SPMM_E4M3) d_scales = p->d_slice_scales;
+    }
+    e = (p->kernel == SPMM_KERNEL_TC) ? launch_pack_tiles(p, d_values, d_scales, nullptr, s)
+                                      : launch_pack_csr(p, d_values, nullptr, s);
     if (e != cudaSuccess) return cuda_fail(e, "pack");
     p->packed = true;
     return SPMM_OK;
@@ -780,6 +867,17 @@ spmm_status spmm_run_host(spmm_plan *plan, const void *h_X, int64_t n, int64_t l
     return SPMM_OK;
 }
 
+spmm_status spmm_plan_set_wait(spmm_plan *plan, int64_t limit_ns, int32_t stall) {
+    g_err[0] = 0;
+    if (!plan || limit_ns < 0 || (stall != 0 && stall != 1)) {
+        set_error("set_wait: plan required, limit_ns >= 0, stall 0 or 1");
+        return SPMM_ERR_ARG;
+    }
+    plan->wait_ns = (uint64_t)limit_ns;
+    plan->stall = stall;
+    return SPMM_OK;
+}
+
 spmm_status spmm_get_status(spmm_plan *plan, int32_t *device_status) {
     g_err[0] = 0;
     if (!plan || !device_status || plan->host_only) {
@@ -830,6 +928,8 @@ spmm_status spmm_plan_get_info(const spmm_plan *cp, spmm_plan_info *info) {
     i.device_bytes = p->device_bytes;
     i.stage_geometry = p->kernel == SPMM_KERNEL_TC ? p->tc_geo : 0;
     i.sddmm_form = sddmm_gathers(p) ? 1 : 0;
+    i.row_begin = p->row_end ? p->row_begin : 0;
+    i.row_end = p->row_end ? p->row_end : p->m;
     *info = i;
     return SPMM_OK;
 }
@@ -863,6 +963,7 @@ spmm_status spmm_plan_get_array(spmm_plan *p, spmm_array which, void *dst, int64
         case SPMM_ARR_WS_ROW0: src = hp.ws_row0.data(); n = hp.ws_row0.size(); es = 8; break;
         case SPMM_ARR_RED: src = hp.red.data(); n = hp.red.size(); break;
         case SPMM_ARR_ENT_COVER: src = hp.ent_cover.data(); n = hp.ent_cover.size(); break;
+        case SPMM_ARR_SRC_INDEX: src = p->src_index.data(); n = p->src_index.size(); break;
         default: set_error("unknown array %d", (int)which); return SPMM_ERR_ARG;
     }
     *count = n;

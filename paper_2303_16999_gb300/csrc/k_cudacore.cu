@@ -431,6 +431,47 @@ cudaError_t launch_restride(const void *src, void *dst, int64_t rows, int64_t n,
     return cudaGetLastError();
 }
 
+// Row-slice plans: the kept blocks' values, gathered from the whole
+// pattern's value array into the slice's order before packing.
+template <typename U>
+__global__ void gather_blocks_kernel(const U *__restrict__ src, const int32_t *__restrict__ idx,
+                                     int64_t nblk, int64_t per, U *__restrict__ dst) {
+    pdl_enter();
+    const int64_t total = nblk * per;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = t / per, e = t - q * per;
+        dst[t] = src[(int64_t)idx[q] * per + e];
+    }
+}
+
+cudaError_t launch_gather_blocks(const void *src, const int32_t *idx, int64_t nblk,
+                                 int64_t block_bytes, void *dst, cudaStream_t s) {
+    if (nblk == 0 || block_bytes == 0) return cudaSuccess;
+    const uintptr_t al = (uintptr_t)src | (uintptr_t)dst;
+    int u = 1;
+    for (int c : {16, 8, 4, 2})
+        if (block_bytes % c == 0 && al % c == 0) {
+            u = c;
+            break;
+        }
+    const int64_t per = block_bytes / u;
+    const unsigned g = grid1d(nblk * per, 256) > 8192u ? 8192u : grid1d(nblk * per, 256);
+    switch (u) {
+        case 16: pdl_launch(gather_blocks_kernel<uint4>, dim3(g), dim3(256), 0, s,
+                     (const uint4 *)src, idx, nblk, per, (uint4 *)dst); break;
+        case 8: pdl_launch(gather_blocks_kernel<uint2>, dim3(g), dim3(256), 0, s,
+                    (const uint2 *)src, idx, nblk, per, (uint2 *)dst); break;
+        case 4: pdl_launch(gather_blocks_kernel<uint32_t>, dim3(g), dim3(256), 0, s,
+                    (const uint32_t *)src, idx, nblk, per, (uint32_t *)dst); break;
+        case 2: pdl_launch(gather_blocks_kernel<uint16_t>, dim3(g), dim3(256), 0, s,
+                    (const uint16_t *)src, idx, nblk, per, (uint16_t *)dst); break;
+        default: pdl_launch(gather_blocks_kernel<uint8_t>, dim3(g), dim3(256), 0, s,
+                     (const uint8_t *)src, idx, nblk, per, (uint8_t *)dst); break;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, const int32_t *d_nnzb,
                             cudaStream_t s) {
     const int bb = p->b * p->b;

@@ -193,7 +193,8 @@ constexpr int kXWarp0 = 6, kXWarp1 = 7;                           // X-slab prod
 constexpr int kXWarp2 = 11;                                       // wide sparse: warps 11, 12 as well
 constexpr int kMmaWarpHi = 8;                                     // MMAs of tile rows 8-15
 constexpr int kProducersMax = 5;                                  // W + up to four X
-constexpr unsigned long long kWaitNs = 2000000000ull;             // 2 s per wait
+constexpr unsigned long long kWaitNs = 2000000000ull;             // 2 s: default per wait, and
+                                                                  // every wait of the abort drain
 
 // A stage's MMA program: one word per MMA (slab index in the stage | first
 // W tile in the stage << 4 | first tile row << 12 | rows << 16), so the MMA
@@ -218,6 +219,9 @@ struct StageMeta {
 // Control block after the stages; S = the geometry's stage count.
 template <int S> struct __align__(8) SmemT {
     uint64_t full[S], empty[S], conv[S], accf[kAccBufs], acce[kAccBufs];
+    uint64_t drain;                // abort: one tcgen05.commit per MMA warp
+    uint64_t never;                // failure-detection tests: nothing arrives here
+    unsigned long long wait_ns;    // limit of each pipeline wait
     StageMeta meta[S];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
@@ -228,10 +232,11 @@ template <int S> struct __align__(8) SmemT {
 
 // ------------------------------------------------------------ PTX helpers
 // (generic ones in tc_ptx.cuh)
-// Bounded wait: false after kWaitNs or once another role has aborted.
+// Bounded wait: false after the launch's wait limit or once another role
+// has aborted.
 template <class SM>
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, SM *sm) {
-    return mbar_wait_bounded(b, parity, &sm->abort_flag, kWaitNs);
+    return mbar_wait_bounded(b, parity, &sm->abort_flag, sm->wait_ns);
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
@@ -272,6 +277,10 @@ struct TcBatch {
     int32_t nprob;
     const int32_t *n_items_dev;  // dynamic single problem: item count on the device
     int32_t *status;
+    unsigned long long wait_ns;  // limit of each pipeline wait (the abort drain waits kWaitNs)
+    int32_t stall;               // failure-detection tests: after their first stage the MMA
+                                 // warps wait on a barrier nothing arrives on, so that wait
+                                 // runs out and the CTA takes its abort path
 };
 
 static_assert(sizeof(TcBatch) <= 32764, "kernel parameter space");
@@ -351,6 +360,9 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
             mbar_init(&sm->accf[b], G::mma_warps);    // MMA completion, every MMA warp
             mbar_init(&sm->acce[b], 128);  // every epilogue thread
         }
+        mbar_init(&sm->drain, G::mma_warps);
+        mbar_init(&sm->never, 1);
+        sm->wait_ns = B.wait_ns ? B.wait_ns : kWaitNs;
         sm->abort_flag = 0;
         for (int i = 0; i < kProducersMax; ++i) sm->issued[i] = 0;
         for (int i = 0; i < kMmaWarpsMax; ++i) sm->consumed[i] = 0;
@@ -608,6 +620,14 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
                     stage = 0;
                     phase ^= 1;
                 }
+                if (B.stall) {
+                    // failure-detection tests: a wait that nothing ends
+                    if (lane == 0) w = mbar_wait(&sm->never, 0, sm) ? 1 : 0;
+                    if (!__shfl_sync(0xffffffffu, w, 0)) {
+                        ok = false;
+                        break;
+                    }
+                }
             }
             if (!ok) break;
             if (lane == 0) tc_commit(&sm->accf[ab]);
@@ -703,7 +723,7 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
                 int okp = 1;
                 while (!mbar_try(&sm->accf[ab], aphase)) {
                     __nanosleep(400);
-                    if (sm->abort_flag || gtimer() - t0 > kWaitNs) {
+                    if (sm->abort_flag || gtimer() - t0 > sm->wait_ns) {
                         okp = 0;
                         break;
                     }
@@ -777,20 +797,33 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
     }
 
     __syncthreads();
-    // after an abort, let copies still in flight land before the CTA exits
-    if (threadIdx.x == 0 && sm->abort_flag) {
-        int32_t hi = 0;
-        for (int i = 0; i < G::producers; ++i) hi = max(hi, sm->issued[i]);
-        int32_t lo = sm->consumed[0];
-        for (int i = 1; i < G::mma_warps; ++i) lo = min(lo, sm->consumed[i]);
-        for (int32_t c = lo; c < hi; ++c) {
-            const int s = c % kStages;
-            const uint32_t par = (uint32_t)((c / kStages) & 1);   // kStages = G::stages
-            // stand in for the arrivals of producers that stopped before stage c
-            for (int i = 0; i < G::producers; ++i)
-                if (c >= sm->issued[i]) mbar_arrive(&sm->full[s]);
+    // after an abort, let copies and MMAs still in flight land before TMEM
+    // and shared memory are released (every wait here is bounded by kWaitNs)
+    if (sm->abort_flag) {
+        if (threadIdx.x == 0) {
+            int32_t hi = 0;
+            for (int i = 0; i < G::producers; ++i) hi = max(hi, sm->issued[i]);
+            int32_t lo = sm->consumed[0];
+            for (int i = 1; i < G::mma_warps; ++i) lo = min(lo, sm->consumed[i]);
+            for (int32_t c = lo; c < hi; ++c) {
+                const int s = c % kStages;
+                const uint32_t par = (uint32_t)((c / kStages) & 1);   // kStages = G::stages
+                // stand in for the arrivals of producers that stopped before stage c
+                for (int i = 0; i < G::producers; ++i)
+                    if (c >= sm->issued[i]) mbar_arrive(&sm->full[s]);
+                const unsigned long long t0 = gtimer();
+                while (!mbar_try(&sm->full[s], par) && gtimer() - t0 < kWaitNs) {
+                }
+            }
+        }
+        // each MMA warp's issuing lane commits once more: the drain barrier
+        // completes when every MMA any of them issued has completed
+        const bool mma_warp = warp == 1 || (warp >= kMmaWarpHi && warp < kMmaWarpHi + G::mma_warps - 1);
+        if (mma_warp && lane == 0) tc_commit(&sm->drain);
+        __syncthreads();
+        if (threadIdx.x == 0) {
             const unsigned long long t0 = gtimer();
-            while (!mbar_try(&sm->full[s], par) && gtimer() - t0 < kWaitNs) {
+            while (!mbar_try(&sm->drain, 0) && gtimer() - t0 < kWaitNs) {
             }
         }
     }
@@ -1146,6 +1179,8 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
     B.nprob = 1;
     B.units = nullptr;
     B.status = p->d_status;
+    B.wait_ns = p->wait_ns;
+    B.stall = p->stall;
     const bool dyn = p->mode == SPMM_DYNAMIC;
     if (wide) B.prob[0].ntn = (B.prob[0].ntn + 1) / 2;   // units of two column tiles
     B.n_items_dev = dyn ? p->d_counts + kCntItems : nullptr;
@@ -1225,6 +1260,8 @@ cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *cons
     B.status = plans[0]->d_status;
     B.n_items_dev = nullptr;
     B.units = nullptr;
+    B.wait_ns = plans[0]->wait_ns;
+    B.stall = plans[0]->stall;
     if (!schedule) {
         // problems in submission order (serving: every launch is a new mix)
         const bool bf16 = plans[0]->xdt == SPMM_BF16, w8 = plans[0]->wdt == SPMM_E4M3;

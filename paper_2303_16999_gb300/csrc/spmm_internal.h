@@ -124,6 +124,17 @@ struct spmm_plan {
     int64_t xbuf_bytes = 0, ybuf_bytes = 0;
     int64_t device_bytes = 0;
     int sm_count = 0;
+    // row-slice plans: the slice of output rows and, for each kept block (the
+    // slice's pattern order), its index in the whole pattern; values are
+    // gathered into d_slice_vals (and E4M3 scales into d_slice_scales)
+    // before packing
+    int64_t row_begin = 0, row_end = 0;
+    std::vector<int32_t> src_index;
+    int32_t *d_src_index = nullptr;
+    void *d_slice_vals = nullptr;
+    float *d_slice_scales = nullptr;
+    uint64_t wait_ns = 0;          // TC launches: limit of each device wait (0: 2 s)
+    int32_t stall = 0;             // TC launches: failure-detection test hook (see spmm.h)
     cudaStream_t last_stream = nullptr;
     cudaEvent_t done = nullptr;
     bool ran = false;
@@ -135,6 +146,9 @@ namespace spmm {
 // kernel launchers (return cudaSuccess or the launch error)
 cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, const int32_t *d_nnzb,
                             cudaStream_t s);
+// dst block q = src block idx[q], nblk blocks of block_bytes bytes each
+cudaError_t launch_gather_blocks(const void *src, const int32_t *idx, int64_t nblk,
+                                 int64_t block_bytes, void *dst, cudaStream_t s);
 cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const float *d_scales,
                               const int32_t *d_nnzb, cudaStream_t s);
 cudaError_t launch_plain(const spmm_plan *p, const void *d_X, int64_t n, int64_t ldx, void *d_Y,

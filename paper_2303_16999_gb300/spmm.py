@@ -29,7 +29,7 @@ KERNEL_AUTO, KERNEL_PLAIN, KERNEL_GATHER, KERNEL_TC = 0, 1, 2, 3
 KERNELS = {"auto": 0, "plain": 1, "gather": 2, "tc": 3}
 ARRAYS = {"row_ptr": 0, "col_idx": 1, "perm": 2, "items": 3, "grp_row0": 4, "grp_rows": 5,
           "grp_ebeg": 6, "ent_col": 7, "ent_tbeg": 8, "tile_row": 9, "blk_slot": 10,
-          "blk_off": 11, "ws_row0": 12, "red": 13, "ent_cover": 14}
+          "blk_off": 11, "ws_row0": 12, "red": 13, "ent_cover": 14, "src_index": 15}
 
 # exported symbols of include/spmm_serve.h
 SERVE_EXPORTS = ["serve_create", "serve_register_weight", "serve_submit", "serve_wait",
@@ -40,7 +40,7 @@ EXPORTS = ["spmm_plan_create", "spmm_pack_values", "spmm_run", "spmm_run_host",
            "spmm_get_status", "spmm_plan_get_info", "spmm_plan_get_array",
            "spmm_plan_destroy", "spmm_equal_partition", "spmm_bucket_size", "spmm_batch_run",
            "spmm_last_error", "spmm_version", "spmm_gather_noalloc", "spmm_quantize_e4m3",
-           "spmm_sddmm", "spmm_run_ell"]
+           "spmm_sddmm", "spmm_run_ell", "spmm_plan_set_wait"]
 
 
 class SpmmError(RuntimeError):
@@ -62,7 +62,8 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("rows_per_group", ctypes.c_int32),
                 ("max_per_item", ctypes.c_int32), ("host_only", ctypes.c_int32),
                 ("transposed", ctypes.c_int32), ("col_tiles", ctypes.c_int32),
-                ("groups", ctypes.c_int64)]
+                ("groups", ctypes.c_int64), ("row_begin", ctypes.c_int64),
+                ("row_end", ctypes.c_int64)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -71,7 +72,8 @@ class PlanInfo(ctypes.Structure):
                                       "rows_per_group", "max_per_item")] + \
         [(n, ctypes.c_int64) for n in ("n_items", "n_groups", "n_entries", "n_tiles",
                                       "ws_rows", "n_reductions", "device_bytes")] + \
-        [(n, ctypes.c_int32) for n in ("stage_geometry", "sddmm_form")]
+        [(n, ctypes.c_int32) for n in ("stage_geometry", "sddmm_form")] + \
+        [(n, ctypes.c_int64) for n in ("row_begin", "row_end")]
 
 
 class ServeConfig(ctypes.Structure):
@@ -122,6 +124,7 @@ def lib():
         L.spmm_sddmm.argtypes = [vp, ctypes.POINTER(DPattern), vp, i64, vp, i64, i64, vp, i32,
                                  vp]
         L.spmm_run_ell.argtypes = [vp, vp, i32, vp, vp, i64, i64, vp, i64, vp]
+        L.spmm_plan_set_wait.argtypes = [vp, i64, i32]
         L.spmm_last_error.restype = ctypes.c_char_p
         L.spmm_version.restype = ctypes.c_char_p
         L.serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
@@ -167,6 +170,10 @@ def spmm_run(plan, d_values, d_scales, dpat, d_X, n, ldx, d_Y, ldy, stream):
 
 def spmm_run_host(plan, h_X, n, ldx, h_Y, ldy, stream):
     return _check(lib().spmm_run_host(plan, h_X, n, ldx, h_Y, ldy, stream))
+
+
+def spmm_plan_set_wait(plan, limit_ns, stall):
+    return _check(lib().spmm_plan_set_wait(plan, limit_ns, stall))
 
 
 def spmm_get_status(plan):
@@ -277,15 +284,19 @@ class Plan:
 
     ``col_tiles``: 128-column tiles of n per tensor-core CTA (0 automatic,
     1, or 2 where the launch allows it), as ``spmm_plan_opts.col_tiles``;
-    ``groups``: near-equal tile-row groups, as ``spmm_plan_opts.groups``."""
+    ``groups``: near-equal tile-row groups, as ``spmm_plan_opts.groups``;
+    ``rows=(row_begin, row_end)``: a static plan of that slice of the output
+    rows (the pattern and values passed stay the whole W's; ``run`` returns
+    the slice's rows only), as ``spmm_plan_opts.row_begin / row_end``."""
 
     def __init__(self, m, k, n_max, b, w_dtype=F16, x_dtype=None, brow=None, bcol=None,
                  mode=STATIC, nnzb_max=0, kernel="auto", rows_per_group=0, max_per_item=0,
-                 host_only=False, transposed=False, col_tiles=0, groups=0):
+                 host_only=False, transposed=False, col_tiles=0, groups=0, rows=None):
         x_dtype = w_dtype if x_dtype is None else x_dtype
+        rb, re = rows if rows is not None else (0, 0)
         opts = PlanOpts(KERNELS[kernel] if isinstance(kernel, str) else kernel,
                         rows_per_group, max_per_item, 1 if host_only else 0,
-                        1 if transposed else 0, col_tiles, groups)
+                        1 if transposed else 0, col_tiles, groups, rb, re)
         pat = None
         self._keep = None
         if mode == STATIC:
@@ -296,6 +307,8 @@ class Plan:
         self.h = spmm_plan_create(m, k, n_max, b, mode, w_dtype, x_dtype, pat, nnzb_max, opts)
         if transposed:
             m, k = k, m                       # the operator the plan applies is k x m
+        if rows is not None:
+            m = re - rb                       # the plan writes its slice of rows only
         self.m, self.k, self.n_max, self.b = m, k, n_max, b
         self.transposed = transposed
         self.mode, self.w_dtype, self.x_dtype = mode, w_dtype, x_dtype
@@ -342,6 +355,11 @@ class Plan:
 
     def status(self):
         return spmm_get_status(self.h)
+
+    def set_wait(self, limit_ns=0, stall=False):
+        """Limit of each device wait of the tensor-core launches (0: 2 s);
+        stall=True is the failure-detection test hook (see spmm.h)."""
+        spmm_plan_set_wait(self.h, int(limit_ns), 1 if stall else 0)
 
     def run_ell(self, ell_cols, values, X, Y=None, stream=None):
         """Y = W.X for W in Blocked-ELL form: ell_cols (m/16, E) int32 and

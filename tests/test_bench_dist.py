@@ -120,3 +120,12 @@ def test_sweep_traffic_only_for_the_captured_sources():
     finally:
         bench.SWEEP_TRAFFIC.clear()
         bench.SWEEP_TRAFFIC.update(saved)
+
+
+def test_strong_scaling_row_ranges_match_the_oracle_split():
+    """The benchmark's per-rank rows (strong scaling) are the oracle's row
+    split of m on the 16-row grid, for the rank counts the benchmark takes."""
+    from oracle import plan as P
+    bench = _bench()
+    for world in (1, 2, 3, 4, 8):
+        assert [bench.row_range(r, world) for r in range(world)] == P.row_split(4096, 1, world)

@@ -341,3 +341,33 @@ def test_near_equal_groups(b, d, n, ct):
                             col_tiles=ct)
     if pq.info()["n_reductions"] == 0 and p0.info()["n_reductions"] == 0:
         assert torch.equal(Yq, Y0)
+
+
+@pytest.mark.parametrize("b,d,n,ct", [(16, 1 / 4, 512, 1), (1, 1 / 4, 512, 2), (8, 1 / 16, 200, 0)])
+def test_device_wait_times_out_and_recovers(b, d, n, ct):
+    """Failure detection on the device: with the test hook on, the MMA warps
+    of every CTA wait on a barrier nothing arrives on; the wait runs out after
+    its 200 us limit, the CTA records SPMM_ERR_TIMEOUT, lets its copies and
+    MMAs land, frees its tensor memory and exits.  The context stays usable:
+    the next call, with the default limit, is correct against the oracle.
+    Covers one and two column tiles per CTA and both stage geometries."""
+    m = k = 1024
+    c = wl.problem(6100 + b, m, k, n, b, wl.nnzb_for(m, k, b, d))
+    dt = torch.float16
+    vals = torch.from_numpy(c["vals"]).to(dt)
+    X = torch.from_numpy(c["X"]).to(dt)
+    plan = S.Plan(m, k, n, b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"], kernel="tc",
+                  col_tiles=ct)
+    plan.pack(vals.cuda())
+    Xd = _x_dev(X, dt, ((n + 7) // 8) * 8)
+    plan.set_wait(200_000, stall=True)
+    Y = torch.zeros((m, n), dtype=dt, device="cuda")
+    plan.run(Xd, Y)
+    torch.cuda.synchronize()
+    assert plan.status() == S.ERR_TIMEOUT
+    plan.set_wait(0, stall=False)
+    Y = plan.run(Xd)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X)
+    assert oracle.normwise_err(Y.cpu(), Yo, oracle.block_fro(vals), X) <= 4e-3
