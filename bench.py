@@ -707,6 +707,16 @@ def run_dynamic(torch, S, wl, dev, peaks, calls=4, reps=10):
 
     t_dyn = graph_time_us(torch, calls_fn, reps) / calls
     t_part = graph_time_us(torch, part_fn, reps) / calls
+    # the same calls with the re-partition as a chain of launches
+    cplan = S.Plan(m, k, n, 16, w_dtype=S.BF16, mode=S.DYNAMIC, nnzb_max=cap, dyn_chain=True)
+
+    def chain_fn():
+        for i in inputs:
+            cplan.run(i["X"], Y, values=i["vals"], pattern=i["pat"])
+    t_chain = graph_time_us(torch, chain_fn, reps) / calls
+    if cplan.status() != 0 or dplan.status() != 0:
+        raise RuntimeError("dynamic status %d / %d" % (dplan.status(), cplan.status()))
+    cplan.close()
     i0 = inputs[0]
     splan = S.Plan(m, k, n, 16, w_dtype=S.BF16, brow=i0["c"]["brow"], bcol=i0["c"]["bcol"])
     splan.pack(i0["vals"][:len(i0["c"]["brow"])].contiguous())
@@ -736,6 +746,9 @@ def run_dynamic(torch, S, wl, dev, peaks, calls=4, reps=10):
     out = {"workload": "dynamic m=k=8192 n=1024 b=16 d_max=1/16 BF16, fresh pattern per call",
            "us_per_call": round(t_dyn, 1), "tflops_nz": round(flops / calls / t_dyn / 1e6, 2),
            "repartition_pack_us": round(t_part, 1),
+           "launch_chain_us_per_call": round(t_chain, 1),
+           "repartition": "one cooperative launch (re-partition, packing, stage records), then "
+                          "the product launch",
            "static_same_pattern_us": round(t_static, 1),
            "dynamic_same_pattern_us": round(t_dyn0, 1),
            "dynamic_over_static_time": round(t_dyn0 / t_static, 3),
@@ -745,7 +758,9 @@ def run_dynamic(torch, S, wl, dev, peaks, calls=4, reps=10):
                    "widths": widths, "ell_over_csr_time": round(t_ell / t_dyn, 3),
                    "ell_over_static_time": round(t_ell / t_static, 3),
                    "launches_per_call": 2},
-           "gpu_launches_per_call": None}
+           # the cooperative re-partition, tc_kernel, reduce_kernel (it finds
+           # its split rows on the device, so it is launched every call)
+           "gpu_launches_per_call": 3}
     # compulsory bytes of a call: values, the pattern (8 B per block), the
     # block CSR written and read back (8 B per block each way), X and Y
     def dyn_bytes(nb):

@@ -122,6 +122,15 @@ typedef struct {
                                      rows_per_group rows.  0 = planner's choice.  Plan info then
                                      reports rows_per_group = 0 and n_groups = groups.  Not combined
                                      with rows_per_group; SPMM_ERR_ARG if out of range. */
+    int32_t stage_geometry;       /* TC plans: the pipeline's stage shape.  0 = by the plan's tiles
+                                     per entry (at least 8: dense), 1 = dense-tile stages (few X
+                                     slabs, many W tiles), 2 = sparse-tile stages (many slabs, fewer
+                                     tiles).  Results are identical either way; other values
+                                     SPMM_ERR_ARG. */
+    int32_t dyn_chain;            /* dynamic TC plans: 1 = run each call's re-partition, packing and
+                                     stage records as a chain of launches instead of one cooperative
+                                     launch (identical results; the chain is also what runs where the
+                                     device has no cooperative launch).  0 or 1, else SPMM_ERR_ARG. */
     int64_t row_begin, row_end;   /* static plans: a slice of the output rows, rows [row_begin,
                                      row_end) of Y = W.X (of Z = W^T.Y for transposed plans), for
                                      running one product row-split over several GPUs (Section 3.2's

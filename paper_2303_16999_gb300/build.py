@@ -20,6 +20,10 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3",
           "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
+# Per-file flags.  The fused dynamic re-partition reads, in one launch, data
+# that other CTAs wrote earlier in the same launch: its global loads bypass
+# L1 (cache in L2 only), so no CTA can see a stale line.
+PER_FILE = {"k_dynamic.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def sources():
@@ -36,7 +40,8 @@ def _compile(src, extra):
     if os.path.exists(obj) and os.path.getmtime(obj) >= newest and not extra:
         return obj
     lang = ["-x", "cu"] if src.endswith(".cu") else ["-x", "c++"]
-    cmd = [NVCC] + ARCH + COMMON + list(extra) + lang + ["-c", src, "-o", obj]
+    cmd = [NVCC] + ARCH + COMMON + PER_FILE.get(os.path.basename(src), []) + list(extra) + lang + \
+        ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))

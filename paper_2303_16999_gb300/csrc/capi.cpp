@@ -449,11 +449,13 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
     st = check_types(kernel, b, w_dtype, x_dtype, m, k);
     if (st != SPMM_OK) return st;
     if (o.rows_per_group < 0 || o.rows_per_group > kMaxGroupRows || o.max_per_item < 0 ||
-        o.col_tiles < 0 || o.col_tiles > 2 || o.groups < 0 ||
+        o.col_tiles < 0 || o.col_tiles > 2 || o.groups < 0 || o.stage_geometry < 0 ||
+        o.stage_geometry > 2 || o.dyn_chain < 0 || o.dyn_chain > 1 ||
         (o.groups > 0 && (o.rows_per_group || o.groups > m / kTile ||
                           (m / kTile + o.groups - 1) / o.groups > kMaxGroupRows))) {
-        set_error("rows_per_group must be in 0..%d, max_per_item >= 0, col_tiles in 0..2, "
-                  "groups in 0 or ceil(m/16/%d)..m/16 without rows_per_group",
+        set_error("rows_per_group must be in 0..%d, max_per_item >= 0, col_tiles and "
+                  "stage_geometry in 0..2, dyn_chain 0 or 1, groups in 0 or ceil(m/16/%d)..m/16 without "
+                  "rows_per_group",
                   kMaxGroupRows, kMaxGroupRows);
         return SPMM_ERR_ARG;
     }
@@ -552,6 +554,7 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
             p->n_tiles = (int64_t)p->hp.tile_row.size();
             if (kernel == SPMM_KERNEL_TC && p->n_entries > 0)
                 p->tc_geo = tc_geometry((double)p->n_tiles / (double)p->n_entries);
+            if (kernel == SPMM_KERNEL_TC && o.stage_geometry) p->tc_geo = o.stage_geometry - 1;
         } else {
             p->nnzb_max = nnzb_max;
             if (kernel == SPMM_KERNEL_TC) {
@@ -588,6 +591,14 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
                 const double R = (double)p->R;
                 const double hit = 1.0 - std::pow(1.0 - q, R);
                 p->tc_geo = tc_geometry(hit > 0 ? R * q / hit : 0.0);
+                if (o.stage_geometry) p->tc_geo = o.stage_geometry - 1;
+                // one cooperative launch for the re-partition where the device
+                // runs cooperative kernels (else the launch chain)
+                if (!p->host_only) {
+                    int dev = 0;
+                    p->dyn_fused = cudaGetDevice(&dev) == cudaSuccess && dyn_fused_supported(dev) &&
+                                   !o.dyn_chain;
+                }
             } else if (kernel == SPMM_KERNEL_PLAIN) {
                 set_error("dynamic plans use the GATHER (b = 1) or TC (b >= 4) kernels");
                 free_plan(p);
@@ -781,11 +792,18 @@ spmm_status spmm_run(spmm_plan *plan, const void *d_values, const float *d_scale
         }
         // a transposed plan reads W's pattern with rows and columns swapped
         const spmm_dpattern tdp{dpat->d_nnzb, dpat->d_bcol, dpat->d_brow};
-        cudaError_t e = launch_dynamic_partition(plan, plan->transposed ? &tdp : dpat, s);
-        if (e == cudaSuccess)
-            e = plan->kernel == SPMM_KERNEL_TC
-                    ? launch_pack_tiles(plan, d_values, d_scales, dpat->d_nnzb, s)
-                    : launch_pack_csr(plan, d_values, dpat->d_nnzb, s);
+        const spmm_dpattern *pp = plan->transposed ? &tdp : dpat;
+        cudaError_t e = cudaSuccess;
+        if (plan->dyn_fused) {
+            // re-partition, packing and stage records in one cooperative launch
+            e = launch_dynamic_tc_fused(plan, pp, d_values, d_scales, s);
+        } else {
+            e = launch_dynamic_partition(plan, pp, s);
+            if (e == cudaSuccess)
+                e = plan->kernel == SPMM_KERNEL_TC
+                        ? launch_pack_tiles(plan, d_values, d_scales, dpat->d_nnzb, s)
+                        : launch_pack_csr(plan, d_values, dpat->d_nnzb, s);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "dynamic re-partition");
         if (n > 0) {
             st = launch_product(plan, d_X, n, ldx, d_Y, ldy, s);

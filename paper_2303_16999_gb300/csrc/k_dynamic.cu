@@ -21,8 +21,15 @@
 // status word; the product kernels then skip, leaving Y unwritten.
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <atomic>
+
 #include "pdl.cuh"
 #include "spmm_internal.h"
+#include "tc_stage.cuh"
 
 namespace spmm {
 namespace {
@@ -165,20 +172,12 @@ __global__ void dyn_scatter(const int32_t *d_nnzb, const int32_t *brow, const in
     }
 }
 
-// 3. one warp per row: rank of each element among the row's columns (keys
-// are unique unless the pattern repeats a block, which is flagged); for
-// b = 1 the warp also writes its row's items.
-__global__ void dyn_sort_rows(int32_t mb, const int32_t *row_ptr, const int32_t *tmp_col,
-                              const int32_t *tmp_perm, int32_t *col_idx, int32_t *perm,
-                              int32_t *status, int rows_items, const int32_t *row_ibeg,
-                              const int32_t *row_wbeg, const int32_t *row_rbeg,
-                              const int32_t *counts, int32_t *items, int64_t *ws_row0,
-                              int32_t *red) {
-    pdl_enter();
-    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (wid >= mb) return;
-    const int32_t r = (int32_t)wid, beg = row_ptr[r], end = row_ptr[r + 1];
+// One warp orders one row's slots by column: the rank of each element among
+// the row's columns (keys are unique unless the pattern repeats a block,
+// which is flagged).
+__device__ void sort_row(int32_t beg, int32_t end, int lane, const int32_t *tmp_col,
+                         const int32_t *tmp_perm, int32_t *col_idx, int32_t *perm,
+                         int32_t *status) {
     for (int32_t i = beg + lane; i < end; i += 32) {
         const int32_t ci = tmp_col[i];
         int32_t rank = 0;
@@ -193,6 +192,23 @@ __global__ void dyn_sort_rows(int32_t mb, const int32_t *row_ptr, const int32_t 
         col_idx[beg + rank] = ci;
         perm[beg + rank] = tmp_perm[i];
     }
+}
+
+// 3. one warp per row: rank of each element among the row's columns (keys
+// are unique unless the pattern repeats a block, which is flagged); for
+// b = 1 the warp also writes its row's items.
+__global__ void dyn_sort_rows(int32_t mb, const int32_t *row_ptr, const int32_t *tmp_col,
+                              const int32_t *tmp_perm, int32_t *col_idx, int32_t *perm,
+                              int32_t *status, int rows_items, const int32_t *row_ibeg,
+                              const int32_t *row_wbeg, const int32_t *row_rbeg,
+                              const int32_t *counts, int32_t *items, int64_t *ws_row0,
+                              int32_t *red) {
+    pdl_enter();
+    const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (wid >= mb) return;
+    const int32_t r = (int32_t)wid, beg = row_ptr[r], end = row_ptr[r + 1];
+    sort_row(beg, end, lane, tmp_col, tmp_perm, col_idx, perm, status);
     if (!rows_items || lane != 0) return;
     const int64_t C1 = counts[kCntChunk];
     const int32_t L = end - beg, nch = nchunks(L, C1);
@@ -224,16 +240,13 @@ __device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *gr
                            int32_t *grp_wbeg, int64_t *grp_wrow, int32_t *grp_rbeg,
                            int32_t *ent_tbeg, int32_t *counts);
 
-// 4a. per group: bitmap of group rows per tile column -> entry and slot
-// counts; the last block scans the groups
-__global__ void __launch_bounds__(1024) dyn_group_count_scan(
-    int32_t kt, int32_t T, const int32_t *grp_row0, const int32_t *grp_rows,
-    const int32_t *row_ptr, const int32_t *col_idx, int32_t *grp_cnt, int32_t *grp_ebeg,
-    int32_t *grp_sbeg, int32_t *grp_ibeg, int32_t *grp_wbeg, int64_t *grp_wrow,
-    int32_t *grp_rbeg, int32_t *ent_tbeg, int32_t *counts) {
-    pdl_enter();
-    extern __shared__ uint32_t colmask[];
-    const int g = blockIdx.x;
+// The column masks of group g in shared memory (colmask[kt], whole CTA):
+// bit r of colmask[c] is set when tile row r of the group holds a block in
+// tile column c.  [*s0, *s1) receives the group's CSR slots.
+__device__ void group_colmask(int g, int32_t kt, int32_t T, const int32_t *grp_row0,
+                              const int32_t *grp_rows, const int32_t *row_ptr,
+                              const int32_t *col_idx, uint32_t *colmask, int32_t *s0_out,
+                              int32_t *s1_out) {
     for (int32_t c = threadIdx.x; c < kt; c += blockDim.x) colmask[c] = 0;
     __syncthreads();
     const int32_t t0 = grp_row0[g], nrows = grp_rows[g];
@@ -248,6 +261,13 @@ __global__ void __launch_bounds__(1024) dyn_group_count_scan(
         atomicOr(&colmask[col_idx[s] / T], 1u << (lo / T - t0));
     }
     __syncthreads();
+    *s0_out = s0;
+    *s1_out = s1;
+}
+
+// Entries (non-empty tile columns) and slots (non-empty tiles) of group g
+// from its column masks -> grp_cnt[2g], grp_cnt[2g + 1] (whole CTA).
+__device__ void group_counts(int g, int32_t kt, const uint32_t *colmask, int32_t *grp_cnt) {
     int32_t ne = 0, ns = 0;
     for (int32_t c = threadIdx.x; c < kt; c += blockDim.x) {
         ne += colmask[c] != 0;
@@ -267,6 +287,22 @@ __global__ void __launch_bounds__(1024) dyn_group_count_scan(
         grp_cnt[g * 2] = acc[0];
         grp_cnt[g * 2 + 1] = acc[1];
     }
+    __syncthreads();
+}
+
+// 4a. per group: bitmap of group rows per tile column -> entry and slot
+// counts; the last block scans the groups
+__global__ void __launch_bounds__(1024) dyn_group_count_scan(
+    int32_t kt, int32_t T, const int32_t *grp_row0, const int32_t *grp_rows,
+    const int32_t *row_ptr, const int32_t *col_idx, int32_t *grp_cnt, int32_t *grp_ebeg,
+    int32_t *grp_sbeg, int32_t *grp_ibeg, int32_t *grp_wbeg, int64_t *grp_wrow,
+    int32_t *grp_rbeg, int32_t *ent_tbeg, int32_t *counts) {
+    pdl_enter();
+    extern __shared__ uint32_t colmask[];
+    const int g = blockIdx.x;
+    int32_t s0, s1;
+    group_colmask(g, kt, T, grp_row0, grp_rows, row_ptr, col_idx, colmask, &s0, &s1);
+    group_counts(g, kt, colmask, grp_cnt);
     if (!last_block_done(counts + kCntTicketGroups)) return;
     group_scan((int32_t)gridDim.x, grp_rows, grp_cnt, grp_ebeg, grp_sbeg, grp_ibeg, grp_wbeg,
                grp_wrow, grp_rbeg, ent_tbeg, counts);
@@ -332,36 +368,21 @@ __device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *gr
     }
 }
 
-// 4c. per group: entries (ascending tile column), slots (ascending rows, one
-// per tile), block -> slot / offset, items and workspace / reduction records
-__global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *grp_row0,
-                               const int32_t *grp_rows, const int32_t *row_ptr,
-                               const int32_t *col_idx, const int32_t *perm, const int32_t *grp_ebeg,
-                               const int32_t *grp_sbeg, const int32_t *grp_ibeg,
-                               const int32_t *grp_wbeg, const int64_t *grp_wrow,
-                               const int32_t *grp_rbeg, const int32_t *counts, int32_t *ent_col,
-                               int32_t *ent_tbeg, int32_t *ent_cover, int32_t *tile_row,
-                               int32_t *blk_slot, int32_t *blk_off, int32_t *items,
-                               int64_t *ws_row0, int32_t *red) {
-    pdl_enter();
-    extern __shared__ uint32_t sm[];
-    uint32_t *colmask = sm;                 // kt
-    int32_t *ent_of = (int32_t *)(sm + kt); // kt: entry index of each column, slot base in ent_tbeg
-    int32_t *slot_of = ent_of + kt;         // kt: first slot of the column's entry
-    const int g = blockIdx.x;
-    for (int32_t c = threadIdx.x; c < kt; c += blockDim.x) colmask[c] = 0;
-    __syncthreads();
+// Group g's entries (ascending tile column), slots (ascending rows, one per
+// tile), block -> slot / offset, items and workspace / reduction records,
+// from its column masks (whole CTA of 1024 threads; slot_of[kt] in shared
+// memory; [s0, s1) the group's CSR slots).
+__device__ void group_fill(int g, int32_t kt, int32_t T, int32_t b, const int32_t *grp_row0,
+                           const int32_t *grp_rows, const int32_t *row_ptr,
+                           const int32_t *col_idx, const int32_t *perm, const int32_t *grp_ebeg,
+                           const int32_t *grp_sbeg, const int32_t *grp_ibeg,
+                           const int32_t *grp_wbeg, const int64_t *grp_wrow,
+                           const int32_t *grp_rbeg, const int32_t *counts,
+                           const uint32_t *colmask, int32_t *slot_of, int32_t s0, int32_t s1,
+                           int32_t *ent_col, int32_t *ent_tbeg, int32_t *ent_cover,
+                           int32_t *tile_row, int32_t *blk_slot, int32_t *blk_off, int32_t *items,
+                           int64_t *ws_row0, int32_t *red) {
     const int32_t t0 = grp_row0[g], nrows = grp_rows[g];
-    const int32_t s0 = row_ptr[t0 * T], s1 = row_ptr[(t0 + nrows) * T];
-    for (int32_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
-        int32_t lo = t0 * T, hi = (t0 + nrows) * T;
-        while (hi - lo > 1) {
-            const int32_t mid = (lo + hi) >> 1;
-            if (row_ptr[mid] <= s) lo = mid; else hi = mid;
-        }
-        atomicOr(&colmask[col_idx[s] / T], 1u << (lo / T - t0));
-    }
-    __syncthreads();
     // column prefix over entries and slots, in chunks of blockDim (1024)
     int64_t eb = grp_ebeg[g], sb = grp_sbeg[g];
     for (int32_t c0 = 0; c0 < kt; c0 += 1024) {
@@ -372,7 +393,6 @@ __global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *
         const int64_t xs = block_scan(__popc(mk), &ts);
         if (c < kt && mk) {
             const int32_t e = (int32_t)(eb + xe);
-            ent_of[c] = e;
             slot_of[c] = (int32_t)(sb + xs);
             ent_col[e] = c;
             ent_tbeg[e] = (int32_t)(sb + xs);
@@ -403,6 +423,7 @@ __global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *
         blk_slot[p] = slot;
         blk_off[p] = ((br * b) % kTile) * kTile + (bc * b) % kTile;
     }
+    __syncthreads();   // the masks may be reused by the calling CTA after this
     if (threadIdx.x != 0) return;
     // items: near-equal chunks of the group's entries
     const int64_t C = counts[kCntChunk];
@@ -427,6 +448,228 @@ __global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *
         rd[0] = g;
         rd[1] = grp_wbeg[g];
         rd[2] = nch;
+    }
+}
+
+
+// 4c. per group: entries (ascending tile column), slots (ascending rows, one
+// per tile), block -> slot / offset, items and workspace / reduction records
+__global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *grp_row0,
+                               const int32_t *grp_rows, const int32_t *row_ptr,
+                               const int32_t *col_idx, const int32_t *perm, const int32_t *grp_ebeg,
+                               const int32_t *grp_sbeg, const int32_t *grp_ibeg,
+                               const int32_t *grp_wbeg, const int64_t *grp_wrow,
+                               const int32_t *grp_rbeg, const int32_t *counts, int32_t *ent_col,
+                               int32_t *ent_tbeg, int32_t *ent_cover, int32_t *tile_row,
+                               int32_t *blk_slot, int32_t *blk_off, int32_t *items,
+                               int64_t *ws_row0, int32_t *red) {
+    pdl_enter();
+    extern __shared__ uint32_t sm[];
+    uint32_t *colmask = sm;                 // kt
+    int32_t *slot_of = (int32_t *)(sm + kt); // kt: first slot of the column's entry
+    const int g = blockIdx.x;
+    int32_t s0, s1;
+    group_colmask(g, kt, T, grp_row0, grp_rows, row_ptr, col_idx, colmask, &s0, &s1);
+    group_fill(g, kt, T, b, grp_row0, grp_rows, row_ptr, col_idx, perm, grp_ebeg, grp_sbeg,
+               grp_ibeg, grp_wbeg, grp_wrow, grp_rbeg, counts, colmask, slot_of, s0, s1, ent_col,
+               ent_tbeg, ent_cover, tile_row, blk_slot, blk_off, items, ws_row0, red);
+}
+
+// ------------------------------------------------ fused (cooperative) ---
+// Dynamic tensor-core plans run the whole chain above, the value packing and
+// the stage records in ONE cooperative launch: every CTA is resident, and
+// the steps are separated by grid barriers instead of kernel boundaries
+// (each boundary of the chain costs a few microseconds of launch latency;
+// a barrier about one).  The steps and their arithmetic are those of the
+// kernels above, run by the same device functions:
+//   0. zero the row counts and the status word           | barrier
+//   1. validate + block-row histogram (grid over pattern) | barrier
+//   2. CTA 0: row scan -> row_ptr, cursor                 | barrier
+//   3. scatter into rows                                  | barrier
+//   4. per-row rank sort, duplicate check                 | barrier
+//      (a rejected pattern ends the launch here: nothing else is written)
+//   5. per-group column masks -> entry / slot counts      | barrier
+//   6. CTA 0: group scan -> offsets, chunk size           | barrier
+//   7. per-group fill (entries, slots, items, block -> slot; the group's
+//      tiles cleared where blocks do not cover them)      | barrier
+//   8. value packing (grid) and stage records (CTA per work item).
+// Every barrier wait is bounded; on expiry the status word records
+// SPMM_ERR_TIMEOUT and the launch ends (the product launch then skips).
+struct DynFusedArgs {
+    const int32_t *d_nnzb, *brow, *bcol;
+    int64_t cap;
+    int32_t mb, kb, kt, T, b, G;
+    int32_t *row_cnt, *status, *row_ptr, *cursor, *counts, *tmp_col, *tmp_perm, *col_idx, *perm;
+    const int32_t *grp_row0, *grp_rows;
+    int32_t *grp_cnt, *grp_ebeg, *grp_sbeg, *grp_ibeg, *grp_wbeg;
+    int64_t *grp_wrow;
+    int32_t *grp_rbeg;
+    int32_t *ent_col, *ent_tbeg, *ent_cover, *tile_row, *blk_slot, *blk_off, *items;
+    int64_t *ws_row0;
+    int32_t *red;
+    const void *values;      // user-order values (16-bit) or E4M3 codes
+    const float *scales;     // E4M3 block scales
+    void *packed;            // tiles
+    float *tile_scale;       // E4M3 tile scales
+    int32_t w8, tr, seg;     // E4M3 weights; transposed plan; 16-bit vector width (8, 4 or 1)
+    int32_t ent_cap, tiles_cap;
+    int64_t items_cap;
+    uint32_t *srec, *sprog;
+    unsigned long long wait_ns;
+};
+
+__device__ __forceinline__ unsigned long long dyn_timer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier over all CTAs of a cooperative launch (counter + generation
+// in global memory, zeroed before the launch); false when the wait ran out.
+__device__ bool grid_sync(int32_t *count, int32_t *gen, int32_t *status,
+                          unsigned long long limit_ns) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const int32_t g0 = *(volatile int32_t *)gen;
+        __threadfence();
+        if (atomicAdd(count, 1) == (int32_t)gridDim.x - 1) {
+            atomicExch(count, 0);
+            __threadfence();
+            atomicExch(gen, g0 + 1);
+        } else {
+            const unsigned long long t0 = dyn_timer();
+            while (*(volatile int32_t *)gen == g0) {
+                if (dyn_timer() - t0 > limit_ns) {
+                    flag(status, kDevTimeout);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+// Packs this launch's share of the blocks into tiles (grid-stride).
+__device__ void fused_pack(const DynFusedArgs &a, int64_t nnzb, int64_t t0, int64_t stride) {
+    if (a.w8) {
+        pack_tiles_e4m3_range((const uint8_t *)a.values, a.scales, a.blk_slot, a.blk_off, nnzb, a.b,
+                              a.tr, (uint8_t *)a.packed, a.tile_scale, t0, stride);
+        return;
+    }
+    const uint16_t *v = (const uint16_t *)a.values;
+    uint16_t *o = (uint16_t *)a.packed;
+    switch (a.b * 16 + a.seg) {
+        case 16 * 16 + 8: pack_tiles_range<uint16_t, 16, 8>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
+        case 16 * 16 + 1: pack_tiles_range<uint16_t, 16, 1>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
+        case 8 * 16 + 8: pack_tiles_range<uint16_t, 8, 8>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
+        case 8 * 16 + 1: pack_tiles_range<uint16_t, 8, 1>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
+        case 4 * 16 + 4: pack_tiles_range<uint16_t, 4, 4>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
+        case 4 * 16 + 1: pack_tiles_range<uint16_t, 4, 1>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
+        default: pack_tiles_range<uint16_t, 1, 1>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
+    }
+}
+
+__global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_constant__ DynFusedArgs a) {
+    pdl_enter();
+    extern __shared__ uint32_t dsm[];   // colmask[kt], slot_of[kt]
+    __shared__ int32_t bcounts[32];
+    int32_t *bar = a.counts + kCntBarrier, *gen = a.counts + kCntBarrierGen;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t gs = (int64_t)gridDim.x * blockDim.x;
+    const unsigned long long lim = a.wait_ns;
+    // 0.
+    for (int64_t r = gt; r < a.mb; r += gs) a.row_cnt[r] = 0;
+    if (gt == 0) *a.status = 0;
+    if (!grid_sync(bar, gen, a.status, lim)) return;
+    // 1.
+    const int64_t raw = *a.d_nnzb;
+    if (gt == 0 && (raw < 0 || raw > a.cap)) flag(a.status, kDevCapacity);
+    const int64_t n = raw < 0 ? 0 : (raw > a.cap ? a.cap : raw);
+    for (int64_t p = gt; p < n; p += gs) {
+        const int32_t r = a.brow[p], c = a.bcol[p];
+        if (r < 0 || r >= a.mb || c < 0 || c >= a.kb) {
+            flag(a.status, kDevPattern);
+            continue;
+        }
+        atomicAdd(&a.row_cnt[r], 1);
+    }
+    if (!grid_sync(bar, gen, a.status, lim)) return;
+    // 2.
+    if (blockIdx.x == 0)
+        scan_rows(a.d_nnzb, a.cap, a.mb, a.row_cnt, a.row_ptr, a.cursor, nullptr, nullptr, nullptr,
+                  a.counts, 0);
+    if (!grid_sync(bar, gen, a.status, lim)) return;
+    // 3.
+    for (int64_t p = gt; p < n; p += gs) {
+        const int32_t r = a.brow[p], c = a.bcol[p];
+        if (r < 0 || r >= a.mb || c < 0 || c >= a.kb) continue;
+        const int32_t pos = atomicAdd(&a.cursor[r], 1);
+        a.tmp_col[pos] = c;
+        a.tmp_perm[pos] = (int32_t)p;
+    }
+    if (!grid_sync(bar, gen, a.status, lim)) return;
+    // 4.
+    {
+        const int lane = threadIdx.x & 31;
+        for (int64_t r = gt >> 5; r < a.mb; r += gs >> 5) {
+            const int32_t beg = __ldcg(a.row_ptr + r), end = __ldcg(a.row_ptr + r + 1);
+            sort_row(beg, end, lane, a.tmp_col, a.tmp_perm, a.col_idx, a.perm, a.status);
+        }
+    }
+    if (!grid_sync(bar, gen, a.status, lim)) return;
+    if (*(volatile int32_t *)a.status != 0) return;   // every CTA sees the same word here
+    // 5.
+    uint32_t *colmask = dsm;
+    int32_t *slot_of = (int32_t *)(dsm + a.kt);
+    for (int g = blockIdx.x; g < a.G; g += gridDim.x) {
+        int32_t s0, s1;
+        group_colmask(g, a.kt, a.T, a.grp_row0, a.grp_rows, a.row_ptr, a.col_idx, colmask, &s0, &s1);
+        group_counts(g, a.kt, colmask, a.grp_cnt);
+    }
+    if (!grid_sync(bar, gen, a.status, lim)) return;
+    // 6.
+    if (blockIdx.x == 0)
+        group_scan(a.G, a.grp_rows, a.grp_cnt, a.grp_ebeg, a.grp_sbeg, a.grp_ibeg, a.grp_wbeg,
+                   a.grp_wrow, a.grp_rbeg, a.ent_tbeg, a.counts);
+    if (!grid_sync(bar, gen, a.status, lim)) return;
+    // 7.
+    const int64_t tile_bytes = a.w8 ? kTile * kTile : kTile * kTile * 2;
+    for (int g = blockIdx.x; g < a.G; g += gridDim.x) {
+        if (a.b < 16) {
+            // tiles hold several blocks: clear the group's tiles (and E4M3
+            // scales) first; 16 x 16 blocks fill their tile and every scale
+            const int64_t sb = __ldcg(a.grp_sbeg + g);
+            const int64_t se = g + 1 < a.G ? __ldcg(a.grp_sbeg + g + 1)
+                                           : (int64_t)__ldcg(a.counts + kCntSlots);
+            uint4 *t = (uint4 *)((uint8_t *)a.packed + sb * tile_bytes);
+            const int64_t nv = (se - sb) * tile_bytes / 16;
+            for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) t[i] = make_uint4(0, 0, 0, 0);
+            if (a.w8) {
+                float *ts = a.tile_scale + sb * 16;
+                for (int64_t i = threadIdx.x; i < (se - sb) * 16; i += blockDim.x) ts[i] = 0.f;
+            }
+        }
+        int32_t s0, s1;
+        group_colmask(g, a.kt, a.T, a.grp_row0, a.grp_rows, a.row_ptr, a.col_idx, colmask, &s0, &s1);
+        group_fill(g, a.kt, a.T, a.b, a.grp_row0, a.grp_rows, a.row_ptr, a.col_idx, a.perm,
+                   a.grp_ebeg, a.grp_sbeg, a.grp_ibeg, a.grp_wbeg, a.grp_wrow, a.grp_rbeg, a.counts,
+                   colmask, slot_of, s0, s1, a.ent_col, a.ent_tbeg, a.ent_cover, a.tile_row,
+                   a.blk_slot, a.blk_off, a.items, a.ws_row0, a.red);
+        __syncthreads();
+    }
+    if (!grid_sync(bar, gen, a.status, lim)) return;
+    // 8.
+    fused_pack(a, n, gt, gs);
+    const int64_t ni = min(a.items_cap, (int64_t)max(__ldcg(a.counts + kCntItems), 0));
+    for (int64_t item = blockIdx.x; item < ni; item += gridDim.x) {
+        build_item_stages(a.items + item * kItemFields, a.ent_cap, a.tiles_cap, a.ent_col,
+                          a.ent_tbeg, a.ent_cover, a.srec, a.sprog, bcounts);
     }
 }
 
@@ -488,6 +731,93 @@ cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cuda
             p->d_ent_tbeg, p->d_ent_cover, p->d_tile_row, p->d_blk_slot, p->d_blk_off, p->d_items,
             p->d_ws_row0, p->d_red);
     }
+    return cudaGetLastError();
+}
+
+
+bool dyn_fused_supported(int dev) {
+    int coop = 0;
+    return cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) == cudaSuccess && coop;
+}
+
+cudaError_t launch_dynamic_tc_fused(spmm_plan *p, const spmm_dpattern *dp, const void *d_values,
+                                    const float *d_scales, cudaStream_t s) {
+    DynBufs &d = p->dyn;
+    DynFusedArgs a;
+    a.d_nnzb = dp->d_nnzb;
+    a.brow = dp->d_brow;
+    a.bcol = dp->d_bcol;
+    a.cap = p->nnzb_max;
+    a.mb = (int32_t)(p->m / p->b);
+    a.kb = (int32_t)(p->k / p->b);
+    a.kt = (int32_t)(p->k / kTile);
+    a.T = kTile / p->b;
+    a.b = p->b;
+    a.G = (int32_t)p->n_groups;
+    a.row_cnt = d.row_cnt;
+    a.status = p->d_status;
+    a.row_ptr = p->d_row_ptr;
+    a.cursor = d.cursor;
+    a.counts = p->d_counts;
+    a.tmp_col = d.tmp_col;
+    a.tmp_perm = d.tmp_perm;
+    a.col_idx = p->d_col_idx;
+    a.perm = p->d_perm;
+    a.grp_row0 = p->d_grp_row0;
+    a.grp_rows = p->d_grp_rows;
+    a.grp_cnt = d.grp_cnt;
+    a.grp_ebeg = p->d_grp_ebeg;
+    a.grp_sbeg = d.grp_sbeg;
+    a.grp_ibeg = d.grp_ibeg;
+    a.grp_wbeg = d.grp_wbeg;
+    a.grp_wrow = d.grp_wrow;
+    a.grp_rbeg = d.grp_rbeg;
+    a.ent_col = p->d_ent_col;
+    a.ent_tbeg = p->d_ent_tbeg;
+    a.ent_cover = p->d_ent_cover;
+    a.tile_row = p->d_tile_row;
+    a.blk_slot = p->d_blk_slot;
+    a.blk_off = p->d_blk_off;
+    a.items = p->d_items;
+    a.ws_row0 = p->d_ws_row0;
+    a.red = p->d_red;
+    a.values = d_values;
+    a.scales = d_scales;
+    a.packed = p->d_packed;
+    a.tile_scale = p->d_tile_scale;
+    a.w8 = p->wdt == SPMM_E4M3 ? 1 : 0;
+    a.tr = p->transposed ? 1 : 0;
+    // vector copies need aligned values and untransposed blocks
+    const bool al = ((uintptr_t)d_values % 16) == 0 && !p->transposed;
+    a.seg = al ? (p->b >= 8 ? 8 : (p->b == 4 ? 4 : 1)) : 1;
+    stage_caps(p, &a.ent_cap, &a.tiles_cap);
+    a.items_cap = d.items_cap;
+    a.srec = p->d_srec;
+    a.sprog = p->d_sprog;
+    a.wait_ns = p->wait_ns ? p->wait_ns : 2000000000ull;
+    const size_t smem = sizeof(uint32_t) * 2 * (size_t)a.kt;
+    static std::atomic<uint64_t> attrs{0};
+    cudaError_t e = set_smem_attrs_once(attrs, dyn_tc_fused_kernel, (int)smem, false);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dyn_tc_fused_kernel, 1024, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    const int grid = std::min(per_sm * std::max(p->sm_count, 1), 128);
+    e = cudaMemsetAsync(p->d_counts, 0, sizeof(int32_t) * kCntCount, s);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, dyn_tc_fused_kernel, a);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -30,7 +30,9 @@ enum CountIdx : int {
     kCntChunk = 7,    // chunk size C chosen on the device
     kCntTicketRows = 8,    // blocks done with the row histogram (the last one scans)
     kCntTicketGroups = 9,  // blocks done with the group counts (the last one scans)
-    kCntCount = 10
+    kCntBarrier = 10,      // fused re-partition: CTAs arrived at the current grid barrier
+    kCntBarrierGen = 11,   // fused re-partition: grid barriers completed
+    kCntCount = 12
 };
 
 // device status word codes (mirrors spmm_status where applicable)
@@ -133,6 +135,8 @@ struct spmm_plan {
     int32_t *d_src_index = nullptr;
     void *d_slice_vals = nullptr;
     float *d_slice_scales = nullptr;
+    bool dyn_fused = false;        // dynamic TC: re-partition, packing and stage records in one
+                                   // cooperative launch (else the launch chain)
     uint64_t wait_ns = 0;          // TC launches: limit of each device wait (0: 2 s)
     int32_t stall = 0;             // TC launches: failure-detection test hook (see spmm.h)
     cudaStream_t last_stream = nullptr;
@@ -160,6 +164,10 @@ cudaError_t launch_restride(const void *src, void *dst, int64_t rows, int64_t n,
                             size_t elem, cudaStream_t s);
 // TC stage records of every work item (plan arrays only; no values)
 cudaError_t launch_stage_build(const spmm_plan *p, cudaStream_t s);
+// entries (X slabs) and W tiles per stage of the plan's stage geometry
+void stage_caps(const spmm_plan *p, int *ent_cap, int *tiles_cap);
+// the device can run the fused dynamic re-partition (cooperative launches)
+bool dyn_fused_supported(int dev);
 int64_t stage_record_words();
 // TC stage geometry for a plan whose entries hold this many tiles on average
 int tc_geometry(double tiles_per_entry);
@@ -174,6 +182,10 @@ cudaError_t launch_quantize_e4m3(int64_t nnzb, int b, spmm_dtype src, const void
                                  uint8_t *d_codes, float *d_scales, cudaStream_t s);
 constexpr int kMaxBatchProblems = 64;
 cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s);
+// dynamic TC plans: the whole re-partition, the value packing and the stage
+// records in one cooperative launch (when p->dyn_fused)
+cudaError_t launch_dynamic_tc_fused(spmm_plan *p, const spmm_dpattern *dp, const void *d_values,
+                                    const float *d_scales, cudaStream_t s);
 // the block CSR part of the re-partition only (row_ptr, col_idx, perm; validation)
 cudaError_t launch_dynamic_csr(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s);
 // Blocked-ELL product, b = 16 (k_ell.cu): validation + one product launch

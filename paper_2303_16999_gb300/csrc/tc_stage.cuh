@@ -1,0 +1,245 @@
+// Stage records and value packing of the tensor-core plans, shared by the
+// product launches (k_tc.cu) and the fused dynamic re-partition
+// (k_dynamic.cu): one statement of each rule, run by either.  No pointer
+// here is __restrict__: in the fused launch these functions read arrays
+// that other CTAs of the same launch wrote, which the read-only data path
+// must not serve.
+#ifndef SPMM_TC_STAGE_CUH
+#define SPMM_TC_STAGE_CUH
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "spmm_internal.h"
+
+namespace spmm {
+namespace {
+
+constexpr int kRecWords = 16;           // words per stage record
+constexpr int kMmaStage = 32;           // MMAs per stage and row half (one per lane)
+constexpr int kJointSlabs = 4;          // slabs of a joint X box
+// A stage whose entries are 2 to 4 consecutive tile columns (record info
+// bit 20) gets its X slabs in one TMA box of kJointSlabs slabs when X's map
+// is 3-D; the slabs then lie 2048 B apart inside each 64-column half, the
+// halves 8192 B apart.
+constexpr uint32_t kJointBit = 1u << 20;
+constexpr int kBuildWarps = 16;         // warps of a stage_build_kernel CTA
+
+// Stages never span two 32-entry batches of an item, so the batches are cut
+// independently: one CTA per work item, one warp per batch.  A warp cuts
+// its batch exactly as the producers consume it (consecutive entries while
+// the stage holds at most `ent_cap` X slabs, `tiles_cap` W tiles and
+// kMmaStage MMAs per row half; one entry always fits), counts its stages,
+// and after a CTA-wide prefix of the counts writes its records at
+// e0 + (stages of earlier batches) + i, expanding every entry's row
+// intervals (runs of covered rows cut at interval starts) into MMA words:
+// slab | first W tile in the stage << 4 | first tile row << 12 | rows << 16,
+// one list per row half (an interval across row 8 is cut there).  Dynamic
+// plans read the item count and the status word on the device (a rejected
+// pattern builds nothing).
+// One batch of entries: cuts its stages; with `write`, stores their records
+// starting at record index `rec`.  Returns the number of stages.
+__device__ int build_batch(int32_t eb, int32_t e1, int ent_cap, int tiles_cap,
+                           const int32_t *ent_col, const int32_t *ent_tbeg,
+                           const int32_t *ent_cover, bool last_batch, bool write,
+                           int32_t rec, uint32_t *srec, uint32_t *sprog) {
+    const int lane = threadIdx.x & 31;
+    const int32_t e = eb + lane;
+    const bool valid = e < e1;
+    const int32_t mcol = valid ? ent_col[e] : 0;
+    const int32_t mtb = valid ? ent_tbeg[e] : 0;
+    const uint32_t mcov = valid ? (uint32_t)ent_cover[e] : 0u;
+    const uint32_t cov = mcov & 0xFFFFu;
+    // this entry's MMAs per row half: intervals below / above row 8, an
+    // interval across it counting in both
+    int nlo = 0, nhi = 0;
+    for (uint32_t st = mcov >> 16; st; st &= st - 1) {
+        const uint32_t r0 = __ffs(st) - 1;
+        const uint32_t rest = st & (st - 1);
+        const uint32_t next = rest ? (uint32_t)(__ffs(rest) - 1) : 16u;
+        uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;   // run of covered rows
+        len = len < next - r0 ? len : next - r0;
+        nlo += r0 < 8;
+        nhi += r0 + len > 8;
+    }
+    const int mslots = __popc(cov);
+    // inclusive prefix sums over the batch: tiles, MMAs of each half
+    int S = mslots, L = nlo, H = nhi;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int s2 = __shfl_up_sync(0xffffffffu, S, o);
+        const int l2 = __shfl_up_sync(0xffffffffu, L, o);
+        const int h2 = __shfl_up_sync(0xffffffffu, H, o);
+        if (lane >= o) {
+            S += s2;
+            L += l2;
+            H += h2;
+        }
+    }
+    const int cnt = min(32, e1 - eb);
+    int nst = 0;
+    for (int j = 0; j < cnt; ++nst) {
+        // sums are monotone: the fitting lanes are contiguous from j
+        const int Sb = j ? __shfl_sync(0xffffffffu, S, j - 1) : 0;
+        const int Lb = j ? __shfl_sync(0xffffffffu, L, j - 1) : 0;
+        const int Hb = j ? __shfl_sync(0xffffffffu, H, j - 1) : 0;
+        const bool fits = lane >= j && lane < j + ent_cap && lane < cnt && S - Sb <= tiles_cap &&
+                          L - Lb <= kMmaStage && H - Hb <= kMmaStage;
+        const int nent = __popc(__ballot_sync(0xffffffffu, fits));
+        if (write) {
+            const int slots = __shfl_sync(0xffffffffu, S, j + nent - 1) - Sb;
+            const int mlo = __shfl_sync(0xffffffffu, L, j + nent - 1) - Lb;
+            const int mhi = __shfl_sync(0xffffffffu, H, j + nent - 1) - Hb;
+            const int32_t stb = __shfl_sync(0xffffffffu, mtb, j);
+            // record word 3 + i holds the X column of the stage's entry i
+            const int32_t xc = __shfl_sync(0xffffffffu, mcol, min(j + max(lane - 3, 0), 31));
+            const bool last = last_batch && j + nent == cnt;
+            const int32_t r = rec + nst;
+            // 2 to 4 entries on consecutive tile columns: one X box serves the stage
+            const int32_t pcol = __shfl_up_sync(0xffffffffu, mcol, 1);
+            const bool consec = __all_sync(0xffffffffu, !(lane > j && lane < j + nent) ||
+                                                            mcol == pcol + 1);
+            const bool joint = consec && nent >= 2 && nent <= kJointSlabs;
+            if (lane >= j && lane < j + nent) {
+                uint32_t klo = (uint32_t)(L - nlo - Lb), khi = (uint32_t)(H - nhi - Hb);
+                uint32_t toff = (uint32_t)(S - mslots - Sb);
+                const uint32_t slab = (uint32_t)(lane - j);
+                uint32_t *pr = sprog + (int64_t)r * 2 * kMmaStage;
+                for (uint32_t st = mcov >> 16; st; st &= st - 1) {
+                    const uint32_t r0 = __ffs(st) - 1;
+                    const uint32_t rest = st & (st - 1);
+                    const uint32_t next = rest ? (uint32_t)(__ffs(rest) - 1) : 16u;
+                    uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;
+                    len = len < next - r0 ? len : next - r0;
+                    if (r0 < 8) {
+                        const uint32_t l0 = r0 + len > 8 ? 8 - r0 : len;
+                        pr[2 * klo++] = slab | toff << 4 | r0 << 12 | l0 << 16;
+                    }
+                    if (r0 + len > 8) {
+                        const uint32_t a = r0 < 8 ? 8u : r0;   // first row at or above 8
+                        pr[2 * khi++ + 1] =
+                            slab | (toff + (a - r0)) << 4 | a << 12 | (r0 + len - a) << 16;
+                    }
+                    toff += len;
+                }
+            }
+            if (lane < kRecWords) {
+                uint32_t v = 0;
+                if (lane == 0)
+                    v = (uint32_t)mlo | (uint32_t)mhi << 6 | (uint32_t)nent << 12 |
+                        (joint ? kJointBit : 0u) | (last ? 0x80000000u : 0u);
+                else if (lane == 1) v = (uint32_t)slots;
+                else if (lane == 2) v = (uint32_t)stb;
+                else if (lane - 3 < nent) v = (uint32_t)xc;
+                srec[(int64_t)r * kRecWords + lane] = v;
+            }
+        }
+        j += nent;
+    }
+    return nst;
+}
+
+// The stage records of one work item (fields as in the items array), cut by
+// all warps of the calling CTA, 32 entries per warp at a time; `counts`
+// holds one int per warp of the CTA (shared memory).
+__device__ void build_item_stages(const int32_t *it, int ent_cap, int tiles_cap,
+                                  const int32_t *ent_col,
+                                  const int32_t *ent_tbeg,
+                                  const int32_t *ent_cover,
+                                  uint32_t *srec, uint32_t *sprog,
+                                  int32_t *counts) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = (int)(blockDim.x >> 5);
+    const int32_t e0 = it[1], e1 = it[2];
+    const int32_t nb = (e1 - e0 + 31) / 32;
+    int32_t base = e0;
+    for (int32_t b0 = 0; b0 < nb; b0 += nwarps) {
+        const int32_t b = b0 + warp;
+        const bool active = b < nb;
+        const int32_t eb = e0 + 32 * b;
+        int nst = 0;
+        if (active)
+            nst = build_batch(eb, e1, ent_cap, tiles_cap, ent_col, ent_tbeg, ent_cover, false,
+                              false, 0, srec, sprog);
+        if (lane == 0) counts[warp] = nst;
+        __syncthreads();
+        int32_t off = base, tot = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            if (w < warp) off += counts[w];
+            tot += counts[w];
+        }
+        if (active)
+            build_batch(eb, e1, ent_cap, tiles_cap, ent_col, ent_tbeg, ent_cover, b == nb - 1,
+                        true, off, srec, sprog);
+        base += tot;
+        __syncthreads();
+    }
+}
+
+// Tile layout of the MMA B operand, K-major without swizzle: 8 x 8 core
+// matrices of 128 contiguous bytes; element (i = row of W in the tile,
+// j = column) at byte (i/8)*256 + (j/8)*128 + (i%8)*16 + (j%8)*2.
+// One thread per (block, row, segment of SEG columns): it reads SEG
+// consecutive values of the block row and writes them as one piece of an
+// 8 x 8 core-matrix row (SEG = min(b, 8): 8 or 16 bytes of 16-bit values;
+// SEG = 1 for values not aligned to a segment).
+template <typename U, int B, int SEG>
+__device__ __forceinline__ void pack_tiles_range(const U *vals,
+                                                 const int32_t *blk_slot,
+                                                 const int32_t *blk_off,
+                                                 int64_t nnzb, int tr, U *out,
+                                                 int64_t t0, int64_t stride) {
+    constexpr int kSeg = SEG;                           // values per thread
+    constexpr int kPer = B * (B / kSeg);                // threads per block
+    const int64_t total = nnzb * kPer;
+    for (int64_t t = t0; t < total; t += stride) {
+        const int64_t p = t / kPer;
+        const int r = (int)(t - p * kPer);
+        const int i = r / (B / kSeg), seg = r % (B / kSeg);   // block row, segment
+        const int off = blk_off[p];
+        const int ti = off / kTile + i, tj = off % kTile + seg * kSeg;
+        // transposed plans (SEG = 1 only): element (i, j) is W's (j, i)
+        const U *src = vals + p * (B * B) + (tr ? seg * B + i : i * B + seg * kSeg);
+        U *dst = out + (int64_t)blk_slot[p] * (kTile * kTile) + (ti >> 3) * 128 + (tj >> 3) * 64 +
+                 (ti & 7) * 8 + (tj & 7);
+        if constexpr (kSeg == 8) {
+            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(src);
+        } else if constexpr (kSeg == 4) {
+            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(src);
+        } else {
+            *dst = *src;
+        }
+    }
+}
+
+// E4M3 tiles: codes row-major (16 x 16 bytes per slot) and, per slot, the
+// scale of each 4 x 4 sub-square (the block covering it: one scale for
+// b = 16, four for b = 8, sixteen for b = 4).
+__device__ __forceinline__ void pack_tiles_e4m3_range(const uint8_t *codes,
+                                                      const float *scales,
+                                                      const int32_t *blk_slot,
+                                                      const int32_t *blk_off,
+                                                      int64_t nnzb, int b, int tr,
+                                                      uint8_t *out,
+                                                      float *tile_scale, int64_t t0,
+                                                      int64_t stride) {
+    const int bb = b * b;
+    const int64_t total = nnzb * bb;
+    for (int64_t t = t0; t < total; t += stride) {
+        const int64_t p = t / bb;
+        const int e = (int)(t - p * bb);
+        const int off = blk_off[p];
+        const int ti = off / kTile + e / b, tj = off % kTile + e % b;
+        const int64_t s = blk_slot[p];
+        // transposed plans: element (i, j) is W's (j, i); a block's scale is
+        // the same either way
+        out[s * (kTile * kTile) + ti * kTile + tj] = codes[tr ? p * bb + (e % b) * b + e / b : t];
+        if ((ti & 3) == 0 && (tj & 3) == 0) tile_scale[s * 16 + (ti >> 2) * 4 + (tj >> 2)] = scales[p];
+    }
+}
+
+}  // namespace
+}  // namespace spmm
+
+#endif

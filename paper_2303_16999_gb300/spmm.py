@@ -62,7 +62,8 @@ class PlanOpts(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("rows_per_group", ctypes.c_int32),
                 ("max_per_item", ctypes.c_int32), ("host_only", ctypes.c_int32),
                 ("transposed", ctypes.c_int32), ("col_tiles", ctypes.c_int32),
-                ("groups", ctypes.c_int64), ("row_begin", ctypes.c_int64),
+                ("groups", ctypes.c_int64), ("stage_geometry", ctypes.c_int32),
+                ("dyn_chain", ctypes.c_int32), ("row_begin", ctypes.c_int64),
                 ("row_end", ctypes.c_int64)]
 
 
@@ -285,18 +286,22 @@ class Plan:
     ``col_tiles``: 128-column tiles of n per tensor-core CTA (0 automatic,
     1, or 2 where the launch allows it), as ``spmm_plan_opts.col_tiles``;
     ``groups``: near-equal tile-row groups, as ``spmm_plan_opts.groups``;
+    ``stage_geometry``: 0 automatic, 1 dense-tile, 2 sparse-tile stages;
+    ``dyn_chain``: dynamic TC plans re-partition through the launch chain
+    instead of the one cooperative launch (identical results);
     ``rows=(row_begin, row_end)``: a static plan of that slice of the output
     rows (the pattern and values passed stay the whole W's; ``run`` returns
     the slice's rows only), as ``spmm_plan_opts.row_begin / row_end``."""
 
     def __init__(self, m, k, n_max, b, w_dtype=F16, x_dtype=None, brow=None, bcol=None,
                  mode=STATIC, nnzb_max=0, kernel="auto", rows_per_group=0, max_per_item=0,
-                 host_only=False, transposed=False, col_tiles=0, groups=0, rows=None):
+                 host_only=False, transposed=False, col_tiles=0, groups=0, rows=None,
+                 stage_geometry=0, dyn_chain=False):
         x_dtype = w_dtype if x_dtype is None else x_dtype
         rb, re = rows if rows is not None else (0, 0)
         opts = PlanOpts(KERNELS[kernel] if isinstance(kernel, str) else kernel,
                         rows_per_group, max_per_item, 1 if host_only else 0,
-                        1 if transposed else 0, col_tiles, groups, rb, re)
+                        1 if transposed else 0, col_tiles, groups, stage_geometry, 1 if dyn_chain else 0, rb, re)
         pat = None
         self._keep = None
         if mode == STATIC:

@@ -237,3 +237,44 @@ def test_dynamic_near_equal_groups(b):
         _check_arrays(plan, m, k, b, c["brow"], c["bcol"])
         if call == 2 and b == 16:
             assert info["n_reductions"] > 0
+
+
+@pytest.mark.parametrize("b,dt,w8", [(16, torch.bfloat16, False), (8, torch.float16, False),
+                                     (4, torch.bfloat16, False), (16, torch.bfloat16, True),
+                                     (8, torch.bfloat16, True)])
+def test_fused_repartition_equals_launch_chain(b, dt, w8):
+    """Dynamic tensor-core plans re-partition, pack and cut their stages in
+    one cooperative launch; the same calls through the launch chain
+    (dyn_chain) must give the same device-built arrays and the same Y bit
+    for bit, on consecutive calls with different block counts (E4M3 values
+    too, where the fused launch clears and fills the tiles' scales)."""
+    m, k, n = 1024, 1024, 136
+    cap = wl.nnzb_for(m, k, b, 1 / 16)
+    wd = S.E4M3 if w8 else S.dtype_code(dt)
+    plans = [S.Plan(m, k, n, b, w_dtype=wd, x_dtype=S.dtype_code(dt), mode=S.DYNAMIC,
+                    nnzb_max=cap, dyn_chain=ch) for ch in (False, True)]
+    for call in range(3):
+        c = wl.dynamic_call(call + 60 * b, m=m, k=k, n=n, b=b, d_max=1 / 16)
+        X = torch.from_numpy(c["X"]).to(dt).cuda()
+        vd = torch.zeros((cap, b, b), dtype=dt)
+        vd[:len(c["vals"])] = torch.from_numpy(c["vals"]).to(dt)
+        vd = vd.cuda()
+        pat = _dev_pattern(c["brow"], c["bcol"], cap)
+        outs = []
+        for p in plans:
+            if w8:
+                codes, scales = S.quantize_e4m3(vd)
+                Y = p.run(X, values=codes.view(torch.uint8), scales=scales, pattern=pat)
+            else:
+                Y = p.run(X, values=vd, pattern=pat)
+            torch.cuda.synchronize()
+            assert p.status() == 0
+            outs.append(Y.cpu())
+        assert torch.equal(outs[0], outs[1])
+        for key in ("row_ptr", "col_idx", "perm", "items", "grp_ebeg", "ent_col", "ent_tbeg",
+                    "ent_cover", "tile_row", "blk_slot", "blk_off", "ws_row0", "red"):
+            assert np.array_equal(plans[0].array(key), plans[1].array(key)), key
+        if not w8:
+            vals = torch.from_numpy(c["vals"]).to(dt)
+            Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X.cpu())
+            assert oracle.normwise_err(outs[0], Yo, oracle.block_fro(vals), X.cpu()) <= 4e-3
