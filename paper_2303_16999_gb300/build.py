@@ -20,10 +20,8 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3",
           "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
-# Per-file flags.  The fused dynamic re-partition reads, in one launch, data
-# that other CTAs wrote earlier in the same launch: its global loads bypass
-# L1 (cache in L2 only), so no CTA can see a stale line.
-PER_FILE = {"k_dynamic.cu": ["-Xptxas", "-dlcm=cg"]}
+# Per-file flags (none at present).
+PER_FILE = {}
 
 
 def sources():

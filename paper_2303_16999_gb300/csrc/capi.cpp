@@ -219,6 +219,17 @@ static spmm_status alloc_dynamic(spmm_plan *p) {
         AL(d.grp_wbeg, G);
         AL(d.grp_rbeg, G);
         AL(d.grp_wrow, G);
+        if (p->dyn_fused) {
+            const int64_t kw = (p->k / p->b + 31) / 32;
+            if (mb * kw > kFusedMaxBitmapWords) {
+                p->dyn_fused = false;   // the launch chain needs no bitmap
+            } else {
+                AL(d.bits, mb * kw);
+                AL(d.wpre, mb * kw);
+                AL(d.gmask, G * (p->k / kTile));
+                AL(d.bar, kFusedMaxCtas + 1);
+            }
+        }
         AL(p->d_grp_ebeg, G + 1);
         AL(p->d_ent_col, cap);
         AL(p->d_ent_tbeg, cap + 1);

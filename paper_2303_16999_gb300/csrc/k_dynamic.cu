@@ -15,7 +15,15 @@
 //      block -> slot maps.
 // A scan runs in the last block of the kernel before it (a ticket counter,
 // with fences on both sides) rather than as its own launch: each launch of
-// this latency-bound chain costs a few microseconds.
+// this latency-bound chain costs a few microseconds.  Dynamic tensor-core
+// plans run all of it, with the packing and the stage records, in one
+// cooperative launch instead (see "fused" below); the chain remains for the
+// b = 1 gather plans, the sampled product's block CSR, devices without
+// cooperative launches and spmm_plan_opts.dyn_chain.  Measured at m = k =
+// 8192, b = 16, d_max = 1/16 (GB300): the fused launch takes about 40 us,
+// the chain about the same (39 us of re-partition and packing plus 6 us of
+// stage records); each of its four grid barriers costs about 2 us, about
+// what a kernel boundary of the chain costs.
 // The arrays equal the oracle's dynamic-plan rules bit for bit (no item
 // reordering, no zero-padded intervals).  A rejected pattern sets the plan's
 // status word; the product kernels then skip, leaving Y unwritten.
@@ -381,7 +389,8 @@ __device__ void group_fill(int g, int32_t kt, int32_t T, int32_t b, const int32_
                            const uint32_t *colmask, int32_t *slot_of, int32_t s0, int32_t s1,
                            int32_t *ent_col, int32_t *ent_tbeg, int32_t *ent_cover,
                            int32_t *tile_row, int32_t *blk_slot, int32_t *blk_off, int32_t *items,
-                           int64_t *ws_row0, int32_t *red) {
+                           int64_t *ws_row0, int32_t *red, const int32_t *rp_s = nullptr,
+                           int32_t *pk = nullptr) {
     const int32_t t0 = grp_row0[g], nrows = grp_rows[g];
     // column prefix over entries and slots, in chunks of blockDim (1024)
     int64_t eb = grp_ebeg[g], sb = grp_sbeg[g];
@@ -409,19 +418,28 @@ __device__ void group_fill(int g, int32_t kt, int32_t T, int32_t b, const int32_
     }
     __syncthreads();
     // blocks of the group -> slot and offset (indexed by user position)
+    // (rp_s: the group's row pointers in shared memory, rp_s[i] = row_ptr of
+    // block row t0 * T + i; pk: per slot of the group, the block's user
+    // index, tile slot and offset, for the caller to pack from)
     for (int32_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
         int32_t lo = t0 * T, hi = (t0 + nrows) * T;
         while (hi - lo > 1) {
             const int32_t mid = (lo + hi) >> 1;
-            if (row_ptr[mid] <= s) lo = mid; else hi = mid;
+            if ((rp_s ? rp_s[mid - t0 * T] : row_ptr[mid]) <= s) lo = mid; else hi = mid;
         }
         const int32_t br = lo, bc = col_idx[s];
         const int32_t tc = bc / T, trow = br / T - t0;
         const uint32_t mk = colmask[tc];
         const int32_t slot = slot_of[tc] + __popc(mk & ((1u << trow) - 1u));
         const int32_t p = perm[s];
+        const int32_t off = ((br * b) % kTile) * kTile + (bc * b) % kTile;
         blk_slot[p] = slot;
-        blk_off[p] = ((br * b) % kTile) * kTile + (bc * b) % kTile;
+        blk_off[p] = off;
+        if (pk) {
+            pk[3 * (s - s0)] = p;
+            pk[3 * (s - s0) + 1] = slot;
+            pk[3 * (s - s0) + 2] = off;
+        }
     }
     __syncthreads();   // the masks may be reused by the calling CTA after this
     if (threadIdx.x != 0) return;
@@ -476,30 +494,40 @@ __global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *
 }
 
 // ------------------------------------------------ fused (cooperative) ---
-// Dynamic tensor-core plans run the whole chain above, the value packing and
-// the stage records in ONE cooperative launch: every CTA is resident, and
-// the steps are separated by grid barriers instead of kernel boundaries
-// (each boundary of the chain costs a few microseconds of launch latency;
-// a barrier about one).  The steps and their arithmetic are those of the
-// kernels above, run by the same device functions:
-//   0. zero the row counts and the status word           | barrier
-//   1. validate + block-row histogram (grid over pattern) | barrier
-//   2. CTA 0: row scan -> row_ptr, cursor                 | barrier
-//   3. scatter into rows                                  | barrier
-//   4. per-row rank sort, duplicate check                 | barrier
+// Dynamic tensor-core plans run the re-partition, the value packing and the
+// stage records in ONE cooperative launch: every CTA is resident and the
+// steps are separated by four grid barriers instead of seven kernel
+// boundaries (each costs a few microseconds).  The arrays are the same as
+// the launch chain's, bit for bit; the block CSR is built from a bitmap of
+// each block row's block columns instead of a scatter and a row sort:
+//   A. clear the bitmap, the row counts and the status word       | barrier
+//   B. validate; set each block's bit (a bit already set is a
+//      repeated block)                                              | barrier,
+//      then CTA 0 scans the bitmap's popcounts (row_ptr, and the
+//      blocks before each bitmap word)
 //      (a rejected pattern ends the launch here: nothing else is written)
-//   5. per-group column masks -> entry / slot counts      | barrier
-//   6. CTA 0: group scan -> offsets, chunk size           | barrier
-//   7. per-group fill (entries, slots, items, block -> slot; the group's
-//      tiles cleared where blocks do not cover them)      | barrier
-//   8. value packing (grid) and stage records (CTA per work item).
-// Every barrier wait is bounded; on expiry the status word records
+//   C. place each block in the CSR after the set bits before it; per
+//      group, the column masks (from the bitmap) and the entry / slot
+//      counts                                                       | barrier,
+//      then CTA 0 scans the groups (offsets, chunk size)
+//   D. per group: entries, slots, block -> slot, items (the chain's fill,
+//      with the group's row pointers and its blocks' slots in shared
+//      memory), the group's tiles cleared where blocks do not fill them,
+//      and its blocks' values packed, a warp per block               | barrier
+//   E. stage records, a CTA per work item.
+// Barrier: each CTA publishes its arrival in a flag of its own; CTA 0
+// waits for all flags, runs the step that follows a barrier (a scan) and
+// then publishes the barrier's generation, which the other CTAs wait for.
+// Every wait is bounded; on expiry the status word records
 // SPMM_ERR_TIMEOUT and the launch ends (the product launch then skips).
 struct DynFusedArgs {
     const int32_t *d_nnzb, *brow, *bcol;
     int64_t cap;
-    int32_t mb, kb, kt, T, b, G;
-    int32_t *row_cnt, *status, *row_ptr, *cursor, *counts, *tmp_col, *tmp_perm, *col_idx, *perm;
+    int32_t mb, kb, kw, kt, T, b, G;
+    uint32_t *bits, *gmask;
+    int32_t *wpre;           // per bitmap word: blocks in the CSR before it
+    int32_t *bar;
+    int32_t *row_cnt, *status, *row_ptr, *cursor, *counts, *col_idx, *perm;
     const int32_t *grp_row0, *grp_rows;
     int32_t *grp_cnt, *grp_ebeg, *grp_sbeg, *grp_ibeg, *grp_wbeg;
     int64_t *grp_wrow;
@@ -524,70 +552,225 @@ __device__ __forceinline__ unsigned long long dyn_timer() {
     return t;
 }
 
-// Grid barrier over all CTAs of a cooperative launch (counter + generation
-// in global memory, zeroed before the launch); false when the wait ran out.
-__device__ bool grid_sync(int32_t *count, int32_t *gen, int32_t *status,
-                          unsigned long long limit_ns) {
+// The flag barrier described above, with CTA 0 running `step` (all its
+// threads) between the arrivals and the release.  Each CTA publishes its
+// flag with a release store after a CTA barrier, CTA 0 reads the flags with
+// acquire loads and releases the generation, which the others acquire; the
+// CTA barriers around carry that order to every thread, so plain loads
+// after the barrier see every write made before it by any CTA.  Returns
+// false when a wait ran out (the status word then says so).
+__device__ __forceinline__ void st_release(int32_t *p, int32_t v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int32_t ld_acquire(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename Step>
+__device__ bool flag_sync(int32_t *flags, int32_t *gen, int32_t epoch, int32_t *status,
+                          unsigned long long lim, Step step) {
     __shared__ int ok_s;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const int32_t g0 = *(volatile int32_t *)gen;
-        __threadfence();
-        if (atomicAdd(count, 1) == (int32_t)gridDim.x - 1) {
-            atomicExch(count, 0);
-            __threadfence();
-            atomicExch(gen, g0 + 1);
-        } else {
+    if (blockIdx.x != 0) {
+        if (threadIdx.x == 0) {
+            st_release(&flags[blockIdx.x], epoch);
+            int ok = 1;
             const unsigned long long t0 = dyn_timer();
-            while (*(volatile int32_t *)gen == g0) {
-                if (dyn_timer() - t0 > limit_ns) {
+            while (ld_acquire(gen) < epoch) {
+                if (dyn_timer() - t0 > lim) {
                     flag(status, kDevTimeout);
                     ok = 0;
                     break;
                 }
             }
+            ok_s = ok;
         }
-        __threadfence();
-        ok_s = ok;
+        __syncthreads();
+        return ok_s != 0;
+    }
+    if (threadIdx.x < 32) {
+        int ok = 1;
+        const unsigned long long t0 = dyn_timer();
+        for (int i = 1 + (int)threadIdx.x; ok && i < (int)gridDim.x; i += 32) {
+            while (ld_acquire(flags + i) < epoch) {
+                if (dyn_timer() - t0 > lim) {
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        ok = __all_sync(0xffffffffu, ok);
+        if (threadIdx.x == 0) {
+            if (!ok) flag(status, kDevTimeout);
+            ok_s = ok;
+        }
     }
     __syncthreads();
-    return ok_s != 0;
+    if (!ok_s) return false;
+    step();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(gen, epoch);
+    return true;
 }
 
-// Packs this launch's share of the blocks into tiles (grid-stride).
-__device__ void fused_pack(const DynFusedArgs &a, int64_t nnzb, int64_t t0, int64_t stride) {
-    if (a.w8) {
-        pack_tiles_e4m3_range((const uint8_t *)a.values, a.scales, a.blk_slot, a.blk_off, nnzb, a.b,
-                              a.tr, (uint8_t *)a.packed, a.tile_scale, t0, stride);
-        return;
+struct NoStep {
+    __device__ void operator()() const {}
+};
+
+// CTA 0 after the bitmap is set: the exclusive prefix of the bitmap words'
+// popcounts in row-major order (wpre), hence row_ptr[r] = wpre[r * kw] and
+// the block count (1024 threads, each a contiguous run of whole 16-byte
+// vectors of words; the bitmap and wpre are 256-byte aligned allocations).
+__device__ void scan_bits(const DynFusedArgs &a) {
+    const int64_t W = (int64_t)a.mb * a.kw;
+    int64_t q = (W + blockDim.x - 1) / blockDim.x;
+    q = (q + 3) & ~(int64_t)3;                           // whole uint4 per thread
+    const int64_t lo = min(W, (int64_t)threadIdx.x * q), hi = min(W, lo + q);
+    int64_t local = 0;
+    for (int64_t i = lo; i < hi; i += 4) {
+        if (i + 4 <= hi) {
+            const uint4 v = __ldcg((const uint4 *)(a.bits + i));
+            local += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        } else {
+            for (int64_t j = i; j < hi; ++j) local += __popc(__ldcg(a.bits + j));
+        }
     }
-    const uint16_t *v = (const uint16_t *)a.values;
-    uint16_t *o = (uint16_t *)a.packed;
-    switch (a.b * 16 + a.seg) {
-        case 16 * 16 + 8: pack_tiles_range<uint16_t, 16, 8>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
-        case 16 * 16 + 1: pack_tiles_range<uint16_t, 16, 1>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
-        case 8 * 16 + 8: pack_tiles_range<uint16_t, 8, 8>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
-        case 8 * 16 + 1: pack_tiles_range<uint16_t, 8, 1>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
-        case 4 * 16 + 4: pack_tiles_range<uint16_t, 4, 4>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
-        case 4 * 16 + 1: pack_tiles_range<uint16_t, 4, 1>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
-        default: pack_tiles_range<uint16_t, 1, 1>(v, a.blk_slot, a.blk_off, nnzb, a.tr, o, t0, stride); break;
+    int64_t total;
+    int64_t run = block_scan(local, &total);
+    for (int64_t i = lo; i < hi; i += 4) {
+        if (i + 4 <= hi) {
+            const uint4 v = __ldcg((const uint4 *)(a.bits + i));
+            int4 o;
+            o.x = (int32_t)run;
+            run += __popc(v.x);
+            o.y = (int32_t)run;
+            run += __popc(v.y);
+            o.z = (int32_t)run;
+            run += __popc(v.z);
+            o.w = (int32_t)run;
+            run += __popc(v.w);
+            *(int4 *)(a.wpre + i) = o;
+        } else {
+            for (int64_t j = i; j < hi; ++j) {
+                a.wpre[j] = (int32_t)run;
+                run += __popc(__ldcg(a.bits + j));
+            }
+        }
     }
+    __syncthreads();
+    for (int32_t r = threadIdx.x; r < a.mb; r += blockDim.x) a.row_ptr[r] = a.wpre[(int64_t)r * a.kw];
+    if (threadIdx.x == 0) {
+        a.row_ptr[a.mb] = (int32_t)total;
+        a.counts[kCntNnzb] = (int32_t)total;
+    }
+}
+
+// The column masks of group g from the bitmap (bit r of colmask[c]: tile
+// row r of the group holds a block in tile column c), into shared memory.
+__device__ void group_colmask_bits(const DynFusedArgs &a, int g, uint32_t *colmask) {
+    const int32_t t0 = a.grp_row0[g], nrows = a.grp_rows[g];
+    const uint32_t tmask = a.T >= 32 ? 0xffffffffu : ((1u << a.T) - 1u);
+    const int32_t nb = nrows * a.T;                       // block rows of the group
+    const uint32_t *base = a.bits + (int64_t)t0 * a.T * a.kw;
+    for (int32_t c = threadIdx.x; c < a.kt; c += blockDim.x) {
+        const int32_t bc = c * a.T;                       // first block column of tile column c
+        const int32_t w = bc >> 5, sh = bc & 31;
+        uint32_t mk = 0;
+#pragma unroll 16
+        for (int32_t j = 0; j < nb; ++j)
+            if ((base[(int64_t)j * a.kw + w] >> sh) & tmask) mk |= 1u << (j / a.T);
+        colmask[c] = mk;
+    }
+    __syncthreads();
+}
+
+// Packs the blocks of CSR slots [s0, s1), a warp per block: their user
+// index, slot and offset from `pk` (shared memory) when given, else read
+// through perm / blk_slot / blk_off.
+__device__ void pack_group(const DynFusedArgs &a, int32_t s0, int32_t s1, const int32_t *pk) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int32_t q0 = s0 + warp;
+    if (pk && !a.w8 && a.b == 16 && a.seg == 8 && !a.tr) {
+        // 16 x 16 blocks, 16-byte pieces: four blocks per round, every load
+        // issued before any store (the block's 512 B is one piece per lane,
+        // row lane / 2, half lane % 2, placed as pack_block_warp places it)
+        const uint4 *v = (const uint4 *)a.values;
+        uint16_t *o = (uint16_t *)a.packed;
+        const int i = lane >> 1, seg = lane & 1;
+        const int toff = (i >> 3) * 128 + seg * 64 + (i & 7) * 8;
+        for (; q0 + 3 * nw < s1; q0 += 4 * nw) {
+            uint4 d[4];
+            int32_t sl[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int32_t qq = q0 + u * nw - s0;
+                d[u] = v[(int64_t)pk[3 * qq] * 32 + lane];
+                sl[u] = pk[3 * qq + 1];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                *(uint4 *)(o + (int64_t)sl[u] * (kTile * kTile) + toff) = d[u];
+        }
+    }
+    for (int32_t q = q0; q < s1; q += nw) {
+        int64_t p;
+        int32_t slot, off;
+        if (pk) {
+            p = pk[3 * (q - s0)];
+            slot = pk[3 * (q - s0) + 1];
+            off = pk[3 * (q - s0) + 2];
+        } else {
+            p = a.perm[q];
+            slot = a.blk_slot[p];
+            off = a.blk_off[p];
+        }
+        if (a.w8) {
+            pack_block_e4m3_warp((const uint8_t *)a.values, a.scales, p, a.b, slot, off, a.tr,
+                                 (uint8_t *)a.packed, a.tile_scale, lane);
+            continue;
+        }
+        const uint16_t *v = (const uint16_t *)a.values;
+        uint16_t *o = (uint16_t *)a.packed;
+        switch (a.b * 16 + a.seg) {
+            case 16 * 16 + 8: pack_block_warp<uint16_t, 16, 8>(v, p, slot, off, a.tr, o, lane); break;
+            case 16 * 16 + 1: pack_block_warp<uint16_t, 16, 1>(v, p, slot, off, a.tr, o, lane); break;
+            case 8 * 16 + 8: pack_block_warp<uint16_t, 8, 8>(v, p, slot, off, a.tr, o, lane); break;
+            case 8 * 16 + 1: pack_block_warp<uint16_t, 8, 1>(v, p, slot, off, a.tr, o, lane); break;
+            case 4 * 16 + 4: pack_block_warp<uint16_t, 4, 4>(v, p, slot, off, a.tr, o, lane); break;
+            case 4 * 16 + 1: pack_block_warp<uint16_t, 4, 1>(v, p, slot, off, a.tr, o, lane); break;
+            default: pack_block_warp<uint16_t, 1, 1>(v, p, slot, off, a.tr, o, lane); break;
+        }
+    }
+}
+
+// Shared memory of the fused launch: colmask[kt], slot_of[kt], the group's
+// row pointers (at most 16 * 16 + 1) and kFusedPk (user index, slot,
+// offset) triples.
+constexpr int kFusedPk = 4096;
+constexpr int kFusedRp = 16 * 16 + 1;
+inline size_t fused_smem(int32_t kt) {
+    return sizeof(int32_t) * (2 * (size_t)kt + kFusedRp + 3 * (size_t)kFusedPk);
 }
 
 __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_constant__ DynFusedArgs a) {
     pdl_enter();
-    extern __shared__ uint32_t dsm[];   // colmask[kt], slot_of[kt]
+    extern __shared__ uint32_t dsm[];   // see fused_smem
     __shared__ int32_t bcounts[32];
-    int32_t *bar = a.counts + kCntBarrier, *gen = a.counts + kCntBarrierGen;
+    int32_t *flags = a.bar, *gen = a.bar + kFusedMaxCtas;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t gs = (int64_t)gridDim.x * blockDim.x;
     const unsigned long long lim = a.wait_ns;
-    // 0.
-    for (int64_t r = gt; r < a.mb; r += gs) a.row_cnt[r] = 0;
+    uint32_t *colmask = dsm;
+    int32_t *slot_of = (int32_t *)(dsm + a.kt);
+    int32_t *rp_s = slot_of + a.kt;
+    int32_t *pk = rp_s + kFusedRp;
+    // A.
+    for (int64_t i = gt; i < (int64_t)a.mb * a.kw; i += gs) a.bits[i] = 0;
     if (gt == 0) *a.status = 0;
-    if (!grid_sync(bar, gen, a.status, lim)) return;
-    // 1.
+    if (!flag_sync(flags, gen, 1, a.status, lim, NoStep())) return;
+    // B.
     const int64_t raw = *a.d_nnzb;
     if (gt == 0 && (raw < 0 || raw > a.cap)) flag(a.status, kDevCapacity);
     const int64_t n = raw < 0 ? 0 : (raw > a.cap ? a.cap : raw);
@@ -597,56 +780,38 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
             flag(a.status, kDevPattern);
             continue;
         }
-        atomicAdd(&a.row_cnt[r], 1);
+        const uint32_t bit = 1u << (c & 31);
+        if (atomicOr(&a.bits[(int64_t)r * a.kw + (c >> 5)], bit) & bit) flag(a.status, kDevPattern);
     }
-    if (!grid_sync(bar, gen, a.status, lim)) return;
-    // 2.
-    if (blockIdx.x == 0)
-        scan_rows(a.d_nnzb, a.cap, a.mb, a.row_cnt, a.row_ptr, a.cursor, nullptr, nullptr, nullptr,
-                  a.counts, 0);
-    if (!grid_sync(bar, gen, a.status, lim)) return;
-    // 3.
+    if (!flag_sync(flags, gen, 2, a.status, lim, [&] { scan_bits(a); })) return;
+    if (*(volatile int32_t *)a.status != 0) return;   // every CTA sees the same word here
+    // C.
     for (int64_t p = gt; p < n; p += gs) {
         const int32_t r = a.brow[p], c = a.bcol[p];
-        if (r < 0 || r >= a.mb || c < 0 || c >= a.kb) continue;
-        const int32_t pos = atomicAdd(&a.cursor[r], 1);
-        a.tmp_col[pos] = c;
-        a.tmp_perm[pos] = (int32_t)p;
+        const int64_t wi = (int64_t)r * a.kw + (c >> 5);
+        const int32_t pos = a.wpre[wi] + __popc(a.bits[wi] & ((1u << (c & 31)) - 1u));
+        a.col_idx[pos] = c;
+        a.perm[pos] = (int32_t)p;
     }
-    if (!grid_sync(bar, gen, a.status, lim)) return;
-    // 4.
-    {
-        const int lane = threadIdx.x & 31;
-        for (int64_t r = gt >> 5; r < a.mb; r += gs >> 5) {
-            const int32_t beg = __ldcg(a.row_ptr + r), end = __ldcg(a.row_ptr + r + 1);
-            sort_row(beg, end, lane, a.tmp_col, a.tmp_perm, a.col_idx, a.perm, a.status);
-        }
-    }
-    if (!grid_sync(bar, gen, a.status, lim)) return;
-    if (*(volatile int32_t *)a.status != 0) return;   // every CTA sees the same word here
-    // 5.
-    uint32_t *colmask = dsm;
-    int32_t *slot_of = (int32_t *)(dsm + a.kt);
     for (int g = blockIdx.x; g < a.G; g += gridDim.x) {
-        int32_t s0, s1;
-        group_colmask(g, a.kt, a.T, a.grp_row0, a.grp_rows, a.row_ptr, a.col_idx, colmask, &s0, &s1);
+        group_colmask_bits(a, g, colmask);
+        for (int32_t c = threadIdx.x; c < a.kt; c += blockDim.x)
+            a.gmask[(int64_t)g * a.kt + c] = colmask[c];
         group_counts(g, a.kt, colmask, a.grp_cnt);
     }
-    if (!grid_sync(bar, gen, a.status, lim)) return;
-    // 6.
-    if (blockIdx.x == 0)
-        group_scan(a.G, a.grp_rows, a.grp_cnt, a.grp_ebeg, a.grp_sbeg, a.grp_ibeg, a.grp_wbeg,
-                   a.grp_wrow, a.grp_rbeg, a.ent_tbeg, a.counts);
-    if (!grid_sync(bar, gen, a.status, lim)) return;
-    // 7.
+    if (!flag_sync(flags, gen, 3, a.status, lim, [&] {
+            group_scan(a.G, a.grp_rows, a.grp_cnt, a.grp_ebeg, a.grp_sbeg, a.grp_ibeg, a.grp_wbeg,
+                       a.grp_wrow, a.grp_rbeg, a.ent_tbeg, a.counts);
+        }))
+        return;
+    // D.
     const int64_t tile_bytes = a.w8 ? kTile * kTile : kTile * kTile * 2;
     for (int g = blockIdx.x; g < a.G; g += gridDim.x) {
         if (a.b < 16) {
             // tiles hold several blocks: clear the group's tiles (and E4M3
-            // scales) first; 16 x 16 blocks fill their tile and every scale
-            const int64_t sb = __ldcg(a.grp_sbeg + g);
-            const int64_t se = g + 1 < a.G ? __ldcg(a.grp_sbeg + g + 1)
-                                           : (int64_t)__ldcg(a.counts + kCntSlots);
+            // scales); 16 x 16 blocks fill their tile and every scale
+            const int64_t sb = a.grp_sbeg[g];
+            const int64_t se = g + 1 < a.G ? a.grp_sbeg[g + 1] : (int64_t)a.counts[kCntSlots];
             uint4 *t = (uint4 *)((uint8_t *)a.packed + sb * tile_bytes);
             const int64_t nv = (se - sb) * tile_bytes / 16;
             for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) t[i] = make_uint4(0, 0, 0, 0);
@@ -655,18 +820,26 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
                 for (int64_t i = threadIdx.x; i < (se - sb) * 16; i += blockDim.x) ts[i] = 0.f;
             }
         }
-        int32_t s0, s1;
-        group_colmask(g, a.kt, a.T, a.grp_row0, a.grp_rows, a.row_ptr, a.col_idx, colmask, &s0, &s1);
+        for (int32_t c = threadIdx.x; c < a.kt; c += blockDim.x)
+            colmask[c] = a.gmask[(int64_t)g * a.kt + c];
+        __syncthreads();
+        const int32_t t0 = a.grp_row0[g], nrows = a.grp_rows[g];
+        for (int32_t i = threadIdx.x; i <= nrows * a.T; i += blockDim.x)
+            rp_s[i] = a.row_ptr[t0 * a.T + i];
+        __syncthreads();
+        const int32_t s0 = rp_s[0], s1 = rp_s[nrows * a.T];
+        const bool stage = s1 - s0 <= kFusedPk;
         group_fill(g, a.kt, a.T, a.b, a.grp_row0, a.grp_rows, a.row_ptr, a.col_idx, a.perm,
                    a.grp_ebeg, a.grp_sbeg, a.grp_ibeg, a.grp_wbeg, a.grp_wrow, a.grp_rbeg, a.counts,
                    colmask, slot_of, s0, s1, a.ent_col, a.ent_tbeg, a.ent_cover, a.tile_row,
-                   a.blk_slot, a.blk_off, a.items, a.ws_row0, a.red);
+                   a.blk_slot, a.blk_off, a.items, a.ws_row0, a.red, rp_s, stage ? pk : nullptr);
+        __syncthreads();   // this CTA's block -> slot writes, and the cleared tiles
+        pack_group(a, s0, s1, stage ? pk : nullptr);
         __syncthreads();
     }
-    if (!grid_sync(bar, gen, a.status, lim)) return;
-    // 8.
-    fused_pack(a, n, gt, gs);
-    const int64_t ni = min(a.items_cap, (int64_t)max(__ldcg(a.counts + kCntItems), 0));
+    if (!flag_sync(flags, gen, 4, a.status, lim, NoStep())) return;
+    // E.
+    const int64_t ni = min(a.items_cap, (int64_t)max(a.counts[kCntItems], 0));
     for (int64_t item = blockIdx.x; item < ni; item += gridDim.x) {
         build_item_stages(a.items + item * kItemFields, a.ent_cap, a.tiles_cap, a.ent_col,
                           a.ent_tbeg, a.ent_cover, a.srec, a.sprog, bcounts);
@@ -750,17 +923,20 @@ cudaError_t launch_dynamic_tc_fused(spmm_plan *p, const spmm_dpattern *dp, const
     a.cap = p->nnzb_max;
     a.mb = (int32_t)(p->m / p->b);
     a.kb = (int32_t)(p->k / p->b);
+    a.kw = (a.kb + 31) / 32;
     a.kt = (int32_t)(p->k / kTile);
     a.T = kTile / p->b;
     a.b = p->b;
     a.G = (int32_t)p->n_groups;
+    a.bits = d.bits;
+    a.gmask = d.gmask;
+    a.wpre = d.wpre;
+    a.bar = d.bar;
     a.row_cnt = d.row_cnt;
     a.status = p->d_status;
     a.row_ptr = p->d_row_ptr;
     a.cursor = d.cursor;
     a.counts = p->d_counts;
-    a.tmp_col = d.tmp_col;
-    a.tmp_perm = d.tmp_perm;
     a.col_idx = p->d_col_idx;
     a.perm = p->d_perm;
     a.grp_row0 = p->d_grp_row0;
@@ -795,16 +971,20 @@ cudaError_t launch_dynamic_tc_fused(spmm_plan *p, const spmm_dpattern *dp, const
     a.srec = p->d_srec;
     a.sprog = p->d_sprog;
     a.wait_ns = p->wait_ns ? p->wait_ns : 2000000000ull;
-    const size_t smem = sizeof(uint32_t) * 2 * (size_t)a.kt;
+    // the kernel's shared-memory limit is set once per device for the
+    // largest k of a dynamic TC plan (k / 16 <= kDynMaxTileCols)
+    const size_t smem = fused_smem(a.kt);
     static std::atomic<uint64_t> attrs{0};
-    cudaError_t e = set_smem_attrs_once(attrs, dyn_tc_fused_kernel, (int)smem, false);
+    cudaError_t e = set_smem_attrs_once(attrs, dyn_tc_fused_kernel,
+                                        (int)fused_smem(kDynMaxTileCols), false);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dyn_tc_fused_kernel, 1024, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    const int grid = std::min(per_sm * std::max(p->sm_count, 1), 128);
+    const int grid = std::min(per_sm * std::max(p->sm_count, 1), kFusedMaxCtas);
     e = cudaMemsetAsync(p->d_counts, 0, sizeof(int32_t) * kCntCount, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d.bar, 0, sizeof(int32_t) * (kFusedMaxCtas + 1), s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);

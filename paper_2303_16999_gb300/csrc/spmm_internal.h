@@ -30,9 +30,7 @@ enum CountIdx : int {
     kCntChunk = 7,    // chunk size C chosen on the device
     kCntTicketRows = 8,    // blocks done with the row histogram (the last one scans)
     kCntTicketGroups = 9,  // blocks done with the group counts (the last one scans)
-    kCntBarrier = 10,      // fused re-partition: CTAs arrived at the current grid barrier
-    kCntBarrierGen = 11,   // fused re-partition: grid barriers completed
-    kCntCount = 12
+    kCntCount = 10
 };
 
 // device status word codes (mirrors spmm_status where applicable)
@@ -82,8 +80,16 @@ struct DynBufs {
     int32_t *grp_cnt = nullptr, *grp_sbeg = nullptr, *grp_ibeg = nullptr, *grp_wbeg = nullptr,
             *grp_rbeg = nullptr;
     int64_t *grp_wrow = nullptr;
+    // fused re-partition (dynamic TC): block-column bitmap of every block
+    // row (mb x ceil(kb/32) words), the groups' column masks (G x kt words)
+    // and the grid barrier's flags (one per CTA, then the generation word)
+    uint32_t *bits = nullptr, *gmask = nullptr;
+    int32_t *wpre = nullptr;   // per bitmap word: blocks before it in row-major order
+    int32_t *bar = nullptr;
     int64_t items_cap = 0, ws_slots_cap = 0, red_cap = 0;
 };
+constexpr int kFusedMaxCtas = 128;           // CTAs of the fused re-partition (at most)
+constexpr int64_t kFusedMaxBitmapWords = 1 << 22;  // 16 MB of block-column bitmap at most
 
 }  // namespace spmm
 

@@ -239,6 +239,46 @@ __device__ __forceinline__ void pack_tiles_e4m3_range(const uint8_t *codes,
     }
 }
 
+// One block's values into its tile by the 32 lanes of a warp, with the
+// element placement of pack_tiles_range (block p of the user order, tile
+// slot `slot`, offset `off` = row * 16 + column of the block in the tile).
+template <typename U, int B, int SEG>
+__device__ __forceinline__ void pack_block_warp(const U *vals, int64_t p, int32_t slot,
+                                                int32_t off, int tr, U *out, int lane) {
+    constexpr int kSeg = SEG;
+    constexpr int kPer = B * (B / kSeg);
+    for (int r = lane; r < kPer; r += 32) {
+        const int i = r / (B / kSeg), seg = r % (B / kSeg);
+        const int ti = off / kTile + i, tj = off % kTile + seg * kSeg;
+        const U *src = vals + p * (B * B) + (tr ? seg * B + i : i * B + seg * kSeg);
+        U *dst = out + (int64_t)slot * (kTile * kTile) + (ti >> 3) * 128 + (tj >> 3) * 64 +
+                 (ti & 7) * 8 + (tj & 7);
+        if constexpr (kSeg == 8) {
+            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(src);
+        } else if constexpr (kSeg == 4) {
+            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(src);
+        } else {
+            *dst = *src;
+        }
+    }
+}
+
+// The same for E4M3 codes and the block's scale (pack_tiles_e4m3_range's
+// placement).
+__device__ __forceinline__ void pack_block_e4m3_warp(const uint8_t *codes, const float *scales,
+                                                     int64_t p, int b, int32_t slot, int32_t off,
+                                                     int tr, uint8_t *out, float *tile_scale,
+                                                     int lane) {
+    const int bb = b * b;
+    for (int e = lane; e < bb; e += 32) {
+        const int ti = off / kTile + e / b, tj = off % kTile + e % b;
+        const int64_t s = slot;
+        out[s * (kTile * kTile) + ti * kTile + tj] =
+            codes[tr ? p * bb + (e % b) * b + e / b : p * bb + e];
+        if ((ti & 3) == 0 && (tj & 3) == 0) tile_scale[s * 16 + (ti >> 2) * 4 + (tj >> 2)] = scales[p];
+    }
+}
+
 }  // namespace
 }  // namespace spmm
 
