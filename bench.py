@@ -540,7 +540,7 @@ def main():
 
     points, tc_launches = [], []
     for i, p in enumerate(pts):
-        kern = {1: "plain", 2: "gather", 3: "tc"}[p["kernel"]]
+        kern = {1: "plain", 2: "gather", 3: "tc", 4: "bgather"}[p["kernel"]]
         fl, by, bound, t_roof = roof_of(p["b"], p["nnzb"], peaks, kern, p["m"])
         us = per[i] * 1e3
         points.append({"b": p["b"], "d": "1/%d" % round(1 / p["d"]), "kernel": kern,
@@ -787,6 +787,31 @@ def run_batched(torch, S, wl, dev, peaks, reps=5):
     plans, p32, Xs, Ys, X32, Y32 = [], [], [], [], [], []
     flops = 0.0
     comp_bytes = 0
+    # the autotuner: one tuning run per (b, density, n) bucket of the batch,
+    # on that bucket's first problem; every plan below is AUTO and takes its
+    # bucket's choice
+    S.spmm_tune_clear()
+    t_tune = time.perf_counter()
+    tuned, seen = [], set()
+    for i in range(48):
+        sp = wl.batched_spec(i)
+        key = (sp["m"], sp["k"], sp["b"], sp["d"], max(sp["n"] - 1, 0).bit_length())
+        if key in seen:
+            continue
+        seen.add(key)
+        c = wl.batched_case(i)
+        codes, scales = S.quantize_e4m3(torch.from_numpy(c["vals"]).to(bf).to(dev))
+        ld = (c["n"] + 7) // 8 * 8
+        xb = torch.zeros((c["k"], ld), dtype=bf, device=dev)
+        xb[:, :c["n"]] = torch.from_numpy(c["X"]).to(bf).to(dev)
+        r = S.spmm_tune(c["m"], c["k"], c["b"], c["brow"], c["bcol"], codes.view(torch.uint8),
+                        xb[:, :c["n"]], w_dtype=S.E4M3, x_dtype=S.BF16, scales=scales, reps=5)
+        tuned.append({"m": c["m"], "k": c["k"], "b": c["b"], "d": "1/%d" % round(1 / sp["d"]),
+                      "n_bucket": "(%d, %d]" % (2 ** (key[4] - 1) if key[4] else 0, 2 ** key[4]),
+                      "tuned_on_n": c["n"], "choice": r["kernel"],
+                      "stage_geometry": r["stage_geometry"], "candidates": r["candidates"]})
+        del codes, scales, xb
+    t_tune = time.perf_counter() - t_tune
     for i in range(48):
         c = wl.batched_case(i)
         v = torch.from_numpy(c["vals"]).to(dev)
@@ -825,19 +850,30 @@ def run_batched(torch, S, wl, dev, peaks, reps=5):
         for p, x, y in zip(p32, X32, Y32):
             p.run(x, y)
     t_32 = graph_time_us(torch, seq32, 2)
-    w_bytes = sum(p.info()["n_tiles"] * 256 + p.info()["n_tiles"] * 64 for p in plans)
+    infos = [p.info() for p in plans]
+    w_bytes = sum(q["n_tiles"] * (256 + 64) if q["kernel"] == 3 else q["nnzb"] * (q["b"] ** 2 + 4)
+                  for q in infos)
+    kinds = [q["kernel"] for q in infos]
+    n_bg = sum(1 for k_ in kinds if k_ == 4)
+    n_red = sum(1 for q in infos if q["kernel"] == 3 and q["n_reductions"] > 0)
     out = {"workload": "batched: 48 FFN-like products, E4M3 W + FP32 block scales, BF16 X",
            "us": round(t_batch, 1), "tflops_nz": round(flops / t_batch / 1e6, 2),
            "sequential_same_plans_us": round(t_seq, 1),
            "plain_fp32_sequential_us": round(t_32, 1),
            "speedup_vs_plain_fp32": round(t_32 / t_batch, 2),
            "speedup_vs_sequential": round(t_seq / t_batch, 3),
-           "packed_weight_gb": round(w_bytes / 1e9, 3), "gpu_launches": 1}
-    # one launch: its roofline is that of all 48 problems together, compulsory
-    # bytes = E4M3 values + one FP32 scale and one int32 column per block + row
-    # pointers + X once + Y once (BF16)
+           "packed_weight_gb": round(w_bytes / 1e9, 3),
+           "problems_on_bgather": n_bg, "problems_on_tc": len(kinds) - n_bg,
+           # one BGATHER launch, one tensor-core launch (both stage
+           # geometries merged), one reduction launch per split problem
+           "gpu_launches": (1 if n_bg else 0) + (1 if n_bg < len(kinds) else 0) + n_red,
+           "tuner": {"buckets": len(tuned), "seconds": round(t_tune, 1), "table": tuned}}
+    # the batch call as one unit: its roofline is that of all 48 problems
+    # together, compulsory bytes = E4M3 values + one FP32 scale and one int32
+    # column per block + row pointers + X once + Y once (BF16)
     out["roofline"] = roofline_obj([(flops, comp_bytes, t_batch * 1e-6)], peaks, "tensor",
-                                   kernel="tc_kernel (E4M3 weights, 48 problems)")
+                                   kernel="batch call: bgather_kernel (%d problems) + tc_kernel "
+                                          "(%d problems), E4M3 weights" % (n_bg, len(kinds) - n_bg))
     for p in plans + p32:
         p.close()
     return out
@@ -1004,7 +1040,7 @@ def run_transposed(torch, S, wl, dev, peaks, reps=15,
             if plan.status() != 0:
                 raise RuntimeError("plan status %d" % plan.status())
             us = statistics.median(ts)
-            row[name] = {"us": round(us, 2), "kernel": {1: "plain", 2: "gather", 3: "tc"}[
+            row[name] = {"us": round(us, 2), "kernel": {1: "plain", 2: "gather", 3: "tc", 4: "bgather"}[
                 plan.info()["kernel"]],
                 "tflops_nz": round(2.0 * len(c["brow"]) * b * b * N / us / 1e6, 2)}
             plan.close()

@@ -75,13 +75,19 @@ typedef enum { SPMM_F32 = 0, SPMM_F16 = 1, SPMM_BF16 = 2, SPMM_E4M3 = 3 } spmm_d
 /* Kernel family.  AUTO picks, for b = 1: TC for a static plan with 16-bit
  * W = X type, n_max >= 128, m and k multiples of 16 and on average at least
  * 4 non-zeros per non-empty 16 x 16 tile (the tensor cores then beat the
- * gather), else GATHER; for b >= 4: TC for 16-bit or E4M3 W, PLAIN for FP32
- * W. */
+ * gather), else GATHER; for b >= 4: BGATHER for a static plan with 16-bit X,
+ * 16-bit or E4M3 W and n_max <= 16 (n_max <= 8 for b = 16; small n: the
+ * tensor-core tiles would cost more than the product), else TC for 16-bit
+ * or E4M3 W, and PLAIN for FP32 W.  A choice tuned by spmm_tune for the
+ * plan's (b, density, n) bucket overrides these rules. */
 typedef enum {
     SPMM_KERNEL_AUTO = 0,
     SPMM_KERNEL_PLAIN = 1,   /* plain FP32 CUDA-core kernel: one thread per (row, column), F32 only */
     SPMM_KERNEL_GATHER = 2,  /* b = 1 gather kernel: 128-bit X row loads, warp-shuffle reductions */
-    SPMM_KERNEL_TC = 3       /* b >= 4 tensor-core kernel (tcgen05 + TMEM + TMA), 16-bit X */
+    SPMM_KERNEL_TC = 3,      /* b >= 4 tensor-core kernel (tcgen05 + TMEM + TMA), 16-bit X */
+    SPMM_KERNEL_BGATHER = 4  /* b in {4, 8, 16} CUDA-core block gather for n <= 16: static plans,
+                                16-bit X, W of the same type or E4M3; each block read once in CSR
+                                order, FP32 accumulation */
 } spmm_kernel;
 
 /* Host pattern (static mode): nnzb entries, block (brow[p], bcol[p]). */
@@ -288,17 +294,22 @@ int64_t spmm_bucket_size(int64_t m, int64_t k, int64_t d_max_num, int64_t d_max_
                          int64_t q_k);
 
 /*
- * spmm_batch_run -- `count` (<= 64) static TC plans with packed values in
- * one persistent tensor-core launch per stage geometry among the plans.
- * The launch's CTAs walk one schedule of (problem, work item, n tile)
- * units, precomputed on the host when this plan set is first run
- * (costliest units first) and cached; each CTA takes every gridDim-th unit
- * of it (no atomic work queue).  Each problem with rows split over several
- * work items adds one reduction launch.  d_X[i], n[i], ldx[i], d_Y[i],
- * ldy[i] as in spmm_run (ldx/ldy may be NULL for dense n).  All plans must
- * share w_dtype and x_dtype; uneven m, k, n, b and density are allowed.
- * The first call with a plan set allocates its schedule (make it outside
- * any stream capture); later calls are CUDA-graph capturable.
+ * spmm_batch_run -- `count` (<= 64) static TC or BGATHER plans with packed
+ * values, run as one persistent launch per kernel family: the BGATHER
+ * problems (small n, CUDA cores) in one launch, then the tensor-core
+ * problems in one launch.  Tensor-core plans of both stage geometries run
+ * in the geometry that holds most of the batch's work; the others use
+ * stage records cut for it (built once per plan on first use; results are
+ * identical).  The tensor-core launch's CTAs walk one schedule of
+ * (problem, work item, n tile) units, precomputed on the host when the
+ * plan set is first run (costliest units first) and cached; each CTA takes
+ * every gridDim-th unit of it (no atomic work queue).  Each problem with
+ * rows split over several work items adds one reduction launch.  d_X[i],
+ * n[i], ldx[i], d_Y[i], ldy[i] as in spmm_run (ldx/ldy may be NULL for
+ * dense n).  All plans must share w_dtype and x_dtype; uneven m, k, n, b and
+ * density are allowed.  The first call with a plan set allocates (its
+ * schedule, other-geometry stage records): make it outside any stream
+ * capture; later calls are CUDA-graph capturable.
  */
 spmm_status spmm_batch_run(int32_t count, spmm_plan *const *plans, const void *const *d_X,
                            const int64_t *n, const int64_t *ldx, void *const *d_Y,
@@ -396,6 +407,47 @@ spmm_status spmm_run_ell(spmm_plan *plan, const int32_t *d_ell_cols, int32_t ell
 spmm_status spmm_sddmm(spmm_plan *plan, const spmm_dpattern *pattern, const void *d_dY,
                        int64_t lddy, const void *d_X, int64_t ldx, int64_t n, void *d_dW,
                        spmm_dtype dw_dtype, void *stream);
+
+/*
+ * spmm_tune -- the autotuner of this library (the paper fixes its
+ * partitions ahead of time for a known pattern, Section 3.2; here the
+ * tuned quantity is the GPU launch configuration).  For the static product
+ * described by (m, k, n, b, types, pattern, d_values, d_scales, d_X, ldx)
+ * it builds one plan per candidate -- the tensor-core kernel with dense-tile
+ * and with sparse-tile stages, and the CUDA-core block gather (BGATHER)
+ * where n <= 16 and b >= 4 -- times `reps` runs of each on `stream` after
+ * two warm-up runs (CUDA events, median), and records the fastest for the
+ * product's bucket: (b, W and X types, ceil(log2 m), ceil(log2 k),
+ * round(log2(1/d)) with d the block density, ceil(log2 n)).  From then on
+ * spmm_plan_create, for a static plan with kernel AUTO and no forced
+ * stage_geometry, takes the tuned choice for its bucket (n = its n_max).
+ *   reps          : 1 .. 64.
+ *   out           : the choice and each candidate's median time (us, -1 if
+ *                   it failed).
+ * Allocates a Y scratch of m x n, synchronises `stream`; not for use inside
+ * a stream capture.  SPMM_ERR_UNSUPPORTED if no candidate could run.
+ */
+typedef struct {
+    int32_t kernel;          /* spmm_kernel */
+    int32_t stage_geometry;  /* TC: 1 dense-tile, 2 sparse-tile stages; 0 otherwise */
+} spmm_tune_choice;
+
+typedef struct {
+    spmm_tune_choice choice;
+    float best_us;
+    int32_t n_candidates;
+    int32_t cand_kernel[4], cand_geometry[4];
+    float cand_us[4];
+} spmm_tune_result;
+
+spmm_status spmm_tune(int64_t m, int64_t k, int64_t n, int32_t b, spmm_dtype w_dtype,
+                      spmm_dtype x_dtype, const spmm_pattern *pattern, const void *d_values,
+                      const float *d_scales, const void *d_X, int64_t ldx, int32_t reps,
+                      void *stream, spmm_tune_result *out);
+
+/* Forgets every tuned choice; the number of buckets tuned so far. */
+void spmm_tune_clear(void);
+int64_t spmm_tune_size(void);
 
 /* Thread-local message describing the last error on this thread ("" if none). */
 const char *spmm_last_error(void);

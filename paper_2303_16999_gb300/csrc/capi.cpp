@@ -70,10 +70,17 @@ static void free_plan(spmm_plan *p) {
     delete p;
 }
 
-static int pick_kernel(int req, int b, spmm_dtype w, spmm_dtype x) {
+static int pick_kernel(int req, int b, spmm_dtype w, spmm_dtype x, spmm_mode mode, int64_t n_max) {
     if (req != SPMM_KERNEL_AUTO) return req;
     if (b == 1) return SPMM_KERNEL_GATHER;
     if (w == SPMM_F32) return SPMM_KERNEL_PLAIN;
+    // small n: every block read once on the CUDA cores beats 16 x 16 tiles
+    // against 128-column MMA tiles
+    // (measured on the batched FFN-like shapes: 16 x 16 blocks win on the
+    // tensor cores from n = 11 on, smaller blocks keep the gather to n = 16)
+    if (mode == SPMM_STATIC && n_max <= (b == 16 ? kBgAutoMaxN16 : kBgAutoMaxN) &&
+        (x == SPMM_F16 || x == SPMM_BF16) && (w == x || w == SPMM_E4M3))
+        return SPMM_KERNEL_BGATHER;
     return SPMM_KERNEL_TC;
 }
 
@@ -92,6 +99,14 @@ static spmm_status check_types(int kernel, int b, spmm_dtype w, spmm_dtype x, in
             }
             if (w == x && w != SPMM_E4M3) return SPMM_OK;
             set_error("GATHER kernel needs W and X of one type in {F32, F16, BF16}");
+            return SPMM_ERR_UNSUPPORTED;
+        case SPMM_KERNEL_BGATHER:
+            if (b < 4) {
+                set_error("BGATHER kernel needs b in {4, 8, 16}");
+                return SPMM_ERR_UNSUPPORTED;
+            }
+            if (x16 && (w == x || w == SPMM_E4M3)) return SPMM_OK;
+            set_error("BGATHER kernel needs 16-bit X and W of the same type (or E4M3 W)");
             return SPMM_ERR_UNSUPPORTED;
         case SPMM_KERNEL_TC:
             if (m % kTile || k % kTile) {
@@ -453,12 +468,26 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
     if (opts) o = *opts;
     spmm_status st = validate_pattern(m, k, b, 0, nullptr, nullptr);
     if (st != SPMM_OK) return st;
-    int kernel = pick_kernel(o.kernel, b, w_dtype, x_dtype);
+    int kernel = pick_kernel(o.kernel, b, w_dtype, x_dtype, mode, n_max);
+    {
+        // the autotuner's choice for this bucket, if it has one
+        spmm_tune_choice tch{};
+        if (o.kernel == SPMM_KERNEL_AUTO && o.stage_geometry == 0 && mode == SPMM_STATIC &&
+            pattern && b >= 4 &&
+            tune_lookup(m, k, b, pattern->nnzb, n_max, w_dtype, x_dtype, &tch)) {
+            kernel = tch.kernel;
+            o.stage_geometry = tch.stage_geometry;
+        }
+    }
     if (o.kernel == SPMM_KERNEL_AUTO && b == 1 && mode == SPMM_STATIC &&
         b1_prefers_tc(m, k, n_max, w_dtype, x_dtype, pattern))
         kernel = SPMM_KERNEL_TC;
     st = check_types(kernel, b, w_dtype, x_dtype, m, k);
     if (st != SPMM_OK) return st;
+    if (kernel == SPMM_KERNEL_BGATHER && (mode != SPMM_STATIC || n_max > kBgMaxN)) {
+        set_error("BGATHER plans are static with n_max <= %d", kBgMaxN);
+        return SPMM_ERR_UNSUPPORTED;
+    }
     if (o.rows_per_group < 0 || o.rows_per_group > kMaxGroupRows || o.max_per_item < 0 ||
         o.col_tiles < 0 || o.col_tiles > 2 || o.groups < 0 || o.stage_geometry < 0 ||
         o.stage_geometry > 2 || o.dyn_chain < 0 || o.dyn_chain > 1 ||
@@ -514,7 +543,9 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
                 free_plan(p);
                 return SPMM_ERR_PATTERN;
             }
-            if (kernel == SPMM_KERNEL_GATHER) {
+            if (kernel == SPMM_KERNEL_BGATHER) {
+                // the block CSR is the whole plan: a CTA per block row
+            } else if (kernel == SPMM_KERNEL_GATHER) {
                 const int64_t avg = mb ? (p->nnzb + mb - 1) / mb : 0;
                 p->C = o.max_per_item ? o.max_per_item : (int)std::max<int64_t>(64, 2 * avg);
                 build_row_plan(mb, p->C, true, p->hp);
@@ -643,8 +674,10 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
             else
                 p->packed_bytes = nb * b * b * (int64_t)dtype_size(w_dtype);
             e = dalloc(p, (char **)&p->d_packed, p->packed_bytes);
+            // E4M3 scales: per 4 x 4 sub-square of each tile (TC), per
+            // block in CSR order (BGATHER)
             if (e == cudaSuccess && w_dtype == SPMM_E4M3)
-                e = dalloc(p, &p->d_tile_scale, nt * 16);
+                e = dalloc(p, &p->d_tile_scale, kernel == SPMM_KERNEL_TC ? nt * 16 : nb);
         }
         if (st == SPMM_OK && e == cudaSuccess && kernel == SPMM_KERNEL_TC &&
             p->mode == SPMM_STATIC) {
@@ -723,6 +756,8 @@ static spmm_status do_pack(spmm_plan *p, const void *d_values, const float *d_sc
     }
     e = (p->kernel == SPMM_KERNEL_TC) ? launch_pack_tiles(p, d_values, d_scales, nullptr, s)
                                       : launch_pack_csr(p, d_values, nullptr, s);
+    if (e == cudaSuccess && p->kernel == SPMM_KERNEL_BGATHER && p->wdt == SPMM_E4M3)
+        e = launch_gather_blocks(d_scales, p->d_perm, p->nnzb, 4, p->d_tile_scale, s);
     if (e != cudaSuccess) return cuda_fail(e, "pack");
     p->packed = true;
     return SPMM_OK;
@@ -754,6 +789,7 @@ static spmm_status launch_product(spmm_plan *p, const void *d_X, int64_t n, int6
         case SPMM_KERNEL_PLAIN: e = launch_plain(p, d_X, n, ldx, d_Y, ldy, s); break;
         case SPMM_KERNEL_GATHER: e = launch_gather(p, d_X, n, ldx, d_Y, ldy, s); break;
         case SPMM_KERNEL_TC: e = launch_tc(p, d_X, n, ldx, d_Y, ldy, s); break;
+        case SPMM_KERNEL_BGATHER: e = launch_bgather(p, d_X, n, ldx, d_Y, ldy, s); break;
         default: set_error("bad kernel"); return SPMM_ERR_ARG;
     }
     if (e == cudaSuccess && p->n_red > 0 && p->kernel != SPMM_KERNEL_PLAIN)
@@ -1016,8 +1052,9 @@ spmm_status spmm_batch_run(int32_t count, spmm_plan *const *plans, const void *c
     cudaStream_t s = (cudaStream_t)stream;
     for (int i = 0; i < count; ++i) {
         spmm_plan *p = plans[i];
-        if (!p || p->host_only || p->mode != SPMM_STATIC || p->kernel != SPMM_KERNEL_TC) {
-            set_error("batch: problem %d is not a device static TC plan", i);
+        if (!p || p->host_only || p->mode != SPMM_STATIC ||
+            (p->kernel != SPMM_KERNEL_TC && p->kernel != SPMM_KERNEL_BGATHER)) {
+            set_error("batch: problem %d is not a device static TC or BGATHER plan", i);
             return SPMM_ERR_UNSUPPORTED;
         }
         if (p->xdt != plans[0]->xdt || p->wdt != plans[0]->wdt) {
@@ -1039,11 +1076,33 @@ spmm_status spmm_batch_run(int32_t count, spmm_plan *const *plans, const void *c
                 return SPMM_ERR_ARG;
             }
     }
-    cudaError_t e = launch_tc_batch(count, plans, d_X, n, ldx, d_Y, ldy, s, true);
+    // one launch per kernel family: the small-n problems (BGATHER) first,
+    // then the tensor-core ones
+    spmm_plan *gp[kMaxBatchProblems], *tp[kMaxBatchProblems];
+    const void *gx[kMaxBatchProblems], *tx[kMaxBatchProblems];
+    void *gy[kMaxBatchProblems], *ty[kMaxBatchProblems];
+    int64_t gn[kMaxBatchProblems], tn[kMaxBatchProblems], glx[kMaxBatchProblems],
+        tlx[kMaxBatchProblems], gly[kMaxBatchProblems], tly[kMaxBatchProblems];
+    int ng = 0, nt = 0;
+    for (int i = 0; i < count; ++i) {
+        const int64_t lx = ldx ? ldx[i] : n[i], ly = ldy ? ldy[i] : n[i];
+        if (plans[i]->kernel == SPMM_KERNEL_BGATHER) {
+            gp[ng] = plans[i], gx[ng] = d_X[i], gy[ng] = d_Y[i], gn[ng] = n[i];
+            glx[ng] = lx, gly[ng] = ly;
+            ++ng;
+        } else {
+            tp[nt] = plans[i], tx[nt] = d_X[i], ty[nt] = d_Y[i], tn[nt] = n[i];
+            tlx[nt] = lx, tly[nt] = ly;
+            ++nt;
+        }
+    }
+    cudaError_t e = cudaSuccess;
+    if (ng) e = launch_bgather_batch(ng, gp, gx, gn, glx, gy, gly, s);
+    if (e == cudaSuccess && nt) e = launch_tc_batch(nt, tp, tx, tn, tlx, ty, tly, s, true);
     if (e != cudaSuccess) return cuda_fail(e, "batched launch");
     for (int i = 0; i < count; ++i) {
         spmm_plan *p = plans[i];
-        if (p->n_red > 0 && n[i] > 0) {
+        if (p->kernel == SPMM_KERNEL_TC && p->n_red > 0 && n[i] > 0) {
             e = launch_reduce(p, n[i], d_Y[i], ldy ? ldy[i] : n[i], s);
             if (e != cudaSuccess) return cuda_fail(e, "batched reduction");
         }

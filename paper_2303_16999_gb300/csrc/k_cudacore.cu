@@ -491,6 +491,11 @@ cudaError_t launch_pack_csr(const spmm_plan *p, const void *d_values, const int3
                 (const uint16_t *)d_values, p->d_perm, nmax, p->b, p->transposed ? 1 : 0, d_nnzb, st,
                 (uint16_t *)p->d_packed);
             break;
+        case 1:   // E4M3 codes (BGATHER plans)
+            pdl_launch(pack_csr_kernel<uint8_t>, dim3(g), dim3(256), 0, s,
+                (const uint8_t *)d_values, p->d_perm, nmax, p->b, p->transposed ? 1 : 0, d_nnzb, st,
+                (uint8_t *)p->d_packed);
+            break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -923,7 +923,8 @@ bool use_wide(const spmm_plan *p, int64_t n, int x3d) {
     return p->tc_geo == 0 && 2 * units >= (int64_t)SPMM_TC_WIDE_MIN * p->sm_count;
 }
 
-void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, int x3d) {
+void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, int x3d,
+               bool alt = false) {
     P.items = p->d_items;
     P.grp_row0 = p->d_grp_row0;
     P.grp_rows = p->d_grp_rows;
@@ -935,8 +936,8 @@ void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, i
     P.Y = Y;
     P.ws = p->d_ws;
     P.ws_row0 = p->d_ws_row0;
-    P.srec = p->d_srec;
-    P.sprog = p->d_sprog;
+    P.srec = alt ? p->d_srec_alt : p->d_srec;
+    P.sprog = alt ? p->d_sprog_alt : p->d_sprog;
     P.ldy = ldy;
     P.n = n;
     P.ntn = (int)((n + kNTile - 1) / kNTile);
@@ -1019,44 +1020,69 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
 namespace {
 cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *const *X,
                             const int64_t *n, const int64_t *ldx, void *const *Y,
-                            const int64_t *ldy, cudaStream_t s, bool schedule);
+                            const int64_t *ldy, cudaStream_t s, bool schedule, int geo);
+cudaError_t ensure_alt_records(spmm_plan *p, int geo, cudaStream_t s);
 }
 
-// Plans of both stage geometries in one batch: one launch per geometry.
+// Plans of both stage geometries in one batch: ONE launch, in the geometry
+// that holds most of the batch's work units; plans of the other geometry
+// use stage records cut for it (built once per plan, on first use).  Only
+// the stage shapes differ, never the arithmetic of a unit, so every result
+// is the same as in its own geometry.
 cudaError_t launch_tc_batch(int count, spmm_plan *const *plans, const void *const *X,
                             const int64_t *n, const int64_t *ldx, void *const *Y,
                             const int64_t *ldy, cudaStream_t s, bool schedule) {
     if (count <= 0 || count > kMaxBatch) return cudaErrorInvalidValue;
-    bool mixed = false;
-    for (int i = 1; i < count; ++i) mixed |= plans[i]->tc_geo != plans[0]->tc_geo;
-    if (!mixed) return launch_tc_group(count, plans, X, n, ldx, Y, ldy, s, schedule);
-    for (int geo = 0; geo < 2; ++geo) {
-        spmm_plan *gp[kMaxBatch];
-        const void *gx[kMaxBatch];
-        void *gy[kMaxBatch];
-        int64_t gn[kMaxBatch], glx[kMaxBatch], gly[kMaxBatch];
-        int c = 0;
-        for (int i = 0; i < count; ++i) {
-            if (plans[i]->tc_geo != geo) continue;
-            gp[c] = plans[i];
-            gx[c] = X[i];
-            gy[c] = Y[i];
-            gn[c] = n[i];
-            glx[c] = ldx ? ldx[i] : n[i];
-            gly[c] = ldy ? ldy[i] : n[i];
-            ++c;
-        }
-        if (!c) continue;
-        cudaError_t e = launch_tc_group(c, gp, gx, gn, glx, gy, gly, s, schedule);
+    int64_t units[2] = {0, 0};
+    for (int i = 0; i < count; ++i)
+        units[plans[i]->tc_geo & 1] += plans[i]->n_items * ((n[i] + kNTile - 1) / kNTile);
+    const int geo = units[1] > units[0] ? 1 : 0;
+    for (int i = 0; i < count; ++i) {
+        if (plans[i]->tc_geo == geo) continue;
+        cudaError_t e = ensure_alt_records(plans[i], geo, s);
         if (e != cudaSuccess) return e;
     }
-    return cudaSuccess;
+    return launch_tc_group(count, plans, X, n, ldx, Y, ldy, s, schedule, geo);
 }
 
 namespace {
+// Stage records of plan p cut for stage geometry `geo` (not its own) into
+// d_srec_alt / d_sprog_alt, allocated on first use (outside any stream
+// capture: the first batched launch of a plan set allocates).
+cudaError_t ensure_alt_records(spmm_plan *p, int geo, cudaStream_t s) {
+    if (p->alt_geo == geo) return cudaSuccess;
+    const int64_t E = std::max<int64_t>(p->n_entries, 1);
+    if (!p->d_srec_alt) {
+        void *a = nullptr, *b = nullptr;
+        cudaError_t e = cudaMalloc(&a, (size_t)E * kRecWords * sizeof(uint32_t));
+        if (e == cudaSuccess) e = cudaMalloc(&b, (size_t)E * 2 * kMmaStage * sizeof(uint32_t));
+        if (e != cudaSuccess) {
+            if (a) cudaFree(a);
+            return e;
+        }
+        p->allocations.push_back(a);
+        p->allocations.push_back(b);
+        p->device_bytes += E * (kRecWords + 2 * kMmaStage) * (int64_t)sizeof(uint32_t);
+        p->d_srec_alt = (uint32_t *)a;
+        p->d_sprog_alt = (uint32_t *)b;
+    }
+    const bool w8 = p->wdt == SPMM_E4M3;
+    const int tiles_cap = w8 ? (geo ? StageGeom<true, 1>::tiles : StageGeom<true, 0>::tiles)
+                             : (geo ? StageGeom<false, 1>::tiles : StageGeom<false, 0>::tiles);
+    const int ent_cap = w8 ? (geo ? StageGeom<true, 1>::ent : StageGeom<true, 0>::ent)
+                           : (geo ? StageGeom<false, 1>::ent : StageGeom<false, 0>::ent);
+    if (p->n_items > 0)
+        pdl_launch(stage_build_kernel, dim3((unsigned)p->n_items), dim3(kBuildWarps * 32), 0, s,
+            p->d_items, p->n_items, (const int32_t *)nullptr, p->d_status, p->d_ent_col,
+            p->d_ent_tbeg, p->d_ent_cover, ent_cap, tiles_cap, p->d_srec_alt, p->d_sprog_alt);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) p->alt_geo = geo;
+    return e;
+}
+
 cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *const *X,
                             const int64_t *n, const int64_t *ldx, void *const *Y,
-                            const int64_t *ldy, cudaStream_t s, bool schedule) {
+                            const int64_t *ldy, cudaStream_t s, bool schedule, int geo) {
     TcBatch B;
     std::lock_guard<std::mutex> lk(g_sched_mu);
     SchedKey key;
@@ -1071,7 +1097,7 @@ cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *cons
             e = encode_x(&B.maps4[i], &x3d, p->xdt == SPMM_BF16, X[i], p->k, n[i], lx,
                          kJointSlabs);
         if (e != cudaSuccess) return e;
-        fill_prob(B.prob[i], p, Y[i], n[i], ly, x3d);
+        fill_prob(B.prob[i], p, Y[i], n[i], ly, x3d, p->tc_geo != geo);
         B.prob[i].unit_base = base;
         base += p->n_items * B.prob[i].ntn;
         key.plans.push_back(p);
@@ -1087,7 +1113,7 @@ cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *cons
     if (!schedule) {
         // problems in submission order (serving: every launch is a new mix)
         const bool bf16 = plans[0]->xdt == SPMM_BF16, w8 = plans[0]->wdt == SPMM_E4M3;
-        return dispatch_batch(B, plans[0]->tc_geo, bf16, w8, plans[0]->sm_count, s);
+        return dispatch_batch(B, geo, bf16, w8, plans[0]->sm_count, s);
     }
     auto it = g_sched.find(key);
     if (it == g_sched.end()) {
@@ -1127,7 +1153,7 @@ cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *cons
     }
     B.units = it->second;
     const bool bf16 = plans[0]->xdt == SPMM_BF16, w8 = plans[0]->wdt == SPMM_E4M3;
-    return dispatch_batch(B, plans[0]->tc_geo, bf16, w8, plans[0]->sm_count, s);
+    return dispatch_batch(B, geo, bf16, w8, plans[0]->sm_count, s);
 }
 }  // namespace
 

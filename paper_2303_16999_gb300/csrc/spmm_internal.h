@@ -109,6 +109,10 @@ struct spmm_plan {
             *d_ent_tbeg = nullptr, *d_ent_cover = nullptr, *d_tile_row = nullptr, *d_blk_slot = nullptr,
             *d_blk_off = nullptr, *d_grp_ebeg = nullptr;
     uint32_t *d_srec = nullptr, *d_sprog = nullptr;  // TC: stage records and MMA programs
+    // TC, batched with plans of the other stage geometry: this plan's stage
+    // records cut for that geometry (built on first use), geometry alt_geo
+    uint32_t *d_srec_alt = nullptr, *d_sprog_alt = nullptr;
+    int alt_geo = -1;
     int tc_geo = 0;                // TC stage geometry: 0 dense tiles, 1 sparse tiles
     int col_tiles = 0;             // TC: column tiles per CTA, 0 automatic (launch-time choice)
     int64_t groups = 0;            // static TC: near-equal tile-row groups (0: equal partition by R)
@@ -187,6 +191,19 @@ cudaError_t launch_tc_batch(int count, spmm_plan *const *plans, const void *cons
 cudaError_t launch_quantize_e4m3(int64_t nnzb, int b, spmm_dtype src, const void *d_src,
                                  uint8_t *d_codes, float *d_scales, cudaStream_t s);
 constexpr int kMaxBatchProblems = 64;
+constexpr int kBgMaxBatch = 64;    // BGATHER problems per launch
+constexpr int kBgMaxN = 16;        // BGATHER: largest n
+constexpr int kBgAutoMaxN = 16;    // AUTO picks BGATHER (b = 4, 8, static) up to this n_max
+constexpr int kBgAutoMaxN16 = 8;   // ... and for b = 16 up to this one
+// the autotuner's choice for a static product's bucket (tune.cpp)
+bool tune_lookup(int64_t m, int64_t k, int b, int64_t nnzb, int64_t n, spmm_dtype w, spmm_dtype x,
+                 spmm_tune_choice *out);
+// BGATHER (k_bgather.cu): CUDA-core block gather for small n
+cudaError_t launch_bgather(const spmm_plan *p, const void *X, int64_t n, int64_t ldx, void *Y,
+                           int64_t ldy, cudaStream_t s);
+cudaError_t launch_bgather_batch(int count, spmm_plan *const *plans, const void *const *X,
+                                 const int64_t *n, const int64_t *ldx, void *const *Y,
+                                 const int64_t *ldy, cudaStream_t s);
 cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s);
 // dynamic TC plans: the whole re-partition, the value packing and the stage
 // records in one cooperative launch (when p->dyn_fused)

@@ -26,7 +26,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_SHAPE", 3: "ERR_PATTERN", 4: "ERR
 STATIC, DYNAMIC = 0, 1
 F32, F16, BF16, E4M3 = 0, 1, 2, 3
 KERNEL_AUTO, KERNEL_PLAIN, KERNEL_GATHER, KERNEL_TC = 0, 1, 2, 3
-KERNELS = {"auto": 0, "plain": 1, "gather": 2, "tc": 3}
+KERNELS = {"auto": 0, "plain": 1, "gather": 2, "tc": 3, "bgather": 4}
 ARRAYS = {"row_ptr": 0, "col_idx": 1, "perm": 2, "items": 3, "grp_row0": 4, "grp_rows": 5,
           "grp_ebeg": 6, "ent_col": 7, "ent_tbeg": 8, "tile_row": 9, "blk_slot": 10,
           "blk_off": 11, "ws_row0": 12, "red": 13, "ent_cover": 14, "src_index": 15}
@@ -40,7 +40,8 @@ EXPORTS = ["spmm_plan_create", "spmm_pack_values", "spmm_run", "spmm_run_host",
            "spmm_get_status", "spmm_plan_get_info", "spmm_plan_get_array",
            "spmm_plan_destroy", "spmm_equal_partition", "spmm_bucket_size", "spmm_batch_run",
            "spmm_last_error", "spmm_version", "spmm_gather_noalloc", "spmm_quantize_e4m3",
-           "spmm_sddmm", "spmm_run_ell", "spmm_plan_set_wait"]
+           "spmm_sddmm", "spmm_run_ell", "spmm_plan_set_wait", "spmm_tune", "spmm_tune_clear",
+           "spmm_tune_size"]
 
 
 class SpmmError(RuntimeError):
@@ -75,6 +76,13 @@ class PlanInfo(ctypes.Structure):
                                       "ws_rows", "n_reductions", "device_bytes")] + \
         [(n, ctypes.c_int32) for n in ("stage_geometry", "sddmm_form")] + \
         [(n, ctypes.c_int64) for n in ("row_begin", "row_end")]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("stage_geometry", ctypes.c_int32),
+                ("best_us", ctypes.c_float), ("n_candidates", ctypes.c_int32),
+                ("cand_kernel", ctypes.c_int32 * 4), ("cand_geometry", ctypes.c_int32 * 4),
+                ("cand_us", ctypes.c_float * 4)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -126,6 +134,10 @@ def lib():
                                  vp]
         L.spmm_run_ell.argtypes = [vp, vp, i32, vp, vp, i64, i64, vp, i64, vp]
         L.spmm_plan_set_wait.argtypes = [vp, i64, i32]
+        L.spmm_tune.argtypes = [i64, i64, i64, i32, i32, i32, ctypes.POINTER(Pattern), vp, vp, vp,
+                                i64, i32, vp, ctypes.POINTER(TuneResult)]
+        L.spmm_tune_clear.restype = None
+        L.spmm_tune_size.restype = i64
         L.spmm_last_error.restype = ctypes.c_char_p
         L.spmm_version.restype = ctypes.c_char_p
         L.serve_create.argtypes = [ctypes.POINTER(ServeConfig), ctypes.POINTER(vp)]
@@ -171,6 +183,36 @@ def spmm_run(plan, d_values, d_scales, dpat, d_X, n, ldx, d_Y, ldy, stream):
 
 def spmm_run_host(plan, h_X, n, ldx, h_Y, ldy, stream):
     return _check(lib().spmm_run_host(plan, h_X, n, ldx, h_Y, ldy, stream))
+
+
+def spmm_tune(m, k, b, brow, bcol, values, X, w_dtype=F16, x_dtype=None, scales=None, reps=7,
+              stream=None):
+    """Times the candidate launch configurations of this static product
+    (device values / scales / X as torch tensors) and records the fastest
+    for its (b, density, n) bucket; returns a dict with the choice and each
+    candidate's median time."""
+    x_dtype = w_dtype if x_dtype is None else x_dtype
+    brow = np.ascontiguousarray(brow, dtype=np.int32)
+    bcol = np.ascontiguousarray(bcol, dtype=np.int32)
+    pat = Pattern(len(brow), brow.ctypes.data, bcol.ctypes.data)
+    r = TuneResult()
+    _check(lib().spmm_tune(m, k, X.shape[1], b, w_dtype, x_dtype, ctypes.byref(pat),
+                           _ptr(values), _ptr(scales), _ptr(X), X.stride(0), reps,
+                           _stream_handle(stream), ctypes.byref(r)))
+    names = {v: k_ for k_, v in KERNELS.items()}
+    cands = [{"kernel": names.get(r.cand_kernel[i], r.cand_kernel[i]),
+              "stage_geometry": r.cand_geometry[i], "us": round(r.cand_us[i], 2)}
+             for i in range(r.n_candidates)]
+    return {"kernel": names.get(r.kernel, r.kernel), "stage_geometry": r.stage_geometry,
+            "best_us": round(r.best_us, 2), "candidates": cands}
+
+
+def spmm_tune_clear():
+    lib().spmm_tune_clear()
+
+
+def spmm_tune_size():
+    return lib().spmm_tune_size()
 
 
 def spmm_plan_set_wait(plan, limit_ns, stall):

@@ -159,7 +159,7 @@ def test_tc_plan_bit_exact(b):
     for m, k, d, R, C, nmax in cases:
         mb, kb = m // b, k // b
         brow, bcol = _rand(rng, mb, kb, int(d * mb * kb))
-        p = _plan(m, k, b, brow, bcol, rows_per_group=R, max_per_item=C, n_max=nmax)
+        p = _plan(m, k, b, brow, bcol, rows_per_group=R, max_per_item=C, n_max=nmax, kernel="tc")
         info = p.info()
         want = P.tc_plan(m, k, b, brow, bcol, info["rows_per_group"], info["max_per_item"],
                          groups=info["n_groups"])

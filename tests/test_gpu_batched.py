@@ -244,3 +244,71 @@ def test_batched_full_size_integers_exact():
         checks.exact_rows(Y, [0, 1, mb // 2, mb - 1], c["k"], c["b"], c["brow"], c["bcol"],
                           c["v"], c["X"], torch.bfloat16)
         plan.close()
+
+
+def test_batch_mixed_geometries_one_launch_equals_alone():
+    """Plans forced to different stage geometries run in one tensor-core
+    launch (the minority plan on stage records cut for the other geometry):
+    each result bit for bit equal to the plan run alone, and within the
+    bars against the oracle."""
+    cases = [_problem(950 + i, 1024, 2048, n, b, d)
+             for i, (b, d, n) in enumerate(((16, 1 / 16, 130), (8, 1 / 4, 200), (16, 1 / 4, 256)))]
+    plans, Xs, Ys = [], [], []
+    for c, geo in zip(cases, (1, 2, 1)):
+        v = torch.from_numpy(c["vals"]).to(torch.bfloat16)
+        p = S.Plan(c["m"], c["k"], c["n"], c["b"], w_dtype=S.BF16, brow=c["brow"], bcol=c["bcol"],
+                   kernel="tc", stage_geometry=geo)
+        assert p.info()["stage_geometry"] == geo - 1
+        p.pack(v.cuda())
+        plans.append(p)
+        Xs.append(_x(c, torch.bfloat16))
+        Ys.append(torch.full((c["m"], c["n"]), float("nan"), dtype=torch.bfloat16, device="cuda"))
+    for _ in range(2):
+        S.spmm_batch_run(plans, Xs, Ys)
+    torch.cuda.synchronize()
+    for c, p, X, Y in zip(cases, plans, Xs, Ys):
+        assert p.status() == 0
+        alone = p.run(X)
+        torch.cuda.synchronize()
+        assert torch.equal(alone, Y)
+        v = torch.from_numpy(c["vals"]).to(torch.bfloat16)
+        Yo = oracle.spmm(c["m"], c["k"], c["b"], c["brow"], c["bcol"], v, X.cpu())
+        A = oracle.spmm(c["m"], c["k"], c["b"], c["brow"], c["bcol"], np.abs(oracle.to_f64(v)),
+                        np.abs(oracle.to_f64(X.cpu())))
+        checks.assert_parity(Y.cpu(), Yo, oracle.block_fro(v), X.cpu(), A, torch.bfloat16,
+                             checks.max_terms(c["brow"], c["b"]))
+
+
+def test_tuner_choice_applies_to_auto_plans():
+    """spmm_tune times the candidates of a product's bucket and AUTO plans of
+    that bucket then take the fastest; the tuned plan is still within the
+    bars against the oracle."""
+    S.spmm_tune_clear()
+    assert S.spmm_tune_size() == 0
+    c = _problem(970, 2048, 4096, 6, 8, 1 / 8)
+    v = torch.from_numpy(c["vals"]).to(torch.bfloat16).cuda()
+    codes, scales = S.quantize_e4m3(v)
+    X = _x(c, torch.bfloat16)
+    r = S.spmm_tune(c["m"], c["k"], c["b"], c["brow"], c["bcol"], codes.view(torch.uint8), X,
+                    w_dtype=S.E4M3, x_dtype=S.BF16, scales=scales, reps=5)
+    assert S.spmm_tune_size() == 1
+    kinds = {q["kernel"] for q in r["candidates"]}
+    assert kinds == {"tc", "bgather"} and len(r["candidates"]) == 3
+    ok = [q for q in r["candidates"] if q["us"] > 0]
+    best = min(ok, key=lambda q: q["us"])
+    assert r["kernel"] == best["kernel"] and r["best_us"] == best["us"]
+    # a fresh AUTO plan in the same bucket (other values) takes the choice
+    c2 = _problem(971, 2048, 4096, 5, 8, 1 / 8)
+    p, codes2, scales2 = _e4m3_plan(c2)
+    info = p.info()
+    assert info["kernel"] == {"tc": 3, "bgather": 4}[r["kernel"]]
+    if r["kernel"] == "tc":
+        assert info["stage_geometry"] == r["stage_geometry"] - 1
+    X2 = _x(c2, torch.bfloat16)
+    Y = p.run(X2)
+    torch.cuda.synchronize()
+    v2 = oracle.e4m3_block_values(codes2.view(torch.uint8).numpy(), scales2.numpy())
+    Yo = oracle.spmm(c2["m"], c2["k"], 8, c2["brow"], c2["bcol"], v2, X2.cpu())
+    assert oracle.normwise_err(Y.cpu(), Yo, oracle.block_fro(v2), X2.cpu()) <= 4e-3
+    S.spmm_tune_clear()
+    assert S.spmm_tune_size() == 0
