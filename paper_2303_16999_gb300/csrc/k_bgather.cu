@@ -22,6 +22,8 @@
 // E4M3 blocks are decoded and scaled in FP32 (decode(code) * scale, the
 // oracle's value up to one FP32 rounding).  Outputs are rounded once to the
 // 16-bit output type.
+#include <atomic>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -86,12 +88,36 @@ __device__ __forceinline__ void e4m3x4(uint32_t w, float sc, float *o) {
 // A 16-byte shared-memory read kept in program order (an asm volatile: the
 // compiler must not hoist a block's 16 rows of X reads ahead of their use,
 // which would hold them all in registers at once).
-__device__ __forceinline__ uint4 lds128(const uint4 *p) {
+__device__ __forceinline__ uint4 lds128(const uint8_t *p) {
     uint4 v;
     asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
                  : "r"((uint32_t)__cvta_generic_to_shared(p)));
     return v;
+}
+
+// Asynchronous global -> shared copies (cp.async): the bytes land in shared
+// memory without passing through registers, so a warp keeps several rounds
+// of W rows and X rows in flight at no register cost.
+__device__ __forceinline__ uint32_t saddr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+template <int N>
+__device__ __forceinline__ void cp_async(void *dst, const void *src) {
+    if constexpr (N == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr(dst)), "l"(src)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(saddr(dst)), "l"(src),
+                     "n"(N)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // 8 consecutive 16-bit values (one 16-byte piece) -> floats.
@@ -106,34 +132,58 @@ __device__ __forceinline__ void unpack8(const uint4 v, float *x) {
     }
 }
 
-// Shared memory: per warp, 32 staged X rows of up to kBgMaxN 16-bit values
-// (block group g's row l at g * B + l), reused after the main loop for the
-// warps' FP32 partials (B x n per warp).
-constexpr int kBgStageBytes = 32 * kBgMaxN * 2;
-static_assert(kBgStageBytes >= 16 * kBgMaxN * 4, "partials fit the staging area");
+// The first NC 16-bit values of an X row slot -> floats.
+template <typename T, int NC>
+__device__ __forceinline__ void unpack_row(const uint8_t *slot, float *x) {
+    if constexpr (NC >= 8) {
+#pragma unroll
+        for (int v = 0; v < NC / 8; ++v) unpack8<T>(lds128(slot + 16 * v), x + 8 * v);
+    } else if constexpr (NC == 4) {
+        const uint2 u = *reinterpret_cast<const uint2 *>(slot);
+        const float2 a = Cv<T>::f2(u.x), b = Cv<T>::f2(u.y);
+        x[0] = a.x, x[1] = a.y, x[2] = b.x, x[3] = b.y;
+    } else if constexpr (NC == 2) {
+        const float2 a = Cv<T>::f2(*reinterpret_cast<const uint32_t *>(slot));
+        x[0] = a.x, x[1] = a.y;
+    } else {
+        x[0] = Cv<T>::f(*reinterpret_cast<const T *>(slot));
+    }
+}
+// Shared memory: per warp a ring of kBgStages rounds.  One round holds the
+// 32 X rows of the warp's blocks (block group g's row l at g * B + l, up to
+// kBgMaxN 16-bit values, 32 bytes a row), each lane's W row (up to 32
+// bytes) and each lane's block scale (E4M3).  After the main loop the ring
+// holds the warp's FP32 partials (B x n).
+constexpr int kBgStages = 4;
+constexpr int kBgXBytes = 32 * 32;
+constexpr int kBgWBytes = 32 * 32;
+constexpr int kBgStageBytes = kBgXBytes + kBgWBytes + 32 * 4;
+constexpr int kBgRingBytes = kBgStages * kBgStageBytes;
+constexpr int kBgSmemBytes = kBgWarps * kBgRingBytes;
+static_assert(kBgMaxN * 2 <= 32, "an X row fits its 32-byte slot");
+static_assert(kBgRingBytes >= 16 * kBgMaxN * 4, "partials fit the ring");
+static_assert(kBgStageBytes % 16 == 0 && kBgRingBytes % 16 == 0, "16-byte aligned stages");
 
 // Raw bytes of one block row of W: B values of 16 bits (B / 2 words) or B
-// E4M3 codes (B / 4 words).
+// E4M3 codes (B / 4 words), read back from the lane's shared-memory slot.
 template <int B, bool W8> struct RawRow {
     static constexpr int kWords = W8 ? B / 4 : B / 2;
     uint32_t w[kWords];
 };
 template <int B, bool W8>
-__device__ __forceinline__ void fetch_row(const BgProb &P, int64_t q, int i, RawRow<B, W8> &r) {
-    const uint8_t *src = P.vals + (q * (B * B) + i * B) * (W8 ? 1 : 2);
+__device__ __forceinline__ void read_row(const uint8_t *slot, RawRow<B, W8> &r) {
     if constexpr (RawRow<B, W8>::kWords == 8) {
-        const uint4 v0 = *reinterpret_cast<const uint4 *>(src);
-        const uint4 v1 = *reinterpret_cast<const uint4 *>(src + 16);
+        const uint4 v0 = lds128(slot), v1 = lds128(slot + 16);
         r.w[0] = v0.x, r.w[1] = v0.y, r.w[2] = v0.z, r.w[3] = v0.w;
         r.w[4] = v1.x, r.w[5] = v1.y, r.w[6] = v1.z, r.w[7] = v1.w;
     } else if constexpr (RawRow<B, W8>::kWords == 4) {
-        const uint4 v = *reinterpret_cast<const uint4 *>(src);
+        const uint4 v = lds128(slot);
         r.w[0] = v.x, r.w[1] = v.y, r.w[2] = v.z, r.w[3] = v.w;
     } else if constexpr (RawRow<B, W8>::kWords == 2) {
-        const uint2 v = *reinterpret_cast<const uint2 *>(src);
+        const uint2 v = *reinterpret_cast<const uint2 *>(slot);
         r.w[0] = v.x, r.w[1] = v.y;
     } else {
-        r.w[0] = *reinterpret_cast<const uint32_t *>(src);
+        r.w[0] = *reinterpret_cast<const uint32_t *>(slot);
     }
 }
 template <typename T, int B, bool W8>
@@ -151,20 +201,56 @@ __device__ __forceinline__ void decode_row(const RawRow<B, W8> &r, float sc, flo
     }
 }
 
-// Block row r of problem P, this warp's share `part` of its wpr warps.
-// NC: columns kept per lane (n rounded up to a multiple of 8, at most 16).
-// The warp's blocks are taken in rounds of NB (one per block group); the
-// column indices of 32 / NB rounds come in one coalesced load, so a round's
-// W row and X rows are requested together.
+// Requests round u of a warp's share of a block row into ring stage
+// u % kBgStages: lane (g, i) copies row i of block group g's W block (and
+// its scale) and row i of the X rows that block multiplies.  X rows go by
+// cp.async when they are 16-byte aligned, else by plain loads (n values,
+// zero-filled to NC).  Called by the whole warp; always commits one group.
 template <typename T, int B, bool W8, int NC>
-__device__ __forceinline__ void bg_row(const BgProb &P, int32_t r, int part, uint8_t *stage) {
+__device__ __forceinline__ void bg_issue(const BgProb &P, int32_t q, int32_t end, int64_t col,
+                                         uint8_t *st, int lane, int g, int i) {
+    constexpr int WB = W8 ? B : 2 * B;             // bytes of one W row
+    if (q < end) {
+        const uint8_t *wsrc = P.vals + (int64_t)q * (B * B) * (W8 ? 1 : 2) + i * WB;
+        uint8_t *wdst = st + kBgXBytes + lane * 32;
+        if constexpr (WB == 32) {
+            cp_async<16>(wdst, wsrc);
+            cp_async<16>(wdst + 16, wsrc + 16);
+        } else {
+            cp_async<WB>(wdst, wsrc);
+        }
+        if (W8) cp_async<4>(st + kBgXBytes + kBgWBytes + lane * 4, P.scales + q);
+        const T *xsrc = reinterpret_cast<const T *>(P.X) + (col * B + i) * P.ldx;
+        uint8_t *xdst = st + (g * B + i) * 32;
+        if (P.xvec) {
+            // NC values (at least 4 bytes); the row is 16-byte aligned and
+            // its first value is in range, so the piece stays in bounds
+            if constexpr (NC >= 8) {
+#pragma unroll
+                for (int v = 0; v < NC / 8; ++v) cp_async<16>(xdst + 16 * v, xsrc + 8 * v);
+            } else {
+                cp_async<(NC * 2 > 4 ? NC * 2 : 4)>(xdst, xsrc);
+            }
+        } else {
+            uint16_t *d = reinterpret_cast<uint16_t *>(xdst);
+            for (int j = 0; j < NC; ++j) d[j] = j < P.n ? (uint16_t)Cv<T>::bits(xsrc[j]) : 0;
+        }
+    }
+    cp_async_commit();
+}
+
+// Block row r of problem P, this warp's share `part` of its wpr warps.
+// NC: columns kept per lane (n rounded up to 1, 2, 4, 8 or 16).
+// The warp's blocks are taken in rounds of NB (one per block group); the
+// column indices of 32 / NB rounds come in one coalesced load (the next
+// batch's is requested one batch ahead), and kBgStages rounds of W rows and
+// X rows are in flight while the oldest one is multiplied.
+template <typename T, int B, bool W8, int NC>
+__device__ __forceinline__ void bg_row(const BgProb &P, int32_t r, int part, uint8_t *ring) {
     constexpr int NB = 32 / B;                      // blocks per warp round
-    constexpr int NV = NC / 8;                      // 16-byte pieces of an X row
+    constexpr int RB = 32 / NB;                     // rounds per column batch
     const int lane = threadIdx.x & 31;
     const int i = lane % B, g = lane / B;
-    const int n = P.n;
-    uint4 *srow = reinterpret_cast<uint4 *>(stage) + (g * B + i) * (kBgMaxN / 8);
-    const uint4 *sblk = reinterpret_cast<const uint4 *>(stage) + (g * B) * (kBgMaxN / 8);
     float acc[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] = 0.f;
@@ -173,77 +259,85 @@ __device__ __forceinline__ void bg_row(const BgProb &P, int32_t r, int part, uin
     const int32_t first = beg + part * NB;          // slot of round 0, block group 0
     const int32_t stride = P.wpr * NB;              // slots between rounds
     const int32_t rounds = end > first ? (end - first + stride - 1) / stride : 0;
-    for (int32_t t0 = 0; t0 < rounds; t0 += 32 / NB) {
-        // column of round t0 + l / NB, block group l % NB, in lane l
-        int32_t cols;
-        {
-            const int32_t q = first + (t0 + lane / NB) * stride + lane % NB;
-            cols = q < end ? P.col_idx[q] : 0;
-        }
-        const int32_t tn = min(rounds - t0, 32 / NB);
-        for (int32_t u = 0; u < tn; ++u) {
-            const int32_t q = first + (t0 + u) * stride + g;
-            const int64_t col = __shfl_sync(0xffffffffu, cols, u * NB + g);
-            const bool ok = q < end;
-            RawRow<B, W8> wr;
-            float sc = 1.f;
-            if (ok) {
-                fetch_row<B, W8>(P, q, i, wr);
-                if (W8) sc = P.scales[q];
-                const T *src = reinterpret_cast<const T *>(P.X) + (col * B + i) * P.ldx;
-                if (P.xvec) {
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) srow[v] = reinterpret_cast<const uint4 *>(src)[v];
-                } else {
-                    uint16_t *dst = reinterpret_cast<uint16_t *>(srow);
-                    for (int j = 0; j < NC; ++j) dst[j] = j < n ? (uint16_t)Cv<T>::bits(src[j]) : 0;
-                }
-            }
-            __syncwarp();
-            if (ok) {
-                float w[B];
-                decode_row<T, B, W8>(wr, sc, w);
-#pragma unroll
-                for (int l = 0; l < B; ++l) {
-#pragma unroll
-                    for (int v = 0; v < NV; ++v) {
-                        float x[8];
-                        unpack8<T>(lds128(sblk + l * (kBgMaxN / 8) + v), x);
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) acc[v * 8 + e] = fmaf(w[l], x[e], acc[v * 8 + e]);
-                    }
-                }
-            }
-            __syncwarp();
-        }
+    // column of round (batch * RB + l / NB), block group l % NB, in lane l
+    int32_t cols = 0, cols_next = 0;
+    {
+        const int32_t q0 = first + (lane / NB) * stride + lane % NB;
+        const int32_t q1 = q0 + RB * stride;
+        if (q0 < end) cols = P.col_idx[q0];
+        if (q1 < end) cols_next = P.col_idx[q1];
     }
+    int32_t u = 0;                                  // next round to request
+    auto issue_next = [&]() {
+        if (u < rounds) {
+            if (u > 0 && u % RB == 0) {
+                cols = cols_next;
+                const int32_t q2 = first + (u + RB + lane / NB) * stride + lane % NB;
+                cols_next = q2 < end ? P.col_idx[q2] : 0;
+            }
+            const int64_t col = __shfl_sync(0xffffffffu, cols, (u % RB) * NB + g);
+            bg_issue<T, B, W8, NC>(P, first + u * stride + g, end, col,
+                                   ring + (u % kBgStages) * kBgStageBytes, lane, g, i);
+        } else {
+            cp_async_commit();
+        }
+        ++u;
+    };
+#pragma unroll
+    for (int s = 0; s < kBgStages; ++s) issue_next();
+    for (int32_t t = 0; t < rounds; ++t) {
+        cp_async_wait<kBgStages - 1>();             // this lane's copies of round t
+        __syncwarp();                               // ... and every lane's
+        const uint8_t *st = ring + (t % kBgStages) * kBgStageBytes;
+        if (first + t * stride + g < end) {
+            RawRow<B, W8> wr;
+            read_row<B, W8>(st + kBgXBytes + lane * 32, wr);
+            const float sc =
+                W8 ? *reinterpret_cast<const float *>(st + kBgXBytes + kBgWBytes + lane * 4) : 1.f;
+            float w[B];
+            decode_row<T, B, W8>(wr, sc, w);
+#pragma unroll
+            for (int l = 0; l < B; ++l) {
+                float x[NC];
+                unpack_row<T, NC>(st + (g * B + l) * 32, x);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) acc[c] = fmaf(w[l], x[c], acc[c]);
+            }
+        }
+        __syncwarp();                               // stage t % S is free again
+        issue_next();
+    }
+    cp_async_wait<0>();
+    __syncwarp();
     // the warp's block groups: fixed butterfly over the lane bits above B
 #pragma unroll
     for (int o = B; o < 32; o <<= 1) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], o);
     }
-    __syncwarp();
-    float *part_out = reinterpret_cast<float *>(stage);   // B x n partials of this warp
+    float *part_out = reinterpret_cast<float *>(ring);   // B x n partials of this warp
     if (g == 0) {
 #pragma unroll
         for (int c = 0; c < NC; ++c)
-            if (c < n) part_out[i * n + c] = acc[c];
+            if (c < P.n) part_out[i * P.n + c] = acc[c];
     }
 }
 
 template <typename T, int B, bool W8>
-__device__ __forceinline__ void bg_row_n(const BgProb &P, int32_t r, int part, uint8_t *stage) {
-    if (P.n > 8) bg_row<T, B, W8, 16>(P, r, part, stage);
-    else bg_row<T, B, W8, 8>(P, r, part, stage);
+__device__ __forceinline__ void bg_row_n(const BgProb &P, int32_t r, int part, uint8_t *ring) {
+    if (P.n > 8) bg_row<T, B, W8, 16>(P, r, part, ring);
+    else if (P.n > 4) bg_row<T, B, W8, 8>(P, r, part, ring);
+    else if (P.n > 2) bg_row<T, B, W8, 4>(P, r, part, ring);
+    else if (P.n > 1) bg_row<T, B, W8, 2>(P, r, part, ring);
+    else bg_row<T, B, W8, 1>(P, r, part, ring);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBgThreads, 3) bgather_kernel(const __grid_constant__ BgBatch Bt) {
     pdl_enter();
-    __shared__ __align__(16) uint8_t stage_all[kBgWarps * kBgStageBytes];
+    extern __shared__ __align__(128) uint8_t bg_smem[];
     const int warp = threadIdx.x >> 5;
-    uint8_t *stage = stage_all + warp * kBgStageBytes;
+    uint8_t *ring = bg_smem + warp * kBgRingBytes;
     for (int64_t u = blockIdx.x; u < Bt.total_units; u += gridDim.x) {
         int pi = 0;
         while (pi + 1 < Bt.nprob && Bt.prob[pi + 1].unit_base <= u) ++pi;
@@ -253,15 +347,15 @@ __global__ void __launch_bounds__(kBgThreads, 3) bgather_kernel(const __grid_con
         const int part = warp % P.wpr;
         if (P.w8) {
             switch (P.b) {
-                case 16: bg_row_n<T, 16, true>(P, r, part, stage); break;
-                case 8: bg_row_n<T, 8, true>(P, r, part, stage); break;
-                default: bg_row_n<T, 4, true>(P, r, part, stage); break;
+                case 16: bg_row_n<T, 16, true>(P, r, part, ring); break;
+                case 8: bg_row_n<T, 8, true>(P, r, part, ring); break;
+                default: bg_row_n<T, 4, true>(P, r, part, ring); break;
             }
         } else {
             switch (P.b) {
-                case 16: bg_row_n<T, 16, false>(P, r, part, stage); break;
-                case 8: bg_row_n<T, 8, false>(P, r, part, stage); break;
-                default: bg_row_n<T, 4, false>(P, r, part, stage); break;
+                case 16: bg_row_n<T, 16, false>(P, r, part, ring); break;
+                case 8: bg_row_n<T, 8, false>(P, r, part, ring); break;
+                default: bg_row_n<T, 4, false>(P, r, part, ring); break;
             }
         }
         __syncthreads();
@@ -274,7 +368,7 @@ __global__ void __launch_bounds__(kBgThreads, 3) bgather_kernel(const __grid_con
             if (rr >= P.mb) continue;
             float sum = 0.f;
             for (int w = 0; w < P.wpr; ++w)
-                sum += reinterpret_cast<const float *>(stage_all + (rs * P.wpr + w) * kBgStageBytes)[k];
+                sum += reinterpret_cast<const float *>(bg_smem + (rs * P.wpr + w) * kBgRingBytes)[k];
             const int ii = k / P.n, jj = k - ii * P.n;
             Y[((int64_t)rr * P.b + ii) * P.ldy + jj] = Cv<T>::t(sum);
         }
@@ -308,11 +402,11 @@ cudaError_t launch_bgather_batch(int count, spmm_plan *const *plans, const void 
         P.b = p->b;
         P.mb = (int32_t)(p->m / p->b);
         P.w8 = p->wdt == SPMM_E4M3 ? 1 : 0;
-        // warps per block row: about two rounds (of 32 / b blocks) per
-        // warp, at most the CTA's 8 warps (the rounds are latency-bound, so
-        // more warps in flight beat longer warps)
+        // warps per block row: about one ring of rounds (of 32 / b blocks)
+        // per warp, so a warp's whole share is requested at once, at most
+        // the CTA's 8 warps
         const int64_t per_row = P.mb ? (p->nnzb + P.mb - 1) / P.mb : 0;
-        const int64_t per_warp = 2 * (32 / p->b);
+        const int64_t per_warp = kBgStages * (32 / p->b);
         int wpr = 1;
         while (wpr < kBgWarps && per_row > (int64_t)wpr * per_warp) wpr <<= 1;
         P.wpr = wpr;
@@ -324,10 +418,19 @@ cudaError_t launch_bgather_batch(int count, spmm_plan *const *plans, const void 
     Bt.nprob = c;
     Bt.total_units = base;
     const unsigned grid = (unsigned)(base < (1 << 30) ? base : (1 << 30));
-    if (plans[0]->xdt == SPMM_BF16)
-        pdl_launch(bgather_kernel<__nv_bfloat16>, dim3(grid), dim3(kBgThreads), 0, s, Bt);
-    else
-        pdl_launch(bgather_kernel<__half>, dim3(grid), dim3(kBgThreads), 0, s, Bt);
+    if (plans[0]->xdt == SPMM_BF16) {
+        static std::atomic<uint64_t> attrs{0};
+        const cudaError_t e =
+            set_smem_attrs_once(attrs, bgather_kernel<__nv_bfloat16>, kBgSmemBytes, false);
+        if (e != cudaSuccess) return e;
+        pdl_launch(bgather_kernel<__nv_bfloat16>, dim3(grid), dim3(kBgThreads), kBgSmemBytes, s,
+                   Bt);
+    } else {
+        static std::atomic<uint64_t> attrs{0};
+        const cudaError_t e = set_smem_attrs_once(attrs, bgather_kernel<__half>, kBgSmemBytes, false);
+        if (e != cudaSuccess) return e;
+        pdl_launch(bgather_kernel<__half>, dim3(grid), dim3(kBgThreads), kBgSmemBytes, s, Bt);
+    }
     return cudaGetLastError();
 }
 
