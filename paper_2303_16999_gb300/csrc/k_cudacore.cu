@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "pdl.cuh"
 #include "spmm_internal.h"
@@ -175,46 +176,231 @@ __global__ void __launch_bounds__(256) gather_kernel(
     }
 }
 
-// n <= V (one vector per X row).  The row's indices and values stream in as
-// 16-byte / 8-byte vectors, four non-zeros per lane per load and kRounds
-// loads per lane in flight, and every lane gathers the X rows of its own
-// non-zeros.  With SX, X (k x n, at most a few hundred KB at these n) is
-// first copied into shared memory by the persistent block: a warp's 32
-// random X reads then cost a few bank wavefronts instead of 32 L1 lines,
-// which was the limit at n = 1 (about one cycle per non-zero per SM), and
-// the kernel is left bound by the HBM stream of indices and values.  The
-// lanes' sums meet in a fixed butterfly (deterministic).
-template <typename T, int V, bool SX>
+// n <= V (one vector per X row): the HBM-bound case, 4 + sizeof(T) bytes
+// per non-zero.  Each warp streams the column indices and values of its
+// items (rows or row chunks, taken with a grid stride) through a ring of
+// kG1Stages chunks of 256 non-zeros in shared memory: every lane requests 8
+// indices and 8 values per chunk with cp.async, so about kG1Stages chunks
+// per warp are in flight without holding registers, and the stream runs on
+// across item boundaries with no drain.  A chunk starts at a multiple of 8
+// non-zeros (16-byte aligned indices and values); non-zeros outside the
+// item are masked, and copies stop at the end of the arrays.  Each lane
+// adds its own non-zeros in order and the lanes meet in a fixed butterfly
+// (deterministic).  X (k x n, up to the shared memory the ring leaves: 79 KB
+// of 16-bit values, 31 KB of FP32) is copied into shared memory once per CTA
+// (by cp.async when its rows are contiguous), so the X gathers are
+// shared-memory reads.
+constexpr int kG1Stages = 6;
+constexpr int kG1Warps = 16;
+constexpr int kG1Chunk = 256;                        // non-zeros per chunk, 8 per lane
+// one stage: the chunk's indices, then its values
+template <typename T> __host__ __device__ constexpr int g1_stage_bytes() { return kG1Chunk * (4 + (int)sizeof(T)); }
+template <typename T> __host__ __device__ constexpr int g1_ring_bytes() { return kG1Stages * g1_stage_bytes<T>(); }
+
+struct G1Meta {
+    int32_t beg, end, row, slot, base, last, pad0, pad1;
+};
+constexpr int kG1MetaBytes = kG1Warps * kG1Stages * (int)sizeof(G1Meta);
+template <typename T> __host__ __device__ constexpr int g1_fixed_smem() {
+    return kG1Warps * g1_ring_bytes<T>() + kG1MetaBytes;
+}
+// shared memory left for X (of the 227 KB a CTA may hold, 1 KB spare)
+template <typename T> __host__ __device__ constexpr int g1_x_budget() { return 226 * 1024 - g1_fixed_smem<T>(); }
+static_assert(g1_x_budget<float>() >= 16 * 1024, "room for X");
+
+// cp.async of 16 bytes of which the first src_bytes come from src and the
+// rest are zero-filled.
+__device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
+    const int32_t *__restrict__ items, int64_t n_items, const int32_t *__restrict__ col_idx,
+    const T *__restrict__ vals, int64_t cap, const T *__restrict__ X, int64_t ldx, int64_t k,
+    T *__restrict__ Y, int64_t ldy, float *__restrict__ ws, const int64_t *__restrict__ ws_row0,
+    const int32_t *__restrict__ n_items_dev, const int32_t *__restrict__ status) {
+    pdl_enter();
+    constexpr int VB = 8 * (int)sizeof(T);          // value bytes per lane per chunk (16 or 32)
+    constexpr int kStage = g1_stage_bytes<T>(), kRing = g1_ring_bytes<T>();
+    extern __shared__ __align__(128) uint8_t g1_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (n_items_dev) {
+        if (*status != 0) return;
+        n_items = min(n_items, (int64_t)*n_items_dev);
+    }
+    uint8_t *ring = g1_smem + warp * kRing;
+    G1Meta *meta = reinterpret_cast<G1Meta *>(g1_smem + kG1Warps * kRing) + warp * kG1Stages;
+    const int64_t W = (int64_t)gridDim.x * kG1Warps;
+    // the item being requested (c_*) and the next one's header (x_*), read
+    // one item ahead so the request stream never waits on a header
+    int64_t it = (int64_t)blockIdx.x * kG1Warps + warp;
+    int32_t c_beg = 0, c_end = 0, c_row = 0, c_slot = -1, c_pos = 0;
+    int32_t x_beg = 0, x_end = 0, x_row = 0, x_slot = -1;
+    if (it < n_items) {
+        const int32_t *d = items + it * kItemFields;
+        c_row = d[0], c_beg = d[1], c_end = d[2], c_slot = d[5];
+        c_pos = c_beg & ~7;
+    }
+    if (it + W < n_items) {
+        const int32_t *d = items + (it + W) * kItemFields;
+        x_row = d[0], x_beg = d[1], x_end = d[2], x_slot = d[5];
+    }
+    // X first (its own cp.async group, so it can be waited for alone)
+    T *xs = reinterpret_cast<T *>(g1_smem + g1_fixed_smem<T>());
+    const int64_t xbytes = k * V * (int64_t)sizeof(T);
+    const bool xbulk = ldx == V && ((uintptr_t)X % 16) == 0;
+    if (xbulk) {
+        const int64_t pieces = xbytes / 16;
+        for (int64_t i = threadIdx.x; i < pieces; i += blockDim.x)
+            cp_async16_zfill(reinterpret_cast<uint8_t *>(xs) + 16 * i,
+                             reinterpret_cast<const uint8_t *>(X) + 16 * i, 16);
+        for (int64_t i = pieces * 16 / (int64_t)sizeof(T) + threadIdx.x; i < k * V; i += blockDim.x)
+            xs[i] = X[i];
+    } else {
+#pragma unroll 8
+        for (int64_t i = threadIdx.x; i < k; i += blockDim.x)
+            *reinterpret_cast<Pack<T, V> *>(xs + i * V) =
+                *reinterpret_cast<const Pack<T, V> *>(X + i * ldx);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    int32_t issued = 0;
+    int is = 0;                                       // ring stage of the next request
+    const int32_t cap32 = (int32_t)min(cap, (int64_t)INT32_MAX);
+    auto issue_next = [&]() {
+        if (it < n_items) {
+            const int s = is;
+            is = is + 1 == kG1Stages ? 0 : is + 1;
+            uint8_t *st = ring + s * kStage;
+            const int32_t pos = c_pos + 8 * lane;
+            // entries of this lane's 8 that the arrays hold; the others lie
+            // past every item's end and are masked, so nothing is read there
+            const int ne = max(0, min(8, cap32 - pos));
+            if (ne > 0) {
+                cp_async16_zfill(st + lane * 32, col_idx + pos, min(ne, 4) * 4);
+                if (ne > 4) cp_async16_zfill(st + lane * 32 + 16, col_idx + pos + 4, (ne - 4) * 4);
+                uint8_t *vd = st + kG1Chunk * 4 + lane * VB;
+                const uint8_t *vs = reinterpret_cast<const uint8_t *>(vals + pos);
+                const int vbytes = ne * (int)sizeof(T);
+                cp_async16_zfill(vd, vs, min(vbytes, 16));
+                if (VB == 32 && vbytes > 16) cp_async16_zfill(vd + 16, vs + 16, vbytes - 16);
+            }
+            const bool last = c_pos + kG1Chunk >= c_end;
+            if (lane == 0) meta[s] = G1Meta{c_beg, c_end, c_row, c_slot, c_pos, last ? 1 : 0, 0, 0};
+            c_pos += kG1Chunk;
+            if (last) {
+                it += W;
+                c_beg = x_beg, c_end = x_end, c_row = x_row, c_slot = x_slot;
+                c_pos = c_beg & ~7;
+                if (it + W < n_items) {
+                    const int32_t *d = items + (it + W) * kItemFields;
+                    x_row = d[0], x_beg = d[1], x_end = d[2], x_slot = d[5];
+                }
+            }
+            ++issued;
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+#pragma unroll 1
+    for (int q = 0; q < kG1Stages; ++q) issue_next();
+    // X landed (every thread's share), the ring's chunks may still be in flight
+    asm volatile("cp.async.wait_group %0;" ::"n"(kG1Stages) : "memory");
+    __syncthreads();
+    float acc[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.f;
+    int cs = 0;                                       // ring stage of chunk t
+#pragma unroll 1
+    for (int32_t t = 0; t < issued; ++t) {
+        asm volatile("cp.async.wait_group %0;" ::"n"(kG1Stages - 1) : "memory");
+        __syncwarp();
+        const uint8_t *st = ring + cs * kStage;
+        const G1Meta m = meta[cs];
+        cs = cs + 1 == kG1Stages ? 0 : cs + 1;
+        const int4 c0 = *reinterpret_cast<const int4 *>(st + lane * 32);
+        const int4 c1 = *reinterpret_cast<const int4 *>(st + lane * 32 + 16);
+        const Pack<T, 8> w = *reinterpret_cast<const Pack<T, 8> *>(st + kG1Chunk * 4 + lane * VB);
+        const int32_t cq[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        if (m.base >= m.beg && m.base + kG1Chunk <= m.end) {
+            // a chunk wholly inside its item (all but an item's first and
+            // last): no masks
+            Pack<T, V> x[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) x[e] = *reinterpret_cast<const Pack<T, V> *>(xs + cq[e] * V);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float wf = Vec<T>::to_f(w.v[e]);
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] = fmaf(wf, Vec<T>::to_f(x[e].v[v]), acc[v]);
+            }
+        } else {
+            const int32_t p0 = m.base + 8 * lane;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                if (p0 + e >= m.beg && p0 + e < m.end) {
+                    const Pack<T, V> x = *reinterpret_cast<const Pack<T, V> *>(xs + cq[e] * V);
+                    const float wf = Vec<T>::to_f(w.v[e]);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) acc[v] = fmaf(wf, Vec<T>::to_f(x.v[v]), acc[v]);
+                }
+            }
+        }
+        if (m.last) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], off);
+            if (lane == 0) {
+                if (m.slot >= 0) {
+                    float *dst = ws + ws_row0[m.slot] * (int64_t)V;   // n == V here
+#pragma unroll
+                    for (int v = 0; v < V; ++v) dst[v] = acc[v];
+                } else {
+                    Pack<T, V> out;
+#pragma unroll
+                    for (int v = 0; v < V; ++v) out.v[v] = Vec<T>::from_f(acc[v]);
+                    *reinterpret_cast<Pack<T, V> *>(Y + (int64_t)m.row * ldy) = out;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = 0.f;
+        }
+        __syncwarp();                                 // stage s is free again
+        issue_next();
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// n <= V with X too large for shared memory: the row's indices and values
+// stream in as 16-byte / 8-byte vectors, four non-zeros per lane per load
+// and kRounds loads per lane in flight, and every lane gathers the X rows of
+// its own non-zeros from global memory (L2), up to 4 kRounds gathers in
+// flight per lane.  The lanes' sums meet in a fixed butterfly
+// (deterministic).
 #ifndef SPMM_G1_ROUNDS
 #define SPMM_G1_ROUNDS 4    // 16-byte index loads in flight per lane per pass
 #endif
 #ifndef SPMM_G1_BLOCKS
 #define SPMM_G1_BLOCKS 2    // resident 512-thread blocks per SM (bounds registers)
 #endif
-__global__ void __launch_bounds__(512, SPMM_G1_BLOCKS) gather1_kernel(
+template <typename T, int V>
+__global__ void __launch_bounds__(512, SPMM_G1_BLOCKS) gather1g_kernel(
     const int32_t *__restrict__ items, int64_t n_items, const int32_t *__restrict__ col_idx,
-    const T *__restrict__ vals, const T *__restrict__ X, int64_t ldx, int64_t k, T *__restrict__ Y,
+    const T *__restrict__ vals, const T *__restrict__ X, int64_t ldx, T *__restrict__ Y,
     int64_t ldy, float *__restrict__ ws, const int64_t *__restrict__ ws_row0,
     const int32_t *__restrict__ n_items_dev, const int32_t *__restrict__ status) {
     pdl_enter();
     constexpr int kRounds = SPMM_G1_ROUNDS;   // kRounds x 4 non-zeros per lane per pass
-    extern __shared__ __align__(16) uint8_t xs_raw[];
     const int lane = threadIdx.x & 31;
     if (n_items_dev) {
         if (*status != 0) return;
         n_items = min(n_items, (int64_t)*n_items_dev);
     }
     const T *xb = X;
-    int64_t lx = ldx;
-    if (SX) {
-        T *xs = (T *)xs_raw;
-        for (int64_t i = threadIdx.x; i < k; i += blockDim.x)
-            *reinterpret_cast<Pack<T, V> *>(xs + i * V) =
-                *reinterpret_cast<const Pack<T, V> *>(X + i * ldx);
-        __syncthreads();
-        xb = xs;
-        lx = V;
-    }
+    const int64_t lx = ldx;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; item < n_items;
          item += nwarps) {
@@ -296,28 +482,39 @@ __global__ void __launch_bounds__(512, SPMM_G1_BLOCKS) gather1_kernel(
     }
 }
 
-#ifndef SPMM_GATHER_SMEMX
-#define SPMM_GATHER_SMEMX (48 * 1024)   // X copied to shared memory up to this size
-#endif
-template <typename T, int V, bool SX>
+// X in shared memory: one 16-warp CTA per SM, streaming through the ring.
+template <typename T, int V>
 cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const void *X, int64_t ldx, void *Y,
                            int64_t ldy, cudaStream_t s) {
     const bool dyn = p->mode == SPMM_DYNAMIC;
-    const size_t smem = SX ? (size_t)p->k * V * sizeof(T) : 0;
-    if (SX) {
-        static std::atomic<uint64_t> attrs{0};
-        const cudaError_t e =
-            set_smem_attrs_once(attrs, gather1_kernel<T, V, SX>, 200 * 1024, false);
-        if (e != cudaSuccess) return e;
-    }
-    // persistent: as many 512-thread blocks as fit (shared memory allowing)
-    const int per_sm = SX ? (smem <= 100 * 1024 ? 2 : 1) : SPMM_G1_BLOCKS;
+    const size_t smem = g1_fixed_smem<T>() + (size_t)p->k * V * sizeof(T);
+    static std::atomic<uint64_t> attrs{0};
+    const cudaError_t e = set_smem_attrs_once(attrs, gather1_kernel<T, V>,
+                                              g1_fixed_smem<T>() + g1_x_budget<T>(), false);
+    if (e != cudaSuccess) return e;
+    int64_t blocks = (n_items + kG1Warps - 1) / kG1Warps;
+    const int64_t cap_blocks = (int64_t)std::max(p->sm_count, 1);
+    if (blocks > cap_blocks) blocks = cap_blocks;
+    if (blocks < 1) blocks = 1;
+    // entries the index and value arrays hold (copies past them are not made)
+    const int64_t cap = dyn ? p->nnzb_max : p->nnzb;
+    pdl_launch(gather1_kernel<T, V>, dim3((unsigned)blocks), dim3(kG1Warps * 32), smem, s,
+        p->d_items, n_items, p->d_col_idx, (const T *)p->d_packed, cap, (const T *)X, ldx, p->k,
+        (T *)Y, ldy, p->d_ws, p->d_ws_row0, dyn ? p->d_counts + kCntItems : nullptr, p->d_status);
+    return cudaGetLastError();
+}
+
+// X in global memory: persistent 512-thread blocks, SPMM_G1_BLOCKS per SM.
+template <typename T, int V>
+cudaError_t gather1g_launch(const spmm_plan *p, int64_t n_items, const void *X, int64_t ldx,
+                            void *Y, int64_t ldy, cudaStream_t s) {
+    const bool dyn = p->mode == SPMM_DYNAMIC;
     int64_t blocks = (n_items * 32 + 511) / 512;
-    const int64_t cap = (int64_t)std::max(p->sm_count, 1) * per_sm;
+    const int64_t cap = (int64_t)std::max(p->sm_count, 1) * SPMM_G1_BLOCKS;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    pdl_launch(gather1_kernel<T, V, SX>, dim3((unsigned)blocks), dim3(512), smem, s, p->d_items,
-        n_items, p->d_col_idx, (const T *)p->d_packed, (const T *)X, ldx, p->k, (T *)Y, ldy,
+    pdl_launch(gather1g_kernel<T, V>, dim3((unsigned)blocks), dim3(512), 0, s, p->d_items,
+        n_items, p->d_col_idx, (const T *)p->d_packed, (const T *)X, ldx, (T *)Y, ldy,
         p->d_ws, p->d_ws_row0, dyn ? p->d_counts + kCntItems : nullptr, p->d_status);
     return cudaGetLastError();
 }
@@ -387,9 +584,9 @@ cudaError_t gather_launch(const spmm_plan *p, const void *X, int64_t n, int64_t 
     if (warps == 0) return cudaSuccess;
     if (vecs == 1) {
         // n == V: one vector per X row; X in shared memory when it fits
-        if ((int64_t)p->k * V * (int64_t)sizeof(T) <= SPMM_GATHER_SMEMX)
-            return gather1_launch<T, V, true>(p, n_items, X, ldx, Y, ldy, s);
-        return gather1_launch<T, V, false>(p, n_items, X, ldx, Y, ldy, s);
+        if ((int64_t)p->k * V * (int64_t)sizeof(T) <= g1_x_budget<T>())
+            return gather1_launch<T, V>(p, n_items, X, ldx, Y, ldy, s);
+        return gather1g_launch<T, V>(p, n_items, X, ldx, Y, ldy, s);
     }
     pdl_launch(gather_kernel<T, V>, dim3(grid1d(warps * 32, 256)), dim3(256), 0, s, p->d_items,
         n_items, nchunk, LN, p->d_col_idx, (const T *)p->d_packed, (const T *)X, ldx, (T *)Y, ldy,
