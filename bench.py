@@ -809,7 +809,9 @@ def run_batched(torch, S, wl, dev, peaks, reps=5):
         tuned.append({"m": c["m"], "k": c["k"], "b": c["b"], "d": "1/%d" % round(1 / sp["d"]),
                       "n_bucket": "(%d, %d]" % (2 ** (key[4] - 1) if key[4] else 0, 2 ** key[4]),
                       "tuned_on_n": c["n"], "choice": r["kernel"],
-                      "stage_geometry": r["stage_geometry"], "candidates": r["candidates"]})
+                      "stage_geometry": r["stage_geometry"],
+                      "rows_per_group": r["rows_per_group"], "k_splits": r["k_splits"],
+                      "candidates": r["candidates"]})
         del codes, scales, xb
     t_tune = time.perf_counter() - t_tune
     for i in range(48):

@@ -153,6 +153,12 @@ typedef struct {
                                      the slice (m = row_end - row_begin); spmm_sddmm on a
                                      slice writes the kept blocks in the slice's order.
                                      Dynamic plans: SPMM_ERR_UNSUPPORTED. */
+    int32_t k_splits;             /* static TC plans: split every tile-row group's entries (its
+                                     tile columns, i.e. its share of k) into about this many work
+                                     items of near-equal length, whose FP32 partials the split-row
+                                     reduction sums in a fixed order; 0 = only groups well above the
+                                     mean length are split.  Overrides max_per_item.  0 .. 1024,
+                                     else SPMM_ERR_ARG. */
 } spmm_plan_opts;
 
 typedef struct spmm_plan spmm_plan;
@@ -196,7 +202,9 @@ spmm_status spmm_pack_values(spmm_plan *plan, const void *d_values, const float 
  *              user-order values matching the device pattern.
  *   d_scales : E4M3 per-block scales for d_values (NULL otherwise / if packed).
  *   dpat     : dynamic mode only: the device pattern of this call.
- *   d_X, n, ldx : X (k x n), 0 <= n <= n_max.
+ *   d_X, n, ldx : X (k x n), 0 <= n <= n_max.  Tensor-core plans read X
+ *                 by TMA: d_X 16-byte aligned and ldx a multiple of 8, else
+ *                 SPMM_ERR_UNSUPPORTED (pad X's rows).
  *   d_Y, ldy    : Y (m x n).
  * In dynamic mode the device validates the pattern; on an invalid pattern or
  * nnzb outside [0, nnzb_max] the status word is set (see spmm_get_status)
@@ -414,13 +422,17 @@ spmm_status spmm_sddmm(spmm_plan *plan, const spmm_dpattern *pattern, const void
  * tuned quantity is the GPU launch configuration).  For the static product
  * described by (m, k, n, b, types, pattern, d_values, d_scales, d_X, ldx)
  * it builds one plan per candidate -- the tensor-core kernel with dense-tile
- * and with sparse-tile stages, and the CUDA-core block gather (BGATHER)
- * where n <= 16 and b >= 4 -- times `reps` runs of each on `stream` after
+ * and with sparse-tile stages, each with the planner's default groups and,
+ * where those shrink below 16 tile rows to fill the GPU, with 16-row groups
+ * split along k into enough work items to fill it (k_splits); and the
+ * CUDA-core block gather (BGATHER) where n <= 16 and b >= 4 -- times `reps`
+ * runs of each on `stream` after
  * two warm-up runs (CUDA events, median), and records the fastest for the
  * product's bucket: (b, W and X types, ceil(log2 m), ceil(log2 k),
  * round(log2(1/d)) with d the block density, ceil(log2 n)).  From then on
- * spmm_plan_create, for a static plan with kernel AUTO and no forced
- * stage_geometry, takes the tuned choice for its bucket (n = its n_max).
+ * spmm_plan_create, for a static plan with kernel AUTO, no forced
+ * stage_geometry, rows_per_group, groups or k_splits, takes the tuned
+ * choice for its bucket (n = its n_max).
  *   reps          : 1 .. 64.
  *   out           : the choice and each candidate's median time (us, -1 if
  *                   it failed).
@@ -430,14 +442,16 @@ spmm_status spmm_sddmm(spmm_plan *plan, const spmm_dpattern *pattern, const void
 typedef struct {
     int32_t kernel;          /* spmm_kernel */
     int32_t stage_geometry;  /* TC: 1 dense-tile, 2 sparse-tile stages; 0 otherwise */
+    int32_t rows_per_group;  /* TC: 16 = 16-row groups split along k (see k_splits); 0 = default */
+    int32_t k_splits;        /* TC: work items per group when rows_per_group = 16 */
 } spmm_tune_choice;
 
 typedef struct {
     spmm_tune_choice choice;
     float best_us;
     int32_t n_candidates;
-    int32_t cand_kernel[4], cand_geometry[4];
-    float cand_us[4];
+    spmm_tune_choice cand[8];
+    float cand_us[8];
 } spmm_tune_result;
 
 spmm_status spmm_tune(int64_t m, int64_t k, int64_t n, int32_t b, spmm_dtype w_dtype,

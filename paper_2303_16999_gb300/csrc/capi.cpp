@@ -472,11 +472,13 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
     {
         // the autotuner's choice for this bucket, if it has one
         spmm_tune_choice tch{};
-        if (o.kernel == SPMM_KERNEL_AUTO && o.stage_geometry == 0 && mode == SPMM_STATIC &&
-            pattern && b >= 4 &&
+        if (o.kernel == SPMM_KERNEL_AUTO && o.stage_geometry == 0 && o.rows_per_group == 0 &&
+            o.groups == 0 && o.k_splits == 0 && mode == SPMM_STATIC && pattern && b >= 4 &&
             tune_lookup(m, k, b, pattern->nnzb, n_max, w_dtype, x_dtype, &tch)) {
             kernel = tch.kernel;
             o.stage_geometry = tch.stage_geometry;
+            o.rows_per_group = tch.rows_per_group;
+            o.k_splits = tch.k_splits;
         }
     }
     if (o.kernel == SPMM_KERNEL_AUTO && b == 1 && mode == SPMM_STATIC &&
@@ -489,13 +491,14 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
         return SPMM_ERR_UNSUPPORTED;
     }
     if (o.rows_per_group < 0 || o.rows_per_group > kMaxGroupRows || o.max_per_item < 0 ||
+        o.k_splits < 0 || o.k_splits > 1024 ||
         o.col_tiles < 0 || o.col_tiles > 2 || o.groups < 0 || o.stage_geometry < 0 ||
         o.stage_geometry > 2 || o.dyn_chain < 0 || o.dyn_chain > 1 ||
         (o.groups > 0 && (o.rows_per_group || o.groups > m / kTile ||
                           (m / kTile + o.groups - 1) / o.groups > kMaxGroupRows))) {
-        set_error("rows_per_group must be in 0..%d, max_per_item >= 0, col_tiles and "
-                  "stage_geometry in 0..2, dyn_chain 0 or 1, groups in 0 or ceil(m/16/%d)..m/16 without "
-                  "rows_per_group",
+        set_error("rows_per_group must be in 0..%d, max_per_item >= 0, k_splits in 0..1024, "
+                  "col_tiles and stage_geometry in 0..2, dyn_chain 0 or 1, groups in 0 or "
+                  "ceil(m/16/%d)..m/16 without rows_per_group",
                   kMaxGroupRows, kMaxGroupRows);
         return SPMM_ERR_ARG;
     }
@@ -574,17 +577,23 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
                     p->R = (int)((mt + p->groups - 1) / p->groups);
                 else
                     p->R = o.rows_per_group ? o.rows_per_group : default_R(mt, n_max, p->sm_count);
-                if (o.max_per_item) {
+                if (o.max_per_item && !o.k_splits) {
                     p->C = o.max_per_item;
                 } else {
-                    // entries per group if spread evenly, with headroom: only
-                    // groups well above the mean are split
                     HostPlan probe;
                     build_tc_plan(m, k, b, p->nnzb, pattern->brow, pattern->bcol, p->R, 1 << 30,
                                   false, false, probe, p->groups);
                     const int64_t G = (int64_t)probe.grp_rows.size();
                     const int64_t E = (int64_t)probe.ent_col.size();
-                    p->C = (int)std::max<int64_t>(16, G ? (5 * E + 4 * G - 1) / (4 * G) : 16);
+                    if (o.k_splits) {
+                        // about k_splits items per group of mean length
+                        const int64_t per = G ? (E + G * o.k_splits - 1) / (G * o.k_splits) : 1;
+                        p->C = (int)std::max<int64_t>(1, per);
+                    } else {
+                        // entries per group if spread evenly, with headroom:
+                        // only groups well above the mean are split
+                        p->C = (int)std::max<int64_t>(16, G ? (5 * E + 4 * G - 1) / (4 * G) : 16);
+                    }
                 }
                 build_tc_plan(m, k, b, p->nnzb, pattern->brow, pattern->bcol, p->R, p->C, true,
                               true, p->hp, p->groups);
@@ -798,8 +807,10 @@ static spmm_status launch_product(spmm_plan *p, const void *d_X, int64_t n, int6
     return SPMM_OK;
 }
 
+// dev_x: X is the caller's device array that the kernels read in place
+// (TMA alignment applies); false where the library stages X itself.
 static spmm_status check_run_args(spmm_plan *p, const void *d_X, int64_t n, int64_t ldx,
-                                  const void *d_Y, int64_t ldy) {
+                                  const void *d_Y, int64_t ldy, bool dev_x = true) {
     if (n < 0 || n > p->n_max) {
         set_error("n=%lld outside [0, n_max=%lld]", (long long)n, (long long)p->n_max);
         return SPMM_ERR_SHAPE;
@@ -811,6 +822,11 @@ static spmm_status check_run_args(spmm_plan *p, const void *d_X, int64_t n, int6
     if (n > 0 && (!d_X || !d_Y)) {
         set_error("X and Y required");
         return SPMM_ERR_ARG;
+    }
+    if (dev_x && n > 0 && p->kernel == SPMM_KERNEL_TC && ((uintptr_t)d_X % 16 || ldx % 8)) {
+        set_error("tensor-core plans read X by TMA: X must be 16-byte aligned with ldx a "
+                  "multiple of 8 (ldx=%lld)", (long long)ldx);
+        return SPMM_ERR_UNSUPPORTED;
     }
     return SPMM_OK;
 }
@@ -879,7 +895,7 @@ spmm_status spmm_run_host(spmm_plan *plan, const void *h_X, int64_t n, int64_t l
         set_error("spmm_run_host needs a device static plan");
         return SPMM_ERR_ARG;
     }
-    spmm_status st = check_run_args(plan, h_X, n, ldx, h_Y, ldy);
+    spmm_status st = check_run_args(plan, h_X, n, ldx, h_Y, ldy, false);
     if (st != SPMM_OK) return st;
     if (!plan->packed) {
         set_error("static plan has no values");
@@ -889,7 +905,10 @@ spmm_status spmm_run_host(spmm_plan *plan, const void *h_X, int64_t n, int64_t l
     st = busy_check(plan, s);
     if (st != SPMM_OK) return st;
     const size_t es = dtype_size(plan->xdt);
-    const int64_t xb = plan->k * std::max<int64_t>(n, 1) * (int64_t)es;
+    // the staged X's rows: 16-byte aligned for the tensor-core kernel's TMA
+    const int64_t xld = plan->kernel == SPMM_KERNEL_TC ? (std::max<int64_t>(n, 1) + 7) / 8 * 8
+                                                       : std::max<int64_t>(n, 1);
+    const int64_t xb = plan->k * xld * (int64_t)es;
     const int64_t yb = plan->m * std::max<int64_t>(n, 1) * (int64_t)es;
     cudaError_t e = cudaSuccess;
     if (xb > plan->xbuf_bytes) {
@@ -914,11 +933,12 @@ spmm_status spmm_run_host(spmm_plan *plan, const void *h_X, int64_t n, int64_t l
     if (n > 0) {
         // one contiguous copy when the host rows are dense (a pitched copy
         // moves k short rows one by one)
-        e = ldx == n ? cudaMemcpyAsync(plan->d_xbuf, h_X, plan->k * n * es, cudaMemcpyHostToDevice, s)
-                     : cudaMemcpy2DAsync(plan->d_xbuf, n * es, h_X, ldx * es, n * es, plan->k,
-                                         cudaMemcpyHostToDevice, s);
+        e = (ldx == n && xld == n)
+                ? cudaMemcpyAsync(plan->d_xbuf, h_X, plan->k * n * es, cudaMemcpyHostToDevice, s)
+                : cudaMemcpy2DAsync(plan->d_xbuf, xld * es, h_X, ldx * es, n * es, plan->k,
+                                    cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) return cuda_fail(e, "X upload");
-        st = launch_product(plan, plan->d_xbuf, n, n, plan->d_ybuf, n, s);
+        st = launch_product(plan, plan->d_xbuf, n, xld, plan->d_ybuf, n, s);
         if (st != SPMM_OK) return st;
         e = ldy == n ? cudaMemcpyAsync(h_Y, plan->d_ybuf, plan->m * n * es, cudaMemcpyDeviceToHost, s)
                      : cudaMemcpy2DAsync(h_Y, ldy * es, plan->d_ybuf, n * es, n * es, plan->m,
@@ -1140,7 +1160,7 @@ spmm_status spmm_run_ell(spmm_plan *plan, const int32_t *d_ell_cols, int32_t ell
         set_error("ell: ell_width must be in [0, k/16]");
         return SPMM_ERR_SHAPE;
     }
-    spmm_status st = check_run_args(plan, d_X, n, ldx, d_Y, ldy);
+    spmm_status st = check_run_args(plan, d_X, n, ldx, d_Y, ldy, false);
     if (st != SPMM_OK) return st;
     if (ell_width > 0 && (!d_ell_cols || !d_values || (uintptr_t)d_values % 16)) {
         set_error("ell: columns and 16-byte aligned values required");

@@ -72,15 +72,29 @@ spmm_status spmm_tune(int64_t m, int64_t k, int64_t n, int32_t b, spmm_dtype w_d
     }
     cudaStream_t s = (cudaStream_t)stream;
     std::memset(out, 0, sizeof(*out));
-    // the candidates: the tensor-core kernel with each stage geometry, and
-    // the CUDA-core block gather where it applies
-    struct Cand {
-        int32_t kernel, geometry;
-    };
-    std::vector<Cand> cands = {{SPMM_KERNEL_TC, 1}, {SPMM_KERNEL_TC, 2}};
+    // the candidates: the tensor-core kernel with each stage geometry, with
+    // the planner's groups and, where those shrink below 16 tile rows to
+    // fill the CTA slots, with 16-row groups split along k instead; and the
+    // CUDA-core block gather where it applies
+    std::vector<spmm_tune_choice> cands = {{SPMM_KERNEL_TC, 1, 0, 0}, {SPMM_KERNEL_TC, 2, 0, 0}};
+    {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            sms > 0 && m % kTile == 0) {
+            const int64_t mt = m / kTile, g16 = (mt + kMaxGroupRows - 1) / kMaxGroupRows;
+            const int64_t ntn = (n + kNTile - 1) / kNTile, slots = 2 * (int64_t)sms;
+            if (g16 * ntn < slots) {
+                const int32_t split =
+                    (int32_t)std::min<int64_t>(1024, (slots + g16 * ntn - 1) / (g16 * ntn));
+                cands.push_back({SPMM_KERNEL_TC, 1, kMaxGroupRows, split});
+                cands.push_back({SPMM_KERNEL_TC, 2, kMaxGroupRows, split});
+            }
+        }
+    }
     const bool x16 = x_dtype == SPMM_F16 || x_dtype == SPMM_BF16;
     if (b >= 4 && n <= kBgMaxN && x16 && (w_dtype == x_dtype || w_dtype == SPMM_E4M3))
-        cands.push_back({SPMM_KERNEL_BGATHER, 0});
+        cands.push_back({SPMM_KERNEL_BGATHER, 0, 0, 0});
     void *d_Y = nullptr;
     cudaError_t e = cudaMalloc(&d_Y, (size_t)m * n * dtype_size(x_dtype));
     if (e != cudaSuccess) {
@@ -94,10 +108,12 @@ spmm_status spmm_tune(int64_t m, int64_t k, int64_t n, int32_t b, spmm_dtype w_d
     spmm_status st = SPMM_OK;
     float best = 0.f;
     int found = 0;
-    for (size_t ci = 0; ci < cands.size() && st == SPMM_OK && nev == 2 * reps; ++ci) {
+    for (size_t ci = 0; ci < cands.size() && ci < 8 && st == SPMM_OK && nev == 2 * reps; ++ci) {
         spmm_plan_opts o{};
         o.kernel = cands[ci].kernel;
-        o.stage_geometry = cands[ci].geometry;
+        o.stage_geometry = cands[ci].stage_geometry;
+        o.rows_per_group = cands[ci].rows_per_group;
+        o.k_splits = cands[ci].k_splits;
         spmm_plan *p = nullptr;
         spmm_status cs = spmm_plan_create(m, k, n, b, SPMM_STATIC, w_dtype, x_dtype, pattern, 0,
                                           &o, &p);
@@ -128,14 +144,13 @@ spmm_status spmm_tune(int64_t m, int64_t k, int64_t n, int32_t b, spmm_dtype w_d
         spmm_plan_destroy(p);
         if (cs != SPMM_OK && cs != SPMM_ERR_UNSUPPORTED) st = cs;
         const int c = out->n_candidates++;
-        out->cand_kernel[c] = cands[ci].kernel;
-        out->cand_geometry[c] = cands[ci].kernel == SPMM_KERNEL_TC ? info.stage_geometry + 1 : 0;
+        out->cand[c] = cands[ci];
+        if (cands[ci].kernel == SPMM_KERNEL_TC) out->cand[c].stage_geometry = info.stage_geometry + 1;
         out->cand_us[c] = t;
         if (t > 0.f && (!found || t < best)) {
             best = t;
             found = 1;
-            out->choice.kernel = cands[ci].kernel;
-            out->choice.stage_geometry = out->cand_geometry[c];
+            out->choice = out->cand[c];
         }
     }
     for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);

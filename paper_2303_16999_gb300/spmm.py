@@ -65,7 +65,7 @@ class PlanOpts(ctypes.Structure):
                 ("transposed", ctypes.c_int32), ("col_tiles", ctypes.c_int32),
                 ("groups", ctypes.c_int64), ("stage_geometry", ctypes.c_int32),
                 ("dyn_chain", ctypes.c_int32), ("row_begin", ctypes.c_int64),
-                ("row_end", ctypes.c_int64)]
+                ("row_end", ctypes.c_int64), ("k_splits", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -78,11 +78,15 @@ class PlanInfo(ctypes.Structure):
         [(n, ctypes.c_int64) for n in ("row_begin", "row_end")]
 
 
-class TuneResult(ctypes.Structure):
+class TuneChoice(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("stage_geometry", ctypes.c_int32),
-                ("best_us", ctypes.c_float), ("n_candidates", ctypes.c_int32),
-                ("cand_kernel", ctypes.c_int32 * 4), ("cand_geometry", ctypes.c_int32 * 4),
-                ("cand_us", ctypes.c_float * 4)]
+                ("rows_per_group", ctypes.c_int32), ("k_splits", ctypes.c_int32)]
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("choice", TuneChoice), ("best_us", ctypes.c_float),
+                ("n_candidates", ctypes.c_int32), ("cand", TuneChoice * 8),
+                ("cand_us", ctypes.c_float * 8)]
 
 
 class ServeConfig(ctypes.Structure):
@@ -200,11 +204,11 @@ def spmm_tune(m, k, b, brow, bcol, values, X, w_dtype=F16, x_dtype=None, scales=
                            _ptr(values), _ptr(scales), _ptr(X), X.stride(0), reps,
                            _stream_handle(stream), ctypes.byref(r)))
     names = {v: k_ for k_, v in KERNELS.items()}
-    cands = [{"kernel": names.get(r.cand_kernel[i], r.cand_kernel[i]),
-              "stage_geometry": r.cand_geometry[i], "us": round(r.cand_us[i], 2)}
-             for i in range(r.n_candidates)]
-    return {"kernel": names.get(r.kernel, r.kernel), "stage_geometry": r.stage_geometry,
-            "best_us": round(r.best_us, 2), "candidates": cands}
+    def desc(c):
+        return {"kernel": names.get(c.kernel, c.kernel), "stage_geometry": c.stage_geometry,
+                "rows_per_group": c.rows_per_group, "k_splits": c.k_splits}
+    cands = [dict(desc(r.cand[i]), us=round(r.cand_us[i], 2)) for i in range(r.n_candidates)]
+    return dict(desc(r.choice), best_us=round(r.best_us, 2), candidates=cands)
 
 
 def spmm_tune_clear():
@@ -338,12 +342,13 @@ class Plan:
     def __init__(self, m, k, n_max, b, w_dtype=F16, x_dtype=None, brow=None, bcol=None,
                  mode=STATIC, nnzb_max=0, kernel="auto", rows_per_group=0, max_per_item=0,
                  host_only=False, transposed=False, col_tiles=0, groups=0, rows=None,
-                 stage_geometry=0, dyn_chain=False):
+                 stage_geometry=0, dyn_chain=False, k_splits=0):
         x_dtype = w_dtype if x_dtype is None else x_dtype
         rb, re = rows if rows is not None else (0, 0)
         opts = PlanOpts(KERNELS[kernel] if isinstance(kernel, str) else kernel,
                         rows_per_group, max_per_item, 1 if host_only else 0,
-                        1 if transposed else 0, col_tiles, groups, stage_geometry, 1 if dyn_chain else 0, rb, re)
+                        1 if transposed else 0, col_tiles, groups, stage_geometry, 1 if dyn_chain else 0, rb, re,
+                        k_splits)
         pat = None
         self._keep = None
         if mode == STATIC:

@@ -171,6 +171,31 @@ def test_tc_plan_bit_exact(b):
         assert info["n_tiles"] == len(want["tile_row"])
 
 
+@pytest.mark.parametrize("b", [4, 8, 16])
+def test_tc_plan_k_splits_bit_exact(b):
+    """k_splits: every group's entries in about k_splits items of at most
+    ceil(E / (G k_splits)) entries (E entries, G groups), every group with
+    more entries than that split; the arrays bit for bit against the
+    oracle's plan with that chunk size."""
+    rng = np.random.default_rng(90 + b)
+    for m, k, d, s in ((1024, 8192, 1 / 8, 19), (512, 4096, 1 / 16, 4), (256, 2048, 1 / 4, 1)):
+        mb, kb = m // b, k // b
+        brow, bcol = _rand(rng, mb, kb, int(d * mb * kb))
+        p0 = _plan(m, k, b, brow, bcol, rows_per_group=16, kernel="tc")
+        E, G = p0.info()["n_entries"], p0.info()["n_groups"]
+        p = _plan(m, k, b, brow, bcol, rows_per_group=16, k_splits=s, kernel="tc")
+        info = p.info()
+        C = -(-E // (G * s))
+        assert info["max_per_item"] == C and info["n_entries"] == E and info["n_groups"] == G
+        want = P.tc_plan(m, k, b, brow, bcol, 16, C)
+        for key in TC_KEYS:
+            assert np.array_equal(p.array(key), want[key]), key
+        assert np.array_equal(p.array("items").reshape(-1, 6), want["items"])
+        assert np.array_equal(p.array("red").reshape(-1, 3), want["red"])
+        ents = np.diff(p.array("grp_ebeg"))
+        assert info["n_items"] == sum(-(-int(e) // C) if e > C else 1 for e in ents)
+
+
 @pytest.mark.parametrize("b", [1, 4, 16])
 def test_tc_plan_near_equal_groups_bit_exact(b):
     """Plans with an explicit group count: the tile rows in near-equal groups

@@ -293,10 +293,16 @@ def test_tuner_choice_applies_to_auto_plans():
                     w_dtype=S.E4M3, x_dtype=S.BF16, scales=scales, reps=5)
     assert S.spmm_tune_size() == 1
     kinds = {q["kernel"] for q in r["candidates"]}
-    assert kinds == {"tc", "bgather"} and len(r["candidates"]) == 3
+    # both stage geometries with the default groups and (m / 16 = 128 tile
+    # rows: 8 groups of 16, too few for the SMs) with 16-row groups split
+    # along k, and the block gather
+    assert kinds == {"tc", "bgather"} and len(r["candidates"]) == 5
+    split = [q for q in r["candidates"] if q["rows_per_group"] == 16]
+    assert len(split) == 2 and all(q["k_splits"] >= 2 for q in split)
     ok = [q for q in r["candidates"] if q["us"] > 0]
     best = min(ok, key=lambda q: q["us"])
     assert r["kernel"] == best["kernel"] and r["best_us"] == best["us"]
+    assert (r["rows_per_group"], r["k_splits"]) == (best["rows_per_group"], best["k_splits"])
     # a fresh AUTO plan in the same bucket (other values) takes the choice
     c2 = _problem(971, 2048, 4096, 5, 8, 1 / 8)
     p, codes2, scales2 = _e4m3_plan(c2)
@@ -304,6 +310,8 @@ def test_tuner_choice_applies_to_auto_plans():
     assert info["kernel"] == {"tc": 3, "bgather": 4}[r["kernel"]]
     if r["kernel"] == "tc":
         assert info["stage_geometry"] == r["stage_geometry"] - 1
+        if r["rows_per_group"]:
+            assert info["rows_per_group"] == 16 and info["n_reductions"] > 0
     X2 = _x(c2, torch.bfloat16)
     Y = p.run(X2)
     torch.cuda.synchronize()

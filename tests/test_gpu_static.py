@@ -188,6 +188,27 @@ def test_run_host_buffers():
     assert oracle.normwise_err(Y, Yo, oracle.block_fro(vals), X) <= 4e-3
 
 
+@pytest.mark.parametrize("n", [82, 5])
+def test_tc_unaligned_x_rows(n):
+    """Tensor-core plans read X by TMA, which needs 16-byte aligned rows: a
+    device X with ldx not a multiple of 8 is refused up front with a clear
+    status, while spmm_run_host (which stages X itself, rows padded) takes
+    the same X and matches the oracle."""
+    m, k, b = 256, 1024, 16
+    c = wl.problem(40 + n, m, k, n, b, wl.nnzb_for(m, k, b, 1 / 8))
+    vals = torch.from_numpy(c["vals"]).half()
+    plan = S.Plan(m, k, n, b, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"], kernel="tc")
+    plan.pack(vals.cuda())
+    X = torch.from_numpy(c["X"]).half()
+    with pytest.raises(S.SpmmError) as e:
+        plan.run(X.cuda())
+    assert e.value.status == S.ERR_UNSUPPORTED and "ldx" in str(e.value)
+    Y = torch.empty((m, n), dtype=torch.float16).pin_memory()
+    plan.run_host(X.pin_memory(), Y)
+    Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X)
+    assert oracle.normwise_err(Y, Yo, oracle.block_fro(vals), X) <= 4e-3
+
+
 def test_not_packed_and_bad_n():
     plan = S.Plan(256, 256, 64, 16, w_dtype=S.F16, brow=[0], bcol=[0])
     X = torch.zeros(256, 64, dtype=torch.float16, device="cuda")
@@ -341,6 +362,32 @@ def test_near_equal_groups(b, d, n, ct):
                             col_tiles=ct)
     if pq.info()["n_reductions"] == 0 and p0.info()["n_reductions"] == 0:
         assert torch.equal(Yq, Y0)
+
+
+@pytest.mark.parametrize("b,d,n,s", [(8, 1 / 8, 82, 19), (16, 1 / 16, 40, 7), (4, 1 / 16, 136, 3),
+                                     (8, 1 / 16, 256, 38)])
+def test_k_splits_integers_exact_and_bars(b, d, n, s):
+    """16-row groups split along k into about s work items each (k_splits,
+    the tuner's choice for tall-k problems at small n): integer inputs give
+    the oracle's Y exactly (one rounding of exact sums), and N(0,1) inputs
+    stay within the bars."""
+    m, k = 512, 8192
+    nnzb = wl.nnzb_for(m, k, b, d)
+    brow, bcol, vals, X = _int_case(m, k, n, b, nnzb, seed=300 + s)
+    plan = S.Plan(m, k, n, b, w_dtype=S.F16, brow=brow, bcol=bcol, kernel="tc",
+                  rows_per_group=16, k_splits=s)
+    info = plan.info()
+    assert info["n_reductions"] == info["n_groups"] and info["n_items"] >= info["n_groups"] * (s // 2)
+    plan.pack(torch.from_numpy(vals).half().cuda())
+    ld = ((n + 7) // 8) * 8
+    Y = plan.run(_x_dev(torch.from_numpy(X).half(), torch.float16, ld)).cpu()
+    assert plan.status() == 0
+    Yo = oracle.spmm(m, k, b, brow, bcol, vals, X)
+    assert torch.equal(Y, torch.from_numpy(Yo).half())
+    err, Yn, _, _ = run_case(m, k, n, b, nnzb, torch.bfloat16, "tc", seed=310 + s,
+                             ldx=((n + 7) // 8) * 8, rows_per_group=16, k_splits=s)
+    assert not torch.isnan(Yn).any()
+    assert err <= 4e-3, err
 
 
 @pytest.mark.parametrize("b,d,n,ct", [(16, 1 / 4, 512, 1), (1, 1 / 4, 512, 2), (8, 1 / 16, 200, 0)])
