@@ -219,7 +219,6 @@ template <int S> struct __align__(8) SmemT {
     uint64_t full[S], empty[S], conv[S], accf[kAccBufs], acce[kAccBufs];
     uint64_t drain;                // abort: one tcgen05.commit per MMA warp
     uint64_t never;                // failure-detection tests: nothing arrives here
-    unsigned long long wait_ns;    // limit of each pipeline wait
     StageMeta meta[S];
     uint32_t tmem_base;
     volatile int32_t abort_flag;
@@ -230,11 +229,14 @@ template <int S> struct __align__(8) SmemT {
 
 // ------------------------------------------------------------ PTX helpers
 // (generic ones in tc_ptx.cuh)
-// Bounded wait: false after the launch's wait limit or once another role
+// Bounded wait: false after the launch's wait limit (`lim`, read from the
+// kernel's parameters: reading it from shared memory in every wait cost
+// about a fifth of the two-column-tile kernel's time) or once another role
 // has aborted.
 template <class SM>
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, SM *sm) {
-    return mbar_wait_bounded(b, parity, &sm->abort_flag, sm->wait_ns);
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, SM *sm,
+                                          unsigned long long lim) {
+    return mbar_wait_bounded(b, parity, &sm->abort_flag, lim);
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), A and B
@@ -274,7 +276,7 @@ struct TcBatch {
     int32_t nprob;
     const int32_t *n_items_dev;  // dynamic single problem: item count on the device
     int32_t *status;
-    unsigned long long wait_ns;  // limit of each pipeline wait (the abort drain waits kWaitNs)
+    unsigned long long wait_ns;  // limit of each pipeline wait, never 0 (the abort drain waits kWaitNs)
     int32_t stall;               // failure-detection tests: after their first stage the MMA
                                  // warps wait on a barrier nothing arrives on, so that wait
                                  // runs out and the CTA takes its abort path
@@ -359,7 +361,6 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
         }
         mbar_init(&sm->drain, G::mma_warps);
         mbar_init(&sm->never, 1);
-        sm->wait_ns = B.wait_ns ? B.wait_ns : kWaitNs;
         sm->abort_flag = 0;
         for (int i = 0; i < kProducersMax; ++i) sm->issued[i] = 0;
         for (int i = 0; i < kMmaWarpsMax; ++i) sm->consumed[i] = 0;
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
                 const int xlo = pid == 2 ? h : 0, mine = pid == 2 ? nent - h : h;
                 const uint32_t col = __shfl_sync(0xffffffffu, rc, min(3 + xlo + lane, kRecWords - 1));
                 int w = 1;
-                if (lane == 0) w = mbar_wait(&sm->empty[stage], phase ^ 1, sm) ? 1 : 0;
+                if (lane == 0) w = mbar_wait(&sm->empty[stage], phase ^ 1, sm, B.wait_ns) ? 1 : 0;
                 if (!__shfl_sync(0xffffffffu, w, 0)) return -1;
                 uint8_t *st = stages + stage * G::bytes;
                 if (wprod) {
@@ -573,14 +574,14 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
             const int ab = local % kBufs;
             const uint32_t aphase = (local / kBufs) & 1;
             int w = 1;
-            if (lane == 0) w = mbar_wait(&sm->acce[ab], aphase ^ 1, sm) ? 1 : 0;
+            if (lane == 0) w = mbar_wait(&sm->acce[ab], aphase ^ 1, sm, B.wait_ns) ? 1 : 0;
             ok = __shfl_sync(0xffffffffu, w, 0) != 0;
             tc_fence_after();
             const uint32_t dbase = tmem + ab * G::sets * kAccCols;
             bool last = !has_entries;
             while (ok && !last) {
                 if (lane == 0)
-                    w = mbar_wait(W8 ? &sm->conv[stage] : &sm->full[stage], phase, sm) ? 1 : 0;
+                    w = mbar_wait(W8 ? &sm->conv[stage] : &sm->full[stage], phase, sm, B.wait_ns) ? 1 : 0;
                 if (!__shfl_sync(0xffffffffu, w, 0)) {
                     ok = false;
                     break;
@@ -619,7 +620,7 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
                 }
                 if (B.stall) {
                     // failure-detection tests: a wait that nothing ends
-                    if (lane == 0) w = mbar_wait(&sm->never, 0, sm) ? 1 : 0;
+                    if (lane == 0) w = mbar_wait(&sm->never, 0, sm, B.wait_ns) ? 1 : 0;
                     if (!__shfl_sync(0xffffffffu, w, 0)) {
                         ok = false;
                         break;
@@ -655,7 +656,7 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
                 bool last = false;
                 while (!last) {
                     int w = 1;
-                    if (lane == 0) w = mbar_wait(&sm->full[cstage], cphase, sm) ? 1 : 0;
+                    if (lane == 0) w = mbar_wait(&sm->full[cstage], cphase, sm, B.wait_ns) ? 1 : 0;
                     if (!__shfl_sync(0xffffffffu, w, 0)) {
                         // every epilogue warp still meets the named barrier
                         // below, where the poller sees the abort
@@ -720,7 +721,7 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
                 int okp = 1;
                 while (!mbar_try(&sm->accf[ab], aphase)) {
                     __nanosleep(400);
-                    if (sm->abort_flag || gtimer() - t0 > sm->wait_ns) {
+                    if (sm->abort_flag || gtimer() - t0 > B.wait_ns) {
                         okp = 0;
                         break;
                     }
@@ -1001,7 +1002,7 @@ cudaError_t launch_tc(const spmm_plan *p, const void *X, int64_t n, int64_t ldx,
     B.nprob = 1;
     B.units = nullptr;
     B.status = p->d_status;
-    B.wait_ns = p->wait_ns;
+    B.wait_ns = p->wait_ns ? p->wait_ns : kWaitNs;
     B.stall = p->stall;
     const bool dyn = p->mode == SPMM_DYNAMIC;
     if (wide) B.prob[0].ntn = (B.prob[0].ntn + 1) / 2;   // units of two column tiles
@@ -1108,7 +1109,7 @@ cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *cons
     B.status = plans[0]->d_status;
     B.n_items_dev = nullptr;
     B.units = nullptr;
-    B.wait_ns = plans[0]->wait_ns;
+    B.wait_ns = plans[0]->wait_ns ? plans[0]->wait_ns : kWaitNs;
     B.stall = plans[0]->stall;
     if (!schedule) {
         // problems in submission order (serving: every launch is a new mix)
