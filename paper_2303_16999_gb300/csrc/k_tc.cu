@@ -688,12 +688,9 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
                                 (__nv_fp8x2_storage_t)(cw[qd] >> 16), __NV_E4M3);
                             const float2 f01 = __half22float2(*(const __half2 *)&h01);
                             const float2 f23 = __half22float2(*(const __half2 *)&h23);
-                            const T o0 = Cvt<T>::f(f01.x * scl), o1 = Cvt<T>::f(f01.y * scl);
-                            const T o2 = Cvt<T>::f(f23.x * scl), o3 = Cvt<T>::f(f23.y * scl);
-                            outw[qd * 2] = (uint32_t)(*(const uint16_t *)&o0) |
-                                           ((uint32_t)(*(const uint16_t *)&o1) << 16);
-                            outw[qd * 2 + 1] = (uint32_t)(*(const uint16_t *)&o2) |
-                                               ((uint32_t)(*(const uint16_t *)&o3) << 16);
+                            // code x scale in FP32, rounded once; a pair per conversion
+                            outw[qd * 2] = pack2_rn<T>(f01.x * scl, f01.y * scl);
+                            outw[qd * 2 + 1] = pack2_rn<T>(f23.x * scl, f23.y * scl);
                         }
                         // columns 0-7 and 8-15 land in two core matrices
                         uint8_t *dst = st + G::w16 + slot * kTileBytes16 + (i >> 3) * 256 + (i & 7) * 16;

@@ -189,6 +189,17 @@ template <> struct Cvt<__nv_bfloat16> {
     static constexpr uint32_t fmt = 1;
     static __device__ __forceinline__ __nv_bfloat16 f(float v) { return __float2bfloat16_rn(v); }
 };
+// Two floats rounded (to nearest even) to the 16-bit type and packed into
+// one word, lo in the low half: one conversion instruction for the pair.
+template <typename T> __device__ __forceinline__ uint32_t pack2_rn(float lo, float hi);
+template <> __device__ __forceinline__ uint32_t pack2_rn<__half>(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+template <> __device__ __forceinline__ uint32_t pack2_rn<__nv_bfloat16>(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point (no -lcuda).
 inline PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
