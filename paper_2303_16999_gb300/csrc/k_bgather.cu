@@ -73,6 +73,17 @@ template <> struct Cv<__nv_bfloat16> {
     }
 };
 
+// (a0, a1) += w (x0, x1), each lane's FMA rounded as a scalar fmaf would be:
+// one packed FP32 FMA for the pair.
+__device__ __forceinline__ void fma2_rn(float &a0, float &a1, float w, float x0, float x1) {
+    unsigned long long av, wv, xv, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(av) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(wv) : "f"(w));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(xv) : "f"(x0), "f"(x1));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(wv), "l"(xv), "l"(av));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(d));
+}
+
 // Four E4M3 codes (one 32-bit word, lowest byte first) -> floats x scale.
 __device__ __forceinline__ void e4m3x4(uint32_t w, float sc, float *o) {
     const __half2_raw h01 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xFFFFu), __NV_E4M3);
@@ -300,8 +311,12 @@ __device__ __forceinline__ void bg_row(const BgProb &P, int32_t r, int part, uin
             for (int l = 0; l < B; ++l) {
                 float x[NC];
                 unpack_row<T, NC>(st + (g * B + l) * 32, x);
+                if constexpr (NC == 1) {
+                    acc[0] = fmaf(w[l], x[0], acc[0]);
+                } else {
 #pragma unroll
-                for (int c = 0; c < NC; ++c) acc[c] = fmaf(w[l], x[c], acc[c]);
+                    for (int c = 0; c < NC; c += 2) fma2_rn(acc[c], acc[c + 1], w[l], x[c], x[c + 1]);
+                }
             }
         }
         __syncwarp();                               // stage t % S is free again

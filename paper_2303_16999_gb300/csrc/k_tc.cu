@@ -688,9 +688,11 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
                                 (__nv_fp8x2_storage_t)(cw[qd] >> 16), __NV_E4M3);
                             const float2 f01 = __half22float2(*(const __half2 *)&h01);
                             const float2 f23 = __half22float2(*(const __half2 *)&h23);
-                            // code x scale in FP32, rounded once; a pair per conversion
-                            outw[qd * 2] = pack2_rn<T>(f01.x * scl, f01.y * scl);
-                            outw[qd * 2 + 1] = pack2_rn<T>(f23.x * scl, f23.y * scl);
+                            // code x scale in FP32, rounded once; a pair per multiply
+                            // and per conversion
+                            const float2 p01 = mul2_rn(f01, scl), p23 = mul2_rn(f23, scl);
+                            outw[qd * 2] = pack2_rn<T>(p01.x, p01.y);
+                            outw[qd * 2 + 1] = pack2_rn<T>(p23.x, p23.y);
                         }
                         // columns 0-7 and 8-15 land in two core matrices
                         uint8_t *dst = st + G::w16 + slot * kTileBytes16 + (i >> 3) * 256 + (i & 7) * 16;

@@ -189,6 +189,17 @@ template <> struct Cvt<__nv_bfloat16> {
     static constexpr uint32_t fmt = 1;
     static __device__ __forceinline__ __nv_bfloat16 f(float v) { return __float2bfloat16_rn(v); }
 };
+// (a.x s, a.y s), each product rounded to nearest as a scalar multiply
+// would be: one packed FP32 multiply for the pair.
+__device__ __forceinline__ float2 mul2_rn(float2 a, float s) {
+    unsigned long long av, sv, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(av) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(sv) : "f"(s));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(av), "l"(sv));
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
+    return r;
+}
 // Two floats rounded (to nearest even) to the 16-bit type and packed into
 // one word, lo in the low half: one conversion instruction for the pair.
 template <typename T> __device__ __forceinline__ uint32_t pack2_rn(float lo, float hi);
