@@ -128,13 +128,13 @@ namespace {
 #define SPMM_TC_TILES8 24
 #endif
 #ifndef SPMM_TC_STAGES8_S
-#define SPMM_TC_STAGES8_S 2 // E4M3 weights, sparse: 8 slabs, 24 tiles
+#define SPMM_TC_STAGES8_S 2 // E4M3 weights, sparse: 8 slabs, 26 tiles
 #endif
 #ifndef SPMM_TC_ENT8_S
 #define SPMM_TC_ENT8_S 8
 #endif
 #ifndef SPMM_TC_TILES8_S
-#define SPMM_TC_TILES8_S 24
+#define SPMM_TC_TILES8_S 26 // the most that leaves two CTAs per SM
 #endif
 constexpr int kSlabBytes = kTile * kNTile * 2;                    // 4096: 16 k x 128 n, 16-bit
 constexpr int kTileBytes8 = kTile * kTile;                        // 256: E4M3 tile, row-major
@@ -176,7 +176,10 @@ template <bool W8, int GEO> struct StageGeom {
     static constexpr int w16 = sets * xset;
     static constexpr int w8 = w16 + tiles * kTileBytes16;
     static constexpr int sc = w8 + tiles * kTileBytes8;
-    static constexpr int bytes = W8 ? sc + tiles * kScaleBytes : w8;
+    // every stage starts on a 1024-byte boundary: the 128-byte-swizzled X
+    // slabs (TMA destinations and MMA A operands) need it
+    static constexpr int bytes = ((W8 ? sc + tiles * kScaleBytes : w8) + 1023) / 1024 * 1024;
+    static_assert(bytes % 1024 == 0 && xset % 1024 == 0, "swizzle-aligned stages");
 };
 // Two CTAs share an SM: each holds one accumulator set (256 of the SM's 512
 // TMEM columns) and half the shared memory, so the two CTAs' producer / MMA
@@ -944,13 +947,25 @@ void fill_prob(TcProb &P, const spmm_plan *p, void *Y, int64_t n, int64_t ldy, i
     P.x3d = x3d;
 }
 
+// Shared memory of one CTA of a geometry; one-column-tile geometries must
+// leave room for two CTAs per SM (228 KB, 1 KB of it reserved per CTA).
+template <bool W8, int GEO> constexpr size_t tc_smem_bytes() {
+    using G = StageGeom<W8, GEO>;
+    return 1024 + (size_t)G::stages * G::bytes + sizeof(SmemT<G::stages>);
+}
+static_assert(kCtasPerSm * (tc_smem_bytes<false, 0>() + 1024) <= 228 * 1024 &&
+                  kCtasPerSm * (tc_smem_bytes<false, 1>() + 1024) <= 228 * 1024 &&
+                  kCtasPerSm * (tc_smem_bytes<true, 0>() + 1024) <= 228 * 1024 &&
+                  kCtasPerSm * (tc_smem_bytes<true, 1>() + 1024) <= 228 * 1024,
+              "two CTAs per SM");
+
 template <typename T, bool W8, int GEO>
 cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
     if (B.total_units == 0) return cudaSuccess;
     const int64_t slots = (int64_t)sm_count * (GEO >= 2 ? 1 : kCtasPerSm);
     const int grid = (int)(B.total_units < slots ? B.total_units : slots);
     using G = StageGeom<W8, GEO>;
-    const size_t smem = 1024 + (size_t)G::stages * G::bytes + sizeof(SmemT<G::stages>);
+    const size_t smem = tc_smem_bytes<W8, GEO>();
     static std::atomic<uint64_t> attrs{0};
     const cudaError_t e = set_smem_attrs_once(attrs, tc_kernel<T, W8, GEO>, (int)smem, GEO >= 2);
     if (e != cudaSuccess) return e;
