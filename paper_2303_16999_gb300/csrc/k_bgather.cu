@@ -84,16 +84,28 @@ __device__ __forceinline__ void fma2_rn(float &a0, float &a1, float w, float x0,
     asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(d));
 }
 
+// (a.x s, a.y s), each product rounded to nearest as a scalar multiply
+// would be: one packed FP32 multiply for the pair.
+__device__ __forceinline__ float2 mul2_rn(float2 a, float s) {
+    unsigned long long av, sv, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(av) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(sv) : "f"(s));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(av), "l"(sv));
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
+    return r;
+}
+
 // Four E4M3 codes (one 32-bit word, lowest byte first) -> floats x scale.
 __device__ __forceinline__ void e4m3x4(uint32_t w, float sc, float *o) {
     const __half2_raw h01 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xFFFFu), __NV_E4M3);
     const __half2_raw h23 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
-    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&h01));
-    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&h23));
-    o[0] = a.x * sc;
-    o[1] = a.y * sc;
-    o[2] = b.x * sc;
-    o[3] = b.y * sc;
+    const float2 a = mul2_rn(__half22float2(*reinterpret_cast<const __half2 *>(&h01)), sc);
+    const float2 b = mul2_rn(__half22float2(*reinterpret_cast<const __half2 *>(&h23)), sc);
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = b.x;
+    o[3] = b.y;
 }
 
 // A 16-byte shared-memory read kept in program order (an asm volatile: the
