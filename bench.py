@@ -811,6 +811,7 @@ def run_batched(torch, S, wl, dev, peaks, reps=5):
                       "tuned_on_n": c["n"], "choice": r["kernel"],
                       "stage_geometry": r["stage_geometry"],
                       "rows_per_group": r["rows_per_group"], "k_splits": r["k_splits"],
+                      "col_tiles": r["col_tiles"],
                       "candidates": r["candidates"]})
         del codes, scales, xb
     t_tune = time.perf_counter() - t_tune
@@ -858,6 +859,8 @@ def run_batched(torch, S, wl, dev, peaks, reps=5):
     kinds = [q["kernel"] for q in infos]
     n_bg = sum(1 for k_ in kinds if k_ == 4)
     n_red = sum(1 for q in infos if q["kernel"] == 3 and q["n_reductions"] > 0)
+    wide = [q["kernel"] == 3 and q["col_tiles"] == 2 and y.shape[1] > 128 for q, y in zip(infos, Ys)]
+    tc_launches = int(any(wide)) + int(any(q["kernel"] == 3 and not w for q, w in zip(infos, wide)))
     out = {"workload": "batched: 48 FFN-like products, E4M3 W + FP32 block scales, BF16 X",
            "us": round(t_batch, 1), "tflops_nz": round(flops / t_batch / 1e6, 2),
            "sequential_same_plans_us": round(t_seq, 1),
@@ -866,9 +869,11 @@ def run_batched(torch, S, wl, dev, peaks, reps=5):
            "speedup_vs_sequential": round(t_seq / t_batch, 3),
            "packed_weight_gb": round(w_bytes / 1e9, 3),
            "problems_on_bgather": n_bg, "problems_on_tc": len(kinds) - n_bg,
-           # one BGATHER launch, one tensor-core launch (both stage
-           # geometries merged), one reduction launch per split problem
-           "gpu_launches": (1 if n_bg else 0) + (1 if n_bg < len(kinds) else 0) + n_red,
+           # one BGATHER launch, one tensor-core launch per kind of CTA
+           # (one or two column tiles; both stage geometries merged in each),
+           # one reduction launch per split problem
+           "gpu_launches": (1 if n_bg else 0) + tc_launches + n_red,
+           "problems_on_tc_two_column_tiles": sum(wide),
            "tuner": {"buckets": len(tuned), "seconds": round(t_tune, 1), "table": tuned}}
     # the batch call as one unit: its roofline is that of all 48 problems
     # together, compulsory bytes = E4M3 values + one FP32 scale and one int32

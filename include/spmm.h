@@ -117,11 +117,12 @@ typedef struct {
                                      Y m x n) for the W that the pattern and values describe in W's own
                                      coordinates (m x k, blocks row-major); internally the plan is the
                                      block-transposed operand, so plan info and arrays report k x m */
-    int32_t col_tiles;            /* TC, static plans with 16-bit weights: 128-column tiles of n per
-                                     CTA.  1 = one; 2 = two where the launch allows it (n > 128 and a
-                                     multiple of 64): the two tiles share every W stage, one CTA per SM;
-                                     0 = automatic (two for dense-tile plans with enough work units).
-                                     Results are identical either way.  Other values SPMM_ERR_ARG. */
+    int32_t col_tiles;            /* TC, static plans: 128-column tiles of n per CTA.  1 = one;
+                                     2 = two whenever n > 128 (16-bit or E4M3 weights): the two
+                                     tiles share every W stage (and its E4M3 expansion), one CTA
+                                     per SM; 0 = automatic (two for 16-bit dense-tile plans with n
+                                     a multiple of 64 and enough work units).  Results are
+                                     identical either way.  Other values SPMM_ERR_ARG. */
     int64_t groups;               /* TC plans: split the m/16 tile rows into exactly this many
                                      groups of near-equal size (sizes differ by at most one, larger
                                      first; at most 16 rows each), instead of the equal partition with
@@ -256,6 +257,7 @@ typedef struct {
     int32_t stage_geometry;       /* TC: 0 dense-tile stages, 1 sparse-tile stages (other kernels: 0) */
     int32_t sddmm_form;           /* spmm_sddmm on this plan: 0 dense tiles, 1 gathered blocks */
     int64_t row_begin, row_end;   /* the plan's slice of output rows (0, m for a whole plan) */
+    int32_t col_tiles;            /* TC: the col_tiles option the plan runs with (0, 1 or 2) */
 } spmm_plan_info;
 
 spmm_status spmm_plan_get_info(const spmm_plan *plan, spmm_plan_info *info);
@@ -424,14 +426,15 @@ spmm_status spmm_sddmm(spmm_plan *plan, const spmm_dpattern *pattern, const void
  * it builds one plan per candidate -- the tensor-core kernel with dense-tile
  * and with sparse-tile stages, each with the planner's default groups and,
  * where those shrink below 16 tile rows to fill the GPU, with 16-row groups
- * split along k into enough work items to fill it (k_splits); and the
+ * split along k into enough work items to fill it (k_splits); for n > 128
+ * both geometries with two column tiles per CTA (col_tiles = 2); and the
  * CUDA-core block gather (BGATHER) where n <= 16 and b >= 4 -- times `reps`
  * runs of each on `stream` after
  * two warm-up runs (CUDA events, median), and records the fastest for the
  * product's bucket: (b, W and X types, ceil(log2 m), ceil(log2 k),
  * round(log2(1/d)) with d the block density, ceil(log2 n)).  From then on
  * spmm_plan_create, for a static plan with kernel AUTO, no forced
- * stage_geometry, rows_per_group, groups or k_splits, takes the tuned
+ * stage_geometry, rows_per_group, groups, k_splits or col_tiles, takes the tuned
  * choice for its bucket (n = its n_max).
  *   reps          : 1 .. 64.
  *   out           : the choice and each candidate's median time (us, -1 if
@@ -444,6 +447,7 @@ typedef struct {
     int32_t stage_geometry;  /* TC: 1 dense-tile, 2 sparse-tile stages; 0 otherwise */
     int32_t rows_per_group;  /* TC: 16 = 16-row groups split along k (see k_splits); 0 = default */
     int32_t k_splits;        /* TC: work items per group when rows_per_group = 16 */
+    int32_t col_tiles;       /* TC: 2 = two column tiles per CTA (spmm_plan_opts.col_tiles); 0 */
 } spmm_tune_choice;
 
 typedef struct {

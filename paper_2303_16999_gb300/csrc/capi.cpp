@@ -473,12 +473,13 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
         // the autotuner's choice for this bucket, if it has one
         spmm_tune_choice tch{};
         if (o.kernel == SPMM_KERNEL_AUTO && o.stage_geometry == 0 && o.rows_per_group == 0 &&
-            o.groups == 0 && o.k_splits == 0 && mode == SPMM_STATIC && pattern && b >= 4 &&
-            tune_lookup(m, k, b, pattern->nnzb, n_max, w_dtype, x_dtype, &tch)) {
+            o.groups == 0 && o.k_splits == 0 && o.col_tiles == 0 && mode == SPMM_STATIC &&
+            pattern && b >= 4 && tune_lookup(m, k, b, pattern->nnzb, n_max, w_dtype, x_dtype, &tch)) {
             kernel = tch.kernel;
             o.stage_geometry = tch.stage_geometry;
             o.rows_per_group = tch.rows_per_group;
             o.k_splits = tch.k_splits;
+            o.col_tiles = tch.col_tiles;
         }
     }
     if (o.kernel == SPMM_KERNEL_AUTO && b == 1 && mode == SPMM_STATIC &&
@@ -558,8 +559,10 @@ static spmm_status plan_create(int64_t m, int64_t k, int64_t n_max, int32_t b, s
                     // the launch shape the plan will take (two column tiles
                     // per CTA for dense-tile plans), from a 16-row probe
                     // when the two shapes would want different group counts
-                    const bool can_wide = w_dtype != SPMM_E4M3 && o.col_tiles != 1 &&
-                                          n_max > kNTile && n_max % 64 == 0;
+                    const bool can_wide = o.col_tiles == 2
+                                              ? n_max > kNTile
+                                              : (w_dtype != SPMM_E4M3 && o.col_tiles != 1 &&
+                                                 n_max > kNTile && n_max % 64 == 0);
                     const int64_t qn = auto_groups(mt, n_max, p->sm_count, false);
                     const int64_t qw = can_wide ? auto_groups(mt, n_max, p->sm_count, true) : qn;
                     if (qn == qw) {
@@ -1012,6 +1015,7 @@ spmm_status spmm_plan_get_info(const spmm_plan *cp, spmm_plan_info *info) {
     i.n_reductions = dynran ? p->dyn_red : p->n_red;
     i.device_bytes = p->device_bytes;
     i.stage_geometry = p->kernel == SPMM_KERNEL_TC ? p->tc_geo : 0;
+    i.col_tiles = p->kernel == SPMM_KERNEL_TC ? p->col_tiles : 0;
     i.sddmm_form = sddmm_gathers(p) ? 1 : 0;
     i.row_begin = p->row_end ? p->row_begin : 0;
     i.row_end = p->row_end ? p->row_end : p->m;

@@ -151,7 +151,6 @@ constexpr int kMaxBatch = 64;                                     // problems pe
 // CTA ("wide": one CTA per SM, each W tile serves 256 columns of n; the
 // same entry and tile caps, hence the same stage records, as GEO - 2).
 template <bool W8, int GEO> struct StageGeom {
-    static_assert(GEO < 2 || !W8, "wide stages take 16-bit weights only");
     static constexpr int base = GEO & 1;            // dense (0) or sparse (1) tiles
     static constexpr int sets = GEO >= 2 ? 2 : 1;   // column tiles per CTA
     // X producer warps per column tile in wide CTAs: sparse-tile stages
@@ -160,14 +159,16 @@ template <bool W8, int GEO> struct StageGeom {
     static constexpr int producers = sets > 1 ? 1 + sets * xprod : 3;   // W + X warps
     static constexpr int threads = GEO == 3 ? 416 : sets > 1 ? 352 : 288;
     static constexpr int mma_warps = 2 * sets;      // one per row half and column tile
-    static constexpr int stages = W8 ? (GEO ? SPMM_TC_STAGES8_S : SPMM_TC_STAGES8)
+    // E4M3 weights: the same stage shapes whether a CTA covers one column
+    // tile or two (its W tiles, codes and scales serve both)
+    static constexpr int stages = W8 ? (base ? SPMM_TC_STAGES8_S : SPMM_TC_STAGES8)
                                      : GEO == 3   ? SPMM_TC_STAGES_WS
                                        : GEO == 2 ? SPMM_TC_STAGES_W
                                        : GEO      ? SPMM_TC_STAGES_S
                                                   : SPMM_TC_STAGES_D;
-    static constexpr int ent = W8 ? (GEO ? SPMM_TC_ENT8_S : SPMM_TC_ENT8)
+    static constexpr int ent = W8 ? (base ? SPMM_TC_ENT8_S : SPMM_TC_ENT8)
                                   : (base ? SPMM_TC_ENT_S : SPMM_TC_ENT_D);   // X slabs
-    static constexpr int tiles = W8 ? (GEO ? SPMM_TC_TILES8_S : SPMM_TC_TILES8)
+    static constexpr int tiles = W8 ? (base ? SPMM_TC_TILES8_S : SPMM_TC_TILES8)
                                     : (base ? SPMM_TC_TILES_S : SPMM_TC_TILES_D);
     static_assert(stages <= kStagesMax && ent <= 12 && tiles >= 16, "stage geometry");
     // a joint box of consecutive slabs must fit one column tile's slab area
@@ -459,12 +460,14 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
                         mbar_arrive(&sm->full[stage]);
                     }
                 } else if (G::sets > 1) {
-                    // wide (3-D X map only): producers 1 and 3 bring the
-                    // stage's slabs of the first column tile, 2 and 4 those
-                    // of the second (G::xprod warps per tile, each a share of
-                    // the slabs), as one box of consecutive slabs (the first
-                    // warp of the tile) or one box per slab
-                    const bool joint = (info & kJointBit) != 0;
+                    // wide: producers 1 and 3 bring the stage's slabs of the
+                    // first column tile, 2 and 4 those of the second
+                    // (G::xprod warps per tile, each a share of the slabs):
+                    // with a 3-D X map as one box of consecutive slabs (the
+                    // first warp of the tile) or one box per slab, with a 2-D
+                    // map as two 64-column boxes per slab (the lower one only
+                    // when the upper 64 columns lie past n)
+                    const bool joint = (info & kJointBit) && P.x3d;
                     const int tset = (pid - 1) & 1, part = (pid - 1) >> 1;
                     const bool act = tset == 0 || two;
                     const int per = (nent + G::xprod - 1) / G::xprod;
@@ -472,16 +475,28 @@ __global__ void __launch_bounds__(GEO == 3 ? 416 : GEO == 2 ? 352 : kThreads, GE
                     const int cnt = joint ? (part == 0 ? kJointSlabs : 0) : max(0, min(nent, lo + per) - lo);
                     const uint32_t xc =
                         __shfl_sync(0xffffffffu, rc, min(3 + (joint ? 0 : lo) + lane, kRecWords - 1));
+                    const int64_t ncol = n0 + (int64_t)tset * kNTile;     // this tile's first column
+                    const bool half = !P.x3d && ncol + kNTile / 2 >= P.n;
                     // (a joint box always lands all kJointSlabs slabs)
-                    if (lane == 0) mbar_arrive_tx(&sm->full[stage], act ? cnt * kSlabBytes : 0);
+                    if (lane == 0)
+                        mbar_arrive_tx(&sm->full[stage],
+                                       act ? cnt * (half ? kSlabBytes / 2 : kSlabBytes) : 0);
                     __syncwarp();
                     uint8_t *xs = st + tset * G::xset;
                     const int nh = n0 / (kNTile / 2) + tset * 2;
-                    if (act && joint && cnt && lane == 0)
-                        tma_load_3d(xs, &B.maps4[un.p], 0, (int)xc * kTile, nh, &sm->full[stage]);
-                    if (act && !joint && lane < cnt)
-                        tma_load_3d(xs + (lo + lane) * kSlabBytes, &B.maps[un.p], 0, (int)xc * kTile,
-                                    nh, &sm->full[stage]);
+                    if (P.x3d) {
+                        if (act && joint && cnt && lane == 0)
+                            tma_load_3d(xs, &B.maps4[un.p], 0, (int)xc * kTile, nh, &sm->full[stage]);
+                        if (act && !joint && lane < cnt)
+                            tma_load_3d(xs + (lo + lane) * kSlabBytes, &B.maps[un.p], 0,
+                                        (int)xc * kTile, nh, &sm->full[stage]);
+                    } else if (act && lane < cnt) {
+                        uint8_t *slab = xs + (lo + lane) * kSlabBytes;
+                        tma_load_2d(slab, &B.maps[un.p], (int)ncol, (int)xc * kTile, &sm->full[stage]);
+                        if (!half)
+                            tma_load_2d(slab + kSlabBytes / 2, &B.maps[un.p], (int)ncol + kNTile / 2,
+                                        (int)xc * kTile, &sm->full[stage]);
+                    }
                 } else if ((info & kJointBit) && P.x3d) {
                     // consecutive columns: X producer 1 requests all slabs in one box
                     if (lane == 0) {
@@ -918,10 +933,10 @@ __global__ void quantize_e4m3_kernel(const U *__restrict__ src, int64_t nnzb, in
 // faster wide; every sparse-tile point 6-11 % slower (two 86 KB stages per
 // CTA, against two narrow CTAs whose stages interleave).
 bool use_wide(const spmm_plan *p, int64_t n, int x3d) {
-    if (!x3d || p->col_tiles == 1 || p->mode != SPMM_STATIC || p->wdt == SPMM_E4M3 ||
-        n <= kNTile)
-        return false;
+    if (p->col_tiles == 1 || p->mode != SPMM_STATIC || n <= kNTile) return false;
+    // forced: any n > 128 (2-D X maps included) and E4M3 weights as well
     if (p->col_tiles == 2) return true;
+    if (!x3d || p->wdt == SPMM_E4M3) return false;
     const int64_t units = p->n_items * ((n + kNTile - 1) / kNTile);
     return p->tc_geo == 0 && 2 * units >= (int64_t)SPMM_TC_WIDE_MIN * p->sm_count;
 }
@@ -975,7 +990,11 @@ cudaError_t launch_batch(const TcBatch &B, int sm_count, cudaStream_t s) {
 
 template <typename T>
 cudaError_t launch_geo(const TcBatch &B, int geo, bool w8, int sm_count, cudaStream_t s) {
-    if (w8) return geo ? launch_batch<T, true, 1>(B, sm_count, s) : launch_batch<T, true, 0>(B, sm_count, s);
+    if (w8) {
+        if (geo == 3) return launch_batch<T, true, 3>(B, sm_count, s);
+        if (geo == 2) return launch_batch<T, true, 2>(B, sm_count, s);
+        return geo ? launch_batch<T, true, 1>(B, sm_count, s) : launch_batch<T, true, 0>(B, sm_count, s);
+    }
     if (geo == 3) return launch_batch<T, false, 3>(B, sm_count, s);
     if (geo == 2) return launch_batch<T, false, 2>(B, sm_count, s);
     return geo ? launch_batch<T, false, 1>(B, sm_count, s) : launch_batch<T, false, 0>(B, sm_count, s);
@@ -1039,25 +1058,46 @@ cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *cons
 cudaError_t ensure_alt_records(spmm_plan *p, int geo, cudaStream_t s);
 }
 
-// Plans of both stage geometries in one batch: ONE launch, in the geometry
-// that holds most of the batch's work units; plans of the other geometry
-// use stage records cut for it (built once per plan, on first use).  Only
-// the stage shapes differ, never the arithmetic of a unit, so every result
-// is the same as in its own geometry.
+// Plans of both stage geometries in one launch, in the geometry that holds
+// most of its work units; plans of the other geometry use stage records cut
+// for it (built once per plan, on first use).  Only the stage shapes differ,
+// never the arithmetic of a unit, so every result is the same as in its own
+// geometry.  Plans that ask for two column tiles per CTA (col_tiles = 2,
+// n > 128) run in a second launch of the two-column-tile kernel.
 cudaError_t launch_tc_batch(int count, spmm_plan *const *plans, const void *const *X,
                             const int64_t *n, const int64_t *ldx, void *const *Y,
                             const int64_t *ldy, cudaStream_t s, bool schedule) {
     if (count <= 0 || count > kMaxBatch) return cudaErrorInvalidValue;
-    int64_t units[2] = {0, 0};
-    for (int i = 0; i < count; ++i)
-        units[plans[i]->tc_geo & 1] += plans[i]->n_items * ((n[i] + kNTile - 1) / kNTile);
-    const int geo = units[1] > units[0] ? 1 : 0;
-    for (int i = 0; i < count; ++i) {
-        if (plans[i]->tc_geo == geo) continue;
-        cudaError_t e = ensure_alt_records(plans[i], geo, s);
+    for (int wide = 0; wide < 2; ++wide) {
+        spmm_plan *gp[kMaxBatch];
+        const void *gx[kMaxBatch];
+        void *gy[kMaxBatch];
+        int64_t gn[kMaxBatch], glx[kMaxBatch], gly[kMaxBatch];
+        int c = 0;
+        int64_t units[2] = {0, 0};
+        for (int i = 0; i < count; ++i) {
+            const bool w = plans[i]->col_tiles == 2 && n[i] > kNTile;
+            if (w != (wide != 0)) continue;
+            gp[c] = plans[i];
+            gx[c] = X[i];
+            gy[c] = Y[i];
+            gn[c] = n[i];
+            glx[c] = ldx ? ldx[i] : n[i];
+            gly[c] = ldy ? ldy[i] : n[i];
+            units[plans[i]->tc_geo & 1] += plans[i]->n_items * ((n[i] + kNTile - 1) / kNTile);
+            ++c;
+        }
+        if (!c) continue;
+        const int geo = units[1] > units[0] ? 1 : 0;
+        for (int i = 0; i < c; ++i) {
+            if (gp[i]->tc_geo == geo) continue;
+            cudaError_t e = ensure_alt_records(gp[i], geo, s);
+            if (e != cudaSuccess) return e;
+        }
+        cudaError_t e = launch_tc_group(c, gp, gx, gn, glx, gy, gly, s, schedule, geo + 2 * wide);
         if (e != cudaSuccess) return e;
     }
-    return launch_tc_group(count, plans, X, n, ldx, Y, ldy, s, schedule, geo);
+    return cudaSuccess;
 }
 
 namespace {
@@ -1112,12 +1152,14 @@ cudaError_t launch_tc_group(int count, spmm_plan *const *plans, const void *cons
             e = encode_x(&B.maps4[i], &x3d, p->xdt == SPMM_BF16, X[i], p->k, n[i], lx,
                          kJointSlabs);
         if (e != cudaSuccess) return e;
-        fill_prob(B.prob[i], p, Y[i], n[i], ly, x3d, p->tc_geo != geo);
+        fill_prob(B.prob[i], p, Y[i], n[i], ly, x3d, p->tc_geo != (geo & 1));
+        if (geo >= 2) B.prob[i].ntn = (B.prob[i].ntn + 1) / 2;   // units of two column tiles
         B.prob[i].unit_base = base;
         base += p->n_items * B.prob[i].ntn;
         key.plans.push_back(p);
         key.n.push_back(n[i]);
     }
+    key.n.push_back(geo);   // the same plans may run in either kind of launch
     B.nprob = count;
     B.total_units = base;
     B.status = plans[0]->d_status;

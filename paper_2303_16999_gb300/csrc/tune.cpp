@@ -76,7 +76,7 @@ spmm_status spmm_tune(int64_t m, int64_t k, int64_t n, int32_t b, spmm_dtype w_d
     // the planner's groups and, where those shrink below 16 tile rows to
     // fill the CTA slots, with 16-row groups split along k instead; and the
     // CUDA-core block gather where it applies
-    std::vector<spmm_tune_choice> cands = {{SPMM_KERNEL_TC, 1, 0, 0}, {SPMM_KERNEL_TC, 2, 0, 0}};
+    std::vector<spmm_tune_choice> cands = {{SPMM_KERNEL_TC, 1, 0, 0, 0}, {SPMM_KERNEL_TC, 2, 0, 0, 0}};
     {
         int dev = 0, sms = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -87,14 +87,18 @@ spmm_status spmm_tune(int64_t m, int64_t k, int64_t n, int32_t b, spmm_dtype w_d
             if (g16 * ntn < slots) {
                 const int32_t split =
                     (int32_t)std::min<int64_t>(1024, (slots + g16 * ntn - 1) / (g16 * ntn));
-                cands.push_back({SPMM_KERNEL_TC, 1, kMaxGroupRows, split});
-                cands.push_back({SPMM_KERNEL_TC, 2, kMaxGroupRows, split});
+                cands.push_back({SPMM_KERNEL_TC, 1, kMaxGroupRows, split, 0});
+                cands.push_back({SPMM_KERNEL_TC, 2, kMaxGroupRows, split, 0});
             }
         }
     }
+    if (n > kNTile) {
+        cands.push_back({SPMM_KERNEL_TC, 1, 0, 0, 2});
+        cands.push_back({SPMM_KERNEL_TC, 2, 0, 0, 2});
+    }
     const bool x16 = x_dtype == SPMM_F16 || x_dtype == SPMM_BF16;
     if (b >= 4 && n <= kBgMaxN && x16 && (w_dtype == x_dtype || w_dtype == SPMM_E4M3))
-        cands.push_back({SPMM_KERNEL_BGATHER, 0, 0, 0});
+        cands.push_back({SPMM_KERNEL_BGATHER, 0, 0, 0, 0});
     void *d_Y = nullptr;
     cudaError_t e = cudaMalloc(&d_Y, (size_t)m * n * dtype_size(x_dtype));
     if (e != cudaSuccess) {
@@ -114,6 +118,7 @@ spmm_status spmm_tune(int64_t m, int64_t k, int64_t n, int32_t b, spmm_dtype w_d
         o.stage_geometry = cands[ci].stage_geometry;
         o.rows_per_group = cands[ci].rows_per_group;
         o.k_splits = cands[ci].k_splits;
+        o.col_tiles = cands[ci].col_tiles;
         spmm_plan *p = nullptr;
         spmm_status cs = spmm_plan_create(m, k, n, b, SPMM_STATIC, w_dtype, x_dtype, pattern, 0,
                                           &o, &p);

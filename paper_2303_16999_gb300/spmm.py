@@ -75,12 +75,14 @@ class PlanInfo(ctypes.Structure):
         [(n, ctypes.c_int64) for n in ("n_items", "n_groups", "n_entries", "n_tiles",
                                       "ws_rows", "n_reductions", "device_bytes")] + \
         [(n, ctypes.c_int32) for n in ("stage_geometry", "sddmm_form")] + \
-        [(n, ctypes.c_int64) for n in ("row_begin", "row_end")]
+        [(n, ctypes.c_int64) for n in ("row_begin", "row_end")] + \
+        [("col_tiles", ctypes.c_int32)]
 
 
 class TuneChoice(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("stage_geometry", ctypes.c_int32),
-                ("rows_per_group", ctypes.c_int32), ("k_splits", ctypes.c_int32)]
+                ("rows_per_group", ctypes.c_int32), ("k_splits", ctypes.c_int32),
+                ("col_tiles", ctypes.c_int32)]
 
 
 class TuneResult(ctypes.Structure):
@@ -206,7 +208,8 @@ def spmm_tune(m, k, b, brow, bcol, values, X, w_dtype=F16, x_dtype=None, scales=
     names = {v: k_ for k_, v in KERNELS.items()}
     def desc(c):
         return {"kernel": names.get(c.kernel, c.kernel), "stage_geometry": c.stage_geometry,
-                "rows_per_group": c.rows_per_group, "k_splits": c.k_splits}
+                "rows_per_group": c.rows_per_group, "k_splits": c.k_splits,
+                "col_tiles": c.col_tiles}
     cands = [dict(desc(r.cand[i]), us=round(r.cand_us[i], 2)) for i in range(r.n_candidates)]
     return dict(desc(r.choice), best_us=round(r.best_us, 2), candidates=cands)
 

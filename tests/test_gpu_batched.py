@@ -279,6 +279,63 @@ def test_batch_mixed_geometries_one_launch_equals_alone():
                              checks.max_terms(c["brow"], c["b"]))
 
 
+@pytest.mark.parametrize("b,d,n,geo", [(8, 1 / 8, 331, 2), (16, 1 / 16, 257, 2), (8, 1 / 16, 200, 1),
+                                       (16, 1 / 4, 384, 1), (4, 1 / 8, 136, 2)])
+def test_e4m3_two_column_tiles_equal_one(b, d, n, geo):
+    """E4M3 plans whose CTAs cover two column tiles (col_tiles = 2: each
+    stage's W tiles expanded once for both), with 3-D X maps (n a multiple of
+    64) and 2-D ones (331, 257, 200, 136): bit for bit equal to one column
+    tile per CTA (each accumulator column sees the same MMAs in the same
+    order), and within the bars against the oracle."""
+    c = _problem(990 + n, 1024, 4096, n, b, d)
+    p2, codes, scales = _e4m3_plan(c, kernel="tc", stage_geometry=geo, col_tiles=2)
+    p1, _, _ = _e4m3_plan(c, kernel="tc", stage_geometry=geo, col_tiles=1)
+    assert p2.info()["col_tiles"] == 2 and p1.info()["col_tiles"] == 1
+    X = _x(c, torch.bfloat16)
+    Y2 = torch.full((c["m"], n), float("nan"), dtype=torch.bfloat16, device="cuda")
+    p2.run(X, Y2)
+    Y1 = p1.run(X)
+    torch.cuda.synchronize()
+    assert p2.status() == 0 and p1.status() == 0
+    assert torch.equal(Y1, Y2)
+    v = oracle.e4m3_block_values(codes.view(torch.uint8).numpy(), scales.numpy())
+    Yo = oracle.spmm(c["m"], c["k"], b, c["brow"], c["bcol"], v, X.cpu())
+    A = oracle.spmm(c["m"], c["k"], b, c["brow"], c["bcol"], np.abs(v), np.abs(oracle.to_f64(X.cpu())))
+    checks.assert_parity(Y2.cpu(), Yo, oracle.block_fro(v), X.cpu(), A, torch.bfloat16,
+                         checks.max_terms(c["brow"], b), u_w=2.0 ** -8)
+
+
+def test_batch_with_two_column_tile_plans_equals_alone():
+    """A batch mixing plans with two column tiles per CTA (n > 128), plans
+    asking for two with n <= 128 (they run with one) and default plans: the
+    two kinds run as two tensor-core launches, and each result is bit for
+    bit the plan run alone."""
+    spec = ((8, 1 / 8, 331, 2), (16, 1 / 16, 90, 2), (8, 1 / 16, 257, 0), (16, 1 / 8, 200, 2),
+            (16, 1 / 16, 40, 0))
+    cases = [_problem(1100 + i, 1024, 2048, n, b, d) for i, (b, d, n, _) in enumerate(spec)]
+    plans, Xs, Ys, keep = [], [], [], []
+    for c, (_, _, n, ct) in zip(cases, spec):
+        p, codes, scales = _e4m3_plan(c, kernel="tc", col_tiles=ct)
+        plans.append(p)
+        keep.append((codes, scales))
+        Xs.append(_x(c, torch.bfloat16))
+        Ys.append(torch.full((c["m"], n), float("nan"), dtype=torch.bfloat16, device="cuda"))
+    for _ in range(2):
+        S.spmm_batch_run(plans, Xs, Ys)
+    torch.cuda.synchronize()
+    for c, p, X, Y, (codes, scales) in zip(cases, plans, Xs, Ys, keep):
+        assert p.status() == 0
+        alone = p.run(X)
+        torch.cuda.synchronize()
+        assert torch.equal(alone, Y)
+        v = oracle.e4m3_block_values(codes.view(torch.uint8).numpy(), scales.numpy())
+        Yo = oracle.spmm(c["m"], c["k"], c["b"], c["brow"], c["bcol"], v, X.cpu())
+        A = oracle.spmm(c["m"], c["k"], c["b"], c["brow"], c["bcol"], np.abs(v),
+                        np.abs(oracle.to_f64(X.cpu())))
+        checks.assert_parity(Y.cpu(), Yo, oracle.block_fro(v), X.cpu(), A, torch.bfloat16,
+                             checks.max_terms(c["brow"], c["b"]), u_w=2.0 ** -8)
+
+
 def test_tuner_choice_applies_to_auto_plans():
     """spmm_tune times the candidates of a product's bucket and AUTO plans of
     that bucket then take the fastest; the tuned plan is still within the

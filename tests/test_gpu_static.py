@@ -305,9 +305,11 @@ def test_two_column_tiles_per_cta(b, d, n, geo, dt):
     of n (the two share each stage's W tiles; the second tile's slabs,
     accumulators and MMA warps are separate).  n = 192: the second tile is
     partly past n; 320, 448 and 640: the last CTA has one tile only; 200 and
-    130: not multiples of 64, so the launch keeps one tile per CTA.  Within
-    the bound against the oracle, and bit for bit equal to one tile per CTA
-    (every accumulator column sees the same MMAs in the same order)."""
+    130: not multiples of 64, so X is read through a 2-D map, two 64-column
+    boxes per slab (130: the second tile's upper half lies past n and is not
+    fetched).  Within the bound against the oracle, and bit for bit equal to
+    one tile per CTA (every accumulator column sees the same MMAs in the
+    same order)."""
     m, k = 1024, 1024
     nnzb = wl.nnzb_for(m, k, b, d)
     err, Y2, _, plan = run_case(m, k, n, b, nnzb, dt, "tc", seed=5 * b + n,
