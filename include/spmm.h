@@ -305,9 +305,10 @@ int64_t spmm_bucket_size(int64_t m, int64_t k, int64_t d_max_num, int64_t d_max_
 
 /*
  * spmm_batch_run -- `count` (<= 64) static TC or BGATHER plans with packed
- * values, run as one persistent launch per kernel family: the BGATHER
- * problems (small n, CUDA cores) in one launch, then the tensor-core
- * problems in one launch.  Tensor-core plans of both stage geometries run
+ * values, run as persistent launches: the BGATHER problems (small n, CUDA
+ * cores) in one launch, then the tensor-core problems in one launch (two
+ * when some plans take two column tiles per CTA: col_tiles = 2 with
+ * n > 128; those run in a launch of their own).  Tensor-core plans of both stage geometries run
  * in the geometry that holds most of the batch's work; the others use
  * stage records cut for it (built once per plan on first use; results are
  * identical).  The tensor-core launch's CTAs walk one schedule of

@@ -1100,8 +1100,9 @@ spmm_status spmm_batch_run(int32_t count, spmm_plan *const *plans, const void *c
                 return SPMM_ERR_ARG;
             }
     }
-    // one launch per kernel family: the small-n problems (BGATHER) first,
-    // then the tensor-core ones
+    // the small-n problems (BGATHER) in one launch first, then the
+    // tensor-core ones (one launch, or two when some plans take two column
+    // tiles per CTA)
     spmm_plan *gp[kMaxBatchProblems], *tp[kMaxBatchProblems];
     const void *gx[kMaxBatchProblems], *tx[kMaxBatchProblems];
     void *gy[kMaxBatchProblems], *ty[kMaxBatchProblems];
