@@ -243,7 +243,7 @@ def kernel_source_sha16(files=("csrc/k_tc.cu", "csrc/tc_ptx.cuh", "csrc/capi.cpp
 # of one step; the command and the per-launch table are in
 # profiles/tc_kernel_sweep_dram.md).  Used only while the kernel and planner
 # sources hash to `sha16`; otherwise the bench reports traffic null.
-SWEEP_TRAFFIC = {"sha16": "3c1bf316e5ae37ab", "bytes_per_launch": 38578544.0,
+SWEEP_TRAFFIC = {"sha16": "8d4ff2df56a8a4b9", "bytes_per_launch": 38592560.0,
                  "source": "profiles/tc_kernel_sweep_dram.md"}
 
 
@@ -1362,6 +1362,22 @@ def run_comparators(torch, S, wl, dev, pts):
     out["cublas_dense_fp16"] = {"us": round(us, 1), "tflops_nz": round(fl / us / 1e6, 2),
                                 "tflops_dense": round(2.0 * M * K * N / us / 1e6, 1)}
     out["point"] = "b=16, d=1/16, m=k=4096, n=2048"
+    # AUTO's kernel for b = 1 at n = 2048: the CUDA-core gather kernel against
+    # the tensor-core plan the sweep runs, same pattern, values and X (warm L2)
+    b1 = []
+    for q in pts:
+        if q["b"] != 1 or q["m"] != M:    # (row-split plans cover a slice of Y)
+            continue
+        cq = q["c"]
+        pg = S.Plan(M, K, N, 1, w_dtype=S.F16, brow=cq["brow"], bcol=cq["bcol"], kernel="gather")
+        pg.pack(torch.from_numpy(cq["vals"].reshape(-1)).half().to(dev))
+        Yg = torch.empty((M, N), dtype=torch.float16, device=dev)
+        g_us = timeit(lambda: pg.run(q["X"], Yg), reps=5)
+        t_us = timeit(lambda: q["plan"].run(q["X"], q["Y"]), reps=5)
+        b1.append({"d": "1/%d" % round(1 / q["d"]), "gather_us": round(g_us, 1),
+                   "tc_us": round(t_us, 1), "auto": {2: "gather", 3: "tc"}[q["kernel"]]})
+        pg.close()
+    out["b1_gather_vs_tc_n2048"] = b1
     return out
 
 
