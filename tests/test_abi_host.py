@@ -76,6 +76,14 @@ def test_errors():
         with pytest.raises(S.SpmmError) as e:
             _plan(16, 16, 4, [0], [0], col_tiles=bad)
         assert e.value.status == S.ERR_ARG
+    for bad in (-1, 1025):
+        with pytest.raises(S.SpmmError) as e:
+            _plan(16, 16, 4, [0], [0], kernel="tc", k_splits=bad)
+        assert e.value.status == S.ERR_ARG and "k_splits" in str(e.value)
+    # the options a plan runs with are reported back
+    q = _plan(64, 64, 4, [0, 5], [1, 3], kernel="tc", col_tiles=2, n_max=256)
+    assert q.info()["col_tiles"] == 2
+    assert _plan(64, 64, 4, [0], [1], kernel="tc").info()["col_tiles"] == 0
     p = _plan(16, 16, 4, [], [])
     assert p.info()["nnzb"] == 0
     # the sampled product refuses host-only plans before touching the device
