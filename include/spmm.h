@@ -239,10 +239,14 @@ spmm_status spmm_get_status(spmm_plan *plan, int32_t *device_status);
  * SPMM_ERR_TIMEOUT in the plan's status word, stops, lets its copies and
  * MMAs in flight complete, frees its tensor memory and exits; Y is then not
  * to be trusted, and spmm_get_status reports the timeout.  The context
- * stays usable and the next call runs normally.  stall = 1 is a test hook:
- * after their first stage the MMA warps wait on a barrier that nothing
- * arrives on, so that every CTA takes the timeout path after limit_ns
- * (use a short limit).  This library's own extension, not in the paper.
+ * stays usable and the next call runs normally.  Dynamic tensor-core plans
+ * bound the grid barriers of their re-partition launch the same way (the
+ * launch ends, the product launch skips).  stall = 1 is a test hook: after
+ * their first stage the MMA warps wait on a barrier that nothing arrives
+ * on, and in a dynamic plan's re-partition one CTA skips its arrival at the
+ * first grid barrier, so that every CTA takes the timeout path after
+ * limit_ns (use a short limit).  This library's own extension, not in the
+ * paper.
  * Returns SPMM_ERR_ARG for a NULL plan, limit_ns < 0 or stall not 0/1.
  */
 spmm_status spmm_plan_set_wait(spmm_plan *plan, int64_t limit_ns, int32_t stall);

@@ -19,11 +19,11 @@
 // plans run all of it, with the packing and the stage records, in one
 // cooperative launch instead (see "fused" below); the chain remains for the
 // b = 1 gather plans, the sampled product's block CSR, devices without
-// cooperative launches and spmm_plan_opts.dyn_chain.  Measured at m = k =
-// 8192, b = 16, d_max = 1/16 (GB300): the fused launch takes about 40 us,
-// the chain about the same (39 us of re-partition and packing plus 6 us of
-// stage records); each of its four grid barriers costs about 2 us, about
-// what a kernel boundary of the chain costs.
+// cooperative launches and spmm_plan_opts.dyn_chain.  The whole job is a
+// chain of dependent steps over a few megabytes: its time goes to memory
+// round trips, CTA barriers and the grid barriers between steps, not to
+// bytes or arithmetic (a kernel boundary of the chain costs a few
+// microseconds, a grid barrier of the fused launch about one).
 // The arrays equal the oracle's dynamic-plan rules bit for bit (no item
 // reordering, no zero-padded intervals).  A rejected pattern sets the plan's
 // status word; the product kernels then skip, leaving Y unwritten.
@@ -113,6 +113,42 @@ __device__ int64_t block_scan(int64_t v, int64_t *total) {
     *total = warp_sums[31];
     __syncthreads();
     return excl;
+}
+
+// N block-wide exclusive scans at once (blockDim.x == 1024): v[i] in,
+// the exclusive prefix in v[i], the block's total in tot[i].
+template <int N>
+__device__ void block_scan_n(int64_t (&v)[N], int64_t (&tot)[N]) {
+    __shared__ int64_t warp_sums[N][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int64_t x[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        x[i] = v[i];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x[i], o);
+            if (lane >= o) x[i] += y;
+        }
+        if (lane == 31) warp_sums[i][w] = x[i];
+    }
+    __syncthreads();
+    if (w < N) {
+        int64_t t = warp_sums[w][lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        warp_sums[w][lane] = t;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        v[i] = x[i] - v[i] + (w > 0 ? warp_sums[i][w - 1] : 0);
+        tot[i] = warp_sums[i][31];
+    }
+    __syncthreads();
 }
 
 __device__ __forceinline__ int32_t nchunks(int64_t L, int64_t C) {
@@ -324,9 +360,19 @@ __device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *gr
                            int32_t *ent_tbeg, int32_t *counts) {
     __shared__ int64_t sE;
     int64_t tot;
+    // this thread's group among the first 1024, read once for both passes
+    int64_t L0 = 0, S0 = 0, R0 = 0;
     {
         int64_t part = 0;
-        for (int32_t g = threadIdx.x; g < G; g += 1024) part += __ldcg(grp_cnt + g * 2);
+        for (int32_t g = threadIdx.x; g < G; g += 1024) {
+            const int64_t L = __ldcg(grp_cnt + g * 2);
+            if (g < 1024) {
+                L0 = L;
+                S0 = __ldcg(grp_cnt + g * 2 + 1);
+                R0 = grp_rows[g];
+            }
+            part += L;
+        }
         block_scan(part, &tot);
         if (threadIdx.x == 0) sE = tot;
         __syncthreads();
@@ -337,31 +383,27 @@ __device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *gr
     int64_t be = 0, bs = 0, bi = 0, bw = 0, bwr = 0, br = 0;
     for (int32_t g0 = 0; g0 < G; g0 += 1024) {
         const int32_t g = g0 + threadIdx.x;
-        const int64_t L = g < G ? __ldcg(grp_cnt + g * 2) : 0;
-        const int64_t S = g < G ? __ldcg(grp_cnt + g * 2 + 1) : 0;
+        const int64_t L = g < G ? (g0 == 0 ? L0 : __ldcg(grp_cnt + g * 2)) : 0;
+        const int64_t S = g < G ? (g0 == 0 ? S0 : __ldcg(grp_cnt + g * 2 + 1)) : 0;
         const int32_t nch = g < G ? nchunks(L, C) : 0;
-        const int64_t rows = g < G ? (int64_t)grp_rows[g] * kTile : 0;
-        int64_t t0, t1, t2, t3, t4, t5;
-        const int64_t e0 = block_scan(L, &t0);
-        const int64_t e1 = block_scan(S, &t1);
-        const int64_t e2 = block_scan(nch, &t2);
-        const int64_t e3 = block_scan(nch > 1 ? nch : 0, &t3);
-        const int64_t e4 = block_scan(nch > 1 ? nch * rows : 0, &t4);
-        const int64_t e5 = block_scan(nch > 1 ? 1 : 0, &t5);
+        const int64_t rows = g < G ? (g0 == 0 ? R0 : (int64_t)grp_rows[g]) * kTile : 0;
+        int64_t v[6] = {L, S, nch, nch > 1 ? nch : 0, nch > 1 ? nch * rows : 0, nch > 1 ? 1 : 0};
+        int64_t t[6];
+        block_scan_n<6>(v, t);
         if (g < G) {
-            grp_ebeg[g] = (int32_t)(be + e0);
-            grp_sbeg[g] = (int32_t)(bs + e1);
-            grp_ibeg[g] = (int32_t)(bi + e2);
-            grp_wbeg[g] = (int32_t)(bw + e3);
-            grp_wrow[g] = bwr + e4;
-            grp_rbeg[g] = (int32_t)(br + e5);
+            grp_ebeg[g] = (int32_t)(be + v[0]);
+            grp_sbeg[g] = (int32_t)(bs + v[1]);
+            grp_ibeg[g] = (int32_t)(bi + v[2]);
+            grp_wbeg[g] = (int32_t)(bw + v[3]);
+            grp_wrow[g] = bwr + v[4];
+            grp_rbeg[g] = (int32_t)(br + v[5]);
         }
-        be += t0;
-        bs += t1;
-        bi += t2;
-        bw += t3;
-        bwr += t4;
-        br += t5;
+        be += t[0];
+        bs += t[1];
+        bi += t[2];
+        bw += t[3];
+        bwr += t[4];
+        br += t[5];
     }
     if (threadIdx.x == 0) {
         grp_ebeg[G] = (int32_t)be;
@@ -376,24 +418,53 @@ __device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *gr
     }
 }
 
+// Group g's offsets from the group scan, read once before the fill.
+struct GroupOff {
+    int32_t row0, rows;          // first tile row, tile rows
+    int32_t ebeg, eend;          // entries [ebeg, eend)
+    int32_t sbeg, send;          // slots [sbeg, send)
+    int32_t ibeg, wbeg, rbeg;    // first item, workspace slot, reduction
+    int64_t wrow, C;             // first workspace row, chunk size
+};
+
+__device__ __forceinline__ GroupOff load_group_off(int g, const int32_t *grp_row0,
+                                                   const int32_t *grp_rows,
+                                                   const int32_t *grp_ebeg,
+                                                   const int32_t *grp_sbeg,
+                                                   const int32_t *grp_ibeg,
+                                                   const int32_t *grp_wbeg,
+                                                   const int64_t *grp_wrow,
+                                                   const int32_t *grp_rbeg,
+                                                   const int32_t *counts, int32_t G) {
+    GroupOff o;
+    o.row0 = grp_row0[g];
+    o.rows = grp_rows[g];
+    o.ebeg = grp_ebeg[g];
+    o.eend = grp_ebeg[g + 1];
+    o.sbeg = grp_sbeg[g];
+    o.send = g + 1 < G ? grp_sbeg[g + 1] : counts[kCntSlots];
+    o.ibeg = grp_ibeg[g];
+    o.wbeg = grp_wbeg[g];
+    o.rbeg = grp_rbeg[g];
+    o.wrow = grp_wrow[g];
+    o.C = counts[kCntChunk];
+    return o;
+}
+
 // Group g's entries (ascending tile column), slots (ascending rows, one per
 // tile), block -> slot / offset, items and workspace / reduction records,
 // from its column masks (whole CTA of 1024 threads; slot_of[kt] in shared
-// memory; [s0, s1) the group's CSR slots).
-__device__ void group_fill(int g, int32_t kt, int32_t T, int32_t b, const int32_t *grp_row0,
-                           const int32_t *grp_rows, const int32_t *row_ptr,
-                           const int32_t *col_idx, const int32_t *perm, const int32_t *grp_ebeg,
-                           const int32_t *grp_sbeg, const int32_t *grp_ibeg,
-                           const int32_t *grp_wbeg, const int64_t *grp_wrow,
-                           const int32_t *grp_rbeg, const int32_t *counts,
+// memory; [s0, s1) the group's CSR slots; o its offsets).
+__device__ void group_fill(int g, const GroupOff &o, int32_t kt, int32_t T, int32_t b,
+                           const int32_t *row_ptr, const int32_t *col_idx, const int32_t *perm,
                            const uint32_t *colmask, int32_t *slot_of, int32_t s0, int32_t s1,
                            int32_t *ent_col, int32_t *ent_tbeg, int32_t *ent_cover,
                            int32_t *tile_row, int32_t *blk_slot, int32_t *blk_off, int32_t *items,
                            int64_t *ws_row0, int32_t *red, const int32_t *rp_s = nullptr,
                            int32_t *pk = nullptr) {
-    const int32_t t0 = grp_row0[g], nrows = grp_rows[g];
+    const int32_t t0 = o.row0, nrows = o.rows;
     // column prefix over entries and slots, in chunks of blockDim (1024)
-    int64_t eb = grp_ebeg[g], sb = grp_sbeg[g];
+    int64_t eb = o.ebeg, sb = o.sbeg;
     for (int32_t c0 = 0; c0 < kt; c0 += 1024) {
         const int32_t c = c0 + threadIdx.x;
         const uint32_t mk = c < kt ? colmask[c] : 0u;
@@ -444,27 +515,26 @@ __device__ void group_fill(int g, int32_t kt, int32_t T, int32_t b, const int32_
     __syncthreads();   // the masks may be reused by the calling CTA after this
     if (threadIdx.x != 0) return;
     // items: near-equal chunks of the group's entries
-    const int64_t C = counts[kCntChunk];
-    const int32_t e0 = grp_ebeg[g], L = grp_ebeg[g + 1] - e0, nch = nchunks(L, C);
+    const int32_t e0 = o.ebeg, L = o.eend - e0, nch = nchunks(L, o.C);
     const int32_t base = L / nch, rem = L % nch;
     int32_t e = e0;
     for (int32_t c = 0; c < nch; ++c) {
         const int32_t sz = base + (c < rem ? 1 : 0);
-        int32_t *it = items + (int64_t)(grp_ibeg[g] + c) * kItemFields;
-        const int32_t ws = nch > 1 ? grp_wbeg[g] + c : -1;
+        int32_t *it = items + (int64_t)(o.ibeg + c) * kItemFields;
+        const int32_t ws = nch > 1 ? o.wbeg + c : -1;
         it[0] = g;
         it[1] = e;
         it[2] = e + sz;
         it[3] = c;
         it[4] = nch;
         it[5] = ws;
-        if (ws >= 0) ws_row0[ws] = grp_wrow[g] + (int64_t)c * nrows * kTile;
+        if (ws >= 0) ws_row0[ws] = o.wrow + (int64_t)c * nrows * kTile;
         e += sz;
     }
     if (nch > 1) {
-        int32_t *rd = red + (int64_t)grp_rbeg[g] * 3;
+        int32_t *rd = red + (int64_t)o.rbeg * 3;
         rd[0] = g;
-        rd[1] = grp_wbeg[g];
+        rd[1] = o.wbeg;
         rd[2] = nch;
     }
 }
@@ -486,21 +556,22 @@ __global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *
     uint32_t *colmask = sm;                 // kt
     int32_t *slot_of = (int32_t *)(sm + kt); // kt: first slot of the column's entry
     const int g = blockIdx.x;
+    const GroupOff o = load_group_off(g, grp_row0, grp_rows, grp_ebeg, grp_sbeg, grp_ibeg,
+                                      grp_wbeg, grp_wrow, grp_rbeg, counts, (int32_t)gridDim.x);
     int32_t s0, s1;
     group_colmask(g, kt, T, grp_row0, grp_rows, row_ptr, col_idx, colmask, &s0, &s1);
-    group_fill(g, kt, T, b, grp_row0, grp_rows, row_ptr, col_idx, perm, grp_ebeg, grp_sbeg,
-               grp_ibeg, grp_wbeg, grp_wrow, grp_rbeg, counts, colmask, slot_of, s0, s1, ent_col,
+    group_fill(g, o, kt, T, b, row_ptr, col_idx, perm, colmask, slot_of, s0, s1, ent_col,
                ent_tbeg, ent_cover, tile_row, blk_slot, blk_off, items, ws_row0, red);
 }
 
 // ------------------------------------------------ fused (cooperative) ---
 // Dynamic tensor-core plans run the re-partition, the value packing and the
 // stage records in ONE cooperative launch: every CTA is resident and the
-// steps are separated by four grid barriers instead of seven kernel
+// steps are separated by three grid barriers instead of seven kernel
 // boundaries (each costs a few microseconds).  The arrays are the same as
 // the launch chain's, bit for bit; the block CSR is built from a bitmap of
 // each block row's block columns instead of a scatter and a row sort:
-//   A. clear the bitmap, the row counts and the status word       | barrier
+//   A. clear the bitmap, the count words and the status word      | barrier
 //   B. validate; set each block's bit (a bit already set is a
 //      repeated block)                                              | barrier,
 //      then CTA 0 scans the bitmap's popcounts (row_ptr, and the
@@ -512,13 +583,14 @@ __global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *
 //      then CTA 0 scans the groups (offsets, chunk size)
 //   D. per group: entries, slots, block -> slot, items (the chain's fill,
 //      with the group's row pointers and its blocks' slots in shared
-//      memory), the group's tiles cleared where blocks do not fill them,
-//      and its blocks' values packed, a warp per block               | barrier
-//   E. stage records, a CTA per work item.
-// Barrier: each CTA publishes its arrival in a flag of its own; CTA 0
-// waits for all flags, runs the step that follows a barrier (a scan) and
-// then publishes the barrier's generation, which the other CTAs wait for.
-// Every wait is bounded; on expiry the status word records
+//      memory), the group's tiles cleared where blocks do not fill them;
+//      then, side by side, the stage records of the group's items (8
+//      warps; an item's entries are its group's, so no barrier is
+//      needed) and its blocks' values packed, a warp per block (the rest).
+// Barrier: each CTA counts its arrival on one counter.  Where no step
+// follows, every CTA waits for the count; where one does (a scan), CTA 0
+// waits, runs it and publishes the barrier's generation, which the other
+// CTAs wait for.  Every wait is bounded; on expiry the status word records
 // SPMM_ERR_TIMEOUT and the launch ends (the product launch then skips).
 struct DynFusedArgs {
     const int32_t *d_nnzb, *brow, *bcol;
@@ -544,6 +616,7 @@ struct DynFusedArgs {
     int64_t items_cap;
     uint32_t *srec, *sprog;
     unsigned long long wait_ns;
+    int32_t stall;           // test hook: CTA 0 skips its first arrival
 };
 
 __device__ __forceinline__ unsigned long long dyn_timer() {
@@ -552,115 +625,190 @@ __device__ __forceinline__ unsigned long long dyn_timer() {
     return t;
 }
 
-// The flag barrier described above, with CTA 0 running `step` (all its
-// threads) between the arrivals and the release.  Each CTA publishes its
-// flag with a release store after a CTA barrier, CTA 0 reads the flags with
-// acquire loads and releases the generation, which the others acquire; the
-// CTA barriers around carry that order to every thread, so plain loads
-// after the barrier see every write made before it by any CTA.  Returns
-// false when a wait ran out (the status word then says so).
+// The grid barrier described above.  Each CTA adds one to the arrival
+// counter bar[0] with a release reduction after a CTA barrier, so barrier
+// `epoch` (1, 2, ...) is complete once the counter reaches epoch * grid; an
+// acquire load that reads that value orders every CTA's writes before it.
+// grid_sync: every CTA waits on the counter itself.  grid_sync_step: CTA 0
+// waits, reads the status word, runs `step` (all its threads) and
+// publishes the generation bar[1] = epoch (bit 30 set when the status word
+// was not zero once every CTA had arrived), which the other CTAs wait for;
+// all return false on a set status so that every CTA takes the same
+// branch.  Both return false when a wait ran out (the status word then
+// says so).
 __device__ __forceinline__ void st_release(int32_t *p, int32_t v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add(int32_t *p, int32_t v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int32_t ld_acquire(const int32_t *p) {
     int32_t v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ int32_t ld_relaxed(const int32_t *p) {
+    int32_t v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+constexpr int32_t kGenError = 1 << 30;
 
-template <typename Step>
-__device__ bool flag_sync(int32_t *flags, int32_t *gen, int32_t epoch, int32_t *status,
-                          unsigned long long lim, Step step) {
-    __shared__ int ok_s;
-    __syncthreads();
-    if (blockIdx.x != 0) {
-        if (threadIdx.x == 0) {
-            st_release(&flags[blockIdx.x], epoch);
-            int ok = 1;
-            const unsigned long long t0 = dyn_timer();
-            while (ld_acquire(gen) < epoch) {
-                if (dyn_timer() - t0 > lim) {
-                    flag(status, kDevTimeout);
-                    ok = 0;
-                    break;
-                }
-            }
-            ok_s = ok;
-        }
-        __syncthreads();
-        return ok_s != 0;
-    }
-    if (threadIdx.x < 32) {
-        int ok = 1;
-        const unsigned long long t0 = dyn_timer();
-        for (int i = 1 + (int)threadIdx.x; ok && i < (int)gridDim.x; i += 32) {
-            while (ld_acquire(flags + i) < epoch) {
-                if (dyn_timer() - t0 > lim) {
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        ok = __all_sync(0xffffffffu, ok);
-        if (threadIdx.x == 0) {
-            if (!ok) flag(status, kDevTimeout);
-            ok_s = ok;
-        }
-    }
-    __syncthreads();
-    if (!ok_s) return false;
-    step();
-    __syncthreads();
-    if (threadIdx.x == 0) st_release(gen, epoch);
+// Thread 0: waits until *word (masked) reaches `target`; false on expiry.
+__device__ __forceinline__ bool wait_at_least(const int32_t *word, int32_t target, int32_t mask,
+                                              unsigned long long lim, int32_t *seen) {
+    const unsigned long long t0 = dyn_timer();
+    int32_t v;
+    while (((v = ld_acquire(word)) & mask) < target)
+        if (dyn_timer() - t0 > lim) return false;
+    *seen = v;
     return true;
 }
 
-struct NoStep {
-    __device__ void operator()() const {}
-};
+__device__ bool grid_sync(int32_t *bar, int32_t epoch, int32_t *status, unsigned long long lim,
+                          bool arrive = true) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (arrive) red_release_add(bar, 1);
+        int32_t v;
+        const bool ok = wait_at_least(bar, epoch * (int32_t)gridDim.x, 0x7fffffff, lim, &v);
+        if (!ok) flag(status, kDevTimeout);
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+template <typename Step>
+__device__ bool grid_sync_step(int32_t *bar, int32_t epoch, int32_t *status,
+                               unsigned long long lim, Step step) {
+    __shared__ int ok_s, err_s;
+    __syncthreads();
+    int32_t st = 0;   // CTA 0, thread 0: the status word once every CTA arrived
+    if (threadIdx.x == 0) {
+        red_release_add(bar, 1);
+        int32_t v = 0;
+        bool ok;
+        if (blockIdx.x == 0) {
+            ok = wait_at_least(bar, epoch * (int32_t)gridDim.x, 0x7fffffff, lim, &v);
+            // ordered after the acquire above; read now, used after the step
+            st = ld_relaxed(status);
+        } else {
+            ok = wait_at_least(bar + 1, epoch, kGenError - 1, lim, &v);
+            err_s = (v & kGenError) != 0;
+        }
+        if (!ok) flag(status, kDevTimeout);
+        ok_s = ok;
+    }
+    __syncthreads();
+    if (!ok_s) return false;
+    if (blockIdx.x != 0) return err_s == 0;
+    step();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int32_t err = st != 0;
+        st_release(bar + 1, epoch | (err ? kGenError : 0));
+        err_s = err;
+    }
+    __syncthreads();
+    return err_s == 0;
+}
 
 // CTA 0 after the bitmap is set: the exclusive prefix of the bitmap words'
 // popcounts in row-major order (wpre), hence row_ptr[r] = wpre[r * kw] and
 // the block count (1024 threads, each a contiguous run of whole 16-byte
 // vectors of words; the bitmap and wpre are 256-byte aligned allocations).
+// Runs of up to kScanKeep words stay in registers between the count and
+// the prefix; longer runs read the bitmap twice.
+constexpr int kScanKeep = 16;
+
+__device__ __forceinline__ void scan_bits_put(const DynFusedArgs &a, int64_t i, int32_t run,
+                                              int64_t &nbnd, int32_t &r) {
+    if (i == nbnd) {   // first word of block row r
+        a.row_ptr[r] = run;
+        ++r;
+        nbnd += a.kw;
+    }
+}
+
 __device__ void scan_bits(const DynFusedArgs &a) {
     const int64_t W = (int64_t)a.mb * a.kw;
     int64_t q = (W + blockDim.x - 1) / blockDim.x;
     q = (q + 3) & ~(int64_t)3;                           // whole uint4 per thread
     const int64_t lo = min(W, (int64_t)threadIdx.x * q), hi = min(W, lo + q);
+    const bool keep = q <= kScanKeep;
+    uint32_t w[kScanKeep];
     int64_t local = 0;
-    for (int64_t i = lo; i < hi; i += 4) {
-        if (i + 4 <= hi) {
-            const uint4 v = __ldcg((const uint4 *)(a.bits + i));
-            local += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
-        } else {
-            for (int64_t j = i; j < hi; ++j) local += __popc(__ldcg(a.bits + j));
+    if (keep) {
+#pragma unroll
+        for (int u = 0; u < kScanKeep; u += 4) {
+            const int64_t i = lo + u;
+            if (i + 4 <= hi) {
+                const uint4 v = __ldcg((const uint4 *)(a.bits + i));
+                w[u] = v.x;
+                w[u + 1] = v.y;
+                w[u + 2] = v.z;
+                w[u + 3] = v.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) w[u + j] = i + j < hi ? __ldcg(a.bits + i + j) : 0u;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kScanKeep; ++u) local += __popc(w[u]);
+    } else {
+        for (int64_t i = lo; i < hi; i += 4) {
+            if (i + 4 <= hi) {
+                const uint4 v = __ldcg((const uint4 *)(a.bits + i));
+                local += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+            } else {
+                for (int64_t j = i; j < hi; ++j) local += __popc(__ldcg(a.bits + j));
+            }
         }
     }
     int64_t total;
     int64_t run = block_scan(local, &total);
-    for (int64_t i = lo; i < hi; i += 4) {
-        if (i + 4 <= hi) {
-            const uint4 v = __ldcg((const uint4 *)(a.bits + i));
-            int4 o;
-            o.x = (int32_t)run;
-            run += __popc(v.x);
-            o.y = (int32_t)run;
-            run += __popc(v.y);
-            o.z = (int32_t)run;
-            run += __popc(v.z);
-            o.w = (int32_t)run;
-            run += __popc(v.w);
-            *(int4 *)(a.wpre + i) = o;
-        } else {
-            for (int64_t j = i; j < hi; ++j) {
-                a.wpre[j] = (int32_t)run;
-                run += __popc(__ldcg(a.bits + j));
+    // the first block row starting in [lo, hi) and its first word
+    int32_t r = (int32_t)((lo + a.kw - 1) / a.kw);
+    int64_t nbnd = (int64_t)r * a.kw;
+    if (keep) {
+#pragma unroll
+        for (int u = 0; u < kScanKeep; u += 4) {
+            const int64_t i = lo + u;
+            if (i + 4 <= hi) {
+                int4 o;
+                o.x = (int32_t)run;
+                scan_bits_put(a, i, o.x, nbnd, r);
+                run += __popc(w[u]);
+                o.y = (int32_t)run;
+                scan_bits_put(a, i + 1, o.y, nbnd, r);
+                run += __popc(w[u + 1]);
+                o.z = (int32_t)run;
+                scan_bits_put(a, i + 2, o.z, nbnd, r);
+                run += __popc(w[u + 2]);
+                o.w = (int32_t)run;
+                scan_bits_put(a, i + 3, o.w, nbnd, r);
+                run += __popc(w[u + 3]);
+                *(int4 *)(a.wpre + i) = o;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (i + j < hi) {
+                        a.wpre[i + j] = (int32_t)run;
+                        scan_bits_put(a, i + j, (int32_t)run, nbnd, r);
+                        run += __popc(w[u + j]);
+                    }
+                }
             }
         }
+    } else {
+        for (int64_t i = lo; i < hi; ++i) {
+            a.wpre[i] = (int32_t)run;
+            scan_bits_put(a, i, (int32_t)run, nbnd, r);
+            run += __popc(__ldcg(a.bits + i));
+        }
     }
-    __syncthreads();
-    for (int32_t r = threadIdx.x; r < a.mb; r += blockDim.x) a.row_ptr[r] = a.wpre[(int64_t)r * a.kw];
     if (threadIdx.x == 0) {
         a.row_ptr[a.mb] = (int32_t)total;
         a.counts[kCntNnzb] = (int32_t)total;
@@ -669,8 +817,8 @@ __device__ void scan_bits(const DynFusedArgs &a) {
 
 // The column masks of group g from the bitmap (bit r of colmask[c]: tile
 // row r of the group holds a block in tile column c), into shared memory.
-__device__ void group_colmask_bits(const DynFusedArgs &a, int g, uint32_t *colmask) {
-    const int32_t t0 = a.grp_row0[g], nrows = a.grp_rows[g];
+__device__ void group_colmask_bits(const DynFusedArgs &a, int32_t t0, int32_t nrows,
+                                   uint32_t *colmask) {
     const uint32_t tmask = a.T >= 32 ? 0xffffffffu : ((1u << a.T) - 1u);
     const int32_t nb = nrows * a.T;                       // block rows of the group
     const uint32_t *base = a.bits + (int64_t)t0 * a.T * a.kw;
@@ -686,33 +834,63 @@ __device__ void group_colmask_bits(const DynFusedArgs &a, int g, uint32_t *colma
     __syncthreads();
 }
 
-// Packs the blocks of CSR slots [s0, s1), a warp per block: their user
-// index, slot and offset from `pk` (shared memory) when given, else read
-// through perm / blk_slot / blk_off.
-__device__ void pack_group(const DynFusedArgs &a, int32_t s0, int32_t s1, const int32_t *pk) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Shared memory of the fused launch: colmask[kt], slot_of[kt], the group's
+// row pointers (at most 16 * 16 + 1), kFusedPk (user index, slot, offset)
+// triples and, from a 16-byte boundary, the packing warps' staging pieces.
+constexpr int kFusedPk = 4096;
+constexpr int kStageWarps = 12;  // warps cutting stage records in step D
+constexpr int kPackDepth = 8;    // blocks in flight per packing warp
+constexpr int kFusedRp = 16 * 16 + 1;
+__host__ __device__ inline size_t fused_pack_buf_offset(int32_t kt) {
+    return (sizeof(int32_t) * (2 * (size_t)kt + kFusedRp + 3 * (size_t)kFusedPk) + 15) / 16 * 16;
+}
+inline size_t fused_smem(int32_t kt) {
+    return fused_pack_buf_offset(kt) + (size_t)(32 - kStageWarps) * kPackDepth * 512;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+// Packs the blocks of CSR slots [s0, s1), a warp per block, on warps
+// [w0, w0 + nw) of the CTA: their user index, slot and offset from `pk`
+// (shared memory) when given, else read through perm / blk_slot / blk_off.
+// `buf`: kPackDepth * 32 16-byte pieces of shared memory per packing warp.
+__device__ void pack_group(const DynFusedArgs &a, int32_t s0, int32_t s1, const int32_t *pk,
+                           int w0, int nw, uint4 *buf) {
+    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - w0;
     int32_t q0 = s0 + warp;
     if (pk && !a.w8 && a.b == 16 && a.seg == 8 && !a.tr) {
-        // 16 x 16 blocks, 16-byte pieces: four blocks per round, every load
-        // issued before any store (the block's 512 B is one piece per lane,
-        // row lane / 2, half lane % 2, placed as pack_block_warp places it)
+        // 16 x 16 blocks, 16-byte pieces: kPackDepth blocks per round copied
+        // into shared memory (cp.async, all in flight together), then
+        // stored (the block's 512 B is one piece per lane, row lane / 2,
+        // half lane % 2, placed as pack_block_warp places it)
         const uint4 *v = (const uint4 *)a.values;
         uint16_t *o = (uint16_t *)a.packed;
+        uint4 *wb = buf + (size_t)warp * kPackDepth * 32 + lane;
         const int i = lane >> 1, seg = lane & 1;
         const int toff = (i >> 3) * 128 + seg * 64 + (i & 7) * 8;
-        for (; q0 + 3 * nw < s1; q0 += 4 * nw) {
-            uint4 d[4];
-            int32_t sl[4];
+        for (; q0 < s1; q0 += kPackDepth * nw) {
+            int32_t sl[kPackDepth];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kPackDepth; ++u) {
                 const int32_t qq = q0 + u * nw - s0;
-                d[u] = v[(int64_t)pk[3 * qq] * 32 + lane];
-                sl[u] = pk[3 * qq + 1];
+                if (q0 + u * nw < s1) {
+                    cp_async16(wb + u * 32, v + (int64_t)pk[3 * qq] * 32 + lane);
+                    sl[u] = pk[3 * qq + 1];
+                }
             }
+            cp_async_wait_all();   // this lane's pieces
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                *(uint4 *)(o + (int64_t)sl[u] * (kTile * kTile) + toff) = d[u];
+            for (int u = 0; u < kPackDepth; ++u)
+                if (q0 + u * nw < s1)
+                    *(uint4 *)(o + (int64_t)sl[u] * (kTile * kTile) + toff) = wb[u * 32];
         }
+        return;
     }
     for (int32_t q = q0; q < s1; q += nw) {
         int64_t p;
@@ -745,20 +923,57 @@ __device__ void pack_group(const DynFusedArgs &a, int32_t s0, int32_t s1, const 
     }
 }
 
-// Shared memory of the fused launch: colmask[kt], slot_of[kt], the group's
-// row pointers (at most 16 * 16 + 1) and kFusedPk (user index, slot,
-// offset) triples.
-constexpr int kFusedPk = 4096;
-constexpr int kFusedRp = 16 * 16 + 1;
-inline size_t fused_smem(int32_t kt) {
-    return sizeof(int32_t) * (2 * (size_t)kt + kFusedRp + 3 * (size_t)kFusedPk);
+// Named barrier 1 over the first n threads of the CTA.
+__device__ __forceinline__ void sync_first(int n) {
+    asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+}
+
+// The stage records of group g's work items (the near-equal chunks of its
+// entries, as group_fill writes them), cut by warps [0, nbw) of the CTA
+// exactly as a CTA per item cuts them (32 entries per warp, the count pass,
+// a prefix of the counts, the write pass), with named barrier 1 between the
+// passes; items at or past the items' capacity are skipped.
+__device__ void build_group_stages(const DynFusedArgs &a, const GroupOff &o, int nbw,
+                                   int32_t *bcounts) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t L = o.eend - o.ebeg, nch = nchunks(L, o.C);
+    const int32_t base = L / nch, rem = L % nch;
+    int32_t e = o.ebeg;
+    for (int32_t c = 0; c < nch; ++c) {
+        const int32_t sz = base + (c < rem ? 1 : 0), e1 = e + sz;
+        if ((int64_t)o.ibeg + c < a.items_cap) {
+            const int32_t nb = (sz + 31) / 32;
+            int32_t rec = e;
+            for (int32_t b0 = 0; b0 < nb; b0 += nbw) {
+                const int32_t bi = b0 + warp;
+                const bool active = bi < nb;
+                const int32_t eb = e + 32 * bi;
+                int nst = 0;
+                if (active)
+                    nst = build_batch(eb, e1, a.ent_cap, a.tiles_cap, a.ent_col, a.ent_tbeg,
+                                      a.ent_cover, false, false, 0, a.srec, a.sprog);
+                if (lane == 0) bcounts[warp] = nst;
+                sync_first(nbw * 32);
+                int32_t off = rec, tot = 0;
+                for (int w = 0; w < nbw; ++w) {
+                    if (w < warp) off += bcounts[w];
+                    tot += bcounts[w];
+                }
+                if (active)
+                    build_batch(eb, e1, a.ent_cap, a.tiles_cap, a.ent_col, a.ent_tbeg,
+                                a.ent_cover, bi == nb - 1, true, off, a.srec, a.sprog);
+                rec += tot;
+                sync_first(nbw * 32);
+            }
+        }
+        e = e1;
+    }
 }
 
 __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_constant__ DynFusedArgs a) {
     pdl_enter();
     extern __shared__ uint32_t dsm[];   // see fused_smem
     __shared__ int32_t bcounts[32];
-    int32_t *flags = a.bar, *gen = a.bar + kFusedMaxCtas;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t gs = (int64_t)gridDim.x * blockDim.x;
     const unsigned long long lim = a.wait_ns;
@@ -766,10 +981,20 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
     int32_t *slot_of = (int32_t *)(dsm + a.kt);
     int32_t *rp_s = slot_of + a.kt;
     int32_t *pk = rp_s + kFusedRp;
+    uint4 *pack_buf = (uint4 *)((uint8_t *)dsm + fused_pack_buf_offset(a.kt));
+    // the first group's rows (plan constants), read while A runs
+    __shared__ int32_t row0_s, rows_s;
+    __shared__ GroupOff go_s;
+    if (threadIdx.x == 0 && (int)blockIdx.x < a.G) {
+        row0_s = a.grp_row0[blockIdx.x];
+        rows_s = a.grp_rows[blockIdx.x];
+    }
     // A.
     for (int64_t i = gt; i < (int64_t)a.mb * a.kw; i += gs) a.bits[i] = 0;
+    if (gt < kCntCount) a.counts[gt] = 0;
     if (gt == 0) *a.status = 0;
-    if (!flag_sync(flags, gen, 1, a.status, lim, NoStep())) return;
+    // (with the test hook on, CTA 0 does not arrive: every wait runs out)
+    if (!grid_sync(a.bar, 1, a.status, lim, !(a.stall && blockIdx.x == 0))) return;
     // B.
     const int64_t raw = *a.d_nnzb;
     if (gt == 0 && (raw < 0 || raw > a.cap)) flag(a.status, kDevCapacity);
@@ -783,8 +1008,8 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
         const uint32_t bit = 1u << (c & 31);
         if (atomicOr(&a.bits[(int64_t)r * a.kw + (c >> 5)], bit) & bit) flag(a.status, kDevPattern);
     }
-    if (!flag_sync(flags, gen, 2, a.status, lim, [&] { scan_bits(a); })) return;
-    if (*(volatile int32_t *)a.status != 0) return;   // every CTA sees the same word here
+    // a rejected pattern ends the launch here, in every CTA
+    if (!grid_sync_step(a.bar, 2, a.status, lim, [&] { scan_bits(a); })) return;
     // C.
     for (int64_t p = gt; p < n; p += gs) {
         const int32_t r = a.brow[p], c = a.bcol[p];
@@ -794,24 +1019,38 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
         a.perm[pos] = (int32_t)p;
     }
     for (int g = blockIdx.x; g < a.G; g += gridDim.x) {
-        group_colmask_bits(a, g, colmask);
+        const bool first = g == (int)blockIdx.x;
+        group_colmask_bits(a, first ? row0_s : a.grp_row0[g], first ? rows_s : a.grp_rows[g],
+                           colmask);
         for (int32_t c = threadIdx.x; c < a.kt; c += blockDim.x)
             a.gmask[(int64_t)g * a.kt + c] = colmask[c];
         group_counts(g, a.kt, colmask, a.grp_cnt);
     }
-    if (!flag_sync(flags, gen, 3, a.status, lim, [&] {
+    if (!grid_sync_step(a.bar, 3, a.status, lim, [&] {
             group_scan(a.G, a.grp_rows, a.grp_cnt, a.grp_ebeg, a.grp_sbeg, a.grp_ibeg, a.grp_wbeg,
                        a.grp_wrow, a.grp_rbeg, a.ent_tbeg, a.counts);
         }))
         return;
-    // D.
+    // D.  Per group: the fill, then the group's stage records on warps
+    // [0, kStageWarps) beside the value packing on the others.
     const int64_t tile_bytes = a.w8 ? kTile * kTile : kTile * kTile * 2;
+    const int warp = threadIdx.x >> 5;
     for (int g = blockIdx.x; g < a.G; g += gridDim.x) {
+        const bool first = g == (int)blockIdx.x;
+        const int32_t t0 = first ? row0_s : a.grp_row0[g], nrows = first ? rows_s : a.grp_rows[g];
+        if (threadIdx.x == 0)
+            go_s = load_group_off(g, a.grp_row0, a.grp_rows, a.grp_ebeg, a.grp_sbeg, a.grp_ibeg,
+                                  a.grp_wbeg, a.grp_wrow, a.grp_rbeg, a.counts, a.G);
+        for (int32_t c = threadIdx.x; c < a.kt; c += blockDim.x)
+            colmask[c] = a.gmask[(int64_t)g * a.kt + c];
+        for (int32_t i = threadIdx.x; i <= nrows * a.T; i += blockDim.x)
+            rp_s[i] = a.row_ptr[t0 * a.T + i];
+        __syncthreads();
+        const GroupOff go = go_s;
         if (a.b < 16) {
             // tiles hold several blocks: clear the group's tiles (and E4M3
             // scales); 16 x 16 blocks fill their tile and every scale
-            const int64_t sb = a.grp_sbeg[g];
-            const int64_t se = g + 1 < a.G ? a.grp_sbeg[g + 1] : (int64_t)a.counts[kCntSlots];
+            const int64_t sb = go.sbeg, se = go.send;
             uint4 *t = (uint4 *)((uint8_t *)a.packed + sb * tile_bytes);
             const int64_t nv = (se - sb) * tile_bytes / 16;
             for (int64_t i = threadIdx.x; i < nv; i += blockDim.x) t[i] = make_uint4(0, 0, 0, 0);
@@ -820,29 +1059,18 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
                 for (int64_t i = threadIdx.x; i < (se - sb) * 16; i += blockDim.x) ts[i] = 0.f;
             }
         }
-        for (int32_t c = threadIdx.x; c < a.kt; c += blockDim.x)
-            colmask[c] = a.gmask[(int64_t)g * a.kt + c];
-        __syncthreads();
-        const int32_t t0 = a.grp_row0[g], nrows = a.grp_rows[g];
-        for (int32_t i = threadIdx.x; i <= nrows * a.T; i += blockDim.x)
-            rp_s[i] = a.row_ptr[t0 * a.T + i];
-        __syncthreads();
         const int32_t s0 = rp_s[0], s1 = rp_s[nrows * a.T];
         const bool stage = s1 - s0 <= kFusedPk;
-        group_fill(g, a.kt, a.T, a.b, a.grp_row0, a.grp_rows, a.row_ptr, a.col_idx, a.perm,
-                   a.grp_ebeg, a.grp_sbeg, a.grp_ibeg, a.grp_wbeg, a.grp_wrow, a.grp_rbeg, a.counts,
-                   colmask, slot_of, s0, s1, a.ent_col, a.ent_tbeg, a.ent_cover, a.tile_row,
-                   a.blk_slot, a.blk_off, a.items, a.ws_row0, a.red, rp_s, stage ? pk : nullptr);
-        __syncthreads();   // this CTA's block -> slot writes, and the cleared tiles
-        pack_group(a, s0, s1, stage ? pk : nullptr);
+        group_fill(g, go, a.kt, a.T, a.b, a.row_ptr, a.col_idx, a.perm, colmask, slot_of, s0, s1,
+                   a.ent_col, a.ent_tbeg, a.ent_cover, a.tile_row, a.blk_slot, a.blk_off,
+                   a.items, a.ws_row0, a.red, rp_s, stage ? pk : nullptr);
+        __syncthreads();   // this CTA's entries, block -> slot writes and cleared tiles
+        if (warp < kStageWarps)
+            build_group_stages(a, go, kStageWarps, bcounts);
+        else
+            pack_group(a, s0, s1, stage ? pk : nullptr, kStageWarps, 32 - kStageWarps,
+                       pack_buf);
         __syncthreads();
-    }
-    if (!flag_sync(flags, gen, 4, a.status, lim, NoStep())) return;
-    // E.
-    const int64_t ni = min(a.items_cap, (int64_t)max(a.counts[kCntItems], 0));
-    for (int64_t item = blockIdx.x; item < ni; item += gridDim.x) {
-        build_item_stages(a.items + item * kItemFields, a.ent_cap, a.tiles_cap, a.ent_col,
-                          a.ent_tbeg, a.ent_cover, a.srec, a.sprog, bcounts);
     }
 }
 
@@ -971,6 +1199,7 @@ cudaError_t launch_dynamic_tc_fused(spmm_plan *p, const spmm_dpattern *dp, const
     a.srec = p->d_srec;
     a.sprog = p->d_sprog;
     a.wait_ns = p->wait_ns ? p->wait_ns : 2000000000ull;
+    a.stall = p->stall;
     // the kernel's shared-memory limit is set once per device for the
     // largest k of a dynamic TC plan (k / 16 <= kDynMaxTileCols)
     const size_t smem = fused_smem(a.kt);
@@ -983,8 +1212,9 @@ cudaError_t launch_dynamic_tc_fused(spmm_plan *p, const spmm_dpattern *dp, const
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     const int grid = std::min(per_sm * std::max(p->sm_count, 1), kFusedMaxCtas);
-    e = cudaMemsetAsync(p->d_counts, 0, sizeof(int32_t) * kCntCount, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.bar, 0, sizeof(int32_t) * (kFusedMaxCtas + 1), s);
+    // the counts are cleared by the launch itself (step A); the barrier's
+    // counter and generation here
+    e = cudaMemsetAsync(d.bar, 0, sizeof(int32_t) * 2, s);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);

@@ -278,3 +278,74 @@ def test_fused_repartition_equals_launch_chain(b, dt, w8):
             vals = torch.from_numpy(c["vals"]).to(dt)
             Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X.cpu())
             assert oracle.normwise_err(outs[0], Yo, oracle.block_fro(vals), X.cpu()) <= 4e-3
+
+
+@pytest.mark.parametrize("b,m,k", [(16, 208, 640), (8, 80, 48), (4, 4096, 4096)])
+def test_fused_repartition_bitmap_edges(b, m, k):
+    """The fused launch's bitmap scan at the edges of its layout: a bitmap
+    whose word count is not a multiple of four (b = 16, 13 block rows of two
+    words; b = 8, 10 block rows of one word) and one with more than sixteen
+    words per thread (b = 4, m = k = 4096: 32768 words).  Arrays and Y equal
+    the launch chain's bit for bit; Y is within the normwise bar."""
+    n = 72
+    dt = torch.bfloat16
+    cap = max(wl.nnzb_for(m, k, b, 1 / 4), 1)
+    plans = [S.Plan(m, k, n, b, w_dtype=S.BF16, mode=S.DYNAMIC, nnzb_max=cap, dyn_chain=ch)
+             for ch in (False, True)]
+    for call in range(2):
+        c = wl.dynamic_call(call + 70 * b, m=m, k=k, n=n, b=b, d_max=1 / 4)
+        X = torch.from_numpy(c["X"]).to(dt).cuda()
+        vals = torch.from_numpy(c["vals"]).to(dt)
+        vd = torch.zeros((cap, b, b), dtype=dt)
+        vd[:len(vals)] = vals
+        vd = vd.cuda()
+        pat = _dev_pattern(c["brow"], c["bcol"], cap)
+        outs = []
+        for p in plans:
+            Y = p.run(X, values=vd, pattern=pat)
+            torch.cuda.synchronize()
+            assert p.status() == 0
+            outs.append(Y.cpu())
+        assert torch.equal(outs[0], outs[1])
+        for key in ("row_ptr", "col_idx", "perm", "items", "grp_ebeg", "ent_col", "ent_tbeg",
+                    "ent_cover", "tile_row", "blk_slot", "blk_off", "ws_row0", "red"):
+            assert np.array_equal(plans[0].array(key), plans[1].array(key)), key
+        rp, ci, pm = P.csr(m // b, c["brow"], c["bcol"])
+        assert np.array_equal(plans[0].array("row_ptr"), rp)
+        assert np.array_equal(plans[0].array("col_idx"), ci)
+        assert np.array_equal(plans[0].array("perm"), pm)
+        if m * k <= 1 << 20:
+            Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X.cpu())
+            assert oracle.normwise_err(outs[0], Yo, oracle.block_fro(vals), X.cpu()) <= 4e-3
+
+
+def test_fused_repartition_wait_times_out_and_recovers():
+    """Failure detection in the fused re-partition: with the test hook on, one
+    CTA skips its arrival at the first grid barrier; every CTA's bounded wait
+    runs out (200 us), the status word reads SPMM_ERR_TIMEOUT, the product
+    launch skips (Y keeps its contents) and the context stays usable: the
+    next call, with the default limit, is correct against the oracle."""
+    m = k = 1024
+    n = 64
+    b = 16
+    cap = wl.nnzb_for(m, k, b, 1 / 16)
+    plan = S.Plan(m, k, n, b, w_dtype=S.BF16, mode=S.DYNAMIC, nnzb_max=cap)
+    c = wl.dynamic_call(7100, m=m, k=k, n=n, b=b, d_max=1 / 16)
+    X = torch.from_numpy(c["X"]).to(torch.bfloat16)
+    vals = torch.from_numpy(c["vals"]).to(torch.bfloat16)
+    vd = torch.zeros((cap, b, b), dtype=torch.bfloat16)
+    vd[:len(vals)] = vals
+    pat = _dev_pattern(c["brow"], c["bcol"], cap)
+    plan.set_wait(200_000, stall=True)
+    Y = torch.full((m, n), 5.0, dtype=torch.bfloat16, device="cuda")
+    plan.run(X.cuda(), Y, values=vd.cuda(), pattern=pat)
+    torch.cuda.synchronize()
+    assert plan.status() == S.ERR_TIMEOUT
+    assert torch.all(Y == 5.0)
+    plan.set_wait(0, stall=False)
+    Y = plan.run(X.cuda(), values=vd.cuda(), pattern=pat)
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X)
+    assert oracle.normwise_err(Y.cpu(), Yo, oracle.block_fro(vals), X) <= 4e-3
+    _check_arrays(plan, m, k, b, c["brow"], c["bcol"])
