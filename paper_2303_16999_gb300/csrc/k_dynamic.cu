@@ -930,9 +930,9 @@ __device__ __forceinline__ void sync_first(int n) {
 
 // The stage records of group g's work items (the near-equal chunks of its
 // entries, as group_fill writes them), cut by warps [0, nbw) of the CTA
-// exactly as a CTA per item cuts them (32 entries per warp, the count pass,
-// a prefix of the counts, the write pass), with named barrier 1 between the
-// passes; items at or past the items' capacity are skipped.
+// exactly as a CTA per item cuts them (32 entries per warp, the cut, a
+// prefix of the stage counts, the write pass), with named barrier 1 between
+// the passes; items at or past the items' capacity are skipped.
 __device__ void build_group_stages(const DynFusedArgs &a, const GroupOff &o, int nbw,
                                    int32_t *bcounts) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -948,20 +948,18 @@ __device__ void build_group_stages(const DynFusedArgs &a, const GroupOff &o, int
                 const int32_t bi = b0 + warp;
                 const bool active = bi < nb;
                 const int32_t eb = e + 32 * bi;
-                int nst = 0;
+                BatchCut cut;
                 if (active)
-                    nst = build_batch(eb, e1, a.ent_cap, a.tiles_cap, a.ent_col, a.ent_tbeg,
-                                      a.ent_cover, false, false, 0, a.srec, a.sprog);
-                if (lane == 0) bcounts[warp] = nst;
+                    cut = cut_batch(eb, e1, a.ent_cap, a.tiles_cap, a.ent_col, a.ent_tbeg,
+                                    a.ent_cover);
+                if (lane == 0) bcounts[warp] = active ? cut.nst : 0;
                 sync_first(nbw * 32);
                 int32_t off = rec, tot = 0;
                 for (int w = 0; w < nbw; ++w) {
                     if (w < warp) off += bcounts[w];
                     tot += bcounts[w];
                 }
-                if (active)
-                    build_batch(eb, e1, a.ent_cap, a.tiles_cap, a.ent_col, a.ent_tbeg,
-                                a.ent_cover, bi == nb - 1, true, off, a.srec, a.sprog);
+                if (active) write_batch(cut, bi == nb - 1, off, a.srec, a.sprog);
                 rec += tot;
                 sync_first(nbw * 32);
             }

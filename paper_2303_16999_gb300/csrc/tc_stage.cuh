@@ -38,23 +38,35 @@ constexpr int kBuildWarps = 16;         // warps of a stage_build_kernel CTA
 // one list per row half (an interval across row 8 is cut there).  Dynamic
 // plans read the item count and the status word on the device (a rejected
 // pattern builds nothing).
-// One batch of entries: cuts its stages; with `write`, stores their records
-// starting at record index `rec`.  Returns the number of stages.
-__device__ int build_batch(int32_t eb, int32_t e1, int ent_cap, int tiles_cap,
-                           const int32_t *ent_col, const int32_t *ent_tbeg,
-                           const int32_t *ent_cover, bool last_batch, bool write,
-                           int32_t rec, uint32_t *srec, uint32_t *sprog) {
+
+// One batch of entries, cut: the per-lane state (lane i = entry eb + i)
+// that the write pass needs.  The cut itself is the one serial part: from
+// stage start j, the stage takes the longest run of entries that fits.
+struct BatchCut {
+    int32_t mcol, mtb;      // entry's tile column and first tile
+    uint32_t mcov;          // covered rows | interval starts << 16
+    int S, L, H;            // inclusive prefixes: tiles, MMAs of each half
+    int nlo, nhi, mslots;   // this entry's MMAs per half and tiles
+    int my_j, my_stage;     // start lane and index of this entry's stage
+    int kst;                // lane k: start lane of stage k
+    int cnt, nst;           // entries in the batch, stages
+};
+
+__device__ BatchCut cut_batch(int32_t eb, int32_t e1, int ent_cap, int tiles_cap,
+                              const int32_t *ent_col, const int32_t *ent_tbeg,
+                              const int32_t *ent_cover) {
     const int lane = threadIdx.x & 31;
+    BatchCut c;
     const int32_t e = eb + lane;
     const bool valid = e < e1;
-    const int32_t mcol = valid ? ent_col[e] : 0;
-    const int32_t mtb = valid ? ent_tbeg[e] : 0;
-    const uint32_t mcov = valid ? (uint32_t)ent_cover[e] : 0u;
-    const uint32_t cov = mcov & 0xFFFFu;
+    c.mcol = valid ? ent_col[e] : 0;
+    c.mtb = valid ? ent_tbeg[e] : 0;
+    c.mcov = valid ? (uint32_t)ent_cover[e] : 0u;
+    const uint32_t cov = c.mcov & 0xFFFFu;
     // this entry's MMAs per row half: intervals below / above row 8, an
     // interval across it counting in both
     int nlo = 0, nhi = 0;
-    for (uint32_t st = mcov >> 16; st; st &= st - 1) {
+    for (uint32_t st = c.mcov >> 16; st; st &= st - 1) {
         const uint32_t r0 = __ffs(st) - 1;
         const uint32_t rest = st & (st - 1);
         const uint32_t next = rest ? (uint32_t)(__ffs(rest) - 1) : 16u;
@@ -63,9 +75,11 @@ __device__ int build_batch(int32_t eb, int32_t e1, int ent_cap, int tiles_cap,
         nlo += r0 < 8;
         nhi += r0 + len > 8;
     }
-    const int mslots = __popc(cov);
+    c.nlo = nlo;
+    c.nhi = nhi;
+    c.mslots = __popc(cov);
     // inclusive prefix sums over the batch: tiles, MMAs of each half
-    int S = mslots, L = nlo, H = nhi;
+    int S = c.mslots, L = nlo, H = nhi;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int s2 = __shfl_up_sync(0xffffffffu, S, o);
@@ -77,67 +91,108 @@ __device__ int build_batch(int32_t eb, int32_t e1, int ent_cap, int tiles_cap,
             H += h2;
         }
     }
-    const int cnt = min(32, e1 - eb);
+    c.S = S;
+    c.L = L;
+    c.H = H;
+    c.cnt = min(32, e1 - eb);
+    c.my_j = 0;
+    c.my_stage = 0;
+    c.kst = 0;
     int nst = 0;
-    for (int j = 0; j < cnt; ++nst) {
+    for (int j = 0; j < c.cnt; ++nst) {
         // sums are monotone: the fitting lanes are contiguous from j
         const int Sb = j ? __shfl_sync(0xffffffffu, S, j - 1) : 0;
         const int Lb = j ? __shfl_sync(0xffffffffu, L, j - 1) : 0;
         const int Hb = j ? __shfl_sync(0xffffffffu, H, j - 1) : 0;
-        const bool fits = lane >= j && lane < j + ent_cap && lane < cnt && S - Sb <= tiles_cap &&
-                          L - Lb <= kMmaStage && H - Hb <= kMmaStage;
+        const bool fits = lane >= j && lane < j + ent_cap && lane < c.cnt &&
+                          S - Sb <= tiles_cap && L - Lb <= kMmaStage && H - Hb <= kMmaStage;
         const int nent = __popc(__ballot_sync(0xffffffffu, fits));
-        if (write) {
-            const int slots = __shfl_sync(0xffffffffu, S, j + nent - 1) - Sb;
-            const int mlo = __shfl_sync(0xffffffffu, L, j + nent - 1) - Lb;
-            const int mhi = __shfl_sync(0xffffffffu, H, j + nent - 1) - Hb;
-            const int32_t stb = __shfl_sync(0xffffffffu, mtb, j);
-            // record word 3 + i holds the X column of the stage's entry i
-            const int32_t xc = __shfl_sync(0xffffffffu, mcol, min(j + max(lane - 3, 0), 31));
-            const bool last = last_batch && j + nent == cnt;
-            const int32_t r = rec + nst;
-            // 2 to 4 entries on consecutive tile columns: one X box serves the stage
-            const int32_t pcol = __shfl_up_sync(0xffffffffu, mcol, 1);
-            const bool consec = __all_sync(0xffffffffu, !(lane > j && lane < j + nent) ||
-                                                            mcol == pcol + 1);
-            const bool joint = consec && nent >= 2 && nent <= kJointSlabs;
-            if (lane >= j && lane < j + nent) {
-                uint32_t klo = (uint32_t)(L - nlo - Lb), khi = (uint32_t)(H - nhi - Hb);
-                uint32_t toff = (uint32_t)(S - mslots - Sb);
-                const uint32_t slab = (uint32_t)(lane - j);
-                uint32_t *pr = sprog + (int64_t)r * 2 * kMmaStage;
-                for (uint32_t st = mcov >> 16; st; st &= st - 1) {
-                    const uint32_t r0 = __ffs(st) - 1;
-                    const uint32_t rest = st & (st - 1);
-                    const uint32_t next = rest ? (uint32_t)(__ffs(rest) - 1) : 16u;
-                    uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;
-                    len = len < next - r0 ? len : next - r0;
-                    if (r0 < 8) {
-                        const uint32_t l0 = r0 + len > 8 ? 8 - r0 : len;
-                        pr[2 * klo++] = slab | toff << 4 | r0 << 12 | l0 << 16;
-                    }
-                    if (r0 + len > 8) {
-                        const uint32_t a = r0 < 8 ? 8u : r0;   // first row at or above 8
-                        pr[2 * khi++ + 1] =
-                            slab | (toff + (a - r0)) << 4 | a << 12 | (r0 + len - a) << 16;
-                    }
-                    toff += len;
-                }
-            }
-            if (lane < kRecWords) {
-                uint32_t v = 0;
-                if (lane == 0)
-                    v = (uint32_t)mlo | (uint32_t)mhi << 6 | (uint32_t)nent << 12 |
-                        (joint ? kJointBit : 0u) | (last ? 0x80000000u : 0u);
-                else if (lane == 1) v = (uint32_t)slots;
-                else if (lane == 2) v = (uint32_t)stb;
-                else if (lane - 3 < nent) v = (uint32_t)xc;
-                srec[(int64_t)r * kRecWords + lane] = v;
-            }
+        if (lane >= j && lane < j + nent) {
+            c.my_j = j;
+            c.my_stage = nst;
         }
+        if (lane == nst) c.kst = j;
         j += nent;
     }
-    return nst;
+    c.nst = nst;
+    return c;
+}
+
+// The write pass of a cut batch, every stage at once: stores its records
+// from record index `rec`, expanding every entry's row intervals (runs of
+// covered rows cut at interval starts) into MMA words: slab | first W tile
+// in the stage << 4 | first tile row << 12 | rows << 16, one list per row
+// half (an interval across row 8 is cut there).
+__device__ void write_batch(const BatchCut &c, bool last_batch, int32_t rec, uint32_t *srec,
+                            uint32_t *sprog) {
+    const int lane = threadIdx.x & 31;
+    const bool in = lane < c.cnt;
+    // the prefixes before this entry's stage
+    const int src = in && c.my_j > 0 ? c.my_j - 1 : 0;
+    const int Sp = __shfl_sync(0xffffffffu, c.S, src);
+    const int Lp = __shfl_sync(0xffffffffu, c.L, src);
+    const int Hp = __shfl_sync(0xffffffffu, c.H, src);
+    if (in) {
+        const bool first = c.my_j == 0;
+        uint32_t klo = (uint32_t)(c.L - c.nlo - (first ? 0 : Lp));
+        uint32_t khi = (uint32_t)(c.H - c.nhi - (first ? 0 : Hp));
+        uint32_t toff = (uint32_t)(c.S - c.mslots - (first ? 0 : Sp));
+        const uint32_t slab = (uint32_t)(lane - c.my_j);
+        const uint32_t cov = c.mcov & 0xFFFFu;
+        uint32_t *pr = sprog + (int64_t)(rec + c.my_stage) * 2 * kMmaStage;
+        for (uint32_t st = c.mcov >> 16; st; st &= st - 1) {
+            const uint32_t r0 = __ffs(st) - 1;
+            const uint32_t rest = st & (st - 1);
+            const uint32_t next = rest ? (uint32_t)(__ffs(rest) - 1) : 16u;
+            uint32_t len = (uint32_t)__ffs(~(cov >> r0)) - 1;
+            len = len < next - r0 ? len : next - r0;
+            if (r0 < 8) {
+                const uint32_t l0 = r0 + len > 8 ? 8 - r0 : len;
+                pr[2 * klo++] = slab | toff << 4 | r0 << 12 | l0 << 16;
+            }
+            if (r0 + len > 8) {
+                const uint32_t a = r0 < 8 ? 8u : r0;   // first row at or above 8
+                pr[2 * khi++ + 1] = slab | (toff + (a - r0)) << 4 | a << 12 | (r0 + len - a) << 16;
+            }
+            toff += len;
+        }
+    }
+    // bit i: entry i is not one tile column past entry i - 1
+    const int32_t pcol = __shfl_up_sync(0xffffffffu, c.mcol, 1);
+    const uint32_t brk = __ballot_sync(0xffffffffu, lane > 0 && c.mcol != pcol + 1);
+    // records, kRecWords words per stage: word 0 the MMA counts, entry
+    // count and flags, 1 the stage's tiles, 2 its first tile, 3 + i the X
+    // column of its entry i
+    for (int w0 = 0; w0 < c.nst * kRecWords; w0 += 32) {
+        const int w = w0 + lane;
+        const int k = min(w / kRecWords, c.nst - 1), i = w % kRecWords;
+        const int j = __shfl_sync(0xffffffffu, c.kst, k);
+        const int jn0 = __shfl_sync(0xffffffffu, c.kst, min(k + 1, 31));
+        const int jn = k + 1 < c.nst ? jn0 : c.cnt;
+        const int nent = jn - j;
+        const int Se = __shfl_sync(0xffffffffu, c.S, jn - 1);
+        const int Le = __shfl_sync(0xffffffffu, c.L, jn - 1);
+        const int He = __shfl_sync(0xffffffffu, c.H, jn - 1);
+        const int Sb0 = __shfl_sync(0xffffffffu, c.S, max(j - 1, 0));
+        const int Lb0 = __shfl_sync(0xffffffffu, c.L, max(j - 1, 0));
+        const int Hb0 = __shfl_sync(0xffffffffu, c.H, max(j - 1, 0));
+        const int32_t stb = __shfl_sync(0xffffffffu, c.mtb, j);
+        const int32_t xc = __shfl_sync(0xffffffffu, c.mcol, min(j + max(i - 3, 0), 31));
+        if (w < c.nst * kRecWords) {
+            const int Sb = j ? Sb0 : 0, Lb = j ? Lb0 : 0, Hb = j ? Hb0 : 0;
+            const bool joint = nent >= 2 && nent <= kJointSlabs &&
+                               ((brk >> (j + 1)) & ((1u << (nent - 1)) - 1u)) == 0;
+            const bool last = last_batch && jn == c.cnt;
+            uint32_t v = 0;
+            if (i == 0)
+                v = (uint32_t)(Le - Lb) | (uint32_t)(He - Hb) << 6 | (uint32_t)nent << 12 |
+                    (joint ? kJointBit : 0u) | (last ? 0x80000000u : 0u);
+            else if (i == 1) v = (uint32_t)(Se - Sb);
+            else if (i == 2) v = (uint32_t)stb;
+            else if (i - 3 < nent) v = (uint32_t)xc;
+            srec[(int64_t)(rec + k) * kRecWords + i] = v;
+        }
+    }
 }
 
 // The stage records of one work item (fields as in the items array), cut by
@@ -158,20 +213,16 @@ __device__ void build_item_stages(const int32_t *it, int ent_cap, int tiles_cap,
         const int32_t b = b0 + warp;
         const bool active = b < nb;
         const int32_t eb = e0 + 32 * b;
-        int nst = 0;
-        if (active)
-            nst = build_batch(eb, e1, ent_cap, tiles_cap, ent_col, ent_tbeg, ent_cover, false,
-                              false, 0, srec, sprog);
-        if (lane == 0) counts[warp] = nst;
+        BatchCut cut;
+        if (active) cut = cut_batch(eb, e1, ent_cap, tiles_cap, ent_col, ent_tbeg, ent_cover);
+        if (lane == 0) counts[warp] = active ? cut.nst : 0;
         __syncthreads();
         int32_t off = base, tot = 0;
         for (int w = 0; w < nwarps; ++w) {
             if (w < warp) off += counts[w];
             tot += counts[w];
         }
-        if (active)
-            build_batch(eb, e1, ent_cap, tiles_cap, ent_col, ent_tbeg, ent_cover, b == nb - 1,
-                        true, off, srec, sprog);
+        if (active) write_batch(cut, b == nb - 1, off, srec, sprog);
         base += tot;
         __syncthreads();
     }
