@@ -279,10 +279,20 @@ __global__ void dyn_sort_rows(int32_t mb, const int32_t *row_ptr, const int32_t 
     }
 }
 
+// Group g's offsets from the group scan.
+struct GroupOff {
+    int32_t row0, rows;          // first tile row, tile rows
+    int32_t ebeg, eend;          // entries [ebeg, eend)
+    int32_t sbeg, send;          // slots [sbeg, send)
+    int32_t ibeg, wbeg, rbeg;    // first item, workspace slot, reduction
+    int64_t wrow, C;             // first workspace row, chunk size
+};
+
 __device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *grp_cnt,
                            int32_t *grp_ebeg, int32_t *grp_sbeg, int32_t *grp_ibeg,
                            int32_t *grp_wbeg, int64_t *grp_wrow, int32_t *grp_rbeg,
-                           int32_t *ent_tbeg, int32_t *counts);
+                           int32_t *ent_tbeg, int32_t *counts, bool write_global = true,
+                           GroupOff *own = nullptr, const int32_t *grp_row0 = nullptr);
 
 // The column masks of group g in shared memory (colmask[kt], whole CTA):
 // bit r of colmask[c] is set when tile row r of the group holds a block in
@@ -353,15 +363,20 @@ __global__ void __launch_bounds__(1024) dyn_group_count_scan(
 }
 
 // 4b. group offsets and the chunk size C = max(16, ceil(5E / 4G)); one block
-// of 1024 threads (the group counts' last).
+// of 1024 threads (the group counts' last).  write_global: store the
+// offsets and counts (else only `own`); own: the offsets of the groups
+// g = blockIdx.x + i * gridDim.x at own[i] (with grp_row0), for a CTA that
+// runs the scan for itself.
 __device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *grp_cnt,
                            int32_t *grp_ebeg, int32_t *grp_sbeg, int32_t *grp_ibeg,
                            int32_t *grp_wbeg, int64_t *grp_wrow, int32_t *grp_rbeg,
-                           int32_t *ent_tbeg, int32_t *counts) {
+                           int32_t *ent_tbeg, int32_t *counts, bool write_global,
+                           GroupOff *own, const int32_t *grp_row0) {
     __shared__ int64_t sE;
     int64_t tot;
     // this thread's group among the first 1024, read once for both passes
     int64_t L0 = 0, S0 = 0, R0 = 0;
+    int32_t Q0 = 0;
     {
         int64_t part = 0;
         for (int32_t g = threadIdx.x; g < G; g += 1024) {
@@ -370,6 +385,7 @@ __device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *gr
                 L0 = L;
                 S0 = __ldcg(grp_cnt + g * 2 + 1);
                 R0 = grp_rows[g];
+                if (own) Q0 = grp_row0[g];
             }
             part += L;
         }
@@ -390,13 +406,27 @@ __device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *gr
         int64_t v[6] = {L, S, nch, nch > 1 ? nch : 0, nch > 1 ? nch * rows : 0, nch > 1 ? 1 : 0};
         int64_t t[6];
         block_scan_n<6>(v, t);
-        if (g < G) {
+        if (g < G && write_global) {
             grp_ebeg[g] = (int32_t)(be + v[0]);
             grp_sbeg[g] = (int32_t)(bs + v[1]);
             grp_ibeg[g] = (int32_t)(bi + v[2]);
             grp_wbeg[g] = (int32_t)(bw + v[3]);
             grp_wrow[g] = bwr + v[4];
             grp_rbeg[g] = (int32_t)(br + v[5]);
+        }
+        if (g < G && own && g % (int32_t)gridDim.x == (int32_t)blockIdx.x) {
+            GroupOff &o = own[g / (int32_t)gridDim.x];
+            o.row0 = g0 == 0 ? Q0 : grp_row0[g];
+            o.rows = (int32_t)(rows / kTile);
+            o.ebeg = (int32_t)(be + v[0]);
+            o.eend = (int32_t)(be + v[0] + L);
+            o.sbeg = (int32_t)(bs + v[1]);
+            o.send = (int32_t)(bs + v[1] + S);
+            o.ibeg = (int32_t)(bi + v[2]);
+            o.wbeg = (int32_t)(bw + v[3]);
+            o.wrow = bwr + v[4];
+            o.rbeg = (int32_t)(br + v[5]);
+            o.C = C;
         }
         be += t[0];
         bs += t[1];
@@ -405,7 +435,7 @@ __device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *gr
         bwr += t[4];
         br += t[5];
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && write_global) {
         grp_ebeg[G] = (int32_t)be;
         ent_tbeg[be] = (int32_t)bs;
         counts[kCntEntries] = (int32_t)be;
@@ -417,15 +447,6 @@ __device__ void group_scan(int32_t G, const int32_t *grp_rows, const int32_t *gr
         counts[kCntChunk] = (int32_t)C;
     }
 }
-
-// Group g's offsets from the group scan, read once before the fill.
-struct GroupOff {
-    int32_t row0, rows;          // first tile row, tile rows
-    int32_t ebeg, eend;          // entries [ebeg, eend)
-    int32_t sbeg, send;          // slots [sbeg, send)
-    int32_t ibeg, wbeg, rbeg;    // first item, workspace slot, reduction
-    int64_t wrow, C;             // first workspace row, chunk size
-};
 
 __device__ __forceinline__ GroupOff load_group_off(int g, const int32_t *grp_row0,
                                                    const int32_t *grp_rows,
@@ -715,24 +736,25 @@ __device__ bool grid_sync_step(int32_t *bar, int32_t epoch, int32_t *status,
     return err_s == 0;
 }
 
-// CTA 0 after the bitmap is set: the exclusive prefix of the bitmap words'
-// popcounts in row-major order (wpre), hence row_ptr[r] = wpre[r * kw] and
-// the block count (1024 threads, each a contiguous run of whole 16-byte
-// vectors of words; the bitmap and wpre are 256-byte aligned allocations).
+// After the bitmap is set: the exclusive prefix of the bitmap words'
+// popcounts in row-major order into `wpre` (global or shared memory, 16-byte
+// aligned), and with write_rows row_ptr[r] = wpre[r * kw] and the block
+// count (1024 threads, each a contiguous run of whole 16-byte vectors of
+// words; the bitmap is a 256-byte aligned allocation).
 // Runs of up to kScanKeep words stay in registers between the count and
 // the prefix; longer runs read the bitmap twice.
-constexpr int kScanKeep = 16;
+constexpr int kScanKeep = 8;
 
 __device__ __forceinline__ void scan_bits_put(const DynFusedArgs &a, int64_t i, int32_t run,
-                                              int64_t &nbnd, int32_t &r) {
-    if (i == nbnd) {   // first word of block row r
+                                              int64_t &nbnd, int32_t &r, bool write_rows) {
+    if (write_rows && i == nbnd) {   // first word of block row r
         a.row_ptr[r] = run;
         ++r;
         nbnd += a.kw;
     }
 }
 
-__device__ void scan_bits(const DynFusedArgs &a) {
+__device__ __noinline__ void scan_bits(const DynFusedArgs &a, int32_t *wpre, bool write_rows) {
     const int64_t W = (int64_t)a.mb * a.kw;
     int64_t q = (W + blockDim.x - 1) / blockDim.x;
     q = (q + 3) & ~(int64_t)3;                           // whole uint4 per thread
@@ -779,24 +801,24 @@ __device__ void scan_bits(const DynFusedArgs &a) {
             if (i + 4 <= hi) {
                 int4 o;
                 o.x = (int32_t)run;
-                scan_bits_put(a, i, o.x, nbnd, r);
+                scan_bits_put(a, i, o.x, nbnd, r, write_rows);
                 run += __popc(w[u]);
                 o.y = (int32_t)run;
-                scan_bits_put(a, i + 1, o.y, nbnd, r);
+                scan_bits_put(a, i + 1, o.y, nbnd, r, write_rows);
                 run += __popc(w[u + 1]);
                 o.z = (int32_t)run;
-                scan_bits_put(a, i + 2, o.z, nbnd, r);
+                scan_bits_put(a, i + 2, o.z, nbnd, r, write_rows);
                 run += __popc(w[u + 2]);
                 o.w = (int32_t)run;
-                scan_bits_put(a, i + 3, o.w, nbnd, r);
+                scan_bits_put(a, i + 3, o.w, nbnd, r, write_rows);
                 run += __popc(w[u + 3]);
-                *(int4 *)(a.wpre + i) = o;
+                *(int4 *)(wpre + i) = o;
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (i + j < hi) {
-                        a.wpre[i + j] = (int32_t)run;
-                        scan_bits_put(a, i + j, (int32_t)run, nbnd, r);
+                        wpre[i + j] = (int32_t)run;
+                        scan_bits_put(a, i + j, (int32_t)run, nbnd, r, write_rows);
                         run += __popc(w[u + j]);
                     }
                 }
@@ -804,12 +826,12 @@ __device__ void scan_bits(const DynFusedArgs &a) {
         }
     } else {
         for (int64_t i = lo; i < hi; ++i) {
-            a.wpre[i] = (int32_t)run;
-            scan_bits_put(a, i, (int32_t)run, nbnd, r);
+            wpre[i] = (int32_t)run;
+            scan_bits_put(a, i, (int32_t)run, nbnd, r, write_rows);
             run += __popc(__ldcg(a.bits + i));
         }
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && write_rows) {
         a.row_ptr[a.mb] = (int32_t)total;
         a.counts[kCntNnzb] = (int32_t)total;
     }
@@ -840,6 +862,9 @@ __device__ void group_colmask_bits(const DynFusedArgs &a, int32_t t0, int32_t nr
 constexpr int kFusedPk = 4096;
 constexpr int kStageWarps = 12;  // warps cutting stage records in step D
 constexpr int kPackDepth = 8;    // blocks in flight per packing warp
+constexpr int kMaxOwnGroups = 16;  // groups per CTA for the per-CTA group scan
+// bitmap words whose prefix fits the packing staging area (per-CTA scan)
+constexpr int64_t kLocalWords = (int64_t)(32 - kStageWarps) * kPackDepth * 512 / 4;
 constexpr int kFusedRp = 16 * 16 + 1;
 __host__ __device__ inline size_t fused_pack_buf_offset(int32_t kt) {
     return (sizeof(int32_t) * (2 * (size_t)kt + kFusedRp + 3 * (size_t)kFusedPk) + 15) / 16 * 16;
@@ -981,8 +1006,8 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
     int32_t *pk = rp_s + kFusedRp;
     uint4 *pack_buf = (uint4 *)((uint8_t *)dsm + fused_pack_buf_offset(a.kt));
     // the first group's rows (plan constants), read while A runs
-    __shared__ int32_t row0_s, rows_s;
-    __shared__ GroupOff go_s;
+    __shared__ int32_t row0_s, rows_s, err_s;
+    __shared__ GroupOff go_s, own_s[kMaxOwnGroups];
     if (threadIdx.x == 0 && (int)blockIdx.x < a.G) {
         row0_s = a.grp_row0[blockIdx.x];
         rows_s = a.grp_rows[blockIdx.x];
@@ -1006,13 +1031,30 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
         const uint32_t bit = 1u << (c & 31);
         if (atomicOr(&a.bits[(int64_t)r * a.kw + (c >> 5)], bit) & bit) flag(a.status, kDevPattern);
     }
-    // a rejected pattern ends the launch here, in every CTA
-    if (!grid_sync_step(a.bar, 2, a.status, lim, [&] { scan_bits(a); })) return;
+    // The bitmap scan: run by every CTA for itself into shared memory (the
+    // packing staging area, free until step D) when the prefix fits there,
+    // else by CTA 0 between the barrier's arrivals and its release.  CTA 0
+    // writes row_ptr either way.  A rejected pattern ends the launch here,
+    // in every CTA.
+    const int64_t W = (int64_t)a.mb * a.kw;
+    const bool local_bits = W <= kLocalWords;
+    const int32_t *wpre = local_bits ? (const int32_t *)pack_buf : a.wpre;
+    if (local_bits) {
+        if (!grid_sync(a.bar, 2, a.status, lim)) return;
+        int32_t st = 0;
+        if (threadIdx.x == 0) st = ld_relaxed(a.status);   // ordered after the barrier's acquire
+        scan_bits(a, (int32_t *)pack_buf, blockIdx.x == 0);
+        if (threadIdx.x == 0) err_s = st;
+        __syncthreads();
+        if (err_s != 0) return;
+    } else if (!grid_sync_step(a.bar, 2, a.status, lim, [&] { scan_bits(a, a.wpre, true); })) {
+        return;
+    }
     // C.
     for (int64_t p = gt; p < n; p += gs) {
         const int32_t r = a.brow[p], c = a.bcol[p];
         const int64_t wi = (int64_t)r * a.kw + (c >> 5);
-        const int32_t pos = a.wpre[wi] + __popc(a.bits[wi] & ((1u << (c & 31)) - 1u));
+        const int32_t pos = wpre[wi] + __popc(a.bits[wi] & ((1u << (c & 31)) - 1u));
         a.col_idx[pos] = c;
         a.perm[pos] = (int32_t)p;
     }
@@ -1024,11 +1066,21 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
             a.gmask[(int64_t)g * a.kt + c] = colmask[c];
         group_counts(g, a.kt, colmask, a.grp_cnt);
     }
-    if (!grid_sync_step(a.bar, 3, a.status, lim, [&] {
-            group_scan(a.G, a.grp_rows, a.grp_cnt, a.grp_ebeg, a.grp_sbeg, a.grp_ibeg, a.grp_wbeg,
-                       a.grp_wrow, a.grp_rbeg, a.ent_tbeg, a.counts);
-        }))
+    // The group scan: every CTA for itself (its own groups' offsets into
+    // shared memory; CTA 0 also stores all of them) while each CTA has at
+    // most kMaxOwnGroups groups, else CTA 0 between arrivals and release.
+    const bool local_groups = a.G <= kMaxOwnGroups * (int)gridDim.x;
+    if (local_groups) {
+        if (!grid_sync(a.bar, 3, a.status, lim)) return;
+        group_scan(a.G, a.grp_rows, a.grp_cnt, a.grp_ebeg, a.grp_sbeg, a.grp_ibeg, a.grp_wbeg,
+                   a.grp_wrow, a.grp_rbeg, a.ent_tbeg, a.counts, blockIdx.x == 0, own_s,
+                   a.grp_row0);
+    } else if (!grid_sync_step(a.bar, 3, a.status, lim, [&] {
+                   group_scan(a.G, a.grp_rows, a.grp_cnt, a.grp_ebeg, a.grp_sbeg, a.grp_ibeg,
+                              a.grp_wbeg, a.grp_wrow, a.grp_rbeg, a.ent_tbeg, a.counts);
+               })) {
         return;
+    }
     // D.  Per group: the fill, then the group's stage records on warps
     // [0, kStageWarps) beside the value packing on the others.
     const int64_t tile_bytes = a.w8 ? kTile * kTile : kTile * kTile * 2;
@@ -1037,8 +1089,11 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
         const bool first = g == (int)blockIdx.x;
         const int32_t t0 = first ? row0_s : a.grp_row0[g], nrows = first ? rows_s : a.grp_rows[g];
         if (threadIdx.x == 0)
-            go_s = load_group_off(g, a.grp_row0, a.grp_rows, a.grp_ebeg, a.grp_sbeg, a.grp_ibeg,
-                                  a.grp_wbeg, a.grp_wrow, a.grp_rbeg, a.counts, a.G);
+            go_s = local_groups
+                       ? own_s[(g - (int)blockIdx.x) / (int)gridDim.x]
+                       : load_group_off(g, a.grp_row0, a.grp_rows, a.grp_ebeg, a.grp_sbeg,
+                                        a.grp_ibeg, a.grp_wbeg, a.grp_wrow, a.grp_rbeg, a.counts,
+                                        a.G);
         for (int32_t c = threadIdx.x; c < a.kt; c += blockDim.x)
             colmask[c] = a.gmask[(int64_t)g * a.kt + c];
         for (int32_t i = threadIdx.x; i <= nrows * a.T; i += blockDim.x)

@@ -280,18 +280,25 @@ def test_fused_repartition_equals_launch_chain(b, dt, w8):
             assert oracle.normwise_err(outs[0], Yo, oracle.block_fro(vals), X.cpu()) <= 4e-3
 
 
-@pytest.mark.parametrize("b,m,k", [(16, 208, 640), (8, 80, 48), (4, 4096, 4096)])
-def test_fused_repartition_bitmap_edges(b, m, k):
-    """The fused launch's bitmap scan at the edges of its layout: a bitmap
-    whose word count is not a multiple of four (b = 16, 13 block rows of two
-    words; b = 8, 10 block rows of one word) and one with more than sixteen
-    words per thread (b = 4, m = k = 4096: 32768 words).  Arrays and Y equal
-    the launch chain's bit for bit; Y is within the normwise bar."""
+@pytest.mark.parametrize("b,m,k,groups", [(16, 208, 640, 0), (8, 80, 48, 0), (4, 4096, 4096, 0),
+                                          (4, 4096, 2048, 0), (16, 33024, 128, 2064)])
+def test_fused_repartition_scan_paths(b, m, k, groups):
+    """The fused launch's two scans on each of their paths: a bitmap whose
+    word count is not a multiple of four (b = 16, 13 block rows of two
+    words; b = 8, 10 block rows of one word), runs longer than the words a
+    thread keeps in registers, scanned by every CTA for itself (b = 4,
+    m = 4096, k = 2048: 16384 words) and by CTA 0 alone (b = 4,
+    m = k = 4096: 32768 words, past the per-CTA limit), and more groups
+    than the per-CTA group scan takes (2064 one-row groups: CTA 0 scans).
+    Arrays and Y equal the launch chain's bit for bit; the CSR equals the
+    oracle's; Y is within the normwise bar."""
     n = 72
     dt = torch.bfloat16
     cap = max(wl.nnzb_for(m, k, b, 1 / 4), 1)
-    plans = [S.Plan(m, k, n, b, w_dtype=S.BF16, mode=S.DYNAMIC, nnzb_max=cap, dyn_chain=ch)
-             for ch in (False, True)]
+    plans = [S.Plan(m, k, n, b, w_dtype=S.BF16, mode=S.DYNAMIC, nnzb_max=cap, dyn_chain=ch,
+                    groups=groups) for ch in (False, True)]
+    if groups:
+        assert plans[0].info()["n_groups"] == groups
     for call in range(2):
         c = wl.dynamic_call(call + 70 * b, m=m, k=k, n=n, b=b, d_max=1 / 4)
         X = torch.from_numpy(c["X"]).to(dt).cuda()
@@ -314,9 +321,8 @@ def test_fused_repartition_bitmap_edges(b, m, k):
         assert np.array_equal(plans[0].array("row_ptr"), rp)
         assert np.array_equal(plans[0].array("col_idx"), ci)
         assert np.array_equal(plans[0].array("perm"), pm)
-        if m * k <= 1 << 20:
-            Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X.cpu())
-            assert oracle.normwise_err(outs[0], Yo, oracle.block_fro(vals), X.cpu()) <= 4e-3
+        Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X.cpu())
+        assert oracle.normwise_err(outs[0], Yo, oracle.block_fro(vals), X.cpu()) <= 4e-3
 
 
 def test_fused_repartition_wait_times_out_and_recovers():
