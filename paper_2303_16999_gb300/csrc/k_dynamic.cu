@@ -475,14 +475,16 @@ __device__ __forceinline__ GroupOff load_group_off(int g, const int32_t *grp_row
 // Group g's entries (ascending tile column), slots (ascending rows, one per
 // tile), block -> slot / offset, items and workspace / reduction records,
 // from its column masks (whole CTA of 1024 threads; slot_of[kt] in shared
-// memory; [s0, s1) the group's CSR slots; o its offsets).
+// memory; [s0, s1) the group's CSR slots; o its offsets; ent_s, when
+// given: the group's entries' columns, first tiles and covers again, in
+// three arrays of kt in shared memory, from the group's first entry).
 __device__ void group_fill(int g, const GroupOff &o, int32_t kt, int32_t T, int32_t b,
                            const int32_t *row_ptr, const int32_t *col_idx, const int32_t *perm,
                            const uint32_t *colmask, int32_t *slot_of, int32_t s0, int32_t s1,
                            int32_t *ent_col, int32_t *ent_tbeg, int32_t *ent_cover,
                            int32_t *tile_row, int32_t *blk_slot, int32_t *blk_off, int32_t *items,
                            int64_t *ws_row0, int32_t *red, const int32_t *rp_s = nullptr,
-                           int32_t *pk = nullptr) {
+                           int32_t *pk = nullptr, int32_t *ent_s = nullptr) {
     const int32_t t0 = o.row0, nrows = o.rows;
     // column prefix over entries and slots, in chunks of blockDim (1024)
     int64_t eb = o.ebeg, sb = o.sbeg;
@@ -498,6 +500,11 @@ __device__ void group_fill(int g, const GroupOff &o, int32_t kt, int32_t T, int3
             ent_col[e] = c;
             ent_tbeg[e] = (int32_t)(sb + xs);
             ent_cover[e] = (int32_t)(mk | (mk << 16));
+            if (ent_s) {   // the same, from the group's first entry
+                ent_s[e - o.ebeg] = c;
+                ent_s[kt + e - o.ebeg] = (int32_t)(sb + xs);
+                ent_s[2 * kt + e - o.ebeg] = (int32_t)(mk | (mk << 16));
+            }
             uint32_t m = mk;
             int32_t q = (int32_t)(sb + xs);
             while (m) {
@@ -738,9 +745,10 @@ __device__ bool grid_sync_step(int32_t *bar, int32_t epoch, int32_t *status,
 
 // After the bitmap is set: the exclusive prefix of the bitmap words'
 // popcounts in row-major order into `wpre` (global or shared memory, 16-byte
-// aligned), and with write_rows row_ptr[r] = wpre[r * kw] and the block
-// count (1024 threads, each a contiguous run of whole 16-byte vectors of
-// words; the bitmap is a 256-byte aligned allocation).
+// aligned), with write_rows row_ptr[r] = wpre[r * kw] and the block count,
+// and with bits_out a copy of the bitmap (shared memory, 16-byte aligned)
+// (1024 threads, each a contiguous run of whole 16-byte vectors of words;
+// the bitmap is a 256-byte aligned allocation).
 // Runs of up to kScanKeep words stay in registers between the count and
 // the prefix; longer runs read the bitmap twice.
 constexpr int kScanKeep = 8;
@@ -754,7 +762,8 @@ __device__ __forceinline__ void scan_bits_put(const DynFusedArgs &a, int64_t i, 
     }
 }
 
-__device__ __noinline__ void scan_bits(const DynFusedArgs &a, int32_t *wpre, bool write_rows) {
+__device__ __noinline__ void scan_bits(const DynFusedArgs &a, int32_t *wpre, bool write_rows,
+                                       uint32_t *bits_out) {
     const int64_t W = (int64_t)a.mb * a.kw;
     int64_t q = (W + blockDim.x - 1) / blockDim.x;
     q = (q + 3) & ~(int64_t)3;                           // whole uint4 per thread
@@ -772,9 +781,13 @@ __device__ __noinline__ void scan_bits(const DynFusedArgs &a, int32_t *wpre, boo
                 w[u + 1] = v.y;
                 w[u + 2] = v.z;
                 w[u + 3] = v.w;
+                if (bits_out) *(uint4 *)(bits_out + i) = v;
             } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) w[u + j] = i + j < hi ? __ldcg(a.bits + i + j) : 0u;
+                for (int j = 0; j < 4; ++j) {
+                    w[u + j] = i + j < hi ? __ldcg(a.bits + i + j) : 0u;
+                    if (bits_out && i + j < hi) bits_out[i + j] = w[u + j];
+                }
             }
         }
 #pragma unroll
@@ -784,8 +797,13 @@ __device__ __noinline__ void scan_bits(const DynFusedArgs &a, int32_t *wpre, boo
             if (i + 4 <= hi) {
                 const uint4 v = __ldcg((const uint4 *)(a.bits + i));
                 local += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+                if (bits_out) *(uint4 *)(bits_out + i) = v;
             } else {
-                for (int64_t j = i; j < hi; ++j) local += __popc(__ldcg(a.bits + j));
+                for (int64_t j = i; j < hi; ++j) {
+                    const uint32_t v = __ldcg(a.bits + j);
+                    local += __popc(v);
+                    if (bits_out) bits_out[j] = v;
+                }
             }
         }
     }
@@ -837,13 +855,14 @@ __device__ __noinline__ void scan_bits(const DynFusedArgs &a, int32_t *wpre, boo
     }
 }
 
-// The column masks of group g from the bitmap (bit r of colmask[c]: tile
+// The column masks of the group of tile rows [t0, t0 + nrows) from the
+// bitmap (global, or its copy in shared memory) (bit r of colmask[c]: tile
 // row r of the group holds a block in tile column c), into shared memory.
-__device__ void group_colmask_bits(const DynFusedArgs &a, int32_t t0, int32_t nrows,
-                                   uint32_t *colmask) {
+__device__ void group_colmask_bits(const DynFusedArgs &a, const uint32_t *bits, int32_t t0,
+                                   int32_t nrows, uint32_t *colmask) {
     const uint32_t tmask = a.T >= 32 ? 0xffffffffu : ((1u << a.T) - 1u);
     const int32_t nb = nrows * a.T;                       // block rows of the group
-    const uint32_t *base = a.bits + (int64_t)t0 * a.T * a.kw;
+    const uint32_t *base = bits + (int64_t)t0 * a.T * a.kw;
     for (int32_t c = threadIdx.x; c < a.kt; c += blockDim.x) {
         const int32_t bc = c * a.T;                       // first block column of tile column c
         const int32_t w = bc >> 5, sh = bc & 31;
@@ -858,7 +877,9 @@ __device__ void group_colmask_bits(const DynFusedArgs &a, int32_t t0, int32_t nr
 
 // Shared memory of the fused launch: colmask[kt], slot_of[kt], the group's
 // row pointers (at most 16 * 16 + 1), kFusedPk (user index, slot, offset)
-// triples and, from a 16-byte boundary, the packing warps' staging pieces.
+// triples, the group's entries (three arrays of kt) and, from a 16-byte
+// boundary, the packing warps' staging pieces (before step D: the bitmap
+// prefix and the bitmap).
 constexpr int kFusedPk = 4096;
 constexpr int kStageWarps = 12;  // warps cutting stage records in step D
 constexpr int kPackDepth = 8;    // blocks in flight per packing warp
@@ -867,7 +888,7 @@ constexpr int kMaxOwnGroups = 16;  // groups per CTA for the per-CTA group scan
 constexpr int64_t kLocalWords = (int64_t)(32 - kStageWarps) * kPackDepth * 512 / 4;
 constexpr int kFusedRp = 16 * 16 + 1;
 __host__ __device__ inline size_t fused_pack_buf_offset(int32_t kt) {
-    return (sizeof(int32_t) * (2 * (size_t)kt + kFusedRp + 3 * (size_t)kFusedPk) + 15) / 16 * 16;
+    return (sizeof(int32_t) * (5 * (size_t)kt + kFusedRp + 3 * (size_t)kFusedPk) + 15) / 16 * 16;
 }
 inline size_t fused_smem(int32_t kt) {
     return fused_pack_buf_offset(kt) + (size_t)(32 - kStageWarps) * kPackDepth * 512;
@@ -954,12 +975,13 @@ __device__ __forceinline__ void sync_first(int n) {
 }
 
 // The stage records of group g's work items (the near-equal chunks of its
-// entries, as group_fill writes them), cut by warps [0, nbw) of the CTA
+// entries, as group_fill writes them; read from its copy in shared memory,
+// ent_s), cut by warps [0, nbw) of the CTA
 // exactly as a CTA per item cuts them (32 entries per warp, the cut, a
 // prefix of the stage counts, the write pass), with named barrier 1 between
 // the passes; items at or past the items' capacity are skipped.
 __device__ void build_group_stages(const DynFusedArgs &a, const GroupOff &o, int nbw,
-                                   int32_t *bcounts) {
+                                   int32_t *bcounts, const int32_t *ent_s) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int32_t L = o.eend - o.ebeg, nch = nchunks(L, o.C);
     const int32_t base = L / nch, rem = L % nch;
@@ -974,9 +996,9 @@ __device__ void build_group_stages(const DynFusedArgs &a, const GroupOff &o, int
                 const bool active = bi < nb;
                 const int32_t eb = e + 32 * bi;
                 BatchCut cut;
-                if (active)
-                    cut = cut_batch(eb, e1, a.ent_cap, a.tiles_cap, a.ent_col, a.ent_tbeg,
-                                    a.ent_cover);
+                if (active)   // entries indexed from the group's first
+                    cut = cut_batch(eb - o.ebeg, e1 - o.ebeg, a.ent_cap, a.tiles_cap, ent_s,
+                                    ent_s + a.kt, ent_s + 2 * a.kt);
                 if (lane == 0) bcounts[warp] = active ? cut.nst : 0;
                 sync_first(nbw * 32);
                 int32_t off = rec, tot = 0;
@@ -1004,6 +1026,7 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
     int32_t *slot_of = (int32_t *)(dsm + a.kt);
     int32_t *rp_s = slot_of + a.kt;
     int32_t *pk = rp_s + kFusedRp;
+    int32_t *ent_s = pk + 3 * kFusedPk;
     uint4 *pack_buf = (uint4 *)((uint8_t *)dsm + fused_pack_buf_offset(a.kt));
     // the first group's rows (plan constants), read while A runs
     __shared__ int32_t row0_s, rows_s, err_s;
@@ -1038,30 +1061,35 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
     // in every CTA.
     const int64_t W = (int64_t)a.mb * a.kw;
     const bool local_bits = W <= kLocalWords;
+    // the bitmap's copy too where both fit (after the prefix, 16-byte aligned)
+    const bool local_copy = ((W + 3) & ~(int64_t)3) + W <= kLocalWords;
     const int32_t *wpre = local_bits ? (const int32_t *)pack_buf : a.wpre;
+    uint32_t *bits_s = (uint32_t *)pack_buf + ((W + 3) & ~(int64_t)3);
+    const uint32_t *bits_c = local_copy ? bits_s : a.bits;
     if (local_bits) {
         if (!grid_sync(a.bar, 2, a.status, lim)) return;
         int32_t st = 0;
         if (threadIdx.x == 0) st = ld_relaxed(a.status);   // ordered after the barrier's acquire
-        scan_bits(a, (int32_t *)pack_buf, blockIdx.x == 0);
+        scan_bits(a, (int32_t *)pack_buf, blockIdx.x == 0, local_copy ? bits_s : nullptr);
         if (threadIdx.x == 0) err_s = st;
         __syncthreads();
         if (err_s != 0) return;
-    } else if (!grid_sync_step(a.bar, 2, a.status, lim, [&] { scan_bits(a, a.wpre, true); })) {
+    } else if (!grid_sync_step(a.bar, 2, a.status, lim,
+                               [&] { scan_bits(a, a.wpre, true, nullptr); })) {
         return;
     }
     // C.
     for (int64_t p = gt; p < n; p += gs) {
         const int32_t r = a.brow[p], c = a.bcol[p];
         const int64_t wi = (int64_t)r * a.kw + (c >> 5);
-        const int32_t pos = wpre[wi] + __popc(a.bits[wi] & ((1u << (c & 31)) - 1u));
+        const int32_t pos = wpre[wi] + __popc(bits_c[wi] & ((1u << (c & 31)) - 1u));
         a.col_idx[pos] = c;
         a.perm[pos] = (int32_t)p;
     }
     for (int g = blockIdx.x; g < a.G; g += gridDim.x) {
         const bool first = g == (int)blockIdx.x;
-        group_colmask_bits(a, first ? row0_s : a.grp_row0[g], first ? rows_s : a.grp_rows[g],
-                           colmask);
+        group_colmask_bits(a, bits_c, first ? row0_s : a.grp_row0[g],
+                           first ? rows_s : a.grp_rows[g], colmask);
         for (int32_t c = threadIdx.x; c < a.kt; c += blockDim.x)
             a.gmask[(int64_t)g * a.kt + c] = colmask[c];
         group_counts(g, a.kt, colmask, a.grp_cnt);
@@ -1116,10 +1144,10 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
         const bool stage = s1 - s0 <= kFusedPk;
         group_fill(g, go, a.kt, a.T, a.b, a.row_ptr, a.col_idx, a.perm, colmask, slot_of, s0, s1,
                    a.ent_col, a.ent_tbeg, a.ent_cover, a.tile_row, a.blk_slot, a.blk_off,
-                   a.items, a.ws_row0, a.red, rp_s, stage ? pk : nullptr);
+                   a.items, a.ws_row0, a.red, rp_s, stage ? pk : nullptr, ent_s);
         __syncthreads();   // this CTA's entries, block -> slot writes and cleared tiles
         if (warp < kStageWarps)
-            build_group_stages(a, go, kStageWarps, bcounts);
+            build_group_stages(a, go, kStageWarps, bcounts, ent_s);
         else
             pack_group(a, s0, s1, stage ? pk : nullptr, kStageWarps, 32 - kStageWarps,
                        pack_buf);
