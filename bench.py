@@ -243,7 +243,7 @@ def kernel_source_sha16(files=("csrc/k_tc.cu", "csrc/tc_ptx.cuh", "csrc/capi.cpp
 # of one step; the command and the per-launch table are in
 # profiles/tc_kernel_sweep_dram.md).  Used only while the kernel and planner
 # sources hash to `sha16`; otherwise the bench reports traffic null.
-SWEEP_TRAFFIC = {"sha16": "8d4ff2df56a8a4b9", "bytes_per_launch": 38592560.0,
+SWEEP_TRAFFIC = {"sha16": "74112429612483d3", "bytes_per_launch": 38580512.0,
                  "source": "profiles/tc_kernel_sweep_dram.md"}
 
 
@@ -966,18 +966,24 @@ def run_serving(torch, S, wl, dev, peaks, per_rate=4000,
 
 def run_gather_small_n(torch, S, wl, dev, peaks, reps=15):
     """The b = 1 gather kernel (CUDA cores) at small n, where it is bound by
-    HBM: m = k = 16384, d = 1/16 (16.8 M non-zeros, 100 MB of FP16 values and
-    int32 indices, so one pass does not fit the 129 MB L2 together with the
-    flush), FP16.  Each timed run follows a 256 MB write and read-back that
-    evict L2 (the read-back lets the written lines drain first); the events
-    bracket the product alone.  Compulsory bytes (values, indices, row
-    pointers, X once, Y once) over the measured time, against the measured
-    HBM copy bandwidth."""
+    HBM: m = k = 16384, d = 1/16 (16.8 M non-zeros: 34 MB of FP16 values and
+    34 MB of 16-bit or 67 MB of int32 column indices), FP16.  Each timed run
+    follows a 256 MB write and read-back that evict L2 (the read-back lets
+    the written lines drain first); the events bracket the product alone.
+    Compulsory bytes (values, the indices the kernel reads, row pointers, X
+    once, Y once) over the measured time, against the measured HBM copy
+    bandwidth."""
     m = k = 16384
     nnzb = wl.nnzb_for(m, k, 1, 1 / 16)
     c = wl.problem(7, m, k, 32, 1, nnzb)
     plan = S.Plan(m, k, 32, 1, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"], kernel="gather")
     plan.pack(torch.from_numpy(c["vals"].reshape(-1)).half().to(dev))
+    # bytes per column index each point's kernel reads: the plan's 16-bit
+    # copy where X stays in shared memory (n = 1 at this k), else int32
+    ib16 = plan.info()["index_bytes"]
+
+    def idx_bytes(n):
+        return ib16 if n == 1 else 4
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = []
     for n in (1, 4, 16, 32):
@@ -998,14 +1004,15 @@ def run_gather_small_n(torch, S, wl, dev, peaks, reps=15):
             b.synchronize()
             ts.append(a.elapsed_time(b) * 1e3)
         us = statistics.median(ts)
-        by = nnzb * 2 + nnzb * 4 + (m + 1) * 4 + (k + m) * n * 2
+        by = nnzb * 2 + nnzb * idx_bytes(n) + (m + 1) * 4 + (k + m) * n * 2
         gbs = by / us / 1e3
-        out.append({"n": n, "us": round(us, 2), "gbs": round(gbs, 1),
+        out.append({"n": n, "us": round(us, 2), "gbs": round(gbs, 1), "index_bytes": idx_bytes(n),
                     "frac_of_hbm": round(gbs / peaks["hbm_gbs"], 3),
                     "tflops_nz": round(2.0 * nnzb * n / us / 1e6, 3)})
     plan.close()
     del flush
-    launches = [(2.0 * nnzb * q["n"], nnzb * 2 + nnzb * 4 + (m + 1) * 4 + (k + m) * q["n"] * 2,
+    launches = [(2.0 * nnzb * q["n"],
+                 nnzb * 2 + nnzb * q["index_bytes"] + (m + 1) * 4 + (k + m) * q["n"] * 2,
                  q["us"] * 1e-6) for q in out]
     return {"workload": "b=1 gather kernel, m=k=16384, d=1/16 (16.8 M non-zeros), FP16, small n; "
                         "L2 evicted (256 MB written and read back) before every timed run",

@@ -262,6 +262,10 @@ typedef struct {
     int32_t sddmm_form;           /* spmm_sddmm on this plan: 0 dense tiles, 1 gathered blocks */
     int64_t row_begin, row_end;   /* the plan's slice of output rows (0, m for a whole plan) */
     int32_t col_tiles;            /* TC: the col_tiles option the plan runs with (0, 1 or 2) */
+    int32_t index_bytes;          /* bytes per column index the product reads: 2 for static
+                                     GATHER plans with k <= 65536 (a 16-bit copy of col_idx,
+                                     read by the n <= 8 kernel that keeps X in shared memory),
+                                     else 4 */
 } spmm_plan_info;
 
 spmm_status spmm_plan_get_info(const spmm_plan *plan, spmm_plan_info *info);

@@ -171,6 +171,12 @@ static int default_R(int64_t mt, int64_t n_max, int sms) {
     return R;
 }
 
+// Static GATHER plans whose block columns fit 16 bits keep a 16-bit copy of
+// col_idx for the gather kernels.
+static bool col16_plan(const spmm_plan *p) {
+    return p->kernel == SPMM_KERNEL_GATHER && p->mode == SPMM_STATIC && p->k / p->b <= 65536;
+}
+
 static spmm_status upload_plan(spmm_plan *p) {
     HostPlan &hp = p->hp;
     cudaError_t e = cudaSuccess;
@@ -182,6 +188,11 @@ static spmm_status upload_plan(spmm_plan *p) {
     UP(d_items, items);
     UP(d_red, red);
     UP(d_ws_row0, ws_row0);
+    if (col16_plan(p) && e == cudaSuccess) {
+        // the b = 1 gather's column indices in half the bytes
+        const std::vector<uint16_t> c16(hp.col_idx.begin(), hp.col_idx.end());
+        e = upload(p, &p->d_col16, c16);
+    }
     if (p->kernel == SPMM_KERNEL_TC) {
         UP(d_grp_row0, grp_row0);
         UP(d_grp_rows, grp_rows);
@@ -1016,6 +1027,7 @@ spmm_status spmm_plan_get_info(const spmm_plan *cp, spmm_plan_info *info) {
     i.device_bytes = p->device_bytes;
     i.stage_geometry = p->kernel == SPMM_KERNEL_TC ? p->tc_geo : 0;
     i.col_tiles = p->kernel == SPMM_KERNEL_TC ? p->col_tiles : 0;
+    i.index_bytes = col16_plan(p) ? 2 : 4;
     i.sddmm_form = sddmm_gathers(p) ? 1 : 0;
     i.row_begin = p->row_end ? p->row_begin : 0;
     i.row_end = p->row_end ? p->row_end : p->m;

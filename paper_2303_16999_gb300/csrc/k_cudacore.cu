@@ -193,20 +193,27 @@ __global__ void __launch_bounds__(256) gather_kernel(
 constexpr int kG1Stages = 6;
 constexpr int kG1Warps = 16;
 constexpr int kG1Chunk = 256;                        // non-zeros per chunk, 8 per lane
-// one stage: the chunk's indices, then its values
-template <typename T> __host__ __device__ constexpr int g1_stage_bytes() { return kG1Chunk * (4 + (int)sizeof(T)); }
-template <typename T> __host__ __device__ constexpr int g1_ring_bytes() { return kG1Stages * g1_stage_bytes<T>(); }
+// one stage: the chunk's indices (I: int32, or the 16-bit copy of static
+// plans), then its values
+template <typename T, typename I> __host__ __device__ constexpr int g1_stage_bytes() {
+    return kG1Chunk * ((int)sizeof(I) + (int)sizeof(T));
+}
+template <typename T, typename I> __host__ __device__ constexpr int g1_ring_bytes() {
+    return kG1Stages * g1_stage_bytes<T, I>();
+}
 
 struct G1Meta {
     int32_t beg, end, row, slot, base, last, pad0, pad1;
 };
 constexpr int kG1MetaBytes = kG1Warps * kG1Stages * (int)sizeof(G1Meta);
-template <typename T> __host__ __device__ constexpr int g1_fixed_smem() {
-    return kG1Warps * g1_ring_bytes<T>() + kG1MetaBytes;
+template <typename T, typename I> __host__ __device__ constexpr int g1_fixed_smem() {
+    return kG1Warps * g1_ring_bytes<T, I>() + kG1MetaBytes;
 }
 // shared memory left for X (of the 227 KB a CTA may hold, 1 KB spare)
-template <typename T> __host__ __device__ constexpr int g1_x_budget() { return 226 * 1024 - g1_fixed_smem<T>(); }
-static_assert(g1_x_budget<float>() >= 16 * 1024, "room for X");
+template <typename T, typename I> __host__ __device__ constexpr int g1_x_budget() {
+    return 226 * 1024 - g1_fixed_smem<T, I>();
+}
+static_assert(g1_x_budget<float, int32_t>() >= 16 * 1024, "room for X");
 
 // cp.async of 16 bytes of which the first src_bytes come from src and the
 // rest are zero-filled.
@@ -217,15 +224,16 @@ __device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, int
                  : "memory");
 }
 
-template <typename T, int V>
+template <typename T, int V, typename I>
 __global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
-    const int32_t *__restrict__ items, int64_t n_items, const int32_t *__restrict__ col_idx,
+    const int32_t *__restrict__ items, int64_t n_items, const I *__restrict__ col_idx,
     const T *__restrict__ vals, int64_t cap, const T *__restrict__ X, int64_t ldx, int64_t k,
     T *__restrict__ Y, int64_t ldy, float *__restrict__ ws, const int64_t *__restrict__ ws_row0,
     const int32_t *__restrict__ n_items_dev, const int32_t *__restrict__ status) {
     pdl_enter();
     constexpr int VB = 8 * (int)sizeof(T);          // value bytes per lane per chunk (16 or 32)
-    constexpr int kStage = g1_stage_bytes<T>(), kRing = g1_ring_bytes<T>();
+    constexpr int IB = 8 * (int)sizeof(I);          // index bytes per lane per chunk (16 or 32)
+    constexpr int kStage = g1_stage_bytes<T, I>(), kRing = g1_ring_bytes<T, I>();
     extern __shared__ __align__(128) uint8_t g1_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (n_items_dev) {
@@ -250,7 +258,7 @@ __global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
         x_row = d[0], x_beg = d[1], x_end = d[2], x_slot = d[5];
     }
     // X first (its own cp.async group, so it can be waited for alone)
-    T *xs = reinterpret_cast<T *>(g1_smem + g1_fixed_smem<T>());
+    T *xs = reinterpret_cast<T *>(g1_smem + g1_fixed_smem<T, I>());
     const int64_t xbytes = k * V * (int64_t)sizeof(T);
     const bool xbulk = ldx == V && ((uintptr_t)X % 16) == 0;
     if (xbulk) {
@@ -280,9 +288,11 @@ __global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
             // past every item's end and are masked, so nothing is read there
             const int ne = max(0, min(8, cap32 - pos));
             if (ne > 0) {
-                cp_async16_zfill(st + lane * 32, col_idx + pos, min(ne, 4) * 4);
-                if (ne > 4) cp_async16_zfill(st + lane * 32 + 16, col_idx + pos + 4, (ne - 4) * 4);
-                uint8_t *vd = st + kG1Chunk * 4 + lane * VB;
+                const uint8_t *is_ = reinterpret_cast<const uint8_t *>(col_idx + pos);
+                const int ibytes = ne * (int)sizeof(I);
+                cp_async16_zfill(st + lane * IB, is_, min(ibytes, 16));
+                if (IB == 32 && ibytes > 16) cp_async16_zfill(st + lane * IB + 16, is_ + 16, ibytes - 16);
+                uint8_t *vd = st + kG1Chunk * (int)sizeof(I) + lane * VB;
                 const uint8_t *vs = reinterpret_cast<const uint8_t *>(vals + pos);
                 const int vbytes = ne * (int)sizeof(T);
                 cp_async16_zfill(vd, vs, min(vbytes, 16));
@@ -320,10 +330,23 @@ __global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
         const uint8_t *st = ring + cs * kStage;
         const G1Meta m = meta[cs];
         cs = cs + 1 == kG1Stages ? 0 : cs + 1;
-        const int4 c0 = *reinterpret_cast<const int4 *>(st + lane * 32);
-        const int4 c1 = *reinterpret_cast<const int4 *>(st + lane * 32 + 16);
-        const Pack<T, 8> w = *reinterpret_cast<const Pack<T, 8> *>(st + kG1Chunk * 4 + lane * VB);
-        const int32_t cq[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        int32_t cq[8];
+        if constexpr (sizeof(I) == 4) {
+            const int4 c0 = *reinterpret_cast<const int4 *>(st + lane * IB);
+            const int4 c1 = *reinterpret_cast<const int4 *>(st + lane * IB + 16);
+            cq[0] = c0.x, cq[1] = c0.y, cq[2] = c0.z, cq[3] = c0.w;
+            cq[4] = c1.x, cq[5] = c1.y, cq[6] = c1.z, cq[7] = c1.w;
+        } else {
+            const uint4 c = *reinterpret_cast<const uint4 *>(st + lane * IB);
+            const uint32_t h[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                cq[2 * q] = (int32_t)(h[q] & 0xFFFFu);
+                cq[2 * q + 1] = (int32_t)(h[q] >> 16);
+            }
+        }
+        const Pack<T, 8> w =
+            *reinterpret_cast<const Pack<T, 8> *>(st + kG1Chunk * (int)sizeof(I) + lane * VB);
         if (m.base >= m.beg && m.base + kG1Chunk <= m.end) {
             // a chunk wholly inside its item (all but an item's first and
             // last): no masks
@@ -483,14 +506,14 @@ __global__ void __launch_bounds__(512, SPMM_G1_BLOCKS) gather1g_kernel(
 }
 
 // X in shared memory: one 16-warp CTA per SM, streaming through the ring.
-template <typename T, int V>
-cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const void *X, int64_t ldx, void *Y,
-                           int64_t ldy, cudaStream_t s) {
+template <typename T, int V, typename I>
+cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const I *col, const void *X,
+                           int64_t ldx, void *Y, int64_t ldy, cudaStream_t s) {
     const bool dyn = p->mode == SPMM_DYNAMIC;
-    const size_t smem = g1_fixed_smem<T>() + (size_t)p->k * V * sizeof(T);
+    const size_t smem = g1_fixed_smem<T, I>() + (size_t)p->k * V * sizeof(T);
     static std::atomic<uint64_t> attrs{0};
-    const cudaError_t e = set_smem_attrs_once(attrs, gather1_kernel<T, V>,
-                                              g1_fixed_smem<T>() + g1_x_budget<T>(), false);
+    const cudaError_t e = set_smem_attrs_once(attrs, gather1_kernel<T, V, I>,
+                                              g1_fixed_smem<T, I>() + g1_x_budget<T, I>(), false);
     if (e != cudaSuccess) return e;
     int64_t blocks = (n_items + kG1Warps - 1) / kG1Warps;
     const int64_t cap_blocks = (int64_t)std::max(p->sm_count, 1);
@@ -498,8 +521,8 @@ cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const void *X, i
     if (blocks < 1) blocks = 1;
     // entries the index and value arrays hold (copies past them are not made)
     const int64_t cap = dyn ? p->nnzb_max : p->nnzb;
-    pdl_launch(gather1_kernel<T, V>, dim3((unsigned)blocks), dim3(kG1Warps * 32), smem, s,
-        p->d_items, n_items, p->d_col_idx, (const T *)p->d_packed, cap, (const T *)X, ldx, p->k,
+    pdl_launch(gather1_kernel<T, V, I>, dim3((unsigned)blocks), dim3(kG1Warps * 32), smem, s,
+        p->d_items, n_items, col, (const T *)p->d_packed, cap, (const T *)X, ldx, p->k,
         (T *)Y, ldy, p->d_ws, p->d_ws_row0, dyn ? p->d_counts + kCntItems : nullptr, p->d_status);
     return cudaGetLastError();
 }
@@ -584,8 +607,12 @@ cudaError_t gather_launch(const spmm_plan *p, const void *X, int64_t n, int64_t 
     if (warps == 0) return cudaSuccess;
     if (vecs == 1) {
         // n == V: one vector per X row; X in shared memory when it fits
-        if ((int64_t)p->k * V * (int64_t)sizeof(T) <= g1_x_budget<T>())
-            return gather1_launch<T, V>(p, n_items, X, ldx, Y, ldy, s);
+        // (with the 16-bit column indices where the plan holds them)
+        const int64_t xb = (int64_t)p->k * V * (int64_t)sizeof(T);
+        if (p->d_col16 && xb <= g1_x_budget<T, uint16_t>())
+            return gather1_launch<T, V, uint16_t>(p, n_items, p->d_col16, X, ldx, Y, ldy, s);
+        if (xb <= g1_x_budget<T, int32_t>())
+            return gather1_launch<T, V, int32_t>(p, n_items, p->d_col_idx, X, ldx, Y, ldy, s);
         return gather1g_launch<T, V>(p, n_items, X, ldx, Y, ldy, s);
     }
     pdl_launch(gather_kernel<T, V>, dim3(grid1d(warps * 32, 256)), dim3(256), 0, s, p->d_items,

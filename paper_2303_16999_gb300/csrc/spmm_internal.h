@@ -109,6 +109,7 @@ struct spmm_plan {
             *d_ent_tbeg = nullptr, *d_ent_cover = nullptr, *d_tile_row = nullptr, *d_blk_slot = nullptr,
             *d_blk_off = nullptr, *d_grp_ebeg = nullptr;
     uint32_t *d_srec = nullptr, *d_sprog = nullptr;  // TC: stage records and MMA programs
+    uint16_t *d_col16 = nullptr;   // static GATHER plans, k <= 65536: col_idx in 16 bits
     // TC, batched with plans of the other stage geometry: this plan's stage
     // records cut for that geometry (built on first use), geometry alt_geo
     uint32_t *d_srec_alt = nullptr, *d_sprog_alt = nullptr;

@@ -76,7 +76,7 @@ class PlanInfo(ctypes.Structure):
                                       "ws_rows", "n_reductions", "device_bytes")] + \
         [(n, ctypes.c_int32) for n in ("stage_geometry", "sddmm_form")] + \
         [(n, ctypes.c_int64) for n in ("row_begin", "row_end")] + \
-        [("col_tiles", ctypes.c_int32)]
+        [(n, ctypes.c_int32) for n in ("col_tiles", "index_bytes")]
 
 
 class TuneChoice(ctypes.Structure):

@@ -84,6 +84,10 @@ def test_errors():
     q = _plan(64, 64, 4, [0, 5], [1, 3], kernel="tc", col_tiles=2, n_max=256)
     assert q.info()["col_tiles"] == 2
     assert _plan(64, 64, 4, [0], [1], kernel="tc").info()["col_tiles"] == 0
+    # static b = 1 gather plans read 16-bit column indices while k <= 65536
+    assert _plan(64, 65536, 1, [0, 3], [65535, 7], kernel="gather").info()["index_bytes"] == 2
+    assert _plan(64, 65552, 1, [0], [65551], kernel="gather").info()["index_bytes"] == 4
+    assert _plan(64, 64, 4, [0], [1], kernel="tc").info()["index_bytes"] == 4
     p = _plan(16, 16, 4, [], [])
     assert p.info()["nnzb"] == 0
     # the sampled product refuses host-only plans before touching the device

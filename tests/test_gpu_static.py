@@ -420,3 +420,35 @@ def test_device_wait_times_out_and_recovers(b, d, n, ct):
     assert plan.status() == 0
     Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X)
     assert oracle.normwise_err(Y.cpu(), Yo, oracle.block_fro(vals), X) <= 4e-3
+
+
+@pytest.mark.parametrize("dt", [torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("n", [1, 4, 8])
+def test_gather_index_widths(n, dt):
+    """The shared-memory gather reads a static plan's 16-bit copy of the
+    column indices and a dynamic plan's int32 indices: on the same pattern
+    (same CSR and items) both give the same Y bit for bit, within the bar
+    against the oracle; k spans several 16-bit index ranges' worth of bank
+    patterns (k = 3000)."""
+    m, k = 640, 3000
+    nnzb = wl.nnzb_for(m, k, 1, 1 / 16)
+    c = wl.problem(900 + n, m, k, n, 1, nnzb)
+    wd = S.dtype_code(dt)
+    sp = S.Plan(m, k, n, 1, w_dtype=wd, brow=c["brow"], bcol=c["bcol"], kernel="gather")
+    assert sp.info()["index_bytes"] == 2
+    vals = torch.from_numpy(c["vals"].reshape(-1)).to(dt)
+    sp.pack(vals.cuda())
+    X = torch.from_numpy(c["X"]).to(dt).cuda()
+    Ys = sp.run(X)
+    dp = S.Plan(m, k, n, 1, w_dtype=wd, mode=S.DYNAMIC, nnzb_max=nnzb)
+    assert dp.info()["index_bytes"] == 4
+    pat = (torch.tensor([nnzb], dtype=torch.int32, device="cuda"),
+           torch.from_numpy(np.asarray(c["brow"], np.int32)).cuda(),
+           torch.from_numpy(np.asarray(c["bcol"], np.int32)).cuda())
+    Yd = dp.run(X, values=vals.reshape(-1, 1, 1).cuda(), pattern=pat)
+    torch.cuda.synchronize()
+    assert dp.status() == 0
+    assert torch.equal(Ys.cpu(), Yd.cpu())
+    Yo = oracle.spmm(m, k, 1, c["brow"], c["bcol"], vals.reshape(-1, 1, 1), X.cpu())
+    assert oracle.normwise_err(Ys.cpu(), Yo, oracle.block_fro(vals.reshape(-1, 1, 1)),
+                               X.cpu()) <= TOL[dt]
