@@ -472,20 +472,22 @@ __device__ __forceinline__ GroupOff load_group_off(int g, const int32_t *grp_row
     return o;
 }
 
-// Group g's entries (ascending tile column), slots (ascending rows, one per
-// tile), block -> slot / offset, items and workspace / reduction records,
-// from its column masks (whole CTA of 1024 threads; slot_of[kt] in shared
-// memory; [s0, s1) the group's CSR slots; o its offsets; ent_s, when
-// given: the group's entries' columns, first tiles and covers again, in
-// three arrays of kt in shared memory, from the group's first entry).
-__device__ void group_fill(int g, const GroupOff &o, int32_t kt, int32_t T, int32_t b,
-                           const int32_t *row_ptr, const int32_t *col_idx, const int32_t *perm,
-                           const uint32_t *colmask, int32_t *slot_of, int32_t s0, int32_t s1,
-                           int32_t *ent_col, int32_t *ent_tbeg, int32_t *ent_cover,
-                           int32_t *tile_row, int32_t *blk_slot, int32_t *blk_off, int32_t *items,
-                           int64_t *ws_row0, int32_t *red, const int32_t *rp_s = nullptr,
-                           int32_t *pk = nullptr, int32_t *ent_s = nullptr) {
-    const int32_t t0 = o.row0, nrows = o.rows;
+// Group g's fill, in three parts (whole CTA of 1024 threads for the first;
+// slot_of[kt] in shared memory; [s0, s1) the group's CSR slots; o its
+// offsets):
+//  * group_fill_entries: entries (ascending tile column), slots (ascending
+//    rows, one per tile) and slot_of from its column masks; with ent_s, the
+//    entries' columns, first tiles and covers again, in three arrays of kt
+//    in shared memory, from the group's first entry;
+//  * group_fill_slots: block -> slot / offset (indexed by user position),
+//    by threads [t0, t0 + nt) of the CTA; rp_s: the group's row pointers in
+//    shared memory, rp_s[i] = row_ptr of block row row0 * T + i; pk: per
+//    slot of the group, the block's user index, tile slot and offset;
+//  * group_fill_items (one thread): items (near-equal chunks of the
+//    group's entries) and workspace / reduction records.
+__device__ void group_fill_entries(const GroupOff &o, int32_t kt, const uint32_t *colmask,
+                                   int32_t *slot_of, int32_t *ent_col, int32_t *ent_tbeg,
+                                   int32_t *ent_cover, int32_t *tile_row, int32_t *ent_s) {
     // column prefix over entries and slots, in chunks of blockDim (1024)
     int64_t eb = o.ebeg, sb = o.sbeg;
     for (int32_t c0 = 0; c0 < kt; c0 += 1024) {
@@ -500,7 +502,7 @@ __device__ void group_fill(int g, const GroupOff &o, int32_t kt, int32_t T, int3
             ent_col[e] = c;
             ent_tbeg[e] = (int32_t)(sb + xs);
             ent_cover[e] = (int32_t)(mk | (mk << 16));
-            if (ent_s) {   // the same, from the group's first entry
+            if (ent_s) {
                 ent_s[e - o.ebeg] = c;
                 ent_s[kt + e - o.ebeg] = (int32_t)(sb + xs);
                 ent_s[2 * kt + e - o.ebeg] = (int32_t)(mk | (mk << 16));
@@ -515,12 +517,15 @@ __device__ void group_fill(int g, const GroupOff &o, int32_t kt, int32_t T, int3
         eb += te;
         sb += ts;
     }
-    __syncthreads();
-    // blocks of the group -> slot and offset (indexed by user position)
-    // (rp_s: the group's row pointers in shared memory, rp_s[i] = row_ptr of
-    // block row t0 * T + i; pk: per slot of the group, the block's user
-    // index, tile slot and offset, for the caller to pack from)
-    for (int32_t s = s0 + threadIdx.x; s < s1; s += blockDim.x) {
+}
+
+__device__ void group_fill_slots(const GroupOff &o, int32_t T, int32_t b, const int32_t *row_ptr,
+                                 const int32_t *col_idx, const int32_t *perm,
+                                 const uint32_t *colmask, const int32_t *slot_of, int32_t s0,
+                                 int32_t s1, int32_t *blk_slot, int32_t *blk_off,
+                                 const int32_t *rp_s, int32_t *pk, int t0n, int nt) {
+    const int32_t t0 = o.row0, nrows = o.rows;
+    for (int32_t s = s0 + (int32_t)threadIdx.x - t0n; s < s1; s += nt) {
         int32_t lo = t0 * T, hi = (t0 + nrows) * T;
         while (hi - lo > 1) {
             const int32_t mid = (lo + hi) >> 1;
@@ -540,9 +545,10 @@ __device__ void group_fill(int g, const GroupOff &o, int32_t kt, int32_t T, int3
             pk[3 * (s - s0) + 2] = off;
         }
     }
-    __syncthreads();   // the masks may be reused by the calling CTA after this
-    if (threadIdx.x != 0) return;
-    // items: near-equal chunks of the group's entries
+}
+
+__device__ void group_fill_items(int g, const GroupOff &o, int32_t *items, int64_t *ws_row0,
+                                 int32_t *red) {
     const int32_t e0 = o.ebeg, L = o.eend - e0, nch = nchunks(L, o.C);
     const int32_t base = L / nch, rem = L % nch;
     int32_t e = e0;
@@ -556,7 +562,7 @@ __device__ void group_fill(int g, const GroupOff &o, int32_t kt, int32_t T, int3
         it[3] = c;
         it[4] = nch;
         it[5] = ws;
-        if (ws >= 0) ws_row0[ws] = o.wrow + (int64_t)c * nrows * kTile;
+        if (ws >= 0) ws_row0[ws] = o.wrow + (int64_t)c * o.rows * kTile;
         e += sz;
     }
     if (nch > 1) {
@@ -588,8 +594,11 @@ __global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *
                                       grp_wbeg, grp_wrow, grp_rbeg, counts, (int32_t)gridDim.x);
     int32_t s0, s1;
     group_colmask(g, kt, T, grp_row0, grp_rows, row_ptr, col_idx, colmask, &s0, &s1);
-    group_fill(g, o, kt, T, b, row_ptr, col_idx, perm, colmask, slot_of, s0, s1, ent_col,
-               ent_tbeg, ent_cover, tile_row, blk_slot, blk_off, items, ws_row0, red);
+    group_fill_entries(o, kt, colmask, slot_of, ent_col, ent_tbeg, ent_cover, tile_row, nullptr);
+    __syncthreads();
+    group_fill_slots(o, T, b, row_ptr, col_idx, perm, colmask, slot_of, s0, s1, blk_slot, blk_off,
+                     nullptr, nullptr, 0, (int)blockDim.x);
+    if (threadIdx.x == 0) group_fill_items(g, o, items, ws_row0, red);
 }
 
 // ------------------------------------------------ fused (cooperative) ---
@@ -609,12 +618,13 @@ __global__ void dyn_group_fill(int32_t kt, int32_t T, int32_t b, const int32_t *
 //      group, the column masks (from the bitmap) and the entry / slot
 //      counts                                                       | barrier,
 //      then CTA 0 scans the groups (offsets, chunk size)
-//   D. per group: entries, slots, block -> slot, items (the chain's fill,
-//      with the group's row pointers and its blocks' slots in shared
-//      memory), the group's tiles cleared where blocks do not fill them;
-//      then, side by side, the stage records of the group's items (8
-//      warps; an item's entries are its group's, so no barrier is
-//      needed) and its blocks' values packed, a warp per block (the rest).
+//   D. per group: the group's tiles cleared where blocks do not fill
+//      them, its entries and slots (the chain's fill); then, side by side,
+//      the stage records of the group's items (12 warps; an item's entries
+//      are its group's, so no barrier is needed) and, on the other 20
+//      warps, block -> slot, the items, and the blocks' values packed, a
+//      warp per block (the group's row pointers and its blocks' slots in
+//      shared memory).
 // Barrier: each CTA counts its arrival on one counter.  Where no step
 // follows, every CTA waits for the count; where one does (a scan), CTA 0
 // waits, runs it and publishes the barrier's generation, which the other
@@ -969,9 +979,13 @@ __device__ void pack_group(const DynFusedArgs &a, int32_t s0, int32_t s1, const 
     }
 }
 
-// Named barrier 1 over the first n threads of the CTA.
+// Named barrier 1 over the first n threads of the CTA (the stage warps),
+// named barrier 2 over the packing warps (n threads).
 __device__ __forceinline__ void sync_first(int n) {
     asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+}
+__device__ __forceinline__ void sync_pack(int n) {
+    asm volatile("bar.sync 2, %0;" ::"r"(n) : "memory");
 }
 
 // The stage records of group g's work items (the near-equal chunks of its
@@ -1142,15 +1156,21 @@ __global__ void __launch_bounds__(1024, 1) dyn_tc_fused_kernel(const __grid_cons
         }
         const int32_t s0 = rp_s[0], s1 = rp_s[nrows * a.T];
         const bool stage = s1 - s0 <= kFusedPk;
-        group_fill(g, go, a.kt, a.T, a.b, a.row_ptr, a.col_idx, a.perm, colmask, slot_of, s0, s1,
-                   a.ent_col, a.ent_tbeg, a.ent_cover, a.tile_row, a.blk_slot, a.blk_off,
-                   a.items, a.ws_row0, a.red, rp_s, stage ? pk : nullptr, ent_s);
-        __syncthreads();   // this CTA's entries, block -> slot writes and cleared tiles
-        if (warp < kStageWarps)
+        group_fill_entries(go, a.kt, colmask, slot_of, a.ent_col, a.ent_tbeg, a.ent_cover,
+                           a.tile_row, ent_s);
+        __syncthreads();   // the group's entries and slot_of, and the cleared tiles
+        if (warp < kStageWarps) {
             build_group_stages(a, go, kStageWarps, bcounts, ent_s);
-        else
+        } else {
+            // the packing warps map the group's blocks to their slots, then pack
+            const int t0n = kStageWarps * 32, nt = (32 - kStageWarps) * 32;
+            group_fill_slots(go, a.T, a.b, a.row_ptr, a.col_idx, a.perm, colmask, slot_of, s0, s1,
+                             a.blk_slot, a.blk_off, rp_s, stage ? pk : nullptr, t0n, nt);
+            if ((int)threadIdx.x == t0n) group_fill_items(g, go, a.items, a.ws_row0, a.red);
+            sync_pack(nt);
             pack_group(a, s0, s1, stage ? pk : nullptr, kStageWarps, 32 - kStageWarps,
                        pack_buf);
+        }
         __syncthreads();
     }
 }
