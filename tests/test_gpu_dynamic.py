@@ -281,17 +281,19 @@ def test_fused_repartition_equals_launch_chain(b, dt, w8):
 
 
 @pytest.mark.parametrize("b,m,k,groups", [(16, 208, 640, 0), (8, 80, 48, 0), (4, 4096, 4096, 0),
-                                          (4, 4096, 2048, 0), (16, 33024, 128, 2064)])
+                                          (4, 4096, 2048, 0), (16, 2048, 1024, 100),
+                                          (16, 41600, 128, 2600)])
 def test_fused_repartition_scan_paths(b, m, k, groups):
-    """The fused launch's two scans on each of their paths: a bitmap whose
-    word count is not a multiple of four (b = 16, 13 block rows of two
-    words; b = 8, 10 block rows of one word), runs longer than the words a
-    thread keeps in registers, scanned by every CTA for itself (b = 4,
-    m = 4096, k = 2048: 16384 words) and by CTA 0 alone (b = 4,
-    m = k = 4096: 32768 words, past the per-CTA limit), and more groups
-    than the per-CTA group scan takes (2064 one-row groups: CTA 0 scans).
-    Arrays and Y equal the launch chain's bit for bit; the CSR equals the
-    oracle's; Y is within the normwise bar."""
+    """The fused launch's scans and stage-record paths: a bitmap whose word
+    count is not a multiple of four (b = 16, 13 block rows of two words;
+    b = 8, 10 block rows of one word), runs longer than the words a thread
+    keeps in registers, scanned by every CTA for itself (b = 4, m = 4096,
+    k = 2048: 16384 words) and by CTA 0 alone (b = 4, m = k = 4096: 32768
+    words, past the per-CTA limit); 100 near-equal groups of one or two
+    tile rows; and more groups than the per-CTA group scan takes (2600
+    one-row groups: CTA 0 scans).  Arrays and Y equal the launch chain's
+    bit for bit; the CSR equals the oracle's; Y is within the normwise
+    bar."""
     n = 72
     dt = torch.bfloat16
     cap = max(wl.nnzb_for(m, k, b, 1 / 4), 1)
