@@ -4,7 +4,6 @@
 // (The paper benchmarks single products; this is the deployment form the
 // library adds around them.)
 #include <cuda_runtime.h>
-#include <sys/prctl.h>
 
 #include <algorithm>
 #include <chrono>
@@ -28,6 +27,10 @@ double now_us() {
                std::chrono::steady_clock::now().time_since_epoch())
         .count();
 }
+
+// The batcher spins (yielding) this long after its last launch before it
+// blocks on its condition variable.
+constexpr double kSpinUs = 200.0;
 
 // First-fit allocator over the staging pool, in 256-byte units.
 struct Pool {
@@ -129,6 +132,7 @@ struct serve_server {
 void serve_server::batcher_loop() {
     cudaSetDevice(dev);
     std::unique_lock<std::mutex> lk(mu);
+    double last_active = now_us();
     while (!stop) {
         int slot = -1;
         for (int i = 0; i < cfg.max_inflight; ++i)
@@ -137,9 +141,19 @@ void serve_server::batcher_loop() {
                 break;
             }
         if (queue.empty() || slot < 0) {
-            cv_batcher.wait(lk);
+            // wait for a request or a free slot: spin (yielding) for a while
+            // after the last activity, then block; a blocked thread's wake-up
+            // would add its latency to the next request's
+            if (now_us() - last_active < kSpinUs) {
+                lk.unlock();
+                std::this_thread::yield();
+                lk.lock();
+            } else {
+                cv_batcher.wait(lk);
+            }
             continue;
         }
+        last_active = now_us();
         // admit from the head of the queue while the launch and the budget allow
         Launch L;
         L.slot = slot;
@@ -278,10 +292,10 @@ void serve_server::batcher_loop() {
 
 void serve_server::completer_loop() {
     cudaSetDevice(dev);
-    // The poll below sleeps 5 us between event queries; with the default
-    // 50 us timer slack of a Linux thread each sleep lasts about 55 us,
-    // which a request's latency pays on top of its copies and product.
-    prctl(PR_SET_TIMERSLACK, 1000UL, 0UL, 0UL, 0UL);   // 1 us, this thread only
+    // While launches are in flight their events are polled back to back
+    // (yielding between rounds): a timed sleep here lasted about 55 us (a
+    // Linux thread's default timer slack is 50 us), which every request's
+    // latency paid.
     std::unique_lock<std::mutex> lk(mu);
     while (true) {
         if (inflight.empty()) {
@@ -319,7 +333,7 @@ void serve_server::completer_loop() {
             cv_batcher.notify_all();
         } else {
             lk.unlock();
-            std::this_thread::sleep_for(std::chrono::microseconds(5));
+            std::this_thread::yield();
             lk.lock();
         }
     }
