@@ -979,11 +979,11 @@ def run_gather_small_n(torch, S, wl, dev, peaks, reps=15):
     plan = S.Plan(m, k, 32, 1, w_dtype=S.F16, brow=c["brow"], bcol=c["bcol"], kernel="gather")
     plan.pack(torch.from_numpy(c["vals"].reshape(-1)).half().to(dev))
     # bytes per column index each point's kernel reads: the plan's 16-bit
-    # copy where X stays in shared memory (n = 1 at this k), else int32
+    # copy where X stays in shared memory (n = 1 and 4 at this k), else int32
     ib16 = plan.info()["index_bytes"]
 
     def idx_bytes(n):
-        return ib16 if n == 1 else 4
+        return ib16 if n in (1, 4) else 4
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     out = []
     for n in (1, 4, 16, 32):

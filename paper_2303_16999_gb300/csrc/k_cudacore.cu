@@ -190,7 +190,8 @@ __global__ void __launch_bounds__(256) gather_kernel(
 // of 16-bit values, 31 KB of FP32) is copied into shared memory once per CTA
 // (by cp.async when its rows are contiguous), so the X gathers are
 // shared-memory reads.
-constexpr int kG1Stages = 6;
+constexpr int kG1Stages = 6;                         // ring stages per warp (a 5-stage
+                                                     // variant leaves X 16 KB more)
 constexpr int kG1Warps = 16;
 constexpr int kG1Chunk = 256;                        // non-zeros per chunk, 8 per lane
 // one stage: the chunk's indices (I: int32, or the 16-bit copy of static
@@ -198,20 +199,25 @@ constexpr int kG1Chunk = 256;                        // non-zeros per chunk, 8 p
 template <typename T, typename I> __host__ __device__ constexpr int g1_stage_bytes() {
     return kG1Chunk * ((int)sizeof(I) + (int)sizeof(T));
 }
-template <typename T, typename I> __host__ __device__ constexpr int g1_ring_bytes() {
-    return kG1Stages * g1_stage_bytes<T, I>();
+template <typename T, typename I, int S = kG1Stages>
+__host__ __device__ constexpr int g1_ring_bytes() {
+    return S * g1_stage_bytes<T, I>();
 }
 
 struct G1Meta {
     int32_t beg, end, row, slot, base, last, pad0, pad1;
 };
-constexpr int kG1MetaBytes = kG1Warps * kG1Stages * (int)sizeof(G1Meta);
-template <typename T, typename I> __host__ __device__ constexpr int g1_fixed_smem() {
-    return kG1Warps * g1_ring_bytes<T, I>() + kG1MetaBytes;
+template <int S = kG1Stages> __host__ __device__ constexpr int g1_meta_bytes() {
+    return kG1Warps * S * (int)sizeof(G1Meta);
+}
+template <typename T, typename I, int S = kG1Stages>
+__host__ __device__ constexpr int g1_fixed_smem() {
+    return kG1Warps * g1_ring_bytes<T, I, S>() + g1_meta_bytes<S>();
 }
 // shared memory left for X (of the 227 KB a CTA may hold, 1 KB spare)
-template <typename T, typename I> __host__ __device__ constexpr int g1_x_budget() {
-    return 226 * 1024 - g1_fixed_smem<T, I>();
+template <typename T, typename I, int S = kG1Stages>
+__host__ __device__ constexpr int g1_x_budget() {
+    return 226 * 1024 - g1_fixed_smem<T, I, S>();
 }
 static_assert(g1_x_budget<float, int32_t>() >= 16 * 1024, "room for X");
 
@@ -224,7 +230,7 @@ __device__ __forceinline__ void cp_async16_zfill(void *dst, const void *src, int
                  : "memory");
 }
 
-template <typename T, int V, typename I>
+template <typename T, int V, typename I, int S>
 __global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
     const int32_t *__restrict__ items, int64_t n_items, const I *__restrict__ col_idx,
     const T *__restrict__ vals, int64_t cap, const T *__restrict__ X, int64_t ldx, int64_t k,
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
     pdl_enter();
     constexpr int VB = 8 * (int)sizeof(T);          // value bytes per lane per chunk (16 or 32)
     constexpr int IB = 8 * (int)sizeof(I);          // index bytes per lane per chunk (16 or 32)
-    constexpr int kStage = g1_stage_bytes<T, I>(), kRing = g1_ring_bytes<T, I>();
+    constexpr int kStage = g1_stage_bytes<T, I>(), kRing = g1_ring_bytes<T, I, S>();
     extern __shared__ __align__(128) uint8_t g1_smem[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (n_items_dev) {
@@ -241,7 +247,7 @@ __global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
         n_items = min(n_items, (int64_t)*n_items_dev);
     }
     uint8_t *ring = g1_smem + warp * kRing;
-    G1Meta *meta = reinterpret_cast<G1Meta *>(g1_smem + kG1Warps * kRing) + warp * kG1Stages;
+    G1Meta *meta = reinterpret_cast<G1Meta *>(g1_smem + kG1Warps * kRing) + warp * S;
     const int64_t W = (int64_t)gridDim.x * kG1Warps;
     // the item being requested (c_*) and the next one's header (x_*), read
     // one item ahead so the request stream never waits on a header
@@ -258,7 +264,7 @@ __global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
         x_row = d[0], x_beg = d[1], x_end = d[2], x_slot = d[5];
     }
     // X first (its own cp.async group, so it can be waited for alone)
-    T *xs = reinterpret_cast<T *>(g1_smem + g1_fixed_smem<T, I>());
+    T *xs = reinterpret_cast<T *>(g1_smem + g1_fixed_smem<T, I, S>());
     const int64_t xbytes = k * V * (int64_t)sizeof(T);
     const bool xbulk = ldx == V && ((uintptr_t)X % 16) == 0;
     if (xbulk) {
@@ -281,7 +287,7 @@ __global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
     auto issue_next = [&]() {
         if (it < n_items) {
             const int s = is;
-            is = is + 1 == kG1Stages ? 0 : is + 1;
+            is = is + 1 == S ? 0 : is + 1;
             uint8_t *st = ring + s * kStage;
             const int32_t pos = c_pos + 8 * lane;
             // entries of this lane's 8 that the arrays hold; the others lie
@@ -315,9 +321,9 @@ __global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
 #pragma unroll 1
-    for (int q = 0; q < kG1Stages; ++q) issue_next();
+    for (int q = 0; q < S; ++q) issue_next();
     // X landed (every thread's share), the ring's chunks may still be in flight
-    asm volatile("cp.async.wait_group %0;" ::"n"(kG1Stages) : "memory");
+    asm volatile("cp.async.wait_group %0;" ::"n"(S) : "memory");
     __syncthreads();
     float acc[V];
 #pragma unroll
@@ -325,11 +331,11 @@ __global__ void __launch_bounds__(kG1Warps * 32, 1) gather1_kernel(
     int cs = 0;                                       // ring stage of chunk t
 #pragma unroll 1
     for (int32_t t = 0; t < issued; ++t) {
-        asm volatile("cp.async.wait_group %0;" ::"n"(kG1Stages - 1) : "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(S - 1) : "memory");
         __syncwarp();
         const uint8_t *st = ring + cs * kStage;
         const G1Meta m = meta[cs];
-        cs = cs + 1 == kG1Stages ? 0 : cs + 1;
+        cs = cs + 1 == S ? 0 : cs + 1;
         int32_t cq[8];
         if constexpr (sizeof(I) == 4) {
             const int4 c0 = *reinterpret_cast<const int4 *>(st + lane * IB);
@@ -506,14 +512,15 @@ __global__ void __launch_bounds__(512, SPMM_G1_BLOCKS) gather1g_kernel(
 }
 
 // X in shared memory: one 16-warp CTA per SM, streaming through the ring.
-template <typename T, int V, typename I>
+template <typename T, int V, typename I, int S = kG1Stages>
 cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const I *col, const void *X,
                            int64_t ldx, void *Y, int64_t ldy, cudaStream_t s) {
     const bool dyn = p->mode == SPMM_DYNAMIC;
-    const size_t smem = g1_fixed_smem<T, I>() + (size_t)p->k * V * sizeof(T);
+    const size_t smem = g1_fixed_smem<T, I, S>() + (size_t)p->k * V * sizeof(T);
     static std::atomic<uint64_t> attrs{0};
-    const cudaError_t e = set_smem_attrs_once(attrs, gather1_kernel<T, V, I>,
-                                              g1_fixed_smem<T, I>() + g1_x_budget<T, I>(), false);
+    const cudaError_t e = set_smem_attrs_once(attrs, gather1_kernel<T, V, I, S>,
+                                              g1_fixed_smem<T, I, S>() + g1_x_budget<T, I, S>(),
+                                              false);
     if (e != cudaSuccess) return e;
     int64_t blocks = (n_items + kG1Warps - 1) / kG1Warps;
     const int64_t cap_blocks = (int64_t)std::max(p->sm_count, 1);
@@ -521,7 +528,7 @@ cudaError_t gather1_launch(const spmm_plan *p, int64_t n_items, const I *col, co
     if (blocks < 1) blocks = 1;
     // entries the index and value arrays hold (copies past them are not made)
     const int64_t cap = dyn ? p->nnzb_max : p->nnzb;
-    pdl_launch(gather1_kernel<T, V, I>, dim3((unsigned)blocks), dim3(kG1Warps * 32), smem, s,
+    pdl_launch(gather1_kernel<T, V, I, S>, dim3((unsigned)blocks), dim3(kG1Warps * 32), smem, s,
         p->d_items, n_items, col, (const T *)p->d_packed, cap, (const T *)X, ldx, p->k,
         (T *)Y, ldy, p->d_ws, p->d_ws_row0, dyn ? p->d_counts + kCntItems : nullptr, p->d_status);
     return cudaGetLastError();
@@ -611,6 +618,9 @@ cudaError_t gather_launch(const spmm_plan *p, const void *X, int64_t n, int64_t 
         const int64_t xb = (int64_t)p->k * V * (int64_t)sizeof(T);
         if (p->d_col16 && xb <= g1_x_budget<T, uint16_t>())
             return gather1_launch<T, V, uint16_t>(p, n_items, p->d_col16, X, ldx, Y, ldy, s);
+        if (p->d_col16 && xb <= g1_x_budget<T, uint16_t, kG1Stages - 1>())
+            return gather1_launch<T, V, uint16_t, kG1Stages - 1>(p, n_items, p->d_col16, X, ldx,
+                                                                 Y, ldy, s);
         if (xb <= g1_x_budget<T, int32_t>())
             return gather1_launch<T, V, int32_t>(p, n_items, p->d_col_idx, X, ldx, Y, ldy, s);
         return gather1g_launch<T, V>(p, n_items, X, ldx, Y, ldy, s);

@@ -263,10 +263,11 @@ def test_full_size_sweep_integers_exact(b, d):
     checks.exact_rows(Y, rows, k, b, c["brow"], c["bcol"], c["vals"], c["X"], dt)
 
 
-@pytest.mark.parametrize("n", [1, 32])
+@pytest.mark.parametrize("n", [1, 4, 32])
 def test_gather_large_small_n_sampled(n):
     """The configuration the benchmark's small-n gather section times:
-    m = k = 16384, d = 1/16, FP16; 4 sampled rows against the oracle."""
+    m = k = 16384, d = 1/16, FP16; sampled rows against the oracle (n = 4:
+    X fills the five-stage ring's shared memory)."""
     m = k = 16384
     c = wl.problem(7, m, k, 32, 1, wl.nnzb_for(m, k, 1, 1 / 16))
     dt = torch.float16
