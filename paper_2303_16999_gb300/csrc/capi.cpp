@@ -885,6 +885,13 @@ spmm_status spmm_run(spmm_plan *plan, const void *d_values, const float *d_scale
         if (n > 0) {
             st = launch_product(plan, d_X, n, ldx, d_Y, ldy, s);
             if (st != SPMM_OK) return st;
+            // the product's reduction launch cleared the fused launch's
+            // barrier words for the next call
+            if (plan->dyn_fused) plan->dyn.bar_clean = plan->n_red > 0;
+        } else if (plan->dyn_fused) {
+            e = cudaMemsetAsync(plan->dyn.bar, 0, sizeof(int32_t) * 2, s);
+            if (e != cudaSuccess) return cuda_fail(e, "barrier reset");
+            plan->dyn.bar_clean = true;
         }
         return finish_call(plan, s);
     }

@@ -565,15 +565,22 @@ __global__ void restride_kernel(const E *__restrict__ src, E *__restrict__ dst, 
 
 // ------------------------------------------------- split-row reduction ---
 // Rows split over several items: Y = sum of the chunks' FP32 partials in
-// chunk order (deterministic), converted once.
+// chunk order (deterministic), converted once.  bar_reset (dynamic plans
+// with the fused re-partition): the re-partition's barrier words, zeroed
+// here for the plan's next call; this launch follows the re-partition and
+// the product in every call with a product, aborted or not.
 template <typename T>
 __global__ void reduce_kernel(const int32_t *__restrict__ red, const int32_t *__restrict__ grp_row0,
                               const int32_t *__restrict__ grp_rows, int rows_per_unit,
                               const float *__restrict__ ws, const int64_t *__restrict__ ws_row0,
                               T *__restrict__ Y, int64_t ldy, int64_t n, int64_t n_red,
                               const int32_t *__restrict__ n_red_dev,
-                              const int32_t *__restrict__ status) {
+                              const int32_t *__restrict__ status, int32_t *bar_reset) {
     pdl_enter();
+  if (bar_reset && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && threadIdx.x == 0) {
+      bar_reset[0] = 0;
+      bar_reset[1] = 0;
+  }
   if (n_red_dev) {
       if (*status != 0) return;
       n_red = min(n_red, (int64_t)*n_red_dev);
@@ -774,21 +781,22 @@ cudaError_t launch_reduce(const spmm_plan *p, int64_t n, void *Y, int64_t ldy, c
     dim3 grid(gx, (unsigned)gy, gz);
     const int32_t *r0 = tc ? p->d_grp_row0 : nullptr;
     const int32_t *rn = tc ? p->d_grp_rows : nullptr;
+    int32_t *bar = dyn && p->dyn_fused ? p->dyn.bar : nullptr;
     switch (p->xdt) {
         case SPMM_F32:
             pdl_launch(reduce_kernel<float>, dim3(grid), dim3(128), 0, s, p->d_red, r0, rn,
                 rows_per_unit, p->d_ws, p->d_ws_row0, (float *)Y, ldy, n, n_red, n_red_dev,
-                p->d_status);
+                p->d_status, bar);
             break;
         case SPMM_F16:
             pdl_launch(reduce_kernel<__half>, dim3(grid), dim3(128), 0, s, p->d_red, r0, rn,
                 rows_per_unit, p->d_ws, p->d_ws_row0, (__half *)Y, ldy, n, n_red, n_red_dev,
-                p->d_status);
+                p->d_status, bar);
             break;
         case SPMM_BF16:
             pdl_launch(reduce_kernel<__nv_bfloat16>, dim3(grid), dim3(128), 0, s, p->d_red, r0, rn,
                 rows_per_unit, p->d_ws, p->d_ws_row0, (__nv_bfloat16 *)Y, ldy, n, n_red, n_red_dev,
-                p->d_status);
+                p->d_status, bar);
             break;
         default: return cudaErrorInvalidValue;
     }

@@ -1314,8 +1314,11 @@ cudaError_t launch_dynamic_tc_fused(spmm_plan *p, const spmm_dpattern *dp, const
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     const int grid = std::min(per_sm * std::max(p->sm_count, 1), kFusedMaxCtas);
     // the counts are cleared by the launch itself (step A); the barrier's
-    // counter and generation here
-    e = cudaMemsetAsync(d.bar, 0, sizeof(int32_t) * 2, s);
+    // counter and generation here, unless the plan's last call left them
+    // zero (its reduction launch, or a memset after a call without a
+    // product, clears them)
+    if (!d.bar_clean) e = cudaMemsetAsync(d.bar, 0, sizeof(int32_t) * 2, s);
+    d.bar_clean = false;
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);

@@ -82,10 +82,14 @@ struct DynBufs {
     int64_t *grp_wrow = nullptr;
     // fused re-partition (dynamic TC): block-column bitmap of every block
     // row (mb x ceil(kb/32) words), the groups' column masks (G x kt words)
-    // and the grid barrier's flags (one per CTA, then the generation word)
+    // and the grid barrier's arrival counter and generation word
     uint32_t *bits = nullptr, *gmask = nullptr;
     int32_t *wpre = nullptr;   // per bitmap word: blocks before it in row-major order
     int32_t *bar = nullptr;
+    // host: the barrier words are zero in stream order (the last call's
+    // reduction launch, or a memset after a call without a product, cleared
+    // them); else the next fused launch clears them first
+    bool bar_clean = false;
     int64_t items_cap = 0, ws_slots_cap = 0, red_cap = 0;
 };
 constexpr int kFusedMaxCtas = 128;           // CTAs of the fused re-partition (at most)

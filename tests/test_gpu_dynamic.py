@@ -357,3 +357,63 @@ def test_fused_repartition_wait_times_out_and_recovers():
     Yo = oracle.spmm(m, k, b, c["brow"], c["bcol"], vals, X)
     assert oracle.normwise_err(Y.cpu(), Yo, oracle.block_fro(vals), X) <= 4e-3
     _check_arrays(plan, m, k, b, c["brow"], c["bcol"])
+
+
+def test_fused_barrier_words_across_calls_and_graph_replays():
+    """The fused re-partition's barrier words are cleared by the previous
+    call (its reduction launch, or a memset after a call without a
+    product) instead of before each launch.  Calls with and without a
+    product in any order, and a captured call replayed between eager calls,
+    all give the oracle's Y and plan arrays."""
+    m = k = 1024
+    n = 64
+    b = 16
+    cap = wl.nnzb_for(m, k, b, 1 / 16)
+    dt = torch.bfloat16
+    plan = S.Plan(m, k, n, b, w_dtype=S.BF16, mode=S.DYNAMIC, nnzb_max=cap)
+    cases = []
+    for call in range(3):
+        c = wl.dynamic_call(7300 + call, m=m, k=k, n=n, b=b, d_max=1 / 16)
+        vals = torch.from_numpy(c["vals"]).to(dt)
+        vd = torch.zeros((cap, b, b), dtype=dt)
+        vd[:len(vals)] = vals
+        cases.append(dict(c=c, vals=vals, vd=vd.cuda(), X=torch.from_numpy(c["X"]).to(dt),
+                          pat=_dev_pattern(c["brow"], c["bcol"], cap)))
+
+    def check(Y, q):
+        Yo = oracle.spmm(m, k, b, q["c"]["brow"], q["c"]["bcol"], q["vals"], q["X"])
+        assert oracle.normwise_err(Y.cpu(), Yo, oracle.block_fro(q["vals"]), q["X"]) <= 4e-3
+        _check_arrays(plan, m, k, b, q["c"]["brow"], q["c"]["bcol"])
+
+    Xe = torch.empty((k, 0), dtype=dt, device="cuda")
+    Ye = torch.empty((m, 0), dtype=dt, device="cuda")
+    for q in (cases[0], cases[1], cases[1], cases[2]):
+        plan.run(Xe, Ye, values=q["vd"], pattern=q["pat"])         # no product
+        Y = plan.run(q["X"].cuda(), values=q["vd"], pattern=q["pat"])
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        check(Y, q)
+    # a captured call, replayed with eager calls (with and without a product) between
+    q = cases[0]
+    Xd = q["X"].cuda()
+    Yg = torch.empty((m, n), dtype=dt, device="cuda")
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        plan.run(Xd, Yg, values=q["vd"], pattern=q["pat"], stream=st)
+        st.synchronize()
+        with torch.cuda.graph(g, stream=st):
+            plan.run(Xd, Yg, values=q["vd"], pattern=q["pat"], stream=st)
+    torch.cuda.synchronize()
+    for other in (cases[1], cases[2], cases[1]):
+        plan.run(Xe, Ye, values=other["vd"], pattern=other["pat"])
+        Y = plan.run(other["X"].cuda(), values=other["vd"], pattern=other["pat"])
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        check(Y, other)
+        Yg.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        check(Yg, q)
