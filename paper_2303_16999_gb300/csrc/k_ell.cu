@@ -98,26 +98,51 @@ __device__ __forceinline__ uint32_t ell_idesc(uint32_t fmt) {
 
 // One warp per block row: 32 slots per step, ascending order checked
 // against the previous slot (a shuffle, and the last slot of the step before).
+// words (when given): two words, zero between calls; each block ORs its
+// finding into words[0] and takes a ticket from words[1], and the last
+// block stores the call's status (0 or the pattern error) and zeroes both
+// words, so that no memset has to clear the status before the launch.
+// Without words the status must be zero already and only errors are set.
 __global__ void ell_validate_kernel(const int32_t *cols, int32_t mb, int32_t E, int32_t kb,
-                                    int32_t *status) {
+                                    int32_t *status, int32_t *words) {
     pdl_enter();
     const int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (r >= mb) return;
-    const int32_t *c = cols + r * E;
-    int32_t carry = -1;          // the previous slot's value (-1 before the first)
     bool bad = false;
-    for (int32_t e0 = 0; e0 < E; e0 += 32) {
-        const int32_t v = e0 + lane < E ? __ldg(c + e0 + lane) : -1;
-        int32_t prev = __shfl_up_sync(0xffffffffu, v, 1);
-        if (lane == 0) prev = carry;
-        const bool in = e0 + lane < E;
-        // a block must follow a block with a smaller column; padding is -1 only
-        bad |= in && (v < -1 || v >= kb || (v >= 0 && (e0 + lane > 0) && prev >= v) ||
-                      (v >= 0 && e0 + lane > 0 && prev == -1));
-        carry = __shfl_sync(0xffffffffu, v, 31);
+    if (r < mb) {
+        const int32_t *c = cols + r * E;
+        int32_t carry = -1;          // the previous slot's value (-1 before the first)
+        for (int32_t e0 = 0; e0 < E; e0 += 32) {
+            const int32_t v = e0 + lane < E ? __ldg(c + e0 + lane) : -1;
+            int32_t prev = __shfl_up_sync(0xffffffffu, v, 1);
+            if (lane == 0) prev = carry;
+            const bool in = e0 + lane < E;
+            // a block must follow a block with a smaller column; padding is -1 only
+            bad |= in && (v < -1 || v >= kb || (v >= 0 && (e0 + lane > 0) && prev >= v) ||
+                          (v >= 0 && e0 + lane > 0 && prev == -1));
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(status, 0, (int32_t)kDevPattern);
+    const bool warp_bad = __any_sync(0xffffffffu, bad);
+    if (!words) {
+        if (warp_bad && lane == 0) atomicCAS(status, 0, (int32_t)kDevPattern);
+        return;
+    }
+    __shared__ int blk_bad;
+    if (threadIdx.x == 0) blk_bad = 0;
+    __syncthreads();
+    if (warp_bad && lane == 0) atomicOr(&blk_bad, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (blk_bad) atomicOr(&words[0], 1);
+        __threadfence();
+        if (atomicAdd(&words[1], 1) == (int)gridDim.x - 1) {
+            __threadfence();
+            const int any_bad = atomicExch(&words[0], 0);
+            *status = any_bad ? (int32_t)kDevPattern : 0;
+            words[1] = 0;
+        }
+    }
 }
 
 template <typename T>
@@ -373,10 +398,21 @@ cudaError_t launch_ell(spmm_plan *p, const int32_t *d_cols, int32_t E, const voi
                        cudaStream_t s) {
     const bool bf16 = p->xdt == SPMM_BF16;
     const int32_t mb = (int32_t)(p->m / 16), kb = (int32_t)(p->k / 16);
-    cudaError_t e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), s);
+    // the status word is written by the validation launch itself (its last
+    // block) through two words of the fused re-partition's barrier area,
+    // which stay zero between calls; plans without that area clear the
+    // status first
+    int32_t *words = p->dyn.bar ? p->dyn.bar + 2 : nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!words) {
+        e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), s);
+    } else if (!p->dyn.ell_clean) {
+        e = cudaMemsetAsync(words, 0, 2 * sizeof(int32_t), s);
+        p->dyn.ell_clean = true;
+    }
     if (e != cudaSuccess) return e;
     pdl_launch(ell_validate_kernel, dim3((unsigned)((mb + 7) / 8)), dim3(256), 0, s, d_cols, mb, E,
-               kb, p->d_status);
+               kb, p->d_status, words);
     e = cudaGetLastError();
     if (e != cudaSuccess || n == 0 || p->m == 0) return e;
     if (E == 0)   // no blocks at all: Y = 0

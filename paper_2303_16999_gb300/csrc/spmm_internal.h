@@ -90,6 +90,9 @@ struct DynBufs {
     // reduction launch, or a memset after a call without a product, cleared
     // them); else the next fused launch clears them first
     bool bar_clean = false;
+    // host: bar[2..3] (the Blocked-ELL validation's flag and ticket) were
+    // zeroed once; the validation launch leaves them zero
+    bool ell_clean = false;
     int64_t items_cap = 0, ws_slots_cap = 0, red_cap = 0;
 };
 constexpr int kFusedMaxCtas = 128;           // CTAs of the fused re-partition (at most)

@@ -129,6 +129,21 @@ def test_ell_rejects_bad_layouts(bad):
     torch.cuda.synchronize()
     assert plan.status() == S.ERR_PATTERN
     assert torch.all(Y == 5.0), "Y must be left unwritten"
+    # the next calls' validation writes their status itself: a rejected call
+    # left unread, then a valid one, reads back 0 and a full Y
+    plan.run_ell(torch.from_numpy(cols).cuda(),
+                 torch.ones((16, 4, 16, 16), dtype=torch.float16, device="cuda"),
+                 torch.ones((k, n), dtype=torch.float16, device="cuda"), Y)
+    good = np.full((16, 4), -1, np.int32)
+    good[:, 0] = np.arange(16) % 16
+    good[:, 1] = (np.arange(16) + 3) % 16
+    good[:, :2].sort(axis=1)
+    Y2 = plan.run_ell(torch.from_numpy(good).cuda(),
+                      torch.ones((16, 4, 16, 16), dtype=torch.float16, device="cuda"),
+                      torch.ones((k, n), dtype=torch.float16, device="cuda"))
+    torch.cuda.synchronize()
+    assert plan.status() == 0
+    assert torch.all(Y2 == 32.0)   # two all-ones blocks per block row, 16 terms each
 
 
 def test_ell_and_csr_calls_share_a_plan():
