@@ -52,39 +52,54 @@ __device__ __forceinline__ int64_t clamp_nnzb(const int32_t *d_nnzb, int64_t cap
 // True in the one block that finishes last: every block fences its writes
 // and takes a ticket; the block that draws the last ticket fences again
 // before it reads what the others wrote.
+// The last block also puts the ticket back to zero for the next launch.
 __device__ bool last_block_done(int32_t *ticket) {
     __shared__ int is_last;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(ticket, 1) == (int)(gridDim.x - 1) ? 1 : 0;
     __syncthreads();
-    if (is_last) __threadfence();
+    if (is_last) {
+        __threadfence();
+        if (threadIdx.x == 0) *ticket = 0;
+    }
     return is_last != 0;
 }
 
-__device__ void scan_rows(const int32_t *d_nnzb, int64_t cap, int32_t mb, const int32_t *row_cnt,
+__device__ void scan_rows(const int32_t *d_nnzb, int64_t cap, int32_t mb, int32_t *row_cnt,
                           int32_t *row_ptr, int32_t *cursor, int32_t *row_ibeg, int32_t *row_wbeg,
                           int32_t *row_rbeg, int32_t *counts, int rows_items);
 
-// 1. range check and block-row histogram; the last block scans the rows
+// 1. range check and block-row histogram; the last block scans the rows.
+// The blocks record what they find in counts[kCntFlags]; the last block
+// stores the call's status from it (capacity first, then pattern, else 0)
+// and leaves the flags, the ticket and the row counts zero for the next
+// call, so that the chain needs no memsets once they start out zero.
 __global__ void __launch_bounds__(1024) dyn_validate_scan(
     const int32_t *d_nnzb, const int32_t *brow, const int32_t *bcol, int64_t cap, int32_t mb,
     int32_t kb, int32_t *row_cnt, int32_t *status, int32_t *row_ptr, int32_t *cursor,
     int32_t *row_ibeg, int32_t *row_wbeg, int32_t *row_rbeg, int32_t *counts, int rows_items) {
     pdl_enter();
     const int64_t raw = *d_nnzb;
-    if (blockIdx.x == 0 && threadIdx.x == 0 && (raw < 0 || raw > cap)) flag(status, kDevCapacity);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (raw < 0 || raw > cap))
+        atomicOr(counts + kCntFlags, 1);
     const int64_t n = raw < 0 ? 0 : (raw > cap ? cap : raw);
+    bool bad = false;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = brow[p], c = bcol[p];
         if (r < 0 || r >= mb || c < 0 || c >= kb) {
-            flag(status, kDevPattern);
+            bad = true;
             continue;
         }
         atomicAdd(&row_cnt[r], 1);
     }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(counts + kCntFlags, 2);
     if (!last_block_done(counts + kCntTicketRows)) return;
+    if (threadIdx.x == 0) {
+        const int32_t f = atomicExch(counts + kCntFlags, 0);
+        *status = (f & 1) ? (int32_t)kDevCapacity : (f & 2) ? (int32_t)kDevPattern : 0;
+    }
     scan_rows(d_nnzb, cap, mb, row_cnt, row_ptr, cursor, row_ibeg, row_wbeg, row_rbeg, counts,
               rows_items);
 }
@@ -158,7 +173,7 @@ __device__ __forceinline__ int32_t nchunks(int64_t L, int64_t C) {
 // row_ptr / cursor; for b = 1 also the row-item, workspace and reduction
 // offsets (C1 = max(64, 2 * ceil(nnzb / mb)), the static default).  One
 // block of 1024 threads (the histogram's last).
-__device__ void scan_rows(const int32_t *d_nnzb, int64_t cap, int32_t mb, const int32_t *row_cnt,
+__device__ void scan_rows(const int32_t *d_nnzb, int64_t cap, int32_t mb, int32_t *row_cnt,
                           int32_t *row_ptr, int32_t *cursor, int32_t *row_ibeg, int32_t *row_wbeg,
                           int32_t *row_rbeg, int32_t *counts, int rows_items) {
     const int64_t nnzb = clamp_nnzb(d_nnzb, cap);
@@ -168,6 +183,7 @@ __device__ void scan_rows(const int32_t *d_nnzb, int64_t cap, int32_t mb, const 
     for (int32_t r0 = 0; r0 < mb; r0 += 1024) {
         const int32_t r = r0 + threadIdx.x;
         const int64_t L = r < mb ? __ldcg(row_cnt + r) : 0;
+        if (r < mb) row_cnt[r] = 0;   // for the next call
         const int32_t nch = r < mb ? nchunks(L, C1) : 0;
         int64_t t0, t1, t2, t3;
         const int64_t e0 = block_scan(L, &t0);
@@ -1183,13 +1199,26 @@ inline unsigned grid_for(int64_t n, int threads, unsigned cap) {
 
 }  // namespace
 
+// The chain's row counts, tickets and error flags start out zero and its
+// launches leave them so (the status word is written by the first launch):
+// memsets only for a plan's first chain call, or after one that failed to
+// enqueue.
+static cudaError_t chain_prepare(spmm_plan *p, int32_t mb, cudaStream_t s) {
+    DynBufs &d = p->dyn;
+    cudaError_t e = cudaSuccess;
+    if (!d.chain_clean) {
+        e = cudaMemsetAsync(d.row_cnt, 0, sizeof(int32_t) * mb, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(p->d_counts, 0, sizeof(int32_t) * kCntCount, s);
+    }
+    d.chain_clean = false;   // until this call's launches are enqueued
+    return e;
+}
+
 cudaError_t launch_dynamic_csr(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s) {
     DynBufs &d = p->dyn;
     const int32_t mb = (int32_t)(p->m / p->b), kb = (int32_t)(p->k / p->b);
     const int64_t cap = p->nnzb_max;
-    cudaError_t e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.row_cnt, 0, sizeof(int32_t) * mb, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_counts, 0, sizeof(int32_t) * kCntCount, s);
+    cudaError_t e = chain_prepare(p, mb, s);
     if (e != cudaSuccess) return e;
     const unsigned gp = grid_for(cap, 256, 4096);
     pdl_launch(dyn_validate_scan, dim3(grid_for(cap, 1024, 1024)), dim3(1024), 0, s, dp->d_nnzb,
@@ -1200,7 +1229,9 @@ cudaError_t launch_dynamic_csr(spmm_plan *p, const spmm_dpattern *dp, cudaStream
     pdl_launch(dyn_sort_rows, dim3(grid_for((int64_t)mb * 32, 256, 1u << 30)), dim3(256), 0, s, mb,
         p->d_row_ptr, d.tmp_col, d.tmp_perm, p->d_col_idx, p->d_perm, p->d_status, 0,
         d.row_ibeg, d.row_wbeg, d.row_rbeg, p->d_counts, p->d_items, p->d_ws_row0, p->d_red);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    d.chain_clean = e == cudaSuccess;
+    return e;
 }
 
 cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cudaStream_t s) {
@@ -1208,9 +1239,7 @@ cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cuda
     const int32_t mb = (int32_t)(p->m / p->b), kb = (int32_t)(p->k / p->b);
     const int64_t cap = p->nnzb_max;
     const bool tc = p->kernel == SPMM_KERNEL_TC;
-    cudaError_t e = cudaMemsetAsync(p->d_status, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(d.row_cnt, 0, sizeof(int32_t) * mb, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p->d_counts, 0, sizeof(int32_t) * kCntCount, s);
+    cudaError_t e = chain_prepare(p, mb, s);
     if (e != cudaSuccess) return e;
     const unsigned gp = grid_for(cap, 256, 4096);
     pdl_launch(dyn_validate_scan, dim3(grid_for(cap, 1024, 1024)), dim3(1024), 0, s, dp->d_nnzb,
@@ -1233,7 +1262,9 @@ cudaError_t launch_dynamic_partition(spmm_plan *p, const spmm_dpattern *dp, cuda
             p->d_ent_tbeg, p->d_ent_cover, p->d_tile_row, p->d_blk_slot, p->d_blk_off, p->d_items,
             p->d_ws_row0, p->d_red);
     }
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    d.chain_clean = e == cudaSuccess;
+    return e;
 }
 
 

@@ -30,7 +30,8 @@ enum CountIdx : int {
     kCntChunk = 7,    // chunk size C chosen on the device
     kCntTicketRows = 8,    // blocks done with the row histogram (the last one scans)
     kCntTicketGroups = 9,  // blocks done with the group counts (the last one scans)
-    kCntCount = 10
+    kCntFlags = 10,        // errors found by the row histogram's blocks (bit 0 capacity, bit 1 pattern)
+    kCntCount = 11
 };
 
 // device status word codes (mirrors spmm_status where applicable)
@@ -93,6 +94,10 @@ struct DynBufs {
     // host: bar[2..3] (the Blocked-ELL validation's flag and ticket) were
     // zeroed once; the validation launch leaves them zero
     bool ell_clean = false;
+    // host: the launch chain's row counts, tickets and error flags are zero
+    // (the chain's own launches leave them so); else its first launch is
+    // preceded by memsets
+    bool chain_clean = false;
     int64_t items_cap = 0, ws_slots_cap = 0, red_cap = 0;
 };
 constexpr int kFusedMaxCtas = 128;           // CTAs of the fused re-partition (at most)
