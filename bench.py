@@ -243,7 +243,7 @@ def kernel_source_sha16(files=("csrc/k_tc.cu", "csrc/tc_ptx.cuh", "csrc/capi.cpp
 # of one step; the command and the per-launch table are in
 # profiles/tc_kernel_sweep_dram.md).  Used only while the kernel and planner
 # sources hash to `sha16`; otherwise the bench reports traffic null.
-SWEEP_TRAFFIC = {"sha16": "14a730801e642a1e", "bytes_per_launch": 38586912.0,
+SWEEP_TRAFFIC = {"sha16": "d203c1bc4cd1969a", "bytes_per_launch": 38571792.0,
                  "source": "profiles/tc_kernel_sweep_dram.md"}
 
 

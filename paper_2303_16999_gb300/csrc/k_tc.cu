@@ -1242,7 +1242,12 @@ int64_t stage_prog_words() { return 2 * kMmaStage; }
 cudaError_t launch_pack_tiles(const spmm_plan *p, const void *d_values, const float *d_scales,
                               const int32_t *d_nnzb, cudaStream_t s) {
     if (p->packed_bytes == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(p->d_packed, 0, p->packed_bytes, s);
+    // tiles hold several smaller blocks, static plans have zero tiles that
+    // join intervals, and E4M3 tiles carry scales: clear them first; in a
+    // dynamic plan (no joining tiles) a 16-bit 16 x 16 block fills its tile
+    cudaError_t e = cudaSuccess;
+    if (p->b < kTile || p->wdt == SPMM_E4M3 || p->mode == SPMM_STATIC)
+        e = cudaMemsetAsync(p->d_packed, 0, p->packed_bytes, s);
     if (e != cudaSuccess) return e;
     const int64_t nmax = d_nnzb ? p->nnzb_max : p->nnzb;
     const int64_t total = nmax * p->b * p->b;
