@@ -253,6 +253,20 @@ def sweep_traffic():
     return None
 
 
+# DRAM traffic of one b = 1 gather launch at n = 1 (m = k = 16384, d = 1/16,
+# L2 evicted), from one ncu capture (profiles/gather1_kernel_small_n.md);
+# used only while the gather kernels and the planner hash to `sha16`.
+GATHER_FILES = ("csrc/k_cudacore.cu", "csrc/capi.cpp", "csrc/plan_host.cpp")
+GATHER_TRAFFIC = {"sha16": "b8c2e5b5ed61398c", "bytes_per_launch": 67988992.0,
+                  "source": "profiles/gather1_kernel_small_n.md"}
+
+
+def gather_traffic():
+    if GATHER_TRAFFIC["sha16"] and GATHER_TRAFFIC["sha16"] == kernel_source_sha16(GATHER_FILES):
+        return GATHER_TRAFFIC["bytes_per_launch"]
+    return None
+
+
 def row_range(rank, world, m=M, align=16):
     """This rank's rows of a product split by rows over ``world`` GPUs:
     near-equal slices on a 16-row grid (the first ones one unit larger)."""
@@ -1017,7 +1031,10 @@ def run_gather_small_n(torch, S, wl, dev, peaks, reps=15):
     return {"workload": "b=1 gather kernel, m=k=16384, d=1/16 (16.8 M non-zeros), FP16, small n; "
                         "L2 evicted (256 MB written and read back) before every timed run",
             "points": out,
-            "roofline_n1": roofline_obj(launches[:1], peaks, "alu", kernel="gather1_kernel n=1"),
+            "roofline_n1": dict(roofline_obj(launches[:1], peaks, "alu", traffic=gather_traffic(),
+                                             kernel="gather1_kernel n=1"),
+                                traffic_source=GATHER_TRAFFIC["source"]
+                                if gather_traffic() is not None else None),
             "roofline": roofline_obj(launches, peaks, "alu", kernel="gather kernels n in {1,4,16,32}")}
 
 
